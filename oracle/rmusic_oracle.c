@@ -1,0 +1,652 @@
+/*
+ * rmusic_oracle.c -- plain, slow, FP64 CPU oracle for the per-pixel sliding-window
+ * root-MUSIC local phase-derivative path of
+ *   J. Ramaiah, S. Ajithaprasad, G. Rajshekhar, D. Ambrosini,
+ *   "Fast and robust method for flow analysis using GPU assisted diffractive optical
+ *    element based background oriented schlieren (BOS)", arXiv:1910.11872.
+ *
+ * THIS FILE IS TEST INFRASTRUCTURE. It is the independent reference that the CUDA path
+ * is checked against. Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg may build, load or call it. The product path never routes through it,
+ * and it shares no code, header, table or helper with the CUDA sources.
+ *
+ * Every step is written out in the order the paper's method takes it, in double
+ * precision, without blocking, fusion or reordering:
+ *   step 1  frame sample -> real intensity                       (image stack, Sec. 2)
+ *   step 2  analytic signal by DFT band-pass along the carrier    (Sec. 2, Eq. 1)
+ *   step 3  moving window along the derivative axis               (Sec. 3, Eq. 2-3)
+ *   step 4  sample auto-correlation matrix, optional FB average   (Sec. 3, Eq. 4-5)
+ *   step 5  eigen-decomposition, signal / noise subspaces         (Sec. 3, Eq. 6-11)
+ *   step 6  root-MUSIC polynomial coefficients                     (Sec. 3, Eq. 12-14)
+ *   step 7  all polynomial roots                                   (Sec. 3, companion / roots)
+ *   step 8  root closest to the unit circle, magnitude below one  (Sec. 3, root selection;
+ *                                                                  Algorithm 1)
+ *   step 9  angle of the root, minus the carrier                   (Sec. 3, Eq. 15)
+ *
+ * Readings taken where the paper is silent or ambiguous (each is exercised by a pin test):
+ *   - band-pass: one-sided FT band |k/W - f0| < B, 1 <= k < W/2, B = f0/2 by default;
+ *   - window: N samples starting at n - floor(N/2) along the derivative axis; a pixel whose
+ *     window leaves the line is a border pixel (output NaN);
+ *   - snapshots: the K = N - L + 1 length-L sub-vectors of the window (covariance order L);
+ *     forward-backward averaging is an option (off reproduces the plain forward estimate);
+ *   - model order 1: the noise projector is I - u1 u1^H with |u1| = 1;
+ *   - polynomial: the standard root-MUSIC continuation u(z)^H -> [1, z^-1, ..., z^-(L-1)],
+ *     giving the Laurent polynomial sum_k c_k z^k, c_k = sum_{l-m=k} C[m,l]; it is made a
+ *     polynomial of degree 2L-2 by multiplying with z^(L-1);
+ *   - selection: roots with |z| <= 1 + 1e-9 are candidates; the one minimising ||z|-1| is
+ *     taken; if another root lies within 1e-6 of it, the two are one double root split by
+ *     rounding, and the root of Q' between them is returned;
+ *   - the eigen-decomposition is a cyclic complex Jacobi iteration; the paper's SVD of the
+ *     window data yields the same subspaces.
+ *
+ * Build: gcc -std=c11 -O2 -ffp-contract=off -fPIC -shared -fopenmp rmusic_oracle.c -lm
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+#define ORC_MAXL 32
+
+/* Per-pixel status codes. */
+#define ORC_OK 0
+#define ORC_BORDER 1
+#define ORC_DEGENERATE 2
+#define ORC_NOT_CONVERGED 3
+
+/* Input sample types. */
+#define ORC_F32 0
+#define ORC_U16 1
+#define ORC_F64 2
+
+typedef struct {
+    int32_t window_len;       /* N: samples in the moving window                     */
+    int32_t cov_order;        /* L: length of a snapshot, order of the covariance     */
+    int32_t model_order;      /* p: number of exponentials per window (1 supported)   */
+    int32_t forward_backward; /* 1: average R with J conj(R) J                        */
+    int32_t deriv_axis;       /* 0: windows along x (rows), 1: along y (columns)      */
+    int32_t carrier_axis;     /* axis of the fringe carrier and of the band-pass      */
+    double carrier_freq;      /* f0, cycles per pixel                                 */
+    double band_halfwidth;    /* B, cycles per pixel; <= 0 selects f0 / 2             */
+} orc_params;
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+/* ---------------------------------------------------------------------------------
+ * Step 1 -- frame sample to a real intensity (Sec. 2: the image stack of carrier
+ * fringes). A 12-bit code is divided by 4095; any positive scale and offset leave the
+ * output unchanged because the band-pass drops DC and R only scales.
+ * ------------------------------------------------------------------------------- */
+static double orc_sample(const void* frame, int dtype, size_t idx) {
+    switch (dtype) {
+        case ORC_F32: return (double)((const float*)frame)[idx];
+        case ORC_U16: return (double)((const uint16_t*)frame)[idx] / 4095.0;
+        default: return ((const double*)frame)[idx];
+    }
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 2 -- analytic signal of one line (Sec. 2, Eq. 1: "bandpass filtering and carrier
+ * removal" turns the real fringe into Gamma = A exp(j phi) + eta).
+ * X = DFT(v) with the unnormalised forward kernel exp(-2 pi j k n / W); bins with
+ * 1 <= k < W/2 and |k/W - f0| < B are kept, all others (DC and the negative band
+ * included) are zeroed; Gamma = IDFT(X) with the 1/W factor. The carrier itself is
+ * removed after the angle (step 9): a rotation of Gamma by exp(-j 2 pi f0 n) rotates
+ * every root by the same angle.
+ * gamma is interleaved (re, im), length 2W.
+ * ------------------------------------------------------------------------------- */
+int orc_analytic_line(const double* v, int32_t W, double f0, double B, double* gamma) {
+    if (W <= 0) return -1;
+    if (B <= 0.0) B = 0.5 * f0;
+    cplx* tw = (cplx*)malloc(sizeof(cplx) * (size_t)W);
+    cplx* X = (cplx*)malloc(sizeof(cplx) * (size_t)W);
+    if (!tw || !X) { free(tw); free(X); return -2; }
+    /* tw[m] = exp(-2 pi j m / W); products k*n are reduced mod W so every twiddle is
+       evaluated from an angle in [0, 2 pi). */
+    for (int32_t m = 0; m < W; ++m) {
+        double a = 2.0 * ORC_PI * (double)m / (double)W;
+        tw[m] = cos(a) - I * sin(a);
+    }
+    for (int32_t k = 0; k < W; ++k) {
+        cplx acc = 0.0;
+        for (int32_t n = 0; n < W; ++n) acc += v[n] * tw[((int64_t)k * n) % W];
+        X[k] = acc;
+    }
+    for (int32_t k = 0; k < W; ++k) {
+        int keep = (k >= 1) && (2 * (int64_t)k < W) && (fabs((double)k / (double)W - f0) < B);
+        if (!keep) X[k] = 0.0;
+    }
+    for (int32_t n = 0; n < W; ++n) {
+        cplx acc = 0.0;
+        for (int32_t k = 0; k < W; ++k) acc += X[k] * conj(tw[((int64_t)k * n) % W]);
+        acc /= (double)W;
+        gamma[2 * n] = creal(acc);
+        gamma[2 * n + 1] = cimag(acc);
+    }
+    free(tw);
+    free(X);
+    return 0;
+}
+
+/* Analytic signal of a whole frame: one line per row (carrier_axis 0) or per column
+   (carrier_axis 1). gamma is H*W interleaved complex, row-major like the frame. */
+int orc_analytic_frame(const void* frame, int32_t dtype, int32_t H, int32_t W,
+                       int32_t carrier_axis, double f0, double B, double* gamma) {
+    int32_t nlines = carrier_axis == 0 ? H : W;
+    int32_t len = carrier_axis == 0 ? W : H;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t li = 0; li < nlines; ++li) {
+        double* v = (double*)malloc(sizeof(double) * (size_t)len);
+        double* g = (double*)malloc(sizeof(double) * 2 * (size_t)len);
+        if (!v || !g) { err = -2; free(v); free(g); continue; }
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = carrier_axis == 0 ? (size_t)li * W + n : (size_t)n * W + li;
+            v[n] = orc_sample(frame, dtype, idx);
+        }
+        orc_analytic_line(v, len, f0, B, g);
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = carrier_axis == 0 ? (size_t)li * W + n : (size_t)n * W + li;
+            gamma[2 * idx] = g[2 * n];
+            gamma[2 * idx + 1] = g[2 * n + 1];
+        }
+        free(v);
+        free(g);
+    }
+    return err;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 4 -- sample auto-correlation matrix of one window (Sec. 3, Eq. 4-5:
+ * R = E{Gamma_w Gamma_w^H} = R_s + sigma^2 I).
+ * The window w[0..N-1] yields K = N - L + 1 snapshots s_i[m] = w[i + m];
+ * R_f[m][l] = (1/K) sum_i s_i[m] conj(s_i[l]). With forward-backward averaging
+ * R = (R_f + J conj(R_f) J) / 2, i.e. R[m][l] = (R_f[m][l] + conj(R_f[L-1-m][L-1-l])) / 2.
+ * R is L*L row-major.
+ * ------------------------------------------------------------------------------- */
+void orc_covariance(const cplx* w, int32_t N, int32_t L, int32_t fb, cplx* R) {
+    int32_t K = N - L + 1;
+    cplx Rf[ORC_MAXL * ORC_MAXL];
+    for (int32_t m = 0; m < L; ++m)
+        for (int32_t l = 0; l < L; ++l) {
+            cplx acc = 0.0;
+            for (int32_t i = 0; i < K; ++i) acc += w[i + m] * conj(w[i + l]);
+            Rf[m * L + l] = acc / (double)K;
+        }
+    for (int32_t m = 0; m < L; ++m)
+        for (int32_t l = 0; l < L; ++l) {
+            if (fb)
+                R[m * L + l] = 0.5 * (Rf[m * L + l] + conj(Rf[(L - 1 - m) * L + (L - 1 - l)]));
+            else
+                R[m * L + l] = Rf[m * L + l];
+        }
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 5 -- eigen-decomposition of the Hermitian R (Sec. 3, Eq. 8-11: u1 is the
+ * eigenvector of the largest eigenvalue, the rest span the noise subspace).
+ * Cyclic complex Jacobi: for each pivot (p, q) with a_pq = |a_pq| e, the unitary G with
+ * G_pp = G_qq = c, G_pq = s e, G_qp = -s conj(e) and t = s/c the smaller root of
+ * t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 |a_pq|), annihilates a_pq in G^H A G.
+ * Sweeps repeat until the off-diagonal Frobenius norm is below 1e-14 ||R||_F.
+ * On return evals[] holds the eigenvalues (unsorted, as the diagonal ends) and column j of
+ * V (row-major L*L) the eigenvector of evals[j]. Returns the sweeps used, or -1 if 100
+ * sweeps did not converge.
+ * ------------------------------------------------------------------------------- */
+int orc_eig_hermitian(const cplx* R, int32_t L, double* evals, cplx* V) {
+    cplx A[ORC_MAXL * ORC_MAXL];
+    memcpy(A, R, sizeof(cplx) * (size_t)L * L);
+    for (int32_t r = 0; r < L; ++r)
+        for (int32_t c = 0; c < L; ++c) V[r * L + c] = (r == c) ? 1.0 : 0.0;
+    double normA = 0.0;
+    for (int32_t i = 0; i < L * L; ++i) normA += creal(A[i] * conj(A[i]));
+    normA = sqrt(normA);
+    int sweeps = 0;
+    int converged = 0;
+    for (sweeps = 0; sweeps <= 100; ++sweeps) {
+        double off = 0.0;
+        for (int32_t p = 0; p < L; ++p)
+            for (int32_t q = 0; q < L; ++q)
+                if (p != q) off += creal(A[p * L + q] * conj(A[p * L + q]));
+        off = sqrt(off);
+        if (off <= 1e-14 * normA) { converged = 1; break; }
+        if (sweeps == 100) break;
+        for (int32_t p = 0; p < L - 1; ++p)
+            for (int32_t q = p + 1; q < L; ++q) {
+                cplx b = A[p * L + q];
+                double ab = cabs(b);
+                if (ab == 0.0) continue;
+                cplx e = b / ab;
+                double tau = (creal(A[q * L + q]) - creal(A[p * L + p])) / (2.0 * ab);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double s = t * c;
+                for (int32_t r = 0; r < L; ++r) {
+                    if (r == p || r == q) continue;
+                    cplx arp = A[r * L + p], arq = A[r * L + q];
+                    A[r * L + p] = c * arp - s * conj(e) * arq;
+                    A[r * L + q] = s * e * arp + c * arq;
+                    A[p * L + r] = conj(A[r * L + p]);
+                    A[q * L + r] = conj(A[r * L + q]);
+                }
+                double app = creal(A[p * L + p]) - t * ab;
+                double aqq = creal(A[q * L + q]) + t * ab;
+                A[p * L + p] = app;
+                A[q * L + q] = aqq;
+                A[p * L + q] = 0.0;
+                A[q * L + p] = 0.0;
+                for (int32_t r = 0; r < L; ++r) {
+                    cplx vrp = V[r * L + p], vrq = V[r * L + q];
+                    V[r * L + p] = c * vrp - s * conj(e) * vrq;
+                    V[r * L + q] = s * e * vrp + c * vrq;
+                }
+            }
+    }
+    for (int32_t j = 0; j < L; ++j) evals[j] = creal(A[j * L + j]);
+    return converged ? sweeps : -1;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 6 -- root-MUSIC polynomial (Sec. 3, Eq. 12-14): with model order 1 the noise
+ * subspace projector is U_n U_n^H = C = I - u1 u1^H. On the unit circle
+ * u(z)^H C u(z) = sum_{m,l} z^-m C[m][l] z^l = sum_k c_k z^k, c_k = sum_{l-m=k} C[m][l].
+ * Multiplying by z^(L-1) gives Q(z) = sum_i q_i z^i, q_i = c_{i-(L-1)}, i = 0..2L-2.
+ * u must have unit norm. q has 2L-1 entries, q[i] multiplies z^i.
+ * ------------------------------------------------------------------------------- */
+void orc_music_poly(const cplx* u, int32_t L, cplx* q) {
+    for (int32_t i = 0; i < 2 * L - 1; ++i) q[i] = 0.0;
+    for (int32_t m = 0; m < L; ++m)
+        for (int32_t l = 0; l < L; ++l) {
+            cplx Cml = (m == l ? 1.0 : 0.0) - u[m] * conj(u[l]);
+            q[(l - m) + (L - 1)] += Cml;
+        }
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 7 -- all roots of Q (Sec. 3: the paper takes the eigenvalues of the companion
+ * matrix; any method that returns all roots gives the same set). Simultaneous
+ * Aberth-Ehrlich iteration in FP64: z_i <- z_i - w_i, w_i = N_i / (1 - N_i S_i),
+ * N_i = Q(z_i)/Q'(z_i), S_i = sum_{j != i} 1/(z_i - z_j), updated in place. A root is
+ * accepted once |Q(z_i)| <= 1e-14 sum_k |q_k| |z_i|^k (the value is at the rounding
+ * level). Exact zero leading coefficients (roots at infinity) are dropped; exact zero
+ * trailing coefficients give roots at 0.
+ * q[0..deg] ascending powers. Writes the finite roots to roots[] and returns their
+ * count; *not_conv is set when 500 iterations did not settle every root.
+ * ------------------------------------------------------------------------------- */
+static void orc_horner(const cplx* q, int32_t deg, cplx z, cplx* p, cplx* dp, double* bound) {
+    cplx pv = q[deg], dv = 0.0;
+    double b = cabs(q[deg]);
+    double az = cabs(z);
+    for (int32_t i = deg - 1; i >= 0; --i) {
+        dv = dv * z + pv;
+        pv = pv * z + q[i];
+        b = b * az + cabs(q[i]);
+    }
+    *p = pv;
+    *dp = dv;
+    *bound = b;
+}
+
+int orc_poly_roots(const cplx* q_in, int32_t deg, cplx* roots, int32_t* not_conv) {
+    cplx q[2 * ORC_MAXL];
+    *not_conv = 0;
+    while (deg > 0 && q_in[deg] == 0.0) --deg; /* roots at infinity */
+    int32_t nzero = 0;
+    while (nzero < deg && q_in[nzero] == 0.0) ++nzero; /* roots at the origin */
+    int32_t n = deg - nzero;
+    for (int32_t i = 0; i <= n; ++i) q[i] = q_in[i + nzero];
+    for (int32_t i = 0; i < nzero; ++i) roots[i] = 0.0;
+    cplx* z = roots + nzero;
+    if (n <= 0) return nzero;
+    /* Initial guesses on the circle of radius |q0/qn|^(1/n), the geometric mean of the
+       root moduli, at angles offset from the real axis. */
+    double r0 = pow(cabs(q[0]) / cabs(q[n]), 1.0 / (double)n);
+    for (int32_t i = 0; i < n; ++i) {
+        double a = 2.0 * ORC_PI * (double)i / (double)n + 0.7;
+        z[i] = r0 * (cos(a) + I * sin(a));
+    }
+    int done[2 * ORC_MAXL];
+    for (int32_t i = 0; i < n; ++i) done[i] = 0;
+    int it;
+    for (it = 0; it < 500; ++it) {
+        int active = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            if (done[i]) continue;
+            cplx p, dp;
+            double b;
+            orc_horner(q, n, z[i], &p, &dp, &b);
+            if (cabs(p) <= 1e-14 * b) { done[i] = 1; continue; }
+            active = 1;
+            if (dp == 0.0) { z[i] *= (1.0 + 1e-7 * I); continue; }
+            cplx Ni = p / dp;
+            cplx Si = 0.0;
+            for (int32_t j = 0; j < n; ++j)
+                if (j != i) Si += 1.0 / (z[i] - z[j]);
+            z[i] -= Ni / (1.0 - Ni * Si);
+        }
+        if (!active) break;
+    }
+    if (it == 500) *not_conv = 1;
+    return n + nzero;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 8 -- root selection (Sec. 3 and Algorithm 1: the root closest to the unit circle
+ * with magnitude less than one). Candidates: |z| <= 1 + 1e-9 (so that a double root lying
+ * on the circle, split by rounding, still qualifies). The candidate with the smallest
+ * ||z| - 1| wins; exact ties go to the smaller |wrap(arg z - omega_ref)|.
+ * A noise-free window makes the winner a double root (Eq. 7-8: R_s has rank one, so the
+ * polynomial touches zero on the circle). Rounding splits a double root into two roots
+ * about sqrt(eps) apart whose positions are only accurate to that level, so when another
+ * root lies within 1e-6 of the winner the pair is taken as one double root and located as
+ * the root of Q' between them (Newton on Q' from the pair's mean). Returns 0, or -1 if no
+ * candidate exists. q[0..deg] are Q's coefficients, ascending.
+ * ------------------------------------------------------------------------------- */
+static double orc_wrap(double a) {
+    while (a > ORC_PI) a -= 2.0 * ORC_PI;
+    while (a <= -ORC_PI) a += 2.0 * ORC_PI;
+    return a;
+}
+
+/* Q'(z) and Q''(z) by Horner's rule. */
+static void orc_horner_d12(const cplx* q, int32_t deg, cplx z, cplx* d1, cplx* d2) {
+    cplx p = q[deg], a1 = 0.0, a2 = 0.0;
+    for (int32_t i = deg - 1; i >= 0; --i) {
+        a2 = a2 * z + a1;
+        a1 = a1 * z + p;
+        p = p * z + q[i];
+    }
+    *d1 = a1;
+    *d2 = 2.0 * a2;
+}
+
+int orc_select_root(const cplx* q, int32_t deg, const cplx* roots, int32_t n, double omega_ref,
+                    cplx* zsel) {
+    int32_t best = -1;
+    double bestd = INFINITY, bestt = INFINITY;
+    for (int32_t i = 0; i < n; ++i) {
+        double r = cabs(roots[i]);
+        if (!(r <= 1.0 + 1e-9)) continue;
+        double d = fabs(r - 1.0);
+        double t = fabs(orc_wrap(carg(roots[i]) - omega_ref));
+        if (d < bestd || (d == bestd && t < bestt)) { best = i; bestd = d; bestt = t; }
+    }
+    if (best < 0) return -1;
+    int32_t near = -1;
+    double neard = INFINITY;
+    for (int32_t j = 0; j < n; ++j) {
+        if (j == best) continue;
+        double d = cabs(roots[j] - roots[best]);
+        if (d < neard) { neard = d; near = j; }
+    }
+    if (near < 0 || !(neard < 1e-6)) {
+        *zsel = roots[best];
+        return 0;
+    }
+    cplx z = 0.5 * (roots[best] + roots[near]);
+    for (int it = 0; it < 16; ++it) {
+        cplx d1, d2;
+        orc_horner_d12(q, deg, z, &d1, &d2);
+        if (d2 == 0.0) break;
+        cplx step = d1 / d2;
+        z -= step;
+        if (cabs(step) <= 1e-16 * cabs(z)) break;
+    }
+    /* keep the polished point only if it stayed inside the cluster */
+    if (cabs(z - roots[best]) <= 2.0 * neard)
+        *zsel = z;
+    else
+        *zsel = 0.5 * (roots[best] + roots[near]);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Steps 4-9 for one window w[0..N-1] of the analytic signal. omega_ref is the carrier
+ * phase step removed from the angle (2 pi f0 when the window runs along the carrier,
+ * else 0). Writes the derivative wrap(arg z - omega_ref) (Sec. 3, Eq. 15) and returns the
+ * status. Optional outputs (may be NULL): u1 (L), q (2L-1), roots (2L-2), zsel (1).
+ * ------------------------------------------------------------------------------- */
+int orc_window_derivative(const cplx* w, int32_t N, int32_t L, int32_t fb, double omega_ref,
+                          double* deriv, cplx* u1_out, cplx* q_out, cplx* roots_out,
+                          int32_t* nroots_out, cplx* zsel_out) {
+    cplx R[ORC_MAXL * ORC_MAXL], V[ORC_MAXL * ORC_MAXL], u[ORC_MAXL], q[2 * ORC_MAXL];
+    cplx roots[2 * ORC_MAXL];
+    double ev[ORC_MAXL];
+    *deriv = NAN;
+    if (L < 2 || L > ORC_MAXL || N < L) return ORC_DEGENERATE;
+    orc_covariance(w, N, L, fb, R);
+    double normR = 0.0;
+    for (int32_t i = 0; i < L * L; ++i) normR += creal(R[i] * conj(R[i]));
+    if (!(normR > 0.0)) return ORC_DEGENERATE;
+    int sweeps = orc_eig_hermitian(R, L, ev, V);
+    int status = sweeps < 0 ? ORC_NOT_CONVERGED : ORC_OK;
+    /* largest and second largest eigenvalue */
+    int32_t j1 = 0;
+    for (int32_t j = 1; j < L; ++j)
+        if (ev[j] > ev[j1]) j1 = j;
+    double l2 = -INFINITY;
+    for (int32_t j = 0; j < L; ++j)
+        if (j != j1 && ev[j] > l2) l2 = ev[j];
+    if (!(ev[j1] - l2 > 1e-12 * ev[j1])) return ORC_DEGENERATE;
+    double nu = 0.0;
+    for (int32_t m = 0; m < L; ++m) nu += creal(V[m * L + j1] * conj(V[m * L + j1]));
+    nu = sqrt(nu);
+    for (int32_t m = 0; m < L; ++m) u[m] = V[m * L + j1] / nu;
+    orc_music_poly(u, L, q);
+    int32_t nc = 0;
+    int32_t nr = orc_poly_roots(q, 2 * L - 2, roots, &nc);
+    if (nc) status = ORC_NOT_CONVERGED;
+    cplx z;
+    if (orc_select_root(q, 2 * L - 2, roots, nr, omega_ref, &z) != 0) return ORC_DEGENERATE;
+    *deriv = orc_wrap(carg(z) - omega_ref);
+    if (u1_out) memcpy(u1_out, u, sizeof(cplx) * (size_t)L);
+    if (q_out) memcpy(q_out, q, sizeof(cplx) * (size_t)(2 * L - 1));
+    if (roots_out) memcpy(roots_out, roots, sizeof(cplx) * (size_t)nr);
+    if (nroots_out) *nroots_out = nr;
+    if (zsel_out) *zsel_out = z;
+    return status;
+}
+
+/* ctypes-friendly form of the above: complex arrays interleaved (re, im). */
+int orc_window_derivative_ri(const double* w_ri, int32_t N, int32_t L, int32_t fb,
+                             double omega_ref, double* deriv, double* u1_ri, double* q_ri,
+                             double* roots_ri, int32_t* nroots, double* zsel_ri) {
+    cplx w[4096];
+    if (N > 4096) return ORC_DEGENERATE;
+    for (int32_t i = 0; i < N; ++i) w[i] = w_ri[2 * i] + I * w_ri[2 * i + 1];
+    cplx u[ORC_MAXL], q[2 * ORC_MAXL], r[2 * ORC_MAXL], z = 0.0;
+    int32_t nr = 0;
+    int st = orc_window_derivative(w, N, L, fb, omega_ref, deriv, u, q, r, &nr, &z);
+    if (u1_ri) for (int32_t i = 0; i < L; ++i) { u1_ri[2 * i] = creal(u[i]); u1_ri[2 * i + 1] = cimag(u[i]); }
+    if (q_ri) for (int32_t i = 0; i < 2 * L - 1; ++i) { q_ri[2 * i] = creal(q[i]); q_ri[2 * i + 1] = cimag(q[i]); }
+    if (roots_ri) for (int32_t i = 0; i < nr; ++i) { roots_ri[2 * i] = creal(r[i]); roots_ri[2 * i + 1] = cimag(r[i]); }
+    if (nroots) *nroots = nr;
+    if (zsel_ri) { zsel_ri[0] = creal(z); zsel_ri[1] = cimag(z); }
+    return st;
+}
+
+/* ctypes-friendly wrappers for the individual steps (used by the pin tests). */
+void orc_covariance_ri(const double* w_ri, int32_t N, int32_t L, int32_t fb, double* R_ri) {
+    cplx w[4096], R[ORC_MAXL * ORC_MAXL];
+    for (int32_t i = 0; i < N && i < 4096; ++i) w[i] = w_ri[2 * i] + I * w_ri[2 * i + 1];
+    orc_covariance(w, N, L, fb, R);
+    for (int32_t i = 0; i < L * L; ++i) { R_ri[2 * i] = creal(R[i]); R_ri[2 * i + 1] = cimag(R[i]); }
+}
+
+int orc_eig_hermitian_ri(const double* R_ri, int32_t L, double* evals, double* V_ri) {
+    cplx R[ORC_MAXL * ORC_MAXL], V[ORC_MAXL * ORC_MAXL];
+    for (int32_t i = 0; i < L * L; ++i) R[i] = R_ri[2 * i] + I * R_ri[2 * i + 1];
+    int s = orc_eig_hermitian(R, L, evals, V);
+    for (int32_t i = 0; i < L * L; ++i) { V_ri[2 * i] = creal(V[i]); V_ri[2 * i + 1] = cimag(V[i]); }
+    return s;
+}
+
+void orc_music_poly_ri(const double* u_ri, int32_t L, double* q_ri) {
+    cplx u[ORC_MAXL], q[2 * ORC_MAXL];
+    for (int32_t i = 0; i < L; ++i) u[i] = u_ri[2 * i] + I * u_ri[2 * i + 1];
+    orc_music_poly(u, L, q);
+    for (int32_t i = 0; i < 2 * L - 1; ++i) { q_ri[2 * i] = creal(q[i]); q_ri[2 * i + 1] = cimag(q[i]); }
+}
+
+int orc_poly_roots_ri(const double* q_ri, int32_t deg, double* roots_ri, int32_t* not_conv) {
+    cplx q[2 * ORC_MAXL], r[2 * ORC_MAXL];
+    if (deg >= 2 * ORC_MAXL) return -1;
+    for (int32_t i = 0; i <= deg; ++i) q[i] = q_ri[2 * i] + I * q_ri[2 * i + 1];
+    int32_t n = orc_poly_roots(q, deg, r, not_conv);
+    for (int32_t i = 0; i < n; ++i) { roots_ri[2 * i] = creal(r[i]); roots_ri[2 * i + 1] = cimag(r[i]); }
+    return n;
+}
+
+int orc_select_root_ri(const double* q_ri, int32_t deg, const double* roots_ri, int32_t n,
+                       double omega_ref, double* zsel_ri) {
+    cplx q[2 * ORC_MAXL], r[2 * ORC_MAXL], z = 0.0;
+    if (deg >= 2 * ORC_MAXL || n > 2 * ORC_MAXL) return -1;
+    for (int32_t i = 0; i <= deg; ++i) q[i] = q_ri[2 * i] + I * q_ri[2 * i + 1];
+    for (int32_t i = 0; i < n; ++i) r[i] = roots_ri[2 * i] + I * roots_ri[2 * i + 1];
+    int s = orc_select_root(q, deg, r, n, omega_ref, &z);
+    zsel_ri[0] = creal(z);
+    zsel_ri[1] = cimag(z);
+    return s;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 3 plus steps 4-9 over the pixels of one frame whose analytic signal gamma (H*W
+ * interleaved complex, row-major) is given. The window of the pixel at position n of its
+ * line along the derivative axis covers n - floor(N/2) .. n - floor(N/2) + N - 1; if that
+ * leaves the line the pixel is a border pixel (Sec. 4: border pixels are neglected).
+ * ------------------------------------------------------------------------------- */
+static int orc_pixel(const double* gamma, int32_t H, int32_t W, const orc_params* p,
+                     int32_t y, int32_t x, double* out) {
+    int32_t N = p->window_len;
+    int32_t len = p->deriv_axis == 0 ? W : H;
+    int32_t n = p->deriv_axis == 0 ? x : y;
+    int32_t start = n - N / 2;
+    *out = NAN;
+    if (start < 0 || start + N - 1 > len - 1) return ORC_BORDER;
+    if (p->model_order != 1) return ORC_DEGENERATE;
+    cplx w[4096];
+    if (N > 4096) return ORC_DEGENERATE;
+    for (int32_t i = 0; i < N; ++i) {
+        size_t idx = p->deriv_axis == 0 ? (size_t)y * W + (size_t)(start + i)
+                                        : (size_t)(start + i) * W + (size_t)x;
+        w[i] = gamma[2 * idx] + I * gamma[2 * idx + 1];
+    }
+    double omega_ref = p->deriv_axis == p->carrier_axis ? 2.0 * ORC_PI * p->carrier_freq : 0.0;
+    return orc_window_derivative(w, N, p->cov_order, p->forward_backward, omega_ref, out,
+                                 NULL, NULL, NULL, NULL, NULL);
+}
+
+/* Whole-frame demodulation: derivative map out[H*W] (NaN where undefined) and status[H*W]
+   (may be NULL). nthreads > 0 sets the OpenMP thread count. Returns the thread count
+   used, or a negative value on error. */
+int orc_demodulate(const void* frame, int32_t dtype, int32_t H, int32_t W, const orc_params* p,
+                   double* out, uint8_t* status, int32_t nthreads) {
+    if (H <= 0 || W <= 0 || p->window_len < 2 || p->cov_order < 2 ||
+        p->cov_order > ORC_MAXL || p->cov_order > p->window_len)
+        return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    double* gamma = (double*)malloc(sizeof(double) * 2 * (size_t)H * W);
+    if (!gamma) return -2;
+    double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
+    int err = orc_analytic_frame(frame, dtype, H, W, p->carrier_axis, p->carrier_freq, B, gamma);
+    if (err) { free(gamma); return err; }
+    int used = 1;
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t y = 0; y < H; ++y) {
+#ifdef _OPENMP
+        if (y == 0) used = omp_get_num_threads();
+#endif
+        for (int32_t x = 0; x < W; ++x) {
+            double d;
+            int st = orc_pixel(gamma, H, W, p, y, x, &d);
+            out[(size_t)y * W + x] = d;
+            if (status) status[(size_t)y * W + x] = (uint8_t)st;
+        }
+    }
+    free(gamma);
+    return used;
+}
+
+/* Sampled demodulation: only the listed pixels (ys[i], xs[i]) are computed. Only the
+   lines the samples need are band-passed. Returns the thread count used, or < 0. */
+int orc_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, int32_t W,
+                          const orc_params* p, int32_t npix, const int32_t* ys,
+                          const int32_t* xs, double* out, uint8_t* status, int32_t nthreads) {
+    if (H <= 0 || W <= 0 || p->window_len < 2 || p->cov_order < 2 ||
+        p->cov_order > ORC_MAXL || p->cov_order > p->window_len)
+        return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    int32_t ca = p->carrier_axis;
+    int32_t nlines = ca == 0 ? H : W;
+    int32_t len = ca == 0 ? W : H;
+    double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
+    /* mark the carrier lines every sample's window touches */
+    uint8_t* need = (uint8_t*)calloc((size_t)nlines, 1);
+    double* gamma = (double*)calloc(2 * (size_t)H * W, sizeof(double));
+    if (!need || !gamma) { free(need); free(gamma); return -2; }
+    int32_t N = p->window_len;
+    for (int32_t i = 0; i < npix; ++i) {
+        int32_t y = ys[i], x = xs[i];
+        if (y < 0 || y >= H || x < 0 || x >= W) { free(need); free(gamma); return -1; }
+        for (int32_t k = -N; k <= N; ++k) {
+            /* lines crossed by the window: along the derivative axis when it differs
+               from the carrier axis, otherwise the sample's own line */
+            int32_t li;
+            if (p->deriv_axis == ca) li = ca == 0 ? y : x;
+            else li = (ca == 0 ? y : x) + k;
+            if (li >= 0 && li < nlines) need[li] = 1;
+        }
+    }
+    int used = 1;
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t li = 0; li < nlines; ++li) {
+#ifdef _OPENMP
+        if (li == 0) used = omp_get_num_threads();
+#endif
+        if (!need[li]) continue;
+        double* v = (double*)malloc(sizeof(double) * (size_t)len);
+        double* g = (double*)malloc(sizeof(double) * 2 * (size_t)len);
+        if (!v || !g) { free(v); free(g); continue; }
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = ca == 0 ? (size_t)li * W + n : (size_t)n * W + li;
+            v[n] = orc_sample(frame, dtype, idx);
+        }
+        orc_analytic_line(v, len, p->carrier_freq, B, g);
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = ca == 0 ? (size_t)li * W + n : (size_t)n * W + li;
+            gamma[2 * idx] = g[2 * n];
+            gamma[2 * idx + 1] = g[2 * n + 1];
+        }
+        free(v);
+        free(g);
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t i = 0; i < npix; ++i) {
+        double d;
+        int st = orc_pixel(gamma, H, W, p, ys[i], xs[i], &d);
+        out[i] = d;
+        if (status) status[i] = (uint8_t)st;
+    }
+    free(need);
+    free(gamma);
+    return used;
+}
+
+/* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

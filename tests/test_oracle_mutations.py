@@ -1,0 +1,77 @@
+"""Planted mistakes: each test copies the oracle's C source, plants one plausible error (a dropped
+conjugate, a transposed operand, a wrong index or sign), compiles the copy on the CPU and checks
+that the pins in test_oracle_pins.py reject it. This shows the pins constrain every step of the
+oracle rather than only re-running it."""
+import numpy as np
+import pytest
+
+import oracle as O
+import test_oracle_pins as P
+
+MUTATIONS = {
+    "band: negative side kept": ("fabs((double)k / (double)W - f0) < B", "fabs((double)k / (double)W + f0) < B"),
+    "band: inverse kernel not conjugated": ("acc += X[k] * conj(tw[((int64_t)k * n) % W]);",
+                                            "acc += X[k] * tw[((int64_t)k * n) % W];"),
+    "band: 1/W dropped": ("acc /= (double)W;", "acc /= 1.0;"),
+    "cov: conjugate dropped": ("acc += w[i + m] * conj(w[i + l]);", "acc += w[i + m] * w[i + l];"),
+    "cov: operands transposed": ("acc += w[i + m] * conj(w[i + l]);", "acc += conj(w[i + m]) * w[i + l];"),
+    "cov: last snapshot dropped": ("for (int32_t i = 0; i < K; ++i) acc +=", "for (int32_t i = 0; i < K - 1; ++i) acc +="),
+    "cov: FB index not reversed": ("conj(Rf[(L - 1 - m) * L + (L - 1 - l)])", "conj(Rf[m * L + l])"),
+    "eig: rotation phase not conjugated": ("A[r * L + p] = c * arp - s * conj(e) * arq;", "A[r * L + p] = c * arp - s * e * arq;"),
+    "eig: eigenvector update sign": ("V[r * L + q] = s * e * vrp + c * vrq;", "V[r * L + q] = -s * e * vrp + c * vrq;"),
+    "eig: diagonal update sign": ("double app = creal(A[p * L + p]) - t * ab;", "double app = creal(A[p * L + p]) + t * ab;"),
+    "poly: lag index transposed": ("q[(l - m) + (L - 1)] += Cml;", "q[(m - l) + (L - 1)] += Cml;"),
+    "poly: projector sign": ("cplx Cml = (m == l ? 1.0 : 0.0) - u[m] * conj(u[l]);", "cplx Cml = (m == l ? 1.0 : 0.0) + u[m] * conj(u[l]);"),
+    "roots: Aberth sum sign": ("z[i] -= Ni / (1.0 - Ni * Si);", "z[i] -= Ni / (1.0 + Ni * Si);"),
+    "select: outside roots": ("if (!(r <= 1.0 + 1e-9)) continue;", "if (!(r >= 1.0 - 1e-9)) continue;"),
+    "select: farthest root": ("if (d < bestd || (d == bestd && t < bestt))", "if (-d < bestd || (d == bestd && t < bestt))"),
+    "angle: carrier added": ("*deriv = orc_wrap(carg(z) - omega_ref);", "*deriv = orc_wrap(carg(z) + omega_ref);"),
+    "window: off by one": ("int32_t start = n - N / 2;", "int32_t start = n - N / 2 + 1;"),
+    "eig: smallest eigenvector": ("if (ev[j] > ev[j1]) j1 = j;", "if (ev[j] < ev[j1]) j1 = j;"),
+}
+
+PINS = [
+    lambda: P.test_analytic_line_matches_fft_bandpass(128),
+    P.test_analytic_line_closed_form_periodic_cosine,
+    lambda: P.test_covariance_rank_one_for_exponential(32, 8, 0),
+    lambda: P.test_covariance_rank_one_for_exponential(32, 8, 1),
+    P.test_covariance_structure_noise,
+    lambda: P.test_eig_matches_lapack(8),
+    P.test_eig_eigenvalues_signal_plus_noise,
+    lambda: P.test_music_poly_on_circle_equals_noise_projection(8),
+    P.test_music_poly_closed_form_steering_vector,
+    lambda: P.test_roots_match_companion_matrix(3),
+    P.test_selection_hand_cases,
+    lambda: P.test_p1_noise_free_linear_phase_exact(32, 8, 1),
+    lambda: P.test_p2_order_two_is_pulse_pair(1),
+    P.test_p4_carrier_rotation,
+    P.test_p7_noisy_selection_by_enumeration,
+]
+
+
+def _failing_pins():
+    failed = []
+    for i, pin in enumerate(PINS):
+        try:
+            with np.errstate(all="ignore"):
+                pin()
+        except Exception:  # an AssertionError, or a crash of the mutated code path
+            failed.append(i)
+    return failed
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = O.source()
+    assert src.count(old) >= 1, f"mutation anchor not found: {old}"
+    path = O.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_mut.so"))
+    with O.use_library(path):
+        failed = _failing_pins()
+    assert failed, f"no pin rejects the planted mistake '{name}'"
+
+
+def test_unmutated_copy_passes(tmp_path):
+    path = O.compile_variant(O.source(), str(tmp_path / "liboracle_copy.so"))
+    with O.use_library(path):
+        assert _failing_pins() == []
