@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Throughput of sliding-window root-MUSIC phase-derivative maps (arXiv:1910.11872) on GB300.
+
+One step = the FP32-batched path over one batch of four 1024 x 1024 float32 fringe frames,
+carrier 0.1 cycles/px, phase = peaks surface scaled to 0-10 rad, one frame per SNR of the sweep
+40 / 20 / 10 / 5 dB; window N = 32, covariance order L = 8, forward-backward, derivative along x.
+
+Printed: one JSON line (rank 0) with the device-timed value (inputs resident in HBM, L2 flushed
+between steps), the end-to-end value through the host-buffer C entry point, the plain
+thread-per-pixel path on the same GPU, the dominant kernel's roofline, the FP64 CPU oracle timed on
+a bounded sample (and the element-wise error of the GPU maps against it), launch counts and the
+SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs an independent replica (its own frames, no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1910_11872_gb300 import synth  # noqa: E402
+
+METRIC = "Mpixel/s root-MUSIC phase-derivative, FP32-batched vs plain on same GB300"
+SNRS = (40.0, 20.0, 10.0, 5.0)
+H = W = 1024
+F0 = 0.1
+N_WIN, L_COV = 32, 8
+WORKLOAD = (f"peaks phase 0-10 rad, {len(SNRS)} x {H}x{W} float32 frames per step (SNR 40/20/10/5 dB), "
+            f"carrier {F0} cyc/px, N={N_WIN}, L={L_COV}, forward-backward, derivative along x")
+# FP32 issue peak of the part: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz (maximum SM clock)
+N_SM, FP32_LANES, MAX_SM_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * MAX_SM_GHZ / 1e3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-rows", type=int, default=16, help="rows per frame in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def frames_for(rank: int):
+    return [synth.peaks_frame(s, F0, H, W, stream=rank) for s in SNRS]
+
+
+def flops_per_pixel(L: int, N: int, sweeps: float, iters: float) -> float:
+    """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1)."""
+    NS = L * (L + 1) // 2
+    NR = 2 * L - 2
+    h = L // 2
+    cov = L * (31 + N) / 32 * (6 + 2) + NS * 4 + h * h * 8
+    rot = 14 + 6 * (L - 2)
+    jac = sweeps * (L * (L - 1) // 2 * rot + L * (L - 1))
+    ldl = sum(3 * j + (L - 1 - j) * (3 * j + 1) for j in range(L))
+    inv = ldl + 2 * (2 * L * (L - 1) + 4 * L)
+    coef = 8 * L * (L - 1) // 2 + 3 * L + 2 * L
+    aberth = iters * NR * (16 * NR + 2 * NR + 10 * (NR - 1) + 30)
+    polish = 2 * (24 * NR + 30) + 20
+    return cov + jac + inv + coef + aberth + polish
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        busy = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)]
+        return {"sm_mhz": statistics.median(busy or sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(frames, rows_per_frame: int):
+    import oracle as O
+
+    p = O.make_params(N_WIN, L_COV, 1, 0, 0, F0)
+    rng = np.random.default_rng(11872)
+    samples = []
+    t0 = time.perf_counter()
+    cores = 0
+    npx = 0
+    for fr in frames:
+        rows = np.sort(rng.choice(H, rows_per_frame, replace=False))
+        ys = np.repeat(rows, W).astype(np.int32)
+        xs = np.tile(np.arange(W), rows_per_frame).astype(np.int32)
+        vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
+        samples.append((ys, xs, vals, st))
+        npx += ys.size
+    dt = time.perf_counter() - t0
+    return samples, npx, dt, cores
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    frames = frames_for(0)
+    rows = max(1, args.cpu_rows // 4)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(frames[:1], 1)
+    times, npx_step, cores = [], 0, 0
+    for _ in range(args.steps):
+        _, npx_step, dt, cores = oracle_sample(frames, rows)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    value = npx_step / (ms * 1e3)
+    sample = f"{rows} random full rows of each of the {len(frames)} frames ({npx_step} px) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "oracle": "FP64 C, OpenMP over pixels"},
+            "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# GPU arms
+# ----------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_1910_11872_gb300 import rmusic
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    frames = frames_for(rank)
+    host = np.stack([f.image for f in frames]).astype(np.float32)
+    x = torch.from_numpy(host).to(dev)
+    npx = host.size
+    out = torch.empty(npx, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    # ---- FP32-batched path (persistent launch, CUDA graph) ------------------------------------
+    dem = rmusic.Demodulator(device=local, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0,
+                             precision="batched", use_graph=1, timing=1)
+    for _ in range(args.warmup):
+        dem.run(x, out=out, with_status=False)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    solver_ms, bandpass_ms, launches, sweeps, iters = [], [], 0, [], []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        dem.run(x, out=out, with_status=False, stream=stream)
+        ev[k][1].record(stream)
+        st = dem.stats()  # waits for the call; reads the event-timed kernel durations
+        solver_ms.append(st.solver_ms)
+        bandpass_ms.append(st.bandpass_ms)
+        launches += st.kernel_launches
+        sweeps.append(st.mean_sweeps)
+        iters.append(st.mean_root_iters)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    step_ms_max = max_over_ranks(world, step_ms)
+    value = npx * world / (step_ms_max * 1e3)
+    result_gpu = out.view(len(frames), H, W).cpu().numpy()
+
+    # ---- plain path on the same GPU (thread per pixel, one launch per frame) -------------------
+    plain = rmusic.Demodulator(device=local, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0,
+                               precision="plain_fp32", timing=1)
+    plain.run(x, out=out, with_status=False)
+    torch.cuda.synchronize()
+    pms = []
+    for _ in range(args.plain_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plain.run(x, out=out, with_status=False, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms.append(a.elapsed_time(b))
+    plain_ms = max_over_ranks(world, statistics.mean(pms))
+    plain_value = npx * world / (plain_ms * 1e3)
+    plain.close()
+
+    # ---- end to end through the host-buffer entry point -----------------------------------------
+    hin = torch.from_numpy(host.reshape(-1)).pin_memory()
+    hout = torch.empty(npx, dtype=torch.float32).pin_memory()
+    descs, nbytes, nout = rmusic.frame_descs([(H, W)] * len(frames), rmusic.RMUSIC_DTYPE_F32, 4)
+    e2e_dem = rmusic.Demodulator(device=local, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0,
+                                 precision="batched", use_graph=1)
+    for _ in range(2):
+        rmusic.rmusic_demodulate_frames_host(e2e_dem.ctx, hin.data_ptr(), nbytes, descs, len(frames),
+                                             hout.data_ptr(), None, stream.cuda_stream)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        rmusic.rmusic_demodulate_frames_host(e2e_dem.ctx, hin.data_ptr(), nbytes, descs, len(frames),
+                                             hout.data_ptr(), None, stream.cuda_stream)
+    e2e_ms = max_over_ranks(world, 1e3 * (time.perf_counter() - t0) / args.e2e_steps)
+    e2e_launches = e2e_dem.stats().kernel_launches
+    e2e_dem.close()
+    e2e_value = npx * world / (e2e_ms * 1e3)
+
+    # ---- roofline of the dominant kernel (batched solver) ---------------------------------------
+    fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(iters))
+    solver_avg = statistics.mean(solver_ms)
+    achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "batched_solver_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "batched_kernel<8>", "flops_per_pixel": fpp, "launch_ms": solver_avg,
+                "peak_note": "FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
+                "mean_jacobi_sweeps": statistics.mean(sweeps), "mean_root_iters": statistics.mean(iters),
+                "bandpass_ms": statistics.mean(bandpass_ms)}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step": len(frames), "pixels_per_step": npx,
+                       "l2": "flushed between steps (256 MiB write)", "cuda_graph": True,
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": int(host.nbytes),
+                    "d2h_bytes_per_step": int(npx * 4), "ms_per_step": e2e_ms, "kernels_per_step": e2e_launches},
+            "gpu_launches": launches, "clocks": clk,
+            "plain": {"value": plain_value, "unit": "Mpixel/s", "ms_per_step": plain_ms,
+                      "path": "plain FP32, thread per pixel, one launch per frame"},
+            "speedup_vs_plain": value / plain_value}
+
+    # ---- CPU oracle on a bounded sample, and the GPU error against it -----------------------
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        samples, n_or, dt, cores = oracle_sample(frames, args.cpu_rows)
+        line["cpu_baseline"] = {"value": n_or / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_rows} random full rows of each frame ({n_or} px), "
+                                          f"{dt:.1f} s wall"}
+        acc = {}
+        for snr, fr, g, (ys, xs, vals, st) in zip(SNRS, frames, result_gpu, samples):
+            gv = g[ys, xs].astype(np.float64)
+            ok = (st == 0) & np.isfinite(gv)
+            d = np.abs(gv[ok] - vals[ok])
+            inner = ok & (xs >= 32) & (xs < W - 32)
+            rms_o = float(np.sqrt(np.mean((vals[inner] - fr.truth[ys[inner], xs[inner]]) ** 2)))
+            rms_g = float(np.sqrt(np.mean((gv[inner] - fr.truth[ys[inner], xs[inner]]) ** 2)))
+            acc[f"{int(snr)}dB"] = {"max_abs_rad_px": float(d.max()), "p999_rad_px": float(np.quantile(d, 0.999)),
+                                    "rms_vs_truth_gpu": rms_g, "rms_vs_truth_oracle": rms_o,
+                                    "rms_rel_diff": abs(rms_g - rms_o) / rms_o}
+        line["accuracy_vs_fp64_oracle"] = acc
+    dem.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * rmusic.h -- C ABI of the GB300 (sm_103a) sliding-window root-MUSIC phase-derivative library.
+ *
+ * The library turns a stack of carrier-fringe frames into per-pixel local phase-derivative
+ * maps with the root-MUSIC estimator of Ramaiah, Ajithaprasad, Rajshekhar and Ambrosini,
+ * "Fast and robust method for flow analysis using GPU assisted diffractive optical element
+ * based background oriented schlieren (BOS)", arXiv:1910.11872:
+ *   - analytic signal of each line by band-pass filtering       (Sec. 2, Eq. 1)
+ *   - moving window and local linear-phase model                  (Sec. 3, Eq. 2-3)
+ *   - sample auto-correlation matrix R of the window               (Sec. 3, Eq. 4-5)
+ *   - signal eigenvector u1 and noise subspace                     (Sec. 3, Eq. 6-11)
+ *   - root-MUSIC polynomial of the noise projector                 (Sec. 3, Eq. 12-14)
+ *   - the root nearest the unit circle with |z| <= 1               (Sec. 3; Algorithm 1)
+ *   - its angle, minus the carrier, is the phase derivative        (Sec. 3, Eq. 15)
+ *
+ * Conventions shared by every entry point:
+ *   - All functions are plain C, callable from any language; no C++ exceptions cross them.
+ *   - Return codes: RMUSIC_OK (0) or a negative RMUSIC_E* value; rmusic_strerror() names it.
+ *   - "Device pointer" means memory of the context's CUDA device (cudaMalloc, a PyTorch
+ *     tensor's data_ptr(), ...). The caller owns every pointer it passes; the library only
+ *     reads inputs and writes outputs during the call's stream-ordered execution.
+ *   - The library owns its workspaces, graphs and tables, all released by rmusic_destroy.
+ *   - Work is queued asynchronously on the caller's stream (cudaStream_t passed as void*;
+ *     NULL = the legacy default stream); results are valid once that stream reaches the
+ *     point after the call.
+ *   - A context is not thread-safe: use one per host thread. Calls on one context share its
+ *     workspace, so they must be ordered (one stream, or synchronised between streams).
+ */
+#ifndef RMUSIC_H
+#define RMUSIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------------------------- */
+#define RMUSIC_OK 0
+#define RMUSIC_EINVAL (-1)       /* an argument is out of range or inconsistent             */
+#define RMUSIC_ENOMEM (-2)       /* a workspace would exceed the HBM budget / cudaMalloc failed */
+#define RMUSIC_EUNSUPPORTED (-3) /* a valid request this build does not implement           */
+#define RMUSIC_ETIMEDOUT (-4)    /* a bounded device-side wait gave up                      */
+#define RMUSIC_ECUDA (-5)        /* a CUDA runtime call failed (see rmusic_last_cuda_error)   */
+
+/* ---- execution paths (rmusic_params.precision) ----------------------------------------- */
+#define RMUSIC_PLAIN_FP64 0   /* thread per pixel, FP64 throughout, one launch per frame     */
+#define RMUSIC_PLAIN_FP32 1   /* thread per pixel, FP32 throughout, one launch per frame     */
+#define RMUSIC_FP32_BATCHED 2 /* persistent warp-scheduled FP32 kernel over all frames       */
+
+/* ---- input sample types (rmusic_frame_desc.dtype) -------------------------------------- */
+#define RMUSIC_DTYPE_F32 0 /* float32 intensity                                             */
+#define RMUSIC_DTYPE_U16 1 /* uint16 camera code (e.g. 12-bit); any scale gives the same map */
+
+/* ---- per-pixel status codes (optional uint8 map) --------------------------------------- */
+#define RMUSIC_STATUS_OK 0
+#define RMUSIC_STATUS_BORDER 1        /* the window leaves the line: derivative is NaN      */
+#define RMUSIC_STATUS_DEGENERATE 2    /* R is zero or its top eigenvalue is not separated   */
+#define RMUSIC_STATUS_NOT_CONVERGED 3 /* an iteration cap was hit; best estimate is stored  */
+
+/* Parameters of the estimator (Sec. 3) and of the execution path.
+ *   window_len       N, samples in the moving window along deriv_axis (2 <= N <= 64). The
+ *                    window of the pixel at position n covers n - N/2 .. n - N/2 + N - 1
+ *                    (integer N/2); pixels whose window leaves the line are border pixels.
+ *   cov_order        L, length of the snapshots s_i = w[i .. i+L-1], i = 0 .. N-L, and order of
+ *                    the L x L auto-correlation matrix (2 <= L <= 12, L <= N). The batched path
+ *                    takes even L with forward_backward = 1; other cases need a plain path.
+ *   model_order      number of complex exponentials per window; the method uses 1 (Eq. 2).
+ *   forward_backward 1: R = (R_f + J conj(R_f) J) / 2 (forward-backward average); 0: R = R_f.
+ *   deriv_axis       0: windows run along x (rows); 1: along y (columns).
+ *   carrier_axis     axis of the carrier and of the band-pass (0 = x, 1 = y).
+ *   carrier_freq     f0 in cycles/pixel; the band keeps 1 <= k < len/2 with |k/len - f0| < B,
+ *                    and 2 pi f0 is subtracted from the angle when deriv_axis == carrier_axis.
+ *   band_halfwidth   B in cycles/pixel; <= 0 selects f0 / 2.
+ *   precision        RMUSIC_PLAIN_FP64, RMUSIC_PLAIN_FP32 or RMUSIC_FP32_BATCHED.
+ *   max_sweeps       cap on Jacobi sweeps (0 = default: 30 plain, 6 batched).
+ *   max_root_iters   cap on root iterations (0 = default: 500 plain, 16 batched).
+ *   polish_fp64      batched path only: 1 adds one FP64 Newton step on the selected root.
+ *   use_graph        batched path only: 1 captures the whole call in a CUDA graph and replays
+ *                    it when the same frames, tables and outputs are passed again.
+ *   timing           1: record CUDA events around every kernel of a call on its stream, so that
+ *                    rmusic_get_stats() can report the device time of each stage.
+ */
+typedef struct {
+    int32_t window_len;
+    int32_t cov_order;
+    int32_t model_order;
+    int32_t forward_backward;
+    int32_t deriv_axis;
+    int32_t carrier_axis;
+    double carrier_freq;
+    double band_halfwidth;
+    int32_t precision;
+    int32_t max_sweeps;
+    int32_t max_root_iters;
+    int32_t polish_fp64;
+    int32_t use_graph;
+    int32_t timing;
+} rmusic_params;
+
+/* One frame of a batch. Frames of one call may differ in size, type and window.
+ *   offset_bytes  byte offset of the frame's first sample from the base input pointer.
+ *   height/width  H, W in pixels (>= 1).
+ *   pitch_elems   elements between the starts of consecutive rows (>= width; 0 = width).
+ *   dtype         RMUSIC_DTYPE_F32 or RMUSIC_DTYPE_U16. offset_bytes and pitch must keep
+ *                 every sample naturally aligned.
+ *   out_offset    element offset of the frame's dense H x W float32 map (row-major) in the
+ *                 output buffer, and of its H x W uint8 map in the status buffer.
+ *   window_len, cov_order  per-frame N and L; 0 = the context's parameters.
+ */
+typedef struct {
+    uint64_t offset_bytes;
+    int32_t height;
+    int32_t width;
+    int32_t pitch_elems;
+    int32_t dtype;
+    uint64_t out_offset;
+    int32_t window_len;
+    int32_t cov_order;
+} rmusic_frame_desc;
+
+typedef struct rmusic_ctx rmusic_ctx;
+
+/* Create a context on CUDA device `device` with the given parameters. hbm_budget_bytes caps
+ * the device memory the library may allocate for its workspaces (0 = no cap); calls whose
+ * workspace would exceed it are split into smaller batches, or fail with RMUSIC_ENOMEM if a
+ * single frame does not fit. On success *out receives the context. Errors: RMUSIC_EINVAL
+ * (bad parameters, out == NULL), RMUSIC_EUNSUPPORTED (model_order != 1), RMUSIC_ECUDA. */
+int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_bytes,
+                  rmusic_ctx** out);
+
+/* Demodulate n_frames frames (Sec. 3, Eq. 2-15, all pixels of all frames).
+ *   d_frames  device pointer; frame f starts at (const char*)d_frames + descs[f].offset_bytes.
+ *   descs     HOST array of n_frames descriptors; copied by the library before return.
+ *   d_out     device float32 buffer; frame f writes H*W values at d_out + descs[f].out_offset:
+ *             the phase derivative in rad/pixel along deriv_axis, NaN where undefined.
+ *   d_status  device uint8 buffer laid out like d_out, or NULL.
+ *   cuda_stream  cudaStream_t (as void*) on which all work is queued.
+ * Errors: RMUSIC_EINVAL (NULL pointers with n_frames > 0, a bad descriptor, unsupported
+ * (N, L) for the path), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a no-op. */
+int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
+                             int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream);
+
+/* Same as rmusic_demodulate_frames, but every buffer is in HOST memory: the library copies the
+ * frames to its device workspace, runs the same kernels and copies the maps back before it
+ * returns (the call synchronises its stream). in_bytes is the size of h_frames. Pinned host
+ * memory makes the copies asynchronous DMA; pageable memory also works. */
+int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
+                                  const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
+                                  uint8_t* h_status, void* cuda_stream);
+
+/* Destroy a context and free everything it owns. NULL is allowed. Waits for the context's
+ * outstanding work on its device. */
+void rmusic_destroy(rmusic_ctx* ctx);
+
+/* Static, human-readable name of a return code. */
+const char* rmusic_strerror(int code);
+
+/* Text of the last CUDA error seen by this context (static storage inside ctx), or "". */
+const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
+
+/* Counters of the last call on this context (for measurement and tests).
+ *   kernel_launches  kernels the last call queued (graph replays count their kernels).
+ *   graph_replayed   1 if the last call replayed a cached CUDA graph.
+ *   workspace_bytes  device bytes the context currently holds.
+ *   pixels           pixels of all frames of the last call.
+ *   mean_sweeps      batched path: Jacobi sweeps per 32-pixel work item, averaged.
+ *   mean_root_iters  batched path: Aberth iterations per 32-pixel work item, averaged.
+ *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
+ *                    call's stream) of the band-pass launches and of the solver launches.
+ * rmusic_get_stats waits until the last call's work has finished. */
+typedef struct {
+    int32_t kernel_launches;
+    int32_t graph_replayed;
+    uint64_t workspace_bytes;
+    uint64_t pixels;
+    double mean_sweeps;
+    double mean_root_iters;
+    float bandpass_ms;
+    float solver_ms;
+} rmusic_stats;
+
+int rmusic_get_stats(const rmusic_ctx* ctx, rmusic_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMUSIC_H */

@@ -1,0 +1,539 @@
+// batched.cu -- the FP32 batched path: one persistent kernel over every pixel of every frame of
+// a call (frames of uneven sizes and windows mixed), one pixel per lane, one 32-pixel run of a
+// window line per warp work item, items taken from a global atomic counter.
+//
+// Per warp item (32 consecutive pixels of one window line):
+//   stage     the 31 + N analytic-signal samples the 32 windows cover, one coalesced read into
+//             shared memory (Sec. 3, Eq. 2: the moving window)
+//   R_f       every entry R_f[m][m+d] = (1/K) sum_{i<K} w[i+m] conj(w[i+m+d]) is a box sum of
+//             the lag-d product sequence g_d[j] = Gamma[j] conj(Gamma[j+d]); per lag d the warp
+//             forms g_d once for the run, takes its prefix sums with a warp scan and reads
+//             R_f[m][m+d] = (P_d[t+m+K] - P_d[t+m]) / K (Eq. 4-5). The scan starts at the run's
+//             fixed absolute position, so each pixel's arithmetic does not depend on how frames
+//             are batched or scheduled.
+//   FB -> S   with forward-backward averaging R = (R_f + J conj(R_f) J)/2 is centro-Hermitian,
+//             so with the unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) (even L) S = Q^H R Q =
+//             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x.
+//   eigen     cyclic Jacobi sweeps on S (real, register resident, fully unrolled) until the
+//             off-diagonal mass is below 1e-4 of the trace -> the largest eigenvalue l1; then two
+//             steps of inverse iteration with (mu I - S) = L D L^T, mu just above l1, give the
+//             signal eigenvector x1 without accumulating rotations (Eq. 8-11).
+//   poly      u1 = Q x1 / |x1|; c_0 = L - 1, c_k = -sum_m u1[m] conj(u1[m+k]) / |u1|^2,
+//             c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14).
+//   roots     Aberth-Ehrlich on all 2L-2 roots. Starting points come from the estimator's
+//             structure: a pair straddling the circle at the angle of conj(rho_1) (the signal
+//             root), and pairs at radius r, 1/r (r = L / (L + 7.3)) at the side-lobe angles
+//             arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window puts the other
+//             roots. Iterations stop when every root of every lane of the warp has a residual
+//             at the FP32 rounding level.
+//   select    the root with |z| <= 1 + 1e-3 nearest the unit circle (Algorithm 1). A noise-free
+//             window gives a double root there, which FP32 splits by ~sqrt(eps); when another
+//             root lies within 4e-3 the pair is located as the root of Q' between them, otherwise
+//             the root is refined by Newton on Q with its conjugate-reciprocal partner 1/conj(z)
+//             divided out. Optionally one more such step runs in FP64.
+//   angle     atan2 of the root minus the carrier step, wrapped (Eq. 15).
+#include <math.h>
+
+#include "rmusic_device.cuh"
+#include "rmusic_launch.h"
+
+namespace rmusic {
+
+constexpr int kBatWarps = 4;
+constexpr int kBatThreads = kBatWarps * 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ constexpr int tri(int r, int c, int L) {
+    return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);
+}
+
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+
+__device__ __forceinline__ cx<float> cdivf(cx<float> a, cx<float> b) {
+    const float inv = frcp(b.r * b.r + b.i * b.i);
+    return mkc((a.r * b.r + a.i * b.i) * inv, (a.i * b.r - a.r * b.i) * inv);
+}
+
+__device__ __forceinline__ cx<float> shfl_up_c(cx<float> v, int o) {
+    return mkc(__shfl_up_sync(kFull, v.r, o), __shfl_up_sync(kFull, v.i, o));
+}
+
+// Coefficient i of Q(z) from c_0 (real) and c_1..c_{L-1}.
+template <int L>
+__device__ __forceinline__ cx<float> qcoef(const cx<float>* c, int i) {
+    const int k = i - (L - 1);
+    if (k == 0) return c[0];
+    return k > 0 ? c[k] : conjg(c[-k]);
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pd(const cx<float>* c, const float* ac, cx<float> z, float az,
+                                          cx<float>& p, cx<float>& d, float& bnd) {
+    p = qcoef<L>(c, 2 * L - 2);
+    d = mkc(0.f, 0.f);
+    bnd = ac[L - 1];
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d = d * z + p;
+        p = p * z + qcoef<L>(c, i);
+        const int k = i - (L - 1);
+        bnd = fmaf(bnd, az, ac[k >= 0 ? k : -k]);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pdd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d1,
+                                           cx<float>& d2) {
+    p = qcoef<L>(c, 2 * L - 2);
+    d1 = mkc(0.f, 0.f);
+    d2 = mkc(0.f, 0.f);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d2 = d2 * z + d1;
+        d1 = d1 * z + p;
+        p = p * z + qcoef<L>(c, i);
+    }
+    d2 = 2.f * d2;
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pdd64(const cx<float>* c, cx<double> z, cx<double>& p, cx<double>& d1,
+                                             cx<double>& d2) {
+    auto q64 = [&](int i) {
+        cx<float> v = qcoef<L>(c, i);
+        return mkc((double)v.r, (double)v.i);
+    };
+    p = q64(2 * L - 2);
+    d1 = mkc(0.0, 0.0);
+    d2 = mkc(0.0, 0.0);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d2 = d2 * z + d1;
+        d1 = d1 * z + p;
+        p = p * z + q64(i);
+    }
+    d2 = 2.0 * d2;
+}
+
+template <int L>
+__global__ void __launch_bounds__(kBatThreads)
+batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
+               unsigned long long* __restrict__ counter, const float2* __restrict__ gam,
+               float* __restrict__ out, uint8_t* __restrict__ status, BatchedArgs args) {
+    static_assert(L % 2 == 0 && L >= 2 && L <= kMaxL, "even L only");
+    constexpr int h = L / 2;
+    constexpr int NS = L * (L + 1) / 2;
+    constexpr int NR = 2 * L - 2;
+    __shared__ float2 sh_seg[kBatWarps][32 + kMaxN];
+    __shared__ float2 sh_pre[kBatWarps][3 * 32 + 1];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* seg = sh_seg[wid];
+    float2* pre = sh_pre[wid];
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)total_items) break;
+        const int f = find_frame(fr, nframes, (int64_t)item, [](const FrameDev& F) { return F.item_start; });
+        const FrameDev& F = fr[f];
+        const int64_t local = (int64_t)item - F.item_start;
+        const int wline = (int)(local / F.nchunks);
+        const int chunk = (int)(local % F.nchunks);
+        const int N = F.N, K = N - L + 1, wlen = F.wlen;
+        const int pos = chunk * kChunk + lane;
+        const int a0 = chunk * kChunk - N / 2;
+        const float2* gl = gam + F.gam_off + (uint64_t)wline * wlen;
+
+        // ---- stage the run's samples (coalesced) --------------------------------------------
+        __syncwarp();
+        for (int j = lane; j < 31 + N; j += 32) {
+            const int p = a0 + j;
+            seg[j] = (p >= 0 && p < wlen) ? gl[p] : make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+        const bool inside = pos < wlen;
+        const bool valid = inside && (pos - N / 2 >= 0) && (pos - N / 2 + N - 1 <= wlen - 1);
+
+        // ---- R_f by lag-product prefix sums -----------------------------------------------------
+        cx<float> Rf[NS];
+        const float invK = 1.0f / (float)K;
+#pragma unroll
+        for (int d = 0; d < L; ++d) {
+            const int G = 31 + N - d;  // lag products g_d[0 .. G-1] are needed
+            const int j0 = 3 * lane;
+            cx<float> s0 = mkc(0.f, 0.f), s1, s2;
+            if (j0 < G) {
+                float2 a = seg[j0], b = seg[j0 + d];
+                s0 = mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+            }
+            s1 = s0;
+            if (j0 + 1 < G) {
+                float2 a = seg[j0 + 1], b = seg[j0 + 1 + d];
+                s1 = s1 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+            }
+            s2 = s1;
+            if (j0 + 2 < G) {
+                float2 a = seg[j0 + 2], b = seg[j0 + 2 + d];
+                s2 = s2 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+            }
+            cx<float> incl = s2;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                cx<float> t = shfl_up_c(incl, o);
+                if (lane >= o) incl = incl + t;
+            }
+            cx<float> excl = shfl_up_c(incl, 1);
+            if (lane == 0) excl = mkc(0.f, 0.f);
+            __syncwarp();
+            const cx<float> p1 = excl + s0, p2 = excl + s1, p3 = excl + s2;
+            pre[j0 + 1] = make_float2(p1.r, p1.i);
+            pre[j0 + 2] = make_float2(p2.r, p2.i);
+            pre[j0 + 3] = make_float2(p3.r, p3.i);
+            if (lane == 0) pre[0] = make_float2(0.f, 0.f);
+            __syncwarp();
+#pragma unroll
+            for (int m = 0; m + d < L; ++m) {
+                const float2 hi = pre[lane + m + K], lo = pre[lane + m];
+                Rf[tri(m, m + d, L)] = mkc((hi.x - lo.x) * invK, (hi.y - lo.y) * invK);
+            }
+        }
+
+        // ---- S = Re(Q^H R_f Q), normalised by its trace -----------------------------------------
+        auto RF = [&](int r, int c) { return r <= c ? Rf[tri(r, c, L)] : conjg(Rf[tri(c, r, L)]); };
+        float S[NS];
+#pragma unroll
+        for (int i = 0; i < h; ++i)
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                const cx<float> a = RF(i, k), b = RF(i, L - 1 - k), c = RF(L - 1 - i, k),
+                                dd = RF(L - 1 - i, L - 1 - k);
+                if (i <= k) {
+                    S[tri(i, k, L)] = 0.5f * (a.r + b.r + c.r + dd.r);
+                    S[tri(h + i, h + k, L)] = 0.5f * (a.r - b.r - c.r + dd.r);
+                }
+                S[tri(i, h + k, L)] = -0.5f * (a.i - b.i + c.i - dd.i);
+            }
+        float tr = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) tr += S[tri(i, i, L)];
+        const bool nonzero = valid && tr > 0.f && isfinite(tr);
+        const float itr = nonzero ? frcp(tr) : 0.f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) S[i] = nonzero ? S[i] * itr : 0.f;
+        if (!nonzero) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) S[tri(i, i, L)] = (float)(L - i);  // any well-separated stand-in
+        }
+
+        // ---- cyclic Jacobi on S for the eigenvalues -----------------------------------------------
+        float A[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) A[i] = S[i];
+        int sweeps = 0;
+        bool jconv = false;
+        for (;;) {
+#pragma unroll
+            for (int p = 0; p < L - 1; ++p)
+#pragma unroll
+                for (int q = p + 1; q < L; ++q) {
+                    const float apq = A[tri(p, q, L)];
+                    const float dq = A[tri(q, q, L)] - A[tri(p, p, L)];
+                    const float den = fabsf(dq) + sqrtf(fmaf(dq, dq, 4.f * apq * apq));
+                    float t = den > 0.f ? __fdividef(2.f * apq, den) : 0.f;
+                    t = dq < 0.f ? -t : t;
+                    const float c = rsqrtf(fmaf(t, t, 1.f));
+                    const float s = t * c;
+                    A[tri(p, p, L)] = fmaf(-t, apq, A[tri(p, p, L)]);
+                    A[tri(q, q, L)] = fmaf(t, apq, A[tri(q, q, L)]);
+                    A[tri(p, q, L)] = 0.f;
+#pragma unroll
+                    for (int r = 0; r < L; ++r) {
+                        if (r == p || r == q) continue;
+                        const float g = A[tri(r, p, L)], hh = A[tri(r, q, L)];
+                        A[tri(r, p, L)] = fmaf(c, g, -s * hh);
+                        A[tri(r, q, L)] = fmaf(s, g, c * hh);
+                    }
+                }
+            ++sweeps;
+            float off = 0.f;
+#pragma unroll
+            for (int p = 0; p < L - 1; ++p)
+#pragma unroll
+                for (int q = p + 1; q < L; ++q) off = fmaf(A[tri(p, q, L)], A[tri(p, q, L)], off);
+            jconv = off <= 1e-8f;
+            if (sweeps >= args.max_sweeps) break;
+            if (sweeps >= 2 && __all_sync(kFull, jconv)) break;
+        }
+        float l1 = A[tri(0, 0, L)], l2 = -1e30f;
+        int k1 = 0;
+#pragma unroll
+        for (int i = 1; i < L; ++i) {
+            const float v = A[tri(i, i, L)];
+            if (v > l1) {
+                l2 = l1;
+                l1 = v;
+                k1 = i;
+            } else if (v > l2) {
+                l2 = v;
+            }
+        }
+        const bool separated = l1 - l2 > 4e-6f * l1;
+
+        // ---- inverse iteration: (mu I - S) x = b, b = column k1 of S ----------------------------
+        const float mu = l1 + 1e-5f * l1 + 1e-30f;
+        float Lm[NS];  // unit lower factor in the packed layout, D on the diagonal slots
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            float dj = mu - S[tri(j, j, L)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) dj = fmaf(-Lm[tri(j, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], dj);
+            if (fabsf(dj) < 1e-30f) dj = dj < 0.f ? -1e-30f : 1e-30f;
+            Lm[tri(j, j, L)] = dj;
+            const float inv = frcp(dj);
+#pragma unroll
+            for (int i = j + 1; i < L; ++i) {
+                float v = -S[tri(i, j, L)];
+#pragma unroll
+                for (int k = 0; k < j; ++k) v = fmaf(-Lm[tri(i, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], v);
+                Lm[tri(i, j, L)] = v * inv;
+            }
+        }
+        float x[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            float v = 0.f;
+#pragma unroll
+            for (int j = 0; j < L; ++j) v = (j == k1) ? S[tri(i, j, L)] : v;
+            x[i] = v;
+        }
+#pragma unroll
+        for (int step = 0; step < 2; ++step) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+#pragma unroll
+                for (int k = 0; k < i; ++k) x[i] = fmaf(-Lm[tri(i, k, L)], x[k], x[i]);
+#pragma unroll
+            for (int i = 0; i < L; ++i) x[i] *= frcp(Lm[tri(i, i, L)]);
+#pragma unroll
+            for (int i = L - 1; i >= 0; --i)
+#pragma unroll
+                for (int k = i + 1; k < L; ++k) x[i] = fmaf(-Lm[tri(k, i, L)], x[k], x[i]);
+            float n2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < L; ++i) n2 = fmaf(x[i], x[i], n2);
+            const float inv = rsqrtf(n2);
+#pragma unroll
+            for (int i = 0; i < L; ++i) x[i] *= inv;
+        }
+
+        // ---- u1 = Q x1 and the polynomial coefficients ---------------------------------------------
+        cx<float> u[L];
+        const float r2 = 0.70710678118654752f;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            u[i] = mkc(r2 * x[i], r2 * x[h + i]);
+            u[h + i] = mkc(r2 * x[h - 1 - i], -r2 * x[L - 1 - i]);
+        }
+        float nu2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) nu2 += norm2(u[i]);
+        const float inu2 = frcp(nu2);
+        cx<float> c[L];
+        float ac[L];
+        c[0] = mkc((float)(L - 1), 0.f);
+        ac[0] = (float)(L - 1);
+#pragma unroll
+        for (int k = 1; k < L; ++k) {
+            cx<float> rho = mkc(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m + k < L; ++m) rho = rho + mulc(u[m], u[m + k]);
+            c[k] = (-inu2) * rho;
+            ac[k] = sqrtf(norm2(c[k]));
+        }
+
+        // ---- Aberth-Ehrlich from structured starting points ---------------------------------------
+        cx<float> z[NR];
+        {
+            const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
+            const float n1 = norm2(rho1);
+            const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
+            z[0] = 0.98f * e;
+            z[1] = (1.f / 0.98f) * e;
+            float sh, ch;
+            sincospif(1.0f / (float)L, &sh, &ch);           // exp(j pi / L)
+            const cx<float> step = mkc(ch * ch - sh * sh, 2.f * sh * ch);  // exp(2 j pi / L)
+            cx<float> ek = e * mkc(ch, sh) * step;            // angle + 2 pi (1 + 1/2) / L
+            const float rin = (float)L / ((float)L + 7.3f);
+#pragma unroll
+            for (int k = 1; k <= L - 2; ++k) {
+                z[2 * k] = rin * ek;
+                z[2 * k + 1] = (1.f / rin) * ek;
+                ek = ek * step;
+            }
+        }
+        int iters = 0;
+        bool rconv = false;
+        for (;;) {
+            rconv = true;
+#pragma unroll
+            for (int i = 0; i < NR; ++i) {
+                const float az = sqrtf(norm2(z[i]));
+                cx<float> p, dp;
+                float bnd;
+                horner_pd<L>(c, ac, z[i], az, p, dp, bnd);
+                const float lim = 3e-6f * bnd;
+                rconv = rconv && (norm2(p) <= lim * lim);
+                const cx<float> Ni = cdivf(p, dp);
+                cx<float> Si = mkc(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    if (j == i) continue;
+                    const cx<float> dz = z[i] - z[j];
+                    const float inv = frcp(norm2(dz));
+                    Si = mkc(fmaf(dz.r, inv, Si.r), fmaf(-dz.i, inv, Si.i));
+                }
+                const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - Ni * Si);
+                if (isfinite(w.r) && isfinite(w.i)) z[i] = z[i] - w;
+            }
+            ++iters;
+            if (iters >= args.max_iters) break;
+            if (__all_sync(kFull, rconv)) break;
+        }
+
+        // ---- selection (Algorithm 1) ------------------------------------------------------------------
+        int best = -1;
+        float bestd = 1e30f;
+        cx<float> zs = mkc(1.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const float r = sqrtf(norm2(z[i]));
+            const float dd = fabsf(r - 1.f);
+            if (r <= 1.f + 1e-3f && dd < bestd) {
+                bestd = dd;
+                best = i;
+                zs = z[i];
+            }
+        }
+        float neard = 1e30f;
+        cx<float> zn = zs;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const float dj = sqrtf(norm2(z[j] - zs));
+            if (j != best && dj < neard) {
+                neard = dj;
+                zn = z[j];
+            }
+        }
+        const bool cluster = neard < 4e-3f;
+        cx<float> zz = cluster ? 0.5f * (zs + zn) : zs;
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            cx<float> p, d1, d2;
+            horner_pdd<L>(c, zz, p, d1, d2);
+            cx<float> stp;
+            if (cluster) {
+                stp = cdivf(d1, d2);
+            } else {
+                const float in2 = frcp(norm2(zz));
+                const cx<float> dzp = zz - in2 * zz;  // z - 1/conj(z)
+                stp = cdivf(p, d1 - cdivf(p, dzp));
+            }
+            if (isfinite(stp.r) && isfinite(stp.i)) zz = zz - stp;
+        }
+        double omd;
+        if (args.polish64) {
+            cx<double> z64 = mkc((double)zz.r, (double)zz.i);
+            cx<double> p, d1, d2;
+            horner_pdd64<L>(c, z64, p, d1, d2);
+            cx<double> stp;
+            if (cluster) {
+                stp = cdiv(d1, d2);
+            } else {
+                const double in2 = 1.0 / norm2(z64);
+                const cx<double> dzp = z64 - in2 * z64;
+                stp = cdiv(p, d1 - cdiv(p, dzp));
+            }
+            if (isfinite(stp.r) && isfinite(stp.i)) z64 = z64 - stp;
+            omd = atan2(z64.i, z64.r) - (double)F.omega_ref;
+            omd = wrap_pi(omd);
+        } else {
+            omd = 0.0;
+        }
+        float om = args.polish64 ? (float)omd : wrap_pi(atan2f(zz.i, zz.r) - (float)F.omega_ref);
+
+        if (lane == 0 && args.counters) {
+            atomicAdd(args.counters + 0, (unsigned long long)sweeps);
+            atomicAdd(args.counters + 1, (unsigned long long)iters);
+            atomicAdd(args.counters + 2, 1ull);
+        }
+
+        // ---- store ---------------------------------------------------------------------------------
+        if (inside) {
+            const uint64_t o = out_index(F, wline, pos);
+            uint8_t st = kStOk;
+            if (!valid) {
+                st = kStBorder;
+            } else if (!nonzero || !separated || best < 0) {
+                st = kStDegenerate;
+            } else if (!rconv || !jconv) {
+                st = kStNotConverged;
+            }
+            out[o] = (st == kStOk || st == kStNotConverged) ? om : __int_as_float(0x7fc00000);
+            if (status) status[o] = st;
+        }
+    }
+}
+
+template <int L>
+static cudaError_t launch_L(const FrameDev* d_frames, int nframes, int64_t total_items,
+                            unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                            uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
+    batched_kernel<L><<<grid, kBatThreads, 0, stream>>>(d_frames, nframes, total_items, d_counter, d_gamma,
+                                                        d_out, d_status, a);
+    return cudaGetLastError();
+}
+
+bool batched_supports(int L) { return L == 2 || L == 4 || L == 6 || L == 8 || L == 10 || L == 12; }
+
+template <int L>
+static int occupancy_blocks() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel<L>, kBatThreads, 0) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+int batched_grid(int L, int device) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int per = 1;
+    switch (L) {
+        case 2: per = occupancy_blocks<2>(); break;
+        case 4: per = occupancy_blocks<4>(); break;
+        case 6: per = occupancy_blocks<6>(); break;
+        case 8: per = occupancy_blocks<8>(); break;
+        case 10: per = occupancy_blocks<10>(); break;
+        case 12: per = occupancy_blocks<12>(); break;
+        default: per = 1;
+    }
+    return sms * per;
+}
+
+cudaError_t init_batched(int) { return cudaSuccess; }
+
+cudaError_t launch_batched(int L, const FrameDev* d_frames, int nframes, int64_t total_items,
+                           unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                           uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
+    switch (L) {
+        case 2: return launch_L<2>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
+        case 4: return launch_L<4>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
+        case 6: return launch_L<6>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
+        case 8: return launch_L<8>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
+        case 10: return launch_L<10>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
+        case 12: return launch_L<12>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rmusic

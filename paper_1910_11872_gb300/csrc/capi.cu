@@ -1,0 +1,630 @@
+// capi.cu -- the library's C ABI (include/rmusic.h): contexts, workspaces, frame tables,
+// batching under an HBM budget, CUDA-graph capture and replay, and the host-buffer entry.
+//
+// A call is: validate descriptors -> build the device frame table (band bins, window-line
+// geometry, work-item ranges) -> band-pass every carrier line (analytic.cu) -> either one
+// thread-per-pixel launch per frame (plain.cu) or one persistent launch per covariance order
+// over all frames (batched.cu). Frames whose analytic signal does not fit the workspace budget
+// together are processed in consecutive groups.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/rmusic.h"
+#include "rmusic_device.cuh"
+#include "rmusic_launch.h"
+
+using namespace rmusic;
+
+namespace {
+
+constexpr int kMaxGraphs = 8;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr int kCounterSlots = 64;  // [0, kMaxL] work counters, [kStatSlot ..] statistics
+constexpr int kStatSlot = 32;
+
+struct GraphEntry {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    FrameDev* h_table = nullptr;  // pinned; read by the graph's upload node at every replay
+    int launches = 0;
+    uint64_t stamp = 0;
+    std::vector<int> a1_ev, solver_ev;  // timing event indices recorded by the graph
+};
+
+}  // namespace
+
+struct rmusic_ctx {
+    rmusic_params p{};
+    int device = 0;
+    size_t budget = 0;
+    int num_sms = 0;
+    // device workspaces
+    float2* d_gamma = nullptr;
+    size_t gamma_cap = 0;  // elements
+    FrameDev* d_table = nullptr;
+    size_t table_cap = 0;  // entries
+    unsigned long long* d_counters = nullptr;  // one per covariance order
+    // pinned staging of the frame table for non-graph calls
+    FrameDev* h_table = nullptr;
+    size_t h_table_cap = 0;
+    cudaEvent_t table_free = nullptr;  // recorded after the last table upload
+    // host-buffer entry staging
+    void* d_in = nullptr;
+    size_t in_cap = 0;
+    float* d_out = nullptr;
+    size_t out_cap = 0;
+    uint8_t* d_st = nullptr;
+    size_t st_cap = 0;
+    // graphs
+    GraphEntry graphs[kMaxGraphs];
+    uint64_t graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;  // graphs are captured here, then launched on the caller's stream
+    // statistics and timing
+    cudaEvent_t call_done = nullptr;
+    std::vector<cudaEvent_t> ev_pool;
+    int ev_used = 0;
+    std::vector<int> a1_ev, solver_ev;  // pairs of event indices of the last call
+    uint64_t last_pixels = 0;
+    // bookkeeping
+    size_t held = 0;
+    rmusic_stats stats{};
+    char last_err[256] = {0};
+    int grid_by_L[kMaxL + 1] = {0};
+};
+
+namespace {
+
+int cuda_fail(rmusic_ctx* c, cudaError_t e, const char* what) {
+    if (c) snprintf(c->last_err, sizeof(c->last_err), "%s: %s", what, cudaGetErrorString(e));
+    return RMUSIC_ECUDA;
+}
+
+#define RM_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+    } while (0)
+
+bool params_ok(const rmusic_params& p) {
+    if (p.window_len < 2 || p.window_len > kMaxN) return false;
+    if (p.cov_order < 2 || p.cov_order > kMaxL || p.cov_order > p.window_len) return false;
+    if (p.forward_backward != 0 && p.forward_backward != 1) return false;
+    if (p.deriv_axis != 0 && p.deriv_axis != 1) return false;
+    if (p.carrier_axis != 0 && p.carrier_axis != 1) return false;
+    if (!(p.carrier_freq > 0.0 && p.carrier_freq < 0.5)) return false;
+    if (!(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5)) return false;
+    if (p.precision < RMUSIC_PLAIN_FP64 || p.precision > RMUSIC_FP32_BATCHED) return false;
+    if (p.max_sweeps < 0 || p.max_root_iters < 0) return false;
+    return true;
+}
+
+// Grow a device buffer to at least `bytes` (never shrinks). Keeps the budget.
+int ensure(rmusic_ctx* ctx, void** ptr, size_t* cap_bytes, size_t bytes) {
+    if (*cap_bytes >= bytes) return RMUSIC_OK;
+    size_t want = std::max(bytes, *cap_bytes + *cap_bytes / 2);
+    if (ctx->budget && ctx->held - *cap_bytes + want > ctx->budget) {
+        want = bytes;
+        if (ctx->held - *cap_bytes + want > ctx->budget) return RMUSIC_ENOMEM;
+    }
+    if (*ptr) {
+        cudaStreamSynchronize(nullptr);
+        cudaDeviceSynchronize();
+        cudaFree(*ptr);
+        ctx->held -= *cap_bytes;
+        *ptr = nullptr;
+        *cap_bytes = 0;
+    }
+    void* np = nullptr;
+    cudaError_t e = cudaMalloc(&np, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RMUSIC_ENOMEM;
+    }
+    *ptr = np;
+    *cap_bytes = want;
+    ctx->held += want;
+    // any cached graph may reference the old buffer
+    for (auto& g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.h_table) cudaFreeHost(g.h_table);
+        g = GraphEntry{};
+    }
+    return RMUSIC_OK;
+}
+
+// Everything the kernels need to know about one frame, derived from its descriptor.
+struct Plan {
+    std::vector<FrameDev> frames;  // in launch order (grouped by L for the batched path)
+    std::vector<int> group_L;      // batched: covariance order of each group
+    std::vector<int> group_first;  // batched: first table entry of each group
+    std::vector<int> group_count;
+    std::vector<int64_t> group_items;
+    int64_t total_lines = 0;
+    int max_len = 0;
+    uint64_t gamma_elems = 0;
+};
+
+int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
+    const rmusic_params& p = ctx->p;
+    if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
+    const int pitch = d.pitch_elems == 0 ? d.width : d.pitch_elems;
+    if (pitch < d.width) return RMUSIC_EINVAL;
+    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16) return RMUSIC_EINVAL;
+    const int esz = d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2;
+    if (d.offset_bytes % esz) return RMUSIC_EINVAL;
+    const int N = d.window_len ? d.window_len : p.window_len;
+    const int L = d.cov_order ? d.cov_order : p.cov_order;
+    if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
+    if (p.precision == RMUSIC_FP32_BATCHED && (!batched_supports(L) || p.forward_backward != 1))
+        return RMUSIC_EUNSUPPORTED;
+    memset(F, 0, sizeof(*F));
+    F->in_off = d.offset_bytes;
+    F->out_off = d.out_offset;
+    F->H = d.height;
+    F->W = d.width;
+    F->pitch = pitch;
+    F->dtype = d.dtype;
+    F->N = N;
+    F->L = L;
+    F->carrier_axis = p.carrier_axis;
+    F->deriv_axis = p.deriv_axis;
+    F->nlines = p.carrier_axis == 0 ? d.height : d.width;
+    F->len = p.carrier_axis == 0 ? d.width : d.height;
+    if (F->len > kMaxLine) return RMUSIC_EUNSUPPORTED;
+    // kept band: 1 <= k < len/2 and |k/len - f0| < B (a contiguous run of bins)
+    const double f0 = p.carrier_freq;
+    const double B = p.band_halfwidth > 0.0 ? p.band_halfwidth : 0.5 * f0;
+    int klo = -1, nb = 0;
+    for (int k = 1; 2 * k < F->len; ++k) {
+        if (fabs((double)k / (double)F->len - f0) < B) {
+            if (klo < 0) klo = k;
+            ++nb;
+        }
+    }
+    F->k_lo = klo < 0 ? 1 : klo;
+    F->nb = nb;
+    F->wlines = p.deriv_axis == 0 ? d.height : d.width;
+    F->wlen = p.deriv_axis == 0 ? d.width : d.height;
+    F->nchunks = (F->wlen + kChunk - 1) / kChunk;
+    F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
+    return RMUSIC_OK;
+}
+
+int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Plan* plan) {
+    plan->frames.resize(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = describe(ctx, descs[i], &plan->frames[i]);
+        if (rc) return rc;
+    }
+    if (ctx->p.precision == RMUSIC_FP32_BATCHED)
+        std::stable_sort(plan->frames.begin(), plan->frames.end(),
+                         [](const FrameDev& a, const FrameDev& b) { return a.L < b.L; });
+    uint64_t goff = 0;
+    int64_t lines = 0;
+    for (int i = 0; i < n; ++i) {
+        FrameDev& F = plan->frames[i];
+        F.gam_off = goff;
+        goff += (uint64_t)F.H * (uint64_t)F.W;
+        F.line_start = lines;
+        lines += F.nlines;
+        plan->max_len = std::max(plan->max_len, F.len);
+        if (i == 0 || F.L != plan->frames[i - 1].L) {
+            plan->group_L.push_back(F.L);
+            plan->group_first.push_back(i);
+            plan->group_count.push_back(0);
+            plan->group_items.push_back(0);
+        }
+        F.item_start = plan->group_items.back();
+        plan->group_items.back() += (int64_t)F.wlines * F.nchunks;
+        plan->group_count.back() += 1;
+    }
+    plan->total_lines = lines;
+    plan->gamma_elems = goff;
+    return RMUSIC_OK;
+}
+
+// Queue the work of one plan (whose frame table has just been copied to d_table) on `s`.
+// Record a timing event on s (an event-record node when s is capturing). Returns its index or -1.
+int stamp(rmusic_ctx* ctx, cudaStream_t s) {
+    if (!ctx->p.timing) return -1;
+    if (ctx->ev_used >= (int)ctx->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        ctx->ev_pool.push_back(e);
+    }
+    cudaEvent_t e = ctx->ev_pool[ctx->ev_used];
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    cudaError_t r = cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                                       : cudaEventRecord(e, s);
+    if (r != cudaSuccess) return -1;
+    return ctx->ev_used++;
+}
+
+void stamp_pair(std::vector<int>& v, int a, int b) {
+    if (a >= 0 && b >= 0) {
+        v.push_back(a);
+        v.push_back(b);
+    }
+}
+
+int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_out, uint8_t* d_status,
+            cudaStream_t s, int* launches) {
+    const int n = (int)plan.frames.size();
+    int e0 = stamp(ctx, s);
+    RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, d_frames, ctx->d_gamma, s));
+    stamp_pair(ctx->a1_ev, e0, stamp(ctx, s));
+    ++*launches;
+    const rmusic_params& p = ctx->p;
+    if (p.precision == RMUSIC_FP32_BATCHED) {
+        BatchedArgs a;
+        a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
+        a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
+        a.polish64 = p.polish_fp64;
+        a.counters = ctx->d_counters + kStatSlot;
+        for (size_t g = 0; g < plan.group_L.size(); ++g) {
+            const int L = plan.group_L[g];
+            if (ctx->grid_by_L[L] == 0) ctx->grid_by_L[L] = batched_grid(L, ctx->device);
+            RM_CUDA(cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s));
+            int e1 = stamp(ctx, s);
+            RM_CUDA(launch_batched(L, ctx->d_table + plan.group_first[g], plan.group_count[g],
+                                   plan.group_items[g], ctx->d_counters + g, ctx->d_gamma, d_out, d_status,
+                                   a, ctx->grid_by_L[L], s));
+            stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
+            ++*launches;
+        }
+    } else {
+        PlainArgs a;
+        a.fb = p.forward_backward;
+        a.max_sweeps = p.max_sweeps ? p.max_sweeps : 30;
+        a.max_iters = p.max_root_iters ? p.max_root_iters : 500;
+        int e1 = stamp(ctx, s);
+        for (int f = 0; f < n; ++f) {
+            if (p.precision == RMUSIC_PLAIN_FP64)
+                RM_CUDA(launch_plain_fp64(ctx->d_table + f, plan.frames[f], ctx->d_gamma, d_out, d_status, a, s));
+            else
+                RM_CUDA(launch_plain_fp32(ctx->d_table + f, plan.frames[f], ctx->d_gamma, d_out, d_status, a, s));
+            ++*launches;
+        }
+        stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
+    }
+    return RMUSIC_OK;
+}
+
+int ensure_tables(rmusic_ctx* ctx, size_t nframes) {
+    if (ctx->table_cap < nframes) {
+        size_t bytes = ctx->table_cap * sizeof(FrameDev);
+        void* ptr = ctx->d_table;
+        int rc = ensure(ctx, &ptr, &bytes, std::max<size_t>(nframes, 64) * sizeof(FrameDev));
+        if (rc) return rc;
+        ctx->d_table = (FrameDev*)ptr;
+        ctx->table_cap = bytes / sizeof(FrameDev);
+    }
+    if (ctx->h_table_cap < nframes) {
+        if (ctx->h_table) {
+            cudaEventSynchronize(ctx->table_free);
+            cudaFreeHost(ctx->h_table);
+        }
+        size_t cap = std::max<size_t>(nframes, 64);
+        if (cudaMallocHost(&ctx->h_table, cap * sizeof(FrameDev)) != cudaSuccess) {
+            ctx->h_table = nullptr;
+            ctx->h_table_cap = 0;
+            return RMUSIC_ENOMEM;
+        }
+        ctx->h_table_cap = cap;
+    }
+    return RMUSIC_OK;
+}
+
+// Process frames [first, first + count) of descs as one workspace group.
+int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int count,
+              float* d_out, uint8_t* d_status, cudaStream_t s) {
+    Plan plan;
+    int rc = build_plan(ctx, descs, count, &plan);
+    if (rc) return rc;
+    size_t gbytes = ctx->gamma_cap * sizeof(float2);
+    void* gptr = ctx->d_gamma;
+    rc = ensure(ctx, &gptr, &gbytes, std::max<uint64_t>(plan.gamma_elems, 1) * sizeof(float2));
+    if (rc) return rc;
+    ctx->d_gamma = (float2*)gptr;
+    ctx->gamma_cap = gbytes / sizeof(float2);
+    rc = ensure_tables(ctx, plan.frames.size());
+    if (rc) return rc;
+
+    const bool graph = ctx->p.use_graph && ctx->p.precision == RMUSIC_FP32_BATCHED;
+    int launches = 0;
+    if (!graph) {
+        RM_CUDA(cudaEventSynchronize(ctx->table_free));
+        memcpy(ctx->h_table, plan.frames.data(), plan.frames.size() * sizeof(FrameDev));
+        RM_CUDA(cudaMemcpyAsync(ctx->d_table, ctx->h_table, plan.frames.size() * sizeof(FrameDev),
+                                cudaMemcpyHostToDevice, s));
+        RM_CUDA(cudaEventRecord(ctx->table_free, s));
+        rc = enqueue(ctx, plan, d_frames, d_out, d_status, s, &launches);
+        if (rc) return rc;
+        ctx->stats.kernel_launches += launches;
+        return RMUSIC_OK;
+    }
+
+    // graph path: key = everything the captured work depends on
+    std::vector<unsigned char> key;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        key.insert(key.end(), b, b + n);
+    };
+    put(&d_frames, sizeof(d_frames));
+    put(&d_out, sizeof(d_out));
+    put(&d_status, sizeof(d_status));
+    put(&ctx->p, sizeof(ctx->p));
+    put(plan.frames.data(), plan.frames.size() * sizeof(FrameDev));
+    for (auto& g : ctx->graphs) {
+        if (g.exec && g.key == key) {
+            g.stamp = ++ctx->graph_clock;
+            ctx->a1_ev.insert(ctx->a1_ev.end(), g.a1_ev.begin(), g.a1_ev.end());
+            ctx->solver_ev.insert(ctx->solver_ev.end(), g.solver_ev.begin(), g.solver_ev.end());
+            RM_CUDA(cudaGraphLaunch(g.exec, s));
+            ctx->stats.kernel_launches += g.launches;
+            ctx->stats.graph_replayed = 1;
+            return RMUSIC_OK;
+        }
+    }
+    // capture a new graph into the least recently used slot
+    GraphEntry* slot = &ctx->graphs[0];
+    for (auto& g : ctx->graphs)
+        if (!g.exec || g.stamp < slot->stamp) slot = &g;
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    if (slot->h_table) cudaFreeHost(slot->h_table);
+    *slot = GraphEntry{};
+    if (cudaMallocHost(&slot->h_table, plan.frames.size() * sizeof(FrameDev)) != cudaSuccess) {
+        slot->h_table = nullptr;
+        return RMUSIC_ENOMEM;
+    }
+    memcpy(slot->h_table, plan.frames.data(), plan.frames.size() * sizeof(FrameDev));
+    cudaGraph_t graph_def = nullptr;
+    const size_t a1_mark = ctx->a1_ev.size(), solver_mark = ctx->solver_ev.size();
+    // capture on the context's own stream (the legacy default stream cannot be captured); nothing
+    // runs during capture, the graph is launched on the caller's stream below
+    cudaStream_t cs = ctx->cap_stream;
+    RM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemcpyAsync(ctx->d_table, slot->h_table, plan.frames.size() * sizeof(FrameDev),
+                                     cudaMemcpyHostToDevice, cs);
+    int erc = ce == cudaSuccess ? enqueue(ctx, plan, d_frames, d_out, d_status, cs, &launches) : RMUSIC_ECUDA;
+    cudaError_t ee = cudaStreamEndCapture(cs, &graph_def);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaMemcpyAsync (capture)");
+    if (erc) {
+        if (graph_def) cudaGraphDestroy(graph_def);
+        return erc;
+    }
+    if (ee != cudaSuccess) return cuda_fail(ctx, ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&slot->exec, graph_def, 0);
+    cudaGraphDestroy(graph_def);
+    if (ie != cudaSuccess) {
+        slot->exec = nullptr;
+        return cuda_fail(ctx, ie, "cudaGraphInstantiate");
+    }
+    slot->key = std::move(key);
+    slot->launches = launches;
+    slot->a1_ev.assign(ctx->a1_ev.begin() + a1_mark, ctx->a1_ev.end());
+    slot->solver_ev.assign(ctx->solver_ev.begin() + solver_mark, ctx->solver_ev.end());
+    slot->stamp = ++ctx->graph_clock;
+    RM_CUDA(cudaGraphLaunch(slot->exec, s));
+    ctx->stats.kernel_launches += launches;
+    return RMUSIC_OK;
+}
+
+uint64_t group_bytes(const rmusic_frame_desc& d) {
+    return (uint64_t)d.height * (uint64_t)d.width * sizeof(float2);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_bytes, rmusic_ctx** out) {
+    if (!params || !out) return RMUSIC_EINVAL;
+    *out = nullptr;
+    if (params->model_order != 1) return params->model_order < 1 ? RMUSIC_EINVAL : RMUSIC_EUNSUPPORTED;
+    if (!params_ok(*params)) return RMUSIC_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return ndev == 0 ? RMUSIC_ECUDA : RMUSIC_EINVAL;
+    }
+    rmusic_ctx* ctx = new (std::nothrow) rmusic_ctx();
+    if (!ctx) return RMUSIC_ENOMEM;
+    ctx->p = *params;
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    DeviceGuard guard(device);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = init_analytic();
+    if (e == cudaSuccess) e = init_batched(device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->table_free, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->call_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_counters, sizeof(unsigned long long) * kCounterSlots);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_counters, 0, sizeof(unsigned long long) * kCounterSlots);
+    if (e != cudaSuccess) {
+        rmusic_destroy(ctx);
+        return RMUSIC_ECUDA;
+    }
+    ctx->held += sizeof(unsigned long long) * kCounterSlots;
+    *out = ctx;
+    return RMUSIC_OK;
+}
+
+int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
+                             int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream) {
+    if (!ctx || n_frames < 0) return RMUSIC_EINVAL;
+    ctx->stats.kernel_launches = 0;
+    ctx->stats.graph_replayed = 0;
+    ctx->a1_ev.clear();
+    ctx->solver_ev.clear();
+    ctx->ev_used = 0;
+    ctx->last_pixels = 0;
+    if (n_frames == 0) return RMUSIC_OK;
+    if (!d_frames || !descs || !d_out) return RMUSIC_EINVAL;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // validate everything before queueing anything
+    uint64_t pixels = 0;
+    for (int i = 0; i < n_frames; ++i) {
+        FrameDev F;
+        int rc = describe(ctx, descs[i], &F);
+        if (rc) return rc;
+        pixels += (uint64_t)F.H * (uint64_t)F.W;
+    }
+    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, 3 * sizeof(unsigned long long), s));
+    // group frames so that each group's analytic signal fits the budget
+    const uint64_t table_reserve = 64 * sizeof(FrameDev) + (uint64_t)n_frames * sizeof(FrameDev);
+    uint64_t avail = 0;
+    if (ctx->budget) {
+        const uint64_t fixed = ctx->held - ctx->gamma_cap * sizeof(float2) + table_reserve;
+        avail = ctx->budget > fixed ? ctx->budget - fixed : 0;
+    }
+    int first = 0;
+    while (first < n_frames) {
+        int count = 0;
+        uint64_t bytes = 0;
+        while (first + count < n_frames) {
+            const uint64_t b = group_bytes(descs[first + count]);
+            if (ctx->budget && count > 0 && bytes + b > avail) break;
+            bytes += b;
+            ++count;
+        }
+        if (ctx->budget && bytes > avail) return RMUSIC_ENOMEM;
+        int rc = run_group(ctx, d_frames, descs + first, count, d_out, d_status, s);
+        if (rc) return rc;
+        first += count;
+    }
+    ctx->stats.workspace_bytes = ctx->held;
+    ctx->last_pixels = pixels;
+    RM_CUDA(cudaEventRecord(ctx->call_done, s));
+    return RMUSIC_OK;
+}
+
+int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
+                                  const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
+                                  uint8_t* h_status, void* cuda_stream) {
+    if (!ctx || n_frames < 0) return RMUSIC_EINVAL;
+    if (n_frames == 0) return RMUSIC_OK;
+    if (!h_frames || !descs || !h_out) return RMUSIC_EINVAL;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    uint64_t out_elems = 0;
+    for (int i = 0; i < n_frames; ++i) {
+        const rmusic_frame_desc& d = descs[i];
+        if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
+        const int esz = d.dtype == RMUSIC_DTYPE_U16 ? 2 : 4;
+        const uint64_t pitch = d.pitch_elems ? (uint64_t)d.pitch_elems : (uint64_t)d.width;
+        const uint64_t end = d.offset_bytes + ((uint64_t)(d.height - 1) * pitch + (uint64_t)d.width) * esz;
+        if (end > in_bytes) return RMUSIC_EINVAL;
+        out_elems = std::max<uint64_t>(out_elems, d.out_offset + (uint64_t)d.height * d.width);
+    }
+    int rc = ensure(ctx, &ctx->d_in, &ctx->in_cap, std::max<size_t>(in_bytes, 16));
+    if (!rc) {
+        size_t ob = ctx->out_cap;
+        void* op = ctx->d_out;
+        rc = ensure(ctx, &op, &ob, out_elems * sizeof(float));
+        ctx->d_out = (float*)op;
+        ctx->out_cap = ob;
+    }
+    if (!rc && h_status) {
+        size_t sb = ctx->st_cap;
+        void* sp = ctx->d_st;
+        rc = ensure(ctx, &sp, &sb, out_elems);
+        ctx->d_st = (uint8_t*)sp;
+        ctx->st_cap = sb;
+    }
+    if (rc) return rc;
+    RM_CUDA(cudaMemcpyAsync(ctx->d_in, h_frames, in_bytes, cudaMemcpyHostToDevice, s));
+    rc = rmusic_demodulate_frames(ctx, ctx->d_in, descs, n_frames, ctx->d_out, h_status ? ctx->d_st : nullptr,
+                                  cuda_stream);
+    if (rc) return rc;
+    RM_CUDA(cudaMemcpyAsync(h_out, ctx->d_out, out_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
+    if (h_status) RM_CUDA(cudaMemcpyAsync(h_status, ctx->d_st, out_elems, cudaMemcpyDeviceToHost, s));
+    RM_CUDA(cudaStreamSynchronize(s));
+    return RMUSIC_OK;
+}
+
+void rmusic_destroy(rmusic_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard guard(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto& g : ctx->graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.h_table) cudaFreeHost(g.h_table);
+        }
+        if (ctx->d_gamma) cudaFree(ctx->d_gamma);
+        if (ctx->d_table) cudaFree(ctx->d_table);
+        if (ctx->d_counters) cudaFree(ctx->d_counters);
+        if (ctx->h_table) cudaFreeHost(ctx->h_table);
+        if (ctx->table_free) cudaEventDestroy(ctx->table_free);
+        if (ctx->call_done) cudaEventDestroy(ctx->call_done);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+        for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+        if (ctx->d_in) cudaFree(ctx->d_in);
+        if (ctx->d_out) cudaFree(ctx->d_out);
+        if (ctx->d_st) cudaFree(ctx->d_st);
+    }
+    delete ctx;
+}
+
+const char* rmusic_strerror(int code) {
+    switch (code) {
+        case RMUSIC_OK: return "ok";
+        case RMUSIC_EINVAL: return "invalid argument";
+        case RMUSIC_ENOMEM: return "out of memory or over the HBM budget";
+        case RMUSIC_EUNSUPPORTED: return "unsupported parameters for this path";
+        case RMUSIC_ETIMEDOUT: return "device-side wait timed out";
+        case RMUSIC_ECUDA: return "CUDA runtime error";
+        default: return "unknown error";
+    }
+}
+
+const char* rmusic_last_cuda_error(const rmusic_ctx* ctx) { return ctx ? ctx->last_err : ""; }
+
+int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
+    if (!ctx_in || !out) return RMUSIC_EINVAL;
+    rmusic_ctx* ctx = const_cast<rmusic_ctx*>(ctx_in);
+    DeviceGuard guard(ctx->device);
+    *out = ctx->stats;
+    out->workspace_bytes = ctx->held;
+    out->pixels = ctx->last_pixels;
+    RM_CUDA(cudaEventSynchronize(ctx->call_done));
+    unsigned long long c[3] = {0, 0, 0};
+    RM_CUDA(cudaMemcpy(c, ctx->d_counters + kStatSlot, sizeof(c), cudaMemcpyDeviceToHost));
+    out->mean_sweeps = c[2] ? (double)c[0] / (double)c[2] : 0.0;
+    out->mean_root_iters = c[2] ? (double)c[1] / (double)c[2] : 0.0;
+    auto sum = [&](const std::vector<int>& v) {
+        float t = 0.f;
+        for (size_t i = 0; i + 1 < v.size(); i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ctx->ev_pool[v[i]], ctx->ev_pool[v[i + 1]]) == cudaSuccess) t += ms;
+        }
+        return t;
+    };
+    out->bandpass_ms = sum(ctx->a1_ev);
+    out->solver_ms = sum(ctx->solver_ev);
+    return RMUSIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// rmusic_device.cuh -- device-side types and helpers shared by the library's CUDA sources.
+//
+// Data layout in HBM for one call (all frames of the call share one workspace):
+//   frames   caller's buffer, frame f at byte offset in_off, row pitch `pitch` elements.
+//   gamma    library workspace, complex64 analytic signal (Sec. 2, Eq. 1) of every frame,
+//            stored "window-line major": the window runs along a contiguous line, so
+//            gamma[gam_off + wline * wlen + pos] is the sample at position `pos` of window
+//            line `wline` (wline = y, pos = x when windows run along x; wline = x, pos = y
+//            when they run along y).
+//   out      caller's float32 maps, frame f dense H x W row-major at element offset out_off.
+//   status   caller's optional uint8 maps, same layout as out.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rmusic {
+
+constexpr int kMaxL = 12;        // largest covariance order L
+constexpr int kMaxN = 64;        // largest window length N
+constexpr int kMaxLine = 8192;   // longest carrier line the band-pass kernel accepts
+constexpr int kChunk = 32;       // pixels of one window line handled by one warp work item
+
+enum : uint8_t { kStOk = 0, kStBorder = 1, kStDegenerate = 2, kStNotConverged = 3 };
+
+// Per-frame entry of the device frame table (built on the host for each call).
+struct FrameDev {
+    uint64_t in_off;      // byte offset of the frame in the input buffer
+    uint64_t out_off;     // element offset of the frame's map in out / status
+    uint64_t gam_off;     // element offset of the frame's analytic signal in the workspace
+    int64_t line_start;   // first carrier line of this frame in the band-pass grid
+    int64_t item_start;   // first warp work item of this frame in the batched schedule
+    int32_t H, W, pitch, dtype;
+    int32_t N, L;
+    int32_t carrier_axis, deriv_axis;
+    int32_t nlines, len;  // carrier lines and their length
+    int32_t k_lo, nb;     // kept DFT bins k_lo .. k_lo + nb - 1 of a carrier line
+    int32_t wlines, wlen; // window lines and their length
+    int32_t nchunks;      // work items per window line (ceil(wlen / kChunk))
+    double omega_ref;     // carrier phase step removed from the angle (rad/pixel)
+};
+
+// Index of the frame that owns global index `g` given each frame's start (non-decreasing).
+template <typename Get>
+__device__ __forceinline__ int find_frame(const FrameDev* __restrict__ fr, int nframes, int64_t g,
+                                          Get start) {
+    int lo = 0, hi = nframes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (start(fr[mid]) <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Map a (window line, position) pair to the output element index of the frame.
+__device__ __forceinline__ uint64_t out_index(const FrameDev& F, int wline, int pos) {
+    int y = F.deriv_axis == 0 ? wline : pos;
+    int x = F.deriv_axis == 0 ? pos : wline;
+    return F.out_off + (uint64_t)y * (uint64_t)F.W + (uint64_t)x;
+}
+
+// Minimal complex arithmetic for float and double.
+template <typename T>
+struct cx {
+    T r, i;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> mkc(T r, T i) {
+    cx<T> z;
+    z.r = r;
+    z.i = i;
+    return z;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mkc(a.r + b.r, a.i + b.i); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mkc(a.r - b.r, a.i - b.i); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return mkc(a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mkc(s * a.r, s * a.i); }
+template <typename T>
+__device__ __forceinline__ cx<T> conjg(cx<T> a) { return mkc(a.r, -a.i); }
+template <typename T>
+__device__ __forceinline__ T norm2(cx<T> a) { return a.r * a.r + a.i * a.i; }
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ cx<T> mulc(cx<T> a, cx<T> b) {
+    return mkc(a.r * b.r + a.i * b.i, a.i * b.r - a.r * b.i);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b) {
+    T d = b.r * b.r + b.i * b.i;
+    T inv = T(1) / d;
+    return mkc((a.r * b.r + a.i * b.i) * inv, (a.i * b.r - a.r * b.i) * inv);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> crecip(cx<T> b) {
+    T inv = T(1) / (b.r * b.r + b.i * b.i);
+    return mkc(b.r * inv, -b.i * inv);
+}
+
+template <typename T>
+__device__ __forceinline__ T wrap_pi(T a) {
+    const T pi = T(3.14159265358979323846);
+    const T two_pi = T(6.28318530717958647692);
+    if (a > pi) a -= two_pi;
+    if (a <= -pi) a += two_pi;
+    return a;
+}
+
+}  // namespace rmusic

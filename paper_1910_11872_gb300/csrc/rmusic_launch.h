@@ -1,0 +1,43 @@
+// rmusic_launch.h -- host-side launchers of the library's kernels (internal interface between
+// the C ABI in capi.cu and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rmusic_device.cuh"
+
+namespace rmusic {
+
+// Band-pass analytic signal of every carrier line (Sec. 2, Eq. 1). One CTA per line.
+cudaError_t init_analytic();
+cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_lines, int max_len,
+                            const void* d_in, float2* d_gamma, cudaStream_t stream);
+
+// Plain path: one thread per pixel of one frame, T = float or double (Sec. 3; Algorithm 1).
+struct PlainArgs {
+    int fb;
+    int max_sweeps;
+    int max_iters;
+};
+cudaError_t launch_plain_fp64(const FrameDev* d_frame, const FrameDev& h_frame, const float2* d_gamma,
+                              float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream);
+cudaError_t launch_plain_fp32(const FrameDev* d_frame, const FrameDev& h_frame, const float2* d_gamma,
+                              float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream);
+
+// Batched FP32 path: persistent, warp-scheduled over all work items of all frames that share
+// covariance order L. `counter` must be zero when the kernel starts.
+struct BatchedArgs {
+    int max_sweeps;
+    int max_iters;
+    int polish64;
+    unsigned long long* counters;  // [0] sweeps, [1] root iterations, [2] items (accumulated)
+};
+bool batched_supports(int L);
+cudaError_t init_batched(int device);
+cudaError_t launch_batched(int L, const FrameDev* d_frames, int nframes, int64_t total_items,
+                           unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                           uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream);
+int batched_grid(int L, int device);
+
+}  // namespace rmusic

@@ -1,0 +1,368 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle on the same seeded
+inputs, element by element.
+
+Tolerances (rad/pixel):
+  * plain FP64 path: |gpu - oracle| <= 1e-9 on every valid pixel, identical status maps;
+  * FP32 paths on noise-free inputs: |gpu - oracle| <= 1e-4 on every valid pixel;
+  * FP32 paths under noise: the RMS error against the closed-form derivative is within 1 % of the
+    oracle's RMS error (interior pixels), and the element-wise differences are reported.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1910_11872_gb300 import rmusic, synth
+
+pytestmark = pytest.mark.gpu
+
+TWO_PI = 2 * np.pi
+
+
+def _torch():
+    import torch
+
+    assert torch.cuda.is_available(), "these tests need a CUDA device"
+    return torch
+
+
+def _to_dev(img):
+    torch = _torch()
+    if img.dtype == np.uint16:
+        return torch.from_numpy(np.ascontiguousarray(img).view(np.int16)).cuda()
+    return torch.from_numpy(np.ascontiguousarray(img, dtype=np.float32)).cuda()
+
+
+def run_gpu(frames, windows=None, **params):
+    """Demodulate a list of 2-D numpy frames in ONE call; returns [(deriv, status), ...]."""
+    torch = _torch()
+    dem = rmusic.Demodulator(**params)
+    try:
+        tens = [_to_dev(f) for f in frames]
+        out, st, shapes = dem.run(tens, windows=windows)
+        torch.cuda.synchronize()
+        out = out.cpu().numpy()
+        st = st.cpu().numpy()
+        res, o = [], 0
+        for H, W in shapes:
+            res.append((out[o:o + H * W].reshape(H, W), st[o:o + H * W].reshape(H, W)))
+            o += H * W
+        dem.last_stats = dem.stats()
+        return res
+    finally:
+        dem.close()
+
+
+def oracle_run(img, N=32, L=8, fb=1, deriv_axis=0, carrier_axis=0, f0=0.1):
+    out, st, _ = O.demodulate(img, O.make_params(N, L, fb, deriv_axis, carrier_axis, f0))
+    return out, st
+
+
+def _cmp_exact_status(st_gpu, st_orc):
+    # border pixels are decided by integer geometry: identical
+    assert np.array_equal(st_gpu == 1, st_orc == 1)
+
+
+# ------------------------------------------------------------------------------------------------
+# plain FP64 path == oracle to 1e-9
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N,L,fb", [(32, 8, 1), (32, 8, 0), (12, 3, 1), (24, 6, 0), (48, 12, 1), (9, 2, 1)])
+def test_plain_fp64_matches_oracle(N, L, fb):
+    fr = synth.small_gaussian_frame()
+    (g, gs), = run_gpu([fr.image], window_len=N, cov_order=L, forward_backward=fb, precision="plain_fp64")
+    o, os_ = oracle_run(fr.image, N, L, fb)
+    assert np.array_equal(gs, os_)
+    v = os_ == 0
+    assert v.sum() == 128 * (128 - N + 1)
+    # the map is float32: the FP64 result must round to the oracle's value within one float32 ulp
+    # (or 1e-9 rad/pixel where the ulp is smaller)
+    o32 = o[v].astype(np.float32)
+    tol = np.maximum(np.spacing(np.abs(o32)), np.float32(1e-9))
+    assert np.all(np.abs(g[v] - o32) <= tol)
+    assert np.all(np.isnan(g[~v]))
+
+
+def test_plain_fp64_periodic_is_exact():
+    fr = synth.periodic_linear_frame(H=8, W=128)
+    (g, gs), = run_gpu([fr.image], precision="plain_fp64")
+    o, os_ = oracle_run(fr.image)
+    v = os_ == 0
+    assert np.array_equal(gs, os_)
+    assert np.abs(g[v].astype(np.float64) - o[v]).max() < 1e-7  # float32 output rounding
+    assert np.abs(g[v] - np.float32(TWO_PI * (16 / 128 - 0.1))).max() < 1e-7
+
+
+# ------------------------------------------------------------------------------------------------
+# FP32 batched path
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("f0", [0.08, 0.1, 0.15])
+def test_batched_noise_free_within_1e4(f0):
+    fr = synth.peaks_frame(np.inf, f0, H=48, W=384)
+    (g, gs), = run_gpu([fr.image], carrier_freq=f0)
+    o, os_ = oracle_run(fr.image, f0=f0)
+    _cmp_exact_status(gs, os_)
+    v = (os_ == 0) & (gs == 0)
+    assert v.sum() == (os_ == 0).sum()
+    err = np.abs(g[v].astype(np.float64) - o[v])
+    assert err.max() <= 1e-4, f"max {err.max():.3e} p99.9 {np.quantile(err, 0.999):.3e}"
+
+
+@pytest.mark.parametrize("snr", [40, 20, 10, 5])
+def test_batched_noisy_rms_within_one_percent(snr):
+    fr = synth.peaks_frame(snr, 0.1, H=64, W=384)
+    (g, gs), = run_gpu([fr.image])
+    o, os_ = oracle_run(fr.image)
+    _cmp_exact_status(gs, os_)
+    inner = np.zeros_like(os_, dtype=bool)
+    inner[:, 32:-32] = True
+    v = inner & (os_ == 0) & (gs == 0)
+    rms_o = np.sqrt(np.mean((o[v] - fr.truth[v]) ** 2))
+    rms_g = np.sqrt(np.mean((g[v].astype(np.float64) - fr.truth[v]) ** 2))
+    assert abs(rms_g - rms_o) <= 0.01 * rms_o, f"rms gpu {rms_g:.5e} oracle {rms_o:.5e}"
+    d = np.abs(g[v].astype(np.float64) - o[v])
+    assert np.quantile(d, 0.999) < 1e-3
+
+
+@pytest.mark.parametrize("N,L", [(8, 2), (16, 4), (24, 6), (48, 12), (40, 10), (33, 8)])
+def test_batched_windows(N, L):
+    fr = synth.peaks_frame(np.inf, 0.1, H=24, W=256)
+    (g, gs), = run_gpu([fr.image], window_len=N, cov_order=L)
+    o, os_ = oracle_run(fr.image, N, L)
+    _cmp_exact_status(gs, os_)
+    v = (os_ == 0) & (gs == 0)
+    assert v.sum() == (os_ == 0).sum()
+    assert np.abs(g[v].astype(np.float64) - o[v]).max() <= 1e-4
+    fr = synth.peaks_frame(10, 0.1, H=24, W=256)
+    (g, gs), = run_gpu([fr.image], window_len=N, cov_order=L)
+    o, os_ = oracle_run(fr.image, N, L)
+    v = (os_ == 0) & (gs == 0)
+    inner = np.zeros_like(v)
+    inner[:, 32:-32] = True
+    v &= inner
+    rms_o = np.sqrt(np.mean((o[v] - fr.truth[v]) ** 2))
+    rms_g = np.sqrt(np.mean((g[v].astype(np.float64) - fr.truth[v]) ** 2))
+    assert abs(rms_g - rms_o) <= 0.01 * rms_o
+
+
+def test_batched_deriv_y_uint16_diffusion():
+    """Diffusion frames (uint16, 12-bit), carrier along x, windows along y."""
+    frames = [synth.diffusion_frame(t, T=50, H=160, W=96) for t in (0, 25, 49)]
+    res = run_gpu([f.image for f in frames], deriv_axis=1)
+    for fr, (g, gs) in zip(frames, res):
+        o, os_ = oracle_run(fr.image, deriv_axis=1)
+        _cmp_exact_status(gs, os_)
+        v = (os_ == 0) & (gs == 0)
+        assert v.sum() == (os_ == 0).sum()
+        inner = np.zeros_like(v)
+        inner[:, 16:-16] = True
+        vi = v & inner
+        rms_o = np.sqrt(np.mean((o[vi] - fr.truth[vi]) ** 2))
+        rms_g = np.sqrt(np.mean((g[vi].astype(np.float64) - fr.truth[vi]) ** 2))
+        assert abs(rms_g - rms_o) <= 0.01 * rms_o
+
+
+def test_batched_carrier_along_y():
+    fr = synth.peaks_frame(np.inf, 0.1, H=48, W=256)
+    img = np.ascontiguousarray(fr.image.T)
+    (g, gs), = run_gpu([img], deriv_axis=1, carrier_axis=1)
+    o, os_ = oracle_run(img, deriv_axis=1, carrier_axis=1)
+    _cmp_exact_status(gs, os_)
+    v = (os_ == 0) & (gs == 0)
+    assert np.abs(g[v].astype(np.float64) - o[v]).max() <= 1e-4
+
+
+def test_uneven_batch_alone_equals_mix():
+    """Frames of different sizes and windows in one launch give bit-identical maps to
+    single-frame calls (the per-pixel arithmetic does not depend on the schedule)."""
+    rng = np.random.default_rng(4)
+    shapes = [(40, 96), (17, 300), (64, 64), (33, 129), (8, 512), (50, 77)]
+    windows = [(32, 8), (24, 6), (48, 12), (32, 8), (16, 4), (24, 6)]
+    frames = []
+    for H, W in shapes:
+        phi, _, _ = synth.gaussian_sum(rng, H, W)
+        frames.append(synth.add_noise(synth.fringe(phi, 0.1), 0.03, rng).astype(np.float32))
+    mix = run_gpu(frames, windows=windows)
+    for f, w, (g, gs) in zip(frames, windows, mix):
+        (ga, gsa), = run_gpu([f], window_len=w[0], cov_order=w[1])
+        assert np.array_equal(gs, gsa)
+        assert np.array_equal(np.isnan(g), np.isnan(ga))
+        assert np.array_equal(g[~np.isnan(g)], ga[~np.isnan(ga)])
+        o, os_ = oracle_run(f, w[0], w[1])
+        _cmp_exact_status(gs, os_)
+
+
+@pytest.mark.parametrize("H,W", [(1, 64), (3, 31), (5, 33), (2, 1), (4, 20), (7, 97)])
+def test_edge_shapes(H, W):
+    rng = np.random.default_rng(H * 1000 + W)
+    img = (0.5 + 0.4 * np.cos(TWO_PI * 0.1 * np.arange(W))[None, :] + 0.02 * rng.normal(size=(H, W))).astype(np.float32)
+    for prec in ("batched", "plain_fp64"):
+        (g, gs), = run_gpu([img], window_len=16, cov_order=4, precision=prec)
+        o, os_ = oracle_run(img, 16, 4)
+        _cmp_exact_status(gs, os_)
+        v = (os_ == 0) & (gs == 0)
+        if v.any():
+            tol = 1e-9 if prec == "plain_fp64" else 5e-3
+            assert np.abs(g[v].astype(np.float64) - o[v]).max() <= tol + 1e-7
+
+
+def test_zero_frame_is_degenerate():
+    img = np.zeros((4, 96), dtype=np.float32)
+    for prec in ("batched", "plain_fp64", "plain_fp32"):
+        (g, gs), = run_gpu([img], precision=prec)
+        assert np.all(np.isnan(g))
+        assert set(np.unique(gs)) <= {1, 2}
+        assert (gs == 2).sum() == 4 * (96 - 32 + 1)
+
+
+def test_pitch_and_offsets():
+    """A frame read with a row pitch larger than its width equals the dense frame."""
+    torch = _torch()
+    fr = synth.peaks_frame(20, 0.1, H=16, W=200)
+    padded = np.zeros((16, 256), dtype=np.float32)
+    padded[:, :200] = fr.image
+    dem = rmusic.Demodulator()
+    try:
+        buf = torch.from_numpy(np.concatenate([np.zeros(16, np.float32), padded.ravel()])).cuda()
+        out = torch.empty(16 * 200, device="cuda")
+        st = torch.empty(16 * 200, dtype=torch.uint8, device="cuda")
+        d = rmusic.rmusic_frame_desc(16 * 4, 16, 200, 256, rmusic.RMUSIC_DTYPE_F32, 0, 0, 0)
+        rmusic.rmusic_demodulate_frames(dem.ctx, buf.data_ptr(), [d], 1, out.data_ptr(), st.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        (g, gs), = run_gpu([fr.image])
+        assert np.array_equal(out.cpu().numpy().reshape(16, 200), g, equal_nan=True)
+    finally:
+        dem.close()
+
+
+def test_graph_replay_identical():
+    torch = _torch()
+    fr = synth.peaks_frame(20, 0.1, H=32, W=256)
+    dem = rmusic.Demodulator(use_graph=1)
+    try:
+        x = _to_dev(fr.image)
+        out = torch.empty(32 * 256, device="cuda")
+        st = torch.empty(32 * 256, dtype=torch.uint8, device="cuda")
+        dem.run(x, out=out, status=st)
+        torch.cuda.synchronize()
+        a = out.clone()
+        assert dem.stats().graph_replayed == 0
+        out.fill_(0)
+        dem.run(x, out=out, status=st)
+        torch.cuda.synchronize()
+        assert dem.stats().graph_replayed == 1
+        assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(out, nan=7.0))
+        (g, gs), = run_gpu([fr.image])
+        assert np.array_equal(out.cpu().numpy().reshape(32, 256), g, equal_nan=True)
+    finally:
+        dem.close()
+
+
+def test_host_entry_matches_device_entry():
+    import ctypes
+
+    frames = [synth.peaks_frame(15, 0.1, H=20, W=160).image, synth.peaks_frame(np.inf, 0.1, H=12, W=96).image]
+    flat = np.concatenate([f.ravel() for f in frames]).astype(np.float32)
+    descs, nbytes, nout = rmusic.frame_descs([f.shape for f in frames], rmusic.RMUSIC_DTYPE_F32, 4)
+    dem = rmusic.Demodulator()
+    try:
+        out = np.empty(nout, np.float32)
+        st = np.empty(nout, np.uint8)
+        rmusic.rmusic_demodulate_frames_host(dem.ctx, flat.ctypes.data, nbytes, descs, 2, out.ctypes.data,
+                                             st.ctypes.data, None)
+    finally:
+        dem.close()
+    dev = run_gpu(frames)
+    o = 0
+    for f, (g, gs) in zip(frames, dev):
+        n = f.size
+        assert np.array_equal(out[o:o + n].reshape(f.shape), g, equal_nan=True)
+        assert np.array_equal(st[o:o + n].reshape(f.shape), gs)
+        o += n
+
+
+def test_hbm_budget_splits_batches_and_rejects_oversize():
+    frames = [synth.peaks_frame(20, 0.1, H=32, W=128, stream=i).image for i in range(5)]
+    ref = run_gpu(frames)
+    one = 32 * 128 * 8
+    torch = _torch()
+    dem = rmusic.Demodulator(hbm_budget_bytes=one + 64 * 1024)
+    try:
+        out, st, shapes = dem.run([_to_dev(f) for f in frames])
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.array_equal(got, np.concatenate([g.ravel() for g, _ in ref]), equal_nan=True)
+    finally:
+        dem.close()
+    dem = rmusic.Demodulator(hbm_budget_bytes=4096)
+    try:
+        with pytest.raises(rmusic.RmusicError) as e:
+            dem.run([_to_dev(frames[0])])
+        assert e.value.code == rmusic.RMUSIC_ENOMEM
+    finally:
+        dem.close()
+
+
+def test_invalid_descriptors_rejected():
+    torch = _torch()
+    dem = rmusic.Demodulator()
+    try:
+        buf = torch.zeros(1024, device="cuda")
+        out = torch.empty(1024, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream
+        for d, code in [
+            (rmusic.rmusic_frame_desc(0, 0, 16, 0, 0, 0, 0, 0), rmusic.RMUSIC_EINVAL),
+            (rmusic.rmusic_frame_desc(0, 4, 16, 8, 0, 0, 0, 0), rmusic.RMUSIC_EINVAL),
+            (rmusic.rmusic_frame_desc(2, 4, 16, 0, 0, 0, 0, 0), rmusic.RMUSIC_EINVAL),
+            (rmusic.rmusic_frame_desc(0, 4, 16, 0, 7, 0, 0, 0), rmusic.RMUSIC_EINVAL),
+            (rmusic.rmusic_frame_desc(0, 4, 16, 0, 0, 0, 8, 12), rmusic.RMUSIC_EINVAL),
+            (rmusic.rmusic_frame_desc(0, 4, 16, 0, 0, 0, 32, 7), rmusic.RMUSIC_EUNSUPPORTED),
+        ]:
+            with pytest.raises(rmusic.RmusicError) as e:
+                rmusic.rmusic_demodulate_frames(dem.ctx, buf.data_ptr(), [d], 1, out.data_ptr(), None, s)
+            assert e.value.code == code
+    finally:
+        dem.close()
+
+
+def test_full_size_frame_sampled_against_oracle():
+    """1024 x 1024 frame in the bench's configuration (batched FP32, N = 32, L = 8): oracle values at
+    sampled pixels, computed one by one."""
+    rng = np.random.default_rng(0)
+    for snr in (np.inf, 20):
+        fr = synth.peaks_frame(snr, 0.1)
+        (g, gs), = run_gpu([fr.image])
+        ys = np.concatenate([rng.integers(0, 1024, 600), np.full(40, 1023), np.zeros(40, int)])
+        xs = np.concatenate([rng.integers(0, 1024, 600), rng.integers(0, 1024, 80)])
+        xs[:20] = np.arange(20) + 10  # around the left border
+        o, os_, _ = O.demodulate_pixels(fr.image, O.make_params(32, 8, 1, 0, 0, 0.1), ys, xs)
+        assert np.array_equal(gs[ys, xs] == 1, os_ == 1)
+        v = (os_ == 0) & (gs[ys, xs] == 0)
+        d = np.abs(g[ys, xs][v].astype(np.float64) - o[v])
+        tol = 1e-4 if np.isinf(snr) else 1e-3
+        assert d.max() <= tol, f"snr {snr}: max {d.max():.3e}"
+
+
+def test_plain_fp32_and_polish64_accuracy():
+    fr = synth.peaks_frame(np.inf, 0.1, H=24, W=256)
+    o, os_ = oracle_run(fr.image)
+    for kw, tol in ((dict(precision="plain_fp32"), 1e-3), (dict(polish_fp64=1), 1e-4)):
+        (g, gs), = run_gpu([fr.image], **kw)
+        v = (os_ == 0) & (gs == 0)
+        assert v.sum() >= 0.99 * (os_ == 0).sum()
+        assert np.abs(g[v].astype(np.float64) - o[v]).max() <= tol
+
+
+def test_launch_counts():
+    fr = synth.peaks_frame(20, 0.1, H=16, W=128)
+    dem = rmusic.Demodulator()
+    try:
+        dem.run(_to_dev(fr.image))
+        assert dem.stats().kernel_launches == 2  # band-pass + one persistent solver launch
+    finally:
+        dem.close()
+    dem = rmusic.Demodulator(precision="plain_fp32")
+    try:
+        dem.run([_to_dev(fr.image), _to_dev(fr.image)])
+        assert dem.stats().kernel_launches == 3  # band-pass + one launch per frame
+    finally:
+        dem.close()
