@@ -61,19 +61,33 @@ def frames_for(rank: int):
     return [synth.peaks_frame(s, F0, H, W, stream=rank) for s in SNRS]
 
 
-def flops_per_pixel(L: int, N: int, sweeps: float, iters: float) -> float:
-    """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1)."""
+def flops_per_pixel(L: int, N: int, sweeps: float, iters: float, updates: float) -> float:
+    """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1),
+    counted from the kernel's steps with the measured sweeps, root iterations and executed root
+    updates per 32-pixel work item:
+      covariance  per lag: (31 + N) / 32 lag products (6) and prefix adds (2) per pixel, a 5-step
+                  warp scan (10); per R_f entry: box difference (2) and accumulation into S (6)
+      Jacobi      per rotation 14 + 6 (L - 2) + 4, L/2 rotations per step, L - 1 steps per sweep,
+                  plus the off-diagonal norm L (L - 1)
+      inverse it. L D L^T of (mu I - S), two forward / diagonal / backward solves with norms
+      polynomial  u = Q x (2 L), rho_k (8 flops per term), scaling and moduli
+      Aberth      per iteration and inner root: Horner of Q, Q' and the bound over 2L - 2 steps
+                  (18 per step) and the residual test (6); per executed update: Q/Q' (11), the
+                  2(L-1) - 1 reciprocal terms (10 each), the correction (12) and the mirror (8)
+      polish      two Horner passes of Q, Q', Q'' (24 per step) and the step (20), angle (20)
+    """
     NS = L * (L + 1) // 2
     NR = 2 * L - 2
-    h = L // 2
-    cov = L * (31 + N) / 32 * (6 + 2) + NS * 4 + h * h * 8
-    rot = 14 + 6 * (L - 2)
-    jac = sweeps * (L * (L - 1) // 2 * rot + L * (L - 1))
-    ldl = sum(3 * j + (L - 1 - j) * (3 * j + 1) for j in range(L))
+    NI = L - 1
+    cov = L * ((31 + N) / 32 * 8 + 10) + NS * 8 + L + NS + 1
+    rot = 14 + 6 * (L - 2) + 4
+    jac = sweeps * ((L - 1) * (L // 2) * rot + L * (L - 1))
+    ldl = sum(3 * j + 1 + (L - 1 - j) * (3 * j + 1) for j in range(L))
     inv = ldl + 2 * (2 * L * (L - 1) + 4 * L)
-    coef = 8 * L * (L - 1) // 2 + 3 * L + 2 * L
-    aberth = iters * NR * (16 * NR + 2 * NR + 10 * (NR - 1) + 30)
-    polish = 2 * (24 * NR + 30) + 20
+    coef = 2 * L + 3 * L + 4 * L * (L - 1) + 5 * (L - 1)
+    per_update = 11 + 10 * (2 * NI - 1) + 12 + 8
+    aberth = iters * NI * (18 * NR + 6) + updates * per_update
+    polish = 2 * (24 * NR + 20) + 20
     return cov + jac + inv + coef + aberth + polish
 
 
@@ -236,7 +250,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    solver_ms, bandpass_ms, launches, sweeps, iters = [], [], 0, [], []
+    solver_ms, bandpass_ms, launches, sweeps, iters, updates = [], [], 0, [], [], []
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -248,6 +262,7 @@ def run_ours(args):
         launches += st.kernel_launches
         sweeps.append(st.mean_sweeps)
         iters.append(st.mean_root_iters)
+        updates.append(st.mean_root_updates)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -294,7 +309,7 @@ def run_ours(args):
     e2e_value = npx * world / (e2e_ms * 1e3)
 
     # ---- roofline of the dominant kernel (batched solver) ---------------------------------------
-    fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(iters))
+    fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(iters), statistics.mean(updates))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
     traffic = None
@@ -309,6 +324,7 @@ def run_ours(args):
                 "kernel": "batched_kernel<8>", "flops_per_pixel": fpp, "launch_ms": solver_avg,
                 "peak_note": "FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "mean_jacobi_sweeps": statistics.mean(sweeps), "mean_root_iters": statistics.mean(iters),
+                "mean_root_updates": statistics.mean(updates),
                 "bandpass_ms": statistics.mean(bandpass_ms)}
 
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,

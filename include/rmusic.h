@@ -167,6 +167,8 @@ const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
  *   pixels           pixels of all frames of the last call.
  *   mean_sweeps      batched path: Jacobi sweeps per 32-pixel work item, averaged.
  *   mean_root_iters  batched path: Aberth iterations per 32-pixel work item, averaged.
+ *   mean_root_updates batched path: Aberth root updates a warp executed per work item, averaged
+ *                    (roots already converged in every lane of the warp are skipped).
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
  *                    call's stream) of the band-pass launches and of the solver launches.
  * rmusic_get_stats waits until the last call's work has finished. */
@@ -177,6 +179,7 @@ typedef struct {
     uint64_t pixels;
     double mean_sweeps;
     double mean_root_iters;
+    double mean_root_updates;
     float bandpass_ms;
     float solver_ms;
 } rmusic_stats;

@@ -274,8 +274,8 @@ void orc_music_poly(const cplx* u, int32_t L, cplx* q) {
  * Aberth-Ehrlich iteration in FP64: z_i <- z_i - w_i, w_i = N_i / (1 - N_i S_i),
  * N_i = Q(z_i)/Q'(z_i), S_i = sum_{j != i} 1/(z_i - z_j), updated in place. A root is
  * accepted once |Q(z_i)| <= 1e-14 sum_k |q_k| |z_i|^k (the value is at the rounding
- * level). Exact zero leading coefficients (roots at infinity) are dropped; exact zero
- * trailing coefficients give roots at 0.
+ * level), and two closing sweeps refine all roots together. Exact zero leading coefficients
+ * (roots at infinity) are dropped; exact zero trailing coefficients give roots at 0.
  * q[0..deg] ascending powers. Writes the finite roots to roots[] and returns their
  * count; *not_conv is set when 500 iterations did not settle every root.
  * ------------------------------------------------------------------------------- */
@@ -333,6 +333,34 @@ int orc_poly_roots(const cplx* q_in, int32_t deg, cplx* roots, int32_t* not_conv
         if (!active) break;
     }
     if (it == 500) *not_conv = 1;
+    /* The residual test accepts a root once its backward error is at the rounding level; for
+       a simple root lying close to another one (a pair z, 1/conj(z) near the circle) the
+       forward error can still be ~1e-9. Two more Aberth sweeps, whose corrections account for
+       the neighbouring roots, bring such roots to the accuracy the double-precision
+       coefficients allow. Roots with another root within 1e-6 (one double root split by
+       rounding, resolved in the selection step) are left as they are, and a correction is
+       kept only if it lowers |Q|. */
+    for (int sweep = 0; sweep < 2; ++sweep)
+        for (int32_t i = 0; i < n; ++i) {
+            double near = INFINITY;
+            for (int32_t j = 0; j < n; ++j)
+                if (j != i && cabs(z[i] - z[j]) < near) near = cabs(z[i] - z[j]);
+            if (!(near >= 1e-6)) continue;
+            cplx p, dp;
+            double b;
+            orc_horner(q, n, z[i], &p, &dp, &b);
+            if (p == 0.0 || dp == 0.0) continue;
+            cplx Ni = p / dp;
+            cplx Si = 0.0;
+            for (int32_t j = 0; j < n; ++j)
+                if (j != i) Si += 1.0 / (z[i] - z[j]);
+            cplx w = Ni / (1.0 - Ni * Si);
+            if (!(isfinite(creal(w)) && isfinite(cimag(w)))) continue;
+            cplx p2, dp2;
+            double b2;
+            orc_horner(q, n, z[i] - w, &p2, &dp2, &b2);
+            if (cabs(p2) < cabs(p)) z[i] -= w;
+        }
     return n + nzero;
 }
 

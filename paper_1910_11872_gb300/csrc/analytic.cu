@@ -11,8 +11,10 @@
 //   G[n]   = (1/len) exp(2 pi j k_lo n / len) sum_i X[k_lo + i] zeta_n^i,  zeta_n = exp(2 pi j n / len)
 // The forward sums are re-anchored every 32 samples with an exactly reduced twiddle
 // exp(-2 pi j (k * n0 mod len) / len), so rounding in xi_k never compounds over more than 32
-// steps. All sincos values come from sincospif on arguments in [0, 2). Work per pixel is
+// steps. All sincos values come from sincospi on arguments in [0, 2). Work per pixel is
 // about 4 nb FMAs each way (nb ~ 100 at len = 1024, f0 = 0.1): a few percent of the solver.
+// T = float feeds the FP32 paths (complex64 output); T = double feeds the plain FP64 path
+// (complex128 output), so that path is double precision end to end.
 #include "rmusic_device.cuh"
 #include "rmusic_launch.h"
 
@@ -21,28 +23,44 @@ namespace rmusic {
 constexpr int kA1Threads = 256;
 constexpr int kA1Block = 32;  // forward Horner re-anchoring period
 
+template <typename T>
+__device__ __forceinline__ void sincospi_t(T x, T* s, T* c);
+template <>
+__device__ __forceinline__ void sincospi_t<float>(float x, float* s, float* c) { sincospif(x, s, c); }
+template <>
+__device__ __forceinline__ void sincospi_t<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename T>
 __global__ void __launch_bounds__(kA1Threads)
 analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned char* __restrict__ in,
-                float2* __restrict__ gam) {
-    extern __shared__ float a1_smem[];
-    __shared__ float red[kA1Threads / 32];
+                cx<T>* __restrict__ gam) {
+    extern __shared__ double a1_smem_d[];
+    T* a1_smem = reinterpret_cast<T*>(a1_smem_d);
+    __shared__ T red[kA1Threads / 32];
     const int64_t line = blockIdx.x;
     const int f = find_frame(fr, nframes, line, [](const FrameDev& F) { return F.line_start; });
     const FrameDev& F = fr[f];
     const int li = (int)(line - F.line_start);
     const int len = F.len;
-    float* v = a1_smem;
-    float2* X = reinterpret_cast<float2*>(a1_smem + ((len + 1) & ~1));
+    T* v = a1_smem;
+    cx<T>* X = reinterpret_cast<cx<T>*>(a1_smem + ((len + 1) & ~1));
 
     // load the line and its sum
-    float s = 0.f;
+    T s = 0;
     for (int n = threadIdx.x; n < len; n += blockDim.x) {
         uint64_t idx = F.carrier_axis == 0 ? (uint64_t)li * F.pitch + n : (uint64_t)n * F.pitch + li;
-        float val;
+        T val;
         if (F.dtype == 0)
-            val = reinterpret_cast<const float*>(in + F.in_off)[idx];
+            val = (T)reinterpret_cast<const float*>(in + F.in_off)[idx];
         else
-            val = (float)reinterpret_cast<const uint16_t*>(in + F.in_off)[idx];
+            val = (T)reinterpret_cast<const uint16_t*>(in + F.in_off)[idx];
         v[n] = val;
         s += val;
     }
@@ -50,80 +68,92 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
-    float tot = 0.f;
+    T tot = 0;
 #pragma unroll
     for (int w = 0; w < kA1Threads / 32; ++w) tot += red[w];
-    const float mean = tot / (float)len;
+    const T mean = tot / (T)len;
     for (int n = threadIdx.x; n < len; n += blockDim.x) v[n] -= mean;
     __syncthreads();
 
     // forward band-limited DFT, one thread per kept bin
-    const float two_over_len = 2.f / (float)len;
+    const T two_over_len = T(2) / (T)len;
     for (int b = threadIdx.x; b < F.nb; b += blockDim.x) {
         const int k = F.k_lo + b;
-        float sk, ck;
-        sincospif((float)k * two_over_len, &sk, &ck);  // xi = ck - j sk
-        float xr = 0.f, xi = 0.f;
+        T sk, ck;
+        sincospi_t<T>((T)k * two_over_len, &sk, &ck);  // xi = ck - j sk
+        T xr = 0, xi = 0;
         const int nblk = (len + kA1Block - 1) / kA1Block;
         for (int blk = nblk - 1; blk >= 0; --blk) {
             const int n0 = blk * kA1Block;
             const int n1 = min(len, n0 + kA1Block);
-            float pr = 0.f, pi = 0.f;  // sum_{i} v[n0 + i] xi^i by Horner
+            T pr = 0, pi = 0;  // sum_{i} v[n0 + i] xi^i by Horner
             for (int n = n1 - 1; n >= n0; --n) {
-                float nr = fmaf(pr, ck, fmaf(pi, sk, v[n]));
-                float ni = fmaf(pi, ck, -pr * sk);
+                T nr = fma_t<T>(pr, ck, fma_t<T>(pi, sk, v[n]));
+                T ni = fma_t<T>(pi, ck, -pr * sk);
                 pr = nr;
                 pi = ni;
             }
             // X += xi^{n0} * partial, with xi^{n0} from the exactly reduced index k n0 mod len
             const int m = (int)(((int64_t)k * n0) % len);
-            float sm, cm;
-            sincospif((float)m * two_over_len, &sm, &cm);  // xi^{n0} = cm - j sm
+            T sm, cm;
+            sincospi_t<T>((T)m * two_over_len, &sm, &cm);  // xi^{n0} = cm - j sm
             xr += pr * cm + pi * sm;
             xi += pi * cm - pr * sm;
         }
-        X[b] = make_float2(xr, xi);
+        X[b] = mkc(xr, xi);
     }
     __syncthreads();
 
     // inverse over the band, one thread per sample, stored window-line major
-    const float inv_len = 1.f / (float)len;
+    const T inv_len = T(1) / (T)len;
     for (int n = threadIdx.x; n < len; n += blockDim.x) {
-        float sn, cn;
-        sincospif((float)n * two_over_len, &sn, &cn);  // zeta = cn + j sn
-        float ar = 0.f, ai = 0.f;
+        T sn, cn;
+        sincospi_t<T>((T)n * two_over_len, &sn, &cn);  // zeta = cn + j sn
+        T ar = 0, ai = 0;
         for (int b = F.nb - 1; b >= 0; --b) {
-            const float2 x = X[b];
-            float nr = fmaf(ar, cn, fmaf(-ai, sn, x.x));
-            float ni = fmaf(ar, sn, fmaf(ai, cn, x.y));
+            const cx<T> x = X[b];
+            T nr = fma_t<T>(ar, cn, fma_t<T>(-ai, sn, x.r));
+            T ni = fma_t<T>(ar, sn, fma_t<T>(ai, cn, x.i));
             ar = nr;
             ai = ni;
         }
         const int m = (int)(((int64_t)F.k_lo * n) % len);
-        float s2, c2;
-        sincospif((float)m * two_over_len, &s2, &c2);
-        const float gr = (ar * c2 - ai * s2) * inv_len;
-        const float gi = (ar * s2 + ai * c2) * inv_len;
+        T s2, c2;
+        sincospi_t<T>((T)m * two_over_len, &s2, &c2);
+        const T gr = (ar * c2 - ai * s2) * inv_len;
+        const T gi = (ar * s2 + ai * c2) * inv_len;
         const int y = F.carrier_axis == 0 ? li : n;
         const int x = F.carrier_axis == 0 ? n : li;
         const int wline = F.deriv_axis == 0 ? y : x;
         const int pos = F.deriv_axis == 0 ? x : y;
-        gam[F.gam_off + (uint64_t)wline * F.wlen + pos] = make_float2(gr, gi);
+        gam[F.gam_off + (uint64_t)wline * F.wlen + pos] = mkc(gr, gi);
     }
 }
 
+template <typename T>
+static size_t a1_smem_bytes(int len) {
+    // v[len] + X[nb <= len/2]
+    return sizeof(T) * (size_t)((len + 1) & ~1) + 2 * sizeof(T) * (size_t)(len / 2 + 1);
+}
+
 cudaError_t init_analytic() {
-    return cudaFuncSetAttribute(analytic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(float) * kMaxLine + sizeof(float2) * (kMaxLine / 2 + 1)));
+    cudaError_t e = cudaFuncSetAttribute(analytic_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)a1_smem_bytes<float>(kMaxLine));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(analytic_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)a1_smem_bytes<double>(kMaxLine));
 }
 
 cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_lines, int max_len,
-                            const void* d_in, float2* d_gamma, cudaStream_t stream) {
+                            const void* d_in, void* d_gamma, bool fp64, cudaStream_t stream) {
     if (total_lines <= 0) return cudaSuccess;
-    // v[len] floats + X[nb <= len/2] float2
-    size_t smem = sizeof(float) * (size_t)((max_len + 1) & ~1) + sizeof(float2) * (size_t)(max_len / 2 + 1);
-    analytic_kernel<<<(unsigned)total_lines, kA1Threads, smem, stream>>>(
-        d_frames, nframes, static_cast<const unsigned char*>(d_in), d_gamma);
+    const unsigned char* in = static_cast<const unsigned char*>(d_in);
+    if (fp64)
+        analytic_kernel<double><<<(unsigned)total_lines, kA1Threads, a1_smem_bytes<double>(max_len), stream>>>(
+            d_frames, nframes, in, static_cast<cx<double>*>(d_gamma));
+    else
+        analytic_kernel<float><<<(unsigned)total_lines, kA1Threads, a1_smem_bytes<float>(max_len), stream>>>(
+            d_frames, nframes, in, static_cast<cx<float>*>(d_gamma));
     return cudaGetLastError();
 }
 

@@ -14,23 +14,25 @@
 //   FB -> S   with forward-backward averaging R = (R_f + J conj(R_f) J)/2 is centro-Hermitian,
 //             so with the unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) (even L) S = Q^H R Q =
 //             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x.
-//   eigen     cyclic Jacobi sweeps on S (real, register resident, fully unrolled) until the
+//   eigen     cyclic Jacobi sweeps on S (real, register resident, tournament order) until the
 //             off-diagonal mass is below 1e-4 of the trace -> the largest eigenvalue l1; then two
 //             steps of inverse iteration with (mu I - S) = L D L^T, mu just above l1, give the
 //             signal eigenvector x1 without accumulating rotations (Eq. 8-11).
-//   poly      u1 = Q x1 / |x1|; c_0 = L - 1, c_k = -sum_m u1[m] conj(u1[m+k]) / |u1|^2,
-//             c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14).
-//   roots     Aberth-Ehrlich on all 2L-2 roots. Starting points come from the estimator's
-//             structure: a pair straddling the circle at the angle of conj(rho_1) (the signal
-//             root), and pairs at radius r, 1/r (r = L / (L + 7.3)) at the side-lobe angles
-//             arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window puts the other
-//             roots. Iterations stop when every root of every lane of the warp has a residual
+//   poly      u1 = Q x1 / |x1|; c_0 = L - 1, c_k = -(1 - 2e-6) sum_m u1[m] conj(u1[m+k]) / |u1|^2,
+//             c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14). The 2e-6 shrink keeps the
+//             polynomial strictly positive on the circle in FP32 (see below).
+//   roots     Aberth-Ehrlich on the L - 1 roots inside the unit disk; the other L - 1 roots are
+//             their mirrors 1/conj(z) (the coefficients are conjugate-symmetric). Starting
+//             points come from the estimator's structure: the signal root just inside the circle
+//             at the angle of conj(rho_1), the others at radius r = L / (L + 7.3) at the
+//             side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window
+//             puts them. Iterations stop when every root of every lane of the warp has a residual
 //             at the FP32 rounding level.
-//   select    the root with |z| <= 1 + 1e-3 nearest the unit circle (Algorithm 1). A noise-free
-//             window gives a double root there, which FP32 splits by ~sqrt(eps); when another
-//             root lies within 4e-3 the pair is located as the root of Q' between them, otherwise
-//             the root is refined by Newton on Q with its conjugate-reciprocal partner 1/conj(z)
-//             divided out. Optionally one more such step runs in FP64.
+//   select    the inner root nearest the unit circle (Algorithm 1). A noise-free window gives a
+//             double root on the circle, which FP32 splits by ~sqrt(eps); when another root lies
+//             within 4e-3 the pair is located as the root of Q' between them, otherwise the root
+//             is refined by Newton on Q with its partner 1/conj(z) divided out. Optionally one
+//             more such step runs in FP64.
 //   angle     atan2 of the root minus the carrier step, wrapped (Eq. 15).
 #include <math.h>
 
@@ -45,6 +47,13 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ constexpr int tri(int r, int c, int L) {
     return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);
+}
+
+// Fixed relabeling of the Jacobi tournament: after a step over the pairs (0,1), (2,3), ...,
+// position p takes the index previously at tperm(p). Over L - 1 steps every pair of indices
+// meets once (the circle method: 0 stays, the others move around a ring).
+__host__ __device__ constexpr int tperm(int p, int L) {
+    return p == 0 ? 0 : (p == 1 ? (L > 2 ? 2 : 1) : (p % 2 == 1 ? p - 2 : (p == L - 2 ? L - 1 : p + 2)));
 }
 
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
@@ -115,17 +124,48 @@ __device__ __forceinline__ void horner_pdd64(const cx<float>* c, cx<double> z, c
     d2 = 2.0 * d2;
 }
 
+// Add entry (r, s) of R_f (value v) to S = Re(Q^H R_f Q) up to the factor 1/2, with the
+// unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) of even order L = 2h. Writing R_f in h x h blocks,
+// with i = fold(r), k = fold(s) (fold(t) = t for t < h, L - 1 - t otherwise):
+//   S11[i][k] =  Re(a + b + c + d),  S22[i][k] = Re(a - b - c + d),  S12[i][k] = -Im(a - b + c - d)
+// where a, b, c, d are the entries (i, k), (i, L-1-k), (L-1-i, k), (L-1-i, L-1-k). Only the upper
+// triangles of the symmetric blocks S11, S22 are kept (i <= k); S12 is kept whole.
 template <int L>
-__global__ void __launch_bounds__(kBatThreads)
+__device__ __forceinline__ void accumulate_s(float* S, int r, int s, cx<float> v) {
+    constexpr int h = L / 2;
+    const int i = r < h ? r : L - 1 - r;
+    const int k = s < h ? s : L - 1 - s;
+    if (s < h)
+        S[tri(i, h + k, L)] -= v.i;
+    else
+        S[tri(i, h + k, L)] += v.i;
+    if (i <= k) {
+        S[tri(i, k, L)] += v.r;
+        if ((r < h) == (s < h))
+            S[tri(h + i, h + k, L)] += v.r;
+        else
+            S[tri(h + i, h + k, L)] -= v.r;
+    }
+}
+
+// Register cap per covariance order: 4 CTAs of 128 threads per SM (<= 128 registers) for L <= 8.
+template <int L>
+struct MinBlocks {
+    static constexpr int value = L <= 8 ? 4 : 2;
+};
+
+template <int L>
+__global__ void __launch_bounds__(kBatThreads, MinBlocks<L>::value)
 batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
                unsigned long long* __restrict__ counter, const float2* __restrict__ gam,
                float* __restrict__ out, uint8_t* __restrict__ status, BatchedArgs args) {
     static_assert(L % 2 == 0 && L >= 2 && L <= kMaxL, "even L only");
     constexpr int h = L / 2;
     constexpr int NS = L * (L + 1) / 2;
-    constexpr int NR = 2 * L - 2;
+    constexpr int NI = L - 1;  // roots inside the unit disk (the other L - 1 are their mirrors)
     __shared__ float2 sh_seg[kBatWarps][32 + kMaxN];
     __shared__ float2 sh_pre[kBatWarps][3 * 32 + 1];
+    __shared__ float sh_S[NS * kBatThreads];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* seg = sh_seg[wid];
     float2* pre = sh_pre[wid];
@@ -155,9 +195,13 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         const bool inside = pos < wlen;
         const bool valid = inside && (pos - N / 2 >= 0) && (pos - N / 2 + N - 1 <= wlen - 1);
 
-        // ---- R_f by lag-product prefix sums -----------------------------------------------------
-        cx<float> Rf[NS];
-        const float invK = 1.0f / (float)K;
+        // ---- S = Re(Q^H R_f Q) accumulated from the lag-product box sums ------------------------
+        // Every box sum K R_f[m][m+d] (and its Hermitian mirror) is added straight into the
+        // entries of S it feeds, so R_f is never held whole. Constant factors (1/K, 1/2) are
+        // dropped: S is normalised by its trace below, which leaves its eigenvectors unchanged.
+        float S[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) S[i] = 0.f;
 #pragma unroll
         for (int d = 0; d < L; ++d) {
             const int G = 31 + N - d;  // lag products g_d[0 .. G-1] are needed
@@ -195,25 +239,11 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
 #pragma unroll
             for (int m = 0; m + d < L; ++m) {
                 const float2 hi = pre[lane + m + K], lo = pre[lane + m];
-                Rf[tri(m, m + d, L)] = mkc((hi.x - lo.x) * invK, (hi.y - lo.y) * invK);
+                const cx<float> v = mkc(hi.x - lo.x, hi.y - lo.y);  // K R_f[m][m+d]
+                accumulate_s<L>(S, m, m + d, v);
+                if (d > 0) accumulate_s<L>(S, m + d, m, conjg(v));
             }
         }
-
-        // ---- S = Re(Q^H R_f Q), normalised by its trace -----------------------------------------
-        auto RF = [&](int r, int c) { return r <= c ? Rf[tri(r, c, L)] : conjg(Rf[tri(c, r, L)]); };
-        float S[NS];
-#pragma unroll
-        for (int i = 0; i < h; ++i)
-#pragma unroll
-            for (int k = 0; k < h; ++k) {
-                const cx<float> a = RF(i, k), b = RF(i, L - 1 - k), c = RF(L - 1 - i, k),
-                                dd = RF(L - 1 - i, L - 1 - k);
-                if (i <= k) {
-                    S[tri(i, k, L)] = 0.5f * (a.r + b.r + c.r + dd.r);
-                    S[tri(h + i, h + k, L)] = 0.5f * (a.r - b.r - c.r + dd.r);
-                }
-                S[tri(i, h + k, L)] = -0.5f * (a.i - b.i + c.i - dd.i);
-            }
         float tr = 0.f;
 #pragma unroll
         for (int i = 0; i < L; ++i) tr += S[tri(i, i, L)];
@@ -227,49 +257,68 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         }
 
         // ---- cyclic Jacobi on S for the eigenvalues -----------------------------------------------
-        float A[NS];
+        // Tournament ("circle") ordering: each of the L - 1 steps of a sweep rotates the disjoint
+        // pairs (0,1), (2,3), ... and then relabels the indices by the fixed permutation tperm, so
+        // that every pair (p, q) is rotated exactly once per sweep and the labels return to the
+        // identity after the sweep. The step is one rolled loop body.
+        // The normalised S is parked in shared memory (one column per thread) for the inverse
+        // iteration; the rotations then work on S in place.
+        float* const Ssh = sh_S + threadIdx.x;
 #pragma unroll
-        for (int i = 0; i < NS; ++i) A[i] = S[i];
+        for (int i = 0; i < NS; ++i) Ssh[i * kBatThreads] = S[i];
         int sweeps = 0;
         bool jconv = false;
         for (;;) {
+#pragma unroll 1
+            for (int stp = 0; stp < L - 1; ++stp) {
 #pragma unroll
-            for (int p = 0; p < L - 1; ++p)
-#pragma unroll
-                for (int q = p + 1; q < L; ++q) {
-                    const float apq = A[tri(p, q, L)];
-                    const float dq = A[tri(q, q, L)] - A[tri(p, p, L)];
+                for (int p = 0; p < L; p += 2) {
+                    const int q = p + 1;
+                    const float apq = S[tri(p, q, L)];
+                    const float dq = S[tri(q, q, L)] - S[tri(p, p, L)];
                     const float den = fabsf(dq) + sqrtf(fmaf(dq, dq, 4.f * apq * apq));
                     float t = den > 0.f ? __fdividef(2.f * apq, den) : 0.f;
                     t = dq < 0.f ? -t : t;
                     const float c = rsqrtf(fmaf(t, t, 1.f));
                     const float s = t * c;
-                    A[tri(p, p, L)] = fmaf(-t, apq, A[tri(p, p, L)]);
-                    A[tri(q, q, L)] = fmaf(t, apq, A[tri(q, q, L)]);
-                    A[tri(p, q, L)] = 0.f;
+                    S[tri(p, p, L)] = fmaf(-t, apq, S[tri(p, p, L)]);
+                    S[tri(q, q, L)] = fmaf(t, apq, S[tri(q, q, L)]);
+                    S[tri(p, q, L)] = 0.f;
 #pragma unroll
                     for (int r = 0; r < L; ++r) {
                         if (r == p || r == q) continue;
-                        const float g = A[tri(r, p, L)], hh = A[tri(r, q, L)];
-                        A[tri(r, p, L)] = fmaf(c, g, -s * hh);
-                        A[tri(r, q, L)] = fmaf(s, g, c * hh);
+                        const float g = S[tri(r, p, L)], hh = S[tri(r, q, L)];
+                        S[tri(r, p, L)] = fmaf(c, g, -s * hh);
+                        S[tri(r, q, L)] = fmaf(s, g, c * hh);
                     }
                 }
+                float B[NS];
+#pragma unroll
+                for (int r = 0; r < L; ++r)
+#pragma unroll
+                    for (int cc = r; cc < L; ++cc) B[tri(r, cc, L)] = S[tri(tperm(r, L), tperm(cc, L), L)];
+#pragma unroll
+                for (int i = 0; i < NS; ++i) S[i] = B[i];
+            }
             ++sweeps;
             float off = 0.f;
 #pragma unroll
             for (int p = 0; p < L - 1; ++p)
 #pragma unroll
-                for (int q = p + 1; q < L; ++q) off = fmaf(A[tri(p, q, L)], A[tri(p, q, L)], off);
-            jconv = off <= 1e-8f;
+                for (int q = p + 1; q < L; ++q) off = fmaf(S[tri(p, q, L)], S[tri(p, q, L)], off);
+            // The sweeps only have to place mu (below) close above l1: with the top eigenvalue
+            // separated, two sweeps leave l1 accurate far beyond the 1e-5 shift, and the inverse
+            // iteration then fixes the eigenvector. More sweeps run only while some lane still
+            // has a large off-diagonal mass.
+            jconv = off <= 1e-4f;
             if (sweeps >= args.max_sweeps) break;
             if (sweeps >= 2 && __all_sync(kFull, jconv)) break;
         }
-        float l1 = A[tri(0, 0, L)], l2 = -1e30f;
+        float l1 = S[tri(0, 0, L)], l2 = -1e30f;
         int k1 = 0;
 #pragma unroll
         for (int i = 1; i < L; ++i) {
-            const float v = A[tri(i, i, L)];
+            const float v = S[tri(i, i, L)];
             if (v > l1) {
                 l2 = l1;
                 l1 = v;
@@ -285,7 +334,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         float Lm[NS];  // unit lower factor in the packed layout, D on the diagonal slots
 #pragma unroll
         for (int j = 0; j < L; ++j) {
-            float dj = mu - S[tri(j, j, L)];
+            float dj = mu - Ssh[tri(j, j, L) * kBatThreads];
 #pragma unroll
             for (int k = 0; k < j; ++k) dj = fmaf(-Lm[tri(j, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], dj);
             if (fabsf(dj) < 1e-30f) dj = dj < 0.f ? -1e-30f : 1e-30f;
@@ -293,7 +342,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             const float inv = frcp(dj);
 #pragma unroll
             for (int i = j + 1; i < L; ++i) {
-                float v = -S[tri(i, j, L)];
+                float v = -Ssh[tri(i, j, L) * kBatThreads];
 #pragma unroll
                 for (int k = 0; k < j; ++k) v = fmaf(-Lm[tri(i, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], v);
                 Lm[tri(i, j, L)] = v * inv;
@@ -301,14 +350,9 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         }
         float x[L];
 #pragma unroll
-        for (int i = 0; i < L; ++i) {
-            float v = 0.f;
-#pragma unroll
-            for (int j = 0; j < L; ++j) v = (j == k1) ? S[tri(i, j, L)] : v;
-            x[i] = v;
-        }
-#pragma unroll
-        for (int step = 0; step < 2; ++step) {
+        for (int i = 0; i < L; ++i) x[i] = Ssh[tri(i, k1, L) * kBatThreads];
+#pragma unroll 1
+        for (int step = 0; step < 3; ++step) {
 #pragma unroll
             for (int i = 0; i < L; ++i)
 #pragma unroll
@@ -338,7 +382,12 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         float nu2 = 0.f;
 #pragma unroll
         for (int i = 0; i < L; ++i) nu2 += norm2(u[i]);
-        const float inu2 = frcp(nu2);
+        // Shrinking the lag coefficients by (1 - eta) makes Q(e^jw) e^-j(L-1)w =
+        // (1 - eta) P(w) + eta (L - 1) >= eta (L - 1) > 0 on the circle, above the FP32 rounding
+        // of the coefficients (~1e-6 of P). Without it, rounding can push a noise-free double root
+        // apart along the circle (two roots at w0 +- d, d ~ 1e-3); with it the pair always splits
+        // radially and keeps the angle of the minimum of P.
+        const float inu2 = (1.f - 2e-6f) * frcp(nu2);
         cx<float> c[L];
         float ac[L];
         c[0] = mkc((float)(L - 1), 0.f);
@@ -352,49 +401,88 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             ac[k] = sqrtf(norm2(c[k]));
         }
 
-        // ---- Aberth-Ehrlich from structured starting points ---------------------------------------
-        cx<float> z[NR];
+        // ---- Aberth-Ehrlich on the inner roots --------------------------------------------------------
+        // Q's coefficients satisfy c_-k = conj(c_k), so its roots come in pairs z, 1/conj(z). Only
+        // the L - 1 roots inside the unit disk are iterated; each Aberth sum runs over the other
+        // inner roots and over all mirrors 1/conj(z_j) (the root's own partner included), and a
+        // root that steps outside is folded back to its mirror. The loop over roots is rolled:
+        // the current root is always position 0 and the arrays rotate by one after each update,
+        // which keeps the code small enough for the instruction cache.
+        cx<float> z[NI], mz[NI];
         {
             const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
             const float n1 = norm2(rho1);
             const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
             z[0] = 0.98f * e;
-            z[1] = (1.f / 0.98f) * e;
             float sh, ch;
-            sincospif(1.0f / (float)L, &sh, &ch);           // exp(j pi / L)
+            sincospif(1.0f / (float)L, &sh, &ch);                           // exp(j pi / L)
             const cx<float> step = mkc(ch * ch - sh * sh, 2.f * sh * ch);  // exp(2 j pi / L)
-            cx<float> ek = e * mkc(ch, sh) * step;            // angle + 2 pi (1 + 1/2) / L
+            cx<float> ek = e * mkc(ch, sh) * step;                           // angle + 2 pi (1 + 1/2) / L
             const float rin = (float)L / ((float)L + 7.3f);
 #pragma unroll
-            for (int k = 1; k <= L - 2; ++k) {
-                z[2 * k] = rin * ek;
-                z[2 * k + 1] = (1.f / rin) * ek;
+            for (int k = 1; k < NI; ++k) {
+                z[k] = rin * ek;
                 ek = ek * step;
             }
+#pragma unroll
+            for (int k = 0; k < NI; ++k) mz[k] = frcp(norm2(z[k])) * z[k];
         }
-        int iters = 0;
+        int iters = 0, updates = 0;
         bool rconv = false;
+        unsigned frozen = 0;  // bit r: the root now at position r has converged in this lane
         for (;;) {
             rconv = true;
-#pragma unroll
-            for (int i = 0; i < NR; ++i) {
-                const float az = sqrtf(norm2(z[i]));
+#pragma unroll 1
+            for (int r = 0; r < NI; ++r) {
+                const cx<float> z0 = z[0];
+                cx<float> nz = z0, nm = mz[0];
+                // A root whose residual reached the rounding level is frozen: near a double root
+                // the corrections below that level are noise and would push it off its angle.
+                // Roots frozen in every lane of the warp are skipped altogether.
+                if (!__all_sync(kFull, frozen & 1u)) {
+                const float az = sqrtf(norm2(z0));
                 cx<float> p, dp;
                 float bnd;
-                horner_pd<L>(c, ac, z[i], az, p, dp, bnd);
+                horner_pd<L>(c, ac, z0, az, p, dp, bnd);
                 const float lim = 3e-6f * bnd;
-                rconv = rconv && (norm2(p) <= lim * lim);
-                const cx<float> Ni = cdivf(p, dp);
-                cx<float> Si = mkc(0.f, 0.f);
+                const bool cv = (frozen & 1u) || norm2(p) <= lim * lim;
+                frozen |= cv ? 1u : 0u;
+                rconv = rconv && cv;
+                if (!__all_sync(kFull, cv)) {
+                    ++updates;
+                    const cx<float> Ni = cdivf(p, dp);
+                    cx<float> Si = mkc(0.f, 0.f);
 #pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    if (j == i) continue;
-                    const cx<float> dz = z[i] - z[j];
-                    const float inv = frcp(norm2(dz));
-                    Si = mkc(fmaf(dz.r, inv, Si.r), fmaf(-dz.i, inv, Si.i));
+                    for (int j = 0; j < NI; ++j) {
+                        if (j > 0) {
+                            const cx<float> dz = z0 - z[j];
+                            const float inv = frcp(norm2(dz));
+                            Si = mkc(fmaf(dz.r, inv, Si.r), fmaf(-dz.i, inv, Si.i));
+                        }
+                        const cx<float> dm = z0 - mz[j];
+                        const float invm = frcp(norm2(dm));
+                        Si = mkc(fmaf(dm.r, invm, Si.r), fmaf(-dm.i, invm, Si.i));
+                    }
+                    const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - Ni * Si);
+                    if (!cv && isfinite(w.r) && isfinite(w.i)) nz = z0 - w;
+                    const float r2n = norm2(nz);
+                    const float ir2 = frcp(r2n);
+                    nm = ir2 * nz;
+                    if (r2n > 1.f) {  // fold back inside: swap the root and its mirror
+                        const cx<float> t = nz;
+                        nz = nm;
+                        nm = t;
+                    }
                 }
-                const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - Ni * Si);
-                if (isfinite(w.r) && isfinite(w.i)) z[i] = z[i] - w;
+                }
+                frozen = (frozen >> 1) | ((frozen & 1u) << (NI - 1));
+#pragma unroll
+                for (int j = 0; j + 1 < NI; ++j) {
+                    z[j] = z[j + 1];
+                    mz[j] = mz[j + 1];
+                }
+                z[NI - 1] = nz;
+                mz[NI - 1] = nm;
             }
             ++iters;
             if (iters >= args.max_iters) break;
@@ -402,32 +490,38 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         }
 
         // ---- selection (Algorithm 1) ------------------------------------------------------------------
+        // every tracked root is inside the disk: the one nearest the circle has the largest modulus
         int best = -1;
-        float bestd = 1e30f;
-        cx<float> zs = mkc(1.f, 0.f);
+        float bestr = -1.f;
+        cx<float> zs = mkc(1.f, 0.f), ms = zs;
 #pragma unroll
-        for (int i = 0; i < NR; ++i) {
-            const float r = sqrtf(norm2(z[i]));
-            const float dd = fabsf(r - 1.f);
-            if (r <= 1.f + 1e-3f && dd < bestd) {
-                bestd = dd;
+        for (int i = 0; i < NI; ++i) {
+            const float r = norm2(z[i]);
+            if (r > bestr) {
+                bestr = r;
                 best = i;
                 zs = z[i];
+                ms = mz[i];
             }
         }
-        float neard = 1e30f;
-        cx<float> zn = zs;
+        // nearest other root of the full set: its own mirror, another inner root or a mirror
+        float neard = norm2(ms - zs);
+        cx<float> zn = ms;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            const float dj = sqrtf(norm2(z[j] - zs));
+        for (int j = 0; j < NI; ++j) {
+            const float dj = norm2(z[j] - zs), dmj = norm2(mz[j] - zs);
             if (j != best && dj < neard) {
                 neard = dj;
                 zn = z[j];
             }
+            if (j != best && dmj < neard) {
+                neard = dmj;
+                zn = mz[j];
+            }
         }
-        const bool cluster = neard < 4e-3f;
+        const bool cluster = neard < 4e-3f * 4e-3f;
         cx<float> zz = cluster ? 0.5f * (zs + zn) : zs;
-#pragma unroll
+#pragma unroll 1
         for (int it = 0; it < 2; ++it) {
             cx<float> p, d1, d2;
             horner_pdd<L>(c, zz, p, d1, d2);
@@ -466,6 +560,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             atomicAdd(args.counters + 0, (unsigned long long)sweeps);
             atomicAdd(args.counters + 1, (unsigned long long)iters);
             atomicAdd(args.counters + 2, 1ull);
+            atomicAdd(args.counters + 3, (unsigned long long)updates);
         }
 
         // ---- store ---------------------------------------------------------------------------------

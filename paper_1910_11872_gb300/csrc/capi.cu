@@ -57,8 +57,8 @@ struct rmusic_ctx {
     size_t budget = 0;
     int num_sms = 0;
     // device workspaces
-    float2* d_gamma = nullptr;
-    size_t gamma_cap = 0;  // elements
+    void* d_gamma = nullptr;
+    size_t gamma_cap = 0;  // bytes
     FrameDev* d_table = nullptr;
     size_t table_cap = 0;  // entries
     unsigned long long* d_counters = nullptr;  // one per covariance order
@@ -208,6 +208,11 @@ int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
     return RMUSIC_OK;
 }
 
+// Bytes per pixel of the analytic-signal workspace: complex128 for the plain FP64 path.
+size_t gamma_elem_bytes(const rmusic_ctx* ctx) {
+    return ctx->p.precision == RMUSIC_PLAIN_FP64 ? sizeof(double2) : sizeof(float2);
+}
+
 int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Plan* plan) {
     plan->frames.resize(n);
     for (int i = 0; i < n; ++i) {
@@ -270,7 +275,8 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
             cudaStream_t s, int* launches) {
     const int n = (int)plan.frames.size();
     int e0 = stamp(ctx, s);
-    RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, d_frames, ctx->d_gamma, s));
+    const bool fp64 = ctx->p.precision == RMUSIC_PLAIN_FP64;
+    RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, d_frames, ctx->d_gamma, fp64, s));
     stamp_pair(ctx->a1_ev, e0, stamp(ctx, s));
     ++*launches;
     const rmusic_params& p = ctx->p;
@@ -286,7 +292,8 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
             RM_CUDA(cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s));
             int e1 = stamp(ctx, s);
             RM_CUDA(launch_batched(L, ctx->d_table + plan.group_first[g], plan.group_count[g],
-                                   plan.group_items[g], ctx->d_counters + g, ctx->d_gamma, d_out, d_status,
+                                   plan.group_items[g], ctx->d_counters + g,
+                                   static_cast<const float2*>(ctx->d_gamma), d_out, d_status,
                                    a, ctx->grid_by_L[L], s));
             stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
             ++*launches;
@@ -299,9 +306,11 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         int e1 = stamp(ctx, s);
         for (int f = 0; f < n; ++f) {
             if (p.precision == RMUSIC_PLAIN_FP64)
-                RM_CUDA(launch_plain_fp64(ctx->d_table + f, plan.frames[f], ctx->d_gamma, d_out, d_status, a, s));
+                RM_CUDA(launch_plain_fp64(ctx->d_table + f, plan.frames[f], static_cast<const double2*>(ctx->d_gamma),
+                                          d_out, d_status, a, s));
             else
-                RM_CUDA(launch_plain_fp32(ctx->d_table + f, plan.frames[f], ctx->d_gamma, d_out, d_status, a, s));
+                RM_CUDA(launch_plain_fp32(ctx->d_table + f, plan.frames[f], static_cast<const float2*>(ctx->d_gamma),
+                                          d_out, d_status, a, s));
             ++*launches;
         }
         stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
@@ -340,12 +349,8 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
     Plan plan;
     int rc = build_plan(ctx, descs, count, &plan);
     if (rc) return rc;
-    size_t gbytes = ctx->gamma_cap * sizeof(float2);
-    void* gptr = ctx->d_gamma;
-    rc = ensure(ctx, &gptr, &gbytes, std::max<uint64_t>(plan.gamma_elems, 1) * sizeof(float2));
+    rc = ensure(ctx, &ctx->d_gamma, &ctx->gamma_cap, std::max<uint64_t>(plan.gamma_elems, 1) * gamma_elem_bytes(ctx));
     if (rc) return rc;
-    ctx->d_gamma = (float2*)gptr;
-    ctx->gamma_cap = gbytes / sizeof(float2);
     rc = ensure_tables(ctx, plan.frames.size());
     if (rc) return rc;
 
@@ -429,8 +434,8 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
     return RMUSIC_OK;
 }
 
-uint64_t group_bytes(const rmusic_frame_desc& d) {
-    return (uint64_t)d.height * (uint64_t)d.width * sizeof(float2);
+uint64_t group_bytes(const rmusic_ctx* ctx, const rmusic_frame_desc& d) {
+    return (uint64_t)d.height * (uint64_t)d.width * gamma_elem_bytes(ctx);
 }
 
 }  // namespace
@@ -491,12 +496,12 @@ int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic
         if (rc) return rc;
         pixels += (uint64_t)F.H * (uint64_t)F.W;
     }
-    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, 3 * sizeof(unsigned long long), s));
+    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, 4 * sizeof(unsigned long long), s));
     // group frames so that each group's analytic signal fits the budget
     const uint64_t table_reserve = 64 * sizeof(FrameDev) + (uint64_t)n_frames * sizeof(FrameDev);
     uint64_t avail = 0;
     if (ctx->budget) {
-        const uint64_t fixed = ctx->held - ctx->gamma_cap * sizeof(float2) + table_reserve;
+        const uint64_t fixed = ctx->held - ctx->gamma_cap + table_reserve;
         avail = ctx->budget > fixed ? ctx->budget - fixed : 0;
     }
     int first = 0;
@@ -504,7 +509,7 @@ int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic
         int count = 0;
         uint64_t bytes = 0;
         while (first + count < n_frames) {
-            const uint64_t b = group_bytes(descs[first + count]);
+            const uint64_t b = group_bytes(ctx, descs[first + count]);
             if (ctx->budget && count > 0 && bytes + b > avail) break;
             bytes += b;
             ++count;
@@ -610,10 +615,11 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->workspace_bytes = ctx->held;
     out->pixels = ctx->last_pixels;
     RM_CUDA(cudaEventSynchronize(ctx->call_done));
-    unsigned long long c[3] = {0, 0, 0};
+    unsigned long long c[4] = {0, 0, 0, 0};
     RM_CUDA(cudaMemcpy(c, ctx->d_counters + kStatSlot, sizeof(c), cudaMemcpyDeviceToHost));
     out->mean_sweeps = c[2] ? (double)c[0] / (double)c[2] : 0.0;
     out->mean_root_iters = c[2] ? (double)c[1] / (double)c[2] : 0.0;
+    out->mean_root_updates = c[2] ? (double)c[3] / (double)c[2] : 0.0;
     auto sum = [&](const std::vector<int>& v) {
         float t = 0.f;
         for (size_t i = 0; i + 1 < v.size(); i += 2) {

@@ -13,7 +13,9 @@
 //   poly     Q(z) = sum_k c_k z^(k+L-1), c_k = sum_{l-m=k} (I - u1 u1^H)[m][l]        (Eq. 12-14)
 //   roots    Aberth-Ehrlich on all 2L-2 roots from a circle of starting points
 //   select   the root with |z| <= 1 + tau_in nearest the unit circle; if another root lies
-//            within tau_c of it the pair is one split double root, located on Q'   (Algorithm 1)
+//            within tau_c of it the pair is one split double root, located on Q'; otherwise two
+//            Newton steps on Q with the conjugate-reciprocal partner 1/conj(z) divided out
+//            refine it                                                          (Algorithm 1)
 //   angle    arg(z) minus the carrier step, wrapped to (-pi, pi]                     (Eq. 15)
 #include <math.h>
 
@@ -31,6 +33,7 @@ struct PlainTol<double> {
     static constexpr double resid = 1e-14;   // |Q(z)| / sum |q_k| |z|^k at a root
     static constexpr double cand = 1e-9;     // candidates: |z| <= 1 + cand
     static constexpr double cluster = 1e-6;  // two roots closer than this are one double root
+    static constexpr double shrink = 0.0;    // relative shrink of the lag coefficients c_k, k != 0
 };
 template <>
 struct PlainTol<float> {
@@ -39,6 +42,9 @@ struct PlainTol<float> {
     static constexpr float resid = 8e-6f;
     static constexpr float cand = 1e-3f;
     static constexpr float cluster = 4e-3f;
+    // keeps Q(e^jw) e^-j(L-1)w >= 2e-6 (L - 1) > 0 above the FP32 rounding of the coefficients,
+    // so a noise-free double root splits radially (same angle) instead of along the circle
+    static constexpr float shrink = 2e-6f;
 };
 
 template <typename T>
@@ -80,10 +86,22 @@ __device__ void horner3(const cx<T>* q, int deg, cx<T> z, cx<T>* p, cx<T>* d1, c
     *bound = b;
 }
 
+// Storage type of the analytic signal each precision reads: complex64 / complex128.
+template <typename T>
+struct GammaOf;
+template <>
+struct GammaOf<float> {
+    using type = float2;
+};
+template <>
+struct GammaOf<double> {
+    using type = double2;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(128)
-plain_kernel(const FrameDev* __restrict__ frame, const float2* __restrict__ gam, float* __restrict__ out,
-             uint8_t* __restrict__ status, PlainArgs args) {
+plain_kernel(const FrameDev* __restrict__ frame, const typename GammaOf<T>::type* __restrict__ gam,
+             float* __restrict__ out, uint8_t* __restrict__ status, PlainArgs args) {
     const FrameDev F = *frame;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)F.wlines * F.wlen) return;
@@ -101,9 +119,9 @@ plain_kernel(const FrameDev* __restrict__ frame, const float2* __restrict__ gam,
 
     // ---- window (Sec. 3, Eq. 2) -------------------------------------------------------------
     cx<T> w[kMaxN];
-    const float2* g = gam + F.gam_off + (uint64_t)wline * F.wlen + start;
+    const typename GammaOf<T>::type* g = gam + F.gam_off + (uint64_t)wline * F.wlen + start;
     for (int i = 0; i < N; ++i) {
-        float2 v = g[i];
+        const auto v = g[i];
         w[i] = mkc((T)v.x, (T)v.y);
     }
 
@@ -217,6 +235,9 @@ plain_kernel(const FrameDev* __restrict__ frame, const float2* __restrict__ gam,
             if (m == l) cml.r += T(1);
             q[l - m + L - 1] = q[l - m + L - 1] + cml;
         }
+    if (PlainTol<T>::shrink != T(0))
+        for (int i = 0; i <= deg; ++i)
+            if (i != L - 1) q[i] = (T(1) - PlainTol<T>::shrink) * q[i];
 
     // ---- all roots by Aberth-Ehrlich ---------------------------------------------------------
     cx<T> z[2 * kMaxL];
@@ -295,6 +316,15 @@ plain_kernel(const FrameDev* __restrict__ frame, const float2* __restrict__ gam,
             if (norm2(stp) <= T(1e-32) * norm2(zm)) break;
         }
         zs = (tsqrt(norm2(zm - z0)) <= T(2) * neard) ? zm : z0;
+    } else {
+        for (int it = 0; it < 2; ++it) {
+            cx<T> p, d1, d2;
+            T bnd;
+            horner3(q, deg, zs, &p, &d1, &d2, &bnd);
+            const cx<T> dzp = zs - (T(1) / norm2(zs)) * zs;  // z - 1/conj(z)
+            const cx<T> stp = cdiv(p, d1 - cdiv(p, dzp));
+            if (isfinite((double)stp.r) && isfinite((double)stp.i)) zs = zs - stp;
+        }
     }
 
     // ---- angle minus carrier (Eq. 15) ----------------------------------------------------------
@@ -304,7 +334,8 @@ plain_kernel(const FrameDev* __restrict__ frame, const float2* __restrict__ gam,
 }
 
 template <typename T>
-static cudaError_t launch_plain(const FrameDev* d_frame, const FrameDev& h, const float2* d_gamma,
+static cudaError_t launch_plain(const FrameDev* d_frame, const FrameDev& h,
+                                const typename GammaOf<T>::type* d_gamma,
                                 float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream) {
     const int64_t n = (int64_t)h.wlines * h.wlen;
     if (n <= 0) return cudaSuccess;
@@ -314,7 +345,7 @@ static cudaError_t launch_plain(const FrameDev* d_frame, const FrameDev& h, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_plain_fp64(const FrameDev* d_frame, const FrameDev& h, const float2* d_gamma,
+cudaError_t launch_plain_fp64(const FrameDev* d_frame, const FrameDev& h, const double2* d_gamma,
                               float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream) {
     return launch_plain<double>(d_frame, h, d_gamma, d_out, d_status, a, stream);
 }

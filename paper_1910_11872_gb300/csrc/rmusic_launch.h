@@ -11,8 +11,9 @@ namespace rmusic {
 
 // Band-pass analytic signal of every carrier line (Sec. 2, Eq. 1). One CTA per line.
 cudaError_t init_analytic();
+// fp64 = true writes complex128 (plain FP64 path), otherwise complex64.
 cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_lines, int max_len,
-                            const void* d_in, float2* d_gamma, cudaStream_t stream);
+                            const void* d_in, void* d_gamma, bool fp64, cudaStream_t stream);
 
 // Plain path: one thread per pixel of one frame, T = float or double (Sec. 3; Algorithm 1).
 struct PlainArgs {
@@ -20,7 +21,7 @@ struct PlainArgs {
     int max_sweeps;
     int max_iters;
 };
-cudaError_t launch_plain_fp64(const FrameDev* d_frame, const FrameDev& h_frame, const float2* d_gamma,
+cudaError_t launch_plain_fp64(const FrameDev* d_frame, const FrameDev& h_frame, const double2* d_gamma,
                               float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream);
 cudaError_t launch_plain_fp32(const FrameDev* d_frame, const FrameDev& h_frame, const float2* d_gamma,
                               float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream);
@@ -31,7 +32,7 @@ struct BatchedArgs {
     int max_sweeps;
     int max_iters;
     int polish64;
-    unsigned long long* counters;  // [0] sweeps, [1] root iterations, [2] items (accumulated)
+    unsigned long long* counters;  // [0] sweeps, [1] root iterations, [2] items, [3] root updates
 };
 bool batched_supports(int L);
 cudaError_t init_batched(int device);

@@ -76,6 +76,7 @@ class rmusic_stats(ctypes.Structure):
         ("pixels", ctypes.c_uint64),
         ("mean_sweeps", ctypes.c_double),
         ("mean_root_iters", ctypes.c_double),
+        ("mean_root_updates", ctypes.c_double),
         ("bandpass_ms", ctypes.c_float),
         ("solver_ms", ctypes.c_float),
     ]
