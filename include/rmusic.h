@@ -150,6 +150,30 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
                                   const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
                                   uint8_t* h_status, void* cuda_stream);
 
+/* For callers that cannot allocate device memory (an application whose allocator belongs to a
+ * host framework or pool, a real-time loop that forbids allocation after start-up, a plug-in
+ * whose host accounts for every byte): the FP32-batched path (precision must be
+ * RMUSIC_FP32_BATCHED, forward_backward 1) without a context and without any cudaMalloc,
+ * cudaFree or other allocating call. The paper has no counterpart; this is an interface
+ * convenience of this library.
+ *   - All device scratch (analytic signal, frame table, work counters) lives in one fixed array
+ *     inside the library's device code, about 32 MiB per GPU, held from the moment that code is
+ *     loaded on the GPU (with CUDA's default lazy loading: this entry point's first call there)
+ *     until the process exits. The caller passes frames and output maps exactly as for
+ *     rmusic_demodulate_frames; descs is a host array read before the call returns.
+ *   - Limits: at most 4,194,304 pixels (e.g. four 1024 x 1024 frames) and 256 frames per call;
+ *     larger requests are rejected with RMUSIC_ENOMEM before any work is queued.
+ *   - The first call on a device looks the array's address up (cudaGetSymbolAddress) and sets
+ *     the kernels' attributes; make that first call before any stream capture.
+ *   - Every call on a device reuses the same array, so calls whose work overlaps on the GPU
+ *     (different streams without ordering, or several host threads) race and corrupt each
+ *     other's results: order them on one stream or synchronise between them.
+ *   - device is the CUDA device to run on; the calling thread's current device is restored.
+ * Errors: RMUSIC_EINVAL, RMUSIC_EUNSUPPORTED, RMUSIC_ENOMEM (over the limits), RMUSIC_ECUDA. */
+int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int device, const void* d_frames,
+                                     const rmusic_frame_desc* descs, int32_t n_frames, float* d_out,
+                                     uint8_t* d_status, void* cuda_stream);
+
 /* Destroy a context and free everything it owns. NULL is allowed. Waits for the context's
  * outstanding work on its device. */
 void rmusic_destroy(rmusic_ctx* ctx);

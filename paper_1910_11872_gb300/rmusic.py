@@ -119,6 +119,9 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_demodulate_frames_host.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(rmusic_frame_desc),
                                                       i32, vp, vp, vp]
         lib.rmusic_demodulate_frames_host.restype = ctypes.c_int
+        lib.rmusic_demodulate_frames_noalloc.argtypes = [ctypes.POINTER(rmusic_params), ctypes.c_int, vp,
+                                                         ctypes.POINTER(rmusic_frame_desc), i32, vp, vp, vp]
+        lib.rmusic_demodulate_frames_noalloc.restype = ctypes.c_int
         lib.rmusic_destroy.argtypes = [vp]
         lib.rmusic_destroy.restype = None
         lib.rmusic_strerror.argtypes = [ctypes.c_int]
@@ -175,6 +178,19 @@ def rmusic_demodulate_frames_host(ctx, h_frames: int, in_bytes: int, descs, n_fr
                                                       h_out or None, h_status or None, cuda_stream or None)
     if rc != RMUSIC_OK:
         raise RmusicError(rc, "rmusic_demodulate_frames_host", rmusic_last_cuda_error(ctx))
+    return rc
+
+
+def rmusic_demodulate_frames_noalloc(params: rmusic_params, device: int, d_frames: int, descs, n_frames: int,
+                                     d_out: int, d_status: int | None, cuda_stream: int | None) -> int:
+    """The context-free FP32-batched entry point that allocates no device memory (for callers
+    that cannot allocate); its scratch is a fixed array inside the library (see rmusic.h)."""
+    arr = _desc_array(descs)
+    rc = load_library().rmusic_demodulate_frames_noalloc(ctypes.byref(params), int(device), d_frames or None, arr,
+                                                         int(n_frames), d_out or None, d_status or None,
+                                                         cuda_stream or None)
+    if rc != RMUSIC_OK:
+        raise RmusicError(rc, "rmusic_demodulate_frames_noalloc")
     return rc
 
 
