@@ -91,6 +91,29 @@ def flops_per_pixel(L: int, N: int, sweeps: float, iters: float, updates: float)
     return cov + jac + inv + coef + aberth + polish
 
 
+SOLVER_PROFILE = os.path.join(ROOT, "profiles", "batched_solver_L8_peaks4x1024.md")
+SOLVER_SOURCES = ["batched.cu", "rmusic_device.cuh", "rmusic_launch.h"]
+
+
+def profiled_traffic():
+    """DRAM bytes per solver launch from the committed ncu summary, or None when the solver's
+    source has changed since those counters were taken."""
+    import hashlib
+    import re
+
+    if not os.path.exists(SOLVER_PROFILE):
+        return None
+    text = open(SOLVER_PROFILE).read()
+    m_bytes = re.search(r"dram_bytes_per_launch = (\d+)", text)
+    m_hash = re.search(r"source_sha256_16 = ([0-9a-f]{16})", text)
+    if not m_bytes or not m_hash:
+        return None
+    h = hashlib.sha256()
+    for f in SOLVER_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1910_11872_gb300", "csrc", f), "rb").read())
+    return int(m_bytes.group(1)) if h.hexdigest()[:16] == m_hash.group(1) else None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
 
@@ -312,13 +335,7 @@ def run_ours(args):
     fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(iters), statistics.mean(updates))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "batched_solver_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "batched_kernel<8>", "flops_per_pixel": fpp, "launch_ms": solver_avg,
