@@ -371,3 +371,55 @@ def test_launch_counts():
         assert dem.stats().kernel_launches == 3  # band-pass + one launch per frame
     finally:
         dem.close()
+
+
+def _sampled_oracle(fr, N, L, deriv_axis, rows, cols):
+    ys = np.repeat(np.asarray(rows), len(cols)).astype(np.int32)
+    xs = np.tile(np.asarray(cols), len(rows)).astype(np.int32)
+    p = O.make_params(N, L, 1, deriv_axis, 0, fr.carrier_freq)
+    vals, st, _ = O.demodulate_pixels(fr.image, p, ys, xs)
+    return ys, xs, vals, st
+
+
+def test_diffusion_stack_full_frames_one_launch_sampled():
+    """Diffusion time-lapse at full frame size (1024 x 1024 uint16, 12-bit), 32 frames spread over the
+    500-frame schedule in one launch, windows along y; oracle at sampled pixels of four frames."""
+    ts = np.linspace(0, 499, 32).astype(int)
+    frames = [synth.diffusion_frame(int(t)) for t in ts]
+    res = run_gpu([f.image for f in frames], deriv_axis=1)
+    rng = np.random.default_rng(3)
+    for i in (0, 11, 22, 31):
+        fr, (g, gs) = frames[i], res[i]
+        r0 = int(rng.integers(400, 560))
+        rows = np.arange(r0, r0 + 24)                   # near the diffusion front
+        cols = np.sort(rng.choice(1024, 40, replace=False))
+        ys, xs, vals, st = _sampled_oracle(fr, 32, 8, 1, rows, cols)
+        assert np.array_equal(gs[ys, xs] == 1, st == 1)
+        v = (st == 0) & (gs[ys, xs] == 0)
+        assert v.sum() > 0.9 * (st == 0).sum()
+        d = np.abs(g[ys, xs][v].astype(np.float64) - vals[v])
+        assert np.quantile(d, 0.999) < 1e-3 and d.max() < 5e-3, f"frame {ts[i]}: max {d.max():.3e}"
+        # accuracy against the closed-form derivative equals the oracle's
+        rms_g = np.sqrt(np.mean((g[ys, xs][v] - fr.truth[ys, xs][v]) ** 2))
+        rms_o = np.sqrt(np.mean((vals[v] - fr.truth[ys, xs][v]) ** 2))
+        assert abs(rms_g - rms_o) <= 0.01 * rms_o + 1e-6
+
+
+def test_uneven_batch_full_sizes_one_launch_sampled():
+    """64 frames with sizes drawn from {256..2048} x {256, 512, 1024} and (N, L) from
+    {24, 32, 48} x {6, 8, 12}, SNR 15 dB, in one call; oracle at sampled pixels of every frame."""
+    frames = synth.uneven_batch(64)
+    windows = [(f.window_len, f.cov_order) for f in frames]
+    res = run_gpu([f.image for f in frames], windows=windows)
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for fr, (g, gs) in zip(frames, res):
+        H, W = fr.image.shape
+        rows = [int(rng.integers(0, H))]
+        cols = np.sort(rng.choice(W, min(W, 24), replace=False))
+        ys, xs, vals, st = _sampled_oracle(fr, fr.window_len, fr.cov_order, 0, rows, cols)
+        assert np.array_equal(gs[ys, xs] == 1, st == 1)
+        v = (st == 0) & (gs[ys, xs] == 0)
+        if v.any():
+            worst = max(worst, float(np.abs(g[ys, xs][v].astype(np.float64) - vals[v]).max()))
+    assert worst < 5e-3, worst
