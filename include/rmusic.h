@@ -43,6 +43,7 @@ extern "C" {
 #define RMUSIC_EUNSUPPORTED (-3) /* a valid request this build does not implement           */
 #define RMUSIC_ETIMEDOUT (-4)    /* a bounded device-side wait gave up                      */
 #define RMUSIC_ECUDA (-5)        /* a CUDA runtime call failed (see rmusic_last_cuda_error)   */
+#define RMUSIC_EAGAIN (-6)       /* serving: every frame slot of the stream is busy, retry later */
 
 /* ---- execution paths (rmusic_params.precision) ----------------------------------------- */
 #define RMUSIC_PLAIN_FP64 0   /* thread per pixel, FP64 throughout, one launch per frame     */

@@ -601,6 +601,7 @@ const char* rmusic_strerror(int code) {
         case RMUSIC_EUNSUPPORTED: return "unsupported parameters for this path";
         case RMUSIC_ETIMEDOUT: return "device-side wait timed out";
         case RMUSIC_ECUDA: return "CUDA runtime error";
+        case RMUSIC_EAGAIN: return "all frame slots of the stream are busy, try again";
         default: return "unknown error";
     }
 }

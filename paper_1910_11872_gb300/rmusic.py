@@ -22,6 +22,7 @@ RMUSIC_ENOMEM = -2
 RMUSIC_EUNSUPPORTED = -3
 RMUSIC_ETIMEDOUT = -4
 RMUSIC_ECUDA = -5
+RMUSIC_EAGAIN = -6
 
 RMUSIC_PLAIN_FP64 = 0
 RMUSIC_PLAIN_FP32 = 1
