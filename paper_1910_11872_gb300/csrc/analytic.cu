@@ -20,7 +20,7 @@
 
 namespace rmusic {
 
-constexpr int kA1Threads = 256;
+constexpr int kA1Threads = 128;
 constexpr int kA1Block = 32;  // forward Horner re-anchoring period
 
 template <typename T>
@@ -37,11 +37,78 @@ __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { retur
 template <>
 __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
 
+// p <- sum_i v[n0 + i] xi^i over n0 <= n < n1 by Horner (xi = ck - j sk), highest index first.
+template <typename T>
+__device__ __forceinline__ void horner_fwd(const T* v, int n0, int n1, T ck, T sk, T& pr, T& pi) {
+    for (int n = n1 - 1; n >= n0; --n) {
+        T nr = fma_t<T>(pr, ck, fma_t<T>(pi, sk, v[n]));
+        T ni = fma_t<T>(pi, ck, -pr * sk);
+        pr = nr;
+        pi = ni;
+    }
+}
+// FP32: four samples per 16-byte shared-memory read (n0 is a multiple of 4).
+template <>
+__device__ __forceinline__ void horner_fwd<float>(const float* v, int n0, int n1, float ck, float sk, float& pr,
+                                                  float& pi) {
+    const int rem = (n1 - n0) & 3;
+    for (int n = n1 - 1; n >= n1 - rem; --n) {
+        float nr = fmaf(pr, ck, fmaf(pi, sk, v[n]));
+        float ni = fmaf(pi, ck, -pr * sk);
+        pr = nr;
+        pi = ni;
+    }
+    for (int n = n1 - rem - 4; n >= n0; n -= 4) {
+        const float4 q = *reinterpret_cast<const float4*>(v + n);
+        const float vv[4] = {q.w, q.z, q.y, q.x};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            float nr = fmaf(pr, ck, fmaf(pi, sk, vv[t]));
+            float ni = fmaf(pi, ck, -pr * sk);
+            pr = nr;
+            pi = ni;
+        }
+    }
+}
+
+// a <- sum_b X[b] zeta^b by Horner (zeta = cn + j sn), highest bin first.
+template <typename T>
+__device__ __forceinline__ void horner_inv(const cx<T>* X, int nb, T cn, T sn, T& ar, T& ai) {
+    for (int b = nb - 1; b >= 0; --b) {
+        const cx<T> x = X[b];
+        T nr = fma_t<T>(ar, cn, fma_t<T>(-ai, sn, x.r));
+        T ni = fma_t<T>(ar, sn, fma_t<T>(ai, cn, x.i));
+        ar = nr;
+        ai = ni;
+    }
+}
+// FP32: two bins per 16-byte shared-memory read (X is 16-byte aligned).
+template <>
+__device__ __forceinline__ void horner_inv<float>(const cx<float>* X, int nb, float cn, float sn, float& ar,
+                                                  float& ai) {
+    int b = nb - 1;
+    if (nb & 1) {
+        const cx<float> x = X[b];
+        float nr = fmaf(ar, cn, fmaf(-ai, sn, x.r));
+        float ni = fmaf(ar, sn, fmaf(ai, cn, x.i));
+        ar = nr;
+        ai = ni;
+        --b;
+    }
+    for (; b >= 1; b -= 2) {
+        const float4 q = *reinterpret_cast<const float4*>(X + (b - 1));  // X[b-1], X[b]
+        float nr = fmaf(ar, cn, fmaf(-ai, sn, q.z));
+        float ni = fmaf(ar, sn, fmaf(ai, cn, q.w));
+        ar = fmaf(nr, cn, fmaf(-ni, sn, q.x));
+        ai = fmaf(nr, sn, fmaf(ni, cn, q.y));
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kA1Threads)
 analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned char* __restrict__ in,
                 cx<T>* __restrict__ gam) {
-    extern __shared__ double a1_smem_d[];
+    extern __shared__ __align__(16) double a1_smem_d[];
     T* a1_smem = reinterpret_cast<T*>(a1_smem_d);
     __shared__ T red[kA1Threads / 32];
     const int64_t line = blockIdx.x;
@@ -50,7 +117,7 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
     const int li = (int)(line - F.line_start);
     const int len = F.len;
     T* v = a1_smem;
-    cx<T>* X = reinterpret_cast<cx<T>*>(a1_smem + ((len + 1) & ~1));
+    cx<T>* X = reinterpret_cast<cx<T>*>(a1_smem + ((len + 3) & ~3));
 
     // load the line and its sum
     T s = 0;
@@ -87,12 +154,7 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
             const int n0 = blk * kA1Block;
             const int n1 = min(len, n0 + kA1Block);
             T pr = 0, pi = 0;  // sum_{i} v[n0 + i] xi^i by Horner
-            for (int n = n1 - 1; n >= n0; --n) {
-                T nr = fma_t<T>(pr, ck, fma_t<T>(pi, sk, v[n]));
-                T ni = fma_t<T>(pi, ck, -pr * sk);
-                pr = nr;
-                pi = ni;
-            }
+            horner_fwd<T>(v, n0, n1, ck, sk, pr, pi);
             // X += xi^{n0} * partial, with xi^{n0} from the exactly reduced index k n0 mod len
             const int m = (int)(((int64_t)k * n0) % len);
             T sm, cm;
@@ -110,13 +172,7 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
         T sn, cn;
         sincospi_t<T>((T)n * two_over_len, &sn, &cn);  // zeta = cn + j sn
         T ar = 0, ai = 0;
-        for (int b = F.nb - 1; b >= 0; --b) {
-            const cx<T> x = X[b];
-            T nr = fma_t<T>(ar, cn, fma_t<T>(-ai, sn, x.r));
-            T ni = fma_t<T>(ar, sn, fma_t<T>(ai, cn, x.i));
-            ar = nr;
-            ai = ni;
-        }
+        horner_inv<T>(X, F.nb, cn, sn, ar, ai);
         const int m = (int)(((int64_t)F.k_lo * n) % len);
         T s2, c2;
         sincospi_t<T>((T)m * two_over_len, &s2, &c2);
@@ -132,8 +188,8 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
 
 template <typename T>
 static size_t a1_smem_bytes(int len) {
-    // v[len] + X[nb <= len/2]
-    return sizeof(T) * (size_t)((len + 1) & ~1) + 2 * sizeof(T) * (size_t)(len / 2 + 1);
+    // v[len] (padded to 4 elements) + X[nb <= len/2]
+    return sizeof(T) * (size_t)((len + 3) & ~3) + 2 * sizeof(T) * (size_t)(len / 2 + 1);
 }
 
 cudaError_t init_analytic() {

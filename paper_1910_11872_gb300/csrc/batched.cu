@@ -27,7 +27,7 @@
 //             at the angle of conj(rho_1), the others at radius r = L / (L + 7.3) at the
 //             side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window
 //             puts them. Iterations stop when every root of every lane of the warp has a residual
-//             at the FP32 rounding level.
+//             at the FP32 rounding level (|Q(z)| <= 3e-6 sum |q_i|).
 //   select    the inner root nearest the unit circle (Algorithm 1). A noise-free window gives a
 //             double root on the circle, which FP32 splits by ~sqrt(eps); when another root lies
 //             within 4e-3 the pair is located as the root of Q' between them, otherwise the root
@@ -76,17 +76,13 @@ __device__ __forceinline__ cx<float> qcoef(const cx<float>* c, int i) {
 }
 
 template <int L>
-__device__ __forceinline__ void horner_pd(const cx<float>* c, const float* ac, cx<float> z, float az,
-                                          cx<float>& p, cx<float>& d, float& bnd) {
+__device__ __forceinline__ void horner_pd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d) {
     p = qcoef<L>(c, 2 * L - 2);
     d = mkc(0.f, 0.f);
-    bnd = ac[L - 1];
 #pragma unroll
     for (int i = 2 * L - 3; i >= 0; --i) {
         d = d * z + p;
         p = p * z + qcoef<L>(c, i);
-        const int k = i - (L - 1);
-        bnd = fmaf(bnd, az, ac[k >= 0 ? k : -k]);
     }
 }
 
@@ -389,17 +385,19 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         // radially and keeps the angle of the minimum of P.
         const float inu2 = (1.f - 2e-6f) * frcp(nu2);
         cx<float> c[L];
-        float ac[L];
         c[0] = mkc((float)(L - 1), 0.f);
-        ac[0] = (float)(L - 1);
+        // sum_i |q_i| bounds sum_i |q_i| |z|^i for every tracked root (all stay in the unit disk):
+        // the scale of Q's rounding error in the residual test below
+        float qsum = (float)(L - 1);
 #pragma unroll
         for (int k = 1; k < L; ++k) {
             cx<float> rho = mkc(0.f, 0.f);
 #pragma unroll
             for (int m = 0; m + k < L; ++m) rho = rho + mulc(u[m], u[m + k]);
             c[k] = (-inu2) * rho;
-            ac[k] = sqrtf(norm2(c[k]));
+            qsum += 2.f * sqrtf(norm2(c[k]));
         }
+        const float res_lim2 = (3e-6f * qsum) * (3e-6f * qsum);
 
         // ---- Aberth-Ehrlich on the inner roots --------------------------------------------------------
         // Q's coefficients satisfy c_-k = conj(c_k), so its roots come in pairs z, 1/conj(z). Only
@@ -413,7 +411,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
             const float n1 = norm2(rho1);
             const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
-            z[0] = 0.98f * e;
+            z[0] = 0.99f * e;
             float sh, ch;
             sincospif(1.0f / (float)L, &sh, &ch);                           // exp(j pi / L)
             const cx<float> step = mkc(ch * ch - sh * sh, 2.f * sh * ch);  // exp(2 j pi / L)
@@ -440,12 +438,9 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
                 // the corrections below that level are noise and would push it off its angle.
                 // Roots frozen in every lane of the warp are skipped altogether.
                 if (!__all_sync(kFull, frozen & 1u)) {
-                const float az = sqrtf(norm2(z0));
                 cx<float> p, dp;
-                float bnd;
-                horner_pd<L>(c, ac, z0, az, p, dp, bnd);
-                const float lim = 3e-6f * bnd;
-                const bool cv = (frozen & 1u) || norm2(p) <= lim * lim;
+                horner_pd<L>(c, z0, p, dp);
+                const bool cv = (frozen & 1u) || norm2(p) <= res_lim2;
                 frozen |= cv ? 1u : 0u;
                 rconv = rconv && cv;
                 if (!__all_sync(kFull, cv)) {
