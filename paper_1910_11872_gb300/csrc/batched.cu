@@ -15,9 +15,10 @@
 //             so with the unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) (even L) S = Q^H R Q =
 //             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x.
 //   eigen     cyclic Jacobi sweeps on S (real, register resident, tournament order) until the
-//             off-diagonal mass is below 1e-4 of the trace -> the largest eigenvalue l1; then two
-//             steps of inverse iteration with (mu I - S) = L D L^T, mu just above l1, give the
-//             signal eigenvector x1 without accumulating rotations (Eq. 8-11).
+//             largest diagonal entry is close to l1 relative to the eigen-gap (usually one
+//             sweep); then three steps of inverse iteration with (mu I - S) = L D L^T, mu just
+//             above that entry, give the signal eigenvector x1 without accumulating rotations
+//             (Eq. 8-11).
 //   poly      u1 = Q x1 / |x1|; c_0 = L - 1, c_k = -(1 - 2e-6) sum_m u1[m] conj(u1[m+k]) / |u1|^2,
 //             c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14). The 2e-6 shrink keeps the
 //             polynomial strictly positive on the circle in FP32 (see below).
@@ -264,6 +265,8 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         for (int i = 0; i < NS; ++i) Ssh[i * kBatThreads] = S[i];
         int sweeps = 0;
         bool jconv = false;
+        float l1 = 0.f, l2 = 0.f;
+        int k1 = 0;
         for (;;) {
 #pragma unroll 1
             for (int stp = 0; stp < L - 1; ++stp) {
@@ -302,26 +305,29 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             for (int p = 0; p < L - 1; ++p)
 #pragma unroll
                 for (int q = p + 1; q < L; ++q) off = fmaf(S[tri(p, q, L)], S[tri(p, q, L)], off);
-            // The sweeps only have to place mu (below) close above l1: with the top eigenvalue
-            // separated, two sweeps leave l1 accurate far beyond the 1e-5 shift, and the inverse
-            // iteration then fixes the eigenvector. More sweeps run only while some lane still
-            // has a large off-diagonal mass.
-            jconv = off <= 1e-4f;
-            if (sweeps >= args.max_sweeps) break;
-            if (sweeps >= 2 && __all_sync(kFull, jconv)) break;
-        }
-        float l1 = S[tri(0, 0, L)], l2 = -1e30f;
-        int k1 = 0;
+            // The sweeps only have to place mu (below) near l1: the largest diagonal entry a_kk
+            // differs from l1 by at most about off / gap, so once off <= 1e-3 gap^2 the shift is
+            // within ~1e-3 gap of l1 and three inverse-iteration steps reduce the other
+            // eigenvectors' share by ~1e-9. A signal-dominated window gets there in one sweep;
+            // more sweeps run only while some lane of the warp is short of it.
+            l1 = S[tri(0, 0, L)];
+            l2 = -1e30f;
+            k1 = 0;
 #pragma unroll
-        for (int i = 1; i < L; ++i) {
-            const float v = S[tri(i, i, L)];
-            if (v > l1) {
-                l2 = l1;
-                l1 = v;
-                k1 = i;
-            } else if (v > l2) {
-                l2 = v;
+            for (int i = 1; i < L; ++i) {
+                const float v = S[tri(i, i, L)];
+                if (v > l1) {
+                    l2 = l1;
+                    l1 = v;
+                    k1 = i;
+                } else if (v > l2) {
+                    l2 = v;
+                }
             }
+            const float gap = l1 - l2;
+            jconv = off <= 1e-3f * gap * gap;
+            if (sweeps >= args.max_sweeps) break;
+            if (__all_sync(kFull, jconv)) break;
         }
         const bool separated = l1 - l2 > 4e-6f * l1;
 
