@@ -82,6 +82,9 @@ extern "C" {
  *                    it when the same frames, tables and outputs are passed again.
  *   timing           1: record CUDA events around every kernel of a call on its stream, so that
  *                    rmusic_get_stats() can report the device time of each stage.
+ *   autotune         batched path: 1 lets the first call that meets a covariance order with no
+ *                    tuned solver variant on this device time all variants on its own work and
+ *                    keep the fastest (that call synchronises its stream). See rmusic_autotune.
  */
 typedef struct {
     int32_t window_len;
@@ -98,6 +101,7 @@ typedef struct {
     int32_t polish_fp64;
     int32_t use_graph;
     int32_t timing;
+    int32_t autotune;
 } rmusic_params;
 
 /* One frame of a batch. Frames of one call may differ in size, type and window.
@@ -142,6 +146,17 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
  * (N, L) for the path), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a no-op. */
 int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
                              int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream);
+
+/* Batched path only: the FP32-batched solver is compiled in several variants per covariance order
+ * that differ in how many CTAs they keep resident per SM (register cap vs latency hiding; the
+ * best one depends on L and on the GPU). This call demodulates like rmusic_demodulate_frames but
+ * first times every variant on the call's own frames for each covariance order they use, keeps
+ * the fastest for this device (all contexts of the process share the choice) and, when the
+ * environment variable RMUSIC_TUNE_CACHE names a file, appends the choice to it as a JSON line
+ * that later processes read. Synchronises its stream. Without tuning a default variant is used.
+ * The paper has no counterpart: this is a property of the GPU implementation. */
+int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int32_t n_frames,
+                    float* d_out, uint8_t* d_status, void* cuda_stream);
 
 /* Same as rmusic_demodulate_frames, but every buffer is in HOST memory: the library copies the
  * frames to its device workspace, runs the same kernels and copies the maps back before it
@@ -196,6 +211,7 @@ const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
  *                    (roots already converged in every lane of the warp are skipped).
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
  *                    call's stream) of the band-pass launches and of the solver launches.
+ *   solver_ctas_per_sm  batched path: resident CTAs per SM of the solver variant last launched.
  * rmusic_get_stats waits until the last call's work has finished. */
 typedef struct {
     int32_t kernel_launches;
@@ -207,6 +223,8 @@ typedef struct {
     double mean_root_updates;
     float bandpass_ms;
     float solver_ms;
+    int32_t solver_ctas_per_sm;
+    int32_t pad_;
 } rmusic_stats;
 
 int rmusic_get_stats(const rmusic_ctx* ctx, rmusic_stats* out);

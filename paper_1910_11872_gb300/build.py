@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "librmusic.so")
-SOURCES = ["analytic.cu", "plain.cu", "batched.cu", "capi.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["analytic.cu", "plain.cu", "batched.cu", "batched_l2_l4.cu", "batched_l6.cu", "batched_l8.cu",
+           "batched_l10.cu", "batched_l12.cu", "capi.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

@@ -1,0 +1,586 @@
+// batched.cu -- the FP32 batched path: one persistent kernel over every pixel of every frame of
+// a call (frames of uneven sizes and windows mixed), one pixel per lane, one 32-pixel run of a
+// window line per warp work item, items taken from a global atomic counter.
+//
+// Per warp item (32 consecutive pixels of one window line):
+//   stage     the 31 + N analytic-signal samples the 32 windows cover, one coalesced read into
+//             shared memory (Sec. 3, Eq. 2: the moving window)
+//   R_f       every entry R_f[m][m+d] = (1/K) sum_{i<K} w[i+m] conj(w[i+m+d]) is a box sum of
+//             the lag-d product sequence g_d[j] = Gamma[j] conj(Gamma[j+d]); per lag d the warp
+//             forms g_d once for the run, takes its prefix sums with a warp scan and reads
+//             R_f[m][m+d] = (P_d[t+m+K] - P_d[t+m]) / K (Eq. 4-5). The scan starts at the run's
+//             fixed absolute position, so each pixel's arithmetic does not depend on how frames
+//             are batched or scheduled.
+//   FB -> S   with forward-backward averaging R = (R_f + J conj(R_f) J)/2 is centro-Hermitian,
+//             so with the unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) (even L) S = Q^H R Q =
+//             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x.
+//   eigen     cyclic Jacobi sweeps on S (real, register resident, tournament order) until the
+//             largest diagonal entry is close to l1 relative to the eigen-gap (usually one
+//             sweep); then three steps of inverse iteration with (mu I - S) = L D L^T, mu just
+//             above that entry, give the signal eigenvector x1 without accumulating rotations
+//             (Eq. 8-11).
+//   poly      u1 = Q x1 / |x1|; c_0 = L - 1, c_k = -(1 - 2e-6) sum_m u1[m] conj(u1[m+k]) / |u1|^2,
+//             c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14). The 2e-6 shrink keeps the
+//             polynomial strictly positive on the circle in FP32 (see below).
+//   roots     Aberth-Ehrlich on the L - 1 roots inside the unit disk; the other L - 1 roots are
+//             their mirrors 1/conj(z) (the coefficients are conjugate-symmetric). Starting
+//             points come from the estimator's structure: the signal root just inside the circle
+//             at the angle of conj(rho_1), the others at radius r = L / (L + 7.3) at the
+//             side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window
+//             puts them. Iterations stop when every root of every lane of the warp has a residual
+//             at the FP32 rounding level (|Q(z)| <= 3e-6 sum |q_i|).
+//   select    the inner root nearest the unit circle (Algorithm 1). A noise-free window gives a
+//             double root on the circle, which FP32 splits by ~sqrt(eps); when another root lies
+//             within 4e-3 the pair is located as the root of Q' between them, otherwise the root
+//             is refined by Newton on Q with its partner 1/conj(z) divided out. Optionally one
+//             more such step runs in FP64.
+//   angle     atan2 of the root minus the carrier step, wrapped (Eq. 15).
+// This header holds the kernel template; batched_l*.cu instantiate it for each covariance order
+// and register-cap variant (compiled in parallel), batched.cu dispatches among them.
+#pragma once
+
+#include <math.h>
+
+#include "rmusic_device.cuh"
+#include "rmusic_launch.h"
+
+namespace rmusic {
+
+constexpr int kBatWarps = 4;
+constexpr int kBatThreads = kBatWarps * 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ constexpr int tri(int r, int c, int L) {
+    return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);
+}
+
+// Fixed relabeling of the Jacobi tournament: after a step over the pairs (0,1), (2,3), ...,
+// position p takes the index previously at tperm(p). Over L - 1 steps every pair of indices
+// meets once (the circle method: 0 stays, the others move around a ring).
+__host__ __device__ constexpr int tperm(int p, int L) {
+    return p == 0 ? 0 : (p == 1 ? (L > 2 ? 2 : 1) : (p % 2 == 1 ? p - 2 : (p == L - 2 ? L - 1 : p + 2)));
+}
+
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+
+__device__ __forceinline__ cx<float> cdivf(cx<float> a, cx<float> b) {
+    const float inv = frcp(b.r * b.r + b.i * b.i);
+    return mkc((a.r * b.r + a.i * b.i) * inv, (a.i * b.r - a.r * b.i) * inv);
+}
+
+__device__ __forceinline__ cx<float> shfl_up_c(cx<float> v, int o) {
+    return mkc(__shfl_up_sync(kFull, v.r, o), __shfl_up_sync(kFull, v.i, o));
+}
+
+// Coefficient i of Q(z) from c_0 (real) and c_1..c_{L-1}.
+template <int L>
+__device__ __forceinline__ cx<float> qcoef(const cx<float>* c, int i) {
+    const int k = i - (L - 1);
+    if (k == 0) return c[0];
+    return k > 0 ? c[k] : conjg(c[-k]);
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d) {
+    p = qcoef<L>(c, 2 * L - 2);
+    d = mkc(0.f, 0.f);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d = d * z + p;
+        p = p * z + qcoef<L>(c, i);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pdd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d1,
+                                           cx<float>& d2) {
+    p = qcoef<L>(c, 2 * L - 2);
+    d1 = mkc(0.f, 0.f);
+    d2 = mkc(0.f, 0.f);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d2 = d2 * z + d1;
+        d1 = d1 * z + p;
+        p = p * z + qcoef<L>(c, i);
+    }
+    d2 = 2.f * d2;
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pdd64(const cx<float>* c, cx<double> z, cx<double>& p, cx<double>& d1,
+                                             cx<double>& d2) {
+    auto q64 = [&](int i) {
+        cx<float> v = qcoef<L>(c, i);
+        return mkc((double)v.r, (double)v.i);
+    };
+    p = q64(2 * L - 2);
+    d1 = mkc(0.0, 0.0);
+    d2 = mkc(0.0, 0.0);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d2 = d2 * z + d1;
+        d1 = d1 * z + p;
+        p = p * z + q64(i);
+    }
+    d2 = 2.0 * d2;
+}
+
+// Add entry (r, s) of R_f (value v) to S = Re(Q^H R_f Q) up to the factor 1/2, with the
+// unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) of even order L = 2h. Writing R_f in h x h blocks,
+// with i = fold(r), k = fold(s) (fold(t) = t for t < h, L - 1 - t otherwise):
+//   S11[i][k] =  Re(a + b + c + d),  S22[i][k] = Re(a - b - c + d),  S12[i][k] = -Im(a - b + c - d)
+// where a, b, c, d are the entries (i, k), (i, L-1-k), (L-1-i, k), (L-1-i, L-1-k). Only the upper
+// triangles of the symmetric blocks S11, S22 are kept (i <= k); S12 is kept whole.
+template <int L>
+__device__ __forceinline__ void accumulate_s(float* S, int r, int s, cx<float> v) {
+    constexpr int h = L / 2;
+    const int i = r < h ? r : L - 1 - r;
+    const int k = s < h ? s : L - 1 - s;
+    if (s < h)
+        S[tri(i, h + k, L)] -= v.i;
+    else
+        S[tri(i, h + k, L)] += v.i;
+    if (i <= k) {
+        S[tri(i, k, L)] += v.r;
+        if ((r < h) == (s < h))
+            S[tri(h + i, h + k, L)] += v.r;
+        else
+            S[tri(h + i, h + k, L)] -= v.r;
+    }
+}
+
+// CTAS is the number of 128-thread CTAs the kernel is compiled to keep resident per SM
+// (__launch_bounds__ minimum blocks, i.e. a register cap of 65536 / (128 CTAS)). More CTAs hide
+// more latency but spill more; the best cap depends on L and is chosen by measurement (the
+// variants of each L are listed in batched_variants.h).
+template <int L, int CTAS>
+__global__ void __launch_bounds__(kBatThreads, CTAS)
+batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
+               unsigned long long* __restrict__ counter, const float2* __restrict__ gam,
+               float* __restrict__ out, uint8_t* __restrict__ status, BatchedArgs args) {
+    static_assert(L % 2 == 0 && L >= 2 && L <= kMaxL, "even L only");
+    constexpr int h = L / 2;
+    constexpr int NS = L * (L + 1) / 2;
+    constexpr int NI = L - 1;  // roots inside the unit disk (the other L - 1 are their mirrors)
+    __shared__ float2 sh_seg[kBatWarps][32 + kMaxN];
+    __shared__ float2 sh_pre[kBatWarps][3 * 32 + 1];
+    __shared__ float sh_S[NS * kBatThreads];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* seg = sh_seg[wid];
+    float2* pre = sh_pre[wid];
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)total_items) break;
+        const int f = find_frame(fr, nframes, (int64_t)item, [](const FrameDev& F) { return F.item_start; });
+        const FrameDev& F = fr[f];
+        const int64_t local = (int64_t)item - F.item_start;
+        const int wline = (int)(local / F.nchunks);
+        const int chunk = (int)(local % F.nchunks);
+        const int N = F.N, K = N - L + 1, wlen = F.wlen;
+        const int pos = chunk * kChunk + lane;
+        const int a0 = chunk * kChunk - N / 2;
+        const float2* gl = gam + F.gam_off + (uint64_t)wline * wlen;
+
+        // ---- stage the run's samples (coalesced) --------------------------------------------
+        __syncwarp();
+        for (int j = lane; j < 31 + N; j += 32) {
+            const int p = a0 + j;
+            seg[j] = (p >= 0 && p < wlen) ? gl[p] : make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+        const bool inside = pos < wlen;
+        const bool valid = inside && (pos - N / 2 >= 0) && (pos - N / 2 + N - 1 <= wlen - 1);
+
+        // ---- S = Re(Q^H R_f Q) accumulated from the lag-product box sums ------------------------
+        // Every box sum K R_f[m][m+d] (and its Hermitian mirror) is added straight into the
+        // entries of S it feeds, so R_f is never held whole. Constant factors (1/K, 1/2) are
+        // dropped: S is normalised by its trace below, which leaves its eigenvectors unchanged.
+        float S[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) S[i] = 0.f;
+#pragma unroll
+        for (int d = 0; d < L; ++d) {
+            const int G = 31 + N - d;  // lag products g_d[0 .. G-1] are needed
+            const int j0 = 3 * lane;
+            cx<float> s0 = mkc(0.f, 0.f), s1, s2;
+            if (j0 < G) {
+                float2 a = seg[j0], b = seg[j0 + d];
+                s0 = mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+            }
+            s1 = s0;
+            if (j0 + 1 < G) {
+                float2 a = seg[j0 + 1], b = seg[j0 + 1 + d];
+                s1 = s1 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+            }
+            s2 = s1;
+            if (j0 + 2 < G) {
+                float2 a = seg[j0 + 2], b = seg[j0 + 2 + d];
+                s2 = s2 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+            }
+            cx<float> incl = s2;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                cx<float> t = shfl_up_c(incl, o);
+                if (lane >= o) incl = incl + t;
+            }
+            cx<float> excl = shfl_up_c(incl, 1);
+            if (lane == 0) excl = mkc(0.f, 0.f);
+            __syncwarp();
+            const cx<float> p1 = excl + s0, p2 = excl + s1, p3 = excl + s2;
+            pre[j0 + 1] = make_float2(p1.r, p1.i);
+            pre[j0 + 2] = make_float2(p2.r, p2.i);
+            pre[j0 + 3] = make_float2(p3.r, p3.i);
+            if (lane == 0) pre[0] = make_float2(0.f, 0.f);
+            __syncwarp();
+#pragma unroll
+            for (int m = 0; m + d < L; ++m) {
+                const float2 hi = pre[lane + m + K], lo = pre[lane + m];
+                const cx<float> v = mkc(hi.x - lo.x, hi.y - lo.y);  // K R_f[m][m+d]
+                accumulate_s<L>(S, m, m + d, v);
+                if (d > 0) accumulate_s<L>(S, m + d, m, conjg(v));
+            }
+        }
+        float tr = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) tr += S[tri(i, i, L)];
+        const bool nonzero = valid && tr > 0.f && isfinite(tr);
+        const float itr = nonzero ? frcp(tr) : 0.f;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) S[i] = nonzero ? S[i] * itr : 0.f;
+        if (!nonzero) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) S[tri(i, i, L)] = (float)(L - i);  // any well-separated stand-in
+        }
+
+        // ---- cyclic Jacobi on S for the eigenvalues -----------------------------------------------
+        // Tournament ("circle") ordering: each of the L - 1 steps of a sweep rotates the disjoint
+        // pairs (0,1), (2,3), ... and then relabels the indices by the fixed permutation tperm, so
+        // that every pair (p, q) is rotated exactly once per sweep and the labels return to the
+        // identity after the sweep. The step is one rolled loop body.
+        // The normalised S is parked in shared memory (one column per thread) for the inverse
+        // iteration; the rotations then work on S in place.
+        float* const Ssh = sh_S + threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) Ssh[i * kBatThreads] = S[i];
+        int sweeps = 0;
+        bool jconv = false;
+        float l1 = 0.f, l2 = 0.f;
+        int k1 = 0;
+        for (;;) {
+#pragma unroll 1
+            for (int stp = 0; stp < L - 1; ++stp) {
+#pragma unroll
+                for (int p = 0; p < L; p += 2) {
+                    const int q = p + 1;
+                    const float apq = S[tri(p, q, L)];
+                    const float dq = S[tri(q, q, L)] - S[tri(p, p, L)];
+                    const float den = fabsf(dq) + sqrtf(fmaf(dq, dq, 4.f * apq * apq));
+                    float t = den > 0.f ? __fdividef(2.f * apq, den) : 0.f;
+                    t = dq < 0.f ? -t : t;
+                    const float c = rsqrtf(fmaf(t, t, 1.f));
+                    const float s = t * c;
+                    S[tri(p, p, L)] = fmaf(-t, apq, S[tri(p, p, L)]);
+                    S[tri(q, q, L)] = fmaf(t, apq, S[tri(q, q, L)]);
+                    S[tri(p, q, L)] = 0.f;
+#pragma unroll
+                    for (int r = 0; r < L; ++r) {
+                        if (r == p || r == q) continue;
+                        const float g = S[tri(r, p, L)], hh = S[tri(r, q, L)];
+                        S[tri(r, p, L)] = fmaf(c, g, -s * hh);
+                        S[tri(r, q, L)] = fmaf(s, g, c * hh);
+                    }
+                }
+                float B[NS];
+#pragma unroll
+                for (int r = 0; r < L; ++r)
+#pragma unroll
+                    for (int cc = r; cc < L; ++cc) B[tri(r, cc, L)] = S[tri(tperm(r, L), tperm(cc, L), L)];
+#pragma unroll
+                for (int i = 0; i < NS; ++i) S[i] = B[i];
+            }
+            ++sweeps;
+            float off = 0.f;
+#pragma unroll
+            for (int p = 0; p < L - 1; ++p)
+#pragma unroll
+                for (int q = p + 1; q < L; ++q) off = fmaf(S[tri(p, q, L)], S[tri(p, q, L)], off);
+            // The sweeps only have to place mu (below) near l1: the largest diagonal entry a_kk
+            // differs from l1 by at most about off / gap, so once off <= 1e-3 gap^2 the shift is
+            // within ~1e-3 gap of l1 and three inverse-iteration steps reduce the other
+            // eigenvectors' share by ~1e-9. A signal-dominated window gets there in one sweep;
+            // more sweeps run only while some lane of the warp is short of it.
+            l1 = S[tri(0, 0, L)];
+            l2 = -1e30f;
+            k1 = 0;
+#pragma unroll
+            for (int i = 1; i < L; ++i) {
+                const float v = S[tri(i, i, L)];
+                if (v > l1) {
+                    l2 = l1;
+                    l1 = v;
+                    k1 = i;
+                } else if (v > l2) {
+                    l2 = v;
+                }
+            }
+            const float gap = l1 - l2;
+            jconv = off <= 1e-3f * gap * gap;
+            if (sweeps >= args.max_sweeps) break;
+            if (__all_sync(kFull, jconv)) break;
+        }
+        const bool separated = l1 - l2 > 4e-6f * l1;
+
+        // ---- inverse iteration: (mu I - S) x = b, b = column k1 of S ----------------------------
+        const float mu = l1 + 1e-5f * l1 + 1e-30f;
+        float Lm[NS];  // unit lower factor in the packed layout, D on the diagonal slots
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            float dj = mu - Ssh[tri(j, j, L) * kBatThreads];
+#pragma unroll
+            for (int k = 0; k < j; ++k) dj = fmaf(-Lm[tri(j, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], dj);
+            if (fabsf(dj) < 1e-30f) dj = dj < 0.f ? -1e-30f : 1e-30f;
+            Lm[tri(j, j, L)] = dj;
+            const float inv = frcp(dj);
+#pragma unroll
+            for (int i = j + 1; i < L; ++i) {
+                float v = -Ssh[tri(i, j, L) * kBatThreads];
+#pragma unroll
+                for (int k = 0; k < j; ++k) v = fmaf(-Lm[tri(i, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], v);
+                Lm[tri(i, j, L)] = v * inv;
+            }
+        }
+        float x[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) x[i] = Ssh[tri(i, k1, L) * kBatThreads];
+#pragma unroll 1
+        for (int step = 0; step < 3; ++step) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+#pragma unroll
+                for (int k = 0; k < i; ++k) x[i] = fmaf(-Lm[tri(i, k, L)], x[k], x[i]);
+#pragma unroll
+            for (int i = 0; i < L; ++i) x[i] *= frcp(Lm[tri(i, i, L)]);
+#pragma unroll
+            for (int i = L - 1; i >= 0; --i)
+#pragma unroll
+                for (int k = i + 1; k < L; ++k) x[i] = fmaf(-Lm[tri(k, i, L)], x[k], x[i]);
+            float n2 = 0.f;
+#pragma unroll
+            for (int i = 0; i < L; ++i) n2 = fmaf(x[i], x[i], n2);
+            const float inv = rsqrtf(n2);
+#pragma unroll
+            for (int i = 0; i < L; ++i) x[i] *= inv;
+        }
+
+        // ---- u1 = Q x1 and the polynomial coefficients ---------------------------------------------
+        cx<float> u[L];
+        const float r2 = 0.70710678118654752f;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            u[i] = mkc(r2 * x[i], r2 * x[h + i]);
+            u[h + i] = mkc(r2 * x[h - 1 - i], -r2 * x[L - 1 - i]);
+        }
+        float nu2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) nu2 += norm2(u[i]);
+        // Shrinking the lag coefficients by (1 - eta) makes Q(e^jw) e^-j(L-1)w =
+        // (1 - eta) P(w) + eta (L - 1) >= eta (L - 1) > 0 on the circle, above the FP32 rounding
+        // of the coefficients (~1e-6 of P). Without it, rounding can push a noise-free double root
+        // apart along the circle (two roots at w0 +- d, d ~ 1e-3); with it the pair always splits
+        // radially and keeps the angle of the minimum of P.
+        const float inu2 = (1.f - 2e-6f) * frcp(nu2);
+        cx<float> c[L];
+        c[0] = mkc((float)(L - 1), 0.f);
+        // sum_i |q_i| bounds sum_i |q_i| |z|^i for every tracked root (all stay in the unit disk):
+        // the scale of Q's rounding error in the residual test below
+        float qsum = (float)(L - 1);
+#pragma unroll
+        for (int k = 1; k < L; ++k) {
+            cx<float> rho = mkc(0.f, 0.f);
+#pragma unroll
+            for (int m = 0; m + k < L; ++m) rho = rho + mulc(u[m], u[m + k]);
+            c[k] = (-inu2) * rho;
+            qsum += 2.f * sqrtf(norm2(c[k]));
+        }
+        const float res_lim2 = (3e-6f * qsum) * (3e-6f * qsum);
+
+        // ---- Aberth-Ehrlich on the inner roots --------------------------------------------------------
+        // Q's coefficients satisfy c_-k = conj(c_k), so its roots come in pairs z, 1/conj(z). Only
+        // the L - 1 roots inside the unit disk are iterated; each Aberth sum runs over the other
+        // inner roots and over all mirrors 1/conj(z_j) (the root's own partner included), and a
+        // root that steps outside is folded back to its mirror. The loop over roots is rolled:
+        // the current root is always position 0 and the arrays rotate by one after each update,
+        // which keeps the code small enough for the instruction cache.
+        cx<float> z[NI], mz[NI];
+        {
+            const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
+            const float n1 = norm2(rho1);
+            const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
+            z[0] = 0.99f * e;
+            float sh, ch;
+            sincospif(1.0f / (float)L, &sh, &ch);                           // exp(j pi / L)
+            const cx<float> step = mkc(ch * ch - sh * sh, 2.f * sh * ch);  // exp(2 j pi / L)
+            cx<float> ek = e * mkc(ch, sh) * step;                           // angle + 2 pi (1 + 1/2) / L
+            const float rin = (float)L / ((float)L + 7.3f);
+#pragma unroll
+            for (int k = 1; k < NI; ++k) {
+                z[k] = rin * ek;
+                ek = ek * step;
+            }
+#pragma unroll
+            for (int k = 0; k < NI; ++k) mz[k] = frcp(norm2(z[k])) * z[k];
+        }
+        int iters = 0, updates = 0;
+        bool rconv = false;
+        unsigned frozen = 0;  // bit r: the root now at position r has converged in this lane
+        for (;;) {
+            rconv = true;
+#pragma unroll 1
+            for (int r = 0; r < NI; ++r) {
+                const cx<float> z0 = z[0];
+                cx<float> nz = z0, nm = mz[0];
+                // A root whose residual reached the rounding level is frozen: near a double root
+                // the corrections below that level are noise and would push it off its angle.
+                // Roots frozen in every lane of the warp are skipped altogether.
+                if (!__all_sync(kFull, frozen & 1u)) {
+                cx<float> p, dp;
+                horner_pd<L>(c, z0, p, dp);
+                const bool cv = (frozen & 1u) || norm2(p) <= res_lim2;
+                frozen |= cv ? 1u : 0u;
+                rconv = rconv && cv;
+                if (!__all_sync(kFull, cv)) {
+                    ++updates;
+                    const cx<float> Ni = cdivf(p, dp);
+                    cx<float> Si = mkc(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < NI; ++j) {
+                        if (j > 0) {
+                            const cx<float> dz = z0 - z[j];
+                            const float inv = frcp(norm2(dz));
+                            Si = mkc(fmaf(dz.r, inv, Si.r), fmaf(-dz.i, inv, Si.i));
+                        }
+                        const cx<float> dm = z0 - mz[j];
+                        const float invm = frcp(norm2(dm));
+                        Si = mkc(fmaf(dm.r, invm, Si.r), fmaf(-dm.i, invm, Si.i));
+                    }
+                    const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - Ni * Si);
+                    if (!cv && isfinite(w.r) && isfinite(w.i)) nz = z0 - w;
+                    const float r2n = norm2(nz);
+                    const float ir2 = frcp(r2n);
+                    nm = ir2 * nz;
+                    if (r2n > 1.f) {  // fold back inside: swap the root and its mirror
+                        const cx<float> t = nz;
+                        nz = nm;
+                        nm = t;
+                    }
+                }
+                }
+                frozen = (frozen >> 1) | ((frozen & 1u) << (NI - 1));
+#pragma unroll
+                for (int j = 0; j + 1 < NI; ++j) {
+                    z[j] = z[j + 1];
+                    mz[j] = mz[j + 1];
+                }
+                z[NI - 1] = nz;
+                mz[NI - 1] = nm;
+            }
+            ++iters;
+            if (iters >= args.max_iters) break;
+            if (__all_sync(kFull, rconv)) break;
+        }
+
+        // ---- selection (Algorithm 1) ------------------------------------------------------------------
+        // every tracked root is inside the disk: the one nearest the circle has the largest modulus
+        int best = -1;
+        float bestr = -1.f;
+        cx<float> zs = mkc(1.f, 0.f), ms = zs;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const float r = norm2(z[i]);
+            if (r > bestr) {
+                bestr = r;
+                best = i;
+                zs = z[i];
+                ms = mz[i];
+            }
+        }
+        // nearest other root of the full set: its own mirror, another inner root or a mirror
+        float neard = norm2(ms - zs);
+        cx<float> zn = ms;
+#pragma unroll
+        for (int j = 0; j < NI; ++j) {
+            const float dj = norm2(z[j] - zs), dmj = norm2(mz[j] - zs);
+            if (j != best && dj < neard) {
+                neard = dj;
+                zn = z[j];
+            }
+            if (j != best && dmj < neard) {
+                neard = dmj;
+                zn = mz[j];
+            }
+        }
+        const bool cluster = neard < 4e-3f * 4e-3f;
+        cx<float> zz = cluster ? 0.5f * (zs + zn) : zs;
+#pragma unroll 1
+        for (int it = 0; it < 2; ++it) {
+            cx<float> p, d1, d2;
+            horner_pdd<L>(c, zz, p, d1, d2);
+            cx<float> stp;
+            if (cluster) {
+                stp = cdivf(d1, d2);
+            } else {
+                const float in2 = frcp(norm2(zz));
+                const cx<float> dzp = zz - in2 * zz;  // z - 1/conj(z)
+                stp = cdivf(p, d1 - cdivf(p, dzp));
+            }
+            if (isfinite(stp.r) && isfinite(stp.i)) zz = zz - stp;
+        }
+        double omd;
+        if (args.polish64) {
+            cx<double> z64 = mkc((double)zz.r, (double)zz.i);
+            cx<double> p, d1, d2;
+            horner_pdd64<L>(c, z64, p, d1, d2);
+            cx<double> stp;
+            if (cluster) {
+                stp = cdiv(d1, d2);
+            } else {
+                const double in2 = 1.0 / norm2(z64);
+                const cx<double> dzp = z64 - in2 * z64;
+                stp = cdiv(p, d1 - cdiv(p, dzp));
+            }
+            if (isfinite(stp.r) && isfinite(stp.i)) z64 = z64 - stp;
+            omd = atan2(z64.i, z64.r) - (double)F.omega_ref;
+            omd = wrap_pi(omd);
+        } else {
+            omd = 0.0;
+        }
+        float om = args.polish64 ? (float)omd : wrap_pi(atan2f(zz.i, zz.r) - (float)F.omega_ref);
+
+        if (lane == 0 && args.counters) {
+            atomicAdd(args.counters + 0, (unsigned long long)sweeps);
+            atomicAdd(args.counters + 1, (unsigned long long)iters);
+            atomicAdd(args.counters + 2, 1ull);
+            atomicAdd(args.counters + 3, (unsigned long long)updates);
+        }
+
+        // ---- store ---------------------------------------------------------------------------------
+        if (inside) {
+            const uint64_t o = out_index(F, wline, pos);
+            uint8_t st = kStOk;
+            if (!valid) {
+                st = kStBorder;
+            } else if (!nonzero || !separated || best < 0) {
+                st = kStDegenerate;
+            } else if (!rconv || !jconv) {
+                st = kStNotConverged;
+            }
+            out[o] = (st == kStOk || st == kStNotConverged) ? om : __int_as_float(0x7fc00000);
+            if (status) status[o] = st;
+        }
+    }
+}
+
+}  // namespace rmusic

@@ -1,0 +1,40 @@
+// batched_variants.h -- register-cap variants of the FP32-batched solver per covariance order.
+// Each variant keeps a different number of 128-thread CTAs resident per SM (its
+// __launch_bounds__ minimum); the autotuner in capi.cu times them and keeps the fastest.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rmusic_device.cuh"
+#include "rmusic_launch.h"
+
+namespace rmusic {
+
+constexpr int kSolverVariants = 3;
+constexpr int kSolverDefaultVariant = 1;
+
+// Resident CTAs per SM of variant v (0 .. kSolverVariants - 1) for covariance order L.
+__host__ __device__ constexpr int solver_variant_ctas(int L, int v) {
+    return L == 2 ? (v == 0 ? 8 : v == 1 ? 12 : 16)
+         : L == 4 ? (v == 0 ? 6 : v == 1 ? 8 : 12)
+         : L == 6 ? (v == 0 ? 4 : v == 1 ? 6 : 8)
+         : L == 8 ? (v == 0 ? 4 : v == 1 ? 6 : 8)
+         : L == 10 ? (v == 0 ? 2 : v == 1 ? 3 : 4)
+         : (v == 0 ? 1 : v == 1 ? 2 : 3);
+}
+
+#define RMUSIC_DECLARE_SOLVER(L)                                                                            \
+    cudaError_t launch_solver_l##L(int v, const FrameDev* d_frames, int nframes, int64_t total_items,       \
+                                   unsigned long long* d_counter, const float2* d_gamma, float* d_out,      \
+                                   uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream);        \
+    int occupancy_solver_l##L(int v);
+RMUSIC_DECLARE_SOLVER(2)
+RMUSIC_DECLARE_SOLVER(4)
+RMUSIC_DECLARE_SOLVER(6)
+RMUSIC_DECLARE_SOLVER(8)
+RMUSIC_DECLARE_SOLVER(10)
+RMUSIC_DECLARE_SOLVER(12)
+#undef RMUSIC_DECLARE_SOLVER
+
+}  // namespace rmusic

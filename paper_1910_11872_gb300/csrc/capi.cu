@@ -11,8 +11,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/rmusic.h"
@@ -87,7 +91,8 @@ struct rmusic_ctx {
     size_t held = 0;
     rmusic_stats stats{};
     char last_err[256] = {0};
-    int grid_by_L[kMaxL + 1] = {0};
+    int grid_by_Lv[kMaxL + 1][4] = {{0}};
+    int variant_by_L[kMaxL + 1];  // solver variant chosen for each covariance order, -1 = none yet
 };
 
 namespace {
@@ -271,6 +276,165 @@ void stamp_pair(std::vector<int>& v, int a, int b) {
     }
 }
 
+// ---- solver variant selection (the autotuner) ---------------------------------------------------
+// Each covariance order has several register-cap variants of the solver (batched_variants.h).
+// A variant is chosen per device and covariance order by timing all of them on real work (the
+// first call with `autotune` set, or rmusic_autotune); the choice is shared by every context on
+// the device and, when RMUSIC_TUNE_CACHE names a file, appended to it as a JSON line
+//   {"device": "<name>/<SMs>sm", "L": 8, "variant": 1, "ctas_per_sm": 6, "ms": 1.917}
+// and read back by later processes. Untuned orders use the default variant.
+constexpr int kTuneDevices = 64;
+std::mutex g_tune_mu;
+int g_tuned[kTuneDevices][kMaxL + 1];
+bool g_tune_loaded[kTuneDevices];
+bool g_tune_ready = false;
+
+void tune_init_locked() {
+    if (g_tune_ready) return;
+    for (int d = 0; d < kTuneDevices; ++d) {
+        g_tune_loaded[d] = false;
+        for (int l = 0; l <= kMaxL; ++l) g_tuned[d][l] = -1;
+    }
+    g_tune_ready = true;
+}
+
+std::string device_key(int device) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
+    return std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "sm";
+}
+
+// Value of "key": in a JSON line written by store_tune (strings without escapes, integers).
+bool json_field(const char* line, const char* key, std::string* out) {
+    std::string pat = std::string("\"") + key + "\": ";
+    const char* p = strstr(line, pat.c_str());
+    if (!p) return false;
+    p += pat.size();
+    if (*p == '"') {
+        const char* e = strchr(p + 1, '"');
+        if (!e) return false;
+        *out = std::string(p + 1, e);
+    } else {
+        const char* e = p;
+        while (*e && *e != ',' && *e != '}') ++e;
+        *out = std::string(p, e);
+    }
+    return true;
+}
+
+void load_tune_locked(int device) {
+    if (device < 0 || device >= kTuneDevices || g_tune_loaded[device]) return;
+    g_tune_loaded[device] = true;
+    const char* path = getenv("RMUSIC_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    const std::string key = device_key(device);
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        std::string dev, ls, vs;
+        if (!json_field(line, "device", &dev) || dev != key) continue;
+        if (!json_field(line, "L", &ls) || !json_field(line, "variant", &vs)) continue;
+        const int L = atoi(ls.c_str()), v = atoi(vs.c_str());
+        if (batched_supports(L) && v >= 0 && v < batched_num_variants(L)) g_tuned[device][L] = v;
+    }
+    fclose(f);
+}
+
+void store_tune(int device, int L, int v, float ms) {
+    const char* path = getenv("RMUSIC_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"device\": \"%s\", \"L\": %d, \"variant\": %d, \"ctas_per_sm\": %d, \"ms\": %.4f}\n",
+            device_key(device).c_str(), L, v, batched_variant_ctas(L, v), ms);
+    fclose(f);
+}
+
+int solver_variant(rmusic_ctx* ctx, int L) {
+    if (ctx->variant_by_L[L] >= 0) return ctx->variant_by_L[L];
+    int v = -1;
+    if (ctx->device < kTuneDevices) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_init_locked();
+        load_tune_locked(ctx->device);
+        v = g_tuned[ctx->device][L];
+    }
+    return v >= 0 ? v : batched_default_variant(L);
+}
+
+bool solver_tuned(rmusic_ctx* ctx, int L) {
+    if (ctx->variant_by_L[L] >= 0) return true;
+    if (ctx->device >= kTuneDevices) return false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_init_locked();
+    load_tune_locked(ctx->device);
+    return g_tuned[ctx->device][L] >= 0;
+}
+
+int solver_grid(rmusic_ctx* ctx, int L, int v) {
+    if (ctx->grid_by_Lv[L][v] == 0) ctx->grid_by_Lv[L][v] = batched_grid(L, v, ctx->device);
+    return ctx->grid_by_Lv[L][v];
+}
+
+// Time every solver variant on `plan`, whose table and analytic signal are already on the device
+// (queued on s), and keep the fastest for each covariance order not tuned yet (all of them when
+// `force`). Synchronises s; the maps it writes are the call's results.
+int tune_plan(rmusic_ctx* ctx, const Plan& plan, float* d_out, uint8_t* d_status, cudaStream_t s, bool force) {
+    const rmusic_params& p = ctx->p;
+    BatchedArgs a;
+    a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
+    a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
+    a.polish64 = p.polish_fp64;
+    a.counters = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    RM_CUDA(cudaEventCreate(&t0));
+    RM_CUDA(cudaEventCreate(&t1));
+    int rc = RMUSIC_OK;
+    for (size_t g = 0; g < plan.group_L.size() && rc == RMUSIC_OK; ++g) {
+        const int L = plan.group_L[g];
+        if (!force && solver_tuned(ctx, L)) continue;
+        float best = 1e30f;
+        int bestv = batched_default_variant(L);
+        for (int v = 0; v < batched_num_variants(L) && rc == RMUSIC_OK; ++v) {
+            float tmin = 1e30f;
+            for (int rep = 0; rep < 2 && rc == RMUSIC_OK; ++rep) {
+                cudaError_t e = cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, s);
+                if (e == cudaSuccess)
+                    e = launch_batched(L, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
+                                       plan.group_items[g], ctx->d_counters + g,
+                                       static_cast<const float2*>(ctx->d_gamma), d_out, d_status, a,
+                                       solver_grid(ctx, L, v), s);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(ctx, e, "autotune");
+                    break;
+                }
+                tmin = std::min(tmin, ms);
+            }
+            if (tmin < best) {
+                best = tmin;
+                bestv = v;
+            }
+        }
+        if (rc) break;
+        ctx->variant_by_L[L] = bestv;
+        if (ctx->device < kTuneDevices) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            tune_init_locked();
+            g_tuned[ctx->device][L] = bestv;
+        }
+        store_tune(ctx->device, L, bestv, best);
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return rc;
+}
+
 int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_out, uint8_t* d_status,
             cudaStream_t s, int* launches) {
     const int n = (int)plan.frames.size();
@@ -288,14 +452,15 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         a.counters = ctx->d_counters + kStatSlot;
         for (size_t g = 0; g < plan.group_L.size(); ++g) {
             const int L = plan.group_L[g];
-            if (ctx->grid_by_L[L] == 0) ctx->grid_by_L[L] = batched_grid(L, ctx->device);
+            const int v = solver_variant(ctx, L);
             RM_CUDA(cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s));
             int e1 = stamp(ctx, s);
-            RM_CUDA(launch_batched(L, ctx->d_table + plan.group_first[g], plan.group_count[g],
+            RM_CUDA(launch_batched(L, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
                                    plan.group_items[g], ctx->d_counters + g,
                                    static_cast<const float2*>(ctx->d_gamma), d_out, d_status,
-                                   a, ctx->grid_by_L[L], s));
+                                   a, solver_grid(ctx, L, v), s));
             stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
+            ctx->stats.solver_ctas_per_sm = batched_variant_ctas(L, v);
             ++*launches;
         }
     } else {
@@ -345,7 +510,7 @@ int ensure_tables(rmusic_ctx* ctx, size_t nframes) {
 
 // Process frames [first, first + count) of descs as one workspace group.
 int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int count,
-              float* d_out, uint8_t* d_status, cudaStream_t s) {
+              float* d_out, uint8_t* d_status, cudaStream_t s, bool force_tune) {
     Plan plan;
     int rc = build_plan(ctx, descs, count, &plan);
     if (rc) return rc;
@@ -353,6 +518,28 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
     if (rc) return rc;
     rc = ensure_tables(ctx, plan.frames.size());
     if (rc) return rc;
+
+    // autotune: time the solver variants on this call's work (band-pass first, outside any graph)
+    if (ctx->p.precision == RMUSIC_FP32_BATCHED && (force_tune || ctx->p.autotune)) {
+        bool need = force_tune;
+        for (int L : plan.group_L) need = need || !solver_tuned(ctx, L);
+        if (need) {
+            RM_CUDA(cudaEventSynchronize(ctx->table_free));
+            memcpy(ctx->h_table, plan.frames.data(), plan.frames.size() * sizeof(FrameDev));
+            RM_CUDA(cudaMemcpyAsync(ctx->d_table, ctx->h_table, plan.frames.size() * sizeof(FrameDev),
+                                    cudaMemcpyHostToDevice, s));
+            RM_CUDA(cudaEventRecord(ctx->table_free, s));
+            RM_CUDA(launch_analytic(ctx->d_table, (int)plan.frames.size(), plan.total_lines, plan.max_len, d_frames,
+                                    ctx->d_gamma, false, s));
+            rc = tune_plan(ctx, plan, d_out, d_status, s, force_tune);
+            if (rc) return rc;
+            for (auto& g : ctx->graphs) {  // captured graphs may hold the previous variants
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                if (g.h_table) cudaFreeHost(g.h_table);
+                g = GraphEntry{};
+            }
+        }
+    }
 
     const bool graph = ctx->p.use_graph && ctx->p.precision == RMUSIC_FP32_BATCHED;
     int launches = 0;
@@ -456,6 +643,7 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
     if (!ctx) return RMUSIC_ENOMEM;
     ctx->p = *params;
     ctx->device = device;
+    for (int l = 0; l <= kMaxL; ++l) ctx->variant_by_L[l] = -1;
     ctx->budget = hbm_budget_bytes;
     DeviceGuard guard(device);
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -475,8 +663,12 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
     return RMUSIC_OK;
 }
 
-int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
-                             int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream) {
+}  // extern "C"
+
+namespace {
+
+int demodulate_impl(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int32_t n_frames,
+                    float* d_out, uint8_t* d_status, void* cuda_stream, bool force_tune) {
     if (!ctx || n_frames < 0) return RMUSIC_EINVAL;
     ctx->stats.kernel_launches = 0;
     ctx->stats.graph_replayed = 0;
@@ -515,7 +707,7 @@ int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic
             ++count;
         }
         if (ctx->budget && bytes > avail) return RMUSIC_ENOMEM;
-        int rc = run_group(ctx, d_frames, descs + first, count, d_out, d_status, s);
+        int rc = run_group(ctx, d_frames, descs + first, count, d_out, d_status, s, force_tune);
         if (rc) return rc;
         first += count;
     }
@@ -523,6 +715,21 @@ int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic
     ctx->last_pixels = pixels;
     RM_CUDA(cudaEventRecord(ctx->call_done, s));
     return RMUSIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
+                             int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream) {
+    return demodulate_impl(ctx, d_frames, descs, n_frames, d_out, d_status, cuda_stream, false);
+}
+
+int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int32_t n_frames,
+                    float* d_out, uint8_t* d_status, void* cuda_stream) {
+    if (ctx && ctx->p.precision != RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
+    return demodulate_impl(ctx, d_frames, descs, n_frames, d_out, d_status, cuda_stream, true);
 }
 
 int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,

@@ -201,8 +201,9 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
         a.counters = nullptr;
         for (int g = 0; g < ngroups && rc == RMUSIC_OK; ++g) {
             const int L = group_L[g];
-            if (launch_batched(L, d_table + group_first[g], group_count[g], group_items[g], counters + g, gamma,
-                               d_out, d_status, a, batched_grid(L, device), s) != cudaSuccess)
+            const int v = batched_default_variant(L);
+            if (launch_batched(L, v, d_table + group_first[g], group_count[g], group_items[g], counters + g, gamma,
+                               d_out, d_status, a, batched_grid(L, v, device), s) != cudaSuccess)
                 rc = RMUSIC_ECUDA;
         }
     } while (0);

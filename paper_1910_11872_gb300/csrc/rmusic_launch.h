@@ -35,10 +35,13 @@ struct BatchedArgs {
     unsigned long long* counters;  // [0] sweeps, [1] root iterations, [2] items, [3] root updates
 };
 bool batched_supports(int L);
+int batched_num_variants(int L);
+int batched_default_variant(int L);
+int batched_variant_ctas(int L, int v);  // resident CTAs per SM variant v is compiled for
 cudaError_t init_batched(int device);
-cudaError_t launch_batched(int L, const FrameDev* d_frames, int nframes, int64_t total_items,
+cudaError_t launch_batched(int L, int v, const FrameDev* d_frames, int nframes, int64_t total_items,
                            unsigned long long* d_counter, const float2* d_gamma, float* d_out,
                            uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream);
-int batched_grid(int L, int device);
+int batched_grid(int L, int v, int device);
 
 }  // namespace rmusic

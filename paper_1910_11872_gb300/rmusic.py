@@ -53,6 +53,7 @@ class rmusic_params(ctypes.Structure):
         ("polish_fp64", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("timing", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -80,6 +81,8 @@ class rmusic_stats(ctypes.Structure):
         ("mean_root_updates", ctypes.c_double),
         ("bandpass_ms", ctypes.c_float),
         ("solver_ms", ctypes.c_float),
+        ("solver_ctas_per_sm", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
     ]
 
 
@@ -123,6 +126,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_demodulate_frames_noalloc.argtypes = [ctypes.POINTER(rmusic_params), ctypes.c_int, vp,
                                                          ctypes.POINTER(rmusic_frame_desc), i32, vp, vp, vp]
         lib.rmusic_demodulate_frames_noalloc.restype = ctypes.c_int
+        lib.rmusic_autotune.argtypes = [vp, vp, ctypes.POINTER(rmusic_frame_desc), i32, vp, vp, vp]
+        lib.rmusic_autotune.restype = ctypes.c_int
         lib.rmusic_destroy.argtypes = [vp]
         lib.rmusic_destroy.restype = None
         lib.rmusic_strerror.argtypes = [ctypes.c_int]
@@ -195,6 +200,16 @@ def rmusic_demodulate_frames_noalloc(params: rmusic_params, device: int, d_frame
     return rc
 
 
+def rmusic_autotune(ctx, d_frames: int, descs, n_frames: int, d_out: int, d_status: int | None,
+                    cuda_stream: int | None) -> int:
+    arr = _desc_array(descs)
+    rc = load_library().rmusic_autotune(ctx, d_frames or None, arr, int(n_frames), d_out or None, d_status or None,
+                                        cuda_stream or None)
+    if rc != RMUSIC_OK:
+        raise RmusicError(rc, "rmusic_autotune", rmusic_last_cuda_error(ctx))
+    return rc
+
+
 def rmusic_destroy(ctx) -> None:
     if ctx:
         load_library().rmusic_destroy(ctx)
@@ -218,11 +233,12 @@ def rmusic_get_stats(ctx) -> rmusic_stats:
 # ------------------------------------------------------------------------------------------
 def make_params(window_len=32, cov_order=8, forward_backward=1, deriv_axis=0, carrier_axis=0,
                 carrier_freq=0.1, band_halfwidth=0.0, precision="batched", max_sweeps=0,
-                max_root_iters=0, polish_fp64=0, use_graph=0, timing=0, model_order=1) -> rmusic_params:
+                max_root_iters=0, polish_fp64=0, use_graph=0, timing=0, autotune=0,
+                model_order=1) -> rmusic_params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return rmusic_params(window_len, cov_order, model_order, forward_backward, deriv_axis, carrier_axis,
                          float(carrier_freq), float(band_halfwidth), prec, max_sweeps, max_root_iters,
-                         polish_fp64, use_graph, timing)
+                         polish_fp64, use_graph, timing, autotune)
 
 
 def frame_descs(shapes, dtype_code: int, elem_bytes: int, windows=None):

@@ -423,3 +423,34 @@ def test_uneven_batch_full_sizes_one_launch_sampled():
         if v.any():
             worst = max(worst, float(np.abs(g[ys, xs][v].astype(np.float64) - vals[v]).max()))
     assert worst < 5e-3, worst
+
+
+def test_autotune_variants_identical_and_cached(tmp_path, monkeypatch):
+    """Every register-cap variant of the solver computes the same maps bit for bit; rmusic_autotune
+    keeps one per covariance order and records it in the cache file named by RMUSIC_TUNE_CACHE."""
+    torch = _torch()
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("RMUSIC_TUNE_CACHE", str(cache))
+    frames = [synth.peaks_frame(10, 0.1, H=64, W=512).image, synth.peaks_frame(np.inf, 0.1, H=32, W=256).image]
+    windows = [(32, 8), (24, 6)]
+    ref = run_gpu(frames, windows=windows)
+    descs, nbytes, nout = rmusic.frame_descs([f.shape for f in frames], rmusic.RMUSIC_DTYPE_F32, 4, windows)
+    x = torch.from_numpy(np.concatenate([f.ravel() for f in frames])).cuda()
+    dem = rmusic.Demodulator()
+    try:
+        out = torch.empty(nout, device="cuda")
+        st = torch.empty(nout, dtype=torch.uint8, device="cuda")
+        s = torch.cuda.current_stream().cuda_stream
+        rmusic.rmusic_autotune(dem.ctx, x.data_ptr(), descs, 2, out.data_ptr(), st.data_ptr(), s)
+        torch.cuda.synchronize()
+        tuned = out.cpu().numpy()
+        rmusic.rmusic_demodulate_frames(dem.ctx, x.data_ptr(), descs, 2, out.data_ptr(), st.data_ptr(), s)
+        torch.cuda.synchronize()
+        again = out.cpu().numpy()
+    finally:
+        dem.close()
+    flat_ref = np.concatenate([g.ravel() for g, _ in ref])
+    assert np.array_equal(tuned, flat_ref, equal_nan=True)
+    assert np.array_equal(again, flat_ref, equal_nan=True)
+    lines = cache.read_text().strip().splitlines()
+    assert {int(l.split('"L": ')[1].split(",")[0]) for l in lines} == {6, 8}
