@@ -92,7 +92,7 @@ def flops_per_pixel(L: int, N: int, sweeps: float, iters: float, updates: float)
 
 
 SOLVER_PROFILE = os.path.join(ROOT, "profiles", "batched_solver_L8_peaks4x1024.md")
-SOLVER_SOURCES = ["batched.cu", "rmusic_device.cuh", "rmusic_launch.h"]
+SOLVER_SOURCES = ["batched_kernel.cuh", "rmusic_device.cuh", "rmusic_launch.h", "batched_variants.h", "batched_l8.cu"]
 
 
 def profiled_traffic():
