@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-F32, U16, F64 = 0, 1, 2
+F32, U16, F64, C64, C128 = 0, 1, 2, 3, 4
 STATUS_OK, STATUS_BORDER, STATUS_DEGENERATE, STATUS_NOT_CONVERGED = 0, 1, 2, 3
 
 
@@ -131,6 +131,11 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_demodulate_pixels.argtypes = [ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(Params),
                                         i32, ip, ip, dp, ctypes.c_void_p, i32]
     L.orc_max_threads.argtypes = []
+    L.orc_square_window_ri.argtypes = [dp, i32, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
+    L.orc_square_demodulate.argtypes = [ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(Params), i32,
+                                        dp, dp, dp, ctypes.c_void_p, i32]
+    L.orc_square_demodulate_pixels.argtypes = [ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(Params),
+                                               i32, i32, ip, ip, dp, dp, dp, ctypes.c_void_p, i32]
 
 
 def _dp(a: np.ndarray):
@@ -153,6 +158,10 @@ def _dtype_code(frame: np.ndarray) -> int:
         return U16
     if frame.dtype == np.float64:
         return F64
+    if frame.dtype == np.complex64:
+        return C64
+    if frame.dtype == np.complex128:
+        return C128
     raise TypeError(f"unsupported frame dtype {frame.dtype}")
 
 
@@ -270,6 +279,58 @@ def demodulate_pixels(frame: np.ndarray, params: Params, ys, xs, nthreads: int =
     if used < 0:
         raise ValueError(f"oracle rejected the input (code {used})")
     return out, st, used
+
+
+# ---------------------------------------------------------------------------------------------
+# The paper's square block geometry (Sec. 3, Eq. 4-15, Algorithm 1)
+# ---------------------------------------------------------------------------------------------
+def square_window(G, ref_x: float = 0.0, ref_y: float = 0.0) -> dict:
+    """One (2Lp+1) x (2Lp+1) block G (rows: y, columns: x). Returns the raw angles omega_x,
+    omega_y (carrier included), alpha, the status and the intermediates u1, v1, zx, zy."""
+    G = np.asarray(G, dtype=np.complex128)
+    M = G.shape[0]
+    assert G.shape == (M, M) and M % 2 == 1
+    Lp = (M - 1) // 2
+    out = np.zeros(3)
+    u = np.zeros(2 * M)
+    v = np.zeros(2 * M)
+    z = np.zeros(4)
+    st = lib().orc_square_window_ri(_dp(_c2ri(G.ravel())), Lp, ref_x, ref_y, _dp(out), _dp(u), _dp(v), _dp(z))
+    return {"wx": float(out[0]), "wy": float(out[1]), "alpha": float(out[2]), "status": int(st),
+            "u1": _ri2c(u), "v1": _ri2c(v), "zx": complex(z[0], z[1]), "zy": complex(z[2], z[3])}
+
+
+def square_demodulate(frame: np.ndarray, params: Params, Lp: int, nthreads: int = 0):
+    """Paper geometry over a whole frame: (dx, dy, alpha, status, threads used); maps are
+    float64 with NaN where undefined."""
+    frame = np.ascontiguousarray(frame)
+    H, W = frame.shape
+    dx, dy, al = np.empty(H * W), np.empty(H * W), np.empty(H * W)
+    st = np.empty(H * W, dtype=np.uint8)
+    used = lib().orc_square_demodulate(frame.ctypes.data, _dtype_code(frame), H, W, ctypes.byref(params),
+                                       Lp, _dp(dx), _dp(dy), _dp(al), st.ctypes.data, nthreads)
+    if used < 0:
+        raise ValueError(f"oracle rejected the input (code {used})")
+    return dx.reshape(H, W), dy.reshape(H, W), al.reshape(H, W), st.reshape(H, W), used
+
+
+def square_demodulate_pixels(frame: np.ndarray, params: Params, Lp: int, ys, xs, nthreads: int = 0):
+    """Paper geometry at the listed pixels only: (dx, dy, alpha, status, threads used)."""
+    frame = np.ascontiguousarray(frame)
+    H, W = frame.shape
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    n = ys.size
+    dx, dy, al = np.empty(n), np.empty(n), np.empty(n)
+    st = np.empty(n, dtype=np.uint8)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    used = lib().orc_square_demodulate_pixels(frame.ctypes.data, _dtype_code(frame), H, W,
+                                              ctypes.byref(params), Lp, n, ys.ctypes.data_as(ip),
+                                              xs.ctypes.data_as(ip), _dp(dx), _dp(dy), _dp(al),
+                                              st.ctypes.data, nthreads)
+    if used < 0:
+        raise ValueError(f"oracle rejected the input (code {used})")
+    return dx, dy, al, st, used
 
 
 def max_threads() -> int:

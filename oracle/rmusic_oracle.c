@@ -22,6 +22,9 @@
  *   step 8  root closest to the unit circle, magnitude below one  (Sec. 3, root selection;
  *                                                                  Algorithm 1)
  *   step 9  angle of the root, minus the carrier                   (Sec. 3, Eq. 15)
+ * and, for the paper's own square block (2 Lp + 1 samples a side), steps 4-9 on the
+ * block's columns and conjugated rows plus the local phase alpha (Sec. 3, Eq. 4-15,
+ * Algorithm 1).
  *
  * Readings taken where the paper is silent or ambiguous (each is exercised by a pin test):
  *   - band-pass: one-sided FT band |k/W - f0| < B, 1 <= k < W/2, B = f0/2 by default;
@@ -37,7 +40,12 @@
  *     taken; if another root lies within 1e-6 of it, the two are one double root split by
  *     rounding, and the root of Q' between them is returned;
  *   - the eigen-decomposition is a cyclic complex Jacobi iteration; the paper's SVD of the
- *     window data yields the same subspaces.
+ *     window data yields the same subspaces;
+ *   - square block: alpha of Eq. 15 is taken with coordinates centred on the pixel, so it
+ *     is the local phase there; the carrier is removed after the angles, from both the
+ *     derivative along the carrier axis and alpha;
+ *   - a complex frame (complex64 / complex128) is the analytic signal itself, as for the
+ *     complex fringe the paper simulates, and is not band-passed.
  *
  * Build: gcc -std=c11 -O2 -ffp-contract=off -fPIC -shared -fopenmp rmusic_oracle.c -lm
  */
@@ -64,6 +72,8 @@ typedef double complex cplx;
 #define ORC_F32 0
 #define ORC_U16 1
 #define ORC_F64 2
+#define ORC_C64 3  /* complex64 (re, im float32): already the analytic signal Gamma */
+#define ORC_C128 4 /* complex128 (re, im double): already the analytic signal Gamma */
 
 typedef struct {
     int32_t window_len;       /* N: samples in the moving window                     */
@@ -138,6 +148,13 @@ int orc_analytic_line(const double* v, int32_t W, double f0, double B, double* g
    (carrier_axis 1). gamma is H*W interleaved complex, row-major like the frame. */
 int orc_analytic_frame(const void* frame, int32_t dtype, int32_t H, int32_t W,
                        int32_t carrier_axis, double f0, double B, double* gamma) {
+    if (dtype == ORC_C64 || dtype == ORC_C128) {
+        /* a complex frame is the analytic signal already (the complex fringe the paper
+           simulates in Sec. 4): it is taken as Gamma without a band-pass */
+        for (size_t i = 0; i < 2 * (size_t)H * (size_t)W; ++i)
+            gamma[i] = dtype == ORC_C64 ? (double)((const float*)frame)[i] : ((const double*)frame)[i];
+        return 0;
+    }
     int32_t nlines = carrier_axis == 0 ? H : W;
     int32_t len = carrier_axis == 0 ? W : H;
     int err = 0;
@@ -435,20 +452,14 @@ int orc_select_root(const cplx* q, int32_t deg, const cplx* roots, int32_t n, do
 }
 
 /* ---------------------------------------------------------------------------------
- * Steps 4-9 for one window w[0..N-1] of the analytic signal. omega_ref is the carrier
- * phase step removed from the angle (2 pi f0 when the window runs along the carrier,
- * else 0). Writes the derivative wrap(arg z - omega_ref) (Sec. 3, Eq. 15) and returns the
- * status. Optional outputs (may be NULL): u1 (L), q (2L-1), roots (2L-2), zsel (1).
+ * Step 5 with model order one (Sec. 3, Eq. 9-11): the unit-norm eigenvector u of the
+ * largest eigenvalue of the Hermitian L x L matrix R spans the signal subspace. Returns
+ * ORC_OK, ORC_NOT_CONVERGED (the Jacobi sweeps did not settle) or ORC_DEGENERATE (R = 0,
+ * or lambda1 - lambda2 <= 1e-12 lambda1: no unique signal subspace).
  * ------------------------------------------------------------------------------- */
-int orc_window_derivative(const cplx* w, int32_t N, int32_t L, int32_t fb, double omega_ref,
-                          double* deriv, cplx* u1_out, cplx* q_out, cplx* roots_out,
-                          int32_t* nroots_out, cplx* zsel_out) {
-    cplx R[ORC_MAXL * ORC_MAXL], V[ORC_MAXL * ORC_MAXL], u[ORC_MAXL], q[2 * ORC_MAXL];
-    cplx roots[2 * ORC_MAXL];
+static int orc_principal_vector(const cplx* R, int32_t L, cplx* u) {
+    cplx V[ORC_MAXL * ORC_MAXL];
     double ev[ORC_MAXL];
-    *deriv = NAN;
-    if (L < 2 || L > ORC_MAXL || N < L) return ORC_DEGENERATE;
-    orc_covariance(w, N, L, fb, R);
     double normR = 0.0;
     for (int32_t i = 0; i < L * L; ++i) normR += creal(R[i] * conj(R[i]));
     if (!(normR > 0.0)) return ORC_DEGENERATE;
@@ -466,6 +477,25 @@ int orc_window_derivative(const cplx* w, int32_t N, int32_t L, int32_t fb, doubl
     for (int32_t m = 0; m < L; ++m) nu += creal(V[m * L + j1] * conj(V[m * L + j1]));
     nu = sqrt(nu);
     for (int32_t m = 0; m < L; ++m) u[m] = V[m * L + j1] / nu;
+    return status;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Steps 4-9 for one window w[0..N-1] of the analytic signal. omega_ref is the carrier
+ * phase step removed from the angle (2 pi f0 when the window runs along the carrier,
+ * else 0). Writes the derivative wrap(arg z - omega_ref) (Sec. 3, Eq. 15) and returns the
+ * status. Optional outputs (may be NULL): u1 (L), q (2L-1), roots (2L-2), zsel (1).
+ * ------------------------------------------------------------------------------- */
+int orc_window_derivative(const cplx* w, int32_t N, int32_t L, int32_t fb, double omega_ref,
+                          double* deriv, cplx* u1_out, cplx* q_out, cplx* roots_out,
+                          int32_t* nroots_out, cplx* zsel_out) {
+    cplx R[ORC_MAXL * ORC_MAXL], u[ORC_MAXL], q[2 * ORC_MAXL];
+    cplx roots[2 * ORC_MAXL];
+    *deriv = NAN;
+    if (L < 2 || L > ORC_MAXL || N < L) return ORC_DEGENERATE;
+    orc_covariance(w, N, L, fb, R);
+    int status = orc_principal_vector(R, L, u);
+    if (status == ORC_DEGENERATE) return ORC_DEGENERATE;
     orc_music_poly(u, L, q);
     int32_t nc = 0;
     int32_t nr = orc_poly_roots(q, 2 * L - 2, roots, &nc);
@@ -603,6 +633,42 @@ int orc_demodulate(const void* frame, int32_t dtype, int32_t H, int32_t W, const
     return used;
 }
 
+/* Step 2 for the carrier lines marked in need[] only (the other lines of gamma are left
+   untouched); a complex frame is copied whole. Returns the OpenMP thread count used. */
+static int orc_gamma_lines(const void* frame, int32_t dtype, int32_t H, int32_t W, int32_t ca,
+                           double f0, double B, const uint8_t* need, double* gamma) {
+    if (dtype == ORC_C64 || dtype == ORC_C128) {
+        orc_analytic_frame(frame, dtype, H, W, ca, f0, B, gamma);
+        return 1;
+    }
+    int32_t nlines = ca == 0 ? H : W;
+    int32_t len = ca == 0 ? W : H;
+    int used = 1;
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t li = 0; li < nlines; ++li) {
+#ifdef _OPENMP
+        if (li == 0) used = omp_get_num_threads();
+#endif
+        if (!need[li]) continue;
+        double* v = (double*)malloc(sizeof(double) * (size_t)len);
+        double* g = (double*)malloc(sizeof(double) * 2 * (size_t)len);
+        if (!v || !g) { free(v); free(g); continue; }
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = ca == 0 ? (size_t)li * W + n : (size_t)n * W + li;
+            v[n] = orc_sample(frame, dtype, idx);
+        }
+        orc_analytic_line(v, len, f0, B, g);
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = ca == 0 ? (size_t)li * W + n : (size_t)n * W + li;
+            gamma[2 * idx] = g[2 * n];
+            gamma[2 * idx + 1] = g[2 * n + 1];
+        }
+        free(v);
+        free(g);
+    }
+    return used;
+}
+
 /* Sampled demodulation: only the listed pixels (ys[i], xs[i]) are computed. Only the
    lines the samples need are band-passed. Returns the thread count used, or < 0. */
 int orc_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, int32_t W,
@@ -616,7 +682,6 @@ int orc_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, int32_t W
 #endif
     int32_t ca = p->carrier_axis;
     int32_t nlines = ca == 0 ? H : W;
-    int32_t len = ca == 0 ? W : H;
     double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
     /* mark the carrier lines every sample's window touches */
     uint8_t* need = (uint8_t*)calloc((size_t)nlines, 1);
@@ -635,34 +700,215 @@ int orc_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, int32_t W
             if (li >= 0 && li < nlines) need[li] = 1;
         }
     }
-    int used = 1;
-#pragma omp parallel for schedule(dynamic)
-    for (int32_t li = 0; li < nlines; ++li) {
-#ifdef _OPENMP
-        if (li == 0) used = omp_get_num_threads();
-#endif
-        if (!need[li]) continue;
-        double* v = (double*)malloc(sizeof(double) * (size_t)len);
-        double* g = (double*)malloc(sizeof(double) * 2 * (size_t)len);
-        if (!v || !g) { free(v); free(g); continue; }
-        for (int32_t n = 0; n < len; ++n) {
-            size_t idx = ca == 0 ? (size_t)li * W + n : (size_t)n * W + li;
-            v[n] = orc_sample(frame, dtype, idx);
-        }
-        orc_analytic_line(v, len, p->carrier_freq, B, g);
-        for (int32_t n = 0; n < len; ++n) {
-            size_t idx = ca == 0 ? (size_t)li * W + n : (size_t)n * W + li;
-            gamma[2 * idx] = g[2 * n];
-            gamma[2 * idx + 1] = g[2 * n + 1];
-        }
-        free(v);
-        free(g);
-    }
+    int used = orc_gamma_lines(frame, dtype, H, W, ca, p->carrier_freq, B, need, gamma);
 #pragma omp parallel for schedule(dynamic)
     for (int32_t i = 0; i < npix; ++i) {
         double d;
         int st = orc_pixel(gamma, H, W, p, ys[i], xs[i], &d);
         out[i] = d;
+        if (status) status[i] = (uint8_t)st;
+    }
+    free(need);
+    free(gamma);
+    return used;
+}
+
+/* =================================================================================
+ * The paper's own geometry (Sec. 3, Eq. 4-15; Algorithm 1): a square block Gamma_w of
+ * M x M samples, M = 2 Lp + 1, centred on the pixel. Its columns are the snapshots of
+ * the y analysis and its conjugated rows those of the x analysis; both angles and the
+ * local phase alpha come out of one block.
+ * ================================================================================= */
+
+/* ---------------------------------------------------------------------------------
+ * One block G (row-major M x M; row r is the y offset r - Lp, column c the x offset
+ * c - Lp). Following Sec. 3:
+ *   R_y = (1/M) G G^H       (Eq. 4-5: E{Gamma_w Gamma_w^H}, columns as snapshots),
+ *   R_x = (1/M) G^H G       (the x analysis: E{Gamma_w^H Gamma_w}, conjugated rows),
+ *   u1, v1 = principal unit eigenvectors of R_y, R_x         (Eq. 9-11; the paper takes
+ *            them from the SVD of Gamma_w, which gives the same vectors),
+ *   Q_y, Q_x = root-MUSIC polynomials of u1, v1 (Eq. 12, Eq. 13; the construction of
+ *            step 6 with L = M), all roots, and the root closest to the unit circle of
+ *            magnitude below one (Algorithm 1),
+ *   omega_y = arg z_y,  omega_x = -arg z_x                   (Eq. 15, rows 1-2),
+ *   alpha   = angle of the block mean of G[r][c] exp(-j(omega_x (c-Lp) + omega_y (r-Lp)))
+ *                                                            (Eq. 15, row 3).
+ * ref_x and ref_y are the angles expected without modulation (the carrier's 2 pi f0 on
+ * its axis, else 0); they only break exact ties in the selection (z_x is compared with
+ * -ref_x). Outputs are the raw angles, carrier included. Optional outputs (may be NULL):
+ * u1, v1 (M each), zx, zy (1 each).
+ * ------------------------------------------------------------------------------- */
+int orc_square_window(const cplx* G, int32_t Lp, double ref_x, double ref_y, double* wx,
+                      double* wy, double* alpha, cplx* u1_out, cplx* v1_out, cplx* zx_out,
+                      cplx* zy_out) {
+    int32_t M = 2 * Lp + 1;
+    *wx = NAN;
+    *wy = NAN;
+    *alpha = NAN;
+    if (Lp < 1 || M > ORC_MAXL) return ORC_DEGENERATE;
+    cplx Ry[ORC_MAXL * ORC_MAXL], Rx[ORC_MAXL * ORC_MAXL], u[ORC_MAXL], v[ORC_MAXL];
+    cplx qy[2 * ORC_MAXL], qx[2 * ORC_MAXL], ry[2 * ORC_MAXL], rx[2 * ORC_MAXL];
+    for (int32_t m = 0; m < M; ++m)
+        for (int32_t l = 0; l < M; ++l) {
+            cplx acc = 0.0;
+            for (int32_t c = 0; c < M; ++c) acc += G[m * M + c] * conj(G[l * M + c]);
+            Ry[m * M + l] = acc / (double)M;
+        }
+    for (int32_t a = 0; a < M; ++a)
+        for (int32_t b = 0; b < M; ++b) {
+            cplx acc = 0.0;
+            for (int32_t r = 0; r < M; ++r) acc += conj(G[r * M + a]) * G[r * M + b];
+            Rx[a * M + b] = acc / (double)M;
+        }
+    int sy = orc_principal_vector(Ry, M, u);
+    int sx = orc_principal_vector(Rx, M, v);
+    if (sy == ORC_DEGENERATE || sx == ORC_DEGENERATE) return ORC_DEGENERATE;
+    int status = (sy != ORC_OK || sx != ORC_OK) ? ORC_NOT_CONVERGED : ORC_OK;
+    orc_music_poly(u, M, qy);
+    orc_music_poly(v, M, qx);
+    int32_t ncy = 0, ncx = 0;
+    int32_t nry = orc_poly_roots(qy, 2 * M - 2, ry, &ncy);
+    int32_t nrx = orc_poly_roots(qx, 2 * M - 2, rx, &ncx);
+    if (ncy || ncx) status = ORC_NOT_CONVERGED;
+    cplx zy, zx;
+    if (orc_select_root(qy, 2 * M - 2, ry, nry, ref_y, &zy) != 0) return ORC_DEGENERATE;
+    if (orc_select_root(qx, 2 * M - 2, rx, nrx, -ref_x, &zx) != 0) return ORC_DEGENERATE;
+    double oy = carg(zy);
+    double ox = -carg(zx);
+    cplx acc = 0.0;
+    for (int32_t r = 0; r < M; ++r)
+        for (int32_t c = 0; c < M; ++c)
+            acc += G[r * M + c] * cexp(-I * (ox * (double)(c - Lp) + oy * (double)(r - Lp)));
+    acc /= (double)(M * M);
+    *wx = ox;
+    *wy = oy;
+    *alpha = carg(acc);
+    if (u1_out) memcpy(u1_out, u, sizeof(cplx) * (size_t)M);
+    if (v1_out) memcpy(v1_out, v, sizeof(cplx) * (size_t)M);
+    if (zx_out) *zx_out = zx;
+    if (zy_out) *zy_out = zy;
+    return status;
+}
+
+/* ctypes-friendly form of orc_square_window: complex arrays interleaved (re, im);
+   out3 receives (omega_x, omega_y, alpha), u1/v1 M entries, z2 (zx, zy). */
+int orc_square_window_ri(const double* G_ri, int32_t Lp, double ref_x, double ref_y,
+                         double* out3, double* u1_ri, double* v1_ri, double* z2_ri) {
+    int32_t M = 2 * Lp + 1;
+    if (Lp < 1 || M > ORC_MAXL) return ORC_DEGENERATE;
+    cplx G[ORC_MAXL * ORC_MAXL], u[ORC_MAXL], v[ORC_MAXL], zx = 0.0, zy = 0.0;
+    for (int32_t i = 0; i < M * M; ++i) G[i] = G_ri[2 * i] + I * G_ri[2 * i + 1];
+    int st = orc_square_window(G, Lp, ref_x, ref_y, &out3[0], &out3[1], &out3[2], u, v, &zx, &zy);
+    for (int32_t i = 0; i < M; ++i) {
+        u1_ri[2 * i] = creal(u[i]);
+        u1_ri[2 * i + 1] = cimag(u[i]);
+        v1_ri[2 * i] = creal(v[i]);
+        v1_ri[2 * i + 1] = cimag(v[i]);
+    }
+    z2_ri[0] = creal(zx);
+    z2_ri[1] = cimag(zx);
+    z2_ri[2] = creal(zy);
+    z2_ri[3] = cimag(zy);
+    return st;
+}
+
+/* ---------------------------------------------------------------------------------
+ * One pixel of the paper geometry on a frame's analytic signal gamma (H*W interleaved
+ * complex, row-major). The block covers rows y-Lp..y+Lp and columns x-Lp..x+Lp; a pixel
+ * whose block leaves the frame is a border pixel (Sec. 4). The carrier is removed after
+ * the angles (a modulation exp(j 2 pi f0 X) along the carrier axis X adds 2 pi f0 to that
+ * axis' angle and 2 pi f0 X to alpha, exactly): dx, dy are the local phase derivatives
+ * and alpha the local phase with the carrier's phase 2 pi f0 X at the pixel subtracted,
+ * all wrapped to (-pi, pi].
+ * ------------------------------------------------------------------------------- */
+static int orc_square_pixel(const double* gamma, int32_t H, int32_t W, const orc_params* p,
+                            int32_t Lp, int32_t y, int32_t x, double* dx, double* dy,
+                            double* alpha) {
+    int32_t M = 2 * Lp + 1;
+    *dx = NAN;
+    *dy = NAN;
+    *alpha = NAN;
+    if (y - Lp < 0 || y + Lp > H - 1 || x - Lp < 0 || x + Lp > W - 1) return ORC_BORDER;
+    if (p->model_order != 1 || Lp < 1 || M > ORC_MAXL) return ORC_DEGENERATE;
+    cplx G[ORC_MAXL * ORC_MAXL];
+    for (int32_t r = 0; r < M; ++r)
+        for (int32_t c = 0; c < M; ++c) {
+            size_t idx = (size_t)(y - Lp + r) * W + (size_t)(x - Lp + c);
+            G[r * M + c] = gamma[2 * idx] + I * gamma[2 * idx + 1];
+        }
+    double w0 = 2.0 * ORC_PI * p->carrier_freq;
+    double ref_x = p->carrier_axis == 0 ? w0 : 0.0;
+    double ref_y = p->carrier_axis == 1 ? w0 : 0.0;
+    double wx, wy, a;
+    int st = orc_square_window(G, Lp, ref_x, ref_y, &wx, &wy, &a, NULL, NULL, NULL, NULL);
+    if (st == ORC_DEGENERATE) return st;
+    *dx = orc_wrap(wx - ref_x);
+    *dy = orc_wrap(wy - ref_y);
+    /* carrier phase at the pixel: 2 pi times the fractional part of f0 X */
+    double t = p->carrier_freq * (double)(p->carrier_axis == 0 ? x : y);
+    t -= floor(t);
+    *alpha = orc_wrap(a - 2.0 * ORC_PI * t);
+    return st;
+}
+
+/* Whole-frame paper geometry: maps dx, dy, alpha (H*W each, NaN where undefined) and
+   status (may be NULL). Returns the OpenMP thread count used, or < 0 on error. */
+int orc_square_demodulate(const void* frame, int32_t dtype, int32_t H, int32_t W,
+                          const orc_params* p, int32_t Lp, double* dx, double* dy,
+                          double* alpha, uint8_t* status, int32_t nthreads) {
+    if (H <= 0 || W <= 0 || Lp < 1 || 2 * Lp + 1 > ORC_MAXL) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    double* gamma = (double*)malloc(sizeof(double) * 2 * (size_t)H * W);
+    if (!gamma) return -2;
+    double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
+    int err = orc_analytic_frame(frame, dtype, H, W, p->carrier_axis, p->carrier_freq, B, gamma);
+    if (err) { free(gamma); return err; }
+    int used = 1;
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t y = 0; y < H; ++y) {
+#ifdef _OPENMP
+        if (y == 0) used = omp_get_num_threads();
+#endif
+        for (int32_t x = 0; x < W; ++x) {
+            size_t i = (size_t)y * W + x;
+            int st = orc_square_pixel(gamma, H, W, p, Lp, y, x, &dx[i], &dy[i], &alpha[i]);
+            if (status) status[i] = (uint8_t)st;
+        }
+    }
+    free(gamma);
+    return used;
+}
+
+/* Sampled paper geometry: only the pixels (ys[i], xs[i]); only the carrier lines their
+   blocks cross are band-passed. Returns the thread count used, or < 0. */
+int orc_square_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, int32_t W,
+                                 const orc_params* p, int32_t Lp, int32_t npix,
+                                 const int32_t* ys, const int32_t* xs, double* dx, double* dy,
+                                 double* alpha, uint8_t* status, int32_t nthreads) {
+    if (H <= 0 || W <= 0 || Lp < 1 || 2 * Lp + 1 > ORC_MAXL) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    int32_t ca = p->carrier_axis;
+    int32_t nlines = ca == 0 ? H : W;
+    double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
+    uint8_t* need = (uint8_t*)calloc((size_t)nlines, 1);
+    double* gamma = (double*)calloc(2 * (size_t)H * W, sizeof(double));
+    if (!need || !gamma) { free(need); free(gamma); return -2; }
+    for (int32_t i = 0; i < npix; ++i) {
+        int32_t y = ys[i], x = xs[i];
+        if (y < 0 || y >= H || x < 0 || x >= W) { free(need); free(gamma); return -1; }
+        for (int32_t k = -Lp; k <= Lp; ++k) {
+            int32_t li = (ca == 0 ? y : x) + k;
+            if (li >= 0 && li < nlines) need[li] = 1;
+        }
+    }
+    int used = orc_gamma_lines(frame, dtype, H, W, ca, p->carrier_freq, B, need, gamma);
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t i = 0; i < npix; ++i) {
+        int st = orc_square_pixel(gamma, H, W, p, Lp, ys[i], xs[i], &dx[i], &dy[i], &alpha[i]);
         if (status) status[i] = (uint8_t)st;
     }
     free(need);

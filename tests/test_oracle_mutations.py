@@ -1,12 +1,13 @@
 """Planted mistakes: each test copies the oracle's C source, plants one plausible error (a dropped
 conjugate, a transposed operand, a wrong index or sign), compiles the copy on the CPU and checks
-that the pins in test_oracle_pins.py reject it. This shows the pins constrain every step of the
+that the pins in test_oracle_pins.py and test_oracle_square.py reject it. This shows the pins constrain every step of the
 oracle rather than only re-running it."""
 import numpy as np
 import pytest
 
 import oracle as O
 import test_oracle_pins as P
+import test_oracle_square as S
 
 MUTATIONS = {
     "band: negative side kept": ("fabs((double)k / (double)W - f0) < B", "fabs((double)k / (double)W + f0) < B"),
@@ -28,6 +29,21 @@ MUTATIONS = {
     "angle: carrier added": ("*deriv = orc_wrap(carg(z) - omega_ref);", "*deriv = orc_wrap(carg(z) + omega_ref);"),
     "window: off by one": ("int32_t start = n - N / 2;", "int32_t start = n - N / 2 + 1;"),
     "eig: smallest eigenvector": ("if (ev[j] > ev[j1]) j1 = j;", "if (ev[j] < ev[j1]) j1 = j;"),
+    # the square block of the paper's geometry
+    "square: R_y operands transposed": ("acc += G[m * M + c] * conj(G[l * M + c]);",
+                                        "acc += conj(G[m * M + c]) * G[l * M + c];"),
+    "square: R_x rows not conjugated": ("acc += conj(G[r * M + a]) * G[r * M + b];",
+                                        "acc += G[r * M + a] * conj(G[r * M + b]);"),
+    "square: x angle sign": ("double ox = -carg(zx);", "double ox = carg(zx);"),
+    "square: u1 used for both axes": ("orc_music_poly(v, M, qx);", "orc_music_poly(u, M, qx);"),
+    "square: alpha coordinates not centred": ("acc += G[r * M + c] * cexp(-I * (ox * (double)(c - Lp) + oy * (double)(r - Lp)));",
+                                              "acc += G[r * M + c] * cexp(-I * (ox * (double)c + oy * (double)r));"),
+    "square: alpha demodulation sign": ("acc += G[r * M + c] * cexp(-I * (ox", "acc += G[r * M + c] * cexp(I * (ox"),
+    "square: carrier left in alpha": ("*alpha = orc_wrap(a - 2.0 * ORC_PI * t);", "*alpha = orc_wrap(a);"),
+    "square: block read transposed": ("size_t idx = (size_t)(y - Lp + r) * W + (size_t)(x - Lp + c);",
+                                      "size_t idx = (size_t)(y - Lp + c) * W + (size_t)(x - Lp + r);"),
+    "square: carrier taken from the wrong axis": ("double t = p->carrier_freq * (double)(p->carrier_axis == 0 ? x : y);",
+                                                  "double t = p->carrier_freq * (double)(p->carrier_axis == 0 ? y : x);"),
 }
 
 PINS = [
@@ -46,10 +62,16 @@ PINS = [
     lambda: P.test_p2_order_two_is_pulse_pair(1),
     P.test_p4_carrier_rotation,
     P.test_p7_noisy_selection_by_enumeration,
+    lambda: S.test_square_plane_wave_exact(3),
+    lambda: S.test_square_real_fringe_with_carrier_exact(0),
+    lambda: S.test_square_real_fringe_with_carrier_exact(1),
+    lambda: S.test_square_eigenvectors_are_singular_vectors(3),
+    lambda: S.test_square_angles_by_enumeration(2),
+    S.test_square_alpha_is_least_squares_phase,
 ]
 
 
-def _failing_pins():
+def _failing_pins(first_only=False):
     failed = []
     for i, pin in enumerate(PINS):
         try:
@@ -57,6 +79,8 @@ def _failing_pins():
                 pin()
         except Exception:  # an AssertionError, or a crash of the mutated code path
             failed.append(i)
+            if first_only:
+                break
     return failed
 
 
@@ -67,7 +91,7 @@ def test_planted_mistake_is_caught(name, tmp_path):
     assert src.count(old) >= 1, f"mutation anchor not found: {old}"
     path = O.compile_variant(src.replace(old, new), str(tmp_path / "liboracle_mut.so"))
     with O.use_library(path):
-        failed = _failing_pins()
+        failed = _failing_pins(first_only=True)
     assert failed, f"no pin rejects the planted mistake '{name}'"
 
 
