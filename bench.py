@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-rows", type=int, default=16, help="rows per frame in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--square-steps", type=int, default=5,
+                    help="timed steps of the paper-geometry leg (square block, both derivatives and alpha)")
     return ap.parse_args()
 
 
@@ -61,9 +63,32 @@ def frames_for(rank: int):
     return [synth.peaks_frame(s, F0, H, W, stream=rank) for s in SNRS]
 
 
-def flops_per_pixel(L: int, N: int, sweeps: float, iters: float, updates: float) -> float:
+# The paper's own geometry and simulation setting (Sec. 3-4): a (2 Lp + 1)^2 block per pixel, Lp = 5,
+# on a complex fringe at 0 dB; both derivatives and the local phase alpha per pixel.
+SQ_LP, SQ_SNR, SQ_FRAMES = 5, 0.0, 4
+SQ_WORKLOAD = (f"paper geometry: {SQ_FRAMES} x {H}x{W} complex64 fringes per step (peaks phase 0-10 rad, "
+               f"SNR {SQ_SNR:g} dB), square block Lp={SQ_LP} (11x11), d/dx, d/dy and alpha per pixel")
+# Table 2 of the paper (context only: other hardware, the full method including unwrapping)
+PAPER_TABLE2_1024 = {"gpu": "Quadro M5000 (Maxwell, 16 SMs), FP32", "seconds_per_1024x1024_frame": 13.88,
+                     "mpixel_per_s": 1024 * 1024 / 13.88 / 1e6}
+
+
+def square_frames(rank: int):
+    return [synth.complex_fringe_frame(SQ_SNR, H, W, 10.0, stream=100 * rank + i) for i in range(SQ_FRAMES)]
+
+
+def aberth_flops(L: int, evals: float, updates: float) -> float:
+    """Flops of the root stage (shared by both solvers) for one polynomial of half-size L, given the
+    measured evaluations of Q and Q' and executed root updates: per evaluation Horner over 2L - 2
+    steps (two complex multiply-adds, 16) and the residual test (4); per update Q/Q' (11), the
+    2(L-1) - 1 reciprocal terms of the Aberth sum (10 each), the correction (21) and the mirror (8)."""
+    NR, NI = 2 * L - 2, L - 1
+    return evals * (16 * NR + 4) + updates * (11 + 10 * (2 * NI - 1) + 21 + 8)
+
+
+def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float) -> float:
     """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1),
-    counted from the kernel's steps with the measured sweeps, root iterations and executed root
+    counted from the kernel's steps with the measured sweeps, root evaluations and executed root
     updates per 32-pixel work item:
       covariance  per lag: (31 + N) / 32 lag products (6) and prefix adds (2) per pixel, a 5-step
                   warp scan (10); per R_f entry: box difference (2) and accumulation into S (6)
@@ -71,9 +96,7 @@ def flops_per_pixel(L: int, N: int, sweeps: float, iters: float, updates: float)
                   plus the off-diagonal norm L (L - 1)
       inverse it. L D L^T of (mu I - S), two forward / diagonal / backward solves with norms
       polynomial  u = Q x (2 L), rho_k (8 flops per term), scaling and moduli
-      Aberth      per iteration and inner root: Horner of Q, Q' and the bound over 2L - 2 steps
-                  (18 per step) and the residual test (6); per executed update: Q/Q' (11), the
-                  2(L-1) - 1 reciprocal terms (10 each), the correction (12) and the mirror (8)
+      Aberth      aberth_flops: per executed evaluation of Q, Q' and per executed root update
       polish      two Horner passes of Q, Q', Q'' (24 per step) and the step (20), angle (20)
     """
     NS = L * (L + 1) // 2
@@ -85,10 +108,32 @@ def flops_per_pixel(L: int, N: int, sweeps: float, iters: float, updates: float)
     ldl = sum(3 * j + 1 + (L - 1 - j) * (3 * j + 1) for j in range(L))
     inv = ldl + 2 * (2 * L * (L - 1) + 4 * L)
     coef = 2 * L + 3 * L + 4 * L * (L - 1) + 5 * (L - 1)
-    per_update = 11 + 10 * (2 * NI - 1) + 12 + 8
-    aberth = iters * NI * (18 * NR + 6) + updates * per_update
-    polish = 2 * (24 * NR + 20) + 20
+    aberth = aberth_flops(L, evals, updates) + NI * 10 + 20  # plus the starting points
+    polish = 2 * (24 * NR + 20) + 20 + 13 * NI  # plus the selection
     return cov + jac + inv + coef + aberth + polish
+
+
+def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: float) -> float:
+    """Algorithmic FP32 flops per pixel of the square-block solver (block side M = 2 Lp + 1), from
+    its steps with the measured power-iteration steps, root evaluations and root updates (the root
+    figures add both polynomials):
+      power it.   per step G^H u and G y (M^2 complex multiply-adds each, 8 flops), the norm (3 M),
+                  normalisation and step size (8 M); the start vector (5 M)
+      polynomials per axis: |u|^2 (3 M), M (M - 1) / 2 lag products (8), scaling and moduli (8 per lag)
+      Aberth      aberth_flops, plus the starting points (10 per root + 20) per axis
+      select      per axis: moduli and nearest-neighbour search (13 per root), two polish steps
+                  (24 per Horner step of degree 2M - 2, plus 20), angle (20)
+      alpha       four sincos (80), the recurrences (6 M), M^2 complex multiply-adds, M row terms
+                  (16 M), angle and carrier phase (25)
+    """
+    M = 2 * Lp + 1
+    NI, NR = M - 1, 2 * M - 2
+    power = 5 * M + power_its * (16 * M * M + 11 * M)
+    coefs = 2 * (3 * M + 4 * M * (M - 1) + 8 * (M - 1))
+    roots = aberth_flops(M, evals, updates) + 2 * (10 * NI + 20)
+    select = 2 * (13 * NI + 2 * (24 * NR + 20) + 20)
+    alpha = 80 + 6 * M + 8 * M * M + 16 * M + 25
+    return power + coefs + roots + select + alpha
 
 
 SOLVER_PROFILE = os.path.join(ROOT, "profiles", "batched_solver_L8_peaks4x1024.md")
@@ -274,7 +319,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    solver_ms, bandpass_ms, launches, sweeps, iters, updates = [], [], 0, [], [], []
+    solver_ms, bandpass_ms, launches, sweeps, iters, updates, evals = [], [], 0, [], [], [], []
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -287,6 +332,7 @@ def run_ours(args):
         sweeps.append(st.mean_sweeps)
         iters.append(st.mean_root_iters)
         updates.append(st.mean_root_updates)
+        evals.append(st.mean_root_evals)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -333,7 +379,7 @@ def run_ours(args):
     e2e_value = npx * world / (e2e_ms * 1e3)
 
     # ---- roofline of the dominant kernel (batched solver) ---------------------------------------
-    fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(iters), statistics.mean(updates))
+    fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(evals), statistics.mean(updates))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
     traffic = profiled_traffic()
@@ -342,9 +388,11 @@ def run_ours(args):
                 "kernel": "batched_kernel<8>", "flops_per_pixel": fpp, "launch_ms": solver_avg,
                 "peak_note": "FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "mean_jacobi_sweeps": statistics.mean(sweeps), "mean_root_iters": statistics.mean(iters),
-                "mean_root_updates": statistics.mean(updates),
+                "mean_root_updates": statistics.mean(updates), "mean_root_evals": statistics.mean(evals),
                 "solver_ctas_per_sm": st.solver_ctas_per_sm,
                 "bandpass_ms": statistics.mean(bandpass_ms)}
+
+    sq = run_square_leg(args, rank, world, dev, stream, flush) if args.square_steps > 0 else None
 
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
@@ -359,6 +407,8 @@ def run_ours(args):
             "plain": {"value": plain_value, "unit": "Mpixel/s", "ms_per_step": plain_ms,
                       "path": "plain FP32, thread per pixel, one launch per frame"},
             "speedup_vs_plain": value / plain_value}
+    if sq is not None:
+        line["paper_geometry"] = sq
 
     # ---- CPU oracle on a bounded sample, and the GPU error against it -----------------------
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -381,6 +431,71 @@ def run_ours(args):
     dem.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_square_leg(args, rank, world, dev, stream, flush):
+    """The paper's square-block geometry on its simulation setting, timed like the main leg
+    (graph replay, L2 flushed between steps, CUDA events); reported beside the main line."""
+    import torch
+
+    from paper_1910_11872_gb300 import rmusic
+
+    frames = square_frames(rank)
+    host = np.stack([f.image for f in frames])
+    x = torch.from_numpy(host).to(dev)
+    npx = host.shape[0] * host.shape[1] * host.shape[2]
+    out = torch.empty(3 * npx, dtype=torch.float32, device=dev)
+    dem = rmusic.Demodulator(device=dev.index, geometry="square", half_width=SQ_LP, carrier_freq=0.0,
+                             precision="batched", use_graph=1, timing=1, autotune=1)
+    for _ in range(args.warmup):
+        dem.run(x, out=out, with_status=False)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.square_steps)]
+    solver_ms, its, evals, updates, launches = [], [], [], [], 0
+    for k in range(args.square_steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        dem.run(x, out=out, with_status=False, stream=stream)
+        ev[k][1].record(stream)
+        st = dem.stats()
+        solver_ms.append(st.solver_ms)
+        its.append(st.mean_sweeps)
+        evals.append(st.mean_root_evals)
+        updates.append(st.mean_root_updates)
+        launches += st.kernel_launches
+    torch.cuda.synchronize()
+    step_ms = max_over_ranks(world, statistics.mean(a.elapsed_time(b) for a, b in ev))
+    value = npx * world / (step_ms * 1e3)
+    fpp = square_flops_per_pixel(SQ_LP, statistics.mean(its), statistics.mean(evals), statistics.mean(updates))
+    solver_avg = statistics.mean(solver_ms)
+    achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
+    res = {"workload": SQ_WORKLOAD, "value": value, "unit": "Mpixel/s", "ms_per_step": step_ms,
+           "steps": args.square_steps, "gpu_launches": launches,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                        "kernel": f"square_kernel<{SQ_LP}, {st.solver_ctas_per_sm}>", "flops_per_pixel": fpp,
+                        "launch_ms": solver_avg, "mean_power_iters": statistics.mean(its),
+                        "mean_root_evals": statistics.mean(evals), "mean_root_updates": statistics.mean(updates)},
+           "paper_table2_context": PAPER_TABLE2_1024}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+
+        maps = out.view(len(frames), 3, H, W).cpu().numpy()
+        rng = np.random.default_rng(5)
+        worst = {"dx": 0.0, "dy": 0.0, "alpha": 0.0}
+        for f, m in zip(frames, maps):
+            ys, xs = rng.integers(0, H, 256), rng.integers(0, W, 256)
+            odx, ody, oal, ost, _ = O.square_demodulate_pixels(f.image, O.make_params(carrier_freq=0.0), SQ_LP, ys, xs)
+            ok = ost == 0
+            for key, g, o in (("dx", m[0], odx), ("dy", m[1], ody), ("alpha", m[2], oal)):
+                d = np.abs((g[ys, xs][ok] - o[ok] + np.pi) % (2 * np.pi) - np.pi)
+                worst[key] = max(worst[key], float(d.max()))
+        res["max_abs_vs_fp64_oracle"] = worst
+        res["oracle_sample"] = f"256 random pixels of each frame ({256 * len(frames)} px)"
+    dem.close()
+    return res
 
 
 def main():

@@ -12,6 +12,10 @@
  *   - root-MUSIC polynomial of the noise projector                 (Sec. 3, Eq. 12-14)
  *   - the root nearest the unit circle with |z| <= 1               (Sec. 3; Algorithm 1)
  *   - its angle, minus the carrier, is the phase derivative        (Sec. 3, Eq. 15)
+ * Two window geometries: a window of N samples along one axis with Hankel snapshots (the
+ * workloads' row windows), and the paper's own square block of (2 Lp + 1) x (2 Lp + 1) samples
+ * whose columns and conjugated rows are the snapshots, giving both derivatives and the local
+ * phase alpha of Eq. 15 at once (Sec. 3, Eq. 4-15; Algorithm 1).
  *
  * Conventions shared by every entry point:
  *   - All functions are plain C, callable from any language; no C++ exceptions cross them.
@@ -53,6 +57,12 @@ extern "C" {
 /* ---- input sample types (rmusic_frame_desc.dtype) -------------------------------------- */
 #define RMUSIC_DTYPE_F32 0 /* float32 intensity                                             */
 #define RMUSIC_DTYPE_U16 1 /* uint16 camera code (e.g. 12-bit); any scale gives the same map */
+#define RMUSIC_DTYPE_C64 2 /* complex64 (re, im float32): already the analytic signal Gamma,  */
+                           /* used as is without the band-pass (the paper's complex fringe)  */
+
+/* ---- window geometries (rmusic_params.geometry) ---------------------------------------- */
+#define RMUSIC_GEOM_ROW 0    /* N samples along deriv_axis, snapshots of length L           */
+#define RMUSIC_GEOM_SQUARE 1 /* the paper's (2 Lp + 1)^2 block: d/dx, d/dy and alpha        */
 
 /* ---- per-pixel status codes (optional uint8 map) --------------------------------------- */
 #define RMUSIC_STATUS_OK 0
@@ -85,6 +95,13 @@ extern "C" {
  *   autotune         batched path: 1 lets the first call that meets a covariance order with no
  *                    tuned solver variant on this device time all variants on its own work and
  *                    keep the fastest (that call synchronises its stream). See rmusic_autotune.
+ *   geometry         RMUSIC_GEOM_ROW (0) or RMUSIC_GEOM_SQUARE (1). The square block needs
+ *                    precision RMUSIC_FP32_BATCHED; window_len, cov_order, forward_backward and
+ *                    deriv_axis are then ignored (the paper's estimate has no FB average).
+ *   half_width       square geometry: Lp, the block is (2 Lp + 1) x (2 Lp + 1) (1 <= Lp <= 8).
+ *                    A pixel whose block leaves the frame is a border pixel. max_sweeps then caps
+ *                    the power-iteration steps of the block's singular vectors (0 = 100).
+ * carrier_freq may be 0 (no carrier) for complex frames; for real frames it must lie in (0, 0.5).
  */
 typedef struct {
     int32_t window_len;
@@ -102,16 +119,21 @@ typedef struct {
     int32_t use_graph;
     int32_t timing;
     int32_t autotune;
+    int32_t geometry;
+    int32_t half_width;
 } rmusic_params;
 
 /* One frame of a batch. Frames of one call may differ in size, type and window.
  *   offset_bytes  byte offset of the frame's first sample from the base input pointer.
  *   height/width  H, W in pixels (>= 1).
  *   pitch_elems   elements between the starts of consecutive rows (>= width; 0 = width).
- *   dtype         RMUSIC_DTYPE_F32 or RMUSIC_DTYPE_U16. offset_bytes and pitch must keep
- *                 every sample naturally aligned.
+ *   dtype         RMUSIC_DTYPE_F32, RMUSIC_DTYPE_U16 or RMUSIC_DTYPE_C64. offset_bytes and
+ *                 pitch must keep every sample naturally aligned.
  *   out_offset    element offset of the frame's dense H x W float32 map (row-major) in the
- *                 output buffer, and of its H x W uint8 map in the status buffer.
+ *                 output buffer, and of its H x W uint8 map in the status buffer. In the square
+ *                 geometry a frame writes three maps: d/dx at out_offset, d/dy at
+ *                 out_offset + H W and alpha at out_offset + 2 H W (3 H W floats), and its
+ *                 status map at out_offset of the status buffer.
  *   window_len, cov_order  per-frame N and L; 0 = the context's parameters.
  */
 typedef struct {
@@ -139,7 +161,10 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
  *   d_frames  device pointer; frame f starts at (const char*)d_frames + descs[f].offset_bytes.
  *   descs     HOST array of n_frames descriptors; copied by the library before return.
  *   d_out     device float32 buffer; frame f writes H*W values at d_out + descs[f].out_offset:
- *             the phase derivative in rad/pixel along deriv_axis, NaN where undefined.
+ *             the phase derivative in rad/pixel along deriv_axis, NaN where undefined. In the
+ *             square geometry three maps of H*W values: d/dx and d/dy in rad/pixel and the
+ *             local phase alpha in rad, wrapped to (-pi, pi], with the carrier's phase
+ *             2 pi f0 X at the pixel removed (X the pixel's coordinate along carrier_axis).
  *   d_status  device uint8 buffer laid out like d_out, or NULL.
  *   cuda_stream  cudaStream_t (as void*) on which all work is queued.
  * Errors: RMUSIC_EINVAL (NULL pointers with n_frames > 0, a bad descriptor, unsupported
@@ -169,7 +194,7 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
 /* For callers that cannot allocate device memory (an application whose allocator belongs to a
  * host framework or pool, a real-time loop that forbids allocation after start-up, a plug-in
  * whose host accounts for every byte): the FP32-batched path (precision must be
- * RMUSIC_FP32_BATCHED, forward_backward 1) without a context and without any cudaMalloc,
+ * RMUSIC_FP32_BATCHED, forward_backward 1, geometry RMUSIC_GEOM_ROW) without a context and without any cudaMalloc,
  * cudaFree or other allocating call. The paper has no counterpart; this is an interface
  * convenience of this library.
  *   - All device scratch (analytic signal, frame table, work counters) lives in one fixed array
@@ -209,6 +234,10 @@ const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
  *   mean_root_iters  batched path: Aberth iterations per 32-pixel work item, averaged.
  *   mean_root_updates batched path: Aberth root updates a warp executed per work item, averaged
  *                    (roots already converged in every lane of the warp are skipped).
+ *   mean_root_evals  batched path: evaluations of Q and Q' a warp executed per work item, averaged
+ *                    (a root frozen in every lane of the warp is not evaluated).
+ *   In the square geometry a work item is one warp's 32 pixels of a tile row, mean_sweeps counts
+ *   power-iteration steps, and the root figures add both polynomials.
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
  *                    call's stream) of the band-pass launches and of the solver launches.
  *   solver_ctas_per_sm  batched path: resident CTAs per SM of the solver variant last launched.
@@ -221,6 +250,7 @@ typedef struct {
     double mean_sweeps;
     double mean_root_iters;
     double mean_root_updates;
+    double mean_root_evals;
     float bandpass_ms;
     float solver_ms;
     int32_t solver_ctas_per_sm;

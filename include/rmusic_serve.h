@@ -79,7 +79,8 @@ typedef struct {
 } rmusic_serve_stats;
 
 /* Create a server on `device` for the given estimator parameters (precision must be
- * RMUSIC_FP32_BATCHED). Allocates its arenas and starts its worker thread.
+ * RMUSIC_FP32_BATCHED, geometry RMUSIC_GEOM_ROW). Allocates its arenas and starts its worker
+ * thread.
  * Errors: RMUSIC_EINVAL, RMUSIC_EUNSUPPORTED, RMUSIC_ENOMEM, RMUSIC_ECUDA. */
 int rmusic_serve_create(const rmusic_params* params, int device, const rmusic_serve_config* cfg,
                         rmusic_server** out);

@@ -14,7 +14,8 @@
 // steps. All sincos values come from sincospi on arguments in [0, 2). Work per pixel is
 // about 4 nb FMAs each way (nb ~ 100 at len = 1024, f0 = 0.1): a few percent of the solver.
 // T = float feeds the FP32 paths (complex64 output); T = double feeds the plain FP64 path
-// (complex128 output), so that path is double precision end to end.
+// (complex128 output), so that path is double precision end to end. Complex64 frames are the
+// analytic signal already and are only copied into the workspace layout.
 #include "rmusic_device.cuh"
 #include "rmusic_launch.h"
 
@@ -119,12 +120,28 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
     T* v = a1_smem;
     cx<T>* X = reinterpret_cast<cx<T>*>(a1_smem + ((len + 3) & ~3));
 
+    if (F.dtype == kDtC64) {
+        // a complex frame is the analytic signal already (the complex fringe the paper simulates
+        // in Sec. 4): copied into the workspace layout without a band-pass
+        const float2* src = reinterpret_cast<const float2*>(in + F.in_off);
+        for (int n = threadIdx.x; n < len; n += blockDim.x) {
+            const uint64_t idx = F.carrier_axis == 0 ? (uint64_t)li * F.pitch + n : (uint64_t)n * F.pitch + li;
+            const float2 g = src[idx];
+            const int y = F.carrier_axis == 0 ? li : n;
+            const int x = F.carrier_axis == 0 ? n : li;
+            const int wline = F.deriv_axis == 0 ? y : x;
+            const int pos = F.deriv_axis == 0 ? x : y;
+            gam[F.gam_off + (uint64_t)wline * F.wlen + pos] = mkc((T)g.x, (T)g.y);
+        }
+        return;
+    }
+
     // load the line and its sum
     T s = 0;
     for (int n = threadIdx.x; n < len; n += blockDim.x) {
         uint64_t idx = F.carrier_axis == 0 ? (uint64_t)li * F.pitch + n : (uint64_t)n * F.pitch + li;
         T val;
-        if (F.dtype == 0)
+        if (F.dtype == kDtF32)
             val = (T)reinterpret_cast<const float*>(in + F.in_off)[idx];
         else
             val = (T)reinterpret_cast<const uint16_t*>(in + F.in_off)[idx];

@@ -19,21 +19,9 @@
 //             sweep); then three steps of inverse iteration with (mu I - S) = L D L^T, mu just
 //             above that entry, give the signal eigenvector x1 without accumulating rotations
 //             (Eq. 8-11).
-//   poly      u1 = Q x1 / |x1|; c_0 = L - 1, c_k = -(1 - 2e-6) sum_m u1[m] conj(u1[m+k]) / |u1|^2,
-//             c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14). The 2e-6 shrink keeps the
-//             polynomial strictly positive on the circle in FP32 (see below).
-//   roots     Aberth-Ehrlich on the L - 1 roots inside the unit disk; the other L - 1 roots are
-//             their mirrors 1/conj(z) (the coefficients are conjugate-symmetric). Starting
-//             points come from the estimator's structure: the signal root just inside the circle
-//             at the angle of conj(rho_1), the others at radius r = L / (L + 7.3) at the
-//             side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window
-//             puts them. Iterations stop when every root of every lane of the warp has a residual
-//             at the FP32 rounding level (|Q(z)| <= 3e-6 sum |q_i|).
-//   select    the inner root nearest the unit circle (Algorithm 1). A noise-free window gives a
-//             double root on the circle, which FP32 splits by ~sqrt(eps); when another root lies
-//             within 4e-3 the pair is located as the root of Q' between them, otherwise the root
-//             is refined by Newton on Q with its partner 1/conj(z) divided out. Optionally one
-//             more such step runs in FP64.
+//   poly,     u1 = Q x1; the root-MUSIC coefficients, Aberth-Ehrlich on the roots inside the
+//   roots,    unit disk, the root nearest the circle and its polish (roots_device.cuh, shared
+//   select    with the square-block solver).
 //   angle     atan2 of the root minus the carrier step, wrapped (Eq. 15).
 // This header holds the kernel template; batched_l*.cu instantiate it for each covariance order
 // and register-cap variant (compiled in parallel), batched.cu dispatches among them.
@@ -43,12 +31,12 @@
 
 #include "rmusic_device.cuh"
 #include "rmusic_launch.h"
+#include "roots_device.cuh"
 
 namespace rmusic {
 
 constexpr int kBatWarps = 4;
 constexpr int kBatThreads = kBatWarps * 32;
-constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ constexpr int tri(int r, int c, int L) {
     return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);
@@ -61,68 +49,8 @@ __host__ __device__ constexpr int tperm(int p, int L) {
     return p == 0 ? 0 : (p == 1 ? (L > 2 ? 2 : 1) : (p % 2 == 1 ? p - 2 : (p == L - 2 ? L - 1 : p + 2)));
 }
 
-__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
-
-__device__ __forceinline__ cx<float> cdivf(cx<float> a, cx<float> b) {
-    const float inv = frcp(b.r * b.r + b.i * b.i);
-    return mkc((a.r * b.r + a.i * b.i) * inv, (a.i * b.r - a.r * b.i) * inv);
-}
-
 __device__ __forceinline__ cx<float> shfl_up_c(cx<float> v, int o) {
     return mkc(__shfl_up_sync(kFull, v.r, o), __shfl_up_sync(kFull, v.i, o));
-}
-
-// Coefficient i of Q(z) from c_0 (real) and c_1..c_{L-1}.
-template <int L>
-__device__ __forceinline__ cx<float> qcoef(const cx<float>* c, int i) {
-    const int k = i - (L - 1);
-    if (k == 0) return c[0];
-    return k > 0 ? c[k] : conjg(c[-k]);
-}
-
-template <int L>
-__device__ __forceinline__ void horner_pd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d) {
-    p = qcoef<L>(c, 2 * L - 2);
-    d = mkc(0.f, 0.f);
-#pragma unroll
-    for (int i = 2 * L - 3; i >= 0; --i) {
-        d = d * z + p;
-        p = p * z + qcoef<L>(c, i);
-    }
-}
-
-template <int L>
-__device__ __forceinline__ void horner_pdd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d1,
-                                           cx<float>& d2) {
-    p = qcoef<L>(c, 2 * L - 2);
-    d1 = mkc(0.f, 0.f);
-    d2 = mkc(0.f, 0.f);
-#pragma unroll
-    for (int i = 2 * L - 3; i >= 0; --i) {
-        d2 = d2 * z + d1;
-        d1 = d1 * z + p;
-        p = p * z + qcoef<L>(c, i);
-    }
-    d2 = 2.f * d2;
-}
-
-template <int L>
-__device__ __forceinline__ void horner_pdd64(const cx<float>* c, cx<double> z, cx<double>& p, cx<double>& d1,
-                                             cx<double>& d2) {
-    auto q64 = [&](int i) {
-        cx<float> v = qcoef<L>(c, i);
-        return mkc((double)v.r, (double)v.i);
-    };
-    p = q64(2 * L - 2);
-    d1 = mkc(0.0, 0.0);
-    d2 = mkc(0.0, 0.0);
-#pragma unroll
-    for (int i = 2 * L - 3; i >= 0; --i) {
-        d2 = d2 * z + d1;
-        d1 = d1 * z + p;
-        p = p * z + q64(i);
-    }
-    d2 = 2.0 * d2;
 }
 
 // Add entry (r, s) of R_f (value v) to S = Re(Q^H R_f Q) up to the factor 1/2, with the
@@ -383,180 +311,19 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             u[i] = mkc(r2 * x[i], r2 * x[h + i]);
             u[h + i] = mkc(r2 * x[h - 1 - i], -r2 * x[L - 1 - i]);
         }
-        float nu2 = 0.f;
-#pragma unroll
-        for (int i = 0; i < L; ++i) nu2 += norm2(u[i]);
-        // Shrinking the lag coefficients by (1 - eta) makes Q(e^jw) e^-j(L-1)w =
-        // (1 - eta) P(w) + eta (L - 1) >= eta (L - 1) > 0 on the circle, above the FP32 rounding
-        // of the coefficients (~1e-6 of P). Without it, rounding can push a noise-free double root
-        // apart along the circle (two roots at w0 +- d, d ~ 1e-3); with it the pair always splits
-        // radially and keeps the angle of the minimum of P.
-        const float inu2 = (1.f - 2e-6f) * frcp(nu2);
         cx<float> c[L];
-        c[0] = mkc((float)(L - 1), 0.f);
-        // sum_i |q_i| bounds sum_i |q_i| |z|^i for every tracked root (all stay in the unit disk):
-        // the scale of Q's rounding error in the residual test below
-        float qsum = (float)(L - 1);
-#pragma unroll
-        for (int k = 1; k < L; ++k) {
-            cx<float> rho = mkc(0.f, 0.f);
-#pragma unroll
-            for (int m = 0; m + k < L; ++m) rho = rho + mulc(u[m], u[m + k]);
-            c[k] = (-inu2) * rho;
-            qsum += 2.f * sqrtf(norm2(c[k]));
-        }
-        const float res_lim2 = (3e-6f * qsum) * (3e-6f * qsum);
+        const float res_lim2 = music_coefs<L>(u, c);
 
         // ---- Aberth-Ehrlich on the inner roots --------------------------------------------------------
-        // Q's coefficients satisfy c_-k = conj(c_k), so its roots come in pairs z, 1/conj(z). Only
-        // the L - 1 roots inside the unit disk are iterated; each Aberth sum runs over the other
-        // inner roots and over all mirrors 1/conj(z_j) (the root's own partner included), and a
-        // root that steps outside is folded back to its mirror. The loop over roots is rolled:
-        // the current root is always position 0 and the arrays rotate by one after each update,
-        // which keeps the code small enough for the instruction cache.
         cx<float> z[NI], mz[NI];
-        {
-            const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
-            const float n1 = norm2(rho1);
-            const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
-            z[0] = 0.99f * e;
-            float sh, ch;
-            sincospif(1.0f / (float)L, &sh, &ch);                           // exp(j pi / L)
-            const cx<float> step = mkc(ch * ch - sh * sh, 2.f * sh * ch);  // exp(2 j pi / L)
-            cx<float> ek = e * mkc(ch, sh) * step;                           // angle + 2 pi (1 + 1/2) / L
-            const float rin = (float)L / ((float)L + 7.3f);
-#pragma unroll
-            for (int k = 1; k < NI; ++k) {
-                z[k] = rin * ek;
-                ek = ek * step;
-            }
-#pragma unroll
-            for (int k = 0; k < NI; ++k) mz[k] = frcp(norm2(z[k])) * z[k];
-        }
-        int iters = 0, updates = 0;
-        bool rconv = false;
-        unsigned frozen = 0;  // bit r: the root now at position r has converged in this lane
-        for (;;) {
-            rconv = true;
-#pragma unroll 1
-            for (int r = 0; r < NI; ++r) {
-                const cx<float> z0 = z[0];
-                cx<float> nz = z0, nm = mz[0];
-                // A root whose residual reached the rounding level is frozen: near a double root
-                // the corrections below that level are noise and would push it off its angle.
-                // Roots frozen in every lane of the warp are skipped altogether.
-                if (!__all_sync(kFull, frozen & 1u)) {
-                cx<float> p, dp;
-                horner_pd<L>(c, z0, p, dp);
-                const bool cv = (frozen & 1u) || norm2(p) <= res_lim2;
-                frozen |= cv ? 1u : 0u;
-                rconv = rconv && cv;
-                if (!__all_sync(kFull, cv)) {
-                    ++updates;
-                    const cx<float> Ni = cdivf(p, dp);
-                    cx<float> Si = mkc(0.f, 0.f);
-#pragma unroll
-                    for (int j = 0; j < NI; ++j) {
-                        if (j > 0) {
-                            const cx<float> dz = z0 - z[j];
-                            const float inv = frcp(norm2(dz));
-                            Si = mkc(fmaf(dz.r, inv, Si.r), fmaf(-dz.i, inv, Si.i));
-                        }
-                        const cx<float> dm = z0 - mz[j];
-                        const float invm = frcp(norm2(dm));
-                        Si = mkc(fmaf(dm.r, invm, Si.r), fmaf(-dm.i, invm, Si.i));
-                    }
-                    const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - Ni * Si);
-                    if (!cv && isfinite(w.r) && isfinite(w.i)) nz = z0 - w;
-                    const float r2n = norm2(nz);
-                    const float ir2 = frcp(r2n);
-                    nm = ir2 * nz;
-                    if (r2n > 1.f) {  // fold back inside: swap the root and its mirror
-                        const cx<float> t = nz;
-                        nz = nm;
-                        nm = t;
-                    }
-                }
-                }
-                frozen = (frozen >> 1) | ((frozen & 1u) << (NI - 1));
-#pragma unroll
-                for (int j = 0; j + 1 < NI; ++j) {
-                    z[j] = z[j + 1];
-                    mz[j] = mz[j + 1];
-                }
-                z[NI - 1] = nz;
-                mz[NI - 1] = nm;
-            }
-            ++iters;
-            if (iters >= args.max_iters) break;
-            if (__all_sync(kFull, rconv)) break;
-        }
+        int iters, evals, updates;
+        bool rconv;
+        inner_roots<L>(c, res_lim2, args.max_iters, z, mz, iters, evals, updates, rconv);
 
         // ---- selection (Algorithm 1) ------------------------------------------------------------------
-        // every tracked root is inside the disk: the one nearest the circle has the largest modulus
-        int best = -1;
-        float bestr = -1.f;
-        cx<float> zs = mkc(1.f, 0.f), ms = zs;
-#pragma unroll
-        for (int i = 0; i < NI; ++i) {
-            const float r = norm2(z[i]);
-            if (r > bestr) {
-                bestr = r;
-                best = i;
-                zs = z[i];
-                ms = mz[i];
-            }
-        }
-        // nearest other root of the full set: its own mirror, another inner root or a mirror
-        float neard = norm2(ms - zs);
-        cx<float> zn = ms;
-#pragma unroll
-        for (int j = 0; j < NI; ++j) {
-            const float dj = norm2(z[j] - zs), dmj = norm2(mz[j] - zs);
-            if (j != best && dj < neard) {
-                neard = dj;
-                zn = z[j];
-            }
-            if (j != best && dmj < neard) {
-                neard = dmj;
-                zn = mz[j];
-            }
-        }
-        const bool cluster = neard < 4e-3f * 4e-3f;
-        cx<float> zz = cluster ? 0.5f * (zs + zn) : zs;
-#pragma unroll 1
-        for (int it = 0; it < 2; ++it) {
-            cx<float> p, d1, d2;
-            horner_pdd<L>(c, zz, p, d1, d2);
-            cx<float> stp;
-            if (cluster) {
-                stp = cdivf(d1, d2);
-            } else {
-                const float in2 = frcp(norm2(zz));
-                const cx<float> dzp = zz - in2 * zz;  // z - 1/conj(z)
-                stp = cdivf(p, d1 - cdivf(p, dzp));
-            }
-            if (isfinite(stp.r) && isfinite(stp.i)) zz = zz - stp;
-        }
-        double omd;
-        if (args.polish64) {
-            cx<double> z64 = mkc((double)zz.r, (double)zz.i);
-            cx<double> p, d1, d2;
-            horner_pdd64<L>(c, z64, p, d1, d2);
-            cx<double> stp;
-            if (cluster) {
-                stp = cdiv(d1, d2);
-            } else {
-                const double in2 = 1.0 / norm2(z64);
-                const cx<double> dzp = z64 - in2 * z64;
-                stp = cdiv(p, d1 - cdiv(p, dzp));
-            }
-            if (isfinite(stp.r) && isfinite(stp.i)) z64 = z64 - stp;
-            omd = atan2(z64.i, z64.r) - (double)F.omega_ref;
-            omd = wrap_pi(omd);
-        } else {
-            omd = 0.0;
-        }
+        bool found, cluster;
+        const cx<float> zz = select_root<L>(c, z, mz, found, cluster);
+        const double omd = args.polish64 ? wrap_pi(polish_arg64<L>(c, zz, cluster) - F.omega_ref) : 0.0;
         float om = args.polish64 ? (float)omd : wrap_pi(atan2f(zz.i, zz.r) - (float)F.omega_ref);
 
         if (lane == 0 && args.counters) {
@@ -564,6 +331,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             atomicAdd(args.counters + 1, (unsigned long long)iters);
             atomicAdd(args.counters + 2, 1ull);
             atomicAdd(args.counters + 3, (unsigned long long)updates);
+            atomicAdd(args.counters + 4, (unsigned long long)evals);
         }
 
         // ---- store ---------------------------------------------------------------------------------
@@ -572,7 +340,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             uint8_t st = kStOk;
             if (!valid) {
                 st = kStBorder;
-            } else if (!nonzero || !separated || best < 0) {
+            } else if (!nonzero || !separated || !found) {
                 st = kStDegenerate;
             } else if (!rconv || !jconv) {
                 st = kStNotConverged;

@@ -4,8 +4,9 @@
 // A call is: validate descriptors -> build the device frame table (band bins, window-line
 // geometry, work-item ranges) -> band-pass every carrier line (analytic.cu) -> either one
 // thread-per-pixel launch per frame (plain.cu) or one persistent launch per covariance order
-// over all frames (batched.cu). Frames whose analytic signal does not fit the workspace budget
-// together are processed in consecutive groups.
+// over all frames (batched.cu; square.cu for the paper's square block, one launch per
+// half-width). Frames whose analytic signal does not fit the workspace budget together are
+// processed in consecutive groups.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -41,8 +42,28 @@ struct DeviceGuard {
     }
 };
 
-constexpr int kCounterSlots = 64;  // [0, kMaxL] work counters, [kStatSlot ..] statistics
+constexpr int kCounterSlots = 64;  // [0, kStatSlot) work counters, [kStatSlot ..] statistics
 constexpr int kStatSlot = 32;
+
+// A solver key names one compiled solver family: the covariance order L of the row-window
+// solver (2 .. kMaxL), or kSquareKey0 + Lp for the square-block solver.
+constexpr int kSquareKey0 = 16;
+constexpr int kKeys = kSquareKey0 + kMaxSquareLp + 1;
+static_assert(kMaxL < kSquareKey0, "solver keys overlap");
+
+bool key_square(int key) { return key >= kSquareKey0; }
+bool solver_supports(int key) {
+    return key_square(key) ? square_supports(key - kSquareKey0) : batched_supports(key);
+}
+int solver_num_variants(int key) {
+    return key_square(key) ? square_num_variants(key - kSquareKey0) : batched_num_variants(key);
+}
+int solver_default_variant(int key) {
+    return key_square(key) ? square_default_variant(key - kSquareKey0) : batched_default_variant(key);
+}
+int solver_ctas(int key, int v) {
+    return key_square(key) ? square_variant_ctas(key - kSquareKey0, v) : batched_variant_ctas(key, v);
+}
 
 struct GraphEntry {
     std::vector<unsigned char> key;
@@ -91,8 +112,8 @@ struct rmusic_ctx {
     size_t held = 0;
     rmusic_stats stats{};
     char last_err[256] = {0};
-    int grid_by_Lv[kMaxL + 1][4] = {{0}};
-    int variant_by_L[kMaxL + 1];  // solver variant chosen for each covariance order, -1 = none yet
+    int grid_by_Lv[kKeys][4] = {{0}};
+    int variant_by_L[kKeys];  // solver variant chosen for each solver key, -1 = none yet
 };
 
 namespace {
@@ -109,12 +130,18 @@ int cuda_fail(rmusic_ctx* c, cudaError_t e, const char* what) {
     } while (0)
 
 bool params_ok(const rmusic_params& p) {
-    if (p.window_len < 2 || p.window_len > kMaxN) return false;
-    if (p.cov_order < 2 || p.cov_order > kMaxL || p.cov_order > p.window_len) return false;
-    if (p.forward_backward != 0 && p.forward_backward != 1) return false;
-    if (p.deriv_axis != 0 && p.deriv_axis != 1) return false;
+    if (p.geometry == RMUSIC_GEOM_SQUARE) {
+        if (p.half_width < 1 || p.half_width > kMaxSquareLp) return false;
+    } else if (p.geometry == RMUSIC_GEOM_ROW) {
+        if (p.window_len < 2 || p.window_len > kMaxN) return false;
+        if (p.cov_order < 2 || p.cov_order > kMaxL || p.cov_order > p.window_len) return false;
+        if (p.forward_backward != 0 && p.forward_backward != 1) return false;
+        if (p.deriv_axis != 0 && p.deriv_axis != 1) return false;
+    } else {
+        return false;
+    }
     if (p.carrier_axis != 0 && p.carrier_axis != 1) return false;
-    if (!(p.carrier_freq > 0.0 && p.carrier_freq < 0.5)) return false;
+    if (!(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5)) return false;
     if (!(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5)) return false;
     if (p.precision < RMUSIC_PLAIN_FP64 || p.precision > RMUSIC_FP32_BATCHED) return false;
     if (p.max_sweeps < 0 || p.max_root_iters < 0) return false;
@@ -158,7 +185,7 @@ int ensure(rmusic_ctx* ctx, void** ptr, size_t* cap_bytes, size_t bytes) {
 // Everything the kernels need to know about one frame, derived from its descriptor.
 struct Plan {
     std::vector<FrameDev> frames;  // in launch order (grouped by L for the batched path)
-    std::vector<int> group_L;      // batched: covariance order of each group
+    std::vector<int> group_L;      // batched: solver key of each group (L, or kSquareKey0 + Lp)
     std::vector<int> group_first;  // batched: first table entry of each group
     std::vector<int> group_count;
     std::vector<int64_t> group_items;
@@ -172,14 +199,24 @@ int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
     if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
     const int pitch = d.pitch_elems == 0 ? d.width : d.pitch_elems;
     if (pitch < d.width) return RMUSIC_EINVAL;
-    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16) return RMUSIC_EINVAL;
-    const int esz = d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2;
+    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16 && d.dtype != RMUSIC_DTYPE_C64)
+        return RMUSIC_EINVAL;
+    const int esz = d.dtype == RMUSIC_DTYPE_C64 ? 8 : d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2;
     if (d.offset_bytes % esz) return RMUSIC_EINVAL;
-    const int N = d.window_len ? d.window_len : p.window_len;
-    const int L = d.cov_order ? d.cov_order : p.cov_order;
-    if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
-    if (p.precision == RMUSIC_FP32_BATCHED && (!batched_supports(L) || p.forward_backward != 1))
-        return RMUSIC_EUNSUPPORTED;
+    const bool square = p.geometry == RMUSIC_GEOM_SQUARE;
+    int N, L;
+    if (square) {
+        // the paper's block: L holds the half-width Lp, N the block side 2 Lp + 1
+        L = p.half_width;
+        N = 2 * L + 1;
+        if (!square_supports(L)) return RMUSIC_EUNSUPPORTED;
+    } else {
+        N = d.window_len ? d.window_len : p.window_len;
+        L = d.cov_order ? d.cov_order : p.cov_order;
+        if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
+        if (p.precision == RMUSIC_FP32_BATCHED && (!batched_supports(L) || p.forward_backward != 1))
+            return RMUSIC_EUNSUPPORTED;
+    }
     memset(F, 0, sizeof(*F));
     F->in_off = d.offset_bytes;
     F->out_off = d.out_offset;
@@ -190,7 +227,8 @@ int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
     F->N = N;
     F->L = L;
     F->carrier_axis = p.carrier_axis;
-    F->deriv_axis = p.deriv_axis;
+    F->deriv_axis = square ? 0 : p.deriv_axis;  // the square block reads a row-major workspace
+    F->geom = square ? kGeomSquare : kGeomRow;
     F->nlines = p.carrier_axis == 0 ? d.height : d.width;
     F->len = p.carrier_axis == 0 ? d.width : d.height;
     if (F->len > kMaxLine) return RMUSIC_EUNSUPPORTED;
@@ -206,10 +244,16 @@ int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
     }
     F->k_lo = klo < 0 ? 1 : klo;
     F->nb = nb;
-    F->wlines = p.deriv_axis == 0 ? d.height : d.width;
-    F->wlen = p.deriv_axis == 0 ? d.width : d.height;
-    F->nchunks = (F->wlen + kChunk - 1) / kChunk;
-    F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
+    F->wlines = F->deriv_axis == 0 ? d.height : d.width;
+    F->wlen = F->deriv_axis == 0 ? d.width : d.height;
+    F->f0 = f0;
+    if (square) {
+        F->nchunks = (d.width + kSqTX - 1) / kSqTX;  // tiles per tile row
+        F->omega_ref = 6.283185307179586476925 * f0;
+    } else {
+        F->nchunks = (F->wlen + kChunk - 1) / kChunk;
+        F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
+    }
     return RMUSIC_OK;
 }
 
@@ -236,14 +280,18 @@ int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Pla
         F.line_start = lines;
         lines += F.nlines;
         plan->max_len = std::max(plan->max_len, F.len);
+        const int key = F.geom == kGeomSquare ? kSquareKey0 + F.L : F.L;
         if (i == 0 || F.L != plan->frames[i - 1].L) {
-            plan->group_L.push_back(F.L);
+            plan->group_L.push_back(key);
             plan->group_first.push_back(i);
             plan->group_count.push_back(0);
             plan->group_items.push_back(0);
         }
         F.item_start = plan->group_items.back();
-        plan->group_items.back() += (int64_t)F.wlines * F.nchunks;
+        if (F.geom == kGeomSquare)
+            plan->group_items.back() += (int64_t)((F.H + kSqTY - 1) / kSqTY) * F.nchunks;
+        else
+            plan->group_items.back() += (int64_t)F.wlines * F.nchunks;
         plan->group_count.back() += 1;
     }
     plan->total_lines = lines;
@@ -277,15 +325,17 @@ void stamp_pair(std::vector<int>& v, int a, int b) {
 }
 
 // ---- solver variant selection (the autotuner) ---------------------------------------------------
-// Each covariance order has several register-cap variants of the solver (batched_variants.h).
-// A variant is chosen per device and covariance order by timing all of them on real work (the
-// first call with `autotune` set, or rmusic_autotune); the choice is shared by every context on
-// the device and, when RMUSIC_TUNE_CACHE names a file, appended to it as a JSON line
-//   {"device": "<name>/<SMs>sm", "L": 8, "variant": 1, "ctas_per_sm": 6, "ms": 1.917}
-// and read back by later processes. Untuned orders use the default variant.
+// Each solver key (covariance order, or square half-width) has several register-cap variants of
+// its solver (batched_variants.h, square_variants.h). A variant is chosen per device and key by
+// timing all of them on real work (the first call with `autotune` set, or rmusic_autotune); the
+// choice is shared by every context on the device and, when RMUSIC_TUNE_CACHE names a file,
+// appended to it as a JSON line
+//   {"device": "<name>/<SMs>sm", "key": 8, "L": 8, "variant": 1, "ctas_per_sm": 6, "ms": 1.917}
+// ("key" is L for row windows and 16 + Lp for the square block) and read back by later
+// processes. Untuned keys use the default variant.
 constexpr int kTuneDevices = 64;
 std::mutex g_tune_mu;
-int g_tuned[kTuneDevices][kMaxL + 1];
+int g_tuned[kTuneDevices][kKeys];
 bool g_tune_loaded[kTuneDevices];
 bool g_tune_ready = false;
 
@@ -293,7 +343,7 @@ void tune_init_locked() {
     if (g_tune_ready) return;
     for (int d = 0; d < kTuneDevices; ++d) {
         g_tune_loaded[d] = false;
-        for (int l = 0; l <= kMaxL; ++l) g_tuned[d][l] = -1;
+        for (int l = 0; l < kKeys; ++l) g_tuned[d][l] = -1;
     }
     g_tune_ready = true;
 }
@@ -332,22 +382,27 @@ void load_tune_locked(int device) {
     const std::string key = device_key(device);
     char line[512];
     while (fgets(line, sizeof(line), f)) {
-        std::string dev, ls, vs;
+        std::string dev, ks, vs;
         if (!json_field(line, "device", &dev) || dev != key) continue;
-        if (!json_field(line, "L", &ls) || !json_field(line, "variant", &vs)) continue;
-        const int L = atoi(ls.c_str()), v = atoi(vs.c_str());
-        if (batched_supports(L) && v >= 0 && v < batched_num_variants(L)) g_tuned[device][L] = v;
+        if (!(json_field(line, "key", &ks) || json_field(line, "L", &ks)) || !json_field(line, "variant", &vs))
+            continue;
+        const int k = atoi(ks.c_str()), v = atoi(vs.c_str());
+        if (k >= 0 && k < kKeys && solver_supports(k) && v >= 0 && v < solver_num_variants(k))
+            g_tuned[device][k] = v;
     }
     fclose(f);
 }
 
-void store_tune(int device, int L, int v, float ms) {
+void store_tune(int device, int key, int v, float ms) {
     const char* path = getenv("RMUSIC_TUNE_CACHE");
     if (!path || !*path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "{\"device\": \"%s\", \"L\": %d, \"variant\": %d, \"ctas_per_sm\": %d, \"ms\": %.4f}\n",
-            device_key(device).c_str(), L, v, batched_variant_ctas(L, v), ms);
+    fprintf(f,
+            "{\"device\": \"%s\", \"key\": %d, \"%s\": %d, \"variant\": %d, \"ctas_per_sm\": %d, "
+            "\"ms\": %.4f}\n",
+            device_key(device).c_str(), key, key_square(key) ? "Lp" : "L",
+            key_square(key) ? key - kSquareKey0 : key, v, solver_ctas(key, v), ms);
     fclose(f);
 }
 
@@ -360,7 +415,7 @@ int solver_variant(rmusic_ctx* ctx, int L) {
         load_tune_locked(ctx->device);
         v = g_tuned[ctx->device][L];
     }
-    return v >= 0 ? v : batched_default_variant(L);
+    return v >= 0 ? v : solver_default_variant(L);
 }
 
 bool solver_tuned(rmusic_ctx* ctx, int L) {
@@ -373,20 +428,43 @@ bool solver_tuned(rmusic_ctx* ctx, int L) {
 }
 
 int solver_grid(rmusic_ctx* ctx, int L, int v) {
-    if (ctx->grid_by_Lv[L][v] == 0) ctx->grid_by_Lv[L][v] = batched_grid(L, v, ctx->device);
+    if (ctx->grid_by_Lv[L][v] == 0)
+        ctx->grid_by_Lv[L][v] =
+            key_square(L) ? square_grid(L - kSquareKey0, v, ctx->device) : batched_grid(L, v, ctx->device);
     return ctx->grid_by_Lv[L][v];
+}
+
+// Launch variant v of the solver of group g of `plan` (solver key plan.group_L[g]) on s; the
+// group's work counter must be zero. stat_counters receives the iteration statistics or is NULL.
+cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, float* d_out, uint8_t* d_status,
+                          unsigned long long* stat_counters, cudaStream_t s) {
+    const rmusic_params& p = ctx->p;
+    const int key = plan.group_L[g];
+    const float2* gamma = static_cast<const float2*>(ctx->d_gamma);
+    if (key_square(key)) {
+        SquareArgs a;
+        a.max_power_iters = p.max_sweeps ? p.max_sweeps : 100;
+        a.max_iters = p.max_root_iters ? p.max_root_iters : 32;
+        a.polish64 = p.polish_fp64;
+        a.tol2 = 1e-11f;
+        a.counters = stat_counters;
+        return launch_square(key - kSquareKey0, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
+                             plan.group_items[g], ctx->d_counters + g, gamma, d_out, d_status, a,
+                             solver_grid(ctx, key, v), s);
+    }
+    BatchedArgs a;
+    a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
+    a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
+    a.polish64 = p.polish_fp64;
+    a.counters = stat_counters;
+    return launch_batched(key, v, ctx->d_table + plan.group_first[g], plan.group_count[g], plan.group_items[g],
+                          ctx->d_counters + g, gamma, d_out, d_status, a, solver_grid(ctx, key, v), s);
 }
 
 // Time every solver variant on `plan`, whose table and analytic signal are already on the device
 // (queued on s), and keep the fastest for each covariance order not tuned yet (all of them when
 // `force`). Synchronises s; the maps it writes are the call's results.
 int tune_plan(rmusic_ctx* ctx, const Plan& plan, float* d_out, uint8_t* d_status, cudaStream_t s, bool force) {
-    const rmusic_params& p = ctx->p;
-    BatchedArgs a;
-    a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
-    a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
-    a.polish64 = p.polish_fp64;
-    a.counters = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     RM_CUDA(cudaEventCreate(&t0));
     RM_CUDA(cudaEventCreate(&t1));
@@ -395,17 +473,13 @@ int tune_plan(rmusic_ctx* ctx, const Plan& plan, float* d_out, uint8_t* d_status
         const int L = plan.group_L[g];
         if (!force && solver_tuned(ctx, L)) continue;
         float best = 1e30f;
-        int bestv = batched_default_variant(L);
-        for (int v = 0; v < batched_num_variants(L) && rc == RMUSIC_OK; ++v) {
+        int bestv = solver_default_variant(L);
+        for (int v = 0; v < solver_num_variants(L) && rc == RMUSIC_OK; ++v) {
             float tmin = 1e30f;
             for (int rep = 0; rep < 2 && rc == RMUSIC_OK; ++rep) {
                 cudaError_t e = cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
-                if (e == cudaSuccess)
-                    e = launch_batched(L, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
-                                       plan.group_items[g], ctx->d_counters + g,
-                                       static_cast<const float2*>(ctx->d_gamma), d_out, d_status, a,
-                                       solver_grid(ctx, L, v), s);
+                if (e == cudaSuccess) e = launch_solver(ctx, plan, g, v, d_out, d_status, nullptr, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 float ms = 0.f;
@@ -445,22 +519,14 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
     ++*launches;
     const rmusic_params& p = ctx->p;
     if (p.precision == RMUSIC_FP32_BATCHED) {
-        BatchedArgs a;
-        a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
-        a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
-        a.polish64 = p.polish_fp64;
-        a.counters = ctx->d_counters + kStatSlot;
         for (size_t g = 0; g < plan.group_L.size(); ++g) {
             const int L = plan.group_L[g];
             const int v = solver_variant(ctx, L);
             RM_CUDA(cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s));
             int e1 = stamp(ctx, s);
-            RM_CUDA(launch_batched(L, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
-                                   plan.group_items[g], ctx->d_counters + g,
-                                   static_cast<const float2*>(ctx->d_gamma), d_out, d_status,
-                                   a, solver_grid(ctx, L, v), s));
+            RM_CUDA(launch_solver(ctx, plan, g, v, d_out, d_status, ctx->d_counters + kStatSlot, s));
             stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
-            ctx->stats.solver_ctas_per_sm = batched_variant_ctas(L, v);
+            ctx->stats.solver_ctas_per_sm = solver_ctas(L, v);
             ++*launches;
         }
     } else {
@@ -634,6 +700,8 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
     *out = nullptr;
     if (params->model_order != 1) return params->model_order < 1 ? RMUSIC_EINVAL : RMUSIC_EUNSUPPORTED;
     if (!params_ok(*params)) return RMUSIC_EINVAL;
+    if (params->geometry == RMUSIC_GEOM_SQUARE && params->precision != RMUSIC_FP32_BATCHED)
+        return RMUSIC_EUNSUPPORTED;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -643,7 +711,7 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
     if (!ctx) return RMUSIC_ENOMEM;
     ctx->p = *params;
     ctx->device = device;
-    for (int l = 0; l <= kMaxL; ++l) ctx->variant_by_L[l] = -1;
+    for (int l = 0; l < kKeys; ++l) ctx->variant_by_L[l] = -1;
     ctx->budget = hbm_budget_bytes;
     DeviceGuard guard(device);
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -688,7 +756,7 @@ int demodulate_impl(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
         if (rc) return rc;
         pixels += (uint64_t)F.H * (uint64_t)F.W;
     }
-    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, 4 * sizeof(unsigned long long), s));
+    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, 5 * sizeof(unsigned long long), s));
     // group frames so that each group's analytic signal fits the budget
     const uint64_t table_reserve = 64 * sizeof(FrameDev) + (uint64_t)n_frames * sizeof(FrameDev);
     uint64_t avail = 0;
@@ -740,15 +808,17 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
     if (!h_frames || !descs || !h_out) return RMUSIC_EINVAL;
     DeviceGuard guard(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    uint64_t out_elems = 0;
+    uint64_t out_elems = 0, st_elems = 0;
+    const int maps = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? 3 : 1;  // maps per frame
     for (int i = 0; i < n_frames; ++i) {
         const rmusic_frame_desc& d = descs[i];
         if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
-        const int esz = d.dtype == RMUSIC_DTYPE_U16 ? 2 : 4;
+        const int esz = d.dtype == RMUSIC_DTYPE_U16 ? 2 : d.dtype == RMUSIC_DTYPE_C64 ? 8 : 4;
         const uint64_t pitch = d.pitch_elems ? (uint64_t)d.pitch_elems : (uint64_t)d.width;
         const uint64_t end = d.offset_bytes + ((uint64_t)(d.height - 1) * pitch + (uint64_t)d.width) * esz;
         if (end > in_bytes) return RMUSIC_EINVAL;
-        out_elems = std::max<uint64_t>(out_elems, d.out_offset + (uint64_t)d.height * d.width);
+        out_elems = std::max<uint64_t>(out_elems, d.out_offset + (uint64_t)maps * d.height * d.width);
+        st_elems = std::max<uint64_t>(st_elems, d.out_offset + (uint64_t)d.height * d.width);
     }
     int rc = ensure(ctx, &ctx->d_in, &ctx->in_cap, std::max<size_t>(in_bytes, 16));
     if (!rc) {
@@ -761,7 +831,7 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
     if (!rc && h_status) {
         size_t sb = ctx->st_cap;
         void* sp = ctx->d_st;
-        rc = ensure(ctx, &sp, &sb, out_elems);
+        rc = ensure(ctx, &sp, &sb, st_elems);
         ctx->d_st = (uint8_t*)sp;
         ctx->st_cap = sb;
     }
@@ -771,7 +841,7 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
                                   cuda_stream);
     if (rc) return rc;
     RM_CUDA(cudaMemcpyAsync(h_out, ctx->d_out, out_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
-    if (h_status) RM_CUDA(cudaMemcpyAsync(h_status, ctx->d_st, out_elems, cudaMemcpyDeviceToHost, s));
+    if (h_status) RM_CUDA(cudaMemcpyAsync(h_status, ctx->d_st, st_elems, cudaMemcpyDeviceToHost, s));
     RM_CUDA(cudaStreamSynchronize(s));
     return RMUSIC_OK;
 }
@@ -823,11 +893,12 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->workspace_bytes = ctx->held;
     out->pixels = ctx->last_pixels;
     RM_CUDA(cudaEventSynchronize(ctx->call_done));
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
     RM_CUDA(cudaMemcpy(c, ctx->d_counters + kStatSlot, sizeof(c), cudaMemcpyDeviceToHost));
     out->mean_sweeps = c[2] ? (double)c[0] / (double)c[2] : 0.0;
     out->mean_root_iters = c[2] ? (double)c[1] / (double)c[2] : 0.0;
     out->mean_root_updates = c[2] ? (double)c[3] / (double)c[2] : 0.0;
+    out->mean_root_evals = c[2] ? (double)c[4] / (double)c[2] : 0.0;
     auto sum = [&](const std::vector<int>& v) {
         float t = 0.f;
         for (size_t i = 0; i + 1 < v.size(); i += 2) {

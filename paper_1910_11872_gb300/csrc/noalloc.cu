@@ -76,8 +76,10 @@ int na_describe(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev* F)
     if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
     const int pitch = d.pitch_elems == 0 ? d.width : d.pitch_elems;
     if (pitch < d.width) return RMUSIC_EINVAL;
-    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16) return RMUSIC_EINVAL;
-    if (d.offset_bytes % (d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2)) return RMUSIC_EINVAL;
+    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16 && d.dtype != RMUSIC_DTYPE_C64)
+        return RMUSIC_EINVAL;
+    if (d.offset_bytes % (d.dtype == RMUSIC_DTYPE_C64 ? 8 : d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2))
+        return RMUSIC_EINVAL;
     const int N = d.window_len ? d.window_len : p.window_len;
     const int L = d.cov_order ? d.cov_order : p.cov_order;
     if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
@@ -110,6 +112,7 @@ int na_describe(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev* F)
     F->wlen = p.deriv_axis == 0 ? d.width : d.height;
     F->nchunks = (F->wlen + kChunk - 1) / kChunk;
     F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
+    F->f0 = f0;
     return RMUSIC_OK;
 }
 
@@ -121,10 +124,11 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
     if (!params || n_frames < 0) return RMUSIC_EINVAL;
     const rmusic_params& p = *params;
     if (p.model_order != 1) return p.model_order < 1 ? RMUSIC_EINVAL : RMUSIC_EUNSUPPORTED;
-    if (p.precision != RMUSIC_FP32_BATCHED || p.forward_backward != 1) return RMUSIC_EUNSUPPORTED;
+    if (p.precision != RMUSIC_FP32_BATCHED || p.forward_backward != 1 || p.geometry != RMUSIC_GEOM_ROW)
+        return RMUSIC_EUNSUPPORTED;
     if (p.window_len < 2 || p.window_len > kMaxN || p.cov_order < 2 || p.cov_order > kMaxL ||
         p.cov_order > p.window_len || (p.deriv_axis != 0 && p.deriv_axis != 1) ||
-        (p.carrier_axis != 0 && p.carrier_axis != 1) || !(p.carrier_freq > 0.0 && p.carrier_freq < 0.5) ||
+        (p.carrier_axis != 0 && p.carrier_axis != 1) || !(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5) ||
         !(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5) || p.max_sweeps < 0 || p.max_root_iters < 0)
         return RMUSIC_EINVAL;
     if (n_frames == 0) return RMUSIC_OK;

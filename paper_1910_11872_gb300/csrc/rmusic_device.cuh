@@ -7,8 +7,10 @@
 //            gamma[gam_off + wline * wlen + pos] is the sample at position `pos` of window
 //            line `wline` (wline = y, pos = x when windows run along x; wline = x, pos = y
 //            when they run along y).
-//   out      caller's float32 maps, frame f dense H x W row-major at element offset out_off.
-//   status   caller's optional uint8 maps, same layout as out.
+//   out      caller's float32 maps, frame f dense H x W row-major at element offset out_off
+//            (square geometry: three maps, d/dx at out_off, d/dy at out_off + H W and the
+//            local phase alpha at out_off + 2 H W).
+//   status   caller's optional uint8 maps, one per frame at element offset out_off.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,6 +25,10 @@ constexpr int kChunk = 32;       // pixels of one window line handled by one war
 
 enum : uint8_t { kStOk = 0, kStBorder = 1, kStDegenerate = 2, kStNotConverged = 3 };
 
+// Frame sample types (the values of RMUSIC_DTYPE_*) and solver geometries (RMUSIC_GEOM_*).
+enum : int32_t { kDtF32 = 0, kDtU16 = 1, kDtC64 = 2 };
+enum : int32_t { kGeomRow = 0, kGeomSquare = 1 };
+
 // Per-frame entry of the device frame table (built on the host for each call).
 struct FrameDev {
     uint64_t in_off;      // byte offset of the frame in the input buffer
@@ -36,8 +42,11 @@ struct FrameDev {
     int32_t nlines, len;  // carrier lines and their length
     int32_t k_lo, nb;     // kept DFT bins k_lo .. k_lo + nb - 1 of a carrier line
     int32_t wlines, wlen; // window lines and their length
-    int32_t nchunks;      // work items per window line (ceil(wlen / kChunk))
+    int32_t nchunks;      // row geometry: work items per window line (ceil(wlen / kChunk));
+                          // square geometry: tiles per tile row (ceil(W / 32))
+    int32_t geom;         // kGeomRow or kGeomSquare (then L holds the half-width Lp, N = 2 Lp + 1)
     double omega_ref;     // carrier phase step removed from the angle (rad/pixel)
+    double f0;            // carrier frequency (cycles/pixel)
 };
 
 // Index of the frame that owns global index `g` given each frame's start (non-decreasing).

@@ -32,7 +32,8 @@ struct BatchedArgs {
     int max_sweeps;
     int max_iters;
     int polish64;
-    unsigned long long* counters;  // [0] sweeps, [1] root iterations, [2] items, [3] root updates
+    unsigned long long* counters;  // [0] sweeps, [1] root iterations, [2] items, [3] root updates,
+                                   // [4] evaluations of Q and Q'
 };
 bool batched_supports(int L);
 int batched_num_variants(int L);
@@ -43,5 +44,27 @@ cudaError_t launch_batched(int L, int v, const FrameDev* d_frames, int nframes, 
                            unsigned long long* d_counter, const float2* d_gamma, float* d_out,
                            uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream);
 int batched_grid(int L, int v, int device);
+
+// Square-block FP32 path (the paper's geometry): persistent, one 32 x 4 pixel tile per CTA work
+// item, over all frames that share the half-width Lp. `counter` must be zero when it starts.
+constexpr int kMaxSquareLp = 8;
+constexpr int kSqTX = 32;  // tile width in pixels: one warp's pixels along x
+constexpr int kSqTY = 4;   // tile height: one row per warp of the 128-thread CTA
+struct SquareArgs {
+    int max_power_iters;
+    int max_iters;
+    int polish64;
+    float tol2;                    // power iteration stops when |u_new - u|^2 <= tol2
+    unsigned long long* counters;  // [0] power iterations, [1] root iterations, [2] warps, [3] root updates,
+                                   // [4] evaluations of Q and Q' (both polynomials)
+};
+bool square_supports(int Lp);
+int square_num_variants(int Lp);
+int square_default_variant(int Lp);
+int square_variant_ctas(int Lp, int v);
+cudaError_t launch_square(int Lp, int v, const FrameDev* d_frames, int nframes, int64_t total_items,
+                          unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                          uint8_t* d_status, SquareArgs a, int grid, cudaStream_t stream);
+int square_grid(int Lp, int v, int device);
 
 }  // namespace rmusic

@@ -1,0 +1,291 @@
+// roots_device.cuh -- the FP32 polynomial stage shared by the batched solvers (row windows and
+// the paper's square block): root-MUSIC coefficients from a signal vector, Aberth-Ehrlich on the
+// roots inside the unit disk, selection of the root nearest the circle and its polish (Sec. 3,
+// Eq. 12-15; Algorithm 1).
+//
+//   poly      u1 the signal vector (any norm); c_0 = L - 1, c_k = -(1 - 2e-6) sum_m u1[m]
+//             conj(u1[m+k]) / |u1|^2, c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14).
+//             The 2e-6 shrink keeps the polynomial strictly positive on the circle in FP32.
+//   roots     Aberth-Ehrlich on the L - 1 roots inside the unit disk; the other L - 1 roots are
+//             their mirrors 1/conj(z) (the coefficients are conjugate-symmetric). Starting
+//             points come from the estimator's structure: the signal root just inside the circle
+//             at the angle of conj(rho_1), the others at radius r = L / (L + 7.3) at the
+//             side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window
+//             puts them. Iterations stop when every root of every lane of the warp has a residual
+//             at the FP32 rounding level (|Q(z)| <= 3e-6 sum |q_i|).
+//   select    the inner root nearest the unit circle (Algorithm 1). A noise-free window gives a
+//             double root on the circle, which FP32 splits by ~sqrt(eps); when another root lies
+//             within 4e-3 the pair is located as the root of Q' between them, otherwise the root
+//             is refined by Newton on Q with its partner 1/conj(z) divided out. Optionally one
+//             more such step runs in FP64.
+// Every function here is called by all 32 lanes of a warp together (warp votes decide when the
+// iterations stop), one polynomial per lane.
+#pragma once
+
+#include <math.h>
+
+#include "rmusic_device.cuh"
+
+namespace rmusic {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+
+__device__ __forceinline__ cx<float> cdivf(cx<float> a, cx<float> b) {
+    const float inv = frcp(b.r * b.r + b.i * b.i);
+    return mkc((a.r * b.r + a.i * b.i) * inv, (a.i * b.r - a.r * b.i) * inv);
+}
+
+// Coefficient i of Q(z) from c_0 (real) and c_1..c_{L-1}.
+template <int L>
+__device__ __forceinline__ cx<float> qcoef(const cx<float>* c, int i) {
+    const int k = i - (L - 1);
+    if (k == 0) return c[0];
+    return k > 0 ? c[k] : conjg(c[-k]);
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d) {
+    p = qcoef<L>(c, 2 * L - 2);
+    d = mkc(0.f, 0.f);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d = d * z + p;
+        p = p * z + qcoef<L>(c, i);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pdd(const cx<float>* c, cx<float> z, cx<float>& p, cx<float>& d1,
+                                           cx<float>& d2) {
+    p = qcoef<L>(c, 2 * L - 2);
+    d1 = mkc(0.f, 0.f);
+    d2 = mkc(0.f, 0.f);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d2 = d2 * z + d1;
+        d1 = d1 * z + p;
+        p = p * z + qcoef<L>(c, i);
+    }
+    d2 = 2.f * d2;
+}
+
+template <int L>
+__device__ __forceinline__ void horner_pdd64(const cx<float>* c, cx<double> z, cx<double>& p, cx<double>& d1,
+                                             cx<double>& d2) {
+    auto q64 = [&](int i) {
+        cx<float> v = qcoef<L>(c, i);
+        return mkc((double)v.r, (double)v.i);
+    };
+    p = q64(2 * L - 2);
+    d1 = mkc(0.0, 0.0);
+    d2 = mkc(0.0, 0.0);
+#pragma unroll
+    for (int i = 2 * L - 3; i >= 0; --i) {
+        d2 = d2 * z + d1;
+        d1 = d1 * z + p;
+        p = p * z + q64(i);
+    }
+    d2 = 2.0 * d2;
+}
+
+// Coefficients c_0 .. c_{L-1} of Q from the signal vector u (Eq. 12-14). Returns
+// res_lim2 = (3e-6 sum_i |q_i|)^2, the squared FP32 rounding level of Q inside the unit disk.
+template <int L>
+__device__ __forceinline__ float music_coefs(const cx<float>* u, cx<float>* c) {
+    float nu2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < L; ++i) nu2 += norm2(u[i]);
+    // Shrinking the lag coefficients by (1 - eta) makes Q(e^jw) e^-j(L-1)w =
+    // (1 - eta) P(w) + eta (L - 1) >= eta (L - 1) > 0 on the circle, above the FP32 rounding
+    // of the coefficients (~1e-6 of P). Without it, rounding can push a noise-free double root
+    // apart along the circle (two roots at w0 +- d, d ~ 1e-3); with it the pair always splits
+    // radially and keeps the angle of the minimum of P.
+    const float inu2 = (1.f - 2e-6f) * frcp(nu2);
+    c[0] = mkc((float)(L - 1), 0.f);
+    // sum_i |q_i| bounds sum_i |q_i| |z|^i for every tracked root (all stay in the unit disk):
+    // the scale of Q's rounding error in the residual test
+    float qsum = (float)(L - 1);
+#pragma unroll
+    for (int k = 1; k < L; ++k) {
+        cx<float> rho = mkc(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m + k < L; ++m) rho = rho + mulc(u[m], u[m + k]);
+        c[k] = (-inu2) * rho;
+        qsum += 2.f * sqrtf(norm2(c[k]));
+    }
+    return (3e-6f * qsum) * (3e-6f * qsum);
+}
+
+// Aberth-Ehrlich on the L - 1 roots of Q inside the unit disk. On return z[] holds them and
+// mz[] their mirrors 1/conj(z); iters counts sweeps, evals the evaluations of Q and Q' that ran
+// (a root frozen in every lane of the warp is skipped), updates the root updates that ran; rconv
+// is false if max_iters sweeps ended before every root of this lane converged.
+template <int L>
+__device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, int max_iters,
+                                            cx<float> (&z)[L - 1], cx<float> (&mz)[L - 1], int& iters,
+                                            int& evals, int& updates, bool& rconv) {
+    constexpr int NI = L - 1;
+    // Q's coefficients satisfy c_-k = conj(c_k), so its roots come in pairs z, 1/conj(z). Only
+    // the L - 1 roots inside the unit disk are iterated; each Aberth sum runs over the other
+    // inner roots and over all mirrors 1/conj(z_j) (the root's own partner included), and a
+    // root that steps outside is folded back to its mirror. The loop over roots is rolled:
+    // the current root is always position 0 and the arrays rotate by one after each update,
+    // which keeps the code small enough for the instruction cache.
+    {
+        const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
+        const float n1 = norm2(rho1);
+        const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
+        z[0] = 0.99f * e;
+        float sh, ch;
+        sincospif(1.0f / (float)L, &sh, &ch);                           // exp(j pi / L)
+        const cx<float> step = mkc(ch * ch - sh * sh, 2.f * sh * ch);  // exp(2 j pi / L)
+        cx<float> ek = e * mkc(ch, sh) * step;                           // angle + 2 pi (1 + 1/2) / L
+        const float rin = (float)L / ((float)L + 7.3f);
+#pragma unroll
+        for (int k = 1; k < NI; ++k) {
+            z[k] = rin * ek;
+            ek = ek * step;
+        }
+#pragma unroll
+        for (int k = 0; k < NI; ++k) mz[k] = frcp(norm2(z[k])) * z[k];
+    }
+    iters = 0;
+    evals = 0;
+    updates = 0;
+    rconv = false;
+    unsigned frozen = 0;  // bit r: the root now at position r has converged in this lane
+    for (;;) {
+        rconv = true;
+#pragma unroll 1
+        for (int r = 0; r < NI; ++r) {
+            const cx<float> z0 = z[0];
+            cx<float> nz = z0, nm = mz[0];
+            // A root whose residual reached the rounding level is frozen: near a double root
+            // the corrections below that level are noise and would push it off its angle.
+            // Roots frozen in every lane of the warp are skipped altogether.
+            if (!__all_sync(kFull, frozen & 1u)) {
+                ++evals;
+                cx<float> p, dp;
+                horner_pd<L>(c, z0, p, dp);
+                const bool cv = (frozen & 1u) || norm2(p) <= res_lim2;
+                frozen |= cv ? 1u : 0u;
+                rconv = rconv && cv;
+                if (!__all_sync(kFull, cv)) {
+                    ++updates;
+                    const cx<float> Ni = cdivf(p, dp);
+                    cx<float> Si = mkc(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < NI; ++j) {
+                        if (j > 0) {
+                            const cx<float> dz = z0 - z[j];
+                            const float inv = frcp(norm2(dz));
+                            Si = mkc(fmaf(dz.r, inv, Si.r), fmaf(-dz.i, inv, Si.i));
+                        }
+                        const cx<float> dm = z0 - mz[j];
+                        const float invm = frcp(norm2(dm));
+                        Si = mkc(fmaf(dm.r, invm, Si.r), fmaf(-dm.i, invm, Si.i));
+                    }
+                    const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - Ni * Si);
+                    if (!cv && isfinite(w.r) && isfinite(w.i)) nz = z0 - w;
+                    const float r2n = norm2(nz);
+                    const float ir2 = frcp(r2n);
+                    nm = ir2 * nz;
+                    if (r2n > 1.f) {  // fold back inside: swap the root and its mirror
+                        const cx<float> t = nz;
+                        nz = nm;
+                        nm = t;
+                    }
+                }
+            }
+            frozen = (frozen >> 1) | ((frozen & 1u) << (NI - 1));
+#pragma unroll
+            for (int j = 0; j + 1 < NI; ++j) {
+                z[j] = z[j + 1];
+                mz[j] = mz[j + 1];
+            }
+            z[NI - 1] = nz;
+            mz[NI - 1] = nm;
+        }
+        ++iters;
+        if (iters >= max_iters) break;
+        if (__all_sync(kFull, rconv)) break;
+    }
+}
+
+// The selected root (Algorithm 1) after inner_roots, refined by two FP32 Newton steps (on Q'
+// for a split double root, else on Q with the partner 1/conj(z) divided out). found is false
+// if no root was tracked (never for L >= 2); cluster tells which refinement ran.
+template <int L>
+__device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<float> (&z)[L - 1],
+                                                 const cx<float> (&mz)[L - 1], bool& found, bool& cluster) {
+    constexpr int NI = L - 1;
+    // every tracked root is inside the disk: the one nearest the circle has the largest modulus
+    int best = -1;
+    float bestr = -1.f;
+    cx<float> zs = mkc(1.f, 0.f), ms = zs;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const float r = norm2(z[i]);
+        if (r > bestr) {
+            bestr = r;
+            best = i;
+            zs = z[i];
+            ms = mz[i];
+        }
+    }
+    // nearest other root of the full set: its own mirror, another inner root or a mirror
+    float neard = norm2(ms - zs);
+    cx<float> zn = ms;
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+        const float dj = norm2(z[j] - zs), dmj = norm2(mz[j] - zs);
+        if (j != best && dj < neard) {
+            neard = dj;
+            zn = z[j];
+        }
+        if (j != best && dmj < neard) {
+            neard = dmj;
+            zn = mz[j];
+        }
+    }
+    found = best >= 0;
+    cluster = neard < 4e-3f * 4e-3f;
+    cx<float> zz = cluster ? 0.5f * (zs + zn) : zs;
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+        cx<float> p, d1, d2;
+        horner_pdd<L>(c, zz, p, d1, d2);
+        cx<float> stp;
+        if (cluster) {
+            stp = cdivf(d1, d2);
+        } else {
+            const float in2 = frcp(norm2(zz));
+            const cx<float> dzp = zz - in2 * zz;  // z - 1/conj(z)
+            stp = cdivf(p, d1 - cdivf(p, dzp));
+        }
+        if (isfinite(stp.r) && isfinite(stp.i)) zz = zz - stp;
+    }
+    return zz;
+}
+
+// One more refinement step of the selected root in FP64; returns arg z in double.
+template <int L>
+__device__ __forceinline__ double polish_arg64(const cx<float>* c, cx<float> zz, bool cluster) {
+    cx<double> z64 = mkc((double)zz.r, (double)zz.i);
+    cx<double> p, d1, d2;
+    horner_pdd64<L>(c, z64, p, d1, d2);
+    cx<double> stp;
+    if (cluster) {
+        stp = cdiv(d1, d2);
+    } else {
+        const double in2 = 1.0 / norm2(z64);
+        const cx<double> dzp = z64 - in2 * z64;
+        stp = cdiv(p, d1 - cdiv(p, dzp));
+    }
+    if (isfinite(stp.r) && isfinite(stp.i)) z64 = z64 - stp;
+    return atan2(z64.i, z64.r);
+}
+
+}  // namespace rmusic

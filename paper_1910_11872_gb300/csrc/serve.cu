@@ -230,6 +230,7 @@ int rmusic_serve_create(const rmusic_params* params, int device, const rmusic_se
     *out = nullptr;
     if (!config_ok(*cfg)) return RMUSIC_EINVAL;
     if (params->precision != RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
+    if (params->geometry != RMUSIC_GEOM_ROW) return RMUSIC_EUNSUPPORTED;  // one map per frame slot
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();

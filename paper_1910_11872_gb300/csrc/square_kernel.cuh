@@ -1,0 +1,289 @@
+// square_kernel.cuh -- FP32 solver for the paper's own geometry: the M x M block Gamma_w,
+// M = 2 Lp + 1, centred on each pixel (Sec. 3, Eq. 4-15; Algorithm 1). Both local phase
+// derivatives and the local phase alpha come out of one block:
+//   R_y = Gamma_w Gamma_w^H  (the block's columns are the snapshots), u1 its signal eigenvector,
+//   R_x = Gamma_w^H Gamma_w  (the conjugated rows), v1 its signal eigenvector,
+//   Q_y, Q_x the root-MUSIC polynomials of u1 and v1 (Eq. 12, 13), z_y, z_x their roots nearest
+//   the unit circle inside it, omega_y = arg z_y, omega_x = -arg z_x, and
+//   alpha = angle of the block mean of Gamma_w exp(-j(omega_x x + omega_y y)) (Eq. 15), with
+//   x, y centred on the pixel.
+//
+// Work decomposition: one thread per pixel; a CTA of 4 warps takes one 32 x 4 tile of pixels
+// from a global atomic counter (persistent grid) and stages the tile's (32 + 2 Lp) x (4 + 2 Lp)
+// analytic-signal samples in shared memory with coalesced loads; each lane then reads its own
+// block from there. Tiles sit at absolute positions of their frame, so the warps -- and with
+// them every warp-level iteration count -- are the same whether a frame runs alone or batched.
+//
+// Eigenvectors: u1 and v1 are the first left and right singular vectors of Gamma_w (the paper
+// takes them from an SVD), computed by the power iteration u <- G G^H u / |.| on the block itself
+// (two M x M products per step, no M x M covariance is formed), started from the centre column.
+// The vectors live in shared memory (one column per thread) and the loops over rows are rolled,
+// so only one M-vector is held in registers.
+// Each step shrinks the other singular directions by (s_2 / s_1)^2 ~ 4 sigma^2 / (M A^2); the
+// iteration stops when the step changes u by less than 3e-6 in every lane of the warp. v1 is
+// G^H u from the last step. Degenerate blocks (all zero) get a stand-in vector so every lane of
+// the warp runs the same bounded loops.
+//
+// Polynomials: the root stage of roots_device.cuh (coefficients, Aberth on the inner roots,
+// selection, polish) with L = M, run once per axis in one rolled loop (the second axis'
+// coefficients wait in shared memory), which keeps the code within the instruction cache.
+#pragma once
+
+#include <math.h>
+
+#include "rmusic_device.cuh"
+#include "rmusic_launch.h"
+#include "roots_device.cuh"
+
+namespace rmusic {
+
+constexpr int kSqThreads = kSqTX * kSqTY;
+
+template <int LP, int CTAS>
+__global__ void __launch_bounds__(kSqThreads, CTAS)
+square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
+              unsigned long long* __restrict__ counter, const float2* __restrict__ gam,
+              float* __restrict__ out, uint8_t* __restrict__ status, SquareArgs args) {
+    static_assert(LP >= 1 && 2 * LP + 1 <= 2 * kMaxSquareLp + 1, "half-width out of range");
+    constexpr int M = 2 * LP + 1;
+    constexpr int NI = M - 1;              // roots of Q inside the disk
+    constexpr int SW = kSqTX + 2 * LP;     // staged columns
+    constexpr int SH = kSqTY + 2 * LP;     // staged rows
+    // per-thread scratch, one float2 column per thread: the power iteration's two vectors
+    // (2 M complex), afterwards the two polynomials' coefficients c_0 .. c_{M-1} (2 M complex)
+    constexpr int NSCR = 4 * M;  // floats per thread
+    __shared__ float2 tile[SH * SW];
+    __shared__ float sh_scr[NSCR * kSqThreads];
+    __shared__ long long sh_item;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float tol2 = args.tol2;
+
+    for (;;) {
+        __syncthreads();  // every thread is done with the previous tile and item
+        if (threadIdx.x == 0) sh_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long item = sh_item;
+        if (item >= total_items) break;
+        const int f = find_frame(fr, nframes, (int64_t)item, [](const FrameDev& F) { return F.item_start; });
+        const FrameDev& F = fr[f];
+        const int64_t local = (int64_t)item - F.item_start;
+        const int ty = (int)(local / F.nchunks);
+        const int tx = (int)(local % F.nchunks);
+        const int H = F.H, W = F.W;
+
+        // ---- stage the tile's samples (coalesced rows) ----------------------------------------
+        {
+            const int x0 = tx * kSqTX - LP, y0 = ty * kSqTY - LP;
+            const float2* g = gam + F.gam_off;
+            for (int i = threadIdx.x; i < SH * SW; i += kSqThreads) {
+                const int r = i / SW, c = i - r * SW;
+                const int gy = y0 + r, gx = x0 + c;
+                tile[i] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? g[(int64_t)gy * W + gx]
+                                                                     : make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        const int px = tx * kSqTX + lane, py = ty * kSqTY + wid;
+        const bool inside = px < W && py < H;
+        const bool valid = inside && px - LP >= 0 && px + LP < W && py - LP >= 0 && py + LP < H;
+        const float2* Gb = tile + wid * SW + lane;  // block entry (r, c) at Gb[r * SW + c]
+        auto G = [&](int r, int c) {
+            const float2 v = Gb[r * SW + c];
+            return mkc(v.x, v.y);
+        };
+        float2* const vec0 = reinterpret_cast<float2*>(sh_scr) + threadIdx.x;  // entry m at [m * kSqThreads]
+        float2* const vec1 = vec0 + M * kSqThreads;
+
+        // ---- power iteration for u1 (and v1) ------------------------------------------------------
+        // u (unit norm) lives in one scratch vector, G y is written to the other, then the roles swap.
+        float nu2 = 0.f;
+#pragma unroll 1
+        for (int m = 0; m < M; ++m) {
+            const cx<float> g = G(m, LP);
+            vec0[m * kSqThreads] = make_float2(g.r, g.i);
+            nu2 += norm2(g);
+        }
+        const bool nonzero = valid && nu2 > 0.f && isfinite(nu2);
+        {
+            const float inv = nonzero ? rsqrtf(nu2) : 0.f;
+#pragma unroll 1
+            for (int m = 0; m < M; ++m) {
+                const float2 v = vec0[m * kSqThreads];
+                vec0[m * kSqThreads] = make_float2(inv * v.x, inv * v.y);
+            }
+        }
+        float2* uv = vec0;
+        float2* wv = vec1;
+        cx<float> y[M];
+        bool pconv = !nonzero;
+        int pits = 0;
+        for (;;) {
+            // y = G^H u
+#pragma unroll
+            for (int c = 0; c < M; ++c) y[c] = mkc(0.f, 0.f);
+#pragma unroll 1
+            for (int m = 0; m < M; ++m) {
+                const float2 um = uv[m * kSqThreads];
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    const cx<float> g = G(m, c);  // y_c += conj(g) u_m
+                    y[c] = mkc(fmaf(g.r, um.x, fmaf(g.i, um.y, y[c].r)), fmaf(g.r, um.y, fmaf(-g.i, um.x, y[c].i)));
+                }
+            }
+            // w = G y
+            float n2 = 0.f;
+#pragma unroll 1
+            for (int m = 0; m < M; ++m) {
+                cx<float> a = mkc(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    const cx<float> g = G(m, c);  // w_m += g y_c
+                    a = mkc(fmaf(g.r, y[c].r, fmaf(-g.i, y[c].i, a.r)), fmaf(g.r, y[c].i, fmaf(g.i, y[c].r, a.i)));
+                }
+                wv[m * kSqThreads] = make_float2(a.r, a.i);
+                n2 += norm2(a);
+            }
+            // normalise w, measure the step |w - u|^2, swap
+            const float inv = n2 > 0.f ? rsqrtf(n2) : 0.f;
+            float d2 = 0.f;
+#pragma unroll 1
+            for (int m = 0; m < M; ++m) {
+                const float2 w = wv[m * kSqThreads], u = uv[m * kSqThreads];
+                const float2 nw = make_float2(inv * w.x, inv * w.y);
+                d2 += (nw.x - u.x) * (nw.x - u.x) + (nw.y - u.y) * (nw.y - u.y);
+                wv[m * kSqThreads] = nw;
+            }
+            float2* t = uv;
+            uv = wv;
+            wv = t;
+            pconv = pconv || d2 <= tol2;
+            ++pits;
+            if (pits >= args.max_power_iters) break;
+            if (__all_sync(kFull, pconv)) break;
+        }
+        cx<float> u[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const float2 v = uv[m * kSqThreads];
+            u[m] = mkc(v.x, v.y);
+        }
+        if (!nonzero) {
+            // stand-in: the noise-free vector of angle 0, so the root stage runs its short path
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                u[m] = mkc(1.f, 0.f);
+                y[m] = mkc(1.f, 0.f);
+            }
+        }
+
+        // ---- both polynomials' coefficients, parked in the scratch (the vectors are done) ----------
+        // same float2 column as the vectors: every thread touches only its own column
+        float2* const cme = vec0;  // coefficient k of axis ax at cme[(ax * M + k) * kSqThreads]
+        float res2_y, res2_x;
+        {
+            cx<float> c[M];
+            res2_y = music_coefs<M>(u, c);
+#pragma unroll
+            for (int k = 0; k < M; ++k) cme[k * kSqThreads] = make_float2(c[k].r, c[k].i);
+            res2_x = music_coefs<M>(y, c);
+#pragma unroll
+            for (int k = 0; k < M; ++k) cme[(M + k) * kSqThreads] = make_float2(c[k].r, c[k].i);
+        }
+
+        // ---- roots, selection and angle: axis 0 is y (z_y), axis 1 is x (z_x) ----------------------
+        float om_y = 0.f, om_x = 0.f;
+        bool rconv_all = true, found_all = true;
+        int riters = 0, revals = 0, rupdates = 0;
+#pragma unroll 1
+        for (int ax = 0; ax < 2; ++ax) {
+            cx<float> c[M];
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const float2 v = cme[(ax * M + k) * kSqThreads];
+                c[k] = mkc(v.x, v.y);
+            }
+            cx<float> z[NI], mz[NI];
+            int iters, evals, updates;
+            bool rconv, found, cluster;
+            inner_roots<M>(c, ax == 0 ? res2_y : res2_x, args.max_iters, z, mz, iters, evals, updates, rconv);
+            const cx<float> zz = select_root<M>(c, z, mz, found, cluster);
+            const float a = args.polish64 ? (float)polish_arg64<M>(c, zz, cluster) : atan2f(zz.i, zz.r);
+            if (ax == 0)
+                om_y = a;
+            else
+                om_x = -a;  // z_x = exp(-j omega_x) (Eq. 15)
+            rconv_all = rconv_all && rconv;
+            found_all = found_all && found;
+            riters += iters;
+            revals += evals;
+            rupdates += updates;
+        }
+
+        // ---- alpha: angle of the demodulated block mean (Eq. 15) ----------------------------------
+        // exp(-j omega (k - Lp)) for k = 0 .. M-1 by recurrence from exp(j omega Lp)
+        cx<float> ex[M];
+        {
+            float s1, c1, s0, c0;
+            sincosf(om_x, &s1, &c1);
+            sincosf(om_x * (float)LP, &s0, &c0);
+            const cx<float> e1 = mkc(c1, -s1);
+            ex[0] = mkc(c0, s0);
+#pragma unroll
+            for (int c = 1; c < M; ++c) ex[c] = ex[c - 1] * e1;
+        }
+        cx<float> acc = mkc(0.f, 0.f);
+        {
+            float s1, c1, s0, c0;
+            sincosf(om_y, &s1, &c1);
+            sincosf(om_y * (float)LP, &s0, &c0);
+            const cx<float> e1 = mkc(c1, -s1);
+            cx<float> ey = mkc(c0, s0);
+#pragma unroll 1
+            for (int r = 0; r < M; ++r) {
+                cx<float> t = mkc(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < M; ++c) t = t + G(r, c) * ex[c];
+                acc = acc + t * ey;
+                ey = ey * e1;
+            }
+        }
+
+        if (lane == 0 && args.counters) {
+            atomicAdd(args.counters + 2, 1ull);
+            atomicAdd(args.counters + 0, (unsigned long long)pits);
+            atomicAdd(args.counters + 1, (unsigned long long)riters);
+            atomicAdd(args.counters + 3, (unsigned long long)rupdates);
+            atomicAdd(args.counters + 4, (unsigned long long)revals);
+        }
+
+        // ---- store the three maps ------------------------------------------------------------------
+        if (inside) {
+            const uint64_t o = F.out_off + (uint64_t)py * (uint64_t)W + (uint64_t)px;
+            const uint64_t hw = (uint64_t)H * (uint64_t)W;
+            uint8_t st = kStOk;
+            if (!valid)
+                st = kStBorder;
+            else if (!nonzero || !found_all)
+                st = kStDegenerate;
+            else if (!pconv || !rconv_all)
+                st = kStNotConverged;
+            const float w0 = (float)F.omega_ref;
+            float dx = F.carrier_axis == 0 ? wrap_pi(om_x - w0) : wrap_pi(om_x);
+            float dy = F.carrier_axis == 1 ? wrap_pi(om_y - w0) : wrap_pi(om_y);
+            // carrier phase at the pixel: 2 pi frac(f0 X), X its coordinate along the carrier
+            double t = F.f0 * (double)(F.carrier_axis == 0 ? px : py);
+            t -= floor(t);
+            float al = wrap_pi(atan2f(acc.i, acc.r) - (float)(6.283185307179586477 * t));
+            if (st == kStBorder || st == kStDegenerate) {
+                const float qnan = __int_as_float(0x7fc00000);
+                dx = dy = al = qnan;
+            }
+            out[o] = dx;
+            out[o + hw] = dy;
+            out[o + 2 * hw] = al;
+            if (status) status[o] = st;
+        }
+    }
+}
+
+}  // namespace rmusic

@@ -1,0 +1,9 @@
+// square_l6.cu -- instantiations of the square-block solver for half-width(s) 6, both register-cap variants (square_variants.h).
+#include "square_kernel.cuh"
+#include "square_variants.h"
+
+namespace rmusic {
+
+RMUSIC_DEFINE_SQUARE(6)
+
+}  // namespace rmusic

@@ -30,6 +30,11 @@ RMUSIC_FP32_BATCHED = 2
 
 RMUSIC_DTYPE_F32 = 0
 RMUSIC_DTYPE_U16 = 1
+RMUSIC_DTYPE_C64 = 2
+
+RMUSIC_GEOM_ROW = 0
+RMUSIC_GEOM_SQUARE = 1
+GEOMETRIES = {"row": RMUSIC_GEOM_ROW, "square": RMUSIC_GEOM_SQUARE}
 
 STATUS_OK, STATUS_BORDER, STATUS_DEGENERATE, STATUS_NOT_CONVERGED = 0, 1, 2, 3
 
@@ -54,6 +59,8 @@ class rmusic_params(ctypes.Structure):
         ("use_graph", ctypes.c_int32),
         ("timing", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("geometry", ctypes.c_int32),
+        ("half_width", ctypes.c_int32),
     ]
 
 
@@ -79,6 +86,7 @@ class rmusic_stats(ctypes.Structure):
         ("mean_sweeps", ctypes.c_double),
         ("mean_root_iters", ctypes.c_double),
         ("mean_root_updates", ctypes.c_double),
+        ("mean_root_evals", ctypes.c_double),
         ("bandpass_ms", ctypes.c_float),
         ("solver_ms", ctypes.c_float),
         ("solver_ctas_per_sm", ctypes.c_int32),
@@ -234,16 +242,18 @@ def rmusic_get_stats(ctx) -> rmusic_stats:
 def make_params(window_len=32, cov_order=8, forward_backward=1, deriv_axis=0, carrier_axis=0,
                 carrier_freq=0.1, band_halfwidth=0.0, precision="batched", max_sweeps=0,
                 max_root_iters=0, polish_fp64=0, use_graph=0, timing=0, autotune=0,
-                model_order=1) -> rmusic_params:
+                model_order=1, geometry="row", half_width=0) -> rmusic_params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    geom = GEOMETRIES[geometry] if isinstance(geometry, str) else int(geometry)
     return rmusic_params(window_len, cov_order, model_order, forward_backward, deriv_axis, carrier_axis,
                          float(carrier_freq), float(band_halfwidth), prec, max_sweeps, max_root_iters,
-                         polish_fp64, use_graph, timing, autotune)
+                         polish_fp64, use_graph, timing, autotune, geom, half_width)
 
 
-def frame_descs(shapes, dtype_code: int, elem_bytes: int, windows=None):
+def frame_descs(shapes, dtype_code: int, elem_bytes: int, windows=None, maps: int = 1):
     """Descriptors for frames packed back to back (frame f after frame f-1) and maps packed the same
-    way. ``shapes`` is a list of (H, W); ``windows`` an optional list of (N, L) per frame."""
+    way. ``shapes`` is a list of (H, W); ``windows`` an optional list of (N, L) per frame; ``maps``
+    the maps a frame writes (3 in the square geometry: d/dx, d/dy, alpha)."""
     descs = (rmusic_frame_desc * max(len(shapes), 1))()
     off = 0
     oo = 0
@@ -251,13 +261,16 @@ def frame_descs(shapes, dtype_code: int, elem_bytes: int, windows=None):
         N, L = windows[i] if windows is not None else (0, 0)
         descs[i] = rmusic_frame_desc(off, H, W, 0, dtype_code, oo, N, L)
         off += H * W * elem_bytes
-        oo += H * W
+        oo += maps * H * W
     return descs, off, oo
 
 
 class Demodulator:
     """Owns one rmusic context. ``run`` takes a CUDA tensor of frames (T, H, W) or a list of 2-D
-    CUDA tensors of uneven sizes, and returns the derivative maps (and status maps)."""
+    CUDA tensors of uneven sizes (float32, uint16 or complex64), and returns the flat map buffer,
+    the status buffer and the shapes. Row geometry: one derivative map per frame. Square geometry:
+    three maps per frame (d/dx, d/dy, alpha), frame f's block of 3 H W floats after frame f-1's;
+    the status buffer has the same length, frame f's status map at the start of its block."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, **params):
         self.params = make_params(**params)
@@ -294,9 +307,12 @@ class Demodulator:
             code, esz = RMUSIC_DTYPE_U16, 2
         elif flat.dtype == torch.int16:
             code, esz = RMUSIC_DTYPE_U16, 2
+        elif flat.dtype == torch.complex64:
+            code, esz = RMUSIC_DTYPE_C64, 8
         else:
-            raise TypeError(f"frames must be float32 or uint16, got {flat.dtype}")
-        descs, _, nout = frame_descs(shapes, code, esz, windows)
+            raise TypeError(f"frames must be float32, uint16 or complex64, got {flat.dtype}")
+        maps = 3 if self.params.geometry == RMUSIC_GEOM_SQUARE else 1
+        descs, _, nout = frame_descs(shapes, code, esz, windows, maps)
         dev = flat.device
         if out is None:
             out = torch.empty(nout, dtype=torch.float32, device=dev)

@@ -130,7 +130,7 @@ def gaussian_sum(rng: np.random.Generator, H: int, W: int, n: int = 5, hi: float
 class Frame:
     """One synthetic frame and the parameters it is meant to be demodulated with."""
 
-    image: np.ndarray                    # float32 or uint16 (12-bit), H x W
+    image: np.ndarray                    # float32, uint16 (12-bit) or complex64, H x W
     carrier_freq: float
     deriv_axis: int = 0
     carrier_axis: int = 0
@@ -181,6 +181,23 @@ def diffusion_frame(t: int, T: int = 500, H: int = 1024, W: int = 1024, seed_ind
     img = quantize12(add_noise(fringe(phi, 0.1), sigma, rng))
     return Frame(img, 0.1, deriv_axis=1, truth=dy,
                  meta={"workload": f"diffusion t={t}/{T} {H}x{W} Dt={Dt:.1f}"})
+
+
+def complex_fringe_frame(snr_db: float = 0.0, H: int = 512, W: int = 512, hi: float = 10.0, f0: float = 0.0,
+                         seed_index: int = 5, stream: int = 0) -> Frame:
+    """Complex fringe A exp(j(2 pi f0 x + phi)) + circular complex Gaussian noise, as the paper
+    simulates it (Sec. 4: a 512 x 512 complex fringe at 0 dB), complex64. A = 1 and
+    SNR(dB) = 10 log10(A^2 / E|noise|^2); phi = peaks scaled to 0 .. hi rad (the paper's own map is
+    not given). truth is dphi/dx; meta holds dphi/dy and phi."""
+    rng = np.random.Generator(np.random.PCG64([SEED_BASE + seed_index, stream]))
+    phi, dx, dy = peaks(H, W, 0.0, hi)
+    x = np.arange(W, dtype=np.float64)[None, :]
+    g = np.exp(1j * (2.0 * math.pi * f0 * x + phi))
+    if math.isfinite(snr_db):
+        s = math.sqrt(0.5 * 10.0 ** (-snr_db / 10.0))
+        g = g + s * (rng.standard_normal((H, W)) + 1j * rng.standard_normal((H, W)))
+    return Frame(g.astype(np.complex64), f0, truth=dx,
+                 meta={"workload": f"complex peaks {H}x{W} 0-{hi} rad snr={snr_db}dB", "truth_dy": dy, "phi": phi})
 
 
 UNEVEN_HEIGHTS = (256, 512, 768, 1024, 2048)

@@ -55,14 +55,16 @@ def test_struct_layout_matches_header(tmp_path):
         " offsetof(rmusic_params, precision), offsetof(rmusic_params, use_graph), sizeof(rmusic_frame_desc));\n"
         'printf("%zu %zu %zu\\n", offsetof(rmusic_frame_desc, out_offset), offsetof(rmusic_frame_desc, cov_order),'
         " sizeof(rmusic_stats));\n"
+        'printf("%zu %zu\\n", offsetof(rmusic_params, geometry), offsetof(rmusic_params, half_width));\n'
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
     P, D, S = rmusic.rmusic_params, rmusic.rmusic_frame_desc, rmusic.rmusic_stats
     assert list(map(int, a.split())) == [ctypes.sizeof(P), P.carrier_freq.offset, P.precision.offset,
                                          P.use_graph.offset, ctypes.sizeof(D)]
     assert list(map(int, b.split())) == [D.out_offset.offset, D.cov_order.offset, ctypes.sizeof(S)]
+    assert list(map(int, c.split())) == [P.geometry.offset, P.half_width.offset]
 
 
 def test_argument_checks_without_cuda(lib):
@@ -79,4 +81,12 @@ def test_argument_checks_without_cuda(lib):
     ctx = ctypes.c_void_p()
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EUNSUPPORTED
     bad = rmusic.make_params(window_len=8, cov_order=12)
+    assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
+    # the square block: half-width 1 .. 8, FP32-batched only
+    for hw in (0, 9):
+        bad = rmusic.make_params(geometry="square", half_width=hw)
+        assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
+    bad = rmusic.make_params(geometry="square", half_width=5, precision="plain_fp32")
+    assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EUNSUPPORTED
+    bad = rmusic.make_params(geometry=2)
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
