@@ -131,6 +131,10 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_demodulate_pixels.argtypes = [ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(Params),
                                         i32, ip, ip, dp, ctypes.c_void_p, i32]
     L.orc_max_threads.argtypes = []
+    fp = ctypes.POINTER(ctypes.c_float)
+    L.orc_unwrap_reliability.argtypes = [fp, i32, i32, fp]
+    L.orc_unwrap_reliability.restype = None
+    L.orc_unwrap.argtypes = [fp, i32, i32, dp, ip]
     L.orc_square_window_ri.argtypes = [dp, i32, ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
     L.orc_square_demodulate.argtypes = [ctypes.c_void_p, i32, i32, i32, ctypes.POINTER(Params), i32,
                                         dp, dp, dp, ctypes.c_void_p, i32]
@@ -331,6 +335,33 @@ def square_demodulate_pixels(frame: np.ndarray, params: Params, Lp: int, ys, xs,
     if used < 0:
         raise ValueError(f"oracle rejected the input (code {used})")
     return dx, dy, al, st, used
+
+
+# ---------------------------------------------------------------------------------------------
+# Phase assembly: the reliability-sorting unwrapper the paper cites (Sec. 3)
+# ---------------------------------------------------------------------------------------------
+def unwrap_reliability(phi) -> np.ndarray:
+    """Reliability map (float32) of a wrapped float32 map (NaN = no value)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    H, W = phi.shape
+    R = np.empty_like(phi)
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib().orc_unwrap_reliability(phi.ctypes.data_as(fp), H, W, R.ctypes.data_as(fp))
+    return R
+
+
+def unwrap(phi):
+    """Unwrap a wrapped float32 map (NaN = no value). Returns (unwrapped float64, k int32 with
+    unwrapped = phi + 2 pi k, number of groups left)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    H, W = phi.shape
+    out = np.empty((H, W))
+    k = np.empty((H, W), dtype=np.int32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    n = lib().orc_unwrap(phi.ctypes.data_as(fp), H, W, _dp(out), k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if n < 0:
+        raise MemoryError("oracle unwrap: allocation failed")
+    return out, k, n
 
 
 def max_threads() -> int:

@@ -916,6 +916,150 @@ int orc_square_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, in
     return used;
 }
 
+/* =================================================================================
+ * Phase assembly (Sec. 3: the local phases alpha are followed by an unwrapping operation,
+ * the reliability-sorting method of Herraez et al., Appl. Opt. 41, 7437 (2002), which the
+ * paper cites). On a wrapped map phi (H x W, row-major; NaN = no value):
+ *   - the wrap operator g(x) maps a difference of two wrapped values into (-pi, pi];
+ *   - reliability of a pixel whose 8 neighbours all hold values: R = 1 / D with
+ *       D^2 = H^2 + V^2 + D1^2 + D2^2, the second differences
+ *       H  = g(phi[i][j-1] - phi[i][j]) - g(phi[i][j] - phi[i][j+1]),
+ *       V  = g(phi[i-1][j] - phi[i][j]) - g(phi[i][j] - phi[i+1][j]),
+ *       D1 = g(phi[i-1][j-1] - phi[i][j]) - g(phi[i][j] - phi[i+1][j+1]),
+ *       D2 = g(phi[i-1][j+1] - phi[i][j]) - g(phi[i][j] - phi[i+1][j-1]);
+ *     every other pixel with a value has R = 0 (reading: no second difference, least reliable);
+ *   - an edge joins horizontally or vertically adjacent pixels that both hold values; its
+ *     reliability is the sum of theirs; edges are taken from the most reliable down (equal
+ *     reliabilities by edge index 2 (i W + j) + (0 right, 1 down), smaller first);
+ *   - each pixel starts as its own group; an edge joining two groups shifts every pixel of the
+ *     smaller group (the second endpoint's on equal sizes) by the multiple of 2 pi that makes the
+ *     two endpoints differ by the wrapped difference g(phi_q - phi_p); the groups merge.
+ * The reliabilities and the 2 pi jumps are decided in float32, the precision of the GPU path
+ * whose result this is compared with (the wrapped input is float32 on both sides).
+ * ================================================================================= */
+#define ORC_PI_F 3.14159265358979f
+#define ORC_TWO_PI_F 6.28318530717959f
+
+static float orc_gam_f(float x) {
+    if (x > ORC_PI_F) return x - ORC_TWO_PI_F;
+    if (x <= -ORC_PI_F) return x + ORC_TWO_PI_F;
+    return x;
+}
+
+/* Reliability map R[H*W] of a wrapped map (R = 0 where a neighbour is missing; NaN where
+   phi itself has no value). */
+void orc_unwrap_reliability(const float* phi, int32_t H, int32_t W, float* R) {
+    for (int32_t i = 0; i < H; ++i)
+        for (int32_t j = 0; j < W; ++j) {
+            float c = phi[(size_t)i * W + j];
+            if (isnan(c)) { R[(size_t)i * W + j] = NAN; continue; }
+            int inner = i >= 1 && i + 1 < H && j >= 1 && j + 1 < W;
+            if (inner)
+                for (int di = -1; di <= 1; ++di)
+                    for (int dj = -1; dj <= 1; ++dj)
+                        if (isnan(phi[(size_t)(i + di) * W + (j + dj)])) inner = 0;
+            if (!inner) { R[(size_t)i * W + j] = 0.0f; continue; }
+#define PH(a, b) phi[(size_t)(i + (a)) * W + (j + (b))]
+            float h = orc_gam_f(PH(0, -1) - c) - orc_gam_f(c - PH(0, 1));
+            float v = orc_gam_f(PH(-1, 0) - c) - orc_gam_f(c - PH(1, 0));
+            float d1 = orc_gam_f(PH(-1, -1) - c) - orc_gam_f(c - PH(1, 1));
+            float d2 = orc_gam_f(PH(-1, 1) - c) - orc_gam_f(c - PH(1, -1));
+#undef PH
+            float hh = h * h;
+            float vv = v * v;
+            float aa = d1 * d1;
+            float bb = d2 * d2;
+            float d = sqrtf(((hh + vv) + aa) + bb);
+            R[(size_t)i * W + j] = 1.0f / d;
+        }
+}
+
+typedef struct {
+    float w;
+    int64_t e;
+} orc_edge;
+
+static int orc_edge_cmp(const void* a, const void* b) {
+    const orc_edge* x = (const orc_edge*)a;
+    const orc_edge* y = (const orc_edge*)b;
+    if (x->w > y->w) return -1;
+    if (x->w < y->w) return 1;
+    return x->e < y->e ? -1 : (x->e > y->e ? 1 : 0);
+}
+
+/* Unwrap phi (H x W float32, NaN = no value) into out (double, NaN where phi is NaN) and the
+   integer map k (out = phi + 2 pi k; 0 where NaN). Returns the number of groups left (the
+   connected components of the pixels with values), or < 0 on allocation failure. */
+int orc_unwrap(const float* phi, int32_t H, int32_t W, double* out, int32_t* k) {
+    size_t n = (size_t)H * W;
+    float* R = (float*)malloc(sizeof(float) * n);
+    orc_edge* E = (orc_edge*)malloc(sizeof(orc_edge) * 2 * n + 1);
+    int32_t* group = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* next = (int32_t*)malloc(sizeof(int32_t) * n);  /* member list of each group */
+    int32_t* last = (int32_t*)malloc(sizeof(int32_t) * n);
+    int32_t* size = (int32_t*)malloc(sizeof(int32_t) * n);
+    if (!R || !E || !group || !next || !last || !size) {
+        free(R); free(E); free(group); free(next); free(last); free(size);
+        return -2;
+    }
+    orc_unwrap_reliability(phi, H, W, R);
+    size_t ne = 0;
+    int ngroups = 0;
+    for (int32_t i = 0; i < H; ++i)
+        for (int32_t j = 0; j < W; ++j) {
+            size_t p = (size_t)i * W + j;
+            k[p] = 0;
+            group[p] = (int32_t)p;
+            next[p] = -1;
+            last[p] = (int32_t)p;
+            size[p] = 1;
+            if (isnan(phi[p])) continue;
+            ++ngroups;
+            if (j + 1 < W && !isnan(phi[p + 1])) {
+                E[ne].w = R[p] + R[p + 1];
+                E[ne].e = 2 * (int64_t)p;
+                ++ne;
+            }
+            if (i + 1 < H && !isnan(phi[p + W])) {
+                E[ne].w = R[p] + R[p + W];
+                E[ne].e = 2 * (int64_t)p + 1;
+                ++ne;
+            }
+        }
+    qsort(E, ne, sizeof(orc_edge), orc_edge_cmp);
+    for (size_t t = 0; t < ne; ++t) {
+        size_t p = (size_t)(E[t].e / 2);
+        size_t q = (E[t].e % 2) ? p + W : p + 1;
+        int32_t gp = group[p], gq = group[q];
+        if (gp == gq) continue;
+        /* k_q - k_p must equal the jump s of the wrapped difference phi_q - phi_p */
+        float dq = phi[q] - phi[p];
+        int32_t s = dq > ORC_PI_F ? -1 : (dq <= -ORC_PI_F ? 1 : 0);
+        int32_t shift, from, into;
+        if (size[gq] <= size[gp]) {
+            shift = k[p] + s - k[q];  /* added to every pixel of q's group */
+            from = gq;
+            into = gp;
+        } else {
+            shift = k[q] - s - k[p];  /* added to every pixel of p's group */
+            from = gp;
+            into = gq;
+        }
+        for (int32_t m = from; m >= 0; m = next[m]) {
+            k[m] += shift;
+            group[m] = into;
+        }
+        next[last[into]] = from;
+        last[into] = last[from];
+        size[into] += size[from];
+        --ngroups;
+    }
+    for (size_t p = 0; p < n; ++p)
+        out[p] = isnan(phi[p]) ? NAN : (double)phi[p] + 2.0 * ORC_PI * (double)k[p];
+    free(R); free(E); free(group); free(next); free(last); free(size);
+    return ngroups;
+}
+
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */
 int orc_max_threads(void) {
 #ifdef _OPENMP

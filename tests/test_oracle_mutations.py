@@ -1,6 +1,6 @@
 """Planted mistakes: each test copies the oracle's C source, plants one plausible error (a dropped
 conjugate, a transposed operand, a wrong index or sign), compiles the copy on the CPU and checks
-that the pins in test_oracle_pins.py and test_oracle_square.py reject it. This shows the pins constrain every step of the
+that the pins in test_oracle_pins.py, test_oracle_square.py and test_oracle_unwrap.py reject it. This shows the pins constrain every step of the
 oracle rather than only re-running it."""
 import numpy as np
 import pytest
@@ -8,6 +8,7 @@ import pytest
 import oracle as O
 import test_oracle_pins as P
 import test_oracle_square as S
+import test_oracle_unwrap as U
 
 MUTATIONS = {
     "band: negative side kept": ("fabs((double)k / (double)W - f0) < B", "fabs((double)k / (double)W + f0) < B"),
@@ -44,6 +45,15 @@ MUTATIONS = {
                                       "size_t idx = (size_t)(y - Lp + c) * W + (size_t)(x - Lp + r);"),
     "square: carrier taken from the wrong axis": ("double t = p->carrier_freq * (double)(p->carrier_axis == 0 ? x : y);",
                                                   "double t = p->carrier_freq * (double)(p->carrier_axis == 0 ? y : x);"),
+    # phase assembly (the reliability-sorting unwrapper)
+    "unwrap: least reliable edge first": ("    if (x->w > y->w) return -1;\n    if (x->w < y->w) return 1;",
+                                          "    if (x->w > y->w) return 1;\n    if (x->w < y->w) return -1;"),
+    "unwrap: jump sign": ("int32_t s = dq > ORC_PI_F ? -1 : (dq <= -ORC_PI_F ? 1 : 0);",
+                          "int32_t s = dq > ORC_PI_F ? 1 : (dq <= -ORC_PI_F ? -1 : 0);"),
+    "unwrap: reliability not inverted": ("R[(size_t)i * W + j] = 1.0f / d;", "R[(size_t)i * W + j] = d;"),
+    "unwrap: second difference sign": ("float h = orc_gam_f(PH(0, -1) - c) - orc_gam_f(c - PH(0, 1));",
+                                       "float h = orc_gam_f(PH(0, -1) - c) + orc_gam_f(c - PH(0, 1));"),
+    "unwrap: group shift sign": ("shift = k[p] + s - k[q];", "shift = k[q] + s - k[p];"),
 }
 
 PINS = [
@@ -68,6 +78,10 @@ PINS = [
     lambda: S.test_square_eigenvectors_are_singular_vectors(3),
     lambda: S.test_square_angles_by_enumeration(2),
     S.test_square_alpha_is_least_squares_phase,
+    lambda: U.test_unwrap_smooth_maps_exact(0),
+    U.test_unwrap_single_row_is_numpy_unwrap,
+    U.test_reliability_closed_form_quadratic,
+    lambda: U.test_unwrap_is_max_spanning_tree_integration(0),
 ]
 
 
