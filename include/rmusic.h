@@ -101,6 +101,9 @@ extern "C" {
  *   half_width       square geometry: Lp, the block is (2 Lp + 1) x (2 Lp + 1) (1 <= Lp <= 8).
  *                    A pixel whose block leaves the frame is a border pixel. max_sweeps then caps
  *                    the power-iteration steps of the block's singular vectors (0 = 100).
+ *   unwrap           square geometry only: 1 also assembles the phase map (Sec. 3: the local
+ *                    phases are unwrapped with the reliability-sorting method the paper cites) and
+ *                    writes it as a fourth map per frame (see rmusic_unwrap_phase).
  * carrier_freq may be 0 (no carrier) for complex frames; for real frames it must lie in (0, 0.5).
  */
 typedef struct {
@@ -121,6 +124,7 @@ typedef struct {
     int32_t autotune;
     int32_t geometry;
     int32_t half_width;
+    int32_t unwrap;
 } rmusic_params;
 
 /* One frame of a batch. Frames of one call may differ in size, type and window.
@@ -132,8 +136,9 @@ typedef struct {
  *   out_offset    element offset of the frame's dense H x W float32 map (row-major) in the
  *                 output buffer, and of its H x W uint8 map in the status buffer. In the square
  *                 geometry a frame writes three maps: d/dx at out_offset, d/dy at
- *                 out_offset + H W and alpha at out_offset + 2 H W (3 H W floats), and its
- *                 status map at out_offset of the status buffer.
+ *                 out_offset + H W and alpha at out_offset + 2 H W (3 H W floats; with
+ *                 params.unwrap = 1 a fourth map, the unwrapped phase, at out_offset + 3 H W),
+ *                 and its status map at out_offset of the status buffer.
  *   window_len, cov_order  per-frame N and L; 0 = the context's parameters.
  */
 typedef struct {
@@ -214,6 +219,25 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
 int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int device, const void* d_frames,
                                      const rmusic_frame_desc* descs, int32_t n_frames, float* d_out,
                                      uint8_t* d_status, void* cuda_stream);
+
+/* Phase assembly (Sec. 3: the local phases are followed by an unwrapping operation, the
+ * reliability-sorting method of Herraez et al. 2002 that the paper cites). Unwraps n_frames wrapped
+ * phase maps, e.g. the alpha maps of the square geometry:
+ *   d_phase  device float32 buffer; frame f's H x W map (row-major) at d_phase + descs[f].out_offset,
+ *            values in (-pi, pi], NaN where a pixel has no value (border pixels).
+ *   d_out    device float32 buffer; frame f's unwrapped map at d_out + descs[f].out_offset, NaN
+ *            where the input is NaN. d_out may equal d_phase (in place).
+ *   descs    HOST array; only height, width and out_offset are read.
+ * Pixels with values that touch horizontally or vertically form regions; each region is unwrapped
+ * as the method does (edges taken by decreasing reliability, the reliability of a pixel being the
+ * inverse of its wrapped second differences, 0 where a neighbour has no value) and then shifted so
+ * that its first pixel in row-major order keeps its wrapped value. Reliabilities and 2 pi jumps
+ * are decided in float32. The work is a fixed sequence of kernels (about 4 + 25 log2(H W) launches
+ * for the largest frame), queued on cuda_stream. Total pixels of a call: below 2^31.
+ * Errors: RMUSIC_EINVAL, RMUSIC_ENOMEM (workspace of 36 bytes per pixel over the budget),
+ * RMUSIC_ECUDA. */
+int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
+                        float* d_out, void* cuda_stream);
 
 /* Destroy a context and free everything it owns. NULL is allowed. Waits for the context's
  * outstanding work on its device. */

@@ -98,6 +98,9 @@ struct rmusic_ctx {
     size_t out_cap = 0;
     uint8_t* d_st = nullptr;
     size_t st_cap = 0;
+    // phase-assembly workspace
+    void* d_unwrap = nullptr;
+    size_t unwrap_cap = 0;
     // graphs
     GraphEntry graphs[kMaxGraphs];
     uint64_t graph_clock = 0;
@@ -141,6 +144,8 @@ bool params_ok(const rmusic_params& p) {
         return false;
     }
     if (p.carrier_axis != 0 && p.carrier_axis != 1) return false;
+    if (p.unwrap != 0 && p.unwrap != 1) return false;
+    if (p.unwrap && p.geometry != RMUSIC_GEOM_SQUARE) return false;
     if (!(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5)) return false;
     if (!(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5)) return false;
     if (p.precision < RMUSIC_PLAIN_FP64 || p.precision > RMUSIC_FP32_BATCHED) return false;
@@ -529,6 +534,13 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
             ctx->stats.solver_ctas_per_sm = solver_ctas(L, v);
             ++*launches;
         }
+        if (p.unwrap) {
+            // phase assembly: the alpha maps (third map) unwrapped into the fourth map
+            int64_t maxpx = 0;
+            for (const FrameDev& F : plan.frames) maxpx = std::max<int64_t>(maxpx, (int64_t)F.H * F.W);
+            RM_CUDA(launch_unwrap(ctx->d_table, n, (int64_t)plan.gamma_elems, maxpx, d_out, 2, d_out, 3,
+                                  ctx->d_unwrap, launches, s));
+        }
     } else {
         PlainArgs a;
         a.fb = p.forward_backward;
@@ -584,6 +596,13 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
     if (rc) return rc;
     rc = ensure_tables(ctx, plan.frames.size());
     if (rc) return rc;
+    if (ctx->p.unwrap) {
+        int64_t maxpx = 0;
+        for (const FrameDev& F : plan.frames) maxpx = std::max<int64_t>(maxpx, (int64_t)F.H * F.W);
+        if (plan.gamma_elems >= (1ull << 31)) return RMUSIC_EINVAL;
+        rc = ensure(ctx, &ctx->d_unwrap, &ctx->unwrap_cap, unwrap_workspace_bytes((int64_t)plan.gamma_elems, maxpx));
+        if (rc) return rc;
+    }
 
     // autotune: time the solver variants on this call's work (band-pass first, outside any graph)
     if (ctx->p.precision == RMUSIC_FP32_BATCHED && (force_tune || ctx->p.autotune)) {
@@ -809,7 +828,7 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
     DeviceGuard guard(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     uint64_t out_elems = 0, st_elems = 0;
-    const int maps = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? 3 : 1;  // maps per frame
+    const int maps = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? 3 + ctx->p.unwrap : 1;  // maps per frame
     for (int i = 0; i < n_frames; ++i) {
         const rmusic_frame_desc& d = descs[i];
         if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
@@ -846,6 +865,43 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
     return RMUSIC_OK;
 }
 
+int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
+                        float* d_out, void* cuda_stream) {
+    if (!ctx || n_frames < 0) return RMUSIC_EINVAL;
+    if (n_frames == 0) return RMUSIC_OK;
+    if (!d_phase || !descs || !d_out) return RMUSIC_EINVAL;
+    DeviceGuard guard(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<FrameDev> frames((size_t)n_frames);
+    uint64_t npx = 0;
+    int64_t maxpx = 0;
+    for (int i = 0; i < n_frames; ++i) {
+        const rmusic_frame_desc& d = descs[i];
+        if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
+        FrameDev& F = frames[(size_t)i];
+        memset(&F, 0, sizeof(F));
+        F.H = d.height;
+        F.W = d.width;
+        F.out_off = d.out_offset;
+        F.gam_off = npx;  // first pixel of the frame in the call's pixel numbering
+        npx += (uint64_t)d.height * (uint64_t)d.width;
+        maxpx = std::max<int64_t>(maxpx, (int64_t)d.height * d.width);
+    }
+    if (npx >= (1ull << 31)) return RMUSIC_EINVAL;
+    int rc = ensure_tables(ctx, frames.size());
+    if (!rc) rc = ensure(ctx, &ctx->d_unwrap, &ctx->unwrap_cap, unwrap_workspace_bytes((int64_t)npx, maxpx));
+    if (rc) return rc;
+    RM_CUDA(cudaEventSynchronize(ctx->table_free));
+    memcpy(ctx->h_table, frames.data(), frames.size() * sizeof(FrameDev));
+    RM_CUDA(cudaMemcpyAsync(ctx->d_table, ctx->h_table, frames.size() * sizeof(FrameDev), cudaMemcpyHostToDevice, s));
+    RM_CUDA(cudaEventRecord(ctx->table_free, s));
+    int launches = 0;
+    RM_CUDA(launch_unwrap(ctx->d_table, n_frames, (int64_t)npx, maxpx, d_phase, 0, d_out, 0, ctx->d_unwrap,
+                          &launches, s));
+    ctx->stats.kernel_launches = launches;
+    return RMUSIC_OK;
+}
+
 void rmusic_destroy(rmusic_ctx* ctx) {
     if (!ctx) return;
     {
@@ -866,6 +922,7 @@ void rmusic_destroy(rmusic_ctx* ctx) {
         if (ctx->d_in) cudaFree(ctx->d_in);
         if (ctx->d_out) cudaFree(ctx->d_out);
         if (ctx->d_st) cudaFree(ctx->d_st);
+        if (ctx->d_unwrap) cudaFree(ctx->d_unwrap);
     }
     delete ctx;
 }

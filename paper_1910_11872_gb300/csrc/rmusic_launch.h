@@ -67,4 +67,13 @@ cudaError_t launch_square(int Lp, int v, const FrameDev* d_frames, int nframes, 
                           uint8_t* d_status, SquareArgs a, int grid, cudaStream_t stream);
 int square_grid(int Lp, int v, int device);
 
+// Phase assembly (unwrap.cu): unwraps the wrapped map of every frame of the table (frame f's
+// pixels are g = F.gam_off .. F.gam_off + H W - 1; its input map at in + F.out_off + in_maps H W,
+// its output at out + F.out_off + out_maps H W; NaN = no value). work must hold
+// unwrap_workspace_bytes(npx, max_frame_px) bytes; npx < 2^31.
+size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_px);
+cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_px,
+                          const float* in, int64_t in_maps, float* out, int64_t out_maps, void* work,
+                          int* launches, cudaStream_t s);
+
 }  // namespace rmusic

@@ -61,6 +61,7 @@ class rmusic_params(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("geometry", ctypes.c_int32),
         ("half_width", ctypes.c_int32),
+        ("unwrap", ctypes.c_int32),
     ]
 
 
@@ -142,6 +143,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_strerror.restype = ctypes.c_char_p
         lib.rmusic_last_cuda_error.argtypes = [vp]
         lib.rmusic_last_cuda_error.restype = ctypes.c_char_p
+        lib.rmusic_unwrap_phase.argtypes = [vp, vp, ctypes.POINTER(rmusic_frame_desc), i32, vp, vp]
+        lib.rmusic_unwrap_phase.restype = ctypes.c_int
         lib.rmusic_get_stats.argtypes = [vp, ctypes.POINTER(rmusic_stats)]
         lib.rmusic_get_stats.restype = ctypes.c_int
         _lib = lib
@@ -218,6 +221,15 @@ def rmusic_autotune(ctx, d_frames: int, descs, n_frames: int, d_out: int, d_stat
     return rc
 
 
+def rmusic_unwrap_phase(ctx, d_phase: int, descs, n_frames: int, d_out: int, cuda_stream: int | None) -> int:
+    arr = _desc_array(descs)
+    rc = load_library().rmusic_unwrap_phase(ctx, d_phase or None, arr, int(n_frames), d_out or None,
+                                            cuda_stream or None)
+    if rc != RMUSIC_OK:
+        raise RmusicError(rc, "rmusic_unwrap_phase", rmusic_last_cuda_error(ctx))
+    return rc
+
+
 def rmusic_destroy(ctx) -> None:
     if ctx:
         load_library().rmusic_destroy(ctx)
@@ -242,12 +254,12 @@ def rmusic_get_stats(ctx) -> rmusic_stats:
 def make_params(window_len=32, cov_order=8, forward_backward=1, deriv_axis=0, carrier_axis=0,
                 carrier_freq=0.1, band_halfwidth=0.0, precision="batched", max_sweeps=0,
                 max_root_iters=0, polish_fp64=0, use_graph=0, timing=0, autotune=0,
-                model_order=1, geometry="row", half_width=0) -> rmusic_params:
+                model_order=1, geometry="row", half_width=0, unwrap=0) -> rmusic_params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     geom = GEOMETRIES[geometry] if isinstance(geometry, str) else int(geometry)
     return rmusic_params(window_len, cov_order, model_order, forward_backward, deriv_axis, carrier_axis,
                          float(carrier_freq), float(band_halfwidth), prec, max_sweeps, max_root_iters,
-                         polish_fp64, use_graph, timing, autotune, geom, half_width)
+                         polish_fp64, use_graph, timing, autotune, geom, half_width, unwrap)
 
 
 def frame_descs(shapes, dtype_code: int, elem_bytes: int, windows=None, maps: int = 1):
@@ -269,8 +281,9 @@ class Demodulator:
     """Owns one rmusic context. ``run`` takes a CUDA tensor of frames (T, H, W) or a list of 2-D
     CUDA tensors of uneven sizes (float32, uint16 or complex64), and returns the flat map buffer,
     the status buffer and the shapes. Row geometry: one derivative map per frame. Square geometry:
-    three maps per frame (d/dx, d/dy, alpha), frame f's block of 3 H W floats after frame f-1's;
-    the status buffer has the same length, frame f's status map at the start of its block."""
+    three maps per frame (d/dx, d/dy, alpha; a fourth, the unwrapped phase, with unwrap=1), frame
+    f's block after frame f-1's; the status buffer has the same length, frame f's status map at the
+    start of its block."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, **params):
         self.params = make_params(**params)
@@ -311,7 +324,7 @@ class Demodulator:
             code, esz = RMUSIC_DTYPE_C64, 8
         else:
             raise TypeError(f"frames must be float32, uint16 or complex64, got {flat.dtype}")
-        maps = 3 if self.params.geometry == RMUSIC_GEOM_SQUARE else 1
+        maps = 3 + self.params.unwrap if self.params.geometry == RMUSIC_GEOM_SQUARE else 1
         descs, _, nout = frame_descs(shapes, code, esz, windows, maps)
         dev = flat.device
         if out is None:
