@@ -1,0 +1,52 @@
+"""Trend checks of the oracle against the paper's accuracy results (Sec. 4). The paper's simulated
+phase map is not given, so its numbers cannot be reproduced (parity of Tables 1-2 is unpinned);
+what it fixes is the shape of its results, checked here on the synthetic stand-in (a 512 x 512
+complex fringe, phi = peaks scaled to 0-150 rad, the paper's 0 dB):
+  * Table 1: the phase error against the half-width L falls steeply from L = 1, reaches its
+    minimum at a middle window (the paper: L = 4) and grows again for large windows, where the
+    local linear-phase model fails;
+  * Fig. 4: the error falls as the SNR rises.
+Errors are those of the local phase alpha on 1500 sampled pixels away from the borders.
+"""
+import numpy as np
+
+import oracle as O
+from paper_1910_11872_gb300 import experiments as E
+from paper_1910_11872_gb300 import synth
+
+
+def _alpha_rmse(fr, Lp, ys, xs):
+    _, _, al, st, _ = O.square_demodulate_pixels(fr.image, O.make_params(carrier_freq=0.0), Lp, ys, xs)
+    assert (st == 0).all()
+    return E.wrapped_rmse(al, fr.meta["phi"][ys, xs])
+
+
+def _samples(n=1500):
+    rng = np.random.default_rng(0)
+    return rng.integers(E.MARGIN, 512 - E.MARGIN, n), rng.integers(E.MARGIN, 512 - E.MARGIN, n)
+
+
+def test_error_against_half_width_has_the_papers_u_shape():
+    fr = synth.complex_fringe_frame(0.0, 512, 512, 150.0)
+    ys, xs = _samples()
+    r = [_alpha_rmse(fr, Lp, ys, xs) for Lp in range(1, 9)]
+    best = int(np.argmin(r)) + 1
+    assert 3 <= best <= 5, r
+    assert r[0] > 4 * min(r) and r[-1] > 1.5 * min(r), r
+    assert all(r[i] > r[i + 1] for i in range(best - 1)), r            # falling to the minimum
+    assert all(r[i] < r[i + 1] for i in range(best - 1, 7)), r         # rising after it
+
+
+def test_error_falls_with_snr():
+    ys, xs = _samples(800)
+    r = [_alpha_rmse(synth.complex_fringe_frame(s, 512, 512, 150.0), 4, ys, xs) for s in (-5.0, 0.0, 5.0, 10.0, 20.0)]
+    assert all(r[i] > r[i + 1] for i in range(len(r) - 1)), r
+
+
+def test_flatter_phase_moves_the_best_window_up():
+    """With a flatter phase (0-10 rad) the linear model holds over larger windows: the error keeps
+    falling up to the largest half-width, as the paper's explanation of Table 1 implies."""
+    fr = synth.complex_fringe_frame(0.0, 512, 512, 10.0)
+    ys, xs = _samples(800)
+    r = [_alpha_rmse(fr, Lp, ys, xs) for Lp in (2, 4, 6, 8)]
+    assert all(r[i] > r[i + 1] for i in range(3)), r
