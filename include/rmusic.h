@@ -232,9 +232,9 @@ int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int device, co
  * as the method does (edges taken by decreasing reliability, the reliability of a pixel being the
  * inverse of its wrapped second differences, 0 where a neighbour has no value) and then shifted so
  * that its first pixel in row-major order keeps its wrapped value. Reliabilities and 2 pi jumps
- * are decided in float32. The work is a fixed sequence of kernels (about 4 + 25 log2(H W) launches
- * for the largest frame), queued on cuda_stream. Total pixels of a call: below 2^31.
- * Errors: RMUSIC_EINVAL, RMUSIC_ENOMEM (workspace of 36 bytes per pixel over the budget),
+ * are decided in float32. The work is a fixed sequence of kernels (3 + 4 (ceil(log2(H W)) + 1)
+ * launches for the largest frame), queued on cuda_stream. Total pixels of a call: below 2^31.
+ * Errors: RMUSIC_EINVAL, RMUSIC_ENOMEM (workspace of 40 bytes per pixel over the budget),
  * RMUSIC_ECUDA. */
 int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
                         float* d_out, void* cuda_stream);

@@ -16,11 +16,13 @@
 //                hooks onto the component across it (of two components that chose the same edge
 //                the smaller label stays the root) with the integer shift that makes the edge's
 //                endpoints differ by their wrapped difference, the hooks are resolved to roots
-//                by pointer jumping (shifts summed along the way; parent and shift share one
-//                64-bit word, so a jump in place always reads a consistent pair), and every pixel
-//                is relabelled.
+//                by pointer jumping in place (shifts summed along the way; parent and shift share
+//                one 64-bit word, so a jump always reads a consistent pair), and every pixel is
+//                relabelled. Four launches per round; a round with nothing left to join makes
+//                the later rounds return at once.
 //                Each round at least halves the components, so ceil(log2(pixels)) rounds finish.
-//   anchor       each connected region keeps its first pixel (row-major) at its wrapped value.
+//   anchor       each connected region keeps its first pixel (row-major) at its wrapped value;
+//                every component carries its smallest pixel index through the merges.
 // All integer bookkeeping is exact; the output is phi + 2 pi k in float32.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -64,9 +66,10 @@ __device__ __forceinline__ const FrameDev& frame_of(const UwArgs& a, int64_t g, 
     return a.fr[f];
 }
 
-// wph[g] = wrapped phase, fid[g] = frame, comp[g] = g, kk[g] = 0
+// wph[g] = wrapped phase, fid[g] = frame, comp[g] = g, kk[g] = 0, minpix[g] = g
 __global__ void __launch_bounds__(kUwThreads) uw_init(UwArgs a, float* __restrict__ wph, int32_t* __restrict__ fid,
-                                                     int32_t* __restrict__ comp, int32_t* __restrict__ kk) {
+                                                     int32_t* __restrict__ comp, int32_t* __restrict__ kk,
+                                                     int32_t* __restrict__ minpix) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
         int f;
         const FrameDev& F = frame_of(a, g, &f);
@@ -75,6 +78,7 @@ __global__ void __launch_bounds__(kUwThreads) uw_init(UwArgs a, float* __restric
         fid[g] = f;
         comp[g] = (int32_t)g;
         kk[g] = 0;
+        minpix[g] = (int32_t)g;
     }
 }
 
@@ -174,29 +178,37 @@ __global__ void __launch_bounds__(kUwThreads) uw_hook(UwArgs a, const float* __r
     }
 }
 
-// one pointer-jumping step on the hook forest, in place: every (parent, shift) word read is a
-// consistent pair (a root's word never changes, other words only move up the same path), so a
-// component may jump over its parent whether or not the parent has already jumped this step.
-// Flags the next step while some component's new parent is not a root.
-__global__ void __launch_bounds__(kUwThreads) uw_jump(int64_t npx, const int32_t* __restrict__ comp,
-                                                     unsigned long long* hook, const int32_t* __restrict__ go,
-                                                     int32_t* __restrict__ go_next) {
-    if (!*go) return;
+// Resolves every hook chain to its root in place and clears the roots' best edges for the next
+// round. Each root component jumps over its parent until the parent is a root; many components do
+// so at once and help each other (every word read is a consistent (parent, shift) pair, so a
+// component may jump over a parent that has itself jumped already). Every jump moves strictly up
+// a chain of fewer than npx components, which bounds the loop.
+__global__ void __launch_bounds__(kUwThreads) uw_compress(int64_t npx, const int32_t* __restrict__ comp,
+                                                         unsigned long long* hook,
+                                                         unsigned long long* __restrict__ best,
+                                                         int32_t* __restrict__ minpix,
+                                                         const int32_t* __restrict__ hooked) {
+    if (!*hooked) return;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < npx; c += (int64_t)gridDim.x * blockDim.x) {
         if (comp[c] != (int32_t)c) continue;
-        const unsigned long long w = *(volatile unsigned long long*)(hook + c);
-        const int32_t p = hook_par(w);
-        if (p == (int32_t)c) continue;
-        const unsigned long long wp = *(volatile unsigned long long*)(hook + p);
-        const int32_t pp = hook_par(wp);
-        if (pp == p) continue;  // the parent is a root
-        *(volatile unsigned long long*)(hook + c) = pack_hook(pp, hook_sh(w) + hook_sh(wp));
-        const unsigned long long wq = *(volatile unsigned long long*)(hook + pp);
-        if (hook_par(wq) != pp) *go_next = 1;
+        best[c] = 0ull;
+        unsigned long long w = *(volatile unsigned long long*)(hook + c);
+        for (int64_t it = 0; it < npx; ++it) {
+            const int32_t p = hook_par(w);
+            if (p == (int32_t)c) break;  // c did not hook: a root of this round
+            const unsigned long long wp = *(volatile unsigned long long*)(hook + p);
+            const int32_t pp = hook_par(wp);
+            if (pp == p) break;  // the parent is a root
+            w = pack_hook(pp, hook_sh(w) + hook_sh(wp));
+            *(volatile unsigned long long*)(hook + c) = w;
+        }
+        // the root this component joins inherits its smallest pixel (roots of the round only
+        // receive, so minpix[c] is final here)
+        const int32_t r = hook_par(w);
+        if (r != (int32_t)c) atomicMin(minpix + r, minpix[c]);
     }
 }
 
-// relabel every pixel to its final root and add its component's accumulated shift
 __global__ void __launch_bounds__(kUwThreads) uw_relabel(int64_t npx, int32_t* __restrict__ comp,
                                                         int32_t* __restrict__ kk,
                                                         const unsigned long long* __restrict__ hook,
@@ -209,23 +221,16 @@ __global__ void __launch_bounds__(kUwThreads) uw_relabel(int64_t npx, int32_t* _
     }
 }
 
-__global__ void __launch_bounds__(kUwThreads) uw_first_pixel(int64_t npx, const float* __restrict__ wph,
-                                                            const int32_t* __restrict__ comp,
-                                                            int32_t* __restrict__ first) {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < npx; g += (int64_t)gridDim.x * blockDim.x)
-        if (!isnan(wph[g])) atomicMin(first + comp[g], (int32_t)g);
-}
-
 __global__ void __launch_bounds__(kUwThreads) uw_write(UwArgs a, const float* __restrict__ wph,
                                                       const int32_t* __restrict__ fid, const int32_t* __restrict__ comp,
-                                                      const int32_t* __restrict__ kk, const int32_t* __restrict__ first) {
+                                                      const int32_t* __restrict__ kk, const int32_t* __restrict__ minpix) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
         const FrameDev& F = a.fr[fid[g]];
         const int64_t local = g - (int64_t)F.gam_off;
         const float p = wph[g];
         float v = p;
         if (!isnan(p)) {
-            const int32_t k = kk[g] - kk[first[comp[g]]];
+            const int32_t k = kk[g] - kk[minpix[comp[g]]];
             v = __fadd_rn(p, __fmul_rn(kTwoPiF, (float)k));
         }
         a.out[F.out_off + a.out_maps * (int64_t)F.H * F.W + local] = v;
@@ -235,7 +240,8 @@ __global__ void __launch_bounds__(kUwThreads) uw_write(UwArgs a, const float* __
 // Workspace carved from one buffer; every array has npx entries.
 struct UwWork {
     float* wph;
-    float* rel;  // reliability; afterwards reused for each component's first pixel (int32)
+    float* rel;
+    int32_t* minpix;  // smallest pixel index of each component (at its root)
     int32_t* fid;
     int32_t* comp;
     int32_t* kk;
@@ -246,7 +252,7 @@ struct UwWork {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-UwWork carve(void* base, int64_t npx, int rounds, int jumps) {
+UwWork carve(void* base, int64_t npx, int rounds) {
     UwWork w;
     char* p = static_cast<char*>(base);
     auto take = [&](size_t bytes) {
@@ -260,8 +266,9 @@ UwWork carve(void* base, int64_t npx, int rounds, int jumps) {
     w.fid = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
     w.comp = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
     w.kk = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
+    w.minpix = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
     w.hook = reinterpret_cast<unsigned long long*>(take(8 * (size_t)npx));
-    w.flags = reinterpret_cast<int32_t*>(take(4 * (size_t)(rounds + 1) * (size_t)(jumps + 2)));
+    w.flags = reinterpret_cast<int32_t*>(take(4 * (size_t)(rounds + 1)));
     return w;
 }
 
@@ -276,17 +283,16 @@ int ceil_log2(int64_t n) {
 int unwrap_rounds(int64_t max_frame_px) { return ceil_log2(max_frame_px < 2 ? 2 : max_frame_px) + 1; }
 
 size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_px) {
-    const int R = unwrap_rounds(max_frame_px), J = R + 1;
-    return 2 * align256(8 * (size_t)npx) + 5 * align256(4 * (size_t)npx) +
-           align256(4 * (size_t)(R + 1) * (size_t)(J + 2));
+    const int R = unwrap_rounds(max_frame_px);
+    return 2 * align256(8 * (size_t)npx) + 6 * align256(4 * (size_t)npx) + align256(4 * (size_t)(R + 1));
 }
 
 cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_px,
                           const float* in, int64_t in_maps, float* out, int64_t out_maps, void* work,
                           int* launches, cudaStream_t s) {
     if (npx <= 0) return cudaSuccess;
-    const int R = unwrap_rounds(max_frame_px), J = R + 1;
-    UwWork w = carve(work, npx, R, J);
+    const int R = unwrap_rounds(max_frame_px);
+    UwWork w = carve(work, npx, R);
     UwArgs a{d_frames, nframes, npx, in, in_maps, out, out_maps};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -294,38 +300,27 @@ cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, in
     const int64_t want = (npx + kUwThreads - 1) / kUwThreads;
     const unsigned grid = (unsigned)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
     cudaError_t e;
-    // flags: [r * (J + 2) + 0] round r live, [r * (J + 2) + 1 + j] jump step j of round r may run
-    e = cudaMemsetAsync(w.flags, 0, 4 * (size_t)(R + 1) * (size_t)(J + 2), s);
+    // flags[r]: round r is live (round 0 always; round r + 1 if round r joined anything)
+    e = cudaMemsetAsync(w.flags, 0, 4 * (size_t)(R + 1), s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(w.flags, 0xff, 4, s);  // round 0 is live
+    e = cudaMemsetAsync(w.flags, 0xff, 4, s);
     if (e != cudaSuccess) return e;
-    uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk);
+    e = cudaMemsetAsync(w.best, 0, 8 * (size_t)npx, s);
+    if (e != cudaSuccess) return e;
+    uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, w.minpix);
     uw_reliability<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel);
     *launches += 2;
     for (int r = 0; r < R; ++r) {
-        int32_t* f = w.flags + (size_t)r * (J + 2);
-        int32_t* f_next = w.flags + (size_t)(r + 1) * (J + 2);
-        e = cudaMemsetAsync(w.best, 0, 8 * (size_t)npx, s);
-        if (e != cudaSuccess) return e;
-        uw_best_edges<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel, w.comp, w.best, f);
-        // a round with any hook makes the next round live and starts the jumping
-        uw_hook<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, w.best, w.hook, f, f_next);
-        *launches += 2;
-        for (int j = 0; j < J; ++j) {
-            // step j runs if step j-1 saw an unresolved parent (step 0: if the round hooked)
-            const int32_t* go = j == 0 ? f_next : f + 1 + j;
-            uw_jump<<<grid, kUwThreads, 0, s>>>(npx, w.comp, w.hook, go, f + 2 + j);
-            ++*launches;
-        }
-        uw_relabel<<<grid, kUwThreads, 0, s>>>(npx, w.comp, w.kk, w.hook, f_next);
-        ++*launches;
+        const int32_t* live = w.flags + r;
+        int32_t* hooked = w.flags + r + 1;
+        uw_best_edges<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel, w.comp, w.best, live);
+        uw_hook<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, w.best, w.hook, live, hooked);
+        uw_compress<<<grid, kUwThreads, 0, s>>>(npx, w.comp, w.hook, w.best, w.minpix, hooked);
+        uw_relabel<<<grid, kUwThreads, 0, s>>>(npx, w.comp, w.kk, w.hook, hooked);
+        *launches += 4;
     }
-    int32_t* first = reinterpret_cast<int32_t*>(w.rel);
-    e = cudaMemsetAsync(first, 0x7f, 4 * (size_t)npx, s);
-    if (e != cudaSuccess) return e;
-    uw_first_pixel<<<grid, kUwThreads, 0, s>>>(npx, w.wph, w.comp, first);
-    uw_write<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, first);
-    *launches += 2;
+    uw_write<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, w.minpix);
+    ++*launches;
     return cudaGetLastError();
 }
 
