@@ -137,24 +137,28 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
 
 
 SOLVER_PROFILE = os.path.join(ROOT, "profiles", "batched_solver_L8_peaks4x1024.md")
-SOLVER_SOURCES = ["batched_kernel.cuh", "rmusic_device.cuh", "rmusic_launch.h", "batched_variants.h", "batched_l8.cu"]
+SOLVER_SOURCES = ["batched_kernel.cuh", "roots_device.cuh", "rmusic_device.cuh", "rmusic_launch.h",
+                  "batched_variants.h", "batched_l8.cu"]
+SQUARE_PROFILE = os.path.join(ROOT, "profiles", "square_solver_Lp5_complex4x1024.md")
+SQUARE_SOURCES = ["square_kernel.cuh", "roots_device.cuh", "rmusic_device.cuh", "rmusic_launch.h",
+                  "square_variants.h", "square_l5.cu"]
 
 
-def profiled_traffic():
+def profiled_traffic(profile: str = SOLVER_PROFILE, sources=SOLVER_SOURCES):
     """DRAM bytes per solver launch from the committed ncu summary, or None when the solver's
-    source has changed since those counters were taken."""
+    source has changed since those counters were taken (the summary records a hash of it)."""
     import hashlib
     import re
 
-    if not os.path.exists(SOLVER_PROFILE):
+    if not os.path.exists(profile):
         return None
-    text = open(SOLVER_PROFILE).read()
+    text = open(profile).read()
     m_bytes = re.search(r"dram_bytes_per_launch = (\d+)", text)
     m_hash = re.search(r"source_sha256_16 = ([0-9a-f]{16})", text)
     if not m_bytes or not m_hash:
         return None
     h = hashlib.sha256()
-    for f in SOLVER_SOURCES:
+    for f in sources:
         h.update(open(os.path.join(ROOT, "paper_1910_11872_gb300", "csrc", f), "rb").read())
     return int(m_bytes.group(1)) if h.hexdigest()[:16] == m_hash.group(1) else None
 
@@ -474,7 +478,8 @@ def run_square_leg(args, rank, world, dev, stream, flush):
     res = {"workload": SQ_WORKLOAD, "value": value, "unit": "Mpixel/s", "ms_per_step": step_ms,
            "steps": args.square_steps, "gpu_launches": launches,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                        "frac": achieved / FP32_PEAK_TFLOPS,
+                        "traffic": profiled_traffic(SQUARE_PROFILE, SQUARE_SOURCES),
                         "kernel": f"square_kernel<{SQ_LP}, {st.solver_ctas_per_sm}>", "flops_per_pixel": fpp,
                         "launch_ms": solver_avg, "mean_power_iters": statistics.mean(its),
                         "mean_root_evals": statistics.mean(evals), "mean_root_updates": statistics.mean(updates)},
