@@ -40,13 +40,14 @@ class Params(ctypes.Structure):
         ("carrier_axis", ctypes.c_int32),
         ("carrier_freq", ctypes.c_double),
         ("band_halfwidth", ctypes.c_double),
+        ("band_cross", ctypes.c_double),
     ]
 
 
 def make_params(window_len=32, cov_order=8, forward_backward=1, deriv_axis=0, carrier_axis=0,
-                carrier_freq=0.1, band_halfwidth=0.0, model_order=1) -> Params:
+                carrier_freq=0.1, band_halfwidth=0.0, model_order=1, band_cross=0.0) -> Params:
     return Params(window_len, cov_order, model_order, forward_backward, deriv_axis, carrier_axis,
-                  float(carrier_freq), float(band_halfwidth))
+                  float(carrier_freq), float(band_halfwidth), float(band_cross))
 
 
 def build(force: bool = False) -> str:
@@ -117,6 +118,7 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_analytic_line.argtypes = [dp, i32, ctypes.c_double, ctypes.c_double, dp]
     L.orc_analytic_frame.argtypes = [ctypes.c_void_p, i32, i32, i32, i32, ctypes.c_double,
                                      ctypes.c_double, dp]
+    L.orc_cross_band.argtypes = [dp, i32, i32, i32, ctypes.c_double]
     L.orc_covariance_ri.argtypes = [dp, i32, i32, i32, dp]
     L.orc_covariance_ri.restype = None
     L.orc_eig_hermitian_ri.argtypes = [dp, i32, dp, dp]
@@ -190,6 +192,17 @@ def analytic_frame(frame: np.ndarray, f0: float, B: float = 0.0, carrier_axis: i
                                   _dp(out))
     assert rc == 0
     return _ri2c(out).reshape(H, W)
+
+
+def cross_band(gamma, Bc: float, carrier_axis: int = 0) -> np.ndarray:
+    """The 2-D variant's second pass on an analytic-signal frame: low-pass |k / len| < Bc across
+    the carrier lines."""
+    g = np.ascontiguousarray(np.asarray(gamma, dtype=np.complex128))
+    H, W = g.shape
+    buf = np.ascontiguousarray(g.view(np.float64).ravel())
+    rc = lib().orc_cross_band(_dp(buf), H, W, carrier_axis, float(Bc))
+    assert rc == 0
+    return buf.view(np.complex128).reshape(H, W)
 
 
 def covariance(w, L: int, fb: int = 1) -> np.ndarray:

@@ -45,7 +45,9 @@
  *     is the local phase there; the carrier is removed after the angles, from both the
  *     derivative along the carrier axis and alpha;
  *   - a complex frame (complex64 / complex128) is the analytic signal itself, as for the
- *     complex fringe the paper simulates, and is not band-passed.
+ *     complex fringe the paper simulates, and is not band-passed;
+ *   - optional 2-D band: the carrier band times a low-pass |k / len| < B_c across the carrier
+ *     lines (a rectangle in the 2-D spectrum), applied as a second 1-D pass.
  *
  * Build: gcc -std=c11 -O2 -ffp-contract=off -fPIC -shared -fopenmp rmusic_oracle.c -lm
  */
@@ -84,6 +86,8 @@ typedef struct {
     int32_t carrier_axis;     /* axis of the fringe carrier and of the band-pass      */
     double carrier_freq;      /* f0, cycles per pixel                                 */
     double band_halfwidth;    /* B, cycles per pixel; <= 0 selects f0 / 2             */
+    double band_cross;        /* B_c: low-pass across the carrier lines, |k / len| < B_c
+                                 (a rectangular 2-D band); 0 = none                    */
 } orc_params;
 
 static const double ORC_PI = 3.14159265358979323846264338327950288;
@@ -176,6 +180,65 @@ int orc_analytic_frame(const void* frame, int32_t dtype, int32_t H, int32_t W,
         free(v);
         free(g);
     }
+    return err;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Step 2, 2-D variant: the band kept by the Fourier method can also be limited across
+ * the carrier (the 2-D transform methods the paper cites for its band-pass, Sec. 2).
+ * Reading: a rectangular 2-D band, the one-sided carrier band of orc_analytic_line times
+ * |k / len| < B_c across it (k the signed bin, -len/2 <= k < len/2). The band is separable,
+ * so it is applied here as a second pass: along every line across the carrier, DFT of the
+ * complex signal, keep the bins with |k| < B_c len, inverse DFT with 1/len.
+ * ------------------------------------------------------------------------------- */
+int orc_cross_band(double* gamma, int32_t H, int32_t W, int32_t carrier_axis, double Bc) {
+    if (!(Bc > 0.0)) return 0;
+    int32_t nlines = carrier_axis == 0 ? W : H;  /* lines across the carrier */
+    int32_t len = carrier_axis == 0 ? H : W;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic)
+    for (int32_t li = 0; li < nlines; ++li) {
+        cplx* g = (cplx*)malloc(sizeof(cplx) * (size_t)len);
+        cplx* X = (cplx*)malloc(sizeof(cplx) * (size_t)len);
+        cplx* tw = (cplx*)malloc(sizeof(cplx) * (size_t)len);
+        if (!g || !X || !tw) { err = -2; free(g); free(X); free(tw); continue; }
+        for (int32_t m = 0; m < len; ++m) {
+            double a = 2.0 * ORC_PI * (double)m / (double)len;
+            tw[m] = cos(a) - I * sin(a);
+        }
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = carrier_axis == 0 ? (size_t)n * W + li : (size_t)li * W + n;
+            g[n] = gamma[2 * idx] + I * gamma[2 * idx + 1];
+        }
+        for (int32_t k = 0; k < len; ++k) {
+            int32_t ks = 2 * (int64_t)k < len ? k : k - len; /* signed bin */
+            if (!(fabs((double)ks) < Bc * (double)len)) { X[k] = 0.0; continue; }
+            cplx acc = 0.0;
+            for (int32_t n = 0; n < len; ++n) acc += g[n] * tw[((int64_t)k * n) % len];
+            X[k] = acc;
+        }
+        for (int32_t n = 0; n < len; ++n) {
+            cplx acc = 0.0;
+            for (int32_t k = 0; k < len; ++k)
+                if (X[k] != 0.0) acc += X[k] * conj(tw[((int64_t)k * n) % len]);
+            acc /= (double)len;
+            size_t idx = carrier_axis == 0 ? (size_t)n * W + li : (size_t)li * W + n;
+            gamma[2 * idx] = creal(acc);
+            gamma[2 * idx + 1] = cimag(acc);
+        }
+        free(g);
+        free(X);
+        free(tw);
+    }
+    return err;
+}
+
+/* Step 2 as configured: the analytic signal of the frame, then the cross band if any. */
+static int orc_gamma_of(const void* frame, int32_t dtype, int32_t H, int32_t W, const orc_params* p,
+                        double* gamma) {
+    double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
+    int err = orc_analytic_frame(frame, dtype, H, W, p->carrier_axis, p->carrier_freq, B, gamma);
+    if (!err) err = orc_cross_band(gamma, H, W, p->carrier_axis, p->band_cross);
     return err;
 }
 
@@ -613,8 +676,7 @@ int orc_demodulate(const void* frame, int32_t dtype, int32_t H, int32_t W, const
 #endif
     double* gamma = (double*)malloc(sizeof(double) * 2 * (size_t)H * W);
     if (!gamma) return -2;
-    double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
-    int err = orc_analytic_frame(frame, dtype, H, W, p->carrier_axis, p->carrier_freq, B, gamma);
+    int err = orc_gamma_of(frame, dtype, H, W, p, gamma);
     if (err) { free(gamma); return err; }
     int used = 1;
 #pragma omp parallel for schedule(dynamic)
@@ -700,7 +762,14 @@ int orc_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, int32_t W
             if (li >= 0 && li < nlines) need[li] = 1;
         }
     }
-    int used = orc_gamma_lines(frame, dtype, H, W, ca, p->carrier_freq, B, need, gamma);
+    int used = 1;
+    if (p->band_cross > 0.0) {
+        /* the cross band mixes all lines: the whole frame is needed */
+        int err = orc_gamma_of(frame, dtype, H, W, p, gamma);
+        if (err) { free(need); free(gamma); return err; }
+    } else {
+        used = orc_gamma_lines(frame, dtype, H, W, ca, p->carrier_freq, B, need, gamma);
+    }
 #pragma omp parallel for schedule(dynamic)
     for (int32_t i = 0; i < npix; ++i) {
         double d;
@@ -862,8 +931,7 @@ int orc_square_demodulate(const void* frame, int32_t dtype, int32_t H, int32_t W
 #endif
     double* gamma = (double*)malloc(sizeof(double) * 2 * (size_t)H * W);
     if (!gamma) return -2;
-    double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
-    int err = orc_analytic_frame(frame, dtype, H, W, p->carrier_axis, p->carrier_freq, B, gamma);
+    int err = orc_gamma_of(frame, dtype, H, W, p, gamma);
     if (err) { free(gamma); return err; }
     int used = 1;
 #pragma omp parallel for schedule(dynamic)
@@ -905,7 +973,13 @@ int orc_square_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, in
             if (li >= 0 && li < nlines) need[li] = 1;
         }
     }
-    int used = orc_gamma_lines(frame, dtype, H, W, ca, p->carrier_freq, B, need, gamma);
+    int used = 1;
+    if (p->band_cross > 0.0) {
+        int err = orc_gamma_of(frame, dtype, H, W, p, gamma);
+        if (err) { free(need); free(gamma); return err; }
+    } else {
+        used = orc_gamma_lines(frame, dtype, H, W, ca, p->carrier_freq, B, need, gamma);
+    }
 #pragma omp parallel for schedule(dynamic)
     for (int32_t i = 0; i < npix; ++i) {
         int st = orc_square_pixel(gamma, H, W, p, Lp, ys[i], xs[i], &dx[i], &dy[i], &alpha[i]);

@@ -1,6 +1,7 @@
 """Planted mistakes: each test copies the oracle's C source, plants one plausible error (a dropped
 conjugate, a transposed operand, a wrong index or sign), compiles the copy on the CPU and checks
-that the pins in test_oracle_pins.py, test_oracle_square.py and test_oracle_unwrap.py reject it. This shows the pins constrain every step of the
+that the pins in test_oracle_pins.py, test_oracle_square.py, test_oracle_unwrap.py and
+test_oracle_band2d.py reject it. This shows the pins constrain every step of the
 oracle rather than only re-running it."""
 import numpy as np
 import pytest
@@ -8,6 +9,7 @@ import pytest
 import oracle as O
 import test_oracle_pins as P
 import test_oracle_square as S
+import test_oracle_band2d as B2
 import test_oracle_unwrap as U
 
 MUTATIONS = {
@@ -54,6 +56,13 @@ MUTATIONS = {
     "unwrap: second difference sign": ("float h = orc_gam_f(PH(0, -1) - c) - orc_gam_f(c - PH(0, 1));",
                                        "float h = orc_gam_f(PH(0, -1) - c) + orc_gam_f(c - PH(0, 1));"),
     "unwrap: group shift sign": ("shift = k[p] + s - k[q];", "shift = k[q] + s - k[p];"),
+    # the 2-D band-pass variant
+    "band2d: one-sided cross band": ("int32_t ks = 2 * (int64_t)k < len ? k : k - len; /* signed bin */",
+                                     "int32_t ks = k; /* signed bin */"),
+    "band2d: 1/len dropped": ("            acc /= (double)len;\n            size_t idx = carrier_axis == 0 ? (size_t)n * W + li",
+                              "            acc /= 1.0;\n            size_t idx = carrier_axis == 0 ? (size_t)n * W + li"),
+    "band2d: along the carrier": ("    int32_t nlines = carrier_axis == 0 ? W : H;  /* lines across the carrier */",
+                                  "    int32_t nlines = carrier_axis == 0 ? H : W;  /* lines across the carrier */"),
 }
 
 PINS = [
@@ -82,6 +91,8 @@ PINS = [
     U.test_unwrap_single_row_is_numpy_unwrap,
     U.test_reliability_closed_form_quadratic,
     lambda: U.test_unwrap_is_max_spanning_tree_integration(0),
+    lambda: B2.test_band2d_matches_fft2_rectangle(0),
+    B2.test_band2d_plane_waves_inside_and_outside,
 ]
 
 
