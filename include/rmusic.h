@@ -104,6 +104,12 @@ extern "C" {
  *   unwrap           square geometry only: 1 also assembles the phase map (Sec. 3: the local
  *                    phases are unwrapped with the reliability-sorting method the paper cites) and
  *                    writes it as a fourth map per frame (see rmusic_unwrap_phase).
+ *   band_cross       B_c in cycles/pixel, 0 <= B_c < 0.5: when > 0, the analytic signal is also
+ *                    low-passed across the carrier lines to |k / len| < B_c (k the signed bin), so
+ *                    the kept band is a rectangle of the 2-D spectrum (a 2-D band-pass variant, after
+ *                    the 2-D Fourier methods the paper cites for its band-pass). At most 361 kept
+ *                    bins per line (B_c len <= 181); applies to complex frames too. Not supported
+ *                    by rmusic_demodulate_frames_noalloc.
  * carrier_freq may be 0 (no carrier) for complex frames; for real frames it must lie in (0, 0.5).
  */
 typedef struct {
@@ -125,6 +131,7 @@ typedef struct {
     int32_t geometry;
     int32_t half_width;
     int32_t unwrap;
+    double band_cross;
 } rmusic_params;
 
 /* One frame of a batch. Frames of one call may differ in size, type and window.

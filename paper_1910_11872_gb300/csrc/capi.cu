@@ -148,6 +148,7 @@ bool params_ok(const rmusic_params& p) {
     if (p.unwrap && p.geometry != RMUSIC_GEOM_SQUARE) return false;
     if (!(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5)) return false;
     if (!(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5)) return false;
+    if (!(p.band_cross >= 0.0 && p.band_cross < 0.5)) return false;
     if (p.precision < RMUSIC_PLAIN_FP64 || p.precision > RMUSIC_FP32_BATCHED) return false;
     if (p.max_sweeps < 0 || p.max_root_iters < 0) return false;
     return true;
@@ -195,6 +196,8 @@ struct Plan {
     std::vector<int> group_count;
     std::vector<int64_t> group_items;
     int64_t total_lines = 0;
+    int64_t cross_groups = 0;  // 32-line groups of the cross-band pass (0: no cross band)
+    int max_kc = 0;
     int max_len = 0;
     uint64_t gamma_elems = 0;
 };
@@ -249,6 +252,15 @@ int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
     }
     F->k_lo = klo < 0 ? 1 : klo;
     F->nb = nb;
+    if (p.band_cross > 0.0) {
+        // kept cross bins: signed k with |k| < B_c len across the carrier
+        const int lenc = p.carrier_axis == 0 ? d.height : d.width;
+        const double lim = p.band_cross * (double)lenc;
+        int kc = 0;
+        while ((double)(kc + 1) < lim) ++kc;
+        if (kc > kMaxCrossKc) return RMUSIC_EUNSUPPORTED;
+        F->cross_kc = kc;
+    }
     F->wlines = F->deriv_axis == 0 ? d.height : d.width;
     F->wlen = F->deriv_axis == 0 ? d.width : d.height;
     F->f0 = f0;
@@ -284,6 +296,11 @@ int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Pla
         goff += (uint64_t)F.H * (uint64_t)F.W;
         F.line_start = lines;
         lines += F.nlines;
+        if (ctx->p.band_cross > 0.0) {
+            F.cross_start = plan->cross_groups;
+            plan->cross_groups += ((F.carrier_axis == 0 ? F.W : F.H) + 31) / 32;
+            plan->max_kc = std::max(plan->max_kc, F.cross_kc);
+        }
         plan->max_len = std::max(plan->max_len, F.len);
         const int key = F.geom == kGeomSquare ? kSquareKey0 + F.L : F.L;
         if (i == 0 || F.L != plan->frames[i - 1].L) {
@@ -520,8 +537,12 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
     int e0 = stamp(ctx, s);
     const bool fp64 = ctx->p.precision == RMUSIC_PLAIN_FP64;
     RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, d_frames, ctx->d_gamma, fp64, s));
-    stamp_pair(ctx->a1_ev, e0, stamp(ctx, s));
     ++*launches;
+    if (plan.cross_groups > 0) {
+        RM_CUDA(launch_crossband(ctx->d_table, n, plan.cross_groups, plan.max_kc, ctx->d_gamma, fp64, s));
+        ++*launches;
+    }
+    stamp_pair(ctx->a1_ev, e0, stamp(ctx, s));
     const rmusic_params& p = ctx->p;
     if (p.precision == RMUSIC_FP32_BATCHED) {
         for (size_t g = 0; g < plan.group_L.size(); ++g) {
@@ -616,6 +637,9 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
             RM_CUDA(cudaEventRecord(ctx->table_free, s));
             RM_CUDA(launch_analytic(ctx->d_table, (int)plan.frames.size(), plan.total_lines, plan.max_len, d_frames,
                                     ctx->d_gamma, false, s));
+            if (plan.cross_groups > 0)
+                RM_CUDA(launch_crossband(ctx->d_table, (int)plan.frames.size(), plan.cross_groups, plan.max_kc,
+                                         ctx->d_gamma, false, s));
             rc = tune_plan(ctx, plan, d_out, d_status, s, force_tune);
             if (rc) return rc;
             for (auto& g : ctx->graphs) {  // captured graphs may hold the previous variants
@@ -735,6 +759,7 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
     DeviceGuard guard(device);
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = init_analytic();
+    if (e == cudaSuccess) e = init_crossband();
     if (e == cudaSuccess) e = init_batched(device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->table_free, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->call_done, cudaEventDisableTiming);

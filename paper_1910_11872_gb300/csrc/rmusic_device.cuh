@@ -47,6 +47,9 @@ struct FrameDev {
     int32_t geom;         // kGeomRow or kGeomSquare (then L holds the half-width Lp, N = 2 Lp + 1)
     double omega_ref;     // carrier phase step removed from the angle (rad/pixel)
     double f0;            // carrier frequency (cycles/pixel)
+    int64_t cross_start;  // first 32-line group of this frame in the cross-band grid
+    int32_t cross_kc;     // cross band: signed bins -kc .. kc kept across the carrier (0: none)
+    int32_t pad_;
 };
 
 // Index of the frame that owns global index `g` given each frame's start (non-decreasing).

@@ -15,6 +15,13 @@ cudaError_t init_analytic();
 cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_lines, int max_len,
                             const void* d_in, void* d_gamma, bool fp64, cudaStream_t stream);
 
+// 2-D band-pass variant: low-pass |k / len| < B_c across the carrier lines of the workspace, in
+// place (signed bins -cross_kc .. cross_kc). One CTA per 32 cross lines of a frame.
+constexpr int kMaxCrossKc = 180;
+cudaError_t init_crossband();
+cudaError_t launch_crossband(const FrameDev* d_frames, int nframes, int64_t total_groups, int max_kc,
+                             void* d_gamma, bool fp64, cudaStream_t stream);
+
 // Plain path: one thread per pixel of one frame, T = float or double (Sec. 3; Algorithm 1).
 struct PlainArgs {
     int fb;

@@ -55,8 +55,8 @@ def test_struct_layout_matches_header(tmp_path):
         " offsetof(rmusic_params, precision), offsetof(rmusic_params, use_graph), sizeof(rmusic_frame_desc));\n"
         'printf("%zu %zu %zu\\n", offsetof(rmusic_frame_desc, out_offset), offsetof(rmusic_frame_desc, cov_order),'
         " sizeof(rmusic_stats));\n"
-        'printf("%zu %zu %zu\\n", offsetof(rmusic_params, geometry), offsetof(rmusic_params, half_width),'
-        " offsetof(rmusic_params, unwrap));\n"
+        'printf("%zu %zu %zu %zu\\n", offsetof(rmusic_params, geometry), offsetof(rmusic_params, half_width),'
+        " offsetof(rmusic_params, unwrap), offsetof(rmusic_params, band_cross));\n"
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -65,7 +65,8 @@ def test_struct_layout_matches_header(tmp_path):
     assert list(map(int, a.split())) == [ctypes.sizeof(P), P.carrier_freq.offset, P.precision.offset,
                                          P.use_graph.offset, ctypes.sizeof(D)]
     assert list(map(int, b.split())) == [D.out_offset.offset, D.cov_order.offset, ctypes.sizeof(S)]
-    assert list(map(int, c.split())) == [P.geometry.offset, P.half_width.offset, P.unwrap.offset]
+    assert list(map(int, c.split())) == [P.geometry.offset, P.half_width.offset, P.unwrap.offset,
+                                         P.band_cross.offset]
 
 
 def test_argument_checks_without_cuda(lib):
@@ -94,3 +95,5 @@ def test_argument_checks_without_cuda(lib):
     bad = rmusic.make_params(unwrap=1)  # phase assembly needs the square geometry's alpha maps
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
     assert L.rmusic_unwrap_phase(None, None, None, 1, None, None) == rmusic.RMUSIC_EINVAL
+    bad = rmusic.make_params(band_cross=0.5)
+    assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
