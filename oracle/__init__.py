@@ -41,13 +41,14 @@ class Params(ctypes.Structure):
         ("carrier_freq", ctypes.c_double),
         ("band_halfwidth", ctypes.c_double),
         ("band_cross", ctypes.c_double),
+        ("raw_input", ctypes.c_int32),
     ]
 
 
 def make_params(window_len=32, cov_order=8, forward_backward=1, deriv_axis=0, carrier_axis=0,
-                carrier_freq=0.1, band_halfwidth=0.0, model_order=1, band_cross=0.0) -> Params:
+                carrier_freq=0.1, band_halfwidth=0.0, model_order=1, band_cross=0.0, raw_input=0) -> Params:
     return Params(window_len, cov_order, model_order, forward_backward, deriv_axis, carrier_axis,
-                  float(carrier_freq), float(band_halfwidth), float(band_cross))
+                  float(carrier_freq), float(band_halfwidth), float(band_cross), int(raw_input))
 
 
 def build(force: bool = False) -> str:
@@ -119,6 +120,7 @@ def _declare(L: ctypes.CDLL) -> None:
     L.orc_analytic_frame.argtypes = [ctypes.c_void_p, i32, i32, i32, i32, ctypes.c_double,
                                      ctypes.c_double, dp]
     L.orc_cross_band.argtypes = [dp, i32, i32, i32, ctypes.c_double]
+    L.orc_window_derivative_p_ri.argtypes = [dp, i32, i32, i32, i32, ctypes.c_double, dp, dp]
     L.orc_covariance_ri.argtypes = [dp, i32, i32, i32, dp]
     L.orc_covariance_ri.restype = None
     L.orc_eig_hermitian_ri.argtypes = [dp, i32, dp, dp]
@@ -263,6 +265,15 @@ def window_derivative(w, L: int, fb: int = 1, omega_ref: float = 0.0) -> dict:
                                         _dp(r), ctypes.byref(nr), _dp(z))
     return {"deriv": float(d[0]), "status": int(st), "u1": _ri2c(u), "q": _ri2c(q),
             "roots": _ri2c(r)[: nr.value].copy(), "zsel": complex(z[0], z[1])}
+
+
+def window_derivative_p(w, L: int, p: int, fb: int = 1, omega_ref: float = 0.0) -> dict:
+    """Steps 4-9 with model order p (1..3) for one window."""
+    wr = _c2ri(w)
+    d = np.zeros(1)
+    z = np.zeros(2)
+    st = lib().orc_window_derivative_p_ri(_dp(wr), wr.size // 2, L, fb, p, omega_ref, _dp(d), _dp(z))
+    return {"deriv": float(d[0]), "status": int(st), "zsel": complex(z[0], z[1])}
 
 
 # ---------------------------------------------------------------------------------------------

@@ -47,7 +47,11 @@
  *   - a complex frame (complex64 / complex128) is the analytic signal itself, as for the
  *     complex fringe the paper simulates, and is not band-passed;
  *   - optional 2-D band: the carrier band times a low-pass |k / len| < B_c across the carrier
- *     lines (a rectangle in the 2-D spectrum), applied as a second 1-D pass.
+ *     lines (a rectangle in the 2-D spectrum), applied as a second 1-D pass;
+ *   - model order p > 1 (real fringes without the analytic step, Gamma = the line minus its
+ *     mean): the noise projector keeps the p largest eigenvalues' eigenvectors out, and the
+ *     derivative comes from the one of the p roots nearest the circle whose angle is nearest
+ *     the expected angle.
  *
  * Build: gcc -std=c11 -O2 -ffp-contract=off -fPIC -shared -fopenmp rmusic_oracle.c -lm
  */
@@ -88,6 +92,7 @@ typedef struct {
     double band_halfwidth;    /* B, cycles per pixel; <= 0 selects f0 / 2             */
     double band_cross;        /* B_c: low-pass across the carrier lines, |k / len| < B_c
                                  (a rectangular 2-D band); 0 = none                    */
+    int32_t raw_input;        /* 1: no band-pass; Gamma = the real line minus its mean  */
 } orc_params;
 
 static const double ORC_PI = 3.14159265358979323846264338327950288;
@@ -233,9 +238,32 @@ int orc_cross_band(double* gamma, int32_t H, int32_t W, int32_t carrier_axis, do
     return err;
 }
 
+/* Step 2 skipped (model orders p > 1 on real fringes): Gamma is the real frame with the mean
+   of every carrier line removed (the band-pass drops that zero frequency too), imaginary part 0. */
+static void orc_raw_frame(const void* frame, int32_t dtype, int32_t H, int32_t W, int32_t carrier_axis,
+                          double* gamma) {
+    int32_t nlines = carrier_axis == 0 ? H : W;
+    int32_t len = carrier_axis == 0 ? W : H;
+    for (int32_t li = 0; li < nlines; ++li) {
+        double mean = 0.0;
+        for (int32_t n = 0; n < len; ++n)
+            mean += orc_sample(frame, dtype, carrier_axis == 0 ? (size_t)li * W + n : (size_t)n * W + li);
+        mean /= (double)len;
+        for (int32_t n = 0; n < len; ++n) {
+            size_t idx = carrier_axis == 0 ? (size_t)li * W + n : (size_t)n * W + li;
+            gamma[2 * idx] = orc_sample(frame, dtype, idx) - mean;
+            gamma[2 * idx + 1] = 0.0;
+        }
+    }
+}
+
 /* Step 2 as configured: the analytic signal of the frame, then the cross band if any. */
 static int orc_gamma_of(const void* frame, int32_t dtype, int32_t H, int32_t W, const orc_params* p,
                         double* gamma) {
+    if (p->raw_input && dtype != ORC_C64 && dtype != ORC_C128) {
+        orc_raw_frame(frame, dtype, H, W, p->carrier_axis, gamma);
+        return orc_cross_band(gamma, H, W, p->carrier_axis, p->band_cross);
+    }
     double B = p->band_halfwidth > 0 ? p->band_halfwidth : 0.5 * p->carrier_freq;
     int err = orc_analytic_frame(frame, dtype, H, W, p->carrier_axis, p->carrier_freq, B, gamma);
     if (!err) err = orc_cross_band(gamma, H, W, p->carrier_axis, p->band_cross);
@@ -592,6 +620,132 @@ int orc_window_derivative_ri(const double* w_ri, int32_t N, int32_t L, int32_t f
     return st;
 }
 
+/* ---------------------------------------------------------------------------------
+ * Model order p > 1 (Sec. 3 with p exponentials per window instead of one: a real fringe
+ * without the analytic step carries the two exponentials exp(+-j omega) of its cosine, plus one
+ * at zero frequency for a local offset). Step 5 keeps the p largest eigenvalues' eigenvectors:
+ * the noise projector is C = I - sum_{i<p} u_i u_i^H (degenerate if lambda_p - lambda_{p+1}
+ * <= 1e-12 lambda_1); step 6 forms the polynomial from C; step 8 takes the p candidate roots
+ * nearest the unit circle (a split double root counted once) and, among them, the one whose
+ * angle is nearest omega_ref (the expected angle: the carrier's along the carrier axis), then
+ * applies the split-double-root rule to it.
+ * ------------------------------------------------------------------------------- */
+static int orc_noise_projector(const cplx* R, int32_t L, int32_t p, cplx* C) {
+    cplx V[ORC_MAXL * ORC_MAXL];
+    double ev[ORC_MAXL];
+    int32_t order[ORC_MAXL];
+    double normR = 0.0;
+    for (int32_t i = 0; i < L * L; ++i) normR += creal(R[i] * conj(R[i]));
+    if (!(normR > 0.0) || p < 1 || p >= L) return ORC_DEGENERATE;
+    int sweeps = orc_eig_hermitian(R, L, ev, V);
+    int status = sweeps < 0 ? ORC_NOT_CONVERGED : ORC_OK;
+    /* eigenvalue indices by decreasing eigenvalue (insertion sort, stable) */
+    for (int32_t j = 0; j < L; ++j) {
+        int32_t t = j;
+        while (t > 0 && ev[order[t - 1]] < ev[j]) { order[t] = order[t - 1]; --t; }
+        order[t] = j;
+    }
+    if (!(ev[order[p - 1]] - ev[order[p]] > 1e-12 * ev[order[0]])) return ORC_DEGENERATE;
+    for (int32_t m = 0; m < L; ++m)
+        for (int32_t l = 0; l < L; ++l) C[m * L + l] = (m == l) ? 1.0 : 0.0;
+    for (int32_t i = 0; i < p; ++i) {
+        int32_t j = order[i];
+        double nu = 0.0;
+        for (int32_t m = 0; m < L; ++m) nu += creal(V[m * L + j] * conj(V[m * L + j]));
+        for (int32_t m = 0; m < L; ++m)
+            for (int32_t l = 0; l < L; ++l) C[m * L + l] -= V[m * L + j] * conj(V[l * L + j]) / nu;
+    }
+    return status;
+}
+
+/* Step 6 from a projector C: c_k = sum_{l-m=k} C[m][l], q[i] = c_{i-(L-1)}. */
+static void orc_music_poly_C(const cplx* C, int32_t L, cplx* q) {
+    for (int32_t i = 0; i < 2 * L - 1; ++i) q[i] = 0.0;
+    for (int32_t m = 0; m < L; ++m)
+        for (int32_t l = 0; l < L; ++l) q[(l - m) + (L - 1)] += C[m * L + l];
+}
+
+int orc_select_root_p(const cplx* q, int32_t deg, const cplx* roots, int32_t n, int32_t p,
+                      double omega_ref, cplx* zsel) {
+    int32_t near_idx[3] = {-1, -1, -1};
+    double near_d[3] = {INFINITY, INFINITY, INFINITY};
+    if (p < 1 || p > 3) return -1;
+    /* the p candidates nearest the circle, taken by increasing distance (earlier index first on
+       equal distance); a root within 1e-6 of one already taken is the other half of a split
+       double root and is not counted again */
+    for (int32_t t = 0; t < p; ++t) {
+        for (int32_t i = 0; i < n; ++i) {
+            double r = cabs(roots[i]);
+            if (!(r <= 1.0 + 1e-9)) continue;
+            double d = fabs(r - 1.0);
+            int taken = 0;
+            for (int32_t u = 0; u < t; ++u)
+                if (i == near_idx[u] || cabs(roots[i] - roots[near_idx[u]]) < 1e-6) taken = 1;
+            if (!taken && d < near_d[t]) { near_d[t] = d; near_idx[t] = i; }
+        }
+    }
+    int32_t best = -1;
+    double bestt = INFINITY;
+    for (int32_t t = 0; t < p; ++t) {
+        if (near_idx[t] < 0) continue;
+        double a = fabs(orc_wrap(carg(roots[near_idx[t]]) - omega_ref));
+        if (a < bestt) { bestt = a; best = near_idx[t]; }
+    }
+    if (best < 0) return -1;
+    /* the split-double-root rule of step 8 for the chosen root */
+    int32_t nb = -1;
+    double nd = INFINITY;
+    for (int32_t j = 0; j < n; ++j) {
+        if (j == best) continue;
+        double d = cabs(roots[j] - roots[best]);
+        if (d < nd) { nd = d; nb = j; }
+    }
+    if (nb < 0 || !(nd < 1e-6)) { *zsel = roots[best]; return 0; }
+    cplx z = 0.5 * (roots[best] + roots[nb]);
+    for (int it = 0; it < 16; ++it) {
+        cplx d1, d2;
+        orc_horner_d12(q, deg, z, &d1, &d2);
+        if (d2 == 0.0) break;
+        cplx step = d1 / d2;
+        z -= step;
+        if (cabs(step) <= 1e-16 * cabs(z)) break;
+    }
+    *zsel = cabs(z - roots[best]) <= 2.0 * nd ? z : 0.5 * (roots[best] + roots[nb]);
+    return 0;
+}
+
+/* Steps 4-9 with model order p (p = 1 is orc_window_derivative). */
+int orc_window_derivative_p(const cplx* w, int32_t N, int32_t L, int32_t fb, int32_t p,
+                            double omega_ref, double* deriv, cplx* zsel_out) {
+    if (p == 1) return orc_window_derivative(w, N, L, fb, omega_ref, deriv, NULL, NULL, NULL, NULL, zsel_out);
+    cplx R[ORC_MAXL * ORC_MAXL], C[ORC_MAXL * ORC_MAXL], q[2 * ORC_MAXL], roots[2 * ORC_MAXL];
+    *deriv = NAN;
+    if (L < 2 || L > ORC_MAXL || N < L || p < 1 || p > 3 || p >= L) return ORC_DEGENERATE;
+    orc_covariance(w, N, L, fb, R);
+    int status = orc_noise_projector(R, L, p, C);
+    if (status == ORC_DEGENERATE) return ORC_DEGENERATE;
+    orc_music_poly_C(C, L, q);
+    int32_t nc = 0;
+    int32_t nr = orc_poly_roots(q, 2 * L - 2, roots, &nc);
+    if (nc) status = ORC_NOT_CONVERGED;
+    cplx z;
+    if (orc_select_root_p(q, 2 * L - 2, roots, nr, p, omega_ref, &z) != 0) return ORC_DEGENERATE;
+    *deriv = orc_wrap(carg(z) - omega_ref);
+    if (zsel_out) *zsel_out = z;
+    return status;
+}
+
+int orc_window_derivative_p_ri(const double* w_ri, int32_t N, int32_t L, int32_t fb, int32_t p,
+                               double omega_ref, double* deriv, double* zsel_ri) {
+    cplx w[4096], z = 0.0;
+    if (N > 4096) return ORC_DEGENERATE;
+    for (int32_t i = 0; i < N; ++i) w[i] = w_ri[2 * i] + I * w_ri[2 * i + 1];
+    int st = orc_window_derivative_p(w, N, L, fb, p, omega_ref, deriv, &z);
+    zsel_ri[0] = creal(z);
+    zsel_ri[1] = cimag(z);
+    return st;
+}
+
 /* ctypes-friendly wrappers for the individual steps (used by the pin tests). */
 void orc_covariance_ri(const double* w_ri, int32_t N, int32_t L, int32_t fb, double* R_ri) {
     cplx w[4096], R[ORC_MAXL * ORC_MAXL];
@@ -650,7 +804,7 @@ static int orc_pixel(const double* gamma, int32_t H, int32_t W, const orc_params
     int32_t start = n - N / 2;
     *out = NAN;
     if (start < 0 || start + N - 1 > len - 1) return ORC_BORDER;
-    if (p->model_order != 1) return ORC_DEGENERATE;
+    if (p->model_order < 1 || p->model_order > 3) return ORC_DEGENERATE;
     cplx w[4096];
     if (N > 4096) return ORC_DEGENERATE;
     for (int32_t i = 0; i < N; ++i) {
@@ -659,8 +813,8 @@ static int orc_pixel(const double* gamma, int32_t H, int32_t W, const orc_params
         w[i] = gamma[2 * idx] + I * gamma[2 * idx + 1];
     }
     double omega_ref = p->deriv_axis == p->carrier_axis ? 2.0 * ORC_PI * p->carrier_freq : 0.0;
-    return orc_window_derivative(w, N, p->cov_order, p->forward_backward, omega_ref, out,
-                                 NULL, NULL, NULL, NULL, NULL);
+    return orc_window_derivative_p(w, N, p->cov_order, p->forward_backward, p->model_order, omega_ref, out,
+                                   NULL);
 }
 
 /* Whole-frame demodulation: derivative map out[H*W] (NaN where undefined) and status[H*W]
@@ -763,8 +917,8 @@ int orc_demodulate_pixels(const void* frame, int32_t dtype, int32_t H, int32_t W
         }
     }
     int used = 1;
-    if (p->band_cross > 0.0) {
-        /* the cross band mixes all lines: the whole frame is needed */
+    if (p->band_cross > 0.0 || p->raw_input) {
+        /* the cross band mixes all lines (and the raw signal is cheap): the whole frame */
         int err = orc_gamma_of(frame, dtype, H, W, p, gamma);
         if (err) { free(need); free(gamma); return err; }
     } else {

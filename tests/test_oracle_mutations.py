@@ -1,7 +1,7 @@
 """Planted mistakes: each test copies the oracle's C source, plants one plausible error (a dropped
 conjugate, a transposed operand, a wrong index or sign), compiles the copy on the CPU and checks
 that the pins in test_oracle_pins.py, test_oracle_square.py, test_oracle_unwrap.py and
-test_oracle_band2d.py reject it. This shows the pins constrain every step of the
+test_oracle_band2d.py, test_oracle_model_order.py reject it. This shows the pins constrain every step of the
 oracle rather than only re-running it."""
 import numpy as np
 import pytest
@@ -10,6 +10,7 @@ import oracle as O
 import test_oracle_pins as P
 import test_oracle_square as S
 import test_oracle_band2d as B2
+import test_oracle_model_order as MO
 import test_oracle_unwrap as U
 
 MUTATIONS = {
@@ -63,6 +64,15 @@ MUTATIONS = {
                               "            acc /= 1.0;\n            size_t idx = carrier_axis == 0 ? (size_t)n * W + li"),
     "band2d: along the carrier": ("    int32_t nlines = carrier_axis == 0 ? W : H;  /* lines across the carrier */",
                                   "    int32_t nlines = carrier_axis == 0 ? H : W;  /* lines across the carrier */"),
+    # model order p > 1
+    "p: projector keeps one eigenvector": ("    for (int32_t i = 0; i < p; ++i) {\n        int32_t j = order[i];",
+                                           "    for (int32_t i = 0; i < 1; ++i) {\n        int32_t j = order[i];"),
+    "p: expected angle ignored": ("if (a < bestt) { bestt = a; best = near_idx[t]; }",
+                                  "if (best < 0) { bestt = a; best = near_idx[t]; }"),
+    "p: split double root counted twice": ("if (i == near_idx[u] || cabs(roots[i] - roots[near_idx[u]]) < 1e-6) taken = 1;",
+                                           "if (i == near_idx[u]) taken = 1;"),
+    "raw: line mean kept": ("        mean /= (double)len;\n        for (int32_t n = 0; n < len; ++n) {",
+                            "        mean = 0.0;\n        for (int32_t n = 0; n < len; ++n) {"),
 }
 
 PINS = [
@@ -93,6 +103,9 @@ PINS = [
     lambda: U.test_unwrap_is_max_spanning_tree_integration(0),
     lambda: B2.test_band2d_matches_fft2_rectangle(0),
     B2.test_band2d_plane_waves_inside_and_outside,
+    lambda: MO.test_p2_noise_free_real_cosine_exact(8, 1),
+    MO.test_p3_models_a_local_offset,
+    lambda: MO.test_p_noisy_windows_by_enumeration(2),
 ]
 
 
