@@ -77,7 +77,12 @@ extern "C" {
  *   cov_order        L, length of the snapshots s_i = w[i .. i+L-1], i = 0 .. N-L, and order of
  *                    the L x L auto-correlation matrix (2 <= L <= 12, L <= N). The batched path
  *                    takes even L with forward_backward = 1; other cases need a plain path.
- *   model_order      number of complex exponentials per window; the method uses 1 (Eq. 2).
+ *   model_order      number of complex exponentials per window; the method uses 1 (Eq. 2). The
+ *                    plain paths also take 2 or 3 (a real fringe without the analytic step holds
+ *                    exp(+-j omega), and a local offset one more at zero frequency): the noise
+ *                    projector then removes the p largest eigenvalues' eigenvectors, and the
+ *                    derivative comes from the one of the p roots nearest the unit circle whose
+ *                    angle is nearest the expected one (2 pi f0). Needs cov_order > model_order.
  *   forward_backward 1: R = (R_f + J conj(R_f) J) / 2 (forward-backward average); 0: R = R_f.
  *   deriv_axis       0: windows run along x (rows); 1: along y (columns).
  *   carrier_axis     axis of the carrier and of the band-pass (0 = x, 1 = y).
@@ -110,6 +115,9 @@ extern "C" {
  *                    the 2-D Fourier methods the paper cites for its band-pass). At most 361 kept
  *                    bins per line (B_c len <= 181); applies to complex frames too. Not supported
  *                    by rmusic_demodulate_frames_noalloc.
+ *   raw_input        1: no band-pass; the window holds the real samples of the carrier line minus
+ *                    the line's mean (for model_order 2 or 3). Needs the row geometry with
+ *                    deriv_axis == carrier_axis (the carrier decides which of +-omega is meant).
  * carrier_freq may be 0 (no carrier) for complex frames; for real frames it must lie in (0, 0.5).
  */
 typedef struct {
@@ -132,6 +140,7 @@ typedef struct {
     int32_t half_width;
     int32_t unwrap;
     double band_cross;
+    int32_t raw_input;
 } rmusic_params;
 
 /* One frame of a batch. Frames of one call may differ in size, type and window.

@@ -159,6 +159,18 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
     for (int n = threadIdx.x; n < len; n += blockDim.x) v[n] -= mean;
     __syncthreads();
 
+    if (F.raw) {
+        // no band-pass (model orders p > 1 on real fringes): the line minus its mean, as is
+        for (int n = threadIdx.x; n < len; n += blockDim.x) {
+            const int y = F.carrier_axis == 0 ? li : n;
+            const int x = F.carrier_axis == 0 ? n : li;
+            const int wline = F.deriv_axis == 0 ? y : x;
+            const int pos = F.deriv_axis == 0 ? x : y;
+            gam[F.gam_off + (uint64_t)wline * F.wlen + pos] = mkc(v[n], (T)0);
+        }
+        return;
+    }
+
     // forward band-limited DFT, one thread per kept bin
     const T two_over_len = T(2) / (T)len;
     for (int b = threadIdx.x; b < F.nb; b += blockDim.x) {

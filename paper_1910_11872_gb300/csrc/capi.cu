@@ -145,6 +145,9 @@ bool params_ok(const rmusic_params& p) {
     }
     if (p.carrier_axis != 0 && p.carrier_axis != 1) return false;
     if (p.unwrap != 0 && p.unwrap != 1) return false;
+    if (p.raw_input != 0 && p.raw_input != 1) return false;
+    if (p.raw_input && (p.geometry != RMUSIC_GEOM_ROW || p.deriv_axis != p.carrier_axis)) return false;
+    if (p.geometry == RMUSIC_GEOM_ROW && p.model_order >= p.cov_order) return false;
     if (p.unwrap && p.geometry != RMUSIC_GEOM_SQUARE) return false;
     if (!(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5)) return false;
     if (!(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5)) return false;
@@ -236,6 +239,7 @@ int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
     F->L = L;
     F->carrier_axis = p.carrier_axis;
     F->deriv_axis = square ? 0 : p.deriv_axis;  // the square block reads a row-major workspace
+    F->raw = p.raw_input && d.dtype != RMUSIC_DTYPE_C64;
     F->geom = square ? kGeomSquare : kGeomRow;
     F->nlines = p.carrier_axis == 0 ? d.height : d.width;
     F->len = p.carrier_axis == 0 ? d.width : d.height;
@@ -564,6 +568,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         }
     } else {
         PlainArgs a;
+        a.p = p.model_order;
         a.fb = p.forward_backward;
         a.max_sweeps = p.max_sweeps ? p.max_sweeps : 30;
         a.max_iters = p.max_root_iters ? p.max_root_iters : 500;
@@ -741,8 +746,10 @@ extern "C" {
 int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_bytes, rmusic_ctx** out) {
     if (!params || !out) return RMUSIC_EINVAL;
     *out = nullptr;
-    if (params->model_order != 1) return params->model_order < 1 ? RMUSIC_EINVAL : RMUSIC_EUNSUPPORTED;
+    if (params->model_order < 1) return RMUSIC_EINVAL;
+    if (params->model_order > kMaxModelOrder) return RMUSIC_EUNSUPPORTED;
     if (!params_ok(*params)) return RMUSIC_EINVAL;
+    if (params->model_order > 1 && params->precision == RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
     if (params->geometry == RMUSIC_GEOM_SQUARE && params->precision != RMUSIC_FP32_BATCHED)
         return RMUSIC_EUNSUPPORTED;
     int ndev = 0;

@@ -125,7 +125,7 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
     const rmusic_params& p = *params;
     if (p.model_order != 1) return p.model_order < 1 ? RMUSIC_EINVAL : RMUSIC_EUNSUPPORTED;
     if (p.precision != RMUSIC_FP32_BATCHED || p.forward_backward != 1 || p.geometry != RMUSIC_GEOM_ROW ||
-        p.band_cross != 0.0)
+        p.band_cross != 0.0 || p.raw_input != 0)
         return RMUSIC_EUNSUPPORTED;
     if (p.window_len < 2 || p.window_len > kMaxN || p.cov_order < 2 || p.cov_order > kMaxL ||
         p.cov_order > p.window_len || (p.deriv_axis != 0 && p.deriv_axis != 1) ||

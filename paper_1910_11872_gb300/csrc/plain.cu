@@ -10,12 +10,16 @@
 //   R        R_f[m][l] = (1/K) sum_{i<K} w[i+m] conj(w[i+l]), K = N - L + 1, optional
 //            forward-backward average (R_f + J conj(R_f) J) / 2                      (Eq. 4-5)
 //   eigen    cyclic complex Jacobi; u1 = eigenvector of the largest eigenvalue      (Eq. 8-11)
+//            (model order p > 1: the eigenvectors of the p largest eigenvalues)
 //   poly     Q(z) = sum_k c_k z^(k+L-1), c_k = sum_{l-m=k} (I - u1 u1^H)[m][l]        (Eq. 12-14)
+//            (p > 1: I - sum_{i<p} u_i u_i^H)
 //   roots    Aberth-Ehrlich on all 2L-2 roots from a circle of starting points
 //   select   the root with |z| <= 1 + tau_in nearest the unit circle; if another root lies
 //            within tau_c of it the pair is one split double root, located on Q'; otherwise two
 //            Newton steps on Q with the conjugate-reciprocal partner 1/conj(z) divided out
 //            refine it                                                          (Algorithm 1)
+//            (p > 1: among the p roots nearest the circle, a split double root counted once,
+//            the one whose angle is nearest the expected angle)
 //   angle    arg(z) minus the carrier step, wrapped to (-pi, pi]                     (Eq. 15)
 #include <math.h>
 
@@ -206,32 +210,42 @@ plain_kernel(const FrameDev* __restrict__ frame, const typename GammaOf<T>::type
             }
     }
     if (!jac_conv) st = kStNotConverged;
-    int j1 = 0;
-    for (int j = 1; j < L; ++j)
-        if (A[j * L + j].r > A[j1 * L + j1].r) j1 = j;
-    T l1 = A[j1 * L + j1].r, l2 = -INFINITY;
-    for (int j = 0; j < L; ++j)
-        if (j != j1 && A[j * L + j].r > l2) l2 = A[j * L + j].r;
-    if (!(l1 - l2 > PlainTol<T>::gap * l1)) {
+    // the p + 1 largest eigenvalues, by decreasing value (an earlier index first on ties)
+    const int P = args.p;
+    int ord[kMaxModelOrder + 1];
+    for (int t = 0; t <= P; ++t) ord[t] = -1;
+    for (int j = 0; j < L; ++j) {
+        const T v = A[j * L + j].r;
+        for (int t = 0; t <= P; ++t)
+            if (ord[t] < 0 || v > A[ord[t] * L + ord[t]].r) {
+                for (int u2 = P; u2 > t; --u2) ord[u2] = ord[u2 - 1];
+                ord[t] = j;
+                break;
+            }
+    }
+    const T l1 = A[ord[0] * L + ord[0]].r;
+    const T lp = A[ord[P - 1] * L + ord[P - 1]].r;
+    const T lq = ord[P] >= 0 ? A[ord[P] * L + ord[P]].r : T(-INFINITY);
+    if (!(lp - lq > PlainTol<T>::gap * l1)) {
         out[o] = __int_as_float(0x7fc00000);
         if (status) status[o] = kStDegenerate;
         return;
     }
-    cx<T> u[kMaxL];
-    T nu = 0;
-    for (int m = 0; m < L; ++m) {
-        u[m] = V[m * L + j1];
-        nu += norm2(u[m]);
-    }
 
-    // ---- root-MUSIC polynomial (Eq. 12-14), normalised by |u1|^2 ------------------------------
+    // ---- root-MUSIC polynomial (Eq. 12-14) of I - sum_{i<p} u_i u_i^H / |u_i|^2 ----------------
     const int deg = 2 * L - 2;
     cx<T> q[2 * kMaxL];
     for (int i = 0; i <= deg; ++i) q[i] = mkc(T(0), T(0));
-    const T inv_nu = T(1) / nu;
+    T inv_nu[kMaxModelOrder];
+    for (int i = 0; i < P; ++i) {
+        T nu = 0;
+        for (int m = 0; m < L; ++m) nu += norm2(V[m * L + ord[i]]);
+        inv_nu[i] = T(1) / nu;
+    }
     for (int m = 0; m < L; ++m)
         for (int l = 0; l < L; ++l) {
-            cx<T> cml = (-inv_nu) * mulc(u[m], u[l]);
+            cx<T> cml = (-inv_nu[0]) * mulc(V[m * L + ord[0]], V[l * L + ord[0]]);
+            for (int i = 1; i < P; ++i) cml = cml - inv_nu[i] * mulc(V[m * L + ord[i]], V[l * L + ord[i]]);
             if (m == l) cml.r += T(1);
             q[l - m + L - 1] = q[l - m + L - 1] + cml;
         }
@@ -276,15 +290,46 @@ plain_kernel(const FrameDev* __restrict__ frame, const typename GammaOf<T>::type
     // ---- selection (Algorithm 1) and split double roots --------------------------------------
     int best = -1;
     T bestd = INFINITY, bestt = INFINITY;
-    for (int i = 0; i < deg; ++i) {
-        const T r = tsqrt(norm2(z[i]));
-        if (!(r <= T(1) + PlainTol<T>::cand)) continue;
-        const T d = fabs(r - T(1));
-        const T t = fabs(wrap_pi(tatan2(z[i].i, z[i].r) - (T)F.omega_ref));
-        if (d < bestd || (d == bestd && t < bestt)) {
-            best = i;
-            bestd = d;
-            bestt = t;
+    if (P == 1) {
+        for (int i = 0; i < deg; ++i) {
+            const T r = tsqrt(norm2(z[i]));
+            if (!(r <= T(1) + PlainTol<T>::cand)) continue;
+            const T d = fabs(r - T(1));
+            const T t = fabs(wrap_pi(tatan2(z[i].i, z[i].r) - (T)F.omega_ref));
+            if (d < bestd || (d == bestd && t < bestt)) {
+                best = i;
+                bestd = d;
+                bestt = t;
+            }
+        }
+    } else {
+        // the p candidates nearest the circle (a split double root counted once), then the one
+        // whose angle is nearest the expected angle
+        int near[kMaxModelOrder];
+        for (int t = 0; t < P; ++t) {
+            near[t] = -1;
+            T nd = INFINITY;
+            for (int i = 0; i < deg; ++i) {
+                const T r = tsqrt(norm2(z[i]));
+                if (!(r <= T(1) + PlainTol<T>::cand)) continue;
+                bool taken = false;
+                for (int u2 = 0; u2 < t; ++u2)
+                    if (near[u2] >= 0 && (i == near[u2] || tsqrt(norm2(z[i] - z[near[u2]])) < PlainTol<T>::cluster))
+                        taken = true;
+                const T d = fabs(r - T(1));
+                if (!taken && d < nd) {
+                    nd = d;
+                    near[t] = i;
+                }
+            }
+        }
+        for (int t = 0; t < P; ++t) {
+            if (near[t] < 0) continue;
+            const T a = fabs(wrap_pi(tatan2(z[near[t]].i, z[near[t]].r) - (T)F.omega_ref));
+            if (a < bestt) {
+                bestt = a;
+                best = near[t];
+            }
         }
     }
     if (best < 0) {

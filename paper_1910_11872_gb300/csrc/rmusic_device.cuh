@@ -49,7 +49,7 @@ struct FrameDev {
     double f0;            // carrier frequency (cycles/pixel)
     int64_t cross_start;  // first 32-line group of this frame in the cross-band grid
     int32_t cross_kc;     // cross band: signed bins -kc .. kc kept across the carrier (0: none)
-    int32_t pad_;
+    int32_t raw;          // 1: no band-pass; Gamma = the real line minus its mean
 };
 
 // Index of the frame that owns global index `g` given each frame's start (non-decreasing).

@@ -23,10 +23,12 @@ cudaError_t launch_crossband(const FrameDev* d_frames, int nframes, int64_t tota
                              void* d_gamma, bool fp64, cudaStream_t stream);
 
 // Plain path: one thread per pixel of one frame, T = float or double (Sec. 3; Algorithm 1).
+constexpr int kMaxModelOrder = 3;
 struct PlainArgs {
     int fb;
     int max_sweeps;
     int max_iters;
+    int p;  // model order 1 .. kMaxModelOrder
 };
 cudaError_t launch_plain_fp64(const FrameDev* d_frame, const FrameDev& h_frame, const double2* d_gamma,
                               float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream);

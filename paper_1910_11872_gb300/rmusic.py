@@ -63,6 +63,7 @@ class rmusic_params(ctypes.Structure):
         ("half_width", ctypes.c_int32),
         ("unwrap", ctypes.c_int32),
         ("band_cross", ctypes.c_double),
+        ("raw_input", ctypes.c_int32),
     ]
 
 
@@ -255,12 +256,14 @@ def rmusic_get_stats(ctx) -> rmusic_stats:
 def make_params(window_len=32, cov_order=8, forward_backward=1, deriv_axis=0, carrier_axis=0,
                 carrier_freq=0.1, band_halfwidth=0.0, precision="batched", max_sweeps=0,
                 max_root_iters=0, polish_fp64=0, use_graph=0, timing=0, autotune=0,
-                model_order=1, geometry="row", half_width=0, unwrap=0, band_cross=0.0) -> rmusic_params:
+                model_order=1, geometry="row", half_width=0, unwrap=0, band_cross=0.0,
+                raw_input=0) -> rmusic_params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     geom = GEOMETRIES[geometry] if isinstance(geometry, str) else int(geometry)
     return rmusic_params(window_len, cov_order, model_order, forward_backward, deriv_axis, carrier_axis,
                          float(carrier_freq), float(band_halfwidth), prec, max_sweeps, max_root_iters,
-                         polish_fp64, use_graph, timing, autotune, geom, half_width, unwrap, float(band_cross))
+                         polish_fp64, use_graph, timing, autotune, geom, half_width, unwrap, float(band_cross),
+                         int(raw_input))
 
 
 def frame_descs(shapes, dtype_code: int, elem_bytes: int, windows=None, maps: int = 1):

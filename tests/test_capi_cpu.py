@@ -57,16 +57,18 @@ def test_struct_layout_matches_header(tmp_path):
         " sizeof(rmusic_stats));\n"
         'printf("%zu %zu %zu %zu\\n", offsetof(rmusic_params, geometry), offsetof(rmusic_params, half_width),'
         " offsetof(rmusic_params, unwrap), offsetof(rmusic_params, band_cross));\n"
+        'printf("%zu\\n", offsetof(rmusic_params, raw_input));\n'
         "return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:3]
+    a, b, c, d = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")[:4]
     P, D, S = rmusic.rmusic_params, rmusic.rmusic_frame_desc, rmusic.rmusic_stats
     assert list(map(int, a.split())) == [ctypes.sizeof(P), P.carrier_freq.offset, P.precision.offset,
                                          P.use_graph.offset, ctypes.sizeof(D)]
     assert list(map(int, b.split())) == [D.out_offset.offset, D.cov_order.offset, ctypes.sizeof(S)]
     assert list(map(int, c.split())) == [P.geometry.offset, P.half_width.offset, P.unwrap.offset,
                                          P.band_cross.offset]
+    assert int(d) == P.raw_input.offset
 
 
 def test_argument_checks_without_cuda(lib):
@@ -79,9 +81,13 @@ def test_argument_checks_without_cuda(lib):
     L.rmusic_destroy(None)
     assert rmusic.rmusic_strerror(rmusic.RMUSIC_ENOMEM).startswith("out of memory")
     assert rmusic.rmusic_strerror(12345) == "unknown error"
-    bad = rmusic.make_params(model_order=2)
+    bad = rmusic.make_params(model_order=4)
     ctx = ctypes.c_void_p()
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EUNSUPPORTED
+    bad = rmusic.make_params(model_order=2)  # the batched solvers keep model order 1
+    assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EUNSUPPORTED
+    bad = rmusic.make_params(model_order=2, precision="plain_fp32", raw_input=1, deriv_axis=1)
+    assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
     bad = rmusic.make_params(window_len=8, cov_order=12)
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
     # the square block: half-width 1 .. 8, FP32-batched only
