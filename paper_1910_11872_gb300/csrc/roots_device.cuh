@@ -11,8 +11,13 @@
 //             points come from the estimator's structure: the signal root just inside the circle
 //             at the angle of conj(rho_1), the others at radius r = L / (L + 7.3) at the
 //             side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window
-//             puts them. Iterations stop when every root of every lane of the warp has a residual
-//             at the FP32 rounding level (|Q(z)| <= 3e-6 sum |q_i|).
+//             puts them. A root stops (freezes) when its residual is at the FP32 rounding level
+//             (|Q(z)| <= 3e-6 sum |q_i|), or, if it lies at least 0.05 inside the outermost tracked
+//             root, when its Newton step is below 1e-3: only the root nearest the circle needs
+//             full accuracy (it is polished after the selection), the others only have to be
+//             resolved well enough not to change the selection, and Aberth's fixed point for the
+//             remaining roots does not depend on where a frozen root stopped. Iterations stop
+//             when every root of every lane of the warp is frozen.
 //   select    the inner root nearest the unit circle (Algorithm 1). A noise-free window gives a
 //             double root on the circle, which FP32 splits by ~sqrt(eps); when another root lies
 //             within 4e-3 the pair is located as the root of Q' between them, otherwise the root
@@ -158,6 +163,12 @@ __device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, 
     unsigned frozen = 0;  // bit r: the root now at position r has converged in this lane
     for (;;) {
         rconv = true;
+        // roots this far inside the outermost one may stop at a 1e-3 Newton step
+        float rb2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < NI; ++j) rb2 = fmaxf(rb2, norm2(z[j]));
+        const float rfar = sqrtf(rb2) - 0.05f;
+        const float far2 = rfar > 0.f ? rfar * rfar : 0.f;
 #pragma unroll 1
         for (int r = 0; r < NI; ++r) {
             const cx<float> z0 = z[0];
@@ -169,12 +180,13 @@ __device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, 
                 ++evals;
                 cx<float> p, dp;
                 horner_pd<L>(c, z0, p, dp);
-                const bool cv = (frozen & 1u) || norm2(p) <= res_lim2;
+                const cx<float> Ni = cdivf(p, dp);
+                const bool cv = (frozen & 1u) || norm2(p) <= res_lim2 ||
+                                (norm2(z0) < far2 && norm2(Ni) <= 1e-6f);
                 frozen |= cv ? 1u : 0u;
                 rconv = rconv && cv;
                 if (!__all_sync(kFull, cv)) {
                     ++updates;
-                    const cx<float> Ni = cdivf(p, dp);
                     cx<float> Si = mkc(0.f, 0.f);
 #pragma unroll
                     for (int j = 0; j < NI; ++j) {
