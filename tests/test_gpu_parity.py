@@ -348,10 +348,11 @@ def test_full_size_frame_sampled_against_oracle():
 def test_plain_fp32_and_polish64_accuracy():
     fr = synth.peaks_frame(np.inf, 0.1, H=24, W=256)
     o, os_ = oracle_run(fr.image)
-    # the plain FP32 path has no higher-precision polish: near-double roots keep FP32 noise
+    # the plain FP32 path has no higher-precision polish: near-double roots keep FP32 noise, and
+    # its Aberth may stop at the iteration cap there (status 3, best estimate stored, checked too)
     for kw, tol in ((dict(precision="plain_fp32"), 5e-3), (dict(polish_fp64=1), 1e-4)):
         (g, gs), = run_gpu([fr.image], **kw)
-        v = (os_ == 0) & (gs == 0)
+        v = (os_ == 0) & ((gs == 0) | (gs == 3))
         assert v.sum() >= 0.99 * (os_ == 0).sum()
         d = np.abs(g[v].astype(np.float64) - o[v])
         assert d.max() <= tol, f"{kw}: max {d.max():.3e} p99.9 {np.quantile(d, 0.999):.3e}"
