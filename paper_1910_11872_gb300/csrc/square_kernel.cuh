@@ -19,9 +19,10 @@
 // (two M x M products per step, no M x M covariance is formed), started from the centre column.
 // The vectors live in shared memory (one column per thread) and the loops over rows are rolled,
 // so only one M-vector is held in registers.
-// Each step shrinks the other singular directions by (s_2 / s_1)^2 ~ 4 sigma^2 / (M A^2); the
-// iteration stops when the step changes u by less than 3e-6 in every lane of the warp. v1 is
-// G^H u from the last step. Degenerate blocks (all zero) get a stand-in vector so every lane of
+// Each step shrinks the other singular directions by (s_2 / s_1)^2 ~ 4 sigma^2 / (M A^2), or,
+// with the shift by twice the mean noise eigenvalue that the kernel applies from the first step,
+// by about half of that; the iteration stops when the step changes u by less than 3e-6 in every
+// lane of the warp. v1 is G^H u from the last step. Degenerate blocks (all zero) get a stand-in vector so every lane of
 // the warp runs the same bounded loops.
 //
 // Polynomials: the root stage of roots_device.cuh (coefficients, Aberth on the inner roots,
@@ -114,9 +115,17 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         }
         float2* uv = vec0;
         float2* wv = vec1;
+        // trace of G G^H: the sum of its eigenvalues, for the shift below
+        float tr = 0.f;
+#pragma unroll 1
+        for (int m = 0; m < M; ++m) {
+#pragma unroll
+            for (int c = 0; c < M; ++c) tr += norm2(G(m, c));
+        }
         cx<float> y[M];
         bool pconv = !nonzero;
         int pits = 0;
+        float sig = 0.f;
         for (;;) {
             // y = G^H u
 #pragma unroll
@@ -130,11 +139,24 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
                     y[c] = mkc(fmaf(g.r, um.x, fmaf(g.i, um.y, y[c].r)), fmaf(g.r, um.y, fmaf(-g.i, um.x, y[c].i)));
                 }
             }
-            // w = G y
+            if (pits == 0) {
+                // Shift: iterate with G G^H - sig I, which shrinks the noise directions by
+                // (l_i - sig) / (l_1 - sig) instead of l_i / l_1. The noise eigenvalues of a
+                // square block spread over about [0, 4 mean], so sig = 2 mean centres them; the
+                // mean comes from the trace and the Rayleigh quotient |G^H u|^2 <= l_1. sig stays
+                // below l_1 / 4, so the signal direction keeps the largest |l - sig|.
+                float rho = 0.f;
+#pragma unroll
+                for (int c = 0; c < M; ++c) rho += norm2(y[c]);
+                const float mean_noise = fmaxf(tr - rho, 0.f) * (1.f / (float)(M - 1));
+                sig = fminf(2.f * mean_noise, 0.25f * rho);
+            }
+            // w = G y - sig u
             float n2 = 0.f;
 #pragma unroll 1
             for (int m = 0; m < M; ++m) {
-                cx<float> a = mkc(0.f, 0.f);
+                const float2 um = uv[m * kSqThreads];
+                cx<float> a = mkc(-sig * um.x, -sig * um.y);
 #pragma unroll
                 for (int c = 0; c < M; ++c) {
                     const cx<float> g = G(m, c);  // w_m += g y_c
