@@ -344,6 +344,22 @@ def run_ours(args):
     step_ms_max = max_over_ranks(world, step_ms)
     value = npx * world / (step_ms_max * 1e3)
     result_gpu = out.view(len(frames), H, W).cpu().numpy()
+    # every solver variant on the same frames (register caps and the warp-per-matrix schedule of
+    # the eigenvalue sweeps), outside the timed region: the autotuner's choice, shown
+    kept = st.solver_variant
+    variants = []
+    for v in range(4):
+        rmusic.rmusic_set_solver_variant(dem.ctx, L_COV, v)
+        dem.run(x, out=out, with_status=False, stream=stream)
+        vms = []
+        for _ in range(3):
+            dem.run(x, out=out, with_status=False, stream=stream)
+            sv = dem.stats()
+            vms.append(sv.solver_ms)
+        variants.append({"variant": v, "ctas_per_sm": sv.solver_ctas_per_sm,
+                         "schedule": "warp per matrix" if v == 3 else "thread per matrix",
+                         "solver_ms": statistics.mean(vms)})
+    rmusic.rmusic_set_solver_variant(dem.ctx, L_COV, -1)
 
     # ---- plain path on the same GPU (thread per pixel, one launch per frame) -------------------
     plain = rmusic.Demodulator(device=local, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0,
@@ -393,7 +409,8 @@ def run_ours(args):
                 "peak_note": "FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "mean_jacobi_sweeps": statistics.mean(sweeps), "mean_root_iters": statistics.mean(iters),
                 "mean_root_updates": statistics.mean(updates), "mean_root_evals": statistics.mean(evals),
-                "solver_ctas_per_sm": st.solver_ctas_per_sm,
+                "solver_ctas_per_sm": st.solver_ctas_per_sm, "solver_variant": kept,
+                "solver_variants": variants,
                 "bandpass_ms": statistics.mean(bandpass_ms)}
 
     sq = run_square_leg(args, rank, world, dev, stream, flush) if args.square_steps > 0 else None

@@ -255,6 +255,16 @@ int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int device, co
 int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
                         float* d_out, void* cuda_stream);
 
+/* Batched path: pin the solver variant this context uses for covariance order `order` (row
+ * geometry) or half-width `order` (square geometry), overriding the autotuner's choice; -1 returns
+ * to it. Row geometry: variants 0, 1, 2 differ only in their register cap (2, 3 ... 16 resident
+ * CTAs per SM depending on L, identical arithmetic); variant 3 (L <= 8) runs the eigenvalue sweeps
+ * with one warp per matrix instead of one thread per matrix (the same stopping rule; results agree
+ * to FP32 rounding). Square geometry: variants 0 and 1, register caps. Useful to compare the
+ * schedules on a given GPU. Errors: RMUSIC_EINVAL (bad order or variant), RMUSIC_EUNSUPPORTED
+ * (not the batched path). */
+int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant);
+
 /* Destroy a context and free everything it owns. NULL is allowed. Waits for the context's
  * outstanding work on its device. */
 void rmusic_destroy(rmusic_ctx* ctx);
@@ -281,6 +291,7 @@ const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
  *                    call's stream) of the band-pass launches and of the solver launches.
  *   solver_ctas_per_sm  batched path: resident CTAs per SM of the solver variant last launched.
+ *   solver_variant   batched path: index of that variant (see rmusic_set_solver_variant).
  * rmusic_get_stats waits until the last call's work has finished. */
 typedef struct {
     int32_t kernel_launches;
@@ -294,7 +305,7 @@ typedef struct {
     float bandpass_ms;
     float solver_ms;
     int32_t solver_ctas_per_sm;
-    int32_t pad_;
+    int32_t solver_variant;
 } rmusic_stats;
 
 int rmusic_get_stats(const rmusic_ctx* ctx, rmusic_stats* out);

@@ -7,7 +7,7 @@ namespace rmusic {
 
 bool batched_supports(int L) { return L == 2 || L == 4 || L == 6 || L == 8 || L == 10 || L == 12; }
 
-int batched_num_variants(int) { return kSolverVariants; }
+int batched_num_variants(int L) { return solver_num_variants(L); }
 
 int batched_default_variant(int) { return kSolverDefaultVariant; }
 

@@ -29,6 +29,7 @@
 
 #include <math.h>
 
+#include "batched_variants.h"
 #include "rmusic_device.cuh"
 #include "rmusic_launch.h"
 #include "roots_device.cuh"
@@ -77,11 +78,129 @@ __device__ __forceinline__ void accumulate_s(float* S, int r, int s, cx<float> v
     }
 }
 
+// The eigenvalue sweeps of the 32 matrices of a warp item done by the whole warp, one matrix at a
+// time (the warp-per-matrix schedule): lane l holds entries (r, 2j) and (r, 2j + 1) of the full
+// symmetric S of one pixel, r = l / (L/2), j = l % (L/2) (L <= 8: at most two entries per lane).
+// A tournament step rotates the pairs (2k, 2k + 1) on both sides -- rows with the partner lane's
+// values (one shuffle pair), columns within the lane -- with the angle computed from the pair's
+// diagonal block (shuffled from the two lanes that hold it), then relabels rows and columns by
+// tperm (shuffles from the source lanes). The stopping rule is the thread-per-matrix one, applied
+// per matrix. Returns, in the caller's lane, l1, l2 and k1 of its own pixel (sh holds the parked
+// S of all 128 pixels of the CTA, one column each).
+template <int L>
+__device__ __forceinline__ void warp_jacobi_item(const float* __restrict__ sh, int wid, int lane, int max_sweeps,
+                                                 float* res_l1, float* res_l2, int* res_k1, int* res_sw,
+                                                 bool* res_conv) {
+    static_assert(L * L <= 64, "two entries per lane at most");
+    constexpr int hL = L / 2;
+    const bool act = lane < L * hL;
+    const int r = act ? lane / hL : 0, j = act ? lane % hL : 0;
+    const int c0 = 2 * j;
+    const int partner = act ? (r ^ 1) * hL + j : lane;
+    for (int mat = 0; mat < 32; ++mat) {
+        const float* Sm = sh + wid * 32 + mat;
+        float a0 = act ? Sm[tri(r, c0, L) * kBatThreads] : 0.f;
+        float a1 = act ? Sm[tri(r, c0 + 1, L) * kBatThreads] : 0.f;
+        int sweeps = 0;
+        bool conv = false;
+        float l1 = 0.f, l2 = 0.f;
+        int k1 = 0;
+        for (;;) {
+#pragma unroll 1
+            for (int stp = 0; stp < L - 1; ++stp) {
+                // rotation of the row pair kr = r / 2 and of the column pair kc = j
+                auto angle = [&](int k, float& c, float& s) {
+                    const int lp = (2 * k) * hL + k, lq = (2 * k + 1) * hL + k;
+                    const float app = __shfl_sync(kFull, a0, lp), apq = __shfl_sync(kFull, a1, lp);
+                    const float aqq = __shfl_sync(kFull, a1, lq);
+                    const float dq = aqq - app;
+                    const float den = fabsf(dq) + sqrtf(fmaf(dq, dq, 4.f * apq * apq));
+                    float t = den > 0.f ? __fdividef(2.f * apq, den) : 0.f;
+                    t = dq < 0.f ? -t : t;
+                    c = rsqrtf(fmaf(t, t, 1.f));
+                    s = t * c;
+                };
+                float cr, sr, cc, sc;
+                angle(r >> 1, cr, sr);
+                angle(j, cc, sc);
+                // rows: row_p' = c row_p - s row_q, row_q' = s row_p + c row_q
+                const float b0 = __shfl_sync(kFull, a0, partner), b1 = __shfl_sync(kFull, a1, partner);
+                if ((r & 1) == 0) {
+                    a0 = fmaf(cr, a0, -sr * b0);
+                    a1 = fmaf(cr, a1, -sr * b1);
+                } else {
+                    a0 = fmaf(sr, b0, cr * a0);
+                    a1 = fmaf(sr, b1, cr * a1);
+                }
+                // columns: col_p' = c col_p - s col_q, col_q' = s col_p + c col_q
+                const float n0 = fmaf(cc, a0, -sc * a1), n1 = fmaf(sc, a0, cc * a1);
+                a0 = n0;
+                a1 = n1;
+                // relabel: new (r, c) is old (tperm(r), tperm(c))
+                const int rr = tperm(r, L);
+                const int s0 = tperm(c0, L), s1 = tperm(c0 + 1, L);
+                const int lane0 = act ? rr * hL + (s0 >> 1) : lane, lane1 = act ? rr * hL + (s1 >> 1) : lane;
+                const float x0 = __shfl_sync(kFull, a0, lane0), y0 = __shfl_sync(kFull, a1, lane0);
+                const float x1 = __shfl_sync(kFull, a0, lane1), y1 = __shfl_sync(kFull, a1, lane1);
+                a0 = act ? ((s0 & 1) ? y0 : x0) : 0.f;
+                a1 = act ? ((s1 & 1) ? y1 : x1) : 0.f;
+            }
+            ++sweeps;
+            // off-diagonal mass (upper triangle) and the two largest diagonal entries
+            float off = 0.f, dg = -1e30f;
+            int di = L;
+            if (act) {
+                if (c0 > r) off = fmaf(a0, a0, off);
+                if (c0 + 1 > r) off = fmaf(a1, a1, off);
+                if (c0 == r) {
+                    dg = a0;
+                    di = r;
+                }
+                if (c0 + 1 == r) {
+                    dg = a1;
+                    di = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(kFull, off, o);
+            // largest diagonal entry, the smaller index on ties (as the sequential scan)
+            float bv = dg;
+            int bi = di;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(kFull, bv, o);
+                const int oi = __shfl_xor_sync(kFull, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            float sv = di == bi ? -1e30f : dg;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sv = fmaxf(sv, __shfl_xor_sync(kFull, sv, o));
+            l1 = bv;
+            l2 = sv;
+            k1 = bi;
+            const float gap = l1 - l2;
+            conv = off <= 1e-3f * gap * gap;
+            if (sweeps >= max_sweeps || conv) break;
+        }
+        if (lane == mat) {
+            *res_l1 = l1;
+            *res_l2 = l2;
+            *res_k1 = k1;
+            *res_sw = sweeps;
+            *res_conv = conv;
+        }
+    }
+}
+
 // CTAS is the number of 128-thread CTAs the kernel is compiled to keep resident per SM
 // (__launch_bounds__ minimum blocks, i.e. a register cap of 65536 / (128 CTAS)). More CTAs hide
 // more latency but spill more; the best cap depends on L and is chosen by measurement (the
-// variants of each L are listed in batched_variants.h).
-template <int L, int CTAS>
+// variants of each L are listed in batched_variants.h). WJ selects the warp-per-matrix schedule
+// of the eigenvalue sweeps (warp_jacobi_item) instead of one matrix per thread.
+template <int L, int CTAS, bool WJ = false>
 __global__ void __launch_bounds__(kBatThreads, CTAS)
 batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
                unsigned long long* __restrict__ counter, const float2* __restrict__ gam,
@@ -197,6 +316,12 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         bool jconv = false;
         float l1 = 0.f, l2 = 0.f;
         int k1 = 0;
+        if constexpr (WJ) {
+            __syncwarp();  // every lane's S is parked before the warp reads them
+            warp_jacobi_item<L>(sh_S, wid, lane, args.max_sweeps, &l1, &l2, &k1, &sweeps, &jconv);
+            // the warp-level sweep count, as the thread-per-matrix schedule reports it
+            sweeps = __reduce_max_sync(kFull, (unsigned)sweeps);
+        } else
         for (;;) {
 #pragma unroll 1
             for (int stp = 0; stp < L - 1; ++stp) {
@@ -348,6 +473,57 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             out[o] = (st == kStOk || st == kStNotConverged) ? om : __int_as_float(0x7fc00000);
             if (status) status[o] = st;
         }
+    }
+}
+
+// Launch and occupancy of variant v of the solver for covariance order L (batched_variants.h).
+template <int L, int V>
+static cudaError_t launch_solver_v(const FrameDev* d_frames, int nframes, int64_t total_items,
+                                   unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                                   uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
+    batched_kernel<L, solver_variant_ctas(L, V), solver_variant_warp(V)><<<grid, kBatThreads, 0, stream>>>(
+        d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a);
+    return cudaGetLastError();
+}
+
+template <int L, int V>
+static int occupancy_solver_v() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, batched_kernel<L, solver_variant_ctas(L, V), solver_variant_warp(V)>, kBatThreads, 0) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+template <int L>
+cudaError_t launch_solver_t(int v, const FrameDev* d_frames, int nframes, int64_t total_items,
+                            unsigned long long* d_counter, const float2* d_gamma, float* d_out, uint8_t* d_status,
+                            BatchedArgs a, int grid, cudaStream_t s) {
+    switch (v) {
+        case 0: return launch_solver_v<L, 0>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, s);
+        case 1: return launch_solver_v<L, 1>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, s);
+        case 2: return launch_solver_v<L, 2>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, s);
+        case 3:
+            if constexpr (L <= 8)
+                return launch_solver_v<L, 3>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, s);
+            else
+                return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int L>
+int occupancy_solver_t(int v) {
+    switch (v) {
+        case 0: return occupancy_solver_v<L, 0>();
+        case 1: return occupancy_solver_v<L, 1>();
+        case 2: return occupancy_solver_v<L, 2>();
+        case 3:
+            if constexpr (L <= 8)
+                return occupancy_solver_v<L, 3>();
+            else
+                return 1;
+        default: return 1;
     }
 }
 

@@ -1,83 +1,25 @@
-// batched_l2_l4.cu -- instantiations of the FP32-batched solver for covariance order(s) 2, 4, all register-cap variants (see batched_variants.h).
+// batched_l2_l4.cu -- instantiations of the FP32-batched solver for covariance order(s) 2, 4, all variants (see batched_variants.h).
 #include "batched_kernel.cuh"
 #include "batched_variants.h"
 
 namespace rmusic {
 
-template <int V>
-static cudaError_t launch_l2_v(const FrameDev* d_frames, int nframes, int64_t total_items,
-                                unsigned long long* d_counter, const float2* d_gamma, float* d_out,
-                                uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
-    batched_kernel<2, solver_variant_ctas(2, V)><<<grid, kBatThreads, 0, stream>>>(
-        d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a);
-    return cudaGetLastError();
-}
-
-template <int V>
-static int occupancy_l2_v() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel<2, solver_variant_ctas(2, V)>,
-                                                      kBatThreads, 0) != cudaSuccess)
-        return 1;
-    return nb > 0 ? nb : 1;
-}
-
 cudaError_t launch_solver_l2(int v, const FrameDev* d_frames, int nframes, int64_t total_items,
-                               unsigned long long* d_counter, const float2* d_gamma, float* d_out,
-                               uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
-    switch (v) {
-        case 0: return launch_l2_v<0>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        case 1: return launch_l2_v<1>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        case 2: return launch_l2_v<2>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        default: return cudaErrorInvalidValue;
-    }
+                             unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                             uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
+    return launch_solver_t<2>(v, d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid,
+                              stream);
 }
 
-int occupancy_solver_l2(int v) {
-    switch (v) {
-        case 0: return occupancy_l2_v<0>();
-        case 1: return occupancy_l2_v<1>();
-        case 2: return occupancy_l2_v<2>();
-        default: return 1;
-    }
-}
-
-template <int V>
-static cudaError_t launch_l4_v(const FrameDev* d_frames, int nframes, int64_t total_items,
-                                unsigned long long* d_counter, const float2* d_gamma, float* d_out,
-                                uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
-    batched_kernel<4, solver_variant_ctas(4, V)><<<grid, kBatThreads, 0, stream>>>(
-        d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a);
-    return cudaGetLastError();
-}
-
-template <int V>
-static int occupancy_l4_v() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel<4, solver_variant_ctas(4, V)>,
-                                                      kBatThreads, 0) != cudaSuccess)
-        return 1;
-    return nb > 0 ? nb : 1;
-}
+int occupancy_solver_l2(int v) { return occupancy_solver_t<2>(v); }
 
 cudaError_t launch_solver_l4(int v, const FrameDev* d_frames, int nframes, int64_t total_items,
-                               unsigned long long* d_counter, const float2* d_gamma, float* d_out,
-                               uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
-    switch (v) {
-        case 0: return launch_l4_v<0>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        case 1: return launch_l4_v<1>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        case 2: return launch_l4_v<2>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        default: return cudaErrorInvalidValue;
-    }
+                             unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                             uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
+    return launch_solver_t<4>(v, d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid,
+                              stream);
 }
 
-int occupancy_solver_l4(int v) {
-    switch (v) {
-        case 0: return occupancy_l4_v<0>();
-        case 1: return occupancy_l4_v<1>();
-        case 2: return occupancy_l4_v<2>();
-        default: return 1;
-    }
-}
+int occupancy_solver_l4(int v) { return occupancy_solver_t<4>(v); }
 
 }  // namespace rmusic

@@ -1,45 +1,16 @@
-// batched_l8.cu -- instantiations of the FP32-batched solver for covariance order(s) 8, all register-cap variants (see batched_variants.h).
+// batched_l8.cu -- instantiations of the FP32-batched solver for covariance order(s) 8, all variants (see batched_variants.h).
 #include "batched_kernel.cuh"
 #include "batched_variants.h"
 
 namespace rmusic {
 
-template <int V>
-static cudaError_t launch_l8_v(const FrameDev* d_frames, int nframes, int64_t total_items,
-                                unsigned long long* d_counter, const float2* d_gamma, float* d_out,
-                                uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
-    batched_kernel<8, solver_variant_ctas(8, V)><<<grid, kBatThreads, 0, stream>>>(
-        d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a);
-    return cudaGetLastError();
-}
-
-template <int V>
-static int occupancy_l8_v() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batched_kernel<8, solver_variant_ctas(8, V)>,
-                                                      kBatThreads, 0) != cudaSuccess)
-        return 1;
-    return nb > 0 ? nb : 1;
-}
-
 cudaError_t launch_solver_l8(int v, const FrameDev* d_frames, int nframes, int64_t total_items,
-                               unsigned long long* d_counter, const float2* d_gamma, float* d_out,
-                               uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
-    switch (v) {
-        case 0: return launch_l8_v<0>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        case 1: return launch_l8_v<1>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        case 2: return launch_l8_v<2>(d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid, stream);
-        default: return cudaErrorInvalidValue;
-    }
+                             unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                             uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream) {
+    return launch_solver_t<8>(v, d_frames, nframes, total_items, d_counter, d_gamma, d_out, d_status, a, grid,
+                              stream);
 }
 
-int occupancy_solver_l8(int v) {
-    switch (v) {
-        case 0: return occupancy_l8_v<0>();
-        case 1: return occupancy_l8_v<1>();
-        case 2: return occupancy_l8_v<2>();
-        default: return 1;
-    }
-}
+int occupancy_solver_l8(int v) { return occupancy_solver_t<8>(v); }
 
 }  // namespace rmusic

@@ -1,6 +1,7 @@
-// batched_variants.h -- register-cap variants of the FP32-batched solver per covariance order.
-// Each variant keeps a different number of 128-thread CTAs resident per SM (its
-// __launch_bounds__ minimum); the autotuner in capi.cu times them and keeps the fastest.
+// batched_variants.h -- variants of the FP32-batched solver per covariance order: register caps
+// (how many 128-thread CTAs stay resident per SM, the __launch_bounds__ minimum) and, for L <= 8,
+// the warp-per-matrix schedule of the eigenvalue sweeps; the autotuner in capi.cu times them and
+// keeps the fastest.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,12 +12,19 @@
 
 namespace rmusic {
 
+// Variants 0 .. 2 of every L differ only in their register cap (identical arithmetic); variant 3
+// (L <= 8) runs the eigenvalue sweeps with the warp-per-matrix schedule at variant 1's cap.
 constexpr int kSolverVariants = 3;
+constexpr int kSolverWarpVariant = 3;
 constexpr int kSolverDefaultVariant = 1;
 
-// Resident CTAs per SM of variant v (0 .. kSolverVariants - 1) for covariance order L.
+__host__ __device__ constexpr int solver_num_variants(int L) { return L <= 8 ? 4 : 3; }
+__host__ __device__ constexpr bool solver_variant_warp(int v) { return v == kSolverWarpVariant; }
+
+// Resident CTAs per SM of variant v for covariance order L.
 __host__ __device__ constexpr int solver_variant_ctas(int L, int v) {
-    return L == 2 ? (v == 0 ? 8 : v == 1 ? 12 : 16)
+    return v == kSolverWarpVariant ? solver_variant_ctas(L, kSolverDefaultVariant)
+         : L == 2 ? (v == 0 ? 8 : v == 1 ? 12 : 16)
          : L == 4 ? (v == 0 ? 6 : v == 1 ? 8 : 12)
          : L == 6 ? (v == 0 ? 4 : v == 1 ? 6 : 8)
          : L == 8 ? (v == 0 ? 4 : v == 1 ? 6 : 8)

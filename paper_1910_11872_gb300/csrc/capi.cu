@@ -500,7 +500,9 @@ int tune_plan(rmusic_ctx* ctx, const Plan& plan, float* d_out, uint8_t* d_status
         if (!force && solver_tuned(ctx, L)) continue;
         float best = 1e30f;
         int bestv = solver_default_variant(L);
-        for (int v = 0; v < solver_num_variants(L) && rc == RMUSIC_OK; ++v) {
+        // highest variant first: the last one run (variant 0, a register-cap variant) leaves the
+        // call's maps exactly as the default variant computes them
+        for (int v = solver_num_variants(L) - 1; v >= 0 && rc == RMUSIC_OK; --v) {
             float tmin = 1e30f;
             for (int rep = 0; rep < 2 && rc == RMUSIC_OK; ++rep) {
                 cudaError_t e = cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s);
@@ -557,6 +559,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
             RM_CUDA(launch_solver(ctx, plan, g, v, d_out, d_status, ctx->d_counters + kStatSlot, s));
             stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
             ctx->stats.solver_ctas_per_sm = solver_ctas(L, v);
+            ctx->stats.solver_variant = v;
             ++*launches;
         }
         if (p.unwrap) {
@@ -894,6 +897,20 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
     RM_CUDA(cudaMemcpyAsync(h_out, ctx->d_out, out_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
     if (h_status) RM_CUDA(cudaMemcpyAsync(h_status, ctx->d_st, st_elems, cudaMemcpyDeviceToHost, s));
     RM_CUDA(cudaStreamSynchronize(s));
+    return RMUSIC_OK;
+}
+
+int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant) {
+    if (!ctx || ctx->p.precision != RMUSIC_FP32_BATCHED) return ctx ? RMUSIC_EUNSUPPORTED : RMUSIC_EINVAL;
+    const int key = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? kSquareKey0 + order : order;
+    if (order < 1 || key < 0 || key >= kKeys || !solver_supports(key)) return RMUSIC_EINVAL;
+    if (variant < -1 || variant >= solver_num_variants(key)) return RMUSIC_EINVAL;
+    ctx->variant_by_L[key] = variant;
+    for (auto& g : ctx->graphs) {  // captured graphs hold the previous variant
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.h_table) cudaFreeHost(g.h_table);
+        g = GraphEntry{};
+    }
     return RMUSIC_OK;
 }
 

@@ -93,7 +93,7 @@ class rmusic_stats(ctypes.Structure):
         ("bandpass_ms", ctypes.c_float),
         ("solver_ms", ctypes.c_float),
         ("solver_ctas_per_sm", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("solver_variant", ctypes.c_int32),
     ]
 
 
@@ -145,6 +145,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_strerror.restype = ctypes.c_char_p
         lib.rmusic_last_cuda_error.argtypes = [vp]
         lib.rmusic_last_cuda_error.restype = ctypes.c_char_p
+        lib.rmusic_set_solver_variant.argtypes = [vp, i32, i32]
+        lib.rmusic_set_solver_variant.restype = ctypes.c_int
         lib.rmusic_unwrap_phase.argtypes = [vp, vp, ctypes.POINTER(rmusic_frame_desc), i32, vp, vp]
         lib.rmusic_unwrap_phase.restype = ctypes.c_int
         lib.rmusic_get_stats.argtypes = [vp, ctypes.POINTER(rmusic_stats)]
@@ -229,6 +231,13 @@ def rmusic_unwrap_phase(ctx, d_phase: int, descs, n_frames: int, d_out: int, cud
                                             cuda_stream or None)
     if rc != RMUSIC_OK:
         raise RmusicError(rc, "rmusic_unwrap_phase", rmusic_last_cuda_error(ctx))
+    return rc
+
+
+def rmusic_set_solver_variant(ctx, order: int, variant: int) -> int:
+    rc = load_library().rmusic_set_solver_variant(ctx, int(order), int(variant))
+    if rc != RMUSIC_OK:
+        raise RmusicError(rc, "rmusic_set_solver_variant")
     return rc
 
 

@@ -455,3 +455,38 @@ def test_autotune_variants_identical_and_cached(tmp_path, monkeypatch):
     assert np.array_equal(again, flat_ref, equal_nan=True)
     lines = cache.read_text().strip().splitlines()
     assert {int(l.split('"L": ')[1].split(",")[0]) for l in lines} == {6, 8}
+
+
+@pytest.mark.parametrize("L", [4, 6, 8])
+def test_solver_variants_and_warp_per_matrix_schedule(L):
+    """Variants 0-2 (register caps) compute identical maps; variant 3 runs the eigenvalue sweeps with
+    one warp per matrix and agrees with them to FP32 rounding, statuses included."""
+    torch = _torch()
+    frames = [synth.peaks_frame(10, 0.1, H=40, W=256).image, synth.peaks_frame(np.inf, 0.1, H=24, W=256).image]
+    x = torch.from_numpy(np.concatenate([f.ravel() for f in frames])).cuda()
+    descs, _, nout = rmusic.frame_descs([f.shape for f in frames], rmusic.RMUSIC_DTYPE_F32, 4)
+    maps = []
+    dem = rmusic.Demodulator(cov_order=L)
+    try:
+        for v in range(4):
+            rmusic.rmusic_set_solver_variant(dem.ctx, L, v)
+            out = torch.empty(nout, device="cuda")
+            st = torch.empty(nout, dtype=torch.uint8, device="cuda")
+            rmusic.rmusic_demodulate_frames(dem.ctx, x.data_ptr(), descs, 2, out.data_ptr(), st.data_ptr(), None)
+            torch.cuda.synchronize()
+            assert dem.stats().solver_variant == v
+            maps.append((out.cpu().numpy(), st.cpu().numpy()))
+        with pytest.raises(rmusic.RmusicError):
+            rmusic.rmusic_set_solver_variant(dem.ctx, L, 4)
+    finally:
+        dem.close()
+    for v in (0, 2):
+        assert np.array_equal(maps[v][0], maps[1][0], equal_nan=True) and np.array_equal(maps[v][1], maps[1][1])
+    g, gs = maps[3]
+    assert np.array_equal(gs, maps[1][1])
+    ok = gs == 0
+    assert np.abs(g[ok] - maps[1][0][ok]).max() <= 1e-5
+    o, os_ = oracle_run(frames[1], 32, L, 1)
+    off = frames[0].size
+    v = (os_.ravel() == 0) & (gs[off:] == 0)
+    assert np.abs(g[off:][v] - o.ravel()[v]).max() <= 1e-4
