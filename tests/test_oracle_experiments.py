@@ -8,6 +8,8 @@ complex fringe, phi = peaks scaled to 0-150 rad, the paper's 0 dB):
   * Fig. 4: the error falls as the SNR rises.
 Errors are those of the local phase alpha on 1500 sampled pixels away from the borders.
 """
+import os
+
 import numpy as np
 
 import oracle as O
@@ -26,12 +28,17 @@ def _samples(n=1500):
     return rng.integers(E.MARGIN, 512 - E.MARGIN, n), rng.integers(E.MARGIN, 512 - E.MARGIN, n)
 
 
+def _paper_best_half_width():
+    t = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "paper_table1_phase_rmse_vs_half_width.txt"))
+    return int(t[np.argmin(t[:, 1]), 0])
+
+
 def test_error_against_half_width_has_the_papers_u_shape():
     fr = synth.complex_fringe_frame(0.0, 512, 512, 150.0)
     ys, xs = _samples()
     r = [_alpha_rmse(fr, Lp, ys, xs) for Lp in range(1, 9)]
     best = int(np.argmin(r)) + 1
-    assert 3 <= best <= 5, r
+    assert abs(best - _paper_best_half_width()) <= 1, r  # Table 1: minimum at Lp = 4
     assert r[0] > 4 * min(r) and r[-1] > 1.5 * min(r), r
     assert all(r[i] > r[i + 1] for i in range(best - 1)), r            # falling to the minimum
     assert all(r[i] < r[i + 1] for i in range(best - 1, 7)), r         # rising after it
