@@ -87,43 +87,65 @@ def aberth_flops(L: int, evals: float, updates: float) -> float:
     return evals * (16 * NR + 4) + updates * (11 + 10 * (2 * NI - 1) + 21 + 8)
 
 
-def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float) -> float:
+def newton_flops(L: int) -> float:
+    """One Newton step of the signal root (degree 2L - 2): Horner for Q and Q' (16 per step), the
+    Newton ratio, the mirror, the deflated correction (three complex divisions, 11 each), the
+    update and the fold (6) and the tests (4)."""
+    return 16 * (2 * L - 2) + 4 + 3 * 11 + 6 + 4
+
+
+def schur_cohn_flops(L: int) -> float:
+    """The Schur-Cohn count on Q(r z), n = 2L - 2: the scaled coefficients (3 per coefficient), then
+    per level of degree d the two moduli (6), the reflection coefficient (9) and d complex
+    multiply-subtracts (8 each), and the count."""
+    n = 2 * L - 2
+    return 3 * (n + 1) + sum(15 + 8 * d for d in range(1, n + 1)) + n
+
+
+def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float, power_steps: float = 0.0,
+                    eig_fallback: float = 0.0, newton: float = 0.0, root_fallback: float = 0.0) -> float:
     """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1),
-    counted from the kernel's steps with the measured sweeps, root evaluations and executed root
-    updates per 32-pixel work item:
+    counted from the kernel's steps with the measured work per 32-pixel work item (power steps,
+    Jacobi sweeps and fallbacks, Newton steps, Aberth evaluations, updates and fallbacks):
       covariance  per lag: (31 + N) / 32 lag products (6) and prefix adds (2) per pixel, a 5-step
                   warp scan (10); per R_f entry: box difference (2) and accumulation into S (6)
-      Jacobi      per rotation 14 + 6 (L - 2) + 4, L/2 rotations per step, L - 1 steps per sweep,
-                  plus the off-diagonal norm L (L - 1)
-      inverse it. L D L^T of (mu I - S), two forward / diagonal / backward solves with norms
+      power it.   start column and Frobenius norm; per step S x (2 L^2), Rayleigh quotient, shift,
+                  norm and the step size (10 L + 5)
+      fallback    Jacobi: per rotation 14 + 6 (L - 2) + 4, L/2 rotations per step, L - 1 steps per
+                  sweep, plus the off-diagonal norm L (L - 1); inverse iteration: L D L^T of
+                  (mu I - S), two forward / diagonal / backward solves with norms
       polynomial  u = Q x (2 L), rho_k (8 flops per term), scaling and moduli
-      Aberth      aberth_flops: per executed evaluation of Q, Q' and per executed root update
+      roots       Newton steps (newton_flops), the Schur-Cohn certificate (schur_cohn_flops); Aberth
+                  fallback: aberth_flops per executed evaluation and update, starting points, selection
       polish      two Horner passes of Q, Q', Q'' (24 per step) and the step (20), angle (20)
     """
     NS = L * (L + 1) // 2
     NR = 2 * L - 2
     NI = L - 1
     cov = L * ((31 + N) / 32 * 8 + 10) + NS * 8 + L + NS + 1
+    power = 2 * L + 3 * NS + 3 * L + 1 + power_steps * (2 * L * L + 10 * L + 5)
     rot = 14 + 6 * (L - 2) + 4
     jac = sweeps * ((L - 1) * (L // 2) * rot + L * (L - 1))
     ldl = sum(3 * j + 1 + (L - 1 - j) * (3 * j + 1) for j in range(L))
-    inv = ldl + 2 * (2 * L * (L - 1) + 4 * L)
+    inv = eig_fallback * (ldl + 2 * (2 * L * (L - 1) + 4 * L))
     coef = 2 * L + 3 * L + 4 * L * (L - 1) + 5 * (L - 1)
-    aberth = aberth_flops(L, evals, updates) + NI * 10 + 20  # plus the starting points
-    polish = 2 * (24 * NR + 20) + 20 + 13 * NI  # plus the selection
-    return cov + jac + inv + coef + aberth + polish
+    roots = newton * newton_flops(L) + schur_cohn_flops(L)
+    aberth = aberth_flops(L, evals, updates) + root_fallback * (NI * 10 + 20 + 13 * NI)
+    polish = 2 * (24 * NR + 20) + 20
+    return cov + power + jac + inv + coef + roots + aberth + polish
 
 
-def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: float) -> float:
+def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: float, newton: float = 0.0,
+                           root_fallback: float = 0.0) -> float:
     """Algorithmic FP32 flops per pixel of the square-block solver (block side M = 2 Lp + 1), from
-    its steps with the measured power-iteration steps, root evaluations and root updates (the root
-    figures add both polynomials):
+    its steps with the measured power-iteration steps, Newton steps, Aberth evaluations, updates and
+    fallbacks (the root figures add both polynomials):
       power it.   per step G^H u and G y (M^2 complex multiply-adds each, 8 flops), the norm (3 M),
                   normalisation and step size (8 M); the start vector (5 M)
       polynomials per axis: |u|^2 (3 M), M (M - 1) / 2 lag products (8), scaling and moduli (8 per lag)
-      Aberth      aberth_flops, plus the starting points (10 per root + 20) per axis
-      select      per axis: moduli and nearest-neighbour search (13 per root), two polish steps
-                  (24 per Horner step of degree 2M - 2, plus 20), angle (20)
+      roots       Newton steps (newton_flops) and per axis the Schur-Cohn certificate; Aberth fallback:
+                  aberth_flops, starting points (10 per root + 20) and selection (13 per root)
+      polish      per axis two polish steps (24 per Horner step of degree 2M - 2, plus 20), angle (20)
       alpha       four sincos (80), the recurrences (6 M), M^2 complex multiply-adds, M row terms
                   (16 M), angle and carrier phase (25)
     """
@@ -131,10 +153,11 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
     NI, NR = M - 1, 2 * M - 2
     power = 5 * M + power_its * (16 * M * M + 11 * M)
     coefs = 2 * (3 * M + 4 * M * (M - 1) + 8 * (M - 1))
-    roots = aberth_flops(M, evals, updates) + 2 * (10 * NI + 20)
-    select = 2 * (13 * NI + 2 * (24 * NR + 20) + 20)
+    roots = newton * newton_flops(M) + 2 * schur_cohn_flops(M)
+    aberth = aberth_flops(M, evals, updates) + root_fallback * (10 * NI + 20 + 13 * NI)
+    select = 2 * (2 * (24 * NR + 20) + 20)
     alpha = 80 + 6 * M + 8 * M * M + 16 * M + 25
-    return power + coefs + roots + select + alpha
+    return power + coefs + roots + aberth + select + alpha
 
 
 SOLVER_PROFILE = os.path.join(ROOT, "profiles", "batched_solver_L8_peaks4x1024.md")
@@ -325,6 +348,7 @@ def run_ours(args):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     solver_ms, bandpass_ms, launches, sweeps, iters, updates, evals = [], [], 0, [], [], [], []
+    psteps, eigfb, newton, rootfb = [], [], [], []
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -338,6 +362,10 @@ def run_ours(args):
         iters.append(st.mean_root_iters)
         updates.append(st.mean_root_updates)
         evals.append(st.mean_root_evals)
+        psteps.append(st.mean_power_steps)
+        eigfb.append(st.eig_fallback_frac)
+        newton.append(st.mean_newton_steps)
+        rootfb.append(st.root_fallback_frac)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -400,7 +428,9 @@ def run_ours(args):
     e2e_value = npx * world / (e2e_ms * 1e3)
 
     # ---- roofline of the dominant kernel (batched solver) ---------------------------------------
-    fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(evals), statistics.mean(updates))
+    fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(evals), statistics.mean(updates),
+                          statistics.mean(psteps), statistics.mean(eigfb), statistics.mean(newton),
+                          statistics.mean(rootfb))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
     traffic = profiled_traffic()
@@ -408,8 +438,10 @@ def run_ours(args):
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "batched_kernel<8>", "flops_per_pixel": fpp, "launch_ms": solver_avg,
                 "peak_note": "FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
-                "mean_jacobi_sweeps": statistics.mean(sweeps), "mean_root_iters": statistics.mean(iters),
-                "mean_root_updates": statistics.mean(updates), "mean_root_evals": statistics.mean(evals),
+                "mean_power_steps": statistics.mean(psteps), "eig_fallback_frac": statistics.mean(eigfb),
+                "mean_jacobi_sweeps": statistics.mean(sweeps), "mean_newton_steps": statistics.mean(newton),
+                "root_fallback_frac": statistics.mean(rootfb), "mean_aberth_iters": statistics.mean(iters),
+                "mean_aberth_updates": statistics.mean(updates), "mean_aberth_evals": statistics.mean(evals),
                 "solver_ctas_per_sm": st.solver_ctas_per_sm, "solver_variant": kept,
                 "solver_variants": variants,
                 "bandpass_ms": statistics.mean(bandpass_ms)}
@@ -475,7 +507,7 @@ def run_square_leg(args, rank, world, dev, stream, flush):
     barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.square_steps)]
-    solver_ms, its, evals, updates, launches = [], [], [], [], 0
+    solver_ms, its, evals, updates, launches, newton, rootfb = [], [], [], [], 0, [], []
     for k in range(args.square_steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -486,11 +518,14 @@ def run_square_leg(args, rank, world, dev, stream, flush):
         its.append(st.mean_sweeps)
         evals.append(st.mean_root_evals)
         updates.append(st.mean_root_updates)
+        newton.append(st.mean_newton_steps)
+        rootfb.append(st.root_fallback_frac)
         launches += st.kernel_launches
     torch.cuda.synchronize()
     step_ms = max_over_ranks(world, statistics.mean(a.elapsed_time(b) for a, b in ev))
     value = npx * world / (step_ms * 1e3)
-    fpp = square_flops_per_pixel(SQ_LP, statistics.mean(its), statistics.mean(evals), statistics.mean(updates))
+    fpp = square_flops_per_pixel(SQ_LP, statistics.mean(its), statistics.mean(evals), statistics.mean(updates),
+                                 statistics.mean(newton), statistics.mean(rootfb))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
     res = {"workload": SQ_WORKLOAD, "value": value, "unit": "Mpixel/s", "ms_per_step": step_ms,
@@ -500,7 +535,8 @@ def run_square_leg(args, rank, world, dev, stream, flush):
                         "traffic": profiled_traffic(SQUARE_PROFILE, SQUARE_SOURCES),
                         "kernel": f"square_kernel<{SQ_LP}, {st.solver_ctas_per_sm}>", "flops_per_pixel": fpp,
                         "launch_ms": solver_avg, "mean_power_iters": statistics.mean(its),
-                        "mean_root_evals": statistics.mean(evals), "mean_root_updates": statistics.mean(updates)},
+                        "mean_newton_steps": statistics.mean(newton), "root_fallback_frac": statistics.mean(rootfb),
+                        "mean_aberth_evals": statistics.mean(evals), "mean_aberth_updates": statistics.mean(updates)},
            "paper_table2_context": PAPER_TABLE2_1024}
 
     # the paper's full method: the same call with phase assembly (the alpha maps unwrapped into a

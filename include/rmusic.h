@@ -118,6 +118,12 @@ extern "C" {
  *   raw_input        1: no band-pass; the window holds the real samples of the carrier line minus
  *                    the line's mean (for model_order 2 or 3). Needs the row geometry with
  *                    deriv_axis == carrier_axis (the carrier decides which of +-omega is meant).
+ *   exhaustive       batched path: 0 (default) finds the selected root by Newton's method and
+ *                    certifies it with a Schur-Cohn root count (every root is computed only where
+ *                    the certificate fails), and the row geometry's eigenvector by power iteration
+ *                    (Jacobi sweeps only where it does not settle); 1 computes every inner root by
+ *                    Aberth-Ehrlich and, in the row geometry, runs the Jacobi sweeps for every
+ *                    pixel. Both select the same root; 1 is slower.
  * carrier_freq may be 0 (no carrier) for complex frames; for real frames it must lie in (0, 0.5).
  */
 typedef struct {
@@ -141,6 +147,7 @@ typedef struct {
     int32_t unwrap;
     double band_cross;
     int32_t raw_input;
+    int32_t exhaustive;
 } rmusic_params;
 
 /* One frame of a batch. Frames of one call may differ in size, type and window.
@@ -280,14 +287,20 @@ const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
  *   graph_replayed   1 if the last call replayed a cached CUDA graph.
  *   workspace_bytes  device bytes the context currently holds.
  *   pixels           pixels of all frames of the last call.
- *   mean_sweeps      batched path: Jacobi sweeps per 32-pixel work item, averaged.
- *   mean_root_iters  batched path: Aberth iterations per 32-pixel work item, averaged.
+ *   mean_sweeps      batched path: Jacobi sweeps per 32-pixel work item, averaged (the eigen
+ *                    fallback's; 0 where the power iteration sufficed).
+ *   mean_root_iters  batched path: Aberth iterations per 32-pixel work item, averaged (the root
+ *                    fallback's; 0 where the Newton root was certified in every lane).
  *   mean_root_updates batched path: Aberth root updates a warp executed per work item, averaged
  *                    (roots already converged in every lane of the warp are skipped).
- *   mean_root_evals  batched path: evaluations of Q and Q' a warp executed per work item, averaged
- *                    (a root frozen in every lane of the warp is not evaluated).
+ *   mean_root_evals  batched path: Aberth evaluations of Q and Q' a warp executed per work item,
+ *                    averaged (a root frozen in every lane of the warp is not evaluated).
+ *   mean_power_steps row geometry: power-iteration steps per work item, averaged.
+ *   eig_fallback_frac row geometry: fraction of work items whose warp ran the Jacobi fallback.
+ *   mean_newton_steps batched path: Newton steps of the signal root per work item, averaged.
+ *   root_fallback_frac batched path: fraction of work items whose warp ran the Aberth fallback.
  *   In the square geometry a work item is one warp's 32 pixels of a tile row, mean_sweeps counts
- *   power-iteration steps, and the root figures add both polynomials.
+ *   power-iteration steps, and the root figures add both polynomials (root_fallback_frac up to 2).
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
  *                    call's stream) of the band-pass launches and of the solver launches.
  *   solver_ctas_per_sm  batched path: resident CTAs per SM of the solver variant last launched.
@@ -306,6 +319,10 @@ typedef struct {
     float solver_ms;
     int32_t solver_ctas_per_sm;
     int32_t solver_variant;
+    double mean_power_steps;
+    double eig_fallback_frac;
+    double mean_newton_steps;
+    double root_fallback_frac;
 } rmusic_stats;
 
 int rmusic_get_stats(const rmusic_ctx* ctx, rmusic_stats* out);

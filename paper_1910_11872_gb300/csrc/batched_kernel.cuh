@@ -14,14 +14,15 @@
 //   FB -> S   with forward-backward averaging R = (R_f + J conj(R_f) J)/2 is centro-Hermitian,
 //             so with the unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) (even L) S = Q^H R Q =
 //             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x.
-//   eigen     cyclic Jacobi sweeps on S (real, register resident, tournament order) until the
-//             largest diagonal entry is close to l1 relative to the eigen-gap (usually one
-//             sweep); then three steps of inverse iteration with (mu I - S) = L D L^T, mu just
-//             above that entry, give the signal eigenvector x1 without accumulating rotations
-//             (Eq. 8-11).
-//   poly,     u1 = Q x1; the root-MUSIC coefficients, Aberth-Ehrlich on the roots inside the
-//   roots,    unit disk, the root nearest the circle and its polish (roots_device.cuh, shared
-//   select    with the square-block solver).
+//   eigen     the signal eigenvector x1 of S (Eq. 8-11) by the shifted power iteration, from the
+//             column of S with the largest diagonal entry (2-3 steps on signal-dominated windows);
+//             lanes whose iteration does not settle or whose eigen-gap is not certified by the
+//             Frobenius bound |l2| <= sqrt(|S|_F^2 - l1^2) take cyclic Jacobi sweeps on S (real,
+//             register resident, tournament order) and three steps of inverse iteration.
+//   poly,     u1 = Q x1; the root-MUSIC coefficients; the root nearest the unit circle inside it,
+//   roots,    by Newton's method with a Schur-Cohn certificate (full Aberth-Ehrlich when the
+//   select    certificate fails), and its polish (roots_device.cuh, shared with the square-block
+//             solver).
 //   angle     atan2 of the root minus the carrier step, wrapped (Eq. 15).
 // This header holds the kernel template; batched_l*.cu instantiate it for each covariance order
 // and register-cap variant (compiled in parallel), batched.cu dispatches among them.
@@ -195,6 +196,206 @@ __device__ __forceinline__ void warp_jacobi_item(const float* __restrict__ sh, i
     }
 }
 
+// Signal eigenvector x of the real-symmetric S (packed upper triangle, trace-normalised) by the
+// shifted power iteration x <- (S - sig I) x / |.|, started from the column of S with the largest
+// diagonal entry (for a rank-one S that column is already the eigenvector). The shift
+// sig = min(mean of the other eigenvalues, rho / 4), rho the current Rayleigh quotient, centres
+// the noise eigenvalues, which lie around their mean, so each step shrinks them by
+// max |l_i - sig| / (l1 - sig) instead of l2 / l1. A lane stops moving when a step changes x by
+// less than 1e-6; the warp stops when every lane has or after 24 steps (conv false). Returns
+// l1 = rho and, as l2, the bound sqrt(|S|_F^2 - rho^2) >= sqrt(sum_{i > 1} l_i^2) >= |l2|.
+template <int L>
+__device__ __forceinline__ void power_eigvec(const float (&S)[L * (L + 1) / 2], const float* Ssh, float (&x)[L],
+                                             float& l1, float& l2, int& steps, bool& conv) {
+    float trS = 0.f, fro2 = 0.f, dmax = -1.f;
+    int kd = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const float v = S[tri(i, i, L)];
+        trS += v;
+        if (v > dmax) {
+            dmax = v;
+            kd = i;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+#pragma unroll
+        for (int j = i; j < L; ++j) fro2 = fmaf((i == j ? 1.f : 2.f) * S[tri(i, j, L)], S[tri(i, j, L)], fro2);
+    {
+        float n2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            x[i] = Ssh[tri(i, kd, L) * kBatThreads];
+            n2 = fmaf(x[i], x[i], n2);
+        }
+        const float inv = rsqrtf(n2);
+#pragma unroll
+        for (int i = 0; i < L; ++i) x[i] *= inv;
+    }
+    steps = 0;
+    conv = false;
+    float rho = dmax;
+#pragma unroll 1
+    for (;;) {
+        float y[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            float a = 0.f;
+#pragma unroll
+            for (int j = 0; j < L; ++j) a = fmaf(S[tri(i, j, L)], x[j], a);
+            y[i] = a;
+        }
+        float rr = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) rr = fmaf(x[i], y[i], rr);
+        rho = rr;
+        const float sig = fminf((trS - rr) * (1.f / (float)(L - 1)), 0.25f * rr);
+        float n2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            y[i] = fmaf(-sig, x[i], y[i]);
+            n2 = fmaf(y[i], y[i], n2);
+        }
+        const float inv = rsqrtf(n2);
+        float d2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const float v = y[i] * inv;
+            const float d = v - x[i];
+            d2 = fmaf(d, d, d2);
+            x[i] = v;
+        }
+        ++steps;
+        conv = conv || d2 <= 1e-12f;
+        if (steps >= 24 || __all_sync(kFull, conv)) break;
+    }
+    l1 = rho;
+    const float u2 = fro2 - rho * rho;
+    l2 = u2 > 0.f ? sqrtf(u2) : 0.f;
+}
+
+// Three steps of inverse iteration with (mu I - S) = L D L^T, mu = l1 (1 + 1e-5) just above the
+// largest eigenvalue estimate l1, from column k1 of S (S read from the thread's parked column).
+template <int L>
+__device__ __forceinline__ void inverse_iteration(const float* Ssh, float l1, int k1, float (&x)[L]) {
+    constexpr int NS = L * (L + 1) / 2;
+    const float mu = l1 + 1e-5f * l1 + 1e-30f;
+    float Lm[NS];  // unit lower factor in the packed layout, D on the diagonal slots
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        float dj = mu - Ssh[tri(j, j, L) * kBatThreads];
+#pragma unroll
+        for (int k = 0; k < j; ++k) dj = fmaf(-Lm[tri(j, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], dj);
+        if (fabsf(dj) < 1e-30f) dj = dj < 0.f ? -1e-30f : 1e-30f;
+        Lm[tri(j, j, L)] = dj;
+        const float inv = frcp(dj);
+#pragma unroll
+        for (int i = j + 1; i < L; ++i) {
+            float v = -Ssh[tri(i, j, L) * kBatThreads];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v = fmaf(-Lm[tri(i, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], v);
+            Lm[tri(i, j, L)] = v * inv;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) x[i] = Ssh[tri(i, k1, L) * kBatThreads];
+#pragma unroll 1
+    for (int step = 0; step < 3; ++step) {
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+#pragma unroll
+            for (int k = 0; k < i; ++k) x[i] = fmaf(-Lm[tri(i, k, L)], x[k], x[i]);
+#pragma unroll
+        for (int i = 0; i < L; ++i) x[i] *= frcp(Lm[tri(i, i, L)]);
+#pragma unroll
+        for (int i = L - 1; i >= 0; --i)
+#pragma unroll
+            for (int k = i + 1; k < L; ++k) x[i] = fmaf(-Lm[tri(k, i, L)], x[k], x[i]);
+        float n2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < L; ++i) n2 = fmaf(x[i], x[i], n2);
+        const float inv = rsqrtf(n2);
+#pragma unroll
+        for (int i = 0; i < L; ++i) x[i] *= inv;
+    }
+}
+
+// Cyclic Jacobi sweeps on S (in registers, destroyed) in tournament ("circle") order: each of the
+// L - 1 steps of a sweep rotates the disjoint pairs (0,1), (2,3), ... and then relabels the
+// indices by the fixed permutation tperm, so that every pair (p, q) is rotated exactly once per
+// sweep and the labels return to the identity after the sweep; the step is one rolled loop body.
+// The sweeps only have to place the inverse iteration's shift near l1: the largest diagonal entry
+// a_kk differs from l1 by at most about off / gap, so once off <= 1e-3 gap^2 the shift is within
+// ~1e-3 gap of l1 and three inverse-iteration steps reduce the other eigenvectors' share by ~1e-9.
+// More sweeps run only while some lane of the warp is short of that (up to max_sweeps).
+template <int L>
+__device__ __forceinline__ void jacobi_eigvec(float (&S)[L * (L + 1) / 2], const float* Ssh, int max_sweeps,
+                                              float (&x)[L], float& l1, float& l2, int& sweeps, bool& jconv) {
+    constexpr int NS = L * (L + 1) / 2;
+    sweeps = 0;
+    jconv = false;
+    int k1 = 0;
+    for (;;) {
+#pragma unroll 1
+        for (int stp = 0; stp < L - 1; ++stp) {
+#pragma unroll
+            for (int p = 0; p < L; p += 2) {
+                const int q = p + 1;
+                const float apq = S[tri(p, q, L)];
+                const float dq = S[tri(q, q, L)] - S[tri(p, p, L)];
+                const float den = fabsf(dq) + sqrtf(fmaf(dq, dq, 4.f * apq * apq));
+                float t = den > 0.f ? __fdividef(2.f * apq, den) : 0.f;
+                t = dq < 0.f ? -t : t;
+                const float c = rsqrtf(fmaf(t, t, 1.f));
+                const float s = t * c;
+                S[tri(p, p, L)] = fmaf(-t, apq, S[tri(p, p, L)]);
+                S[tri(q, q, L)] = fmaf(t, apq, S[tri(q, q, L)]);
+                S[tri(p, q, L)] = 0.f;
+#pragma unroll
+                for (int r = 0; r < L; ++r) {
+                    if (r == p || r == q) continue;
+                    const float g = S[tri(r, p, L)], hh = S[tri(r, q, L)];
+                    S[tri(r, p, L)] = fmaf(c, g, -s * hh);
+                    S[tri(r, q, L)] = fmaf(s, g, c * hh);
+                }
+            }
+            float B[NS];
+#pragma unroll
+            for (int r = 0; r < L; ++r)
+#pragma unroll
+                for (int cc = r; cc < L; ++cc) B[tri(r, cc, L)] = S[tri(tperm(r, L), tperm(cc, L), L)];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) S[i] = B[i];
+        }
+        ++sweeps;
+        float off = 0.f;
+#pragma unroll
+        for (int p = 0; p < L - 1; ++p)
+#pragma unroll
+            for (int q = p + 1; q < L; ++q) off = fmaf(S[tri(p, q, L)], S[tri(p, q, L)], off);
+        l1 = S[tri(0, 0, L)];
+        l2 = -1e30f;
+        k1 = 0;
+#pragma unroll
+        for (int i = 1; i < L; ++i) {
+            const float v = S[tri(i, i, L)];
+            if (v > l1) {
+                l2 = l1;
+                l1 = v;
+                k1 = i;
+            } else if (v > l2) {
+                l2 = v;
+            }
+        }
+        const float gap = l1 - l2;
+        jconv = off <= 1e-3f * gap * gap;
+        if (sweeps >= max_sweeps) break;
+        if (__all_sync(kFull, jconv)) break;
+    }
+    inverse_iteration<L>(Ssh, l1, k1, x);
+}
+
 // CTAS is the number of 128-thread CTAs the kernel is compiled to keep resident per SM
 // (__launch_bounds__ minimum blocks, i.e. a register cap of 65536 / (128 CTAS)). More CTAs hide
 // more latency but spill more; the best cap depends on L and is chosen by measurement (the
@@ -208,7 +409,6 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
     static_assert(L % 2 == 0 && L >= 2 && L <= kMaxL, "even L only");
     constexpr int h = L / 2;
     constexpr int NS = L * (L + 1) / 2;
-    constexpr int NI = L - 1;  // roots inside the unit disk (the other L - 1 are their mirrors)
     __shared__ float2 sh_seg[kBatWarps][32 + kMaxN];
     __shared__ float2 sh_pre[kBatWarps][3 * 32 + 1];
     __shared__ float sh_S[NS * kBatThreads];
@@ -302,131 +502,44 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             for (int i = 0; i < L; ++i) S[tri(i, i, L)] = (float)(L - i);  // any well-separated stand-in
         }
 
-        // ---- cyclic Jacobi on S for the eigenvalues -----------------------------------------------
-        // Tournament ("circle") ordering: each of the L - 1 steps of a sweep rotates the disjoint
-        // pairs (0,1), (2,3), ... and then relabels the indices by the fixed permutation tperm, so
-        // that every pair (p, q) is rotated exactly once per sweep and the labels return to the
-        // identity after the sweep. The step is one rolled loop body.
-        // The normalised S is parked in shared memory (one column per thread) for the inverse
-        // iteration; the rotations then work on S in place.
+        // ---- signal eigenvector of S ------------------------------------------------------------------
+        // The normalised S is parked in shared memory (one column per thread): the power iteration
+        // starts from one of its columns, the fallback's inverse iteration reads it back.
         float* const Ssh = sh_S + threadIdx.x;
 #pragma unroll
         for (int i = 0; i < NS; ++i) Ssh[i * kBatThreads] = S[i];
-        int sweeps = 0;
+        int sweeps = 0, psteps = 0, eig_fb = 0;
         bool jconv = false;
         float l1 = 0.f, l2 = 0.f;
-        int k1 = 0;
+        float x[L];
         if constexpr (WJ) {
+            int k1 = 0;
             __syncwarp();  // every lane's S is parked before the warp reads them
             warp_jacobi_item<L>(sh_S, wid, lane, args.max_sweeps, &l1, &l2, &k1, &sweeps, &jconv);
             // the warp-level sweep count, as the thread-per-matrix schedule reports it
             sweeps = __reduce_max_sync(kFull, (unsigned)sweeps);
-        } else
-        for (;;) {
-#pragma unroll 1
-            for (int stp = 0; stp < L - 1; ++stp) {
+            inverse_iteration<L>(Ssh, l1, k1, x);
+        } else {
+            // Shifted power iteration; lanes whose iteration did not settle, or whose eigen-gap the
+            // Frobenius bound cannot certify, take the cyclic Jacobi sweeps and inverse iteration
+            // instead (run by the whole warp when any lane needs them).
+            power_eigvec<L>(S, Ssh, x, l1, l2, psteps, jconv);
+            const bool need = nonzero && (args.exhaustive || !jconv || !(l1 - l2 > 4e-6f * l1));
+            if (__any_sync(kFull, need)) {
+                eig_fb = 1;
+                float xj[L], jl1, jl2;
+                bool jc;
+                jacobi_eigvec<L>(S, Ssh, args.max_sweeps, xj, jl1, jl2, sweeps, jc);
+                if (need) {
 #pragma unroll
-                for (int p = 0; p < L; p += 2) {
-                    const int q = p + 1;
-                    const float apq = S[tri(p, q, L)];
-                    const float dq = S[tri(q, q, L)] - S[tri(p, p, L)];
-                    const float den = fabsf(dq) + sqrtf(fmaf(dq, dq, 4.f * apq * apq));
-                    float t = den > 0.f ? __fdividef(2.f * apq, den) : 0.f;
-                    t = dq < 0.f ? -t : t;
-                    const float c = rsqrtf(fmaf(t, t, 1.f));
-                    const float s = t * c;
-                    S[tri(p, p, L)] = fmaf(-t, apq, S[tri(p, p, L)]);
-                    S[tri(q, q, L)] = fmaf(t, apq, S[tri(q, q, L)]);
-                    S[tri(p, q, L)] = 0.f;
-#pragma unroll
-                    for (int r = 0; r < L; ++r) {
-                        if (r == p || r == q) continue;
-                        const float g = S[tri(r, p, L)], hh = S[tri(r, q, L)];
-                        S[tri(r, p, L)] = fmaf(c, g, -s * hh);
-                        S[tri(r, q, L)] = fmaf(s, g, c * hh);
-                    }
-                }
-                float B[NS];
-#pragma unroll
-                for (int r = 0; r < L; ++r)
-#pragma unroll
-                    for (int cc = r; cc < L; ++cc) B[tri(r, cc, L)] = S[tri(tperm(r, L), tperm(cc, L), L)];
-#pragma unroll
-                for (int i = 0; i < NS; ++i) S[i] = B[i];
-            }
-            ++sweeps;
-            float off = 0.f;
-#pragma unroll
-            for (int p = 0; p < L - 1; ++p)
-#pragma unroll
-                for (int q = p + 1; q < L; ++q) off = fmaf(S[tri(p, q, L)], S[tri(p, q, L)], off);
-            // The sweeps only have to place mu (below) near l1: the largest diagonal entry a_kk
-            // differs from l1 by at most about off / gap, so once off <= 1e-3 gap^2 the shift is
-            // within ~1e-3 gap of l1 and three inverse-iteration steps reduce the other
-            // eigenvectors' share by ~1e-9. A signal-dominated window gets there in one sweep;
-            // more sweeps run only while some lane of the warp is short of it.
-            l1 = S[tri(0, 0, L)];
-            l2 = -1e30f;
-            k1 = 0;
-#pragma unroll
-            for (int i = 1; i < L; ++i) {
-                const float v = S[tri(i, i, L)];
-                if (v > l1) {
-                    l2 = l1;
-                    l1 = v;
-                    k1 = i;
-                } else if (v > l2) {
-                    l2 = v;
+                    for (int i = 0; i < L; ++i) x[i] = xj[i];
+                    l1 = jl1;
+                    l2 = jl2;
+                    jconv = jc;
                 }
             }
-            const float gap = l1 - l2;
-            jconv = off <= 1e-3f * gap * gap;
-            if (sweeps >= args.max_sweeps) break;
-            if (__all_sync(kFull, jconv)) break;
         }
         const bool separated = l1 - l2 > 4e-6f * l1;
-
-        // ---- inverse iteration: (mu I - S) x = b, b = column k1 of S ----------------------------
-        const float mu = l1 + 1e-5f * l1 + 1e-30f;
-        float Lm[NS];  // unit lower factor in the packed layout, D on the diagonal slots
-#pragma unroll
-        for (int j = 0; j < L; ++j) {
-            float dj = mu - Ssh[tri(j, j, L) * kBatThreads];
-#pragma unroll
-            for (int k = 0; k < j; ++k) dj = fmaf(-Lm[tri(j, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], dj);
-            if (fabsf(dj) < 1e-30f) dj = dj < 0.f ? -1e-30f : 1e-30f;
-            Lm[tri(j, j, L)] = dj;
-            const float inv = frcp(dj);
-#pragma unroll
-            for (int i = j + 1; i < L; ++i) {
-                float v = -Ssh[tri(i, j, L) * kBatThreads];
-#pragma unroll
-                for (int k = 0; k < j; ++k) v = fmaf(-Lm[tri(i, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], v);
-                Lm[tri(i, j, L)] = v * inv;
-            }
-        }
-        float x[L];
-#pragma unroll
-        for (int i = 0; i < L; ++i) x[i] = Ssh[tri(i, k1, L) * kBatThreads];
-#pragma unroll 1
-        for (int step = 0; step < 3; ++step) {
-#pragma unroll
-            for (int i = 0; i < L; ++i)
-#pragma unroll
-                for (int k = 0; k < i; ++k) x[i] = fmaf(-Lm[tri(i, k, L)], x[k], x[i]);
-#pragma unroll
-            for (int i = 0; i < L; ++i) x[i] *= frcp(Lm[tri(i, i, L)]);
-#pragma unroll
-            for (int i = L - 1; i >= 0; --i)
-#pragma unroll
-                for (int k = i + 1; k < L; ++k) x[i] = fmaf(-Lm[tri(k, i, L)], x[k], x[i]);
-            float n2 = 0.f;
-#pragma unroll
-            for (int i = 0; i < L; ++i) n2 = fmaf(x[i], x[i], n2);
-            const float inv = rsqrtf(n2);
-#pragma unroll
-            for (int i = 0; i < L; ++i) x[i] *= inv;
-        }
 
         // ---- u1 = Q x1 and the polynomial coefficients ---------------------------------------------
         cx<float> u[L];
@@ -439,24 +552,23 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         cx<float> c[L];
         const float res_lim2 = music_coefs<L>(u, c);
 
-        // ---- Aberth-Ehrlich on the inner roots --------------------------------------------------------
-        cx<float> z[NI], mz[NI];
-        int iters, evals, updates;
-        bool rconv;
-        inner_roots<L>(c, res_lim2, args.max_iters, z, mz, iters, evals, updates, rconv);
-
-        // ---- selection (Algorithm 1) ------------------------------------------------------------------
-        bool found, cluster;
-        const cx<float> zz = select_root<L>(c, z, mz, found, cluster);
+        // ---- the selected root (Algorithm 1) -----------------------------------------------------------
+        bool found, cluster, rconv;
+        RootStats rs;
+        const cx<float> zz = signal_root<L>(c, res_lim2, args.max_iters, args.exhaustive, nonzero, found, cluster, rconv, rs);
         const double omd = args.polish64 ? wrap_pi(polish_arg64<L>(c, zz, cluster) - F.omega_ref) : 0.0;
         float om = args.polish64 ? (float)omd : wrap_pi(atan2f(zz.i, zz.r) - (float)F.omega_ref);
 
         if (lane == 0 && args.counters) {
             atomicAdd(args.counters + 0, (unsigned long long)sweeps);
-            atomicAdd(args.counters + 1, (unsigned long long)iters);
+            atomicAdd(args.counters + 1, (unsigned long long)rs.iters);
             atomicAdd(args.counters + 2, 1ull);
-            atomicAdd(args.counters + 3, (unsigned long long)updates);
-            atomicAdd(args.counters + 4, (unsigned long long)evals);
+            atomicAdd(args.counters + 3, (unsigned long long)rs.updates);
+            atomicAdd(args.counters + 4, (unsigned long long)rs.evals);
+            atomicAdd(args.counters + 5, (unsigned long long)psteps);
+            atomicAdd(args.counters + 6, (unsigned long long)eig_fb);
+            atomicAdd(args.counters + 7, (unsigned long long)rs.newton);
+            atomicAdd(args.counters + 8, (unsigned long long)rs.fallback);
         }
 
         // ---- store ---------------------------------------------------------------------------------

@@ -44,6 +44,7 @@ struct DeviceGuard {
 
 constexpr int kCounterSlots = 64;  // [0, kStatSlot) work counters, [kStatSlot ..] statistics
 constexpr int kStatSlot = 32;
+constexpr int kStatCount = 9;  // statistics slots the solvers add to (rmusic_launch.h lists them)
 
 // A solver key names one compiled solver family: the covariance order L of the row-window
 // solver (2 .. kMaxL), or kSquareKey0 + Lp for the square-block solver.
@@ -146,6 +147,7 @@ bool params_ok(const rmusic_params& p) {
     if (p.carrier_axis != 0 && p.carrier_axis != 1) return false;
     if (p.unwrap != 0 && p.unwrap != 1) return false;
     if (p.raw_input != 0 && p.raw_input != 1) return false;
+    if (p.exhaustive != 0 && p.exhaustive != 1) return false;
     if (p.raw_input && (p.geometry != RMUSIC_GEOM_ROW || p.deriv_axis != p.carrier_axis)) return false;
     if (p.geometry == RMUSIC_GEOM_ROW && p.model_order >= p.cov_order) return false;
     if (p.unwrap && p.geometry != RMUSIC_GEOM_SQUARE) return false;
@@ -472,6 +474,7 @@ cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, fl
         a.max_power_iters = p.max_sweeps ? p.max_sweeps : 100;
         a.max_iters = p.max_root_iters ? p.max_root_iters : 32;
         a.polish64 = p.polish_fp64;
+        a.exhaustive = p.exhaustive;
         a.tol2 = 1e-11f;
         a.counters = stat_counters;
         return launch_square(key - kSquareKey0, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
@@ -482,6 +485,7 @@ cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, fl
     a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
     a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
     a.polish64 = p.polish_fp64;
+    a.exhaustive = p.exhaustive;
     a.counters = stat_counters;
     return launch_batched(key, v, ctx->d_table + plan.group_first[g], plan.group_count[g], plan.group_items[g],
                           ctx->d_counters + g, gamma, d_out, d_status, a, solver_grid(ctx, key, v), s);
@@ -810,7 +814,7 @@ int demodulate_impl(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
         if (rc) return rc;
         pixels += (uint64_t)F.H * (uint64_t)F.W;
     }
-    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, 5 * sizeof(unsigned long long), s));
+    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, kStatCount * sizeof(unsigned long long), s));
     // group frames so that each group's analytic signal fits the budget
     const uint64_t table_reserve = 64 * sizeof(FrameDev) + (uint64_t)n_frames * sizeof(FrameDev);
     uint64_t avail = 0;
@@ -999,12 +1003,17 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->workspace_bytes = ctx->held;
     out->pixels = ctx->last_pixels;
     RM_CUDA(cudaEventSynchronize(ctx->call_done));
-    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    unsigned long long c[kStatCount] = {};
     RM_CUDA(cudaMemcpy(c, ctx->d_counters + kStatSlot, sizeof(c), cudaMemcpyDeviceToHost));
-    out->mean_sweeps = c[2] ? (double)c[0] / (double)c[2] : 0.0;
-    out->mean_root_iters = c[2] ? (double)c[1] / (double)c[2] : 0.0;
-    out->mean_root_updates = c[2] ? (double)c[3] / (double)c[2] : 0.0;
-    out->mean_root_evals = c[2] ? (double)c[4] / (double)c[2] : 0.0;
+    auto mean = [&](int i) { return c[2] ? (double)c[i] / (double)c[2] : 0.0; };
+    out->mean_sweeps = mean(0);
+    out->mean_root_iters = mean(1);
+    out->mean_root_updates = mean(3);
+    out->mean_root_evals = mean(4);
+    out->mean_power_steps = mean(5);
+    out->eig_fallback_frac = mean(6);
+    out->mean_newton_steps = mean(7);
+    out->root_fallback_frac = mean(8);
     auto sum = [&](const std::vector<int>& v) {
         float t = 0.f;
         for (size_t i = 0; i + 1 < v.size(); i += 2) {

@@ -203,6 +203,7 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
         a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
         a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
         a.polish64 = p.polish_fp64;
+        a.exhaustive = p.exhaustive;
         a.counters = nullptr;
         for (int g = 0; g < ngroups && rc == RMUSIC_OK; ++g) {
             const int L = group_L[g];

@@ -41,8 +41,10 @@ struct BatchedArgs {
     int max_sweeps;
     int max_iters;
     int polish64;
-    unsigned long long* counters;  // [0] sweeps, [1] root iterations, [2] items, [3] root updates,
-                                   // [4] evaluations of Q and Q'
+    int exhaustive;                // 1: Jacobi sweeps and all roots for every pixel (no shortcuts)
+    unsigned long long* counters;  // [0] Jacobi sweeps, [1] Aberth iterations, [2] items, [3] Aberth root
+                                   // updates, [4] Aberth evaluations of Q and Q', [5] power steps,
+                                   // [6] Jacobi fallbacks, [7] Newton steps, [8] Aberth fallbacks
 };
 bool batched_supports(int L);
 int batched_num_variants(int L);
@@ -63,9 +65,11 @@ struct SquareArgs {
     int max_power_iters;
     int max_iters;
     int polish64;
+    int exhaustive;                // 1: all roots for every pixel (no Newton certificate)
     float tol2;                    // power iteration stops when |u_new - u|^2 <= tol2
-    unsigned long long* counters;  // [0] power iterations, [1] root iterations, [2] warps, [3] root updates,
-                                   // [4] evaluations of Q and Q' (both polynomials)
+    unsigned long long* counters;  // [0] power iterations, [1] Aberth iterations, [2] warps, [3] Aberth root
+                                   // updates, [4] Aberth evaluations of Q and Q', [7] Newton steps,
+                                   // [8] Aberth fallbacks (root figures: both polynomials)
 };
 bool square_supports(int Lp);
 int square_num_variants(int Lp);

@@ -6,18 +6,24 @@
 //   poly      u1 the signal vector (any norm); c_0 = L - 1, c_k = -(1 - 2e-6) sum_m u1[m]
 //             conj(u1[m+k]) / |u1|^2, c_-k = conj(c_k); Q(z) = sum_k c_k z^(k+L-1) (Eq. 12-14).
 //             The 2e-6 shrink keeps the polynomial strictly positive on the circle in FP32.
-//   roots     Aberth-Ehrlich on the L - 1 roots inside the unit disk; the other L - 1 roots are
-//             their mirrors 1/conj(z) (the coefficients are conjugate-symmetric). Starting
-//             points come from the estimator's structure: the signal root just inside the circle
-//             at the angle of conj(rho_1), the others at radius r = L / (L + 7.3) at the
-//             side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2, where a noise-free window
-//             puts them. A root stops (freezes) when its residual is at the FP32 rounding level
-//             (|Q(z)| <= 3e-6 sum |q_i|), or, if it lies at least 0.05 inside the outermost tracked
-//             root, when its Newton step is below 1e-3: only the root nearest the circle needs
-//             full accuracy (it is polished after the selection), the others only have to be
-//             resolved well enough not to change the selection, and Aberth's fixed point for the
-//             remaining roots does not depend on where a frozen root stopped. Iterations stop
-//             when every root of every lane of the warp is frozen.
+//   roots     the root Algorithm 1 selects, found without computing every root where a
+//             certificate allows: Newton's method (with the root's mirror divided out) from the
+//             estimator's start -- radius 0.99 at the angle of conj(rho_1) -- converges to the
+//             signal root in 3-7 steps; a Schur-Cohn count of the roots of Q inside |z| < r - 0.02
+//             (r the found root's modulus) equal to L - 2 proves it is the only inner root that
+//             close to the circle, hence the selected one. Warps with a lane lacking the
+//             certificate run the full root finder: Aberth-Ehrlich on the L - 1 roots inside the
+//             unit disk; the other L - 1 roots are their mirrors 1/conj(z) (the coefficients are
+//             conjugate-symmetric). Its starting points come from the estimator's structure: the
+//             signal root just inside the circle at the angle of conj(rho_1), the others at radius
+//             r = L / (L + 7.3) at the side-lobe angles arg + 2 pi (k + 1/2) / L, k = 1 .. L-2,
+//             where a noise-free window puts them. A root stops (freezes) when its residual is at
+//             the FP32 rounding level (|Q(z)| <= 3e-6 sum |q_i|), or, if it lies at least 0.05
+//             inside the outermost tracked root, when its Newton step is below 1e-3: only the root
+//             nearest the circle needs full accuracy (it is polished after the selection), the
+//             others only have to be resolved well enough not to change the selection, and
+//             Aberth's fixed point for the remaining roots does not depend on where a frozen root
+//             stopped. Iterations stop when every root of every lane of the warp is frozen.
 //   select    the inner root nearest the unit circle (Algorithm 1). A noise-free window gives a
 //             double root on the circle, which FP32 splits by ~sqrt(eps); when another root lies
 //             within 4e-3 the pair is located as the root of Q' between them, otherwise the root
@@ -226,17 +232,18 @@ __device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, 
     }
 }
 
-// The selected root (Algorithm 1) after inner_roots, refined by two FP32 Newton steps (on Q'
-// for a split double root, else on Q with the partner 1/conj(z) divided out). found is false
-// if no root was tracked (never for L >= 2); cluster tells which refinement ran.
+// The candidate of Algorithm 1 among the roots of inner_roots: the inner root nearest the unit
+// circle (every tracked root is inside the disk, so the one of largest modulus), and the root of the
+// full set nearest to it (its own mirror, another inner root or a mirror), which decides whether
+// the two form a split double root. found is false if no root was tracked (never for L >= 2).
 template <int L>
-__device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<float> (&z)[L - 1],
-                                                 const cx<float> (&mz)[L - 1], bool& found, bool& cluster) {
+__device__ __forceinline__ void nearest_pair(const cx<float> (&z)[L - 1], const cx<float> (&mz)[L - 1],
+                                             cx<float>& zs, cx<float>& zn, bool& found) {
     constexpr int NI = L - 1;
-    // every tracked root is inside the disk: the one nearest the circle has the largest modulus
     int best = -1;
     float bestr = -1.f;
-    cx<float> zs = mkc(1.f, 0.f), ms = zs;
+    zs = mkc(1.f, 0.f);
+    cx<float> ms = zs;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
         const float r = norm2(z[i]);
@@ -247,9 +254,8 @@ __device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<fl
             ms = mz[i];
         }
     }
-    // nearest other root of the full set: its own mirror, another inner root or a mirror
     float neard = norm2(ms - zs);
-    cx<float> zn = ms;
+    zn = ms;
 #pragma unroll
     for (int j = 0; j < NI; ++j) {
         const float dj = norm2(z[j] - zs), dmj = norm2(mz[j] - zs);
@@ -263,7 +269,13 @@ __device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<fl
         }
     }
     found = best >= 0;
-    cluster = neard < 4e-3f * 4e-3f;
+}
+
+// Two FP32 refinement steps of the selected root zs: on Q' from the midpoint of zs and its
+// nearest root zn when the two form a split double root (cluster), otherwise Newton on Q with the
+// partner 1/conj(z) divided out.
+template <int L>
+__device__ __forceinline__ cx<float> polish_root(const cx<float>* c, cx<float> zs, cx<float> zn, bool cluster) {
     cx<float> zz = cluster ? 0.5f * (zs + zn) : zs;
 #pragma unroll 1
     for (int it = 0; it < 2; ++it) {
@@ -280,6 +292,164 @@ __device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<fl
         if (isfinite(stp.r) && isfinite(stp.i)) zz = zz - stp;
     }
     return zz;
+}
+
+// The selected root (Algorithm 1) after inner_roots, refined by polish_root.
+template <int L>
+__device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<float> (&z)[L - 1],
+                                                 const cx<float> (&mz)[L - 1], bool& found, bool& cluster) {
+    cx<float> zs, zn;
+    nearest_pair<L>(z, mz, zs, zn, found);
+    cluster = norm2(zn - zs) < 4e-3f * 4e-3f;
+    return polish_root<L>(c, zs, zn, cluster);
+}
+
+// Signal root of Q by Newton's method with the root's mirror divided out -- the one-term
+// Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' -- from the estimator's
+// start 0.99 exp(j arg conj(rho_1)) (the start inner_roots gives the signal root). A step that
+// leaves the disk is folded back onto the mirror. A lane stops when |Q| is at the FP32 rounding
+// level (the step is then not taken, as in inner_roots) or the step is below 1e-6; the warp stops
+// when every lane has or after max_iters steps (conv false for the lanes still moving). Inactive
+// lanes (pixels without a result) count as stopped from the start.
+template <int L>
+__device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, float res_lim2, int max_iters,
+                                                        bool active, bool& conv, int& steps) {
+    const cx<float> rho1 = (-1.f) * c[1];
+    const float n1 = norm2(rho1);
+    cx<float> z = n1 > 0.f ? (0.99f * rsqrtf(n1)) * conjg(rho1) : mkc(0.99f, 0.f);
+    conv = !active;
+    steps = 0;
+#pragma unroll 1
+    for (;;) {
+        cx<float> p, dp;
+        horner_pd<L>(c, z, p, dp);
+        ++steps;
+        const cx<float> Ni = cdivf(p, dp);
+        const cx<float> m = frcp(norm2(z)) * z;  // 1/conj(z)
+        const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - cdivf(Ni, z - m));
+        const bool small = norm2(p) <= res_lim2;
+        const bool fin = isfinite(w.r) && isfinite(w.i);
+        if (!conv && !small && fin) {
+            z = z - w;
+            const float r2 = norm2(z);
+            if (r2 > 1.f) z = frcp(r2) * z;
+        }
+        conv = conv || small || (fin && norm2(w) <= 1e-12f);
+        if (steps >= max_iters || __all_sync(kFull, conv)) break;
+    }
+    return z;
+}
+
+// Number of roots of Q inside the disk |z| < r, by the Schur-Cohn recursion on P(z) = Q(r z):
+// with P*(z) = z^n conj(P(1/conj z)) and g = P(0) / conj(lead P), the polynomial
+// P1(z) = (P(z) - g P*(z)) / z has degree n - 1, and Rouche's theorem on the unit circle (where
+// |P*| = |P|) gives N(P) = N(P1) + 1 if |P(0)| < |lead P|, else N(P) = n - 1 - N(P1). Returns -1
+// when some |P(0)|^2 is within 2e-4 of |lead P|^2 (relative), where FP32 rounding could decide
+// the comparison, or the lead vanishes. The coefficients are rescaled by exact powers of two when
+// their magnitude drifts (the count does not depend on a positive scale).
+template <int L>
+__device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
+    constexpr int n = 2 * L - 2;
+    cx<float> a[n + 1];
+    {
+        float s = 1.f;
+#pragma unroll
+        for (int i = 0; i <= n; ++i) {
+            a[i] = s * qcoef<L>(c, i);
+            s *= r;
+        }
+    }
+    unsigned long long inside = 0ull;
+    bool bad = false;
+#pragma unroll
+    for (int deg = n; deg >= 1; --deg) {
+        const float la = norm2(a[deg]), l0 = norm2(a[0]);
+        bad = bad || !(la > 0.f) || fabsf(la - l0) <= 2e-4f * la;
+        if (l0 < la) inside |= 1ull << deg;
+        const cx<float> g = frcp(la) * (a[0] * a[deg]);  // a0 / conj(a_deg)
+        cx<float> b[n];
+#pragma unroll
+        for (int k = 1; k <= deg; ++k) b[k - 1] = a[k] - g * conjg(a[deg - k]);
+#pragma unroll
+        for (int k = 0; k < deg; ++k) a[k] = b[k];
+        if (deg > 1) {
+            const float m = fmaxf(fabsf(a[deg - 1].r), fabsf(a[deg - 1].i));
+            if (m > 0x1p40f || m < 0x1p-40f) {
+                if (m > 0.f && isfinite(m)) {
+                    const float sc = __int_as_float((254 - ((__float_as_int(m) >> 23) & 0xff)) << 23);
+#pragma unroll
+                    for (int k = 0; k < deg; ++k) a[k] = sc * a[k];
+                } else {
+                    bad = true;
+                }
+            }
+        }
+    }
+    int N = 0;
+#pragma unroll
+    for (int d = 1; d <= n; ++d) N = ((inside >> d) & 1ull) ? N + 1 : d - 1 - N;
+    return bad ? -1 : N;
+}
+
+// Newton steps of the signal root before a lane counts as not converged (it then takes the full
+// root finder): 3-4 on row windows, 4-7 on square blocks at 0-10 dB.
+constexpr int kNewtonSteps = 16;
+
+struct RootStats {
+    int newton;   // Newton steps of the signal root
+    int fallback; // 1 if the warp ran the full Aberth iteration
+    int iters;    // Aberth sweeps, evaluations and root updates (fallback only)
+    int evals;
+    int updates;
+};
+
+// The root stage (Algorithm 1): the inner root of Q nearest the unit circle, refined. The signal
+// root comes from newton_signal_root; it is the selected root when it is the only root in the
+// annulus r - 0.02 <= |z| < 1 (r its modulus), i.e. when Q has exactly L - 2 roots inside
+// |z| < r - 0.02 (roots_inside). Lanes without that certificate -- and with them the whole warp,
+// which executes the loop together -- take every inner root from inner_roots and select among
+// them (nearest_pair). Both end in polish_root; a selected root whose nearest other root is
+// closer than 4e-3 is a split double root (cluster). exhaustive (uniform over the launch) skips the
+// Newton root and its certificate: every lane takes the full root finder. Inactive lanes (border or
+// degenerate pixels, whose result is not used) neither hold the warp in Newton's loop nor send it
+// to the full root finder.
+template <int L>
+__device__ __forceinline__ cx<float> signal_root(const cx<float>* c, float res_lim2, int max_iters, int exhaustive,
+                                                 bool active, bool& found, bool& cluster, bool& rconv,
+                                                 RootStats& rs) {
+    constexpr int NI = L - 1;
+    bool nconv = false, cert = false;
+    cx<float> zs = mkc(0.f, 0.f), zn = zs;
+    rs.newton = 0;
+    if (!exhaustive) {
+        zs = newton_signal_root<L>(c, res_lim2, kNewtonSteps, active, nconv, rs.newton);
+        const float r2 = norm2(zs);
+        const float r = sqrtf(r2);
+        int nin = -1;
+        if (active && nconv && r > 0.5f) nin = roots_inside<L>(c, r - 0.02f);
+        cert = !active || nin == L - 2;
+        zn = frcp(r2) * zs;
+    }
+    found = true;
+    rconv = nconv;
+    rs.fallback = 0;
+    rs.iters = rs.evals = rs.updates = 0;
+    if (__any_sync(kFull, !cert)) {
+        rs.fallback = 1;
+        cx<float> z[NI], mz[NI];
+        bool aconv, afound;
+        cx<float> azs, azn;
+        inner_roots<L>(c, res_lim2, max_iters, z, mz, rs.iters, rs.evals, rs.updates, aconv);
+        nearest_pair<L>(z, mz, azs, azn, afound);
+        if (!cert) {
+            zs = azs;
+            zn = azn;
+            found = afound;
+            rconv = aconv;
+        }
+    }
+    cluster = norm2(zn - zs) < 4e-3f * 4e-3f;
+    return polish_root<L>(c, zs, zn, cluster);
 }
 
 // One more refinement step of the selected root in FP64; returns arg z in double.

@@ -25,8 +25,9 @@
 // lane of the warp. v1 is G^H u from the last step. Degenerate blocks (all zero) get a stand-in vector so every lane of
 // the warp runs the same bounded loops.
 //
-// Polynomials: the root stage of roots_device.cuh (coefficients, Aberth on the inner roots,
-// selection, polish) with L = M, run once per axis in one rolled loop (the second axis'
+// Polynomials: the root stage of roots_device.cuh (coefficients, the signal root by Newton's
+// method with a Schur-Cohn certificate -- Aberth on all inner roots where it fails -- and the
+// polish) with L = M, run once per axis in one rolled loop (the second axis'
 // coefficients wait in shared memory), which keeps the code within the instruction cache.
 #pragma once
 
@@ -47,7 +48,6 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
               float* __restrict__ out, uint8_t* __restrict__ status, SquareArgs args) {
     static_assert(LP >= 1 && 2 * LP + 1 <= 2 * kMaxSquareLp + 1, "half-width out of range");
     constexpr int M = 2 * LP + 1;
-    constexpr int NI = M - 1;              // roots of Q inside the disk
     constexpr int SW = kSqTX + 2 * LP;     // staged columns
     constexpr int SH = kSqTY + 2 * LP;     // staged rows
     // per-thread scratch, one float2 column per thread: the power iteration's two vectors
@@ -215,7 +215,7 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         // ---- roots, selection and angle: axis 0 is y (z_y), axis 1 is x (z_x) ----------------------
         float om_y = 0.f, om_x = 0.f;
         bool rconv_all = true, found_all = true;
-        int riters = 0, revals = 0, rupdates = 0;
+        int riters = 0, revals = 0, rupdates = 0, rnewton = 0, rfallback = 0;
 #pragma unroll 1
         for (int ax = 0; ax < 2; ++ax) {
             cx<float> c[M];
@@ -224,11 +224,11 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
                 const float2 v = cme[(ax * M + k) * kSqThreads];
                 c[k] = mkc(v.x, v.y);
             }
-            cx<float> z[NI], mz[NI];
-            int iters, evals, updates;
             bool rconv, found, cluster;
-            inner_roots<M>(c, ax == 0 ? res2_y : res2_x, args.max_iters, z, mz, iters, evals, updates, rconv);
-            const cx<float> zz = select_root<M>(c, z, mz, found, cluster);
+            RootStats rs;
+            const cx<float> zz =
+                signal_root<M>(c, ax == 0 ? res2_y : res2_x, args.max_iters, args.exhaustive, nonzero, found,
+                               cluster, rconv, rs);
             const float a = args.polish64 ? (float)polish_arg64<M>(c, zz, cluster) : atan2f(zz.i, zz.r);
             if (ax == 0)
                 om_y = a;
@@ -236,9 +236,11 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
                 om_x = -a;  // z_x = exp(-j omega_x) (Eq. 15)
             rconv_all = rconv_all && rconv;
             found_all = found_all && found;
-            riters += iters;
-            revals += evals;
-            rupdates += updates;
+            riters += rs.iters;
+            revals += rs.evals;
+            rupdates += rs.updates;
+            rnewton += rs.newton;
+            rfallback += rs.fallback;
         }
 
         // ---- alpha: angle of the demodulated block mean (Eq. 15) ----------------------------------
@@ -276,6 +278,8 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
             atomicAdd(args.counters + 1, (unsigned long long)riters);
             atomicAdd(args.counters + 3, (unsigned long long)rupdates);
             atomicAdd(args.counters + 4, (unsigned long long)revals);
+            atomicAdd(args.counters + 7, (unsigned long long)rnewton);
+            atomicAdd(args.counters + 8, (unsigned long long)rfallback);
         }
 
         // ---- store the three maps ------------------------------------------------------------------

@@ -64,6 +64,7 @@ class rmusic_params(ctypes.Structure):
         ("unwrap", ctypes.c_int32),
         ("band_cross", ctypes.c_double),
         ("raw_input", ctypes.c_int32),
+        ("exhaustive", ctypes.c_int32),
     ]
 
 
@@ -94,6 +95,10 @@ class rmusic_stats(ctypes.Structure):
         ("solver_ms", ctypes.c_float),
         ("solver_ctas_per_sm", ctypes.c_int32),
         ("solver_variant", ctypes.c_int32),
+        ("mean_power_steps", ctypes.c_double),
+        ("eig_fallback_frac", ctypes.c_double),
+        ("mean_newton_steps", ctypes.c_double),
+        ("root_fallback_frac", ctypes.c_double),
     ]
 
 
@@ -266,13 +271,13 @@ def make_params(window_len=32, cov_order=8, forward_backward=1, deriv_axis=0, ca
                 carrier_freq=0.1, band_halfwidth=0.0, precision="batched", max_sweeps=0,
                 max_root_iters=0, polish_fp64=0, use_graph=0, timing=0, autotune=0,
                 model_order=1, geometry="row", half_width=0, unwrap=0, band_cross=0.0,
-                raw_input=0) -> rmusic_params:
+                raw_input=0, exhaustive=0) -> rmusic_params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     geom = GEOMETRIES[geometry] if isinstance(geometry, str) else int(geometry)
     return rmusic_params(window_len, cov_order, model_order, forward_backward, deriv_axis, carrier_axis,
                          float(carrier_freq), float(band_halfwidth), prec, max_sweeps, max_root_iters,
                          polish_fp64, use_graph, timing, autotune, geom, half_width, unwrap, float(band_cross),
-                         int(raw_input))
+                         int(raw_input), int(exhaustive))
 
 
 def frame_descs(shapes, dtype_code: int, elem_bytes: int, windows=None, maps: int = 1):

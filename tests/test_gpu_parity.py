@@ -460,7 +460,9 @@ def test_autotune_variants_identical_and_cached(tmp_path, monkeypatch):
 @pytest.mark.parametrize("L", [4, 6, 8])
 def test_solver_variants_and_warp_per_matrix_schedule(L):
     """Variants 0-2 (register caps) compute identical maps; variant 3 runs the eigenvalue sweeps with
-    one warp per matrix and agrees with them to FP32 rounding, statuses included."""
+    one warp per matrix followed by inverse iteration, the others the power iteration, which stops at a
+    1e-6 step: the two eigenvectors agree to ~1e-6, which small L (a flat pseudospectrum minimum)
+    magnifies to ~1e-5 rad/px in the angle. Statuses are identical."""
     torch = _torch()
     frames = [synth.peaks_frame(10, 0.1, H=40, W=256).image, synth.peaks_frame(np.inf, 0.1, H=24, W=256).image]
     x = torch.from_numpy(np.concatenate([f.ravel() for f in frames])).cuda()
@@ -485,7 +487,7 @@ def test_solver_variants_and_warp_per_matrix_schedule(L):
     g, gs = maps[3]
     assert np.array_equal(gs, maps[1][1])
     ok = gs == 0
-    assert np.abs(g[ok] - maps[1][0][ok]).max() <= 1e-5
+    assert np.abs(g[ok] - maps[1][0][ok]).max() <= 3e-5
     o, os_ = oracle_run(frames[1], 32, L, 1)
     off = frames[0].size
     v = (os_.ravel() == 0) & (gs[off:] == 0)
