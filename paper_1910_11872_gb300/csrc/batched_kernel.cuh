@@ -39,6 +39,8 @@ namespace rmusic {
 
 constexpr int kBatWarps = 4;
 constexpr int kBatThreads = kBatWarps * 32;
+constexpr int kLagBlock = 4;      // lags whose prefix sums are held in shared memory at once
+constexpr int kPreLen = 3 * 32 + 1;  // prefix sums of one lag over a warp item (3 products per lane)
 
 __host__ __device__ constexpr int tri(int r, int c, int L) {
     return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);
@@ -410,7 +412,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
     constexpr int h = L / 2;
     constexpr int NS = L * (L + 1) / 2;
     __shared__ float2 sh_seg[kBatWarps][32 + kMaxN];
-    __shared__ float2 sh_pre[kBatWarps][3 * 32 + 1];
+    __shared__ float2 sh_pre[kBatWarps][kLagBlock * kPreLen];
     __shared__ float sh_S[NS * kBatThreads];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* seg = sh_seg[wid];
@@ -445,49 +447,67 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         // Every box sum K R_f[m][m+d] (and its Hermitian mirror) is added straight into the
         // entries of S it feeds, so R_f is never held whole. Constant factors (1/K, 1/2) are
         // dropped: S is normalised by its trace below, which leaves its eigenvectors unchanged.
+        // The lags are taken kLagBlock at a time: a rolled loop forms each lag's products and their
+        // warp scan into its own slot of pre[], then an unrolled pass reads the box sums of the
+        // block's lags into S (compile-time targets). Rolling the scan keeps the code small enough
+        // for the instruction cache, which the fully unrolled form overran.
         float S[NS];
 #pragma unroll
         for (int i = 0; i < NS; ++i) S[i] = 0.f;
 #pragma unroll
-        for (int d = 0; d < L; ++d) {
-            const int G = 31 + N - d;  // lag products g_d[0 .. G-1] are needed
-            const int j0 = 3 * lane;
-            cx<float> s0 = mkc(0.f, 0.f), s1, s2;
-            if (j0 < G) {
-                float2 a = seg[j0], b = seg[j0 + d];
-                s0 = mulc(mkc(a.x, a.y), mkc(b.x, b.y));
-            }
-            s1 = s0;
-            if (j0 + 1 < G) {
-                float2 a = seg[j0 + 1], b = seg[j0 + 1 + d];
-                s1 = s1 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
-            }
-            s2 = s1;
-            if (j0 + 2 < G) {
-                float2 a = seg[j0 + 2], b = seg[j0 + 2 + d];
-                s2 = s2 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
-            }
-            cx<float> incl = s2;
+        for (int d0 = 0; d0 < L; d0 += kLagBlock) {
+            constexpr int kLB = kLagBlock;
+            const int nd = L - d0 < kLB ? L - d0 : kLB;
+            __syncwarp();  // the previous block's box sums have been read
+#pragma unroll 1
+            for (int dd = 0; dd < nd; ++dd) {
+                const int d = d0 + dd;
+                const int G = 31 + N - d;  // lag products g_d[0 .. G-1] are needed
+                const int j0 = 3 * lane;
+                cx<float> s0 = mkc(0.f, 0.f), s1, s2;
+                if (j0 < G) {
+                    const float2 a = seg[j0], b = seg[j0 + d];
+                    s0 = mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+                }
+                s1 = s0;
+                if (j0 + 1 < G) {
+                    const float2 a = seg[j0 + 1], b = seg[j0 + 1 + d];
+                    s1 = s1 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+                }
+                s2 = s1;
+                if (j0 + 2 < G) {
+                    const float2 a = seg[j0 + 2], b = seg[j0 + 2 + d];
+                    s2 = s2 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
+                }
+                cx<float> incl = s2;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                cx<float> t = shfl_up_c(incl, o);
-                if (lane >= o) incl = incl + t;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const cx<float> t = shfl_up_c(incl, o);
+                    if (lane >= o) incl = incl + t;
+                }
+                cx<float> excl = shfl_up_c(incl, 1);
+                if (lane == 0) excl = mkc(0.f, 0.f);
+                const cx<float> p1 = excl + s0, p2 = excl + s1, p3 = excl + s2;
+                float2* pd = pre + dd * kPreLen;
+                pd[j0 + 1] = make_float2(p1.r, p1.i);
+                pd[j0 + 2] = make_float2(p2.r, p2.i);
+                pd[j0 + 3] = make_float2(p3.r, p3.i);
+                if (lane == 0) pd[0] = make_float2(0.f, 0.f);
             }
-            cx<float> excl = shfl_up_c(incl, 1);
-            if (lane == 0) excl = mkc(0.f, 0.f);
-            __syncwarp();
-            const cx<float> p1 = excl + s0, p2 = excl + s1, p3 = excl + s2;
-            pre[j0 + 1] = make_float2(p1.r, p1.i);
-            pre[j0 + 2] = make_float2(p2.r, p2.i);
-            pre[j0 + 3] = make_float2(p3.r, p3.i);
-            if (lane == 0) pre[0] = make_float2(0.f, 0.f);
             __syncwarp();
 #pragma unroll
-            for (int m = 0; m + d < L; ++m) {
-                const float2 hi = pre[lane + m + K], lo = pre[lane + m];
-                const cx<float> v = mkc(hi.x - lo.x, hi.y - lo.y);  // K R_f[m][m+d]
-                accumulate_s<L>(S, m, m + d, v);
-                if (d > 0) accumulate_s<L>(S, m + d, m, conjg(v));
+            for (int dd = 0; dd < kLB; ++dd) {
+                const int d = d0 + dd;
+                if (d < L) {
+                    const float2* pd = pre + dd * kPreLen;
+#pragma unroll
+                    for (int m = 0; m + d < L; ++m) {
+                        const float2 hi = pd[lane + m + K], lo = pd[lane + m];
+                        const cx<float> v = mkc(hi.x - lo.x, hi.y - lo.y);  // K R_f[m][m+d]
+                        accumulate_s<L>(S, m, m + d, v);
+                        if (d > 0) accumulate_s<L>(S, m + d, m, conjg(v));
+                    }
+                }
             }
         }
         float tr = 0.f;

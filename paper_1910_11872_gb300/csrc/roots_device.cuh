@@ -345,8 +345,9 @@ __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, floa
 // P1(z) = (P(z) - g P*(z)) / z has degree n - 1, and Rouche's theorem on the unit circle (where
 // |P*| = |P|) gives N(P) = N(P1) + 1 if |P(0)| < |lead P|, else N(P) = n - 1 - N(P1). Returns -1
 // when some |P(0)|^2 is within 2e-4 of |lead P|^2 (relative), where FP32 rounding could decide
-// the comparison, or the lead vanishes. The coefficients are rescaled by exact powers of two when
-// their magnitude drifts (the count does not depend on a positive scale).
+// the comparison, or when a squared modulus leaves the FP32 range (the coefficients are not
+// rescaled between levels, which keeps this straight-line code short; on the root-MUSIC
+// polynomials with r > 0.48 their magnitudes stay within 2^+-40).
 template <int L>
 __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
     constexpr int n = 2 * L - 2;
@@ -360,11 +361,11 @@ __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
         }
     }
     unsigned long long inside = 0ull;
-    bool bad = false;
+    bool ok = true;
 #pragma unroll
     for (int deg = n; deg >= 1; --deg) {
         const float la = norm2(a[deg]), l0 = norm2(a[0]);
-        bad = bad || !(la > 0.f) || fabsf(la - l0) <= 2e-4f * la;
+        ok = ok && la > 0.f && la < 3e38f && l0 < 3e38f && fabsf(la - l0) > 2e-4f * la;
         if (l0 < la) inside |= 1ull << deg;
         const cx<float> g = frcp(la) * (a[0] * a[deg]);  // a0 / conj(a_deg)
         cx<float> b[n];
@@ -372,23 +373,11 @@ __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
         for (int k = 1; k <= deg; ++k) b[k - 1] = a[k] - g * conjg(a[deg - k]);
 #pragma unroll
         for (int k = 0; k < deg; ++k) a[k] = b[k];
-        if (deg > 1) {
-            const float m = fmaxf(fabsf(a[deg - 1].r), fabsf(a[deg - 1].i));
-            if (m > 0x1p40f || m < 0x1p-40f) {
-                if (m > 0.f && isfinite(m)) {
-                    const float sc = __int_as_float((254 - ((__float_as_int(m) >> 23) & 0xff)) << 23);
-#pragma unroll
-                    for (int k = 0; k < deg; ++k) a[k] = sc * a[k];
-                } else {
-                    bad = true;
-                }
-            }
-        }
     }
     int N = 0;
 #pragma unroll
     for (int d = 1; d <= n; ++d) N = ((inside >> d) & 1ull) ? N + 1 : d - 1 - N;
-    return bad ? -1 : N;
+    return ok ? N : -1;
 }
 
 // Newton steps of the signal root before a lane counts as not converged (it then takes the full
