@@ -20,6 +20,10 @@
 // T = float feeds the FP32 paths (complex64 output); T = double feeds the plain FP64 path
 // (complex128 output), so that path is double precision end to end. Complex64 frames are the
 // analytic signal already and are only copied into the workspace layout.
+#include <math.h>
+
+#include <algorithm>
+
 #include "rmusic_device.cuh"
 #include "rmusic_launch.h"
 
@@ -190,6 +194,176 @@ __device__ void analytic_line_fft(const FrameDev& F, int li, const unsigned char
     }
 }
 
+// ---- warp-FFT band-pass: lines of len = 32 R samples (R = 8, 16, 32) along rows ------------------
+// A warp takes G = 32 / R adjacent lines whose windows run along the carrier (rows in, rows out). With
+// n = 32 a + l and k = b + R m (a, b < R; l, m < 32) the forward transform factors as
+//   X[b + R m] = sum_l W32^(l m) W_len^(l b) sum_a x[32 a + l] W_R^(a b),
+// so lane l first takes the R-point DFTs over a of its column (registers), the result is twiddled by
+// W_len^(l b) and transposed through shared memory, and lane t = g R + b takes the 32-point DFT over
+// l of line g's column b. The band k_lo <= k < k_lo + nb is kept and the inverse runs the same
+// factorisation backwards (32-point inverse over m per lane, twiddle W_len^(-b l), transpose, R-point
+// inverse over b per lane), which leaves lane l with samples l + 32 a: the loads and stores are
+// coalesced rows and no __syncthreads is needed. The forward transforms are decimation in frequency
+// (natural order in, bit-reversed out), the inverse ones decimation in time (bit-reversed in), so no
+// reordering pass is needed. Twiddles: W32^e from cos(pi e / 16) constants, W_len^j from a table of
+// exp(-2 pi j k / 1024) computed in double on the host.
+constexpr int kFastTile = 32 * 33;  // float2 per warp: a 32 x 32 transpose tile with a padded row
+constexpr size_t kFastSmem = (kA1Threads / 32) * kFastTile * sizeof(float2);
+__device__ float2 g_tw1024[1024];  // exp(-2 pi j k / 1024)
+
+// cos(pi e / 16) for an integer e >= -16 (a constant when e is)
+__device__ __forceinline__ float cos_pi16(int e) {
+    e &= 31;
+    if (e > 16) e = 32 - e;
+    const float t[17] = {1.0f,
+                         0.98078528040323044913f,
+                         0.92387953251128675613f,
+                         0.83146961230254523708f,
+                         0.70710678118654752440f,
+                         0.55557023301960222474f,
+                         0.38268343236508977173f,
+                         0.19509032201612826785f,
+                         0.0f,
+                         -0.19509032201612826785f,
+                         -0.38268343236508977173f,
+                         -0.55557023301960222474f,
+                         -0.70710678118654752440f,
+                         -0.83146961230254523708f,
+                         -0.92387953251128675613f,
+                         -0.98078528040323044913f,
+                         -1.0f};
+    return t[e];
+}
+
+// d W32^e (forward) or d W32^-e (INV), W32 = exp(-2 pi j / 32), 0 <= e < 16
+template <bool INV>
+__device__ __forceinline__ cx<float> tw32(cx<float> d, int e) {
+    if (e == 0) return d;
+    if (e == 8) return INV ? mkc(-d.i, d.r) : mkc(d.i, -d.r);
+    const float c = cos_pi16(e), s = cos_pi16(8 - e);  // cos and sin of pi e / 16
+    return INV ? mkc(d.r * c - d.i * s, d.r * s + d.i * c) : mkc(d.r * c + d.i * s, d.i * c - d.r * s);
+}
+
+__host__ __device__ constexpr int brev_bits(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+__host__ __device__ constexpr int log2_int(int x) { return x <= 1 ? 0 : 1 + log2_int(x >> 1); }
+
+// Radix-2 decimation in frequency on v[o .. o + R): natural order in, bin k at o + brev(k).
+template <int R, bool INV>
+__device__ __forceinline__ void dif_block(cx<float> (&v)[32], int o) {
+#pragma unroll
+    for (int half = R / 2; half >= 1; half >>= 1) {
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * half) {
+#pragma unroll
+            for (int j = 0; j < half; ++j) {
+                const cx<float> a = v[o + g + j], b = v[o + g + j + half];
+                v[o + g + j] = a + b;
+                v[o + g + j + half] = tw32<INV>(a - b, j * (16 / half));
+            }
+        }
+    }
+}
+
+// Radix-2 decimation in time on v[o .. o + R): bin k at o + brev(k) in, natural order out.
+template <int R, bool INV>
+__device__ __forceinline__ void dit_block(cx<float> (&v)[32], int o) {
+#pragma unroll
+    for (int half = 1; half < R; half <<= 1) {
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * half) {
+#pragma unroll
+            for (int j = 0; j < half; ++j) {
+                const cx<float> a = v[o + g + j], b = tw32<INV>(v[o + g + j + half], j * (16 / half));
+                v[o + g + j] = a + b;
+                v[o + g + j + half] = a - b;
+            }
+        }
+    }
+}
+
+// One warp's group of G = 32 / R lines starting at line0 (nvalid of them inside the frame).
+template <int R>
+__device__ void analytic_group_fft(const FrameDev& F, int line0, int nvalid, const unsigned char* __restrict__ in,
+                                   cx<float>* __restrict__ gam, float2* tile) {
+    constexpr int G = 32 / R;
+    constexpr int LR = log2_int(R);
+    constexpr int len = 32 * R;
+    const int lane = threadIdx.x & 31;
+    cx<float> v[32];
+    // load (coalesced rows) and remove each line's mean
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const bool ok = g < nvalid;
+        const uint64_t row = (uint64_t)(line0 + g) * (uint64_t)F.pitch;
+        float s = 0.f;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const float x = ok ? frame_sample<float>(F, in, row + 32 * a + lane) : 0.f;
+            v[g * R + a] = mkc(x, 0.f);
+            s += x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float mean = s * (1.f / (float)len);
+#pragma unroll
+        for (int a = 0; a < R; ++a) v[g * R + a].r -= mean;
+    }
+    // R-point DFTs over a, twiddle W_len^(l b), transpose: row g R + b, column l
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        dif_block<R, false>(v, g * R);
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+            const float2 w = g_tw1024[lane * b * (1024 / len)];
+            const cx<float> y = v[g * R + brev_bits(b, LR)] * mkc(w.x, w.y);
+            tile[(g * R + b) * 33 + lane] = make_float2(y.r, y.i);
+        }
+    }
+    __syncwarp();
+    // lane t = g R + b: 32-point DFT over l, the band, 32-point inverse over m
+    const int t = lane, b = t % R;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+        const float2 z = tile[t * 33 + l];
+        v[l] = mkc(z.x, z.y);
+    }
+    dif_block<32, false>(v, 0);
+#pragma unroll
+    for (int m = 0; m < 32; ++m) {
+        const int k = b + R * m;
+        if (k < F.k_lo || k >= F.k_lo + F.nb) v[brev_bits(m, 5)] = mkc(0.f, 0.f);
+    }
+    dit_block<32, true>(v, 0);
+    __syncwarp();  // every lane has read its tile row
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+        const float2 w = g_tw1024[b * l * (1024 / len)];
+        const cx<float> y = v[l] * mkc(w.x, -w.y);
+        tile[t * 33 + l] = make_float2(y.r, y.i);
+    }
+    __syncwarp();
+    // lane l: R-point inverse over b for each line, samples l + 32 a
+    const float inv_len = 1.f / (float)len;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+#pragma unroll
+        for (int bb = 0; bb < R; ++bb) {
+            const float2 z = tile[(g * R + bb) * 33 + lane];
+            v[g * R + bb] = mkc(z.x, z.y);
+        }
+        dif_block<R, true>(v, g * R);
+        if (g < nvalid) {
+            cx<float>* out = gam + F.gam_off + (uint64_t)(line0 + g) * (uint64_t)F.wlen;
+#pragma unroll
+            for (int a = 0; a < R; ++a) out[32 * a + lane] = inv_len * v[g * R + brev_bits(a, LR)];
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kA1Threads)
 analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned char* __restrict__ in,
@@ -201,6 +375,7 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
     const int f = find_frame(fr, nframes, line, [](const FrameDev& F) { return F.line_start; });
     const FrameDev& F = fr[f];
     const int li = (int)(line - F.line_start);
+    if (F.band_r) return;  // taken by analytic_fast_kernel
     const int len = F.len;
     T* v = a1_smem;
     cx<T>* X = reinterpret_cast<cx<T>*>(a1_smem + ((len + 3) & ~3));
@@ -304,6 +479,30 @@ analytic_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned cha
     }
 }
 
+// The warp-FFT schedule (frames with band_r != 0): each CTA's 4 warps take 4 groups of 32 / R lines.
+// A kernel of its own, so that its register budget (the 32-sample transforms in registers) does not
+// lower the occupancy of the per-line schedule.
+__global__ void __launch_bounds__(kA1Threads, 4)
+analytic_fast_kernel(const FrameDev* __restrict__ fr, int nframes, const unsigned char* __restrict__ in,
+                     cx<float>* __restrict__ gam) {
+    extern __shared__ __align__(16) float2 a1_fast_smem[];
+    const int64_t cta = blockIdx.x;
+    const int f = find_frame(fr, nframes, cta, [](const FrameDev& F) { return F.line_start; });
+    const FrameDev& F = fr[f];
+    if (!F.band_r) return;  // taken by analytic_kernel
+    const int G = 32 / F.band_r;
+    const int line0 = ((int)(cta - F.line_start) * (kA1Threads / 32) + (int)(threadIdx.x >> 5)) * G;
+    const int nvalid = min(G, F.nlines - line0);
+    if (nvalid <= 0) return;
+    float2* tile = a1_fast_smem + (threadIdx.x >> 5) * kFastTile;
+    if (F.band_r == 32)
+        analytic_group_fft<32>(F, line0, nvalid, in, gam, tile);
+    else if (F.band_r == 16)
+        analytic_group_fft<16>(F, line0, nvalid, in, gam, tile);
+    else
+        analytic_group_fft<8>(F, line0, nvalid, in, gam, tile);
+}
+
 template <typename T>
 static size_t a1_smem_bytes(int len) {
     // the band-limited DFT: v[len] (padded to 4 elements) + X[nb <= len/2];
@@ -313,24 +512,49 @@ static size_t a1_smem_bytes(int len) {
     return dft > fft ? dft : fft;
 }
 
+int64_t band_assign(FrameDev* F, bool fp64) {
+    F->band_r = 0;
+    const bool rows = F->carrier_axis == 0 && F->deriv_axis == 0;  // lines in, window lines out: rows
+    if (!fp64 && !F->raw && F->dtype != kDtC64 && rows && (F->len == 256 || F->len == 512 || F->len == 1024))
+        F->band_r = F->len / 32;
+    if (!F->band_r) return F->nlines;
+    const int per_cta = (kA1Threads / 32) * (32 / F->band_r);
+    return (F->nlines + per_cta - 1) / per_cta;
+}
+
 cudaError_t init_analytic() {
-    cudaError_t e = cudaFuncSetAttribute(analytic_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)a1_smem_bytes<float>(kMaxLine));
+    // exp(-2 pi j k / 1024) in double, rounded once
+    float2 tw[1024];
+    for (int k = 0; k < 1024; ++k) {
+        const double a = 6.283185307179586476925 * (double)k / 1024.0;
+        tw[k] = make_float2((float)cos(a), (float)-sin(a));
+    }
+    cudaError_t e = cudaMemcpyToSymbol(g_tw1024, tw, sizeof(tw));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(analytic_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFastSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(analytic_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)a1_smem_bytes<float>(kMaxLine));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(analytic_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)a1_smem_bytes<double>(kMaxLine));
 }
 
-cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_lines, int max_len,
+cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_lines, int max_len, int schedules,
                             const void* d_in, void* d_gamma, bool fp64, cudaStream_t stream) {
     if (total_lines <= 0) return cudaSuccess;
     const unsigned char* in = static_cast<const unsigned char*>(d_in);
     if (fp64)
         analytic_kernel<double><<<(unsigned)total_lines, kA1Threads, a1_smem_bytes<double>(max_len), stream>>>(
             d_frames, nframes, in, static_cast<cx<double>*>(d_gamma));
-    else
-        analytic_kernel<float><<<(unsigned)total_lines, kA1Threads, a1_smem_bytes<float>(max_len), stream>>>(
-            d_frames, nframes, in, static_cast<cx<float>*>(d_gamma));
+    else {
+        if (schedules & kBandPerLine)
+            analytic_kernel<float><<<(unsigned)total_lines, kA1Threads, a1_smem_bytes<float>(max_len), stream>>>(
+                d_frames, nframes, in, static_cast<cx<float>*>(d_gamma));
+        if ((schedules & kBandWarpFft) && cudaPeekAtLastError() == cudaSuccess)
+            analytic_fast_kernel<<<(unsigned)total_lines, kA1Threads, kFastSmem, stream>>>(
+                d_frames, nframes, in, static_cast<cx<float>*>(d_gamma));
+    }
     return cudaGetLastError();
 }
 

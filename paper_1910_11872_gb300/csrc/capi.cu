@@ -200,7 +200,8 @@ struct Plan {
     std::vector<int> group_first;  // batched: first table entry of each group
     std::vector<int> group_count;
     std::vector<int64_t> group_items;
-    int64_t total_lines = 0;
+    int64_t total_lines = 0;  // band-pass CTAs
+    int band_sched = 0;       // kBand* bits of the band-pass schedules the frames take
     int64_t cross_groups = 0;  // 32-line groups of the cross-band pass (0: no cross band)
     int max_kc = 0;
     int max_len = 0;
@@ -301,7 +302,8 @@ int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Pla
         F.gam_off = goff;
         goff += (uint64_t)F.H * (uint64_t)F.W;
         F.line_start = lines;
-        lines += F.nlines;
+        lines += band_assign(&F, ctx->p.precision == RMUSIC_PLAIN_FP64);
+        plan->band_sched |= band_schedule_bit(F);
         if (ctx->p.band_cross > 0.0) {
             F.cross_start = plan->cross_groups;
             plan->cross_groups += ((F.carrier_axis == 0 ? F.W : F.H) + 31) / 32;
@@ -546,7 +548,8 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
     const int n = (int)plan.frames.size();
     int e0 = stamp(ctx, s);
     const bool fp64 = ctx->p.precision == RMUSIC_PLAIN_FP64;
-    RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, d_frames, ctx->d_gamma, fp64, s));
+    RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, plan.band_sched, d_frames, ctx->d_gamma,
+                            fp64, s));
     ++*launches;
     if (plan.cross_groups > 0) {
         RM_CUDA(launch_crossband(ctx->d_table, n, plan.cross_groups, plan.max_kc, ctx->d_gamma, fp64, s));
@@ -647,7 +650,8 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
             RM_CUDA(cudaMemcpyAsync(ctx->d_table, ctx->h_table, plan.frames.size() * sizeof(FrameDev),
                                     cudaMemcpyHostToDevice, s));
             RM_CUDA(cudaEventRecord(ctx->table_free, s));
-            RM_CUDA(launch_analytic(ctx->d_table, (int)plan.frames.size(), plan.total_lines, plan.max_len, d_frames,
+            RM_CUDA(launch_analytic(ctx->d_table, (int)plan.frames.size(), plan.total_lines, plan.max_len,
+                                    plan.band_sched, d_frames,
                                     ctx->d_gamma, false, s));
             if (plan.cross_groups > 0)
                 RM_CUDA(launch_crossband(ctx->d_table, (int)plan.frames.size(), plan.cross_groups, plan.max_kc,

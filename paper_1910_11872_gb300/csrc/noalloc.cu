@@ -151,14 +151,16 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
     int64_t group_items[kMaxL + 1];
     int ngroups = 0;
     uint64_t goff = 0;
-    int64_t lines = 0;
+    int64_t lines = 0;  // band-pass CTAs
+    int band_sched = 0;
     int max_len = 0;
     for (int i = 0; i < n_frames; ++i) {
         FrameDev& F = table[i];
         F.gam_off = goff;
         goff += (uint64_t)F.H * (uint64_t)F.W;
         F.line_start = lines;
-        lines += F.nlines;
+        lines += band_assign(&F, false);
+        band_sched |= band_schedule_bit(F);
         max_len = std::max(max_len, F.len);
         if (i == 0 || F.L != table[i - 1].L) {
             group_L[ngroups] = F.L;
@@ -195,7 +197,7 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
             rc = RMUSIC_ECUDA;
             break;
         }
-        if (launch_analytic(d_table, n_frames, lines, max_len, d_frames, gamma, false, s) != cudaSuccess) {
+        if (launch_analytic(d_table, n_frames, lines, max_len, band_sched, d_frames, gamma, false, s) != cudaSuccess) {
             rc = RMUSIC_ECUDA;
             break;
         }

@@ -50,6 +50,8 @@ struct FrameDev {
     int64_t cross_start;  // first 32-line group of this frame in the cross-band grid
     int32_t cross_kc;     // cross band: signed bins -kc .. kc kept across the carrier (0: none)
     int32_t raw;          // 1: no band-pass; Gamma = the real line minus its mean
+    int32_t band_r;       // band-pass schedule: 0 one CTA per carrier line; 8, 16 or 32: lines of
+                          // 32 band_r samples in groups of 4 x 32 / band_r per CTA (warp FFTs)
 };
 
 // Index of the frame that owns global index `g` given each frame's start (non-decreasing).

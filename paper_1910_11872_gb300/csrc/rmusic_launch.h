@@ -9,10 +9,16 @@
 
 namespace rmusic {
 
-// Band-pass analytic signal of every carrier line (Sec. 2, Eq. 1). One CTA per line.
+// Band-pass analytic signal of every carrier line (Sec. 2, Eq. 1). init_analytic must run once per
+// device (it also uploads the twiddle table). band_assign picks a frame's band-pass schedule
+// (F->band_r) and returns the CTAs it takes; frames' line_start values are the running sums of
+// those counts, total_ctas their sum, schedules the kBand* bits of the schedules the frames take.
+constexpr int kBandPerLine = 1, kBandWarpFft = 2;
 cudaError_t init_analytic();
+int64_t band_assign(FrameDev* F, bool fp64);
+inline int band_schedule_bit(const FrameDev& F) { return F.band_r ? kBandWarpFft : kBandPerLine; }
 // fp64 = true writes complex128 (plain FP64 path), otherwise complex64.
-cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_lines, int max_len,
+cudaError_t launch_analytic(const FrameDev* d_frames, int nframes, int64_t total_ctas, int max_len, int schedules,
                             const void* d_in, void* d_gamma, bool fp64, cudaStream_t stream);
 
 // 2-D band-pass variant: low-pass |k / len| < B_c across the carrier lines of the workspace, in
