@@ -449,8 +449,9 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         // dropped: S is normalised by its trace below, which leaves its eigenvectors unchanged.
         // The lags are taken kLagBlock at a time: a rolled loop forms each lag's products and their
         // warp scan into its own slot of pre[], then an unrolled pass reads the box sums of the
-        // block's lags into S (compile-time targets). Rolling the scan keeps the code small enough
-        // for the instruction cache, which the fully unrolled form overran.
+        // block's lags into S (compile-time targets). Rolling the scan (two lags per pass, so that two
+        // scans' shuffle chains overlap) keeps the code small enough for the instruction cache, which
+        // the fully unrolled form overran.
         float S[NS];
 #pragma unroll
         for (int i = 0; i < NS; ++i) S[i] = 0.f;
@@ -459,7 +460,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             constexpr int kLB = kLagBlock;
             const int nd = L - d0 < kLB ? L - d0 : kLB;
             __syncwarp();  // the previous block's box sums have been read
-#pragma unroll 1
+#pragma unroll 2
             for (int dd = 0; dd < nd; ++dd) {
                 const int d = d0 + dd;
                 const int G = 31 + N - d;  // lag products g_d[0 .. G-1] are needed

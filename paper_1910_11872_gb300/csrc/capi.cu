@@ -477,7 +477,7 @@ cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, fl
         a.max_iters = p.max_root_iters ? p.max_root_iters : 32;
         a.polish64 = p.polish_fp64;
         a.exhaustive = p.exhaustive;
-        a.tol2 = 1e-11f;
+        a.tol2 = 1e-9f;  // power iteration: stop at a step below 3.2e-5 (u1 to ~1e-5)
         a.counters = stat_counters;
         return launch_square(key - kSquareKey0, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
                              plan.group_items[g], ctx->d_counters + g, gamma, d_out, d_status, a,

@@ -308,7 +308,9 @@ __device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<fl
 // Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' -- from the estimator's
 // start 0.99 exp(j arg conj(rho_1)) (the start inner_roots gives the signal root). A step that
 // leaves the disk is folded back onto the mirror. A lane stops when |Q| is at the FP32 rounding
-// level (the step is then not taken, as in inner_roots) or the step is below 1e-6; the warp stops
+// level (the step is then not taken, as in inner_roots) or the step is below 1e-3 (the root is then
+// known to ~1e-6, far inside the certificate's 0.02 margin, and the two polish steps that follow
+// converge quadratically from there); the warp stops
 // when every lane has or after max_iters steps (conv false for the lanes still moving). Inactive
 // lanes (pixels without a result) count as stopped from the start.
 template <int L>
@@ -334,7 +336,7 @@ __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, floa
             const float r2 = norm2(z);
             if (r2 > 1.f) z = frcp(r2) * z;
         }
-        conv = conv || small || (fin && norm2(w) <= 1e-12f);
+        conv = conv || small || (fin && norm2(w) <= 1e-6f);
         if (steps >= max_iters || __all_sync(kFull, conv)) break;
     }
     return z;

@@ -21,7 +21,7 @@
 // so only one M-vector is held in registers.
 // Each step shrinks the other singular directions by (s_2 / s_1)^2 ~ 4 sigma^2 / (M A^2), or,
 // with the shift by twice the mean noise eigenvalue that the kernel applies from the first step,
-// by about half of that; the iteration stops when the step changes u by less than 3e-6 in every
+// by about half of that; the iteration stops when the step changes u by less than 3e-5 in every
 // lane of the warp. v1 is G^H u from the last step. Degenerate blocks (all zero) get a stand-in vector so every lane of
 // the warp runs the same bounded loops.
 //
