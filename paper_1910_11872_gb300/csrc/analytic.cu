@@ -195,7 +195,8 @@ __device__ void analytic_line_fft(const FrameDev& F, int li, const unsigned char
 }
 
 // ---- warp-FFT band-pass: lines of len = 32 R samples (R = 8, 16, 32) along rows ------------------
-// A warp takes G = 32 / R adjacent lines whose windows run along the carrier (rows in, rows out). With
+// A warp takes G = 32 / R adjacent carrier lines (rows; the windows may run along them or across
+// them, in which case the samples are stored column-major). With
 // n = 32 a + l and k = b + R m (a, b < R; l, m < 32) the forward transform factors as
 //   X[b + R m] = sum_l W32^(l m) W_len^(l b) sum_a x[32 a + l] W_R^(a b),
 // so lane l first takes the R-point DFTs over a of its column (registers), the result is twiddled by
@@ -357,9 +358,19 @@ __device__ void analytic_group_fft(const FrameDev& F, int line0, int nvalid, con
         }
         dif_block<R, true>(v, g * R);
         if (g < nvalid) {
-            cx<float>* out = gam + F.gam_off + (uint64_t)(line0 + g) * (uint64_t)F.wlen;
+            if (F.deriv_axis == 0) {
+                // windows along the line: the workspace row is the line (coalesced stores)
+                cx<float>* out = gam + F.gam_off + (uint64_t)(line0 + g) * (uint64_t)F.wlen;
 #pragma unroll
-            for (int a = 0; a < R; ++a) out[32 * a + lane] = inv_len * v[g * R + brev_bits(a, LR)];
+                for (int a = 0; a < R; ++a) out[32 * a + lane] = inv_len * v[g * R + brev_bits(a, LR)];
+            } else {
+                // windows across the lines (columns): sample x of line y goes to x wlen + y; the
+                // CTA's 4 G consecutive lines fill each column's 32-byte sectors in L2
+                cx<float>* out = gam + F.gam_off + (uint64_t)(line0 + g);
+#pragma unroll
+                for (int a = 0; a < R; ++a)
+                    out[(uint64_t)(32 * a + lane) * (uint64_t)F.wlen] = inv_len * v[g * R + brev_bits(a, LR)];
+            }
         }
     }
 }
@@ -514,7 +525,8 @@ static size_t a1_smem_bytes(int len) {
 
 int64_t band_assign(FrameDev* F, bool fp64) {
     F->band_r = 0;
-    const bool rows = F->carrier_axis == 0 && F->deriv_axis == 0;  // lines in, window lines out: rows
+    // carrier lines are rows (coalesced loads); the windows run along them or across them
+    const bool rows = F->carrier_axis == 0;
     if (!fp64 && !F->raw && F->dtype != kDtC64 && rows && (F->len == 256 || F->len == 512 || F->len == 1024))
         F->band_r = F->len / 32;
     if (!F->band_r) return F->nlines;
