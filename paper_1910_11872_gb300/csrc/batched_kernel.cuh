@@ -331,12 +331,20 @@ __device__ __forceinline__ void inverse_iteration(const float* Ssh, float l1, in
 // a_kk differs from l1 by at most about off / gap, so once off <= 1e-3 gap^2 the shift is within
 // ~1e-3 gap of l1 and three inverse-iteration steps reduce the other eigenvectors' share by ~1e-9.
 // More sweeps run only while some lane of the warp is short of that (up to max_sweeps).
+// The fallback of the power iteration: out of line (a call), so that its register demand does not set
+// the register budget of the hot path; S is read back from the thread's parked column, the results
+// go through the caller's small local copies.
 template <int L>
-__device__ __forceinline__ void jacobi_eigvec(float (&S)[L * (L + 1) / 2], const float* Ssh, int max_sweeps,
-                                              float (&x)[L], float& l1, float& l2, int& sweeps, bool& jconv) {
+__device__ __noinline__ void jacobi_eigvec(const float* Ssh, int max_sweeps, float* x_out, float* l12_out,
+                                           int* sweeps_out, bool* jconv_out) {
     constexpr int NS = L * (L + 1) / 2;
-    sweeps = 0;
-    jconv = false;
+    float S[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) S[i] = Ssh[i * kBatThreads];
+    float x[L];
+    float l1 = 0.f, l2 = 0.f;
+    int sweeps = 0;
+    bool jconv = false;
     int k1 = 0;
     for (;;) {
 #pragma unroll 1
@@ -396,6 +404,12 @@ __device__ __forceinline__ void jacobi_eigvec(float (&S)[L * (L + 1) / 2], const
         if (__all_sync(kFull, jconv)) break;
     }
     inverse_iteration<L>(Ssh, l1, k1, x);
+#pragma unroll
+    for (int i = 0; i < L; ++i) x_out[i] = x[i];
+    l12_out[0] = l1;
+    l12_out[1] = l2;
+    *sweeps_out = sweeps;
+    *jconv_out = jconv;
 }
 
 // CTAS is the number of 128-thread CTAs the kernel is compiled to keep resident per SM
@@ -548,14 +562,14 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             const bool need = nonzero && (args.exhaustive || !jconv || !(l1 - l2 > 4e-6f * l1));
             if (__any_sync(kFull, need)) {
                 eig_fb = 1;
-                float xj[L], jl1, jl2;
+                float xj[L], jl[2];
                 bool jc;
-                jacobi_eigvec<L>(S, Ssh, args.max_sweeps, xj, jl1, jl2, sweeps, jc);
+                jacobi_eigvec<L>(Ssh, args.max_sweeps, xj, jl, &sweeps, &jc);
                 if (need) {
 #pragma unroll
                     for (int i = 0; i < L; ++i) x[i] = xj[i];
-                    l1 = jl1;
-                    l2 = jl2;
+                    l1 = jl[0];
+                    l2 = jl[1];
                     jconv = jc;
                 }
             }

@@ -386,6 +386,33 @@ __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
 // root finder): 3-4 on row windows, 4-7 on square blocks at 0-10 dB.
 constexpr int kNewtonSteps = 16;
 
+// The full root finder of the fallback, out of line: inner_roots and nearest_pair on a copy of the
+// coefficients. It runs only in warps where some lane lacks the certificate; compiled as a call, its
+// register demand (every inner root and mirror live at once) does not set the register budget of
+// the certified path, which then fits a tighter cap without spilling. The arguments are the
+// caller's copies made inside the fallback branch, so the hot path's arrays stay in registers.
+template <int L>
+__device__ __noinline__ void aberth_select(const cx<float>* c_in, float res_lim2, int max_iters, cx<float>* zs,
+                                           cx<float>* zn, bool* found, bool* conv, int* stats) {
+    constexpr int NI = L - 1;
+    cx<float> c[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) c[i] = c_in[i];
+    cx<float> z[NI], mz[NI];
+    int iters, evals, updates;
+    bool aconv, afound;
+    cx<float> a, b;
+    inner_roots<L>(c, res_lim2, max_iters, z, mz, iters, evals, updates, aconv);
+    nearest_pair<L>(z, mz, a, b, afound);
+    *zs = a;
+    *zn = b;
+    *found = afound;
+    *conv = aconv;
+    stats[0] = iters;
+    stats[1] = evals;
+    stats[2] = updates;
+}
+
 struct RootStats {
     int newton;   // Newton steps of the signal root
     int fallback; // 1 if the warp ran the full Aberth iteration
@@ -408,7 +435,6 @@ template <int L>
 __device__ __forceinline__ cx<float> signal_root(const cx<float>* c, float res_lim2, int max_iters, int exhaustive,
                                                  bool active, bool& found, bool& cluster, bool& rconv,
                                                  RootStats& rs) {
-    constexpr int NI = L - 1;
     bool nconv = false, cert = false;
     cx<float> zs = mkc(0.f, 0.f), zn = zs;
     rs.newton = 0;
@@ -427,11 +453,16 @@ __device__ __forceinline__ cx<float> signal_root(const cx<float>* c, float res_l
     rs.iters = rs.evals = rs.updates = 0;
     if (__any_sync(kFull, !cert)) {
         rs.fallback = 1;
-        cx<float> z[NI], mz[NI];
+        cx<float> cl[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) cl[i] = c[i];
         bool aconv, afound;
         cx<float> azs, azn;
-        inner_roots<L>(c, res_lim2, max_iters, z, mz, rs.iters, rs.evals, rs.updates, aconv);
-        nearest_pair<L>(z, mz, azs, azn, afound);
+        int st[3];
+        aberth_select<L>(cl, res_lim2, max_iters, &azs, &azn, &afound, &aconv, st);
+        rs.iters = st[0];
+        rs.evals = st[1];
+        rs.updates = st[2];
         if (!cert) {
             zs = azs;
             zn = azn;
