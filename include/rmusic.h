@@ -211,10 +211,14 @@ int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic
 int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int32_t n_frames,
                     float* d_out, uint8_t* d_status, void* cuda_stream);
 
-/* Same as rmusic_demodulate_frames, but every buffer is in HOST memory: the library copies the
- * frames to its device workspace, runs the same kernels and copies the maps back before it
- * returns (the call synchronises its stream). in_bytes is the size of h_frames. Pinned host
- * memory makes the copies asynchronous DMA; pageable memory also works. */
+/* Same as rmusic_demodulate_frames, but every buffer is in HOST memory; the maps are complete when
+ * the call returns (it synchronises its stream). in_bytes is the size of h_frames. Buffers the GPU
+ * can address directly (pinned memory from cudaHostAlloc / cudaMallocHost, or registered with
+ * cudaHostRegister) are used in place: the band-pass kernel reads the frames and the solver writes
+ * the maps over the host link while it runs, instead of a copy before and after the kernels (with
+ * phase assembly, square geometry with unwrap = 1, the maps are still staged on the device).
+ * Pageable buffers are copied to and from the context's device workspace. The results are
+ * identical either way. */
 int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
                                   const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
                                   uint8_t* h_status, void* cuda_stream);

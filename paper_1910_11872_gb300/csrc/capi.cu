@@ -862,6 +862,25 @@ int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
     return demodulate_impl(ctx, d_frames, descs, n_frames, d_out, d_status, cuda_stream, true);
 }
 
+}  // extern "C"
+
+namespace {
+// Device address of a host buffer the GPU can address directly (pinned, registered or mapped host
+// memory: on a Grace-Blackwell node the kernels then read and write it over the coherent
+// NVLink-C2C link), or nullptr for pageable memory, which is staged through the device workspace.
+void* direct_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // an unregistered pointer may report an error: clear it
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+}  // namespace
+
+extern "C" {
+
 int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
                                   const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
                                   uint8_t* h_status, void* cuda_stream) {
@@ -882,15 +901,28 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
         out_elems = std::max<uint64_t>(out_elems, d.out_offset + (uint64_t)maps * d.height * d.width);
         st_elems = std::max<uint64_t>(st_elems, d.out_offset + (uint64_t)d.height * d.width);
     }
-    int rc = ensure(ctx, &ctx->d_in, &ctx->in_cap, std::max<size_t>(in_bytes, 16));
-    if (!rc) {
+    // Pinned (device-addressable) buffers are used in place: the band-pass reads the frames and the
+    // solver writes the maps over the host link while it computes, instead of a copy before and a
+    // copy after the kernels. The unwrapping pass reads and writes its maps many times, so with
+    // phase assembly the maps are staged on the device.
+    const void* d_in = direct_host_ptr(h_frames);
+    const bool staged_maps = ctx->p.geometry == RMUSIC_GEOM_SQUARE && ctx->p.unwrap;
+    float* d_out = staged_maps ? nullptr : static_cast<float*>(direct_host_ptr(h_out));
+    uint8_t* d_st = nullptr;
+    if (d_out && h_status) {
+        d_st = static_cast<uint8_t*>(direct_host_ptr(h_status));
+        if (!d_st) d_out = nullptr;  // both maps go the same way
+    }
+    int rc = RMUSIC_OK;
+    if (!d_in) rc = ensure(ctx, &ctx->d_in, &ctx->in_cap, std::max<size_t>(in_bytes, 16));
+    if (!rc && !d_out) {
         size_t ob = ctx->out_cap;
         void* op = ctx->d_out;
         rc = ensure(ctx, &op, &ob, out_elems * sizeof(float));
         ctx->d_out = (float*)op;
         ctx->out_cap = ob;
     }
-    if (!rc && h_status) {
+    if (!rc && !d_out && h_status) {
         size_t sb = ctx->st_cap;
         void* sp = ctx->d_st;
         rc = ensure(ctx, &sp, &sb, st_elems);
@@ -898,12 +930,21 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
         ctx->st_cap = sb;
     }
     if (rc) return rc;
-    RM_CUDA(cudaMemcpyAsync(ctx->d_in, h_frames, in_bytes, cudaMemcpyHostToDevice, s));
-    rc = rmusic_demodulate_frames(ctx, ctx->d_in, descs, n_frames, ctx->d_out, h_status ? ctx->d_st : nullptr,
-                                  cuda_stream);
+    if (!d_in) {
+        RM_CUDA(cudaMemcpyAsync(ctx->d_in, h_frames, in_bytes, cudaMemcpyHostToDevice, s));
+        d_in = ctx->d_in;
+    }
+    const bool direct_out = d_out != nullptr;
+    if (!direct_out) {
+        d_out = ctx->d_out;
+        d_st = h_status ? ctx->d_st : nullptr;
+    }
+    rc = rmusic_demodulate_frames(ctx, d_in, descs, n_frames, d_out, d_st, cuda_stream);
     if (rc) return rc;
-    RM_CUDA(cudaMemcpyAsync(h_out, ctx->d_out, out_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
-    if (h_status) RM_CUDA(cudaMemcpyAsync(h_status, ctx->d_st, st_elems, cudaMemcpyDeviceToHost, s));
+    if (!direct_out) {
+        RM_CUDA(cudaMemcpyAsync(h_out, ctx->d_out, out_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (h_status) RM_CUDA(cudaMemcpyAsync(h_status, ctx->d_st, st_elems, cudaMemcpyDeviceToHost, s));
+    }
     RM_CUDA(cudaStreamSynchronize(s));
     return RMUSIC_OK;
 }

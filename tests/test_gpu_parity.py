@@ -492,3 +492,35 @@ def test_solver_variants_and_warp_per_matrix_schedule(L):
     off = frames[0].size
     v = (os_.ravel() == 0) & (gs[off:] == 0)
     assert np.abs(g[off:][v] - o.ravel()[v]).max() <= 1e-4
+
+
+def test_host_entry_pinned_buffers_in_place_equal_device_entry():
+    """Pinned host buffers are read and written by the kernels in place (no staging copies); the
+    maps and statuses equal the device entry's, and so do those of a staged (pageable) call."""
+    torch = _torch()
+    frames = [synth.peaks_frame(10, 0.1, H=33, W=1024).image, synth.peaks_frame(np.inf, 0.1, H=20, W=300).image]
+    flat = np.concatenate([f.ravel() for f in frames]).astype(np.float32)
+    descs, nbytes, nout = rmusic.frame_descs([f.shape for f in frames], rmusic.RMUSIC_DTYPE_F32, 4)
+    hin = torch.from_numpy(flat).pin_memory()
+    hout = torch.full((nout,), 7.0).pin_memory()
+    hst = torch.full((nout,), 9, dtype=torch.uint8).pin_memory()
+    dem = rmusic.Demodulator(use_graph=1)
+    try:
+        for _ in range(2):  # the second call replays the captured graph with the host pointers
+            rmusic.rmusic_demodulate_frames_host(dem.ctx, hin.data_ptr(), nbytes, descs, 2, hout.data_ptr(),
+                                                 hst.data_ptr(), None)
+        pout = np.empty(nout, np.float32)
+        pst = np.empty(nout, np.uint8)
+        rmusic.rmusic_demodulate_frames_host(dem.ctx, flat.ctypes.data, nbytes, descs, 2, pout.ctypes.data,
+                                             pst.ctypes.data, None)
+    finally:
+        dem.close()
+    dev = run_gpu(frames)
+    o = 0
+    for f, (g, gs) in zip(frames, dev):
+        n = f.size
+        assert np.array_equal(hout.numpy()[o:o + n].reshape(f.shape), g, equal_nan=True)
+        assert np.array_equal(hst.numpy()[o:o + n].reshape(f.shape), gs)
+        assert np.array_equal(pout[o:o + n].reshape(f.shape), g, equal_nan=True)
+        assert np.array_equal(pst[o:o + n].reshape(f.shape), gs)
+        o += n
