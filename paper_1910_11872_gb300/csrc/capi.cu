@@ -14,6 +14,8 @@
 
 #include <stdlib.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <mutex>
 #include <new>
@@ -543,17 +545,29 @@ int tune_plan(rmusic_ctx* ctx, const Plan& plan, float* d_out, uint8_t* d_status
     return rc;
 }
 
+// An NVTX range around the host-side enqueue of one stage, so that timeline tools (Nsight Systems)
+// group the stage's kernels under its name; a no-op unless such a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_out, uint8_t* d_status,
             cudaStream_t s, int* launches) {
     const int n = (int)plan.frames.size();
     int e0 = stamp(ctx, s);
     const bool fp64 = ctx->p.precision == RMUSIC_PLAIN_FP64;
-    RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, plan.band_sched, d_frames, ctx->d_gamma,
-                            fp64, s));
-    ++*launches;
-    if (plan.cross_groups > 0) {
-        RM_CUDA(launch_crossband(ctx->d_table, n, plan.cross_groups, plan.max_kc, ctx->d_gamma, fp64, s));
+    {
+        NvtxRange r("rmusic.bandpass");
+        RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, plan.band_sched, d_frames,
+                                ctx->d_gamma, fp64, s));
         ++*launches;
+        if (plan.cross_groups > 0) {
+            RM_CUDA(launch_crossband(ctx->d_table, n, plan.cross_groups, plan.max_kc, ctx->d_gamma, fp64, s));
+            ++*launches;
+        }
     }
     stamp_pair(ctx->a1_ev, e0, stamp(ctx, s));
     const rmusic_params& p = ctx->p;
@@ -561,6 +575,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         for (size_t g = 0; g < plan.group_L.size(); ++g) {
             const int L = plan.group_L[g];
             const int v = solver_variant(ctx, L);
+            NvtxRange r("rmusic.solver");
             RM_CUDA(cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s));
             int e1 = stamp(ctx, s);
             RM_CUDA(launch_solver(ctx, plan, g, v, d_out, d_status, ctx->d_counters + kStatSlot, s));
@@ -571,6 +586,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         }
         if (p.unwrap) {
             // phase assembly: the alpha maps (third map) unwrapped into the fourth map
+            NvtxRange r("rmusic.unwrap");
             int64_t maxpx = 0;
             for (const FrameDev& F : plan.frames) maxpx = std::max<int64_t>(maxpx, (int64_t)F.H * F.W);
             RM_CUDA(launch_unwrap(ctx->d_table, n, (int64_t)plan.gamma_elems, maxpx, d_out, 2, d_out, 3,
@@ -582,6 +598,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         a.fb = p.forward_backward;
         a.max_sweeps = p.max_sweeps ? p.max_sweeps : 30;
         a.max_iters = p.max_root_iters ? p.max_root_iters : 500;
+        NvtxRange r("rmusic.plain");
         int e1 = stamp(ctx, s);
         for (int f = 0; f < n; ++f) {
             if (p.precision == RMUSIC_PLAIN_FP64)
