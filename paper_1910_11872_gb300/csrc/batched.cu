@@ -9,7 +9,7 @@ bool batched_supports(int L) { return L == 2 || L == 4 || L == 6 || L == 8 || L 
 
 int batched_num_variants(int L) { return solver_num_variants(L); }
 
-int batched_default_variant(int) { return kSolverDefaultVariant; }
+int batched_default_variant(int L) { return solver_default_variant(L); }
 
 int batched_variant_ctas(int L, int v) { return solver_variant_ctas(L, v); }
 

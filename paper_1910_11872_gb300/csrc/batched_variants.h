@@ -16,14 +16,19 @@ namespace rmusic {
 // (L <= 8) runs the eigenvalue sweeps with the warp-per-matrix schedule at variant 1's cap.
 constexpr int kSolverVariants = 3;
 constexpr int kSolverWarpVariant = 3;
-constexpr int kSolverDefaultVariant = 1;
+constexpr int kSolverMidVariant = 1;
+
+// The variant used without tuning: the measured fastest on a GB300 for L = 8 (4 CTAs/SM: the
+// certified solver with its fallbacks out of line runs best at 128 registers), the middle cap
+// otherwise.
+__host__ __device__ constexpr int solver_default_variant(int L) { return L == 8 ? 0 : kSolverMidVariant; }
 
 __host__ __device__ constexpr int solver_num_variants(int L) { return L <= 8 ? 4 : 3; }
 __host__ __device__ constexpr bool solver_variant_warp(int v) { return v == kSolverWarpVariant; }
 
 // Resident CTAs per SM of variant v for covariance order L.
 __host__ __device__ constexpr int solver_variant_ctas(int L, int v) {
-    return v == kSolverWarpVariant ? solver_variant_ctas(L, kSolverDefaultVariant)
+    return v == kSolverWarpVariant ? solver_variant_ctas(L, kSolverMidVariant)
          : L == 2 ? (v == 0 ? 8 : v == 1 ? 12 : 16)
          : L == 4 ? (v == 0 ? 6 : v == 1 ? 8 : 12)
          : L == 6 ? (v == 0 ? 4 : v == 1 ? 6 : 8)
