@@ -428,7 +428,13 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
     __shared__ float2 sh_seg[kBatWarps][32 + kMaxN];
     __shared__ float2 sh_pre[kBatWarps][kLagBlock * kPreLen];
     __shared__ float sh_S[NS * kBatThreads];
+    // this warp's iteration statistics, added up per item and flushed to args.counters once when
+    // the warp leaves the persistent loop (one atomic per statistic per warp, not per item: the
+    // per-item atomics on one L2 line cost 4 % of the launch)
+    __shared__ unsigned long long sh_stat[kBatWarps][kStatSlots];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < kStatSlots) sh_stat[wid][lane] = 0ull;
+    __syncwarp();
     float2* seg = sh_seg[wid];
     float2* pre = sh_pre[wid];
 
@@ -595,15 +601,16 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         float om = args.polish64 ? (float)omd : wrap_pi(atan2f(zz.i, zz.r) - (float)F.omega_ref);
 
         if (lane == 0 && args.counters) {
-            atomicAdd(args.counters + 0, (unsigned long long)sweeps);
-            atomicAdd(args.counters + 1, (unsigned long long)rs.iters);
-            atomicAdd(args.counters + 2, 1ull);
-            atomicAdd(args.counters + 3, (unsigned long long)rs.updates);
-            atomicAdd(args.counters + 4, (unsigned long long)rs.evals);
-            atomicAdd(args.counters + 5, (unsigned long long)psteps);
-            atomicAdd(args.counters + 6, (unsigned long long)eig_fb);
-            atomicAdd(args.counters + 7, (unsigned long long)rs.newton);
-            atomicAdd(args.counters + 8, (unsigned long long)rs.fallback);
+            unsigned long long* c = sh_stat[wid];
+            c[0] += (unsigned long long)sweeps;
+            c[1] += (unsigned long long)rs.iters;
+            c[2] += 1ull;
+            c[3] += (unsigned long long)rs.updates;
+            c[4] += (unsigned long long)rs.evals;
+            c[5] += (unsigned long long)psteps;
+            c[6] += (unsigned long long)eig_fb;
+            c[7] += (unsigned long long)rs.newton;
+            c[8] += (unsigned long long)rs.fallback;
         }
 
         // ---- store ---------------------------------------------------------------------------------
@@ -621,6 +628,8 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             if (status) status[o] = st;
         }
     }
+    __syncwarp();
+    if (args.counters && lane < kStatSlots && sh_stat[wid][lane]) atomicAdd(args.counters + lane, sh_stat[wid][lane]);
 }
 
 // Launch and occupancy of variant v of the solver for covariance order L (batched_variants.h).

@@ -46,7 +46,6 @@ struct DeviceGuard {
 
 constexpr int kCounterSlots = 64;  // [0, kStatSlot) work counters, [kStatSlot ..] statistics
 constexpr int kStatSlot = 32;
-constexpr int kStatCount = 9;  // statistics slots the solvers add to (rmusic_launch.h lists them)
 
 // A solver key names one compiled solver family: the covariance order L of the row-window
 // solver (2 .. kMaxL), or kSquareKey0 + Lp for the square-block solver.
@@ -835,7 +834,7 @@ int demodulate_impl(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
         if (rc) return rc;
         pixels += (uint64_t)F.H * (uint64_t)F.W;
     }
-    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, kStatCount * sizeof(unsigned long long), s));
+    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, kStatSlots * sizeof(unsigned long long), s));
     // group frames so that each group's analytic signal fits the budget
     const uint64_t table_reserve = 64 * sizeof(FrameDev) + (uint64_t)n_frames * sizeof(FrameDev);
     uint64_t avail = 0;
@@ -1065,7 +1064,7 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->workspace_bytes = ctx->held;
     out->pixels = ctx->last_pixels;
     RM_CUDA(cudaEventSynchronize(ctx->call_done));
-    unsigned long long c[kStatCount] = {};
+    unsigned long long c[kStatSlots] = {};
     RM_CUDA(cudaMemcpy(c, ctx->d_counters + kStatSlot, sizeof(c), cudaMemcpyDeviceToHost));
     auto mean = [&](int i) { return c[2] ? (double)c[i] / (double)c[2] : 0.0; };
     out->mean_sweeps = mean(0);

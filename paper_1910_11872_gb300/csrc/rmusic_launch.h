@@ -41,6 +41,9 @@ cudaError_t launch_plain_fp64(const FrameDev* d_frame, const FrameDev& h_frame, 
 cudaError_t launch_plain_fp32(const FrameDev* d_frame, const FrameDev& h_frame, const float2* d_gamma,
                               float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream);
 
+// Statistics slots of the solvers' counters array (the BatchedArgs / SquareArgs lists below).
+constexpr int kStatSlots = 9;
+
 // Batched FP32 path: persistent, warp-scheduled over all work items of all frames that share
 // covariance order L. `counter` must be zero when the kernel starts.
 struct BatchedArgs {

@@ -56,7 +56,10 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
     __shared__ float2 tile[SH * SW];
     __shared__ float sh_scr[NSCR * kSqThreads];
     __shared__ long long sh_item;
+    // this warp's iteration statistics, flushed to args.counters once when the CTA leaves its loop
+    __shared__ unsigned long long sh_stat[kSqTY][kStatSlots];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < kStatSlots) sh_stat[wid][lane] = 0ull;
     const float tol2 = args.tol2;
 
     for (;;) {
@@ -273,13 +276,14 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         }
 
         if (lane == 0 && args.counters) {
-            atomicAdd(args.counters + 2, 1ull);
-            atomicAdd(args.counters + 0, (unsigned long long)pits);
-            atomicAdd(args.counters + 1, (unsigned long long)riters);
-            atomicAdd(args.counters + 3, (unsigned long long)rupdates);
-            atomicAdd(args.counters + 4, (unsigned long long)revals);
-            atomicAdd(args.counters + 7, (unsigned long long)rnewton);
-            atomicAdd(args.counters + 8, (unsigned long long)rfallback);
+            unsigned long long* c = sh_stat[wid];
+            c[2] += 1ull;
+            c[0] += (unsigned long long)pits;
+            c[1] += (unsigned long long)riters;
+            c[3] += (unsigned long long)rupdates;
+            c[4] += (unsigned long long)revals;
+            c[7] += (unsigned long long)rnewton;
+            c[8] += (unsigned long long)rfallback;
         }
 
         // ---- store the three maps ------------------------------------------------------------------
@@ -310,6 +314,8 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
             if (status) status[o] = st;
         }
     }
+    __syncwarp();
+    if (args.counters && lane < kStatSlots && sh_stat[wid][lane]) atomicAdd(args.counters + lane, sh_stat[wid][lane]);
 }
 
 }  // namespace rmusic
