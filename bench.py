@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -52,8 +53,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-rows", type=int, default=64,
-                    help="rows per frame in the oracle sample (about 20 s of CPU work on 16 cores)")
+    ap.add_argument("--cpu-rows", type=int, default=512,
+                    help="rows per frame in the oracle sample (about 10 s on 16 cores); an eighth of "
+                         "them, of one frame, for the one-core figure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--square-steps", type=int, default=5,
                     help="timed steps of the paper-geometry leg (square block, both derivatives and alpha)")
@@ -89,9 +91,9 @@ def aberth_flops(L: int, evals: float, updates: float) -> float:
 
 def newton_flops(L: int) -> float:
     """One Newton step of the signal root (degree 2L - 2): Horner for Q and Q' (16 per step), the
-    Newton ratio, the mirror, the deflated correction (three complex divisions, 11 each), the
-    update and the fold (6) and the tests (4)."""
-    return 16 * (2 * L - 2) + 4 + 3 * 11 + 6 + 4
+    residual (4), the mirror and D = z - 1/conj(z) (8), Q D and Q' D - Q (14), one complex division
+    (11), the update and the fold (6) and the tests (4)."""
+    return 16 * (2 * L - 2) + 4 + 8 + 14 + 11 + 6 + 4
 
 
 def schur_cohn_flops(L: int) -> float:
@@ -117,7 +119,8 @@ def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float,
       polynomial  u = Q x (2 L), rho_k (8 flops per term), scaling and moduli
       roots       Newton steps (newton_flops), the Schur-Cohn certificate (schur_cohn_flops); Aberth
                   fallback: aberth_flops per executed evaluation and update, starting points, selection
-      polish      two Horner passes of Q, Q', Q'' (24 per step) and the step (20), angle (20)
+      polish      two Horner passes of Q and Q' (16 per step) and the deflated step (37), angle (20);
+                  warps holding a split double root also form Q'' (not counted: rare on noisy frames)
     """
     NS = L * (L + 1) // 2
     NR = 2 * L - 2
@@ -131,7 +134,7 @@ def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float,
     coef = 2 * L + 3 * L + 4 * L * (L - 1) + 5 * (L - 1)
     roots = newton * newton_flops(L) + schur_cohn_flops(L)
     aberth = aberth_flops(L, evals, updates) + root_fallback * (NI * 10 + 20 + 13 * NI)
-    polish = 2 * (24 * NR + 20) + 20
+    polish = 2 * (16 * NR + 37) + 20
     return cov + power + jac + inv + coef + roots + aberth + polish
 
 
@@ -145,7 +148,7 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
       polynomials per axis: |u|^2 (3 M), M (M - 1) / 2 lag products (8), scaling and moduli (8 per lag)
       roots       Newton steps (newton_flops) and per axis the Schur-Cohn certificate; Aberth fallback:
                   aberth_flops, starting points (10 per root + 20) and selection (13 per root)
-      polish      per axis two polish steps (24 per Horner step of degree 2M - 2, plus 20), angle (20)
+      polish      per axis two polish steps (16 per Horner step of degree 2M - 2, plus 37), angle (20)
       alpha       four sincos (80), the recurrences (6 M), M^2 complex multiply-adds, M row terms
                   (16 M), angle and carrier phase (25)
     """
@@ -155,7 +158,7 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
     coefs = 2 * (3 * M + 4 * M * (M - 1) + 8 * (M - 1))
     roots = newton * newton_flops(M) + 2 * schur_cohn_flops(M)
     aberth = aberth_flops(M, evals, updates) + root_fallback * (10 * NI + 20 + 13 * NI)
-    select = 2 * (2 * (24 * NR + 20) + 20)
+    select = 2 * (2 * (16 * NR + 37) + 20)
     alpha = 80 + 6 * M + 8 * M * M + 16 * M + 25
     return power + coefs + roots + aberth + select + alpha
 
@@ -269,7 +272,7 @@ def max_over_ranks(world, v: float) -> float:
 # ----------------------------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the workload
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(frames, rows_per_frame: int):
+def oracle_sample(frames, rows_per_frame: int, nthreads: int = 0):
     import oracle as O
 
     p = O.make_params(N_WIN, L_COV, 1, 0, 0, F0)
@@ -282,7 +285,7 @@ def oracle_sample(frames, rows_per_frame: int):
         rows = np.sort(rng.choice(H, rows_per_frame, replace=False))
         ys = np.repeat(rows, W).astype(np.int32)
         xs = np.tile(np.arange(W), rows_per_frame).astype(np.int32)
-        vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
+        vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs, nthreads)
         samples.append((ys, xs, vals, st))
         npx += ys.size
     dt = time.perf_counter() - t0
@@ -372,6 +375,9 @@ def run_ours(args):
     step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
     step_ms_max = max_over_ranks(world, step_ms)
     value = npx * world / (step_ms_max * 1e3)
+    # pixels whose window lies inside the frame: W - N + 1 positions per row (the others are
+    # border pixels, NaN with status "border")
+    npx_valid = len(frames) * H * (W - N_WIN + 1)
     result_gpu = out.view(len(frames), H, W).cpu().numpy()
     # every solver variant on the same frames (register caps and the warp-per-matrix schedule of
     # the eigenvalue sweeps), outside the timed region: the autotuner's choice, shown
@@ -451,7 +457,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "valid_value": npx_valid * world / (step_ms_max * 1e3),
             "config": {"workload": WORKLOAD, "frames_per_step": len(frames), "pixels_per_step": npx,
+                       "valid_pixels_per_step": npx_valid,
                        "l2": "flushed between steps (256 MiB write)", "cuda_graph": True,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
@@ -467,9 +475,17 @@ def run_ours(args):
     # ---- CPU oracle on a bounded sample, and the GPU error against it -----------------------
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         samples, n_or, dt, cores = oracle_sample(frames, args.cpu_rows)
+        # the same oracle on one core (the paper's sequential baseline), on a smaller sample
+        rows1 = max(1, args.cpu_rows // 8)
+        _, n1, dt1, _ = oracle_sample(frames[:1], rows1, nthreads=1)
         line["cpu_baseline"] = {"value": n_or / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{args.cpu_rows} random full rows of each frame ({n_or} px), "
-                                          f"{dt:.1f} s wall"}
+                                          f"{dt:.1f} s wall",
+                                "per_core": n_or / dt / 1e6 / max(cores, 1),
+                                "one_core": {"value": n1 / dt1 / 1e6, "unit": "Mpixel/s",
+                                             "sample": f"{rows1} random full rows of the 40 dB frame ({n1} px), "
+                                                       f"{dt1:.1f} s wall"},
+                                "host": f"{platform.machine()}, {os.cpu_count()} logical CPUs"}
         acc = {}
         for snr, fr, g, (ys, xs, vals, st) in zip(SNRS, frames, result_gpu, samples):
             gv = g[ys, xs].astype(np.float64)

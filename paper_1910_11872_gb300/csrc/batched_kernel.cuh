@@ -535,12 +535,14 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
 #pragma unroll
         for (int i = 0; i < L; ++i) tr += S[tri(i, i, L)];
         const bool nonzero = valid && tr > 0.f && isfinite(tr);
-        const float itr = nonzero ? frcp(tr) : 0.f;
+        const float itr = frcp(tr);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) S[i] = nonzero ? S[i] * itr : 0.f;
-        if (!nonzero) {
+        for (int i = 0; i < NS; ++i) S[i] *= itr;
+        if (!nonzero) {  // border or empty windows: any well-separated stand-in
 #pragma unroll
-            for (int i = 0; i < L; ++i) S[tri(i, i, L)] = (float)(L - i);  // any well-separated stand-in
+            for (int i = 0; i < NS; ++i) S[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < L; ++i) S[tri(i, i, L)] = (float)(L - i);
         }
 
         // ---- signal eigenvector of S ------------------------------------------------------------------

@@ -271,6 +271,15 @@ __device__ __forceinline__ void nearest_pair(const cx<float> (&z)[L - 1], const 
     found = best >= 0;
 }
 
+// The Newton step on Q with the root's mirror 1/conj(z) divided out -- the one-term Aberth
+// correction N / (1 - N / D), N = Q / Q', D = z - 1/conj(z) -- written with one complex division:
+// N / (1 - N / D) = Q D / (Q' D - Q). At a critical point of Q (Q' = 0) it is the limit -D.
+__device__ __forceinline__ cx<float> mirror_newton_step(cx<float> z, cx<float> p, cx<float> dp) {
+    const cx<float> D = z - frcp(norm2(z)) * z;  // z - 1/conj(z)
+    const cx<float> pD = p * D;
+    return cdivf(pD, dp * D - p);
+}
+
 // Two FP32 refinement steps of the selected root zs: on Q' from the midpoint of zs and its
 // nearest root zn when the two form a split double root (cluster), otherwise Newton on Q with the
 // partner 1/conj(z) divided out.
@@ -281,17 +290,36 @@ __device__ __forceinline__ cx<float> polish_root(const cx<float>* c, cx<float> z
     for (int it = 0; it < 2; ++it) {
         cx<float> p, d1, d2;
         horner_pdd<L>(c, zz, p, d1, d2);
-        cx<float> stp;
-        if (cluster) {
-            stp = cdivf(d1, d2);
-        } else {
-            const float in2 = frcp(norm2(zz));
-            const cx<float> dzp = zz - in2 * zz;  // z - 1/conj(z)
-            stp = cdivf(p, d1 - cdivf(p, dzp));
-        }
+        const cx<float> stp = cluster ? cdivf(d1, d2) : mirror_newton_step(zz, p, d1);
         if (isfinite(stp.r) && isfinite(stp.i)) zz = zz - stp;
     }
     return zz;
+}
+
+// polish_root for an isolated root only: the same two steps without Q'' (Horner on Q and Q'
+// alone gives the same Q and Q' bit for bit, so the result equals polish_root's).
+template <int L>
+__device__ __forceinline__ cx<float> polish_isolated(const cx<float>* c, cx<float> zz) {
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+        cx<float> p, d1;
+        horner_pd<L>(c, zz, p, d1);
+        const cx<float> stp = mirror_newton_step(zz, p, d1);
+        if (isfinite(stp.r) && isfinite(stp.i)) zz = zz - stp;
+    }
+    return zz;
+}
+
+// polish_root out of line, for warps where some lane holds a split double root (rare on noisy
+// frames): the second derivative it needs then stays out of the certified path's code and
+// registers. Takes the caller's copy of the coefficients, made inside the branch.
+template <int L>
+__device__ __noinline__ void polish_cold(const cx<float>* c_in, cx<float> zs, cx<float> zn, bool cluster,
+                                         cx<float>* out) {
+    cx<float> c[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) c[i] = c_in[i];
+    *out = polish_root<L>(c, zs, zn, cluster);
 }
 
 // The selected root (Algorithm 1) after inner_roots, refined by polish_root.
@@ -305,7 +333,7 @@ __device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<fl
 }
 
 // Signal root of Q by Newton's method with the root's mirror divided out -- the one-term
-// Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' -- from the estimator's
+// Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' (mirror_newton_step) -- from the estimator's
 // start 0.99 exp(j arg conj(rho_1)) (the start inner_roots gives the signal root). A step that
 // leaves the disk is folded back onto the mirror. A lane stops when |Q| is at the FP32 rounding
 // level (the step is then not taken, as in inner_roots) or the step is below 1e-3 (the root is then
@@ -326,9 +354,7 @@ __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, floa
         cx<float> p, dp;
         horner_pd<L>(c, z, p, dp);
         ++steps;
-        const cx<float> Ni = cdivf(p, dp);
-        const cx<float> m = frcp(norm2(z)) * z;  // 1/conj(z)
-        const cx<float> w = cdivf(Ni, mkc(1.f, 0.f) - cdivf(Ni, z - m));
+        const cx<float> w = mirror_newton_step(z, p, dp);
         const bool small = norm2(p) <= res_lim2;
         const bool fin = isfinite(w.r) && isfinite(w.i);
         if (!conv && !small && fin) {
@@ -471,7 +497,15 @@ __device__ __forceinline__ cx<float> signal_root(const cx<float>* c, float res_l
         }
     }
     cluster = norm2(zn - zs) < 4e-3f * 4e-3f;
-    return polish_root<L>(c, zs, zn, cluster);
+    if (__any_sync(kFull, cluster)) {
+        cx<float> cl[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) cl[i] = c[i];
+        cx<float> zp;
+        polish_cold<L>(cl, zs, zn, cluster, &zp);
+        return zp;
+    }
+    return polish_isolated<L>(c, zs);
 }
 
 // One more refinement step of the selected root in FP64; returns arg z in double.
