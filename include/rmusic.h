@@ -269,9 +269,11 @@ int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_fram
 /* Batched path: pin the solver variant this context uses for covariance order `order` (row
  * geometry) or half-width `order` (square geometry), overriding the autotuner's choice; -1 returns
  * to it. Row geometry: variants 0, 1, 2 differ only in their register cap (2, 3 ... 16 resident
- * CTAs per SM depending on L, identical arithmetic); variant 3 (L <= 8) runs the eigenvalue sweeps
- * with one warp per matrix instead of one thread per matrix (the same stopping rule; results agree
- * to FP32 rounding). Square geometry: variants 0 and 1, register caps. Useful to compare the
+ * CTAs per SM depending on L; the same source, though the compiler may fuse multiply-adds
+ * differently in each, so maps agree to FP32 rounding and statuses are identical); variant 3
+ * (L <= 8) runs the eigenvalue sweeps with one warp per matrix instead of one thread per matrix
+ * (the same stopping rule; results agree to FP32 rounding). Each variant is deterministic: a
+ * pixel's result does not depend on the frames batched with it or on the schedule. Square geometry: variants 0 and 1, register caps. Useful to compare the
  * schedules on a given GPU. Errors: RMUSIC_EINVAL (bad order or variant), RMUSIC_EUNSUPPORTED
  * (not the batched path). */
 int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant);

@@ -124,7 +124,8 @@ __device__ __forceinline__ float music_coefs(const cx<float>* u, cx<float>* c) {
 #pragma unroll
         for (int m = 0; m + k < L; ++m) rho = rho + mulc(u[m], u[m + k]);
         c[k] = (-inu2) * rho;
-        qsum += 2.f * sqrtf(norm2(c[k]));
+        const float n2 = norm2(c[k]);
+        qsum += n2 > 0.f ? 2.f * n2 * rsqrtf(n2) : 0.f;  // 2 |c_k| (a bound: approximate is fine)
     }
     return (3e-6f * qsum) * (3e-6f * qsum);
 }
@@ -338,9 +339,9 @@ __device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<fl
 // leaves the disk is folded back onto the mirror. A lane stops when |Q| is at the FP32 rounding
 // level (the step is then not taken, as in inner_roots) or the step is below 1e-3 (the root is then
 // known to ~1e-6, far inside the certificate's 0.02 margin, and the two polish steps that follow
-// converge quadratically from there); the warp stops
-// when every lane has or after max_iters steps (conv false for the lanes still moving). Inactive
-// lanes (pixels without a result) count as stopped from the start.
+// converge quadratically from there); the warp stops when every lane has or after max_iters steps
+// (conv false for the lanes still moving). Inactive lanes (pixels without a result) count as
+// stopped from the start.
 template <int L>
 __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, float res_lim2, int max_iters,
                                                         bool active, bool& conv, int& steps) {
@@ -373,9 +374,11 @@ __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, floa
 // P1(z) = (P(z) - g P*(z)) / z has degree n - 1, and Rouche's theorem on the unit circle (where
 // |P*| = |P|) gives N(P) = N(P1) + 1 if |P(0)| < |lead P|, else N(P) = n - 1 - N(P1). Returns -1
 // when some |P(0)|^2 is within 2e-4 of |lead P|^2 (relative), where FP32 rounding could decide
-// the comparison, or when a squared modulus leaves the FP32 range (the coefficients are not
-// rescaled between levels, which keeps this straight-line code short; on the root-MUSIC
-// polynomials with r > 0.48 their magnitudes stay within 2^+-40).
+// the comparison, or when |lead P|^2 is zero, infinite or NaN (the coefficients are not rescaled
+// between levels, which keeps this straight-line code short; on the root-MUSIC polynomials with
+// r > 0.48 their magnitudes stay within 2^+-40). One test covers all of these: with la = |lead P|^2
+// infinite or NaN, |la - l0| > 2e-4 la is false; with l0 = |P(0)|^2 infinite and la finite the
+// comparison l0 < la is still decided correctly, and a NaN l0 fails the test.
 template <int L>
 __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
     constexpr int n = 2 * L - 2;
@@ -393,7 +396,7 @@ __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
 #pragma unroll
     for (int deg = n; deg >= 1; --deg) {
         const float la = norm2(a[deg]), l0 = norm2(a[0]);
-        ok = ok && la > 0.f && la < 3e38f && l0 < 3e38f && fabsf(la - l0) > 2e-4f * la;
+        ok = ok && la > 0.f && fabsf(la - l0) > 2e-4f * la;
         if (l0 < la) inside |= 1ull << deg;
         const cx<float> g = frcp(la) * (a[0] * a[deg]);  // a0 / conj(a_deg)
         cx<float> b[n];
@@ -453,7 +456,9 @@ struct RootStats {
 // |z| < r - 0.02 (roots_inside). Lanes without that certificate -- and with them the whole warp,
 // which executes the loop together -- take every inner root from inner_roots and select among
 // them (nearest_pair). Both end in polish_root; a selected root whose nearest other root is
-// closer than 4e-3 is a split double root (cluster). exhaustive (uniform over the launch) skips the
+// closer than 4e-3 is a split double root (cluster). (The polish also lands a certified root on
+// the FP32 fixed point of the iteration: Newton's own last step, stopped at the rounding level of
+// the residual, leaves up to ~3e-5 rad on noisy windows.) exhaustive (uniform over the launch) skips the
 // Newton root and its certificate: every lane takes the full root finder. Inactive lanes (border or
 // degenerate pixels, whose result is not used) neither hold the warp in Newton's loop nor send it
 // to the full root finder.

@@ -459,10 +459,12 @@ def test_autotune_variants_identical_and_cached(tmp_path, monkeypatch):
 
 @pytest.mark.parametrize("L", [4, 6, 8])
 def test_solver_variants_and_warp_per_matrix_schedule(L):
-    """Variants 0-2 (register caps) compute identical maps; variant 3 runs the eigenvalue sweeps with
-    one warp per matrix followed by inverse iteration, the others the power iteration, which stops at a
-    1e-6 step: the two eigenvectors agree to ~1e-6, which small L (a flat pseudospectrum minimum)
-    magnifies to ~1e-5 rad/px in the angle. Statuses are identical."""
+    """Variants 0-2 (register caps) run the same source; the compiler's instruction selection (which
+    multiply-adds it fuses) may differ between them, so their maps agree to the FP32 rounding of the
+    estimator, which small L (a flat pseudospectrum minimum) magnifies to ~1e-5 rad/px in the angle.
+    Variant 3 runs the eigenvalue sweeps with one warp per matrix followed by inverse iteration, the
+    others the power iteration, which stops at a 1e-6 step: the two eigenvectors agree to ~1e-6, with
+    the same magnification. Statuses are identical throughout."""
     torch = _torch()
     frames = [synth.peaks_frame(10, 0.1, H=40, W=256).image, synth.peaks_frame(np.inf, 0.1, H=24, W=256).image]
     x = torch.from_numpy(np.concatenate([f.ravel() for f in frames])).cuda()
@@ -483,7 +485,10 @@ def test_solver_variants_and_warp_per_matrix_schedule(L):
     finally:
         dem.close()
     for v in (0, 2):
-        assert np.array_equal(maps[v][0], maps[1][0], equal_nan=True) and np.array_equal(maps[v][1], maps[1][1])
+        assert np.array_equal(maps[v][1], maps[1][1])
+        ok = maps[1][1] == 0
+        assert np.array_equal(np.isnan(maps[v][0]), np.isnan(maps[1][0]))
+        assert np.abs(maps[v][0][ok] - maps[1][0][ok]).max() <= 3e-5
     g, gs = maps[3]
     assert np.array_equal(gs, maps[1][1])
     ok = gs == 0
