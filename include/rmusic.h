@@ -211,6 +211,21 @@ int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic
 int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int32_t n_frames,
                     float* d_out, uint8_t* d_status, void* cuda_stream);
 
+/* Pre-allocate the context's device workspace for calls of up to max_pixels pixels in total
+ * (sum of height x width over the call's frames) and up to max_frames frames: the analytic-signal
+ * buffer (8 bytes per pixel, 16 on the plain FP64 path), the frame tables (device and pinned
+ * host) and, with unwrap = 1, the phase-assembly workspace. A later call within these limits
+ * allocates nothing, so it never waits for the device as a buffer that grows does (freeing
+ * device memory synchronises the device): what a serving loop or a real-time caller needs.
+ * Without it the workspace grows on demand. The reservation counts against the context's HBM
+ * budget and is kept until rmusic_destroy. Synchronises the device when it replaces a smaller
+ * buffer. Errors: RMUSIC_EINVAL (NULL context, max_frames < 0, max_pixels >= 2^31 with
+ * unwrap = 1), RMUSIC_ENOMEM (the reservation exceeds the budget: nothing changes; or the device
+ * is out of memory: the buffer being replaced is gone and later calls allocate on demand).
+ * max_pixels = 0 or max_frames = 0 reserves nothing of that kind.
+ * The paper has no counterpart: this is a property of the GPU implementation. */
+int rmusic_reserve(rmusic_ctx* ctx, uint64_t max_pixels, int32_t max_frames);
+
 /* Same as rmusic_demodulate_frames, but every buffer is in HOST memory; the maps are complete when
  * the call returns (it synchronises its stream). in_bytes is the size of h_frames. Buffers the GPU
  * can address directly (pinned memory from cudaHostAlloc / cudaMallocHost, or registered with

@@ -835,8 +835,10 @@ int demodulate_impl(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
         pixels += (uint64_t)F.H * (uint64_t)F.W;
     }
     RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, kStatSlots * sizeof(unsigned long long), s));
-    // group frames so that each group's analytic signal fits the budget
-    const uint64_t table_reserve = 64 * sizeof(FrameDev) + (uint64_t)n_frames * sizeof(FrameDev);
+    // group frames so that each group's analytic signal fits the budget (with room for the frame
+    // table when the one held is too small for this call)
+    const uint64_t table_reserve =
+        ctx->table_cap >= (size_t)n_frames ? 0 : 64 * sizeof(FrameDev) + (uint64_t)n_frames * sizeof(FrameDev);
     uint64_t avail = 0;
     if (ctx->budget) {
         const uint64_t fixed = ctx->held - ctx->gamma_cap + table_reserve;
@@ -876,6 +878,20 @@ int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
                     float* d_out, uint8_t* d_status, void* cuda_stream) {
     if (ctx && ctx->p.precision != RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
     return demodulate_impl(ctx, d_frames, descs, n_frames, d_out, d_status, cuda_stream, true);
+}
+
+int rmusic_reserve(rmusic_ctx* ctx, uint64_t max_pixels, int32_t max_frames) {
+    if (!ctx || max_frames < 0) return RMUSIC_EINVAL;
+    if (ctx->p.unwrap && max_pixels >= (1ull << 31)) return RMUSIC_EINVAL;
+    DeviceGuard guard(ctx->device);
+    int rc = RMUSIC_OK;
+    if (max_frames > 0) rc = ensure_tables(ctx, (size_t)max_frames);
+    if (!rc && max_pixels > 0) rc = ensure(ctx, &ctx->d_gamma, &ctx->gamma_cap, max_pixels * gamma_elem_bytes(ctx));
+    if (!rc && max_pixels > 0 && ctx->p.unwrap)
+        rc = ensure(ctx, &ctx->d_unwrap, &ctx->unwrap_cap,
+                    unwrap_workspace_bytes((int64_t)max_pixels, (int64_t)max_pixels));
+    ctx->stats.workspace_bytes = ctx->held;
+    return rc;
 }
 
 }  // extern "C"

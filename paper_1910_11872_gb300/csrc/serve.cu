@@ -271,6 +271,9 @@ int rmusic_serve_create(const rmusic_params* params, int device, const rmusic_se
             break;
         }
         rc = rmusic_create(&s->params, device, ws, &b.ctx);
+        // the whole workspace a batch can need, now: a workspace that grew during serving would
+        // free device memory, which synchronises the device and stalls every batch in flight
+        if (!rc) rc = rmusic_reserve(b.ctx, cfg->max_batch_pixels, cfg->max_batch_frames);
         s->device_bytes += ws;
     }
     if (prev >= 0) cudaSetDevice(prev);

@@ -144,6 +144,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_demodulate_frames_noalloc.restype = ctypes.c_int
         lib.rmusic_autotune.argtypes = [vp, vp, ctypes.POINTER(rmusic_frame_desc), i32, vp, vp, vp]
         lib.rmusic_autotune.restype = ctypes.c_int
+        lib.rmusic_reserve.argtypes = [vp, ctypes.c_uint64, i32]
+        lib.rmusic_reserve.restype = ctypes.c_int
         lib.rmusic_destroy.argtypes = [vp]
         lib.rmusic_destroy.restype = None
         lib.rmusic_strerror.argtypes = [ctypes.c_int]
@@ -217,6 +219,13 @@ def rmusic_demodulate_frames_noalloc(params: rmusic_params, device: int, d_frame
                                                          cuda_stream or None)
     if rc != RMUSIC_OK:
         raise RmusicError(rc, "rmusic_demodulate_frames_noalloc")
+    return rc
+
+
+def rmusic_reserve(ctx, max_pixels: int, max_frames: int) -> int:
+    rc = load_library().rmusic_reserve(ctx, int(max_pixels), int(max_frames))
+    if rc != RMUSIC_OK:
+        raise RmusicError(rc, "rmusic_reserve", rmusic_last_cuda_error(ctx))
     return rc
 
 
@@ -321,6 +330,10 @@ class Demodulator:
 
     def stats(self) -> rmusic_stats:
         return rmusic_get_stats(self.ctx)
+
+    def reserve(self, max_pixels: int, max_frames: int) -> None:
+        """Pre-allocate the workspace for calls of up to max_pixels pixels in max_frames frames."""
+        rmusic_reserve(self.ctx, max_pixels, max_frames)
 
     def run(self, frames, windows=None, with_status: bool = True, stream=None, out=None, status=None):
         import torch

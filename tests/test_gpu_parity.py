@@ -305,6 +305,38 @@ def test_hbm_budget_splits_batches_and_rejects_oversize():
         dem.close()
 
 
+def test_reserve_allocates_once_and_respects_the_budget():
+    """rmusic_reserve sizes the workspace for calls of up to (max_pixels, max_frames) in advance:
+    later calls within the limits leave the workspace as it is (no allocation, hence no device
+    synchronisation), their maps equal an unreserved context's, and a reservation over the budget
+    is refused with ENOMEM and changes nothing."""
+    frames = [synth.peaks_frame(20, 0.1, H=32 + 16 * i, W=128, stream=i).image for i in range(4)]
+    ref = run_gpu(frames)
+    total = sum(f.size for f in frames)
+    torch = _torch()
+    # room for the analytic signal of all four frames, the frame tables and the counters, not for
+    # twice the pixels
+    dem = rmusic.Demodulator(hbm_budget_bytes=8 * total + (64 << 10))
+    try:
+        dem.reserve(total, 8)
+        held = dem.stats().workspace_bytes
+        assert held >= 8 * total
+        for k in range(1, 5):  # growing calls: 1, 2, 3, then all 4 frames
+            out, st, _ = dem.run([_to_dev(f) for f in frames[:k]])
+            torch.cuda.synchronize()
+            assert dem.stats().workspace_bytes == held, k
+        assert np.array_equal(out.cpu().numpy(), np.concatenate([g.ravel() for g, _ in ref]), equal_nan=True)
+        with pytest.raises(rmusic.RmusicError) as e:
+            dem.reserve(2 * total, 8)
+        assert e.value.code == rmusic.RMUSIC_ENOMEM
+        assert dem.stats().workspace_bytes == held
+        with pytest.raises(rmusic.RmusicError) as e:
+            rmusic.rmusic_reserve(dem.ctx, 16, -1)
+        assert e.value.code == rmusic.RMUSIC_EINVAL
+    finally:
+        dem.close()
+
+
 def test_invalid_descriptors_rejected():
     torch = _torch()
     dem = rmusic.Demodulator()
