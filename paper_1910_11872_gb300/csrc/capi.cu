@@ -73,7 +73,8 @@ struct GraphEntry {
     FrameDev* h_table = nullptr;  // pinned; read by the graph's upload node at every replay
     int launches = 0;
     uint64_t stamp = 0;
-    std::vector<int> a1_ev, solver_ev;  // timing event indices recorded by the graph
+    std::vector<cudaEvent_t> a1_ev, solver_ev;  // timing events recorded by the graph
+    std::vector<cudaEvent_t> owned;              // every event the graph records (it owns them)
 };
 
 }  // namespace
@@ -109,9 +110,11 @@ struct rmusic_ctx {
     cudaStream_t cap_stream = nullptr;  // graphs are captured here, then launched on the caller's stream
     // statistics and timing
     cudaEvent_t call_done = nullptr;
-    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_pool;  // events recorded directly by calls (reused call after call)
     int ev_used = 0;
-    std::vector<int> a1_ev, solver_ev;  // pairs of event indices of the last call
+    std::vector<cudaEvent_t> gev_free;                  // events released by dropped graphs
+    std::vector<cudaEvent_t>* capture_owned = nullptr;  // the graph being captured takes its events here
+    std::vector<cudaEvent_t> a1_ev, solver_ev;          // pairs of events of the last call
     uint64_t last_pixels = 0;
     // bookkeeping
     size_t held = 0;
@@ -160,6 +163,15 @@ bool params_ok(const rmusic_params& p) {
     return true;
 }
 
+// Release a cached graph: its executable, its pinned frame table, and its timing events (kept for
+// later captures).
+void drop_graph(rmusic_ctx* ctx, GraphEntry& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.h_table) cudaFreeHost(g.h_table);
+    ctx->gev_free.insert(ctx->gev_free.end(), g.owned.begin(), g.owned.end());
+    g = GraphEntry{};
+}
+
 // Grow a device buffer to at least `bytes` (never shrinks). Keeps the budget.
 int ensure(rmusic_ctx* ctx, void** ptr, size_t* cap_bytes, size_t bytes) {
     if (*cap_bytes >= bytes) return RMUSIC_OK;
@@ -186,11 +198,7 @@ int ensure(rmusic_ctx* ctx, void** ptr, size_t* cap_bytes, size_t bytes) {
     *cap_bytes = want;
     ctx->held += want;
     // any cached graph may reference the old buffer
-    for (auto& g : ctx->graphs) {
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        if (g.h_table) cudaFreeHost(g.h_table);
-        g = GraphEntry{};
-    }
+    for (auto& g : ctx->graphs) drop_graph(ctx, g);
     return RMUSIC_OK;
 }
 
@@ -331,25 +339,36 @@ int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Pla
 }
 
 // Queue the work of one plan (whose frame table has just been copied to d_table) on `s`.
-// Record a timing event on s (an event-record node when s is capturing). Returns its index or -1.
-int stamp(rmusic_ctx* ctx, cudaStream_t s) {
-    if (!ctx->p.timing) return -1;
-    if (ctx->ev_used >= (int)ctx->ev_pool.size()) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return -1;
-        ctx->ev_pool.push_back(e);
-    }
-    cudaEvent_t e = ctx->ev_pool[ctx->ev_used];
+// Record a timing event on s (an event-record node when s is capturing). Returns it, or nullptr
+// without timing. A graph being captured owns the events it records (taken from the released ones
+// or created), so no later call or capture records into them while the graph is cached.
+cudaEvent_t stamp(rmusic_ctx* ctx, cudaStream_t s) {
+    if (!ctx->p.timing) return nullptr;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
-    cudaError_t r = cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
-                                                       : cudaEventRecord(e, s);
-    if (r != cudaSuccess) return -1;
-    return ctx->ev_used++;
+    const bool capturing = cs == cudaStreamCaptureStatusActive;
+    cudaEvent_t e = nullptr;
+    if (capturing) {
+        if (!ctx->gev_free.empty()) {
+            e = ctx->gev_free.back();
+            ctx->gev_free.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            return nullptr;
+        }
+        if (ctx->capture_owned) ctx->capture_owned->push_back(e);
+    } else {
+        if (ctx->ev_used >= (int)ctx->ev_pool.size()) {
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ctx->ev_pool.push_back(e);
+        }
+        e = ctx->ev_pool[ctx->ev_used++];
+    }
+    const cudaError_t r = capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+    return r == cudaSuccess ? e : nullptr;
 }
 
-void stamp_pair(std::vector<int>& v, int a, int b) {
-    if (a >= 0 && b >= 0) {
+void stamp_pair(std::vector<cudaEvent_t>& v, cudaEvent_t a, cudaEvent_t b) {
+    if (a && b) {
         v.push_back(a);
         v.push_back(b);
     }
@@ -556,7 +575,7 @@ struct NvtxRange {
 int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_out, uint8_t* d_status,
             cudaStream_t s, int* launches) {
     const int n = (int)plan.frames.size();
-    int e0 = stamp(ctx, s);
+    cudaEvent_t e0 = stamp(ctx, s);
     const bool fp64 = ctx->p.precision == RMUSIC_PLAIN_FP64;
     {
         NvtxRange r("rmusic.bandpass");
@@ -576,7 +595,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
             const int v = solver_variant(ctx, L);
             NvtxRange r("rmusic.solver");
             RM_CUDA(cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s));
-            int e1 = stamp(ctx, s);
+            cudaEvent_t e1 = stamp(ctx, s);
             RM_CUDA(launch_solver(ctx, plan, g, v, d_out, d_status, ctx->d_counters + kStatSlot, s));
             stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
             ctx->stats.solver_ctas_per_sm = solver_ctas(L, v);
@@ -598,7 +617,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         a.max_sweeps = p.max_sweeps ? p.max_sweeps : 30;
         a.max_iters = p.max_root_iters ? p.max_root_iters : 500;
         NvtxRange r("rmusic.plain");
-        int e1 = stamp(ctx, s);
+        cudaEvent_t e1 = stamp(ctx, s);
         for (int f = 0; f < n; ++f) {
             if (p.precision == RMUSIC_PLAIN_FP64)
                 RM_CUDA(launch_plain_fp64(ctx->d_table + f, plan.frames[f], static_cast<const double2*>(ctx->d_gamma),
@@ -674,11 +693,7 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
                                          ctx->d_gamma, false, s));
             rc = tune_plan(ctx, plan, d_out, d_status, s, force_tune);
             if (rc) return rc;
-            for (auto& g : ctx->graphs) {  // captured graphs may hold the previous variants
-                if (g.exec) cudaGraphExecDestroy(g.exec);
-                if (g.h_table) cudaFreeHost(g.h_table);
-                g = GraphEntry{};
-            }
+            for (auto& g : ctx->graphs) drop_graph(ctx, g);  // captured graphs may hold the previous variants
         }
     }
 
@@ -722,9 +737,7 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
     GraphEntry* slot = &ctx->graphs[0];
     for (auto& g : ctx->graphs)
         if (!g.exec || g.stamp < slot->stamp) slot = &g;
-    if (slot->exec) cudaGraphExecDestroy(slot->exec);
-    if (slot->h_table) cudaFreeHost(slot->h_table);
-    *slot = GraphEntry{};
+    drop_graph(ctx, *slot);
     if (cudaMallocHost(&slot->h_table, plan.frames.size() * sizeof(FrameDev)) != cudaSuccess) {
         slot->h_table = nullptr;
         return RMUSIC_ENOMEM;
@@ -736,10 +749,12 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
     // runs during capture, the graph is launched on the caller's stream below
     cudaStream_t cs = ctx->cap_stream;
     RM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    ctx->capture_owned = &slot->owned;
     cudaError_t ce = cudaMemcpyAsync(ctx->d_table, slot->h_table, plan.frames.size() * sizeof(FrameDev),
                                      cudaMemcpyHostToDevice, cs);
     int erc = ce == cudaSuccess ? enqueue(ctx, plan, d_frames, d_out, d_status, cs, &launches) : RMUSIC_ECUDA;
     cudaError_t ee = cudaStreamEndCapture(cs, &graph_def);
+    ctx->capture_owned = nullptr;
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaMemcpyAsync (capture)");
     if (erc) {
         if (graph_def) cudaGraphDestroy(graph_def);
@@ -987,11 +1002,7 @@ int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant) {
     if (order < 1 || key < 0 || key >= kKeys || !solver_supports(key)) return RMUSIC_EINVAL;
     if (variant < -1 || variant >= solver_num_variants(key)) return RMUSIC_EINVAL;
     ctx->variant_by_L[key] = variant;
-    for (auto& g : ctx->graphs) {  // captured graphs hold the previous variant
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        if (g.h_table) cudaFreeHost(g.h_table);
-        g = GraphEntry{};
-    }
+    for (auto& g : ctx->graphs) drop_graph(ctx, g);  // captured graphs hold the previous variant
     return RMUSIC_OK;
 }
 
@@ -1037,10 +1048,8 @@ void rmusic_destroy(rmusic_ctx* ctx) {
     {
         DeviceGuard guard(ctx->device);
         cudaDeviceSynchronize();
-        for (auto& g : ctx->graphs) {
-            if (g.exec) cudaGraphExecDestroy(g.exec);
-            if (g.h_table) cudaFreeHost(g.h_table);
-        }
+        for (auto& g : ctx->graphs) drop_graph(ctx, g);
+        for (cudaEvent_t e : ctx->gev_free) cudaEventDestroy(e);
         if (ctx->d_gamma) cudaFree(ctx->d_gamma);
         if (ctx->d_table) cudaFree(ctx->d_table);
         if (ctx->d_counters) cudaFree(ctx->d_counters);
@@ -1091,11 +1100,11 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->eig_fallback_frac = mean(6);
     out->mean_newton_steps = mean(7);
     out->root_fallback_frac = mean(8);
-    auto sum = [&](const std::vector<int>& v) {
+    auto sum = [&](const std::vector<cudaEvent_t>& v) {
         float t = 0.f;
         for (size_t i = 0; i + 1 < v.size(); i += 2) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ctx->ev_pool[v[i]], ctx->ev_pool[v[i + 1]]) == cudaSuccess) t += ms;
+            if (cudaEventElapsedTime(&ms, v[i], v[i + 1]) == cudaSuccess) t += ms;
         }
         return t;
     };

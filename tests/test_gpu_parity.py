@@ -561,3 +561,63 @@ def test_host_entry_pinned_buffers_in_place_equal_device_entry():
         assert np.array_equal(pout[o:o + n].reshape(f.shape), g, equal_nan=True)
         assert np.array_equal(pst[o:o + n].reshape(f.shape), gs)
         o += n
+
+
+def test_host_entry_statistics_and_graph_owned_timing_events():
+    """The host entry's statistics describe its call: the pixel count, one band-pass and one solver
+    launch, the iteration means of the device entry (work items sit at the same absolute
+    positions), positive stage timers, also when the call replays a captured graph. With a budget
+    that splits a call into groups, each group's graph records its own timing events: calls that
+    capture new graphs while replaying older ones in the same call keep positive timers no larger
+    than the wall time of the call."""
+    import time
+
+    torch = _torch()
+    shapes = [(40, 256), (24, 512), (64, 128), (16, 1024), (33, 300)]
+    frames = [synth.peaks_frame(12, 0.1, H=h, W=w, stream=i).image for i, (h, w) in enumerate(shapes)]
+    flat = np.concatenate([f.ravel() for f in frames]).astype(np.float32)
+    descs, nbytes, nout = rmusic.frame_descs(shapes, rmusic.RMUSIC_DTYPE_F32, 4)
+    hin = torch.from_numpy(flat).pin_memory()
+    hout = torch.full((nout,), 7.0).pin_memory()
+    dev = run_gpu(frames)
+    ddem = rmusic.Demodulator(timing=1)
+    try:
+        ddem.run([_to_dev(f) for f in frames])
+        torch.cuda.synchronize()
+        dst = ddem.stats()
+    finally:
+        ddem.close()
+    for graph in (0, 1):
+        dem = rmusic.Demodulator(use_graph=graph, timing=1)
+        try:
+            for _ in range(2):
+                rmusic.rmusic_demodulate_frames_host(dem.ctx, hin.data_ptr(), nbytes, descs, len(frames),
+                                                     hout.data_ptr(), None, None)
+                st = dem.stats()
+                assert st.pixels == sum(h * w for h, w in shapes)
+                assert st.kernel_launches == 2
+                assert st.bandpass_ms > 0 and st.solver_ms > 0
+                assert st.mean_power_steps == dst.mean_power_steps
+                assert st.mean_newton_steps == dst.mean_newton_steps
+            assert st.graph_replayed == graph
+            o = 0
+            for f, (g, gs) in zip(frames, dev):
+                assert np.array_equal(hout.numpy()[o:o + f.size].reshape(f.shape), g, equal_nan=True)
+                o += f.size
+        finally:
+            dem.close()
+    # budget for about two frames' analytic signal: calls split into groups, one graph per group
+    dem = rmusic.Demodulator(use_graph=1, timing=1, hbm_budget_bytes=8 * 2 * 64 * 128 + (64 << 10))
+    try:
+        dframes = [_to_dev(f) for f in frames[:3]]
+        for order in ([0, 1, 2], [2, 1, 0], [0, 1, 2], [1, 2, 0]):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dem.run([dframes[i] for i in order])
+            torch.cuda.synchronize()
+            wall_ms = 1e3 * (time.perf_counter() - t0)
+            st = dem.stats()
+            assert 0 < st.bandpass_ms < wall_ms and 0 < st.solver_ms < wall_ms, (order, st.bandpass_ms,
+                                                                                st.solver_ms, wall_ms)
+    finally:
+        dem.close()
