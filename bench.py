@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--plain-steps", type=int, default=10,
+                    help="timed steps of the plain FP32 path (median reported)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-rows", type=int, default=512,
                     help="rows per frame in the oracle sample (about 10 s on 16 cores); an eighth of "
@@ -399,7 +400,8 @@ def run_ours(args):
     # ---- plain path on the same GPU (thread per pixel, one launch per frame) -------------------
     plain = rmusic.Demodulator(device=local, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0,
                                precision="plain_fp32", timing=1)
-    plain.run(x, out=out, with_status=False)
+    for _ in range(3):  # warm-up
+        plain.run(x, out=out, with_status=False)
     torch.cuda.synchronize()
     pms = []
     for _ in range(args.plain_steps):
@@ -410,7 +412,7 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize()
         pms.append(a.elapsed_time(b))
-    plain_ms = max_over_ranks(world, statistics.mean(pms))
+    plain_ms = max_over_ranks(world, statistics.median(pms))
     plain_value = npx * world / (plain_ms * 1e3)
     plain.close()
 
@@ -467,7 +469,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(npx * 4), "ms_per_step": e2e_ms, "kernels_per_step": e2e_launches},
             "gpu_launches": launches, "clocks": clk,
             "plain": {"value": plain_value, "unit": "Mpixel/s", "ms_per_step": plain_ms,
-                      "path": "plain FP32, thread per pixel, one launch per frame"},
+                      "path": "plain FP32, thread per pixel, one launch per frame",
+                      "timing": f"3 warm-ups, median of {args.plain_steps} event-timed steps, L2 flushed"},
             "speedup_vs_plain": value / plain_value}
     if sq is not None:
         line["paper_geometry"] = sq

@@ -323,16 +323,6 @@ __device__ __noinline__ void polish_cold(const cx<float>* c_in, cx<float> zs, cx
     *out = polish_root<L>(c, zs, zn, cluster);
 }
 
-// The selected root (Algorithm 1) after inner_roots, refined by polish_root.
-template <int L>
-__device__ __forceinline__ cx<float> select_root(const cx<float>* c, const cx<float> (&z)[L - 1],
-                                                 const cx<float> (&mz)[L - 1], bool& found, bool& cluster) {
-    cx<float> zs, zn;
-    nearest_pair<L>(z, mz, zs, zn, found);
-    cluster = norm2(zn - zs) < 4e-3f * 4e-3f;
-    return polish_root<L>(c, zs, zn, cluster);
-}
-
 // Signal root of Q by Newton's method with the root's mirror divided out -- the one-term
 // Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' (mirror_newton_step) -- from the estimator's
 // start 0.99 exp(j arg conj(rho_1)) (the start inner_roots gives the signal root). A step that
