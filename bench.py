@@ -106,7 +106,8 @@ def schur_cohn_flops(L: int) -> float:
 
 
 def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float, power_steps: float = 0.0,
-                    eig_fallback: float = 0.0, newton: float = 0.0, root_fallback: float = 0.0) -> float:
+                    eig_fallback: float = 0.0, newton: float = 0.0, root_fallback: float = 0.0,
+                    polish: float = 2.0) -> float:
     """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1),
     counted from the kernel's steps with the measured work per 32-pixel work item (power steps,
     Jacobi sweeps and fallbacks, Newton steps, Aberth evaluations, updates and fallbacks):
@@ -120,8 +121,9 @@ def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float,
       polynomial  u = Q x (2 L), rho_k (8 flops per term), scaling and moduli
       roots       Newton steps (newton_flops), the Schur-Cohn certificate (schur_cohn_flops); Aberth
                   fallback: aberth_flops per executed evaluation and update, starting points, selection
-      polish      two Horner passes of Q and Q' (16 per step) and the deflated step (37), angle (20);
-                  warps holding a split double root also form Q'' (not counted: rare on noisy frames)
+      polish      per measured step Horner on Q and Q' (16 per degree) and the deflated step (37);
+                  angle (20); warps holding a split double root also form Q'' (not counted: rare on
+                  noisy frames)
     """
     NS = L * (L + 1) // 2
     NR = 2 * L - 2
@@ -135,12 +137,12 @@ def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float,
     coef = 2 * L + 3 * L + 4 * L * (L - 1) + 5 * (L - 1)
     roots = newton * newton_flops(L) + schur_cohn_flops(L)
     aberth = aberth_flops(L, evals, updates) + root_fallback * (NI * 10 + 20 + 13 * NI)
-    polish = 2 * (16 * NR + 37) + 20
+    polish = polish * (16 * NR + 37) + 20
     return cov + power + jac + inv + coef + roots + aberth + polish
 
 
 def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: float, newton: float = 0.0,
-                           root_fallback: float = 0.0) -> float:
+                           root_fallback: float = 0.0, polish: float = 4.0) -> float:
     """Algorithmic FP32 flops per pixel of the square-block solver (block side M = 2 Lp + 1), from
     its steps with the measured power-iteration steps, Newton steps, Aberth evaluations, updates and
     fallbacks (the root figures add both polynomials):
@@ -149,7 +151,8 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
       polynomials per axis: |u|^2 (3 M), M (M - 1) / 2 lag products (8), scaling and moduli (8 per lag)
       roots       Newton steps (newton_flops) and per axis the Schur-Cohn certificate; Aberth fallback:
                   aberth_flops, starting points (10 per root + 20) and selection (13 per root)
-      polish      per axis two polish steps (16 per Horner step of degree 2M - 2, plus 37), angle (20)
+      polish      per measured polish step (both axes together) Horner of degree 2M - 2 (16 per
+                  degree) and the step (37); per axis the angle (20)
       alpha       four sincos (80), the recurrences (6 M), M^2 complex multiply-adds, M row terms
                   (16 M), angle and carrier phase (25)
     """
@@ -159,7 +162,7 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
     coefs = 2 * (3 * M + 4 * M * (M - 1) + 8 * (M - 1))
     roots = newton * newton_flops(M) + 2 * schur_cohn_flops(M)
     aberth = aberth_flops(M, evals, updates) + root_fallback * (10 * NI + 20 + 13 * NI)
-    select = 2 * (2 * (16 * NR + 37) + 20)
+    select = polish * (16 * NR + 37) + 2 * 20
     alpha = 80 + 6 * M + 8 * M * M + 16 * M + 25
     return power + coefs + roots + aberth + select + alpha
 
@@ -352,7 +355,7 @@ def run_ours(args):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     solver_ms, bandpass_ms, launches, sweeps, iters, updates, evals = [], [], 0, [], [], [], []
-    psteps, eigfb, newton, rootfb = [], [], [], []
+    psteps, eigfb, newton, rootfb, polish = [], [], [], [], []
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -370,6 +373,7 @@ def run_ours(args):
         eigfb.append(st.eig_fallback_frac)
         newton.append(st.mean_newton_steps)
         rootfb.append(st.root_fallback_frac)
+        polish.append(st.mean_polish_steps)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -438,7 +442,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (batched solver) ---------------------------------------
     fpp = flops_per_pixel(L_COV, N_WIN, statistics.mean(sweeps), statistics.mean(evals), statistics.mean(updates),
                           statistics.mean(psteps), statistics.mean(eigfb), statistics.mean(newton),
-                          statistics.mean(rootfb))
+                          statistics.mean(rootfb), statistics.mean(polish))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
     traffic = profiled_traffic()
@@ -448,6 +452,7 @@ def run_ours(args):
                 "peak_note": "FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (unit counts and max clock)",
                 "mean_power_steps": statistics.mean(psteps), "eig_fallback_frac": statistics.mean(eigfb),
                 "mean_jacobi_sweeps": statistics.mean(sweeps), "mean_newton_steps": statistics.mean(newton),
+                "mean_polish_steps": statistics.mean(polish),
                 "root_fallback_frac": statistics.mean(rootfb), "mean_aberth_iters": statistics.mean(iters),
                 "mean_aberth_updates": statistics.mean(updates), "mean_aberth_evals": statistics.mean(evals),
                 "solver_ctas_per_sm": st.solver_ctas_per_sm, "solver_variant": kept,
@@ -526,7 +531,7 @@ def run_square_leg(args, rank, world, dev, stream, flush):
     barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.square_steps)]
-    solver_ms, its, evals, updates, launches, newton, rootfb = [], [], [], [], 0, [], []
+    solver_ms, its, evals, updates, launches, newton, rootfb, polish = [], [], [], [], 0, [], [], []
     for k in range(args.square_steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -539,12 +544,13 @@ def run_square_leg(args, rank, world, dev, stream, flush):
         updates.append(st.mean_root_updates)
         newton.append(st.mean_newton_steps)
         rootfb.append(st.root_fallback_frac)
+        polish.append(st.mean_polish_steps)
         launches += st.kernel_launches
     torch.cuda.synchronize()
     step_ms = max_over_ranks(world, statistics.mean(a.elapsed_time(b) for a, b in ev))
     value = npx * world / (step_ms * 1e3)
     fpp = square_flops_per_pixel(SQ_LP, statistics.mean(its), statistics.mean(evals), statistics.mean(updates),
-                                 statistics.mean(newton), statistics.mean(rootfb))
+                                 statistics.mean(newton), statistics.mean(rootfb), statistics.mean(polish))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
     res = {"workload": SQ_WORKLOAD, "value": value, "unit": "Mpixel/s", "ms_per_step": step_ms,
@@ -555,6 +561,7 @@ def run_square_leg(args, rank, world, dev, stream, flush):
                         "kernel": f"square_kernel<{SQ_LP}, {st.solver_ctas_per_sm}>", "flops_per_pixel": fpp,
                         "launch_ms": solver_avg, "mean_power_iters": statistics.mean(its),
                         "mean_newton_steps": statistics.mean(newton), "root_fallback_frac": statistics.mean(rootfb),
+                        "mean_polish_steps": statistics.mean(polish),
                         "mean_aberth_evals": statistics.mean(evals), "mean_aberth_updates": statistics.mean(updates)},
            "paper_table2_context": PAPER_TABLE2_1024}
 

@@ -320,8 +320,10 @@ const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
  *   eig_fallback_frac row geometry: fraction of work items whose warp ran the Jacobi fallback.
  *   mean_newton_steps batched path: Newton steps of the signal root per work item, averaged.
  *   root_fallback_frac batched path: fraction of work items whose warp ran the Aberth fallback.
+ *   mean_polish_steps batched path: polish steps of the selected root per work item, averaged.
  *   In the square geometry a work item is one warp's 32 pixels of a tile row, mean_sweeps counts
- *   power-iteration steps, and the root figures add both polynomials (root_fallback_frac up to 2).
+ *   power-iteration steps, and the root figures add both polynomials (root_fallback_frac up to 2,
+ *   mean_polish_steps counts both).
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
  *                    call's stream) of the band-pass launches and of the solver launches.
  *   solver_ctas_per_sm  batched path: resident CTAs per SM of the solver variant last launched.
@@ -344,6 +346,7 @@ typedef struct {
     double eig_fallback_frac;
     double mean_newton_steps;
     double root_fallback_frac;
+    double mean_polish_steps;
 } rmusic_stats;
 
 int rmusic_get_stats(const rmusic_ctx* ctx, rmusic_stats* out);

@@ -613,6 +613,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             c[6] += (unsigned long long)eig_fb;
             c[7] += (unsigned long long)rs.newton;
             c[8] += (unsigned long long)rs.fallback;
+            c[9] += (unsigned long long)rs.polish;
         }
 
         // ---- store ---------------------------------------------------------------------------------

@@ -1100,6 +1100,7 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->eig_fallback_frac = mean(6);
     out->mean_newton_steps = mean(7);
     out->root_fallback_frac = mean(8);
+    out->mean_polish_steps = mean(9);
     auto sum = [&](const std::vector<cudaEvent_t>& v) {
         float t = 0.f;
         for (size_t i = 0; i + 1 < v.size(); i += 2) {

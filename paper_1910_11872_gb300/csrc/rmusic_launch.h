@@ -42,7 +42,7 @@ cudaError_t launch_plain_fp32(const FrameDev* d_frame, const FrameDev& h_frame, 
                               float* d_out, uint8_t* d_status, PlainArgs a, cudaStream_t stream);
 
 // Statistics slots of the solvers' counters array (the BatchedArgs / SquareArgs lists below).
-constexpr int kStatSlots = 9;
+constexpr int kStatSlots = 10;
 
 // Batched FP32 path: persistent, warp-scheduled over all work items of all frames that share
 // covariance order L. `counter` must be zero when the kernel starts.
@@ -53,7 +53,8 @@ struct BatchedArgs {
     int exhaustive;                // 1: Jacobi sweeps and all roots for every pixel (no shortcuts)
     unsigned long long* counters;  // [0] Jacobi sweeps, [1] Aberth iterations, [2] items, [3] Aberth root
                                    // updates, [4] Aberth evaluations of Q and Q', [5] power steps,
-                                   // [6] Jacobi fallbacks, [7] Newton steps, [8] Aberth fallbacks
+                                   // [6] Jacobi fallbacks, [7] Newton steps, [8] Aberth fallbacks,
+                                   // [9] polish steps
 };
 bool batched_supports(int L);
 int batched_num_variants(int L);
@@ -78,7 +79,8 @@ struct SquareArgs {
     float tol2;                    // power iteration stops when |u_new - u|^2 <= tol2
     unsigned long long* counters;  // [0] power iterations, [1] Aberth iterations, [2] warps, [3] Aberth root
                                    // updates, [4] Aberth evaluations of Q and Q', [7] Newton steps,
-                                   // [8] Aberth fallbacks (root figures: both polynomials)
+                                   // [8] Aberth fallbacks, [9] polish steps (root figures: both
+                                   // polynomials)
 };
 bool square_supports(int Lp);
 int square_num_variants(int Lp);

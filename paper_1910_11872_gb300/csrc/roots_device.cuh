@@ -281,14 +281,17 @@ __device__ __forceinline__ cx<float> mirror_newton_step(cx<float> z, cx<float> p
     return cdivf(pD, dp * D - p);
 }
 
-// Two FP32 refinement steps of the selected root zs: on Q' from the midpoint of zs and its
+// Polish steps of the selected root.
+constexpr int kPolishSteps = 2;
+
+// kPolishSteps FP32 refinement steps of the selected root zs: on Q' from the midpoint of zs and its
 // nearest root zn when the two form a split double root (cluster), otherwise Newton on Q with the
 // partner 1/conj(z) divided out.
 template <int L>
 __device__ __forceinline__ cx<float> polish_root(const cx<float>* c, cx<float> zs, cx<float> zn, bool cluster) {
     cx<float> zz = cluster ? 0.5f * (zs + zn) : zs;
 #pragma unroll 1
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < kPolishSteps; ++it) {
         cx<float> p, d1, d2;
         horner_pdd<L>(c, zz, p, d1, d2);
         const cx<float> stp = cluster ? cdivf(d1, d2) : mirror_newton_step(zz, p, d1);
@@ -297,12 +300,16 @@ __device__ __forceinline__ cx<float> polish_root(const cx<float>* c, cx<float> z
     return zz;
 }
 
-// polish_root for an isolated root only: the same two steps without Q'' (Horner on Q and Q'
-// alone gives the same Q and Q' bit for bit, so the result equals polish_root's).
+// polish_root for an isolated root only: the same kPolishSteps steps without Q'' (Horner on Q and
+// Q' alone gives the same Q and Q' bit for bit, so the result equals polish_root's). Each step is
+// taken whenever it is finite, also at the FP32 rounding level of the residual: a lane that
+// Newton's method left there can still be ~3e-5 rad from the root, and the steps land it on the
+// iteration's FP32 fixed point. (Iterating until the step falls below 1e-6 instead ran into the
+// noise floor of the step in most warps and random-walked the root by ~1e-5.)
 template <int L>
 __device__ __forceinline__ cx<float> polish_isolated(const cx<float>* c, cx<float> zz) {
 #pragma unroll 1
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < kPolishSteps; ++it) {
         cx<float> p, d1;
         horner_pd<L>(c, zz, p, d1);
         const cx<float> stp = mirror_newton_step(zz, p, d1);
@@ -327,11 +334,12 @@ __device__ __noinline__ void polish_cold(const cx<float>* c_in, cx<float> zs, cx
 // Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' (mirror_newton_step) -- from the estimator's
 // start 0.99 exp(j arg conj(rho_1)) (the start inner_roots gives the signal root). A step that
 // leaves the disk is folded back onto the mirror. A lane stops when |Q| is at the FP32 rounding
-// level (the step is then not taken, as in inner_roots) or the step is below 1e-3 (the root is then
-// known to ~1e-6, far inside the certificate's 0.02 margin, and the two polish steps that follow
-// converge quadratically from there); the warp stops when every lane has or after max_iters steps
-// (conv false for the lanes still moving). Inactive lanes (pixels without a result) count as
-// stopped from the start.
+// level (the step is then not taken, as in inner_roots) or after a step below 3.2e-3 (the root is
+// then known to ~1e-5, far inside the certificate's 0.02 margin, and the two polish steps that
+// follow converge quadratically from there; a 1e-3 stop took a third step in most warps, a 1e-2
+// stop left the two polish steps short by up to 1.3e-5 rad in a few pixels per million); the warp
+// stops when every lane has or after max_iters steps (conv false for the lanes still moving).
+// Inactive lanes (pixels without a result) count as stopped from the start.
 template <int L>
 __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, float res_lim2, int max_iters,
                                                         bool active, bool& conv, int& steps) {
@@ -353,7 +361,7 @@ __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, floa
             const float r2 = norm2(z);
             if (r2 > 1.f) z = frcp(r2) * z;
         }
-        conv = conv || small || (fin && norm2(w) <= 1e-6f);
+        conv = conv || small || (fin && norm2(w) <= 1e-5f);
         if (steps >= max_iters || __all_sync(kFull, conv)) break;
     }
     return z;
@@ -434,6 +442,7 @@ __device__ __noinline__ void aberth_select(const cx<float>* c_in, float res_lim2
 
 struct RootStats {
     int newton;   // Newton steps of the signal root
+    int polish;   // polish steps of the selected root
     int fallback; // 1 if the warp ran the full Aberth iteration
     int iters;    // Aberth sweeps, evaluations and root updates (fallback only)
     int evals;
@@ -498,8 +507,10 @@ __device__ __forceinline__ cx<float> signal_root(const cx<float>* c, float res_l
         for (int i = 0; i < L; ++i) cl[i] = c[i];
         cx<float> zp;
         polish_cold<L>(cl, zs, zn, cluster, &zp);
+        rs.polish = kPolishSteps;
         return zp;
     }
+    rs.polish = kPolishSteps;
     return polish_isolated<L>(c, zs);
 }
 

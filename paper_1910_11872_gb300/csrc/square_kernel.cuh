@@ -218,7 +218,7 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         // ---- roots, selection and angle: axis 0 is y (z_y), axis 1 is x (z_x) ----------------------
         float om_y = 0.f, om_x = 0.f;
         bool rconv_all = true, found_all = true;
-        int riters = 0, revals = 0, rupdates = 0, rnewton = 0, rfallback = 0;
+        int riters = 0, revals = 0, rupdates = 0, rnewton = 0, rfallback = 0, rpolish = 0;
 #pragma unroll 1
         for (int ax = 0; ax < 2; ++ax) {
             cx<float> c[M];
@@ -244,6 +244,7 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
             rupdates += rs.updates;
             rnewton += rs.newton;
             rfallback += rs.fallback;
+            rpolish += rs.polish;
         }
 
         // ---- alpha: angle of the demodulated block mean (Eq. 15) ----------------------------------
@@ -284,6 +285,7 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
             c[4] += (unsigned long long)revals;
             c[7] += (unsigned long long)rnewton;
             c[8] += (unsigned long long)rfallback;
+            c[9] += (unsigned long long)rpolish;
         }
 
         // ---- store the three maps ------------------------------------------------------------------

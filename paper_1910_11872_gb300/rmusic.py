@@ -99,6 +99,7 @@ class rmusic_stats(ctypes.Structure):
         ("eig_fallback_frac", ctypes.c_double),
         ("mean_newton_steps", ctypes.c_double),
         ("root_fallback_frac", ctypes.c_double),
+        ("mean_polish_steps", ctypes.c_double),
     ]
 
 

@@ -64,11 +64,13 @@ def test_row_statistics_show_the_shortcuts_taken():
     _, st = _run([fr.image])
     assert 1.0 <= st.mean_power_steps <= 6.0, st.mean_power_steps
     assert st.eig_fallback_frac <= 0.02 and st.mean_sweeps <= 0.1
-    assert 2.0 <= st.mean_newton_steps <= 8.0, st.mean_newton_steps
+    assert 1.0 <= st.mean_newton_steps <= 8.0, st.mean_newton_steps
+    assert st.mean_polish_steps == 2.0, st.mean_polish_steps
     assert st.root_fallback_frac <= 0.02 and st.mean_root_evals <= 1.0
     _, se = _run([fr.image], exhaustive=1)
     assert se.eig_fallback_frac == 1.0 and se.mean_sweeps >= 1.0
     assert se.root_fallback_frac == 1.0 and se.mean_root_evals > 5.0 and se.mean_newton_steps == 0.0
+    assert se.mean_polish_steps == 2.0, se.mean_polish_steps
 
 
 @pytest.mark.parametrize("snr,Lp", [(0.0, 5), (-5.0, 3), (-5.0, 5), (10.0, 8)])

@@ -275,4 +275,5 @@ def test_square_stats_and_launches():
     # the signal root of both polynomials by Newton's method; the Aberth fallback only where the
     # certificate fails in some lane (at most both polynomials of every work item)
     assert 2.0 <= st.mean_newton_steps <= 32.0 and 0.0 <= st.root_fallback_frac <= 2.0
+    assert st.mean_polish_steps == 4.0, st.mean_polish_steps  # two steps for each polynomial
     assert st.solver_ms > 0
