@@ -196,7 +196,9 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
  *   d_status  device uint8 buffer laid out like d_out, or NULL.
  *   cuda_stream  cudaStream_t (as void*) on which all work is queued.
  * Errors: RMUSIC_EINVAL (NULL pointers with n_frames > 0, a bad descriptor, unsupported
- * (N, L) for the path), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a no-op. */
+ * (N, L) for the path), RMUSIC_EUNSUPPORTED (a frame of 2^31 or more 32-pixel work items, about
+ * 6.9e10 pixels: far beyond what fits a GPU), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a
+ * no-op. */
 int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
                              int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream);
 

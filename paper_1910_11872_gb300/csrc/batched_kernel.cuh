@@ -446,8 +446,9 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         const int f = find_frame(fr, nframes, (int64_t)item, [](const FrameDev& F) { return F.item_start; });
         const FrameDev& F = fr[f];
         const int64_t local = (int64_t)item - F.item_start;
-        const int wline = (int)(local / F.nchunks);
-        const int chunk = (int)(local % F.nchunks);
+        // a frame's items number below 2^31: 32-bit division (a 64-bit one is a long routine)
+        const int wline = (int)((uint32_t)local / (uint32_t)F.nchunks);
+        const int chunk = (int)((uint32_t)local % (uint32_t)F.nchunks);
         const int N = F.N, K = N - L + 1, wlen = F.wlen;
         const int pos = chunk * kChunk + lane;
         const int a0 = chunk * kChunk - N / 2;

@@ -287,6 +287,10 @@ int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
         F->nchunks = (F->wlen + kChunk - 1) / kChunk;
         F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
     }
+    // the solvers split a frame's work-item index with 32-bit arithmetic (far above any frame whose
+    // analytic signal fits a GPU)
+    const int64_t rows = square ? ((int64_t)d.height + kSqTY - 1) / kSqTY : (int64_t)F->wlines;
+    if (rows * (int64_t)F->nchunks >= (int64_t)1 << 31) return RMUSIC_EUNSUPPORTED;
     return RMUSIC_OK;
 }
 

@@ -71,8 +71,9 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         const int f = find_frame(fr, nframes, (int64_t)item, [](const FrameDev& F) { return F.item_start; });
         const FrameDev& F = fr[f];
         const int64_t local = (int64_t)item - F.item_start;
-        const int ty = (int)(local / F.nchunks);
-        const int tx = (int)(local % F.nchunks);
+        // a frame's items number below 2^31: 32-bit division (a 64-bit one is a long routine)
+        const int ty = (int)((uint32_t)local / (uint32_t)F.nchunks);
+        const int tx = (int)((uint32_t)local % (uint32_t)F.nchunks);
         const int H = F.H, W = F.W;
 
         // ---- stage the tile's samples (coalesced rows) ----------------------------------------
