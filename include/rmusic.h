@@ -213,6 +213,21 @@ int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic
 int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs, int32_t n_frames,
                     float* d_out, uint8_t* d_status, void* cuda_stream);
 
+/* Same as rmusic_demodulate_frames_host, but asynchronous: the call queues the work on
+ * cuda_stream and returns; the maps are complete once the stream's work is (cudaStreamSynchronize
+ * or an event recorded after the call). The frames are always staged into the context's workspace
+ * by the copy engine -- which needs no SM -- so a caller alternating two contexts on two streams
+ * (double buffering) overlaps the frames' transfer of one call with the kernels of the other;
+ * pinned output buffers are written in place by the solver, others through the workspace and a
+ * copy queued at the end. The host buffers must stay valid and the input unchanged until the
+ * stream has completed the call (pageable input is copied before the call returns), and a context
+ * serves one call at a time: the next call on it must follow on the same stream or after the
+ * previous one completes. Errors: as rmusic_demodulate_frames_host; a CUDA error met while the
+ * work runs surfaces at the caller's synchronisation. */
+int rmusic_demodulate_frames_host_async(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
+                                        const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
+                                        uint8_t* h_status, void* cuda_stream);
+
 /* Pre-allocate the context's device workspace for calls of up to max_pixels pixels in total
  * (sum of height x width over the call's frames) and up to max_frames frames: the analytic-signal
  * buffer (8 bytes per pixel, 16 on the plain FP64 path), the frame tables (device and pinned

@@ -928,13 +928,14 @@ void* direct_host_ptr(const void* p) {
     if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
     return a.devicePointer;
 }
-}  // namespace
 
-extern "C" {
-
-int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
-                                  const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
-                                  uint8_t* h_status, void* cuda_stream) {
+// The host-buffer entries. sync: the maps are complete on return, and pinned frames are read in
+// place by the band-pass kernel. Without sync the call only queues the work: the frames are always
+// staged by the copy engine, which needs no SM, so a caller alternating two contexts overlaps one
+// call's transfer with the other's kernels (reading in place would need the SMs the other call's
+// solver holds).
+int host_entry(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes, const rmusic_frame_desc* descs,
+               int32_t n_frames, float* h_out, uint8_t* h_status, void* cuda_stream, bool sync) {
     if (!ctx || n_frames < 0) return RMUSIC_EINVAL;
     if (n_frames == 0) return RMUSIC_OK;
     if (!h_frames || !descs || !h_out) return RMUSIC_EINVAL;
@@ -956,7 +957,7 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
     // solver writes the maps over the host link while it computes, instead of a copy before and a
     // copy after the kernels. The unwrapping pass reads and writes its maps many times, so with
     // phase assembly the maps are staged on the device.
-    const void* d_in = direct_host_ptr(h_frames);
+    const void* d_in = sync ? direct_host_ptr(h_frames) : nullptr;
     const bool staged_maps = ctx->p.geometry == RMUSIC_GEOM_SQUARE && ctx->p.unwrap;
     float* d_out = staged_maps ? nullptr : static_cast<float*>(direct_host_ptr(h_out));
     uint8_t* d_st = nullptr;
@@ -996,8 +997,24 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
         RM_CUDA(cudaMemcpyAsync(h_out, ctx->d_out, out_elems * sizeof(float), cudaMemcpyDeviceToHost, s));
         if (h_status) RM_CUDA(cudaMemcpyAsync(h_status, ctx->d_st, st_elems, cudaMemcpyDeviceToHost, s));
     }
-    RM_CUDA(cudaStreamSynchronize(s));
+    if (sync) RM_CUDA(cudaStreamSynchronize(s));
     return RMUSIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
+                                  const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
+                                  uint8_t* h_status, void* cuda_stream) {
+    return host_entry(ctx, h_frames, in_bytes, descs, n_frames, h_out, h_status, cuda_stream, true);
+}
+
+int rmusic_demodulate_frames_host_async(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,
+                                        const rmusic_frame_desc* descs, int32_t n_frames, float* h_out,
+                                        uint8_t* h_status, void* cuda_stream) {
+    return host_entry(ctx, h_frames, in_bytes, descs, n_frames, h_out, h_status, cuda_stream, false);
 }
 
 int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant) {

@@ -140,6 +140,9 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_demodulate_frames_host.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(rmusic_frame_desc),
                                                       i32, vp, vp, vp]
         lib.rmusic_demodulate_frames_host.restype = ctypes.c_int
+        lib.rmusic_demodulate_frames_host_async.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(rmusic_frame_desc),
+                                                      i32, vp, vp, vp]
+        lib.rmusic_demodulate_frames_host_async.restype = ctypes.c_int
         lib.rmusic_demodulate_frames_noalloc.argtypes = [ctypes.POINTER(rmusic_params), ctypes.c_int, vp,
                                                          ctypes.POINTER(rmusic_frame_desc), i32, vp, vp, vp]
         lib.rmusic_demodulate_frames_noalloc.restype = ctypes.c_int
@@ -207,6 +210,16 @@ def rmusic_demodulate_frames_host(ctx, h_frames: int, in_bytes: int, descs, n_fr
                                                       h_out or None, h_status or None, cuda_stream or None)
     if rc != RMUSIC_OK:
         raise RmusicError(rc, "rmusic_demodulate_frames_host", rmusic_last_cuda_error(ctx))
+    return rc
+
+
+def rmusic_demodulate_frames_host_async(ctx, h_frames: int, in_bytes: int, descs, n_frames: int, h_out: int,
+                                        h_status: int | None, cuda_stream: int | None) -> int:
+    arr = _desc_array(descs)
+    rc = load_library().rmusic_demodulate_frames_host_async(ctx, h_frames or None, int(in_bytes), arr, int(n_frames),
+                                                            h_out or None, h_status or None, cuda_stream or None)
+    if rc != RMUSIC_OK:
+        raise RmusicError(rc, "rmusic_demodulate_frames_host_async", rmusic_last_cuda_error(ctx))
     return rc
 
 

@@ -624,3 +624,49 @@ def test_host_entry_statistics_and_graph_owned_timing_events():
                                                                                 st.solver_ms, wall_ms)
     finally:
         dem.close()
+
+
+def test_host_entry_async_double_buffered_equals_sync():
+    """The asynchronous host entry queues the call and returns; once its stream is synchronised the
+    maps equal the synchronous entry's (pinned buffers, maps written in place; pageable buffers,
+    staged). Two contexts on two streams, alternated with two calls in flight, give every step its
+    own correct maps."""
+    torch = _torch()
+    shapes = [(40, 256), (24, 512)]
+    steps = [[synth.peaks_frame(snr, 0.1, H=h, W=w, stream=k).image for h, w in shapes]
+             for k, snr in enumerate((30.0, 10.0, np.inf, 5.0, 20.0))]
+    descs, nbytes, nout = rmusic.frame_descs(shapes, rmusic.RMUSIC_DTYPE_F32, 4)
+    ref = []
+    dem = rmusic.Demodulator()
+    try:
+        for fr in steps:
+            flat = np.concatenate([f.ravel() for f in fr]).astype(np.float32)
+            out = np.empty(nout, np.float32)
+            rmusic.rmusic_demodulate_frames_host(dem.ctx, flat.ctypes.data, nbytes, descs, 2, out.ctypes.data, None, None)
+            ref.append(out)
+    finally:
+        dem.close()
+    hins = [torch.from_numpy(np.concatenate([f.ravel() for f in fr]).astype(np.float32)).pin_memory() for fr in steps]
+    houts = [torch.full((nout,), 7.0).pin_memory() for _ in steps]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    dems = [rmusic.Demodulator(use_graph=1), rmusic.Demodulator(use_graph=1)]
+    try:
+        for k in range(len(steps)):
+            i = k % 2
+            streams[i].synchronize()  # this context's previous call is complete
+            rmusic.rmusic_demodulate_frames_host_async(dems[i].ctx, hins[k].data_ptr(), nbytes, descs, 2,
+                                                       houts[k].data_ptr(), None, streams[i].cuda_stream)
+        for st in streams:
+            st.synchronize()
+        for k in range(len(steps)):
+            assert np.array_equal(houts[k].numpy(), ref[k], equal_nan=True), k
+        # pageable buffers
+        flat = np.concatenate([f.ravel() for f in steps[1]]).astype(np.float32)
+        pout = np.empty(nout, np.float32)
+        rmusic.rmusic_demodulate_frames_host_async(dems[0].ctx, flat.ctypes.data, nbytes, descs, 2, pout.ctypes.data,
+                                                   None, streams[0].cuda_stream)
+        streams[0].synchronize()
+        assert np.array_equal(pout, ref[1], equal_nan=True)
+    finally:
+        for d in dems:
+            d.close()
