@@ -331,8 +331,10 @@ __device__ __noinline__ void polish_cold(const cx<float>* c_in, cx<float> zs, cx
 }
 
 // Signal root of Q by Newton's method with the root's mirror divided out -- the one-term
-// Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' (mirror_newton_step) -- from the estimator's
-// start 0.99 exp(j arg conj(rho_1)) (the start inner_roots gives the signal root). A step that
+// Aberth correction z <- z - N / (1 - N / (z - 1/conj(z))), N = Q / Q' (mirror_newton_step) -- from
+// r0 exp(j arg conj(rho_1)): the signal root's direction from the estimator's lag-1 coefficient and
+// the caller's estimate r0 < 1 of its radius (the root sits the closer to the circle the smaller
+// the noise's share of the window's energy). A step that
 // leaves the disk is folded back onto the mirror. A lane stops when |Q| is at the FP32 rounding
 // level (the step is then not taken, as in inner_roots) or after a step below 3.2e-3 (the root is
 // then known to ~1e-5, far inside the certificate's 0.02 margin, and the two polish steps that
@@ -342,10 +344,10 @@ __device__ __noinline__ void polish_cold(const cx<float>* c_in, cx<float> zs, cx
 // Inactive lanes (pixels without a result) count as stopped from the start.
 template <int L>
 __device__ __forceinline__ cx<float> newton_signal_root(const cx<float>* c, float res_lim2, int max_iters,
-                                                        bool active, bool& conv, int& steps) {
+                                                        bool active, float r0, bool& conv, int& steps) {
     const cx<float> rho1 = (-1.f) * c[1];
     const float n1 = norm2(rho1);
-    cx<float> z = n1 > 0.f ? (0.99f * rsqrtf(n1)) * conjg(rho1) : mkc(0.99f, 0.f);
+    cx<float> z = n1 > 0.f ? (r0 * rsqrtf(n1)) * conjg(rho1) : mkc(r0, 0.f);
     conv = !active;
     steps = 0;
 #pragma unroll 1
@@ -450,26 +452,29 @@ struct RootStats {
 };
 
 // The root stage (Algorithm 1): the inner root of Q nearest the unit circle, refined. The signal
-// root comes from newton_signal_root; it is the selected root when it is the only root in the
-// annulus r - 0.02 <= |z| < 1 (r its modulus), i.e. when Q has exactly L - 2 roots inside
+// root comes from newton_signal_root, started at radius r0 (clamped to [0.5, 0.9995]: on the
+// circle the mirror deflation has no step); it is the selected root when it is the only root in
+// the annulus r - 0.02 <= |z| < 1 (r its modulus), i.e. when Q has exactly L - 2 roots inside
 // |z| < r - 0.02 (roots_inside). Lanes without that certificate -- and with them the whole warp,
 // which executes the loop together -- take every inner root from inner_roots and select among
 // them (nearest_pair). Both end in polish_root; a selected root whose nearest other root is
 // closer than 4e-3 is a split double root (cluster). (The polish also lands a certified root on
 // the FP32 fixed point of the iteration: Newton's own last step, stopped at the rounding level of
-// the residual, leaves up to ~3e-5 rad on noisy windows.) exhaustive (uniform over the launch) skips the
-// Newton root and its certificate: every lane takes the full root finder. Inactive lanes (border or
-// degenerate pixels, whose result is not used) neither hold the warp in Newton's loop nor send it
-// to the full root finder.
+// the residual, leaves up to ~3e-5 rad on noisy windows.) exhaustive (uniform over the launch)
+// skips the Newton root and its certificate: every lane takes the full root finder. Inactive lanes
+// (border or degenerate pixels, whose result is not used) neither hold the warp in Newton's loop
+// nor send it to the full root finder.
 template <int L>
 __device__ __forceinline__ cx<float> signal_root(const cx<float>* c, float res_lim2, int max_iters, int exhaustive,
-                                                 bool active, bool& found, bool& cluster, bool& rconv,
+                                                 bool active, float r0, bool& found, bool& cluster, bool& rconv,
                                                  RootStats& rs) {
     bool nconv = false, cert = false;
     cx<float> zs = mkc(0.f, 0.f), zn = zs;
     rs.newton = 0;
     if (!exhaustive) {
-        zs = newton_signal_root<L>(c, res_lim2, kNewtonSteps, active, nconv, rs.newton);
+        // on the circle the mirror deflation has no step: start strictly inside
+        zs = newton_signal_root<L>(c, res_lim2, kNewtonSteps, active, fminf(fmaxf(r0, 0.5f), 0.9995f), nconv,
+                                   rs.newton);
         const float r2 = norm2(zs);
         const float r = sqrtf(r2);
         int nin = -1;
