@@ -400,6 +400,14 @@ def run_ours(args):
                          "schedule": "warp per matrix" if v == 3 else "thread per matrix",
                          "solver_ms": statistics.mean(vms)})
     rmusic.rmusic_set_solver_variant(dem.ctx, L_COV, -1)
+    # per-pixel outcomes of one step, outside the timed region (the timed steps skip the status map)
+    sout, sst, _ = dem.run(x, with_status=True)
+    torch.cuda.synchronize()
+    st_np = sst.cpu().numpy()
+    status_counts = {"ok": int((st_np == 0).sum()), "border": int((st_np == 1).sum()),
+                     "degenerate": int((st_np == 2).sum()), "not_converged": int((st_np == 3).sum()),
+                     "nan_values": int(torch.isnan(sout).sum().item())}
+    del sout, sst
 
     # ---- plain path on the same GPU (thread per pixel, one launch per frame) -------------------
     plain = rmusic.Demodulator(device=local, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0,
@@ -504,7 +512,7 @@ def run_ours(args):
                     "entry": "rmusic_demodulate_frames_host_async, two contexts double-buffered on two streams",
                     "sync": {"value": npx * world / (e2e_sync_ms * 1e3), "ms_per_step": e2e_sync_ms,
                              "entry": "rmusic_demodulate_frames_host, one call at a time"}},
-            "gpu_launches": launches, "clocks": clk,
+            "gpu_launches": launches, "clocks": clk, "status_counts": status_counts,
             "plain": {"value": plain_value, "unit": "Mpixel/s", "ms_per_step": plain_ms,
                       "path": "plain FP32, thread per pixel, one launch per frame",
                       "timing": f"3 warm-ups, median of {args.plain_steps} event-timed steps, L2 flushed"},
