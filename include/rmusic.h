@@ -320,6 +320,12 @@ const char* rmusic_strerror(int code);
 /* Text of the last CUDA error seen by this context (static storage inside ctx), or "". */
 const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
 
+/* 1 if this library was compiled with RMUSIC_CHECKS: the FP32-batched solvers then test their
+ * work items' data-dependent indices (frame, window line, window length, covariance order) and
+ * count failures in rmusic_stats.check_violations instead of touching memory out of range -- the
+ * stand-in for a device memory checker. 0 for the ordinary build, which carries none of it. */
+int rmusic_checked_build(void);
+
 /* Counters of the last call on this context (for measurement and tests).
  *   kernel_launches  kernels the last call queued (graph replays count their kernels).
  *   graph_replayed   1 if the last call replayed a cached CUDA graph.
@@ -338,6 +344,9 @@ const char* rmusic_last_cuda_error(const rmusic_ctx* ctx);
  *   mean_newton_steps batched path: Newton steps of the signal root per work item, averaged.
  *   root_fallback_frac batched path: fraction of work items whose warp ran the Aberth fallback.
  *   mean_polish_steps batched path: polish steps of the selected root per work item, averaged.
+ *   check_violations  batched path, checked builds only (rmusic_checked_build() == 1): index
+ *                    tests of the solvers that failed in the last call (each skips its work item
+ *                    instead of faulting; 0 is the only acceptable value). Always 0 otherwise.
  *   In the square geometry a work item is one warp's 32 pixels of a tile row, mean_sweeps counts
  *   power-iteration steps, and the root figures add both polynomials (root_fallback_frac up to 2,
  *   mean_polish_steps counts both).
@@ -364,6 +373,7 @@ typedef struct {
     double mean_newton_steps;
     double root_fallback_frac;
     double mean_polish_steps;
+    uint64_t check_violations;
 } rmusic_stats;
 
 int rmusic_get_stats(const rmusic_ctx* ctx, rmusic_stats* out);

@@ -450,6 +450,13 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         const int wline = (int)((uint32_t)local / (uint32_t)F.nchunks);
         const int chunk = (int)((uint32_t)local % (uint32_t)F.nchunks);
         const int N = F.N, K = N - L + 1, wlen = F.wlen;
+        // every index below follows from these (the staging reads 31 + N <= 32 + kMaxN samples, the
+        // prefix sums reach lane + L - 1 + K = 31 + N < kPreLen, the store stays in window line wline);
+        // checked builds test them and skip a bad item whole (the test is uniform over the warp)
+        if (!rm_check(f >= 0 && f < nframes && local >= 0 && local < (int64_t)F.wlines * F.nchunks && F.L == L &&
+                          N >= L && N <= kMaxN,
+                      args.counters))
+            continue;
         const int pos = chunk * kChunk + lane;
         const int a0 = chunk * kChunk - N / 2;
         const float2* gl = gam + F.gam_off + (uint64_t)wline * wlen;

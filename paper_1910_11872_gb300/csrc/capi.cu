@@ -853,7 +853,7 @@ int demodulate_impl(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
         if (rc) return rc;
         pixels += (uint64_t)F.H * (uint64_t)F.W;
     }
-    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, kStatSlots * sizeof(unsigned long long), s));
+    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, (kStatSlots + 1) * sizeof(unsigned long long), s));
     // group frames so that each group's analytic signal fits the budget (with room for the frame
     // table when the one held is too small for this call)
     const uint64_t table_reserve =
@@ -1102,6 +1102,14 @@ const char* rmusic_strerror(int code) {
 
 const char* rmusic_last_cuda_error(const rmusic_ctx* ctx) { return ctx ? ctx->last_err : ""; }
 
+int rmusic_checked_build(void) {
+#ifdef RMUSIC_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     if (!ctx_in || !out) return RMUSIC_EINVAL;
     rmusic_ctx* ctx = const_cast<rmusic_ctx*>(ctx_in);
@@ -1110,7 +1118,7 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->workspace_bytes = ctx->held;
     out->pixels = ctx->last_pixels;
     RM_CUDA(cudaEventSynchronize(ctx->call_done));
-    unsigned long long c[kStatSlots] = {};
+    unsigned long long c[kStatSlots + 1] = {};  // the statistics and the failed index checks
     RM_CUDA(cudaMemcpy(c, ctx->d_counters + kStatSlot, sizeof(c), cudaMemcpyDeviceToHost));
     auto mean = [&](int i) { return c[2] ? (double)c[i] / (double)c[2] : 0.0; };
     out->mean_sweeps = mean(0);
@@ -1122,6 +1130,7 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->mean_newton_steps = mean(7);
     out->root_fallback_frac = mean(8);
     out->mean_polish_steps = mean(9);
+    out->check_violations = c[kCheckSlot];
     auto sum = [&](const std::vector<cudaEvent_t>& v) {
         float t = 0.f;
         for (size_t i = 0; i + 1 < v.size(); i += 2) {

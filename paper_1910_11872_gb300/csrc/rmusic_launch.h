@@ -43,6 +43,22 @@ cudaError_t launch_plain_fp32(const FrameDev* d_frame, const FrameDev& h_frame, 
 
 // Statistics slots of the solvers' counters array (the BatchedArgs / SquareArgs lists below).
 constexpr int kStatSlots = 10;
+// Slot after the statistics: index checks that failed (checked builds only).
+constexpr int kCheckSlot = kStatSlots;
+
+#ifdef __CUDACC__
+// Checked builds (-DRMUSIC_CHECKS) test the solvers' data-dependent indices: rm_check(ok, counters)
+// counts a failed test in counters[kCheckSlot] and returns false, so that the caller skips the
+// access instead of faulting. Ordinary builds compile it to true and keep nothing of it.
+#ifdef RMUSIC_CHECKS
+__device__ __forceinline__ bool rm_check(bool ok, unsigned long long* counters) {
+    if (!ok && counters) atomicAdd(counters + kCheckSlot, 1ull);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool rm_check(bool, unsigned long long*) { return true; }
+#endif
+#endif
 
 // Batched FP32 path: persistent, warp-scheduled over all work items of all frames that share
 // covariance order L. `counter` must be zero when the kernel starts.

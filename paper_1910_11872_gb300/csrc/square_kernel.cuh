@@ -75,6 +75,13 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         const int ty = (int)((uint32_t)local / (uint32_t)F.nchunks);
         const int tx = (int)((uint32_t)local % (uint32_t)F.nchunks);
         const int H = F.H, W = F.W;
+        // every index below follows from these (the staged tile and each lane's block inside it have
+        // compile-time extents); checked builds test them and skip a bad item whole (the item is
+        // shared by the block, so the skip is uniform at its barriers)
+        if (!rm_check(f >= 0 && f < nframes && local >= 0 &&
+                          local < (int64_t)((H + kSqTY - 1) / kSqTY) * F.nchunks && F.L == LP,
+                      args.counters))
+            continue;
 
         // ---- stage the tile's samples (coalesced rows) ----------------------------------------
         {

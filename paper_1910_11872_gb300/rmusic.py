@@ -100,6 +100,7 @@ class rmusic_stats(ctypes.Structure):
         ("mean_newton_steps", ctypes.c_double),
         ("root_fallback_frac", ctypes.c_double),
         ("mean_polish_steps", ctypes.c_double),
+        ("check_violations", ctypes.c_uint64),
     ]
 
 
@@ -114,10 +115,21 @@ class RmusicError(RuntimeError):
 
 _lock = threading.Lock()
 _lib: ctypes.CDLL | None = None
+_checked = False
+
+
+def use_checked_build() -> None:
+    """Make this process load the checked build (RMUSIC_CHECKS) instead of the ordinary one. Must be
+    called before the library is first loaded; for tests that look for out-of-range indices."""
+    global _checked
+    with _lock:
+        if _lib is not None and not _checked:
+            raise RuntimeError("the ordinary build is already loaded in this process")
+        _checked = True
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.CHECKED_LIB if _checked else _build.LIB
 
 
 def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
@@ -126,11 +138,12 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
     with _lock:
         if _lib is not None:
             return _lib
+        path = _build.CHECKED_LIB if _checked else _build.LIB
         if build_if_needed:
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"CUDA library not built: {_build.LIB}")
-        lib = ctypes.CDLL(_build.LIB)
+            _build.build(checked=_checked)
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path}")
+        lib = ctypes.CDLL(path)
         vp, i32 = ctypes.c_void_p, ctypes.c_int32
         lib.rmusic_create.argtypes = [ctypes.POINTER(rmusic_params), ctypes.c_int, ctypes.c_size_t,
                                       ctypes.POINTER(vp)]
@@ -156,6 +169,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_strerror.restype = ctypes.c_char_p
         lib.rmusic_last_cuda_error.argtypes = [vp]
         lib.rmusic_last_cuda_error.restype = ctypes.c_char_p
+        lib.rmusic_checked_build.argtypes = []
+        lib.rmusic_checked_build.restype = ctypes.c_int
         lib.rmusic_set_solver_variant.argtypes = [vp, i32, i32]
         lib.rmusic_set_solver_variant.restype = ctypes.c_int
         lib.rmusic_unwrap_phase.argtypes = [vp, vp, ctypes.POINTER(rmusic_frame_desc), i32, vp, vp]
