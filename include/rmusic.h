@@ -235,7 +235,9 @@ int rmusic_demodulate_frames_host_async(rmusic_ctx* ctx, const void* h_frames, s
  * allocates nothing, so it never waits for the device as a buffer that grows does (freeing
  * device memory synchronises the device): what a serving loop or a real-time caller needs.
  * Without it the workspace grows on demand. The reservation counts against the context's HBM
- * budget and is kept until rmusic_destroy. Synchronises the device when it replaces a smaller
+ * budget and is kept until rmusic_destroy. It does not cover the host-buffer entries' staging
+ * buffers (frames and maps in device memory, sized by the frames' element type), which a context
+ * allocates on its first host-buffer call and reuses while the calls do not grow. Synchronises the device when it replaces a smaller
  * buffer. Errors: RMUSIC_EINVAL (NULL context, max_frames < 0, max_pixels >= 2^31 with
  * unwrap = 1), RMUSIC_ENOMEM (the reservation exceeds the budget: nothing changes; or the device
  * is out of memory: the buffer being replaced is gone and later calls allocate on demand).
