@@ -28,6 +28,7 @@ MUTATIONS = {
     "poly: lag index transposed": ("q[(l - m) + (L - 1)] += Cml;", "q[(m - l) + (L - 1)] += Cml;"),
     "poly: projector sign": ("cplx Cml = (m == l ? 1.0 : 0.0) - u[m] * conj(u[l]);", "cplx Cml = (m == l ? 1.0 : 0.0) + u[m] * conj(u[l]);"),
     "roots: Aberth sum sign": ("z[i] -= Ni / (1.0 - Ni * Si);", "z[i] -= Ni / (1.0 + Ni * Si);"),
+    "roots: closing sweeps dropped": ("for (int sweep = 0; sweep < 2; ++sweep)", "for (int sweep = 0; sweep < 0; ++sweep)"),
     "select: outside roots": ("if (!(r <= 1.0 + 1e-9)) continue;", "if (!(r >= 1.0 - 1e-9)) continue;"),
     "select: farthest root": ("if (d < bestd || (d == bestd && t < bestt))", "if (-d < bestd || (d == bestd && t < bestt))"),
     "angle: carrier added": ("*deriv = orc_wrap(carg(z) - omega_ref);", "*deriv = orc_wrap(carg(z) + omega_ref);"),
@@ -86,6 +87,7 @@ PINS = [
     lambda: P.test_music_poly_on_circle_equals_noise_projection(8),
     P.test_music_poly_closed_form_steering_vector,
     lambda: P.test_roots_match_companion_matrix(3),
+    lambda: P.test_roots_near_pair_at_rounding_level(8),
     P.test_selection_hand_cases,
     lambda: P.test_p1_noise_free_linear_phase_exact(32, 8, 1),
     lambda: P.test_p2_order_two_is_pulse_pair(1),

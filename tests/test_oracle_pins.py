@@ -180,6 +180,46 @@ def test_roots_match_companion_matrix(seed):
         assert abs(np.polyval(q[::-1], z)) < 1e-12 * np.polyval(np.abs(q[::-1]), abs(z))
 
 
+def _near_pair_polynomial(L, eps, theta):
+    """Conjugate-self-reciprocal polynomial of degree 2L - 2 (the root-MUSIC structure, Eq. 12-14)
+    with planted roots: a near pair (1 - eps) e^{j theta} and its mirror 1/(1 - eps) e^{j theta},
+    2 eps apart across the unit circle, and L - 2 further inner roots at radius 0.55 / 0.7 with
+    their mirrors. Returns the ascending coefficients (rounded to FP64)."""
+    inner = [(1 - eps) * np.exp(1j * theta)]
+    for k in range(1, L - 1):
+        inner.append((0.55 if k % 2 else 0.7) * np.exp(1j * (theta + TWO_PI * k / (L - 1))))
+    inner = np.array(inner)
+    return np.poly(np.concatenate([inner, 1 / np.conj(inner)]))[::-1]
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 12])
+def test_roots_near_pair_at_rounding_level(L):
+    """Roots of polynomials whose signal root and its mirror straddle the unit circle 2e-3, 2e-4 and
+    2e-5 apart (the configuration the selection of Sec. 3 has to resolve on high-SNR windows) are as
+    accurate as the FP64 coefficients allow: each root is within 3 x its first-order condition bound
+    eps_64 sum_k |q_k| |z|^k / |Q'(z)| of the exact root of the same FP64 coefficients, computed
+    independently with mpmath's polyroots in 60-digit arithmetic. A root finder stopped at the
+    residual level alone leaves the near pair 20-45 x its condition bound off."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    worst = 0.0
+    for eps in (1e-3, 1e-4, 1e-5):
+        for theta in (0.3, 2.0, -1.1):
+            q = _near_pair_polynomial(L, eps, theta)
+            exact = np.array([complex(z) for z in mpmath.polyroots([mpmath.mpc(complex(c)) for c in q[::-1]],
+                                                                   maxsteps=400, extraprec=400)])
+            got, nc = O.poly_roots(q)
+            assert not nc and got.size == 2 * L - 2
+            d = np.abs(got[:, None] - exact[None, :])
+            j = d.argmin(axis=1)
+            assert len(set(j.tolist())) == got.size  # one computed root per exact root
+            k = np.arange(q.size)
+            for z, e in zip(exact[j], d.min(axis=1)):
+                bound = np.finfo(float).eps * np.sum(np.abs(q) * np.abs(z) ** k) / abs(np.sum(k[1:] * q[1:] * z ** (k[1:] - 1)))
+                worst = max(worst, e / bound)
+    assert worst <= 3.0, worst
+
+
 @pytest.mark.parametrize("L", [3, 8, 12])
 def test_roots_conjugate_reciprocal_pairs(L):
     """c_-k = conj(c_k) makes the root set closed under z -> 1/conj(z)."""
