@@ -266,8 +266,18 @@ int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t 
  *   - All device scratch (analytic signal, frame table, work counters) lives in one fixed array
  *     inside the library's device code, about 32 MiB per GPU, held from the moment that code is
  *     loaded on the GPU (with CUDA's default lazy loading: this entry point's first call there)
- *     until the process exits. The caller passes frames and output maps exactly as for
- *     rmusic_demodulate_frames; descs is a host array read before the call returns.
+ *     until the process exits. With eager module loading (CUDA_MODULE_LOADING=EAGER) every
+ *     process that loads the library pays the 32 MiB on each GPU it uses, whether or not it ever
+ *     calls this entry point; a process that also loads the checked build of the library
+ *     (RMUSIC_CHECKS) holds a second, separate array for it. The caller passes frames and output
+ *     maps exactly as for rmusic_demodulate_frames; descs is a host array read before the call
+ *     returns.
+ *   - Parameters and descriptors are validated exactly as rmusic_create and
+ *     rmusic_demodulate_frames validate them (same codes), then this entry point adds its own
+ *     restrictions (RMUSIC_EUNSUPPORTED otherwise).
+ *   - The solver always runs the default register-cap variant for each covariance order (no
+ *     tuning run, which would need timing buffers); its maps equal those of a context pinned to
+ *     that variant with rmusic_set_solver_variant.
  *   - Limits: at most 4,194,304 pixels (e.g. four 1024 x 1024 frames) and 256 frames per call;
  *     larger requests are rejected with RMUSIC_ENOMEM before any work is queued.
  *   - The first call on a device looks the array's address up (cudaGetSymbolAddress) and sets

@@ -25,8 +25,124 @@
 #include "../../include/rmusic.h"
 #include "rmusic_device.cuh"
 #include "rmusic_launch.h"
+#include "rmusic_validate.h"
 
 using namespace rmusic;
+
+namespace rmusic {
+
+static bool params_ok(const rmusic_params& p) {
+    if (p.geometry == RMUSIC_GEOM_SQUARE) {
+        if (p.half_width < 1 || p.half_width > kMaxSquareLp) return false;
+    } else if (p.geometry == RMUSIC_GEOM_ROW) {
+        if (p.window_len < 2 || p.window_len > kMaxN) return false;
+        if (p.cov_order < 2 || p.cov_order > kMaxL || p.cov_order > p.window_len) return false;
+        if (p.forward_backward != 0 && p.forward_backward != 1) return false;
+        if (p.deriv_axis != 0 && p.deriv_axis != 1) return false;
+    } else {
+        return false;
+    }
+    if (p.carrier_axis != 0 && p.carrier_axis != 1) return false;
+    if (p.unwrap != 0 && p.unwrap != 1) return false;
+    if (p.raw_input != 0 && p.raw_input != 1) return false;
+    if (p.exhaustive != 0 && p.exhaustive != 1) return false;
+    if (p.raw_input && (p.geometry != RMUSIC_GEOM_ROW || p.deriv_axis != p.carrier_axis)) return false;
+    if (p.geometry == RMUSIC_GEOM_ROW && p.model_order >= p.cov_order) return false;
+    if (p.unwrap && p.geometry != RMUSIC_GEOM_SQUARE) return false;
+    if (!(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5)) return false;
+    if (!(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5)) return false;
+    if (!(p.band_cross >= 0.0 && p.band_cross < 0.5)) return false;
+    if (p.precision < RMUSIC_PLAIN_FP64 || p.precision > RMUSIC_FP32_BATCHED) return false;
+    if (p.max_sweeps < 0 || p.max_root_iters < 0) return false;
+    return true;
+}
+
+int params_check(const rmusic_params& p) {
+    if (p.model_order < 1) return RMUSIC_EINVAL;
+    if (p.model_order > kMaxModelOrder) return RMUSIC_EUNSUPPORTED;
+    if (!params_ok(p)) return RMUSIC_EINVAL;
+    if (p.model_order > 1 && p.precision == RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
+    if (p.geometry == RMUSIC_GEOM_SQUARE && p.precision != RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
+    return RMUSIC_OK;
+}
+
+int describe_frame(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev* F) {
+    if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
+    const int pitch = d.pitch_elems == 0 ? d.width : d.pitch_elems;
+    if (pitch < d.width) return RMUSIC_EINVAL;
+    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16 && d.dtype != RMUSIC_DTYPE_C64)
+        return RMUSIC_EINVAL;
+    const int esz = d.dtype == RMUSIC_DTYPE_C64 ? 8 : d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2;
+    if (d.offset_bytes % esz) return RMUSIC_EINVAL;
+    const bool square = p.geometry == RMUSIC_GEOM_SQUARE;
+    int N, L;
+    if (square) {
+        // the paper's block: L holds the half-width Lp, N the block side 2 Lp + 1
+        L = p.half_width;
+        N = 2 * L + 1;
+        if (!square_supports(L)) return RMUSIC_EUNSUPPORTED;
+    } else {
+        N = d.window_len ? d.window_len : p.window_len;
+        L = d.cov_order ? d.cov_order : p.cov_order;
+        if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
+        if (p.precision == RMUSIC_FP32_BATCHED && (!batched_supports(L) || p.forward_backward != 1))
+            return RMUSIC_EUNSUPPORTED;
+    }
+    memset(F, 0, sizeof(*F));
+    F->in_off = d.offset_bytes;
+    F->out_off = d.out_offset;
+    F->H = d.height;
+    F->W = d.width;
+    F->pitch = pitch;
+    F->dtype = d.dtype;
+    F->N = N;
+    F->L = L;
+    F->carrier_axis = p.carrier_axis;
+    F->deriv_axis = square ? 0 : p.deriv_axis;  // the square block reads a row-major workspace
+    F->raw = p.raw_input && d.dtype != RMUSIC_DTYPE_C64;
+    F->geom = square ? kGeomSquare : kGeomRow;
+    F->nlines = p.carrier_axis == 0 ? d.height : d.width;
+    F->len = p.carrier_axis == 0 ? d.width : d.height;
+    if (F->len > kMaxLine) return RMUSIC_EUNSUPPORTED;
+    // kept band: 1 <= k < len/2 and |k/len - f0| < B (a contiguous run of bins)
+    const double f0 = p.carrier_freq;
+    const double B = p.band_halfwidth > 0.0 ? p.band_halfwidth : 0.5 * f0;
+    int klo = -1, nb = 0;
+    for (int k = 1; 2 * k < F->len; ++k) {
+        if (fabs((double)k / (double)F->len - f0) < B) {
+            if (klo < 0) klo = k;
+            ++nb;
+        }
+    }
+    F->k_lo = klo < 0 ? 1 : klo;
+    F->nb = nb;
+    if (p.band_cross > 0.0) {
+        // kept cross bins: signed k with |k| < B_c len across the carrier
+        const int lenc = p.carrier_axis == 0 ? d.height : d.width;
+        const double lim = p.band_cross * (double)lenc;
+        int kc = 0;
+        while ((double)(kc + 1) < lim) ++kc;
+        if (kc > kMaxCrossKc) return RMUSIC_EUNSUPPORTED;
+        F->cross_kc = kc;
+    }
+    F->wlines = F->deriv_axis == 0 ? d.height : d.width;
+    F->wlen = F->deriv_axis == 0 ? d.width : d.height;
+    F->f0 = f0;
+    if (square) {
+        F->nchunks = (d.width + kSqTX - 1) / kSqTX;  // tiles per tile row
+        F->omega_ref = 6.283185307179586476925 * f0;
+    } else {
+        F->nchunks = (F->wlen + kChunk - 1) / kChunk;
+        F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
+    }
+    // the solvers split a frame's work-item index with 32-bit arithmetic (far above any frame whose
+    // analytic signal fits a GPU)
+    const int64_t rows = square ? ((int64_t)d.height + kSqTY - 1) / kSqTY : (int64_t)F->wlines;
+    if (rows * (int64_t)F->nchunks >= (int64_t)1 << 31) return RMUSIC_EUNSUPPORTED;
+    return RMUSIC_OK;
+}
+
+}  // namespace rmusic
 
 namespace {
 
@@ -137,32 +253,6 @@ int cuda_fail(rmusic_ctx* c, cudaError_t e, const char* what) {
         if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
     } while (0)
 
-bool params_ok(const rmusic_params& p) {
-    if (p.geometry == RMUSIC_GEOM_SQUARE) {
-        if (p.half_width < 1 || p.half_width > kMaxSquareLp) return false;
-    } else if (p.geometry == RMUSIC_GEOM_ROW) {
-        if (p.window_len < 2 || p.window_len > kMaxN) return false;
-        if (p.cov_order < 2 || p.cov_order > kMaxL || p.cov_order > p.window_len) return false;
-        if (p.forward_backward != 0 && p.forward_backward != 1) return false;
-        if (p.deriv_axis != 0 && p.deriv_axis != 1) return false;
-    } else {
-        return false;
-    }
-    if (p.carrier_axis != 0 && p.carrier_axis != 1) return false;
-    if (p.unwrap != 0 && p.unwrap != 1) return false;
-    if (p.raw_input != 0 && p.raw_input != 1) return false;
-    if (p.exhaustive != 0 && p.exhaustive != 1) return false;
-    if (p.raw_input && (p.geometry != RMUSIC_GEOM_ROW || p.deriv_axis != p.carrier_axis)) return false;
-    if (p.geometry == RMUSIC_GEOM_ROW && p.model_order >= p.cov_order) return false;
-    if (p.unwrap && p.geometry != RMUSIC_GEOM_SQUARE) return false;
-    if (!(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5)) return false;
-    if (!(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5)) return false;
-    if (!(p.band_cross >= 0.0 && p.band_cross < 0.5)) return false;
-    if (p.precision < RMUSIC_PLAIN_FP64 || p.precision > RMUSIC_FP32_BATCHED) return false;
-    if (p.max_sweeps < 0 || p.max_root_iters < 0) return false;
-    return true;
-}
-
 // Release a cached graph: its executable, its pinned frame table, and its timing events (kept for
 // later captures).
 void drop_graph(rmusic_ctx* ctx, GraphEntry& g) {
@@ -217,82 +307,7 @@ struct Plan {
     uint64_t gamma_elems = 0;
 };
 
-int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) {
-    const rmusic_params& p = ctx->p;
-    if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
-    const int pitch = d.pitch_elems == 0 ? d.width : d.pitch_elems;
-    if (pitch < d.width) return RMUSIC_EINVAL;
-    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16 && d.dtype != RMUSIC_DTYPE_C64)
-        return RMUSIC_EINVAL;
-    const int esz = d.dtype == RMUSIC_DTYPE_C64 ? 8 : d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2;
-    if (d.offset_bytes % esz) return RMUSIC_EINVAL;
-    const bool square = p.geometry == RMUSIC_GEOM_SQUARE;
-    int N, L;
-    if (square) {
-        // the paper's block: L holds the half-width Lp, N the block side 2 Lp + 1
-        L = p.half_width;
-        N = 2 * L + 1;
-        if (!square_supports(L)) return RMUSIC_EUNSUPPORTED;
-    } else {
-        N = d.window_len ? d.window_len : p.window_len;
-        L = d.cov_order ? d.cov_order : p.cov_order;
-        if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
-        if (p.precision == RMUSIC_FP32_BATCHED && (!batched_supports(L) || p.forward_backward != 1))
-            return RMUSIC_EUNSUPPORTED;
-    }
-    memset(F, 0, sizeof(*F));
-    F->in_off = d.offset_bytes;
-    F->out_off = d.out_offset;
-    F->H = d.height;
-    F->W = d.width;
-    F->pitch = pitch;
-    F->dtype = d.dtype;
-    F->N = N;
-    F->L = L;
-    F->carrier_axis = p.carrier_axis;
-    F->deriv_axis = square ? 0 : p.deriv_axis;  // the square block reads a row-major workspace
-    F->raw = p.raw_input && d.dtype != RMUSIC_DTYPE_C64;
-    F->geom = square ? kGeomSquare : kGeomRow;
-    F->nlines = p.carrier_axis == 0 ? d.height : d.width;
-    F->len = p.carrier_axis == 0 ? d.width : d.height;
-    if (F->len > kMaxLine) return RMUSIC_EUNSUPPORTED;
-    // kept band: 1 <= k < len/2 and |k/len - f0| < B (a contiguous run of bins)
-    const double f0 = p.carrier_freq;
-    const double B = p.band_halfwidth > 0.0 ? p.band_halfwidth : 0.5 * f0;
-    int klo = -1, nb = 0;
-    for (int k = 1; 2 * k < F->len; ++k) {
-        if (fabs((double)k / (double)F->len - f0) < B) {
-            if (klo < 0) klo = k;
-            ++nb;
-        }
-    }
-    F->k_lo = klo < 0 ? 1 : klo;
-    F->nb = nb;
-    if (p.band_cross > 0.0) {
-        // kept cross bins: signed k with |k| < B_c len across the carrier
-        const int lenc = p.carrier_axis == 0 ? d.height : d.width;
-        const double lim = p.band_cross * (double)lenc;
-        int kc = 0;
-        while ((double)(kc + 1) < lim) ++kc;
-        if (kc > kMaxCrossKc) return RMUSIC_EUNSUPPORTED;
-        F->cross_kc = kc;
-    }
-    F->wlines = F->deriv_axis == 0 ? d.height : d.width;
-    F->wlen = F->deriv_axis == 0 ? d.width : d.height;
-    F->f0 = f0;
-    if (square) {
-        F->nchunks = (d.width + kSqTX - 1) / kSqTX;  // tiles per tile row
-        F->omega_ref = 6.283185307179586476925 * f0;
-    } else {
-        F->nchunks = (F->wlen + kChunk - 1) / kChunk;
-        F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
-    }
-    // the solvers split a frame's work-item index with 32-bit arithmetic (far above any frame whose
-    // analytic signal fits a GPU)
-    const int64_t rows = square ? ((int64_t)d.height + kSqTY - 1) / kSqTY : (int64_t)F->wlines;
-    if (rows * (int64_t)F->nchunks >= (int64_t)1 << 31) return RMUSIC_EUNSUPPORTED;
-    return RMUSIC_OK;
-}
+int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) { return describe_frame(ctx->p, d, F); }
 
 // Bytes per pixel of the analytic-signal workspace: complex128 for the plain FP64 path.
 size_t gamma_elem_bytes(const rmusic_ctx* ctx) {
@@ -792,12 +807,7 @@ extern "C" {
 int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_bytes, rmusic_ctx** out) {
     if (!params || !out) return RMUSIC_EINVAL;
     *out = nullptr;
-    if (params->model_order < 1) return RMUSIC_EINVAL;
-    if (params->model_order > kMaxModelOrder) return RMUSIC_EUNSUPPORTED;
-    if (!params_ok(*params)) return RMUSIC_EINVAL;
-    if (params->model_order > 1 && params->precision == RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
-    if (params->geometry == RMUSIC_GEOM_SQUARE && params->precision != RMUSIC_FP32_BATCHED)
-        return RMUSIC_EUNSUPPORTED;
+    if (int rc = params_check(*params)) return rc;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();

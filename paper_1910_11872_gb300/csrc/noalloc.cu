@@ -25,6 +25,7 @@
 #include "../../include/rmusic.h"
 #include "rmusic_device.cuh"
 #include "rmusic_launch.h"
+#include "rmusic_validate.h"
 
 using namespace rmusic;
 
@@ -70,52 +71,6 @@ int scratch_address(int device, unsigned char** out) {
     return RMUSIC_OK;
 }
 
-// Frame-table entry of one descriptor for the FP32-batched path (same geometry as the regular
-// entry points: band bins, window lines, work items).
-int na_describe(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev* F) {
-    if (d.height < 1 || d.width < 1) return RMUSIC_EINVAL;
-    const int pitch = d.pitch_elems == 0 ? d.width : d.pitch_elems;
-    if (pitch < d.width) return RMUSIC_EINVAL;
-    if (d.dtype != RMUSIC_DTYPE_F32 && d.dtype != RMUSIC_DTYPE_U16 && d.dtype != RMUSIC_DTYPE_C64)
-        return RMUSIC_EINVAL;
-    if (d.offset_bytes % (d.dtype == RMUSIC_DTYPE_C64 ? 8 : d.dtype == RMUSIC_DTYPE_F32 ? 4 : 2))
-        return RMUSIC_EINVAL;
-    const int N = d.window_len ? d.window_len : p.window_len;
-    const int L = d.cov_order ? d.cov_order : p.cov_order;
-    if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
-    if (!batched_supports(L)) return RMUSIC_EUNSUPPORTED;
-    memset(F, 0, sizeof(*F));
-    F->in_off = d.offset_bytes;
-    F->out_off = d.out_offset;
-    F->H = d.height;
-    F->W = d.width;
-    F->pitch = pitch;
-    F->dtype = d.dtype;
-    F->N = N;
-    F->L = L;
-    F->carrier_axis = p.carrier_axis;
-    F->deriv_axis = p.deriv_axis;
-    F->nlines = p.carrier_axis == 0 ? d.height : d.width;
-    F->len = p.carrier_axis == 0 ? d.width : d.height;
-    if (F->len > kMaxLine) return RMUSIC_EUNSUPPORTED;
-    const double f0 = p.carrier_freq;
-    const double B = p.band_halfwidth > 0.0 ? p.band_halfwidth : 0.5 * f0;
-    int klo = -1, nb = 0;
-    for (int k = 1; 2 * k < F->len; ++k)
-        if (fabs((double)k / (double)F->len - f0) < B) {
-            if (klo < 0) klo = k;
-            ++nb;
-        }
-    F->k_lo = klo < 0 ? 1 : klo;
-    F->nb = nb;
-    F->wlines = p.deriv_axis == 0 ? d.height : d.width;
-    F->wlen = p.deriv_axis == 0 ? d.width : d.height;
-    F->nchunks = (F->wlen + kChunk - 1) / kChunk;
-    F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
-    F->f0 = f0;
-    return RMUSIC_OK;
-}
-
 }  // namespace
 
 extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int device, const void* d_frames,
@@ -123,15 +78,12 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
                                                 uint8_t* d_status, void* cuda_stream) {
     if (!params || n_frames < 0) return RMUSIC_EINVAL;
     const rmusic_params& p = *params;
-    if (p.model_order != 1) return p.model_order < 1 ? RMUSIC_EINVAL : RMUSIC_EUNSUPPORTED;
-    if (p.precision != RMUSIC_FP32_BATCHED || p.forward_backward != 1 || p.geometry != RMUSIC_GEOM_ROW ||
-        p.band_cross != 0.0 || p.raw_input != 0)
+    // the checks every entry point makes (the codes rmusic_create returns), then what this entry
+    // point adds: only the FP32-batched row-window path, without the 2-D band-pass or raw input
+    if (int rc = params_check(p)) return rc;
+    if (p.precision != RMUSIC_FP32_BATCHED || p.geometry != RMUSIC_GEOM_ROW || p.band_cross != 0.0 ||
+        p.raw_input != 0)
         return RMUSIC_EUNSUPPORTED;
-    if (p.window_len < 2 || p.window_len > kMaxN || p.cov_order < 2 || p.cov_order > kMaxL ||
-        p.cov_order > p.window_len || (p.deriv_axis != 0 && p.deriv_axis != 1) ||
-        (p.carrier_axis != 0 && p.carrier_axis != 1) || !(p.carrier_freq >= 0.0 && p.carrier_freq < 0.5) ||
-        !(p.band_halfwidth >= 0.0 && p.band_halfwidth < 0.5) || p.max_sweeps < 0 || p.max_root_iters < 0)
-        return RMUSIC_EINVAL;
     if (n_frames == 0) return RMUSIC_OK;
     if (!d_frames || !descs || !d_out) return RMUSIC_EINVAL;
     if (n_frames > kNaMaxFrames) return RMUSIC_ENOMEM;
@@ -141,7 +93,7 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
     FrameDev table[kNaMaxFrames];
     uint64_t pixels = 0;
     for (int i = 0; i < n_frames; ++i) {
-        int rc = na_describe(p, descs[i], &table[i]);
+        int rc = describe_frame(p, descs[i], &table[i]);
         if (rc) return rc;
         pixels += (uint64_t)table[i].H * (uint64_t)table[i].W;
     }

@@ -3,15 +3,20 @@ inputs, element by element.
 
 Tolerances (rad/pixel):
   * plain FP64 path: |gpu - oracle| <= 1e-9 on every valid pixel, identical status maps;
-  * FP32 paths on noise-free inputs: |gpu - oracle| <= 1e-4 on every valid pixel;
-  * FP32 paths under noise: the RMS error against the closed-form derivative is within 1 % of the
-    oracle's RMS error (interior pixels), and the element-wise differences are reported.
+  * FP32-batched path, noise-free and noisy inputs alike: identical status maps and
+    |gpu - oracle| <= 1e-4 on every pixel both call ok, except pixels the oracle's own roots show to
+    be near ties at FP32 resolution (tests/parity.py; counted, at most 1e-4 of the pixels);
+  * FP32 paths under noise, in addition: the RMS error against the closed-form derivative is within
+    1 % of the oracle's RMS error (interior pixels).
 """
 import numpy as np
 import pytest
 
 import oracle as O
+import parity
 from paper_1910_11872_gb300 import rmusic, synth
+
+TOL = 1e-4  # rad/pixel: the FP32-batched path against the FP64 oracle, with or without noise
 
 pytestmark = pytest.mark.gpu
 
@@ -57,11 +62,6 @@ def oracle_run(img, N=32, L=8, fb=1, deriv_axis=0, carrier_axis=0, f0=0.1):
     return out, st
 
 
-def _cmp_exact_status(st_gpu, st_orc):
-    # border pixels are decided by integer geometry: identical
-    assert np.array_equal(st_gpu == 1, st_orc == 1)
-
-
 # ------------------------------------------------------------------------------------------------
 # plain FP64 path == oracle to 1e-9
 # ------------------------------------------------------------------------------------------------
@@ -102,11 +102,10 @@ def test_batched_noise_free_within_1e4(f0):
     fr = synth.peaks_frame(np.inf, f0, H=48, W=384)
     (g, gs), = run_gpu([fr.image], carrier_freq=f0)
     o, os_ = oracle_run(fr.image, f0=f0)
-    _cmp_exact_status(gs, os_)
-    v = (os_ == 0) & (gs == 0)
-    assert v.sum() == (os_ == 0).sum()
+    assert np.array_equal(gs, os_)
+    v = os_ == 0
     err = np.abs(g[v].astype(np.float64) - o[v])
-    assert err.max() <= 1e-4, f"max {err.max():.3e} p99.9 {np.quantile(err, 0.999):.3e}"
+    assert err.max() <= TOL, f"max {err.max():.3e} p99.9 {np.quantile(err, 0.999):.3e}"
 
 
 @pytest.mark.parametrize("snr", [40, 20, 10, 5])
@@ -114,15 +113,11 @@ def test_batched_noisy_rms_within_one_percent(snr):
     fr = synth.peaks_frame(snr, 0.1, H=64, W=384)
     (g, gs), = run_gpu([fr.image])
     o, os_ = oracle_run(fr.image)
-    _cmp_exact_status(gs, os_)
+    parity.check(g, gs, o, os_, TOL, parity.Window(fr.image, 32, 8, 1, 0, 0, 0.1), what=f"{snr} dB")
     inner = np.zeros_like(os_, dtype=bool)
     inner[:, 32:-32] = True
     v = inner & (os_ == 0) & (gs == 0)
-    rms_o = np.sqrt(np.mean((o[v] - fr.truth[v]) ** 2))
-    rms_g = np.sqrt(np.mean((g[v].astype(np.float64) - fr.truth[v]) ** 2))
-    assert abs(rms_g - rms_o) <= 0.01 * rms_o, f"rms gpu {rms_g:.5e} oracle {rms_o:.5e}"
-    d = np.abs(g[v].astype(np.float64) - o[v])
-    assert np.quantile(d, 0.999) < 1e-3
+    parity.rms_check(g, o, fr.truth, v, what=f"{snr} dB")
 
 
 @pytest.mark.parametrize("N,L", [(8, 2), (16, 4), (24, 6), (48, 12), (40, 10), (33, 8)])
@@ -130,20 +125,17 @@ def test_batched_windows(N, L):
     fr = synth.peaks_frame(np.inf, 0.1, H=24, W=256)
     (g, gs), = run_gpu([fr.image], window_len=N, cov_order=L)
     o, os_ = oracle_run(fr.image, N, L)
-    _cmp_exact_status(gs, os_)
-    v = (os_ == 0) & (gs == 0)
-    assert v.sum() == (os_ == 0).sum()
-    assert np.abs(g[v].astype(np.float64) - o[v]).max() <= 1e-4
+    assert np.array_equal(gs, os_)
+    v = os_ == 0
+    assert np.abs(g[v].astype(np.float64) - o[v]).max() <= TOL
     fr = synth.peaks_frame(10, 0.1, H=24, W=256)
     (g, gs), = run_gpu([fr.image], window_len=N, cov_order=L)
     o, os_ = oracle_run(fr.image, N, L)
+    parity.check(g, gs, o, os_, TOL, parity.Window(fr.image, N, L, 1, 0, 0, 0.1), what=f"N={N} L={L} 10 dB")
     v = (os_ == 0) & (gs == 0)
     inner = np.zeros_like(v)
     inner[:, 32:-32] = True
-    v &= inner
-    rms_o = np.sqrt(np.mean((o[v] - fr.truth[v]) ** 2))
-    rms_g = np.sqrt(np.mean((g[v].astype(np.float64) - fr.truth[v]) ** 2))
-    assert abs(rms_g - rms_o) <= 0.01 * rms_o
+    parity.rms_check(g, o, fr.truth, v & inner, what=f"N={N} L={L}")
 
 
 def test_batched_deriv_y_uint16_diffusion():
@@ -152,15 +144,11 @@ def test_batched_deriv_y_uint16_diffusion():
     res = run_gpu([f.image for f in frames], deriv_axis=1)
     for fr, (g, gs) in zip(frames, res):
         o, os_ = oracle_run(fr.image, deriv_axis=1)
-        _cmp_exact_status(gs, os_)
+        parity.check(g, gs, o, os_, TOL, parity.Window(fr.image, 32, 8, 1, 1, 0, 0.1), what="diffusion")
         v = (os_ == 0) & (gs == 0)
-        assert v.sum() == (os_ == 0).sum()
         inner = np.zeros_like(v)
         inner[:, 16:-16] = True
-        vi = v & inner
-        rms_o = np.sqrt(np.mean((o[vi] - fr.truth[vi]) ** 2))
-        rms_g = np.sqrt(np.mean((g[vi].astype(np.float64) - fr.truth[vi]) ** 2))
-        assert abs(rms_g - rms_o) <= 0.01 * rms_o
+        parity.rms_check(g, o, fr.truth, v & inner, what="diffusion")
 
 
 def test_batched_carrier_along_y():
@@ -168,9 +156,9 @@ def test_batched_carrier_along_y():
     img = np.ascontiguousarray(fr.image.T)
     (g, gs), = run_gpu([img], deriv_axis=1, carrier_axis=1)
     o, os_ = oracle_run(img, deriv_axis=1, carrier_axis=1)
-    _cmp_exact_status(gs, os_)
-    v = (os_ == 0) & (gs == 0)
-    assert np.abs(g[v].astype(np.float64) - o[v]).max() <= 1e-4
+    assert np.array_equal(gs, os_)
+    v = os_ == 0
+    assert np.abs(g[v].astype(np.float64) - o[v]).max() <= TOL
 
 
 def test_uneven_batch_alone_equals_mix():
@@ -190,7 +178,7 @@ def test_uneven_batch_alone_equals_mix():
         assert np.array_equal(np.isnan(g), np.isnan(ga))
         assert np.array_equal(g[~np.isnan(g)], ga[~np.isnan(ga)])
         o, os_ = oracle_run(f, w[0], w[1])
-        _cmp_exact_status(gs, os_)
+        parity.check(g, gs, o, os_, TOL, parity.Window(f, w[0], w[1], 1, 0, 0, 0.1), what=f"{f.shape} {w}")
 
 
 @pytest.mark.parametrize("H,W", [(1, 64), (3, 31), (5, 33), (2, 1), (4, 20), (7, 97)])
@@ -200,11 +188,8 @@ def test_edge_shapes(H, W):
     for prec in ("batched", "plain_fp64"):
         (g, gs), = run_gpu([img], window_len=16, cov_order=4, precision=prec)
         o, os_ = oracle_run(img, 16, 4)
-        _cmp_exact_status(gs, os_)
-        v = (os_ == 0) & (gs == 0)
-        if v.any():
-            tol = 1e-9 if prec == "plain_fp64" else 5e-3
-            assert np.abs(g[v].astype(np.float64) - o[v]).max() <= tol + 1e-7
+        tol = 1e-9 + 1e-7 if prec == "plain_fp64" else TOL  # 1e-7: the float32 map's rounding
+        parity.check(g, gs, o, os_, tol, parity.Window(img, 16, 4, 1, 0, 0, 0.1), what=f"{H}x{W} {prec}")
 
 
 def test_zero_frame_is_degenerate():
@@ -373,11 +358,8 @@ def test_full_size_frame_sampled_against_oracle():
         xs = np.concatenate([rng.integers(0, 1024, 600), rng.integers(0, 1024, 80)])
         xs[:20] = np.arange(20) + 10  # around the left border
         o, os_, _ = O.demodulate_pixels(fr.image, O.make_params(32, 8, 1, 0, 0, 0.1), ys, xs)
-        assert np.array_equal(gs[ys, xs] == 1, os_ == 1)
-        v = (os_ == 0) & (gs[ys, xs] == 0)
-        d = np.abs(g[ys, xs][v].astype(np.float64) - o[v])
-        tol = 1e-4 if np.isinf(snr) else 1e-3
-        assert d.max() <= tol, f"snr {snr}: max {d.max():.3e}"
+        parity.check(g[ys, xs], gs[ys, xs], o, os_, TOL, parity.Window(fr.image, 32, 8, 1, 0, 0, 0.1), ys, xs,
+                     what=f"1024^2 at {snr} dB")
 
 
 def test_plain_fp32_and_polish64_accuracy():
@@ -430,15 +412,11 @@ def test_diffusion_stack_full_frames_one_launch_sampled():
         rows = np.arange(r0, r0 + 24)                   # near the diffusion front
         cols = np.sort(rng.choice(1024, 40, replace=False))
         ys, xs, vals, st = _sampled_oracle(fr, 32, 8, 1, rows, cols)
-        assert np.array_equal(gs[ys, xs] == 1, st == 1)
+        parity.check(g[ys, xs], gs[ys, xs], vals, st, TOL, parity.Window(fr.image, 32, 8, 1, 1, 0, 0.1), ys, xs,
+                     what=f"diffusion frame {ts[i]}")
         v = (st == 0) & (gs[ys, xs] == 0)
-        assert v.sum() > 0.9 * (st == 0).sum()
-        d = np.abs(g[ys, xs][v].astype(np.float64) - vals[v])
-        assert np.quantile(d, 0.999) < 1e-3 and d.max() < 5e-3, f"frame {ts[i]}: max {d.max():.3e}"
         # accuracy against the closed-form derivative equals the oracle's
-        rms_g = np.sqrt(np.mean((g[ys, xs][v] - fr.truth[ys, xs][v]) ** 2))
-        rms_o = np.sqrt(np.mean((vals[v] - fr.truth[ys, xs][v]) ** 2))
-        assert abs(rms_g - rms_o) <= 0.01 * rms_o + 1e-6
+        parity.rms_check(g[ys, xs], vals, fr.truth[ys, xs], v, what=f"diffusion frame {ts[i]}")
 
 
 def test_uneven_batch_full_sizes_one_launch_sampled():
@@ -449,16 +427,24 @@ def test_uneven_batch_full_sizes_one_launch_sampled():
     res = run_gpu([f.image for f in frames], windows=windows)
     rng = np.random.default_rng(5)
     worst = 0.0
+    gv, ov, tv = [], [], []
     for fr, (g, gs) in zip(frames, res):
         H, W = fr.image.shape
         rows = [int(rng.integers(0, H))]
         cols = np.sort(rng.choice(W, min(W, 24), replace=False))
         ys, xs, vals, st = _sampled_oracle(fr, fr.window_len, fr.cov_order, 0, rows, cols)
-        assert np.array_equal(gs[ys, xs] == 1, st == 1)
+        rep = parity.check(g[ys, xs], gs[ys, xs], vals, st, TOL,
+                           parity.Window(fr.image, fr.window_len, fr.cov_order, 1, 0, 0, fr.carrier_freq), ys, xs,
+                           what=f"{H}x{W} N={fr.window_len} L={fr.cov_order}")
+        worst = max(worst, rep["max"])
         v = (st == 0) & (gs[ys, xs] == 0)
-        if v.any():
-            worst = max(worst, float(np.abs(g[ys, xs][v].astype(np.float64) - vals[v]).max()))
-    assert worst < 5e-3, worst
+        gv.append(g[ys, xs][v])
+        ov.append(vals[v])
+        tv.append(fr.truth[ys, xs][v])
+    assert worst <= TOL, worst
+    # accuracy against the closed-form derivative over every sampled pixel equals the oracle's
+    g_all, o_all, t_all = np.concatenate(gv), np.concatenate(ov), np.concatenate(tv)
+    parity.rms_check(g_all, o_all, t_all, np.ones(g_all.size, bool), what="uneven batch")
 
 
 def test_autotune_variants_identical_and_cached(tmp_path, monkeypatch):
