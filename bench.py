@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--square-steps", type=int, default=5,
                     help="timed steps of the paper-geometry leg (square block, both derivatives and alpha)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other workloads (Gaussian-bump plain FP64, diffusion stack, uneven batch, serving)")
+    ap.add_argument("--diffusion-frames", type=int, default=500)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
 
 
@@ -519,6 +523,9 @@ def run_ours(args):
             "speedup_vs_plain": value / plain_value}
     if sq is not None:
         line["paper_geometry"] = sq
+    if not args.no_workloads:
+        line["workloads"] = run_workloads(args, dev, stream, flush,
+                                          cpu=rank == 0 and world == 1 and not args.no_cpu_baseline)
 
     # ---- CPU oracle on a bounded sample, and the GPU error against it -----------------------
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -645,6 +652,145 @@ def run_square_leg(args, rank, world, dev, stream, flush):
         res["oracle_sample"] = f"256 random pixels of each frame ({256 * len(frames)} px)"
     dem.close()
     return res
+
+
+# ----------------------------------------------------------------------------------------------
+# The other workloads: Gaussian bump (plain FP64 vs the oracle), diffusion stack, uneven batch,
+# serving. Each is timed on the GPU with its own clock record; the oracle is timed on a bounded
+# sample of each and gives the GPU maps' error on that sample.
+# ----------------------------------------------------------------------------------------------
+def _oracle_compare(g, s, vals, st, truth=None):
+    """Agreement of GPU values/statuses with the oracle's on the same pixels."""
+    g = np.asarray(g, dtype=np.float64)
+    both = (st == 0) & (s == 0)
+    d = np.abs((g[both] - vals[both] + np.pi) % (2 * np.pi) - np.pi)
+    res = {"pixels": int(st.size), "status_equal": bool(np.array_equal(s, st)),
+           "status_differ": int((s != st).sum()), "max_abs_rad_px": float(d.max()) if d.size else 0.0,
+           "p999_rad_px": float(np.quantile(d, 0.999)) if d.size else 0.0}
+    if truth is not None and both.any():
+        rms_o = float(np.sqrt(np.mean((vals[both] - truth[both]) ** 2)))
+        rms_g = float(np.sqrt(np.mean((g[both] - truth[both]) ** 2)))
+        res.update({"rms_vs_truth_gpu": rms_g, "rms_vs_truth_oracle": rms_o,
+                    "rms_rel_diff": abs(rms_g - rms_o) / rms_o if rms_o > 0 else 0.0})
+    return res
+
+
+def run_workloads(args, dev, stream, flush, cpu: bool):
+    import torch
+
+    import oracle as O
+    from paper_1910_11872_gb300 import config_bench, rmusic, serve_bench
+
+    out = {}
+    # ---- Gaussian bump 128 x 128: plain FP64 GPU path vs the FP64 oracle, whole frame --------
+    fr = synth.small_gaussian_frame()
+    x = torch.from_numpy(fr.image).to(dev)
+    dem = rmusic.Demodulator(device=dev.index, precision="plain_fp64")
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for _ in range(3):
+        g1, s1, _ = dem.run(x)
+    ms = []
+    for _ in range(10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dem.run(x, out=g1, status=s1, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    dem.close()
+    res = {"workload": "Gaussian bump 1 x 128x128 float32, noise 0.02, N=32, L=8, plain FP64 GPU path",
+           "value": fr.image.size / statistics.median(ms) / 1e3, "unit": "Mpixel/s",
+           "ms_per_call": statistics.median(ms), "timing": "3 warm-ups, median of 10 event-timed calls",
+           "clocks": clk}
+    if cpu:
+        t0 = time.perf_counter()
+        o, ost, cores = O.demodulate(fr.image, O.make_params(N_WIN, L_COV, 1, 0, 0, F0))
+        dt = time.perf_counter() - t0
+        res["vs_fp64_oracle"] = _oracle_compare(g1.cpu().numpy(), s1.cpu().numpy(), o.ravel(), ost.ravel())
+        res["cpu_baseline"] = {"value": fr.image.size / dt / 1e6, "unit": "Mpixel/s", "cores": cores,
+                               "kind": "oracle", "sample": f"the whole frame ({fr.image.size} px), {dt:.2f} s wall"}
+    out["gaussian_bump_plain_fp64"] = res
+    del x, g1, s1
+
+    # ---- diffusion time-lapse: 500 x 1024^2 uint16 in one call, column windows ----------------
+    stack = config_bench.diffusion_stack(args.diffusion_frames)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    res, dmaps, dst = config_bench.run_diffusion(stack, flush)
+    res["clocks"] = clocks.stop()
+    if cpu:
+        rng = np.random.default_rng(11875)
+        T = stack.shape[0]
+        ts = sorted({0, T // 3, (2 * T) // 3, T - 1})
+        comp, npx, dt, cores = [], 0, 0.0, 0
+        p = O.make_params(N_WIN, L_COV, 1, 1, 0, F0)
+        for t in ts:
+            fr = synth.diffusion_frame(int(t), T=T)
+            r0 = int(rng.integers(380, 580))
+            rows = np.arange(r0, r0 + 64)  # 64 rows through the diffusion front, every column
+            ys = np.repeat(rows, W).astype(np.int32)
+            xs = np.tile(np.arange(W), rows.size).astype(np.int32)
+            t0 = time.perf_counter()
+            vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
+            dt += time.perf_counter() - t0
+            npx += ys.size
+            g = dmaps[t].cpu().numpy()[ys, xs]
+            s_ = dst[t].cpu().numpy()[ys, xs]
+            comp.append((g, s_, vals, st, fr.truth[ys, xs]))
+        cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
+        res["vs_fp64_oracle"] = _oracle_compare(*cat)
+        res["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                               "sample": f"64 rows through the front, all columns, of frames {ts} ({npx} px), "
+                                         f"{dt:.1f} s wall"}
+    out["diffusion_stack"] = res
+    del dmaps, dst, stack
+    torch.cuda.empty_cache()
+
+    # ---- uneven batch: 64 frames of uneven sizes and windows in one call ------------------------
+    frames = synth.uneven_batch()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    res, umaps, ust, shapes = config_bench.run_uneven(frames, flush)
+    res["clocks"] = clocks.stop()
+    if cpu:
+        rng = np.random.default_rng(11876)
+        gm, sm = umaps.cpu().numpy(), ust.cpu().numpy()
+        offs = np.cumsum([0] + [h * w for h, w in shapes])
+        comp, npx, dt, cores = [], 0, 0.0, 0
+        for i in sorted(rng.choice(len(frames), 8, replace=False)):
+            fr = frames[i]
+            Hf, Wf = fr.image.shape
+            rows = np.sort(rng.choice(Hf, 16, replace=False))
+            ys = np.repeat(rows, Wf).astype(np.int32)
+            xs = np.tile(np.arange(Wf), rows.size).astype(np.int32)
+            p = O.make_params(fr.window_len, fr.cov_order, 1, 0, 0, fr.carrier_freq)
+            t0 = time.perf_counter()
+            vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
+            dt += time.perf_counter() - t0
+            npx += ys.size
+            g = gm[offs[i]:offs[i + 1]].reshape(Hf, Wf)[ys, xs]
+            s_ = sm[offs[i]:offs[i + 1]].reshape(Hf, Wf)[ys, xs]
+            comp.append((g, s_, vals, st, fr.truth[ys, xs]))
+        cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
+        res["vs_fp64_oracle"] = _oracle_compare(*cat)
+        res["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                               "sample": f"16 random full rows of each of 8 random frames ({npx} px), {dt:.1f} s wall"}
+    out["uneven_batch"] = res
+    del umaps, ust
+    torch.cuda.empty_cache()
+
+    # ---- serving: 16 camera streams, Poisson arrivals at 2000 frames/s ---------------------------
+    sargs = argparse.Namespace(streams=16, rate=2000.0, seconds=args.serve_seconds, pool=2, ring_depth=4,
+                               max_batch_frames=32, max_batch_mpx=32, inflight=3, budget_gb=64.0, device=dev.index)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    res = serve_bench.run(sargs)
+    res["clocks"] = clocks.stop()
+    res["shed_frac"] = res["frames_rejected"] / max(res["frames_offered"], 1)
+    out["serving"] = res
+    return out
 
 
 def main():

@@ -22,21 +22,33 @@ from . import rmusic, serve, synth
 SIZES = (512, 1024, 1536, 2048)
 
 
-def make_streams(n: int, pool: int, seed: int = 11876):
-    """Per stream: (H, W, pinned uint16 frames (pool x H x W), phase-derivative truth)."""
+def _stream_frame(job):
+    t, side, s = job
+    return synth.diffusion_frame(t, H=side, W=side, seed_index=4 + 100 * s).image
+
+
+def make_streams(n: int, pool: int, seed: int = 11876, workers: int = 0):
+    """Per stream: (H, W, pinned uint16 frames (pool x H x W)). The frames are drawn in spawned
+    processes (the same seeded frames as drawing them one by one)."""
+    import multiprocessing as mp
+    import os
+
     import torch
 
     rng = np.random.default_rng(seed)
-    out = []
+    jobs, sides = [], []
     for s in range(n):
         side = int(rng.choice(SIZES))
-        frames = []
+        sides.append(side)
         for k in range(pool):
-            t = int(rng.integers(0, 500))
-            fr = synth.diffusion_frame(t, H=side, W=side, seed_index=4 + 100 * s)
-            frames.append(fr.image)
-        stack = torch.from_numpy(np.stack(frames).view(np.int16)).pin_memory()
-        out.append((side, side, stack))
+            jobs.append((int(rng.integers(0, 500)), side, s))
+    workers = workers or min(16, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(workers) as p:
+        imgs = p.map(_stream_frame, jobs)
+    out = []
+    for s in range(n):
+        stack = torch.from_numpy(np.stack(imgs[s * pool:(s + 1) * pool]).view(np.int16)).pin_memory()
+        out.append((sides[s], sides[s], stack))
     return out
 
 
