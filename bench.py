@@ -109,22 +109,35 @@ def schur_cohn_flops(L: int) -> float:
     return 3 * (n + 1) + sum(15 + 8 * d for d in range(1, n + 1)) + n
 
 
+def rouche_flops(L: int) -> float:
+    """The Rouche certificate of the selected root (degree n = 2L - 2): the rotation e^k and the
+    rotated coefficients c_k e^k (2L - 3 complex products, 6 each), the division by the real
+    quadratic (n - 1 steps: two multiply-adds and two subtractions, 6) with the weighted distance to
+    the noise-free polynomial (difference, two magnitudes and the Horner step in rho, 5), the
+    remainder and its bounds (20) and the table test (6)."""
+    n = 2 * L - 2
+    return 6 * (2 * L - 3) + 11 * (n - 1) + 26
+
+
 def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float, power_steps: float = 0.0,
                     eig_fallback: float = 0.0, newton: float = 0.0, root_fallback: float = 0.0,
-                    polish: float = 2.0) -> float:
+                    polish: float = 2.0, pixels_per_lane: int = 8) -> float:
     """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1),
-    counted from the kernel's steps with the measured work per 32-pixel work item (power steps,
+    counted from the kernel's steps with the measured work per 32-pixel group (power steps,
     Jacobi sweeps and fallbacks, Newton steps, Aberth evaluations, updates and fallbacks):
-      covariance  per lag: (31 + N) / 32 lag products (6) and prefix adds (2) per pixel, a 5-step
-                  warp scan (10); per R_f entry: box difference (2) and accumulation into S (6)
+      covariance  per rank-2 term: the folded snapshot (4 L adds) and X X^T + Y Y^T on the packed
+                  triangle (L signs, 2 multiply-adds per entry); a lane of P pixels runs K terms for its
+                  first pixel and 2 per further pixel, (K + 2 (P - 1)) / P per pixel; trace and scaling
       power it.   start column and Frobenius norm; per step S x (2 L^2), Rayleigh quotient, shift,
                   norm and the step size (10 L + 5)
       fallback    Jacobi: per rotation 14 + 6 (L - 2) + 4, L/2 rotations per step, L - 1 steps per
                   sweep, plus the off-diagonal norm L (L - 1); inverse iteration: L D L^T of
                   (mu I - S), two forward / diagonal / backward solves with norms
       polynomial  u = Q x (2 L), rho_k (8 flops per term), scaling and moduli
-      roots       Newton steps (newton_flops), the Schur-Cohn certificate (schur_cohn_flops); Aberth
-                  fallback: aberth_flops per executed evaluation and update, starting points, selection
+      roots       Newton steps (newton_flops), the Rouche certificate (rouche_flops; the Schur-Cohn
+                  count that decides where it does not, measured in 0.2 % of the lanes of the bench
+                  workload, is not counted); Aberth fallback: aberth_flops per executed evaluation and
+                  update, starting points, selection
       polish      per measured step Horner on Q and Q' (16 per degree) and the deflated step (37);
                   angle (20); warps holding a split double root also form Q'' (not counted: rare on
                   noisy frames)
@@ -132,14 +145,15 @@ def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float,
     NS = L * (L + 1) // 2
     NR = 2 * L - 2
     NI = L - 1
-    cov = L * ((31 + N) / 32 * 8 + 10) + NS * 8 + L + NS + 1
+    K, P = N - L + 1, pixels_per_lane
+    cov = (K + 2 * (P - 1)) / P * (4 * L + L + 4 * NS) + L + NS + 1
     power = 2 * L + 3 * NS + 3 * L + 1 + power_steps * (2 * L * L + 10 * L + 5)
     rot = 14 + 6 * (L - 2) + 4
     jac = sweeps * ((L - 1) * (L // 2) * rot + L * (L - 1))
     ldl = sum(3 * j + 1 + (L - 1 - j) * (3 * j + 1) for j in range(L))
     inv = eig_fallback * (ldl + 2 * (2 * L * (L - 1) + 4 * L))
     coef = 2 * L + 3 * L + 4 * L * (L - 1) + 5 * (L - 1)
-    roots = newton * newton_flops(L) + schur_cohn_flops(L)
+    roots = newton * newton_flops(L) + rouche_flops(L)
     aberth = aberth_flops(L, evals, updates) + root_fallback * (NI * 10 + 20 + 13 * NI)
     polish = polish * (16 * NR + 37) + 20
     return cov + power + jac + inv + coef + roots + aberth + polish

@@ -119,8 +119,10 @@ extern "C" {
  *                    the line's mean (for model_order 2 or 3). Needs the row geometry with
  *                    deriv_axis == carrier_axis (the carrier decides which of +-omega is meant).
  *   exhaustive       batched path: 0 (default) finds the selected root by Newton's method and
- *                    certifies it with a Schur-Cohn root count (every root is computed only where
- *                    the certificate fails), and the row geometry's eigenvector by power iteration
+ *                    certifies it with a root count -- in the row geometry by Rouche's theorem
+ *                    against the noise-free polynomial, with the Schur-Cohn count where that test
+ *                    does not decide; in the square geometry by the Schur-Cohn count -- (every root is
+ *                    computed only where the certificate fails), and the row geometry's eigenvector by power iteration
  *                    (Jacobi sweeps only where it does not settle); 1 computes every inner root by
  *                    Aberth-Ehrlich and, in the row geometry, runs the Jacobi sweeps for every
  *                    pixel. Both select the same root; 1 is slower.
@@ -196,8 +198,8 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
  *   d_status  device uint8 buffer laid out like d_out, or NULL.
  *   cuda_stream  cudaStream_t (as void*) on which all work is queued.
  * Errors: RMUSIC_EINVAL (NULL pointers with n_frames > 0, a bad descriptor, unsupported
- * (N, L) for the path), RMUSIC_EUNSUPPORTED (a frame of 2^31 or more 32-pixel work items, about
- * 6.9e10 pixels: far beyond what fits a GPU), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a
+ * (N, L) for the path), RMUSIC_EUNSUPPORTED (a frame of 2^31 or more 256-pixel work items, about
+ * 5.5e11 pixels: far beyond what fits a GPU), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a
  * no-op. */
 int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
                              int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream);
@@ -343,23 +345,24 @@ int rmusic_checked_build(void);
  *   graph_replayed   1 if the last call replayed a cached CUDA graph.
  *   workspace_bytes  device bytes the context currently holds.
  *   pixels           pixels of all frames of the last call.
- *   mean_sweeps      batched path: Jacobi sweeps per 32-pixel work item, averaged (the eigen
- *                    fallback's; 0 where the power iteration sufficed).
- *   mean_root_iters  batched path: Aberth iterations per 32-pixel work item, averaged (the root
+ *   mean_sweeps      batched path: Jacobi sweeps per 32-pixel group (the 32 pixels a warp solves
+ *                    together: one per lane), averaged (the eigen fallback's; 0 where the power
+ *                    iteration sufficed).
+ *   mean_root_iters  batched path: Aberth iterations per 32-pixel group, averaged (the root
  *                    fallback's; 0 where the Newton root was certified in every lane).
- *   mean_root_updates batched path: Aberth root updates a warp executed per work item, averaged
+ *   mean_root_updates batched path: Aberth root updates a warp executed per 32-pixel group, averaged
  *                    (roots already converged in every lane of the warp are skipped).
- *   mean_root_evals  batched path: Aberth evaluations of Q and Q' a warp executed per work item,
+ *   mean_root_evals  batched path: Aberth evaluations of Q and Q' a warp executed per 32-pixel group,
  *                    averaged (a root frozen in every lane of the warp is not evaluated).
- *   mean_power_steps row geometry: power-iteration steps per work item, averaged.
- *   eig_fallback_frac row geometry: fraction of work items whose warp ran the Jacobi fallback.
- *   mean_newton_steps batched path: Newton steps of the signal root per work item, averaged.
- *   root_fallback_frac batched path: fraction of work items whose warp ran the Aberth fallback.
- *   mean_polish_steps batched path: polish steps of the selected root per work item, averaged.
+ *   mean_power_steps row geometry: power-iteration steps per 32-pixel group, averaged.
+ *   eig_fallback_frac row geometry: fraction of 32-pixel groups whose warp ran the Jacobi fallback.
+ *   mean_newton_steps batched path: Newton steps of the signal root per 32-pixel group, averaged.
+ *   root_fallback_frac batched path: fraction of 32-pixel groups whose warp ran the Aberth fallback.
+ *   mean_polish_steps batched path: polish steps of the selected root per 32-pixel group, averaged.
  *   check_violations  batched path, checked builds only (rmusic_checked_build() == 1): index
  *                    tests of the solvers that failed in the last call (each skips its work item
  *                    instead of faulting; 0 is the only acceptable value). Always 0 otherwise.
- *   In the square geometry a work item is one warp's 32 pixels of a tile row, mean_sweeps counts
+ *   In the square geometry a 32-pixel group is one warp's 32 pixels of a tile row, mean_sweeps counts
  *   power-iteration steps, and the root figures add both polynomials (root_fallback_frac up to 2,
  *   mean_polish_steps counts both).
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the

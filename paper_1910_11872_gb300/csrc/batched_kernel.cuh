@@ -1,19 +1,22 @@
 // batched.cu -- the FP32 batched path: one persistent kernel over every pixel of every frame of
-// a call (frames of uneven sizes and windows mixed), one pixel per lane, one 32-pixel run of a
-// window line per warp work item, items taken from a global atomic counter.
+// a call (frames of uneven sizes and windows mixed), one window-line run of kRowRun = 32 kRowP
+// consecutive pixels per warp work item, kRowP consecutive pixels per lane, items taken from a
+// global atomic counter.
 //
-// Per warp item (32 consecutive pixels of one window line):
-//   stage     the 31 + N analytic-signal samples the 32 windows cover, one coalesced read into
-//             shared memory (Sec. 3, Eq. 2: the moving window)
-//   R_f       every entry R_f[m][m+d] = (1/K) sum_{i<K} w[i+m] conj(w[i+m+d]) is a box sum of
-//             the lag-d product sequence g_d[j] = Gamma[j] conj(Gamma[j+d]); per lag d the warp
-//             forms g_d once for the run, takes its prefix sums with a warp scan and reads
-//             R_f[m][m+d] = (P_d[t+m+K] - P_d[t+m]) / K (Eq. 4-5). The scan starts at the run's
-//             fixed absolute position, so each pixel's arithmetic does not depend on how frames
-//             are batched or scheduled.
-//   FB -> S   with forward-backward averaging R = (R_f + J conj(R_f) J)/2 is centro-Hermitian,
+// Per warp item (a run of one window line; lane l owns pixels l kRowP .. l kRowP + kRowP - 1):
+//   stage     the kRowRun + N - 1 analytic-signal samples the run's windows cover, one coalesced
+//             read into shared memory (Sec. 3, Eq. 2: the moving window), padded by one sample
+//             every kRowP so that the lanes' strided reads fall in distinct banks
+//   S         with forward-backward averaging R = (R_f + J conj(R_f) J)/2 is centro-Hermitian,
 //             so with the unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) (even L) S = Q^H R Q =
-//             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x.
+//             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x. Written out,
+//             S = sum over the window's K = N - L + 1 snapshots s_j (Eq. 4-5) of X_j X_j^T + Y_j Y_j^T
+//             with the real L-vectors X_j = [Re p, Im q], Y_j = [Im p, -Re q] of the folded snapshot
+//             p_i = s_j[i] + s_j[L-1-i], q_i = s_j[i] - s_j[L-1-i] (i < L/2). A lane sums the K rank-2
+//             terms of its first pixel's window (its anchor, at an absolute position of the line) and
+//             moves to each next pixel by one sliding update: + the entering snapshot's rank-2 term
+//             - the leaving one's (4 L(L+1)/2 multiply-adds). Anchors sit at fixed positions, so
+//             each pixel's arithmetic does not depend on how frames are batched or scheduled.
 //   eigen     the signal eigenvector x1 of S (Eq. 8-11) by the shifted power iteration, from the
 //             column of S with the largest diagonal entry (2-3 steps on signal-dominated windows);
 //             lanes whose iteration does not settle or whose eigen-gap is not certified by the
@@ -39,8 +42,14 @@ namespace rmusic {
 
 constexpr int kBatWarps = 4;
 constexpr int kBatThreads = kBatWarps * 32;
-constexpr int kLagBlock = 4;      // lags whose prefix sums are held in shared memory at once
-constexpr int kPreLen = 3 * 32 + 1;  // prefix sums of one lag over a warp item (3 products per lane)
+static_assert(kRowP == 8, "the staging pads one sample every 8 (shift by 3)");
+// staged samples of one run: kRowRun + N - 1 <= kRowRun + kMaxN - 1, plus one pad every kRowP
+constexpr int kSegLen = kRowRun + kMaxN + (kRowRun + kMaxN) / kRowP;
+
+// Shared-memory slot of staged sample e of a run (one pad slot after every kRowP samples): lane l's
+// sample i is e = l kRowP + i at 9 l + i + i / 8, so 32 lanes reading their own sample i touch 32
+// consecutive 9-strided slots -- distinct banks.
+__device__ __forceinline__ int seg_slot(int e) { return e + (e >> 3); }
 
 __host__ __device__ constexpr int tri(int r, int c, int L) {
     return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);
@@ -89,11 +98,11 @@ __device__ __forceinline__ void accumulate_s(float* S, int r, int s, cx<float> v
 // diagonal block (shuffled from the two lanes that hold it), then relabels rows and columns by
 // tperm (shuffles from the source lanes). The stopping rule is the thread-per-matrix one, applied
 // per matrix. Returns, in the caller's lane, l1, l2 and k1 of its own pixel (sh holds the parked
-// S of all 128 pixels of the CTA, one column each).
+// S of all 128 pixels of the CTA, one column each, to be multiplied by the pixel's sh_sc).
 template <int L>
-__device__ __forceinline__ void warp_jacobi_item(const float* __restrict__ sh, int wid, int lane, int max_sweeps,
-                                                 float* res_l1, float* res_l2, int* res_k1, int* res_sw,
-                                                 bool* res_conv) {
+__device__ __forceinline__ void warp_jacobi_item(const float* __restrict__ sh, const float* __restrict__ sh_sc,
+                                                 int wid, int lane, int max_sweeps, float* res_l1, float* res_l2,
+                                                 int* res_k1, int* res_sw, bool* res_conv) {
     static_assert(L * L <= 64, "two entries per lane at most");
     constexpr int hL = L / 2;
     const bool act = lane < L * hL;
@@ -102,8 +111,9 @@ __device__ __forceinline__ void warp_jacobi_item(const float* __restrict__ sh, i
     const int partner = act ? (r ^ 1) * hL + j : lane;
     for (int mat = 0; mat < 32; ++mat) {
         const float* Sm = sh + wid * 32 + mat;
-        float a0 = act ? Sm[tri(r, c0, L) * kBatThreads] : 0.f;
-        float a1 = act ? Sm[tri(r, c0 + 1, L) * kBatThreads] : 0.f;
+        const float sc = sh_sc[wid * 32 + mat];
+        float a0 = act ? sc * Sm[tri(r, c0, L) * kBatThreads] : 0.f;
+        float a1 = act ? sc * Sm[tri(r, c0 + 1, L) * kBatThreads] : 0.f;
         int sweeps = 0;
         bool conv = false;
         float l1 = 0.f, l2 = 0.f;
@@ -200,15 +210,17 @@ __device__ __forceinline__ void warp_jacobi_item(const float* __restrict__ sh, i
 
 // Signal eigenvector x of the real-symmetric S (packed upper triangle, trace-normalised) by the
 // shifted power iteration x <- (S - sig I) x / |.|, started from the column of S with the largest
-// diagonal entry (for a rank-one S that column is already the eigenvector). The shift
+// diagonal entry (for a rank-one S that column is already the eigenvector; read from the parked
+// column, any positive multiple of S; inactive lanes, whose S is a diagonal stand-in, start from the
+// unit vector of that entry). The shift
 // sig = min(mean of the other eigenvalues, rho / 4), rho the current Rayleigh quotient, centres
 // the noise eigenvalues, which lie around their mean, so each step shrinks them by
 // max |l_i - sig| / (l1 - sig) instead of l2 / l1. A lane stops moving when a step changes x by
 // less than 1e-6; the warp stops when every lane has or after 24 steps (conv false). Returns
 // l1 = rho and, as l2, the bound sqrt(|S|_F^2 - rho^2) >= sqrt(sum_{i > 1} l_i^2) >= |l2|.
 template <int L>
-__device__ __forceinline__ void power_eigvec(const float (&S)[L * (L + 1) / 2], const float* Ssh, float (&x)[L],
-                                             float& l1, float& l2, int& steps, bool& conv) {
+__device__ __forceinline__ void power_eigvec(const float (&S)[L * (L + 1) / 2], const float* Ssh, bool active,
+                                             float (&x)[L], float& l1, float& l2, int& steps, bool& conv) {
     float trS = 0.f, fro2 = 0.f, dmax = -1.f;
     int kd = 0;
 #pragma unroll
@@ -228,7 +240,7 @@ __device__ __forceinline__ void power_eigvec(const float (&S)[L * (L + 1) / 2], 
         float n2 = 0.f;
 #pragma unroll
         for (int i = 0; i < L; ++i) {
-            x[i] = Ssh[tri(i, kd, L) * kBatThreads];
+            x[i] = active ? Ssh[tri(i, kd, L) * kBatThreads] : (i == kd ? 1.f : 0.f);
             n2 = fmaf(x[i], x[i], n2);
         }
         const float inv = rsqrtf(n2);
@@ -278,15 +290,15 @@ __device__ __forceinline__ void power_eigvec(const float (&S)[L * (L + 1) / 2], 
 }
 
 // Three steps of inverse iteration with (mu I - S) = L D L^T, mu = l1 (1 + 1e-5) just above the
-// largest eigenvalue estimate l1, from column k1 of S (S read from the thread's parked column).
+// largest eigenvalue estimate l1, from column k1 of S (S = sc times the thread's parked column).
 template <int L>
-__device__ __forceinline__ void inverse_iteration(const float* Ssh, float l1, int k1, float (&x)[L]) {
+__device__ __forceinline__ void inverse_iteration(const float* Ssh, float sc, float l1, int k1, float (&x)[L]) {
     constexpr int NS = L * (L + 1) / 2;
     const float mu = l1 + 1e-5f * l1 + 1e-30f;
     float Lm[NS];  // unit lower factor in the packed layout, D on the diagonal slots
 #pragma unroll
     for (int j = 0; j < L; ++j) {
-        float dj = mu - Ssh[tri(j, j, L) * kBatThreads];
+        float dj = mu - sc * Ssh[tri(j, j, L) * kBatThreads];
 #pragma unroll
         for (int k = 0; k < j; ++k) dj = fmaf(-Lm[tri(j, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], dj);
         if (fabsf(dj) < 1e-30f) dj = dj < 0.f ? -1e-30f : 1e-30f;
@@ -294,14 +306,14 @@ __device__ __forceinline__ void inverse_iteration(const float* Ssh, float l1, in
         const float inv = frcp(dj);
 #pragma unroll
         for (int i = j + 1; i < L; ++i) {
-            float v = -Ssh[tri(i, j, L) * kBatThreads];
+            float v = -sc * Ssh[tri(i, j, L) * kBatThreads];
 #pragma unroll
             for (int k = 0; k < j; ++k) v = fmaf(-Lm[tri(i, k, L)] * Lm[tri(j, k, L)], Lm[tri(k, k, L)], v);
             Lm[tri(i, j, L)] = v * inv;
         }
     }
 #pragma unroll
-    for (int i = 0; i < L; ++i) x[i] = Ssh[tri(i, k1, L) * kBatThreads];
+    for (int i = 0; i < L; ++i) x[i] = sc * Ssh[tri(i, k1, L) * kBatThreads];
 #pragma unroll 1
     for (int step = 0; step < 3; ++step) {
 #pragma unroll
@@ -332,15 +344,15 @@ __device__ __forceinline__ void inverse_iteration(const float* Ssh, float l1, in
 // ~1e-3 gap of l1 and three inverse-iteration steps reduce the other eigenvectors' share by ~1e-9.
 // More sweeps run only while some lane of the warp is short of that (up to max_sweeps).
 // The fallback of the power iteration: out of line (a call), so that its register demand does not set
-// the register budget of the hot path; S is read back from the thread's parked column, the results
-// go through the caller's small local copies.
+// the register budget of the hot path; S is read back from the thread's parked column (times sc),
+// the results go through the caller's small local copies.
 template <int L>
-__device__ __noinline__ void jacobi_eigvec(const float* Ssh, int max_sweeps, float* x_out, float* l12_out,
+__device__ __noinline__ void jacobi_eigvec(const float* Ssh, float sc, int max_sweeps, float* x_out, float* l12_out,
                                            int* sweeps_out, bool* jconv_out) {
     constexpr int NS = L * (L + 1) / 2;
     float S[NS];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) S[i] = Ssh[i * kBatThreads];
+    for (int i = 0; i < NS; ++i) S[i] = sc * Ssh[i * kBatThreads];
     float x[L];
     float l1 = 0.f, l2 = 0.f;
     int sweeps = 0;
@@ -403,13 +415,41 @@ __device__ __noinline__ void jacobi_eigvec(const float* Ssh, int max_sweeps, flo
         if (sweeps >= max_sweeps) break;
         if (__all_sync(kFull, jconv)) break;
     }
-    inverse_iteration<L>(Ssh, l1, k1, x);
+    inverse_iteration<L>(Ssh, sc, l1, k1, x);
 #pragma unroll
     for (int i = 0; i < L; ++i) x_out[i] = x[i];
     l12_out[0] = l1;
     l12_out[1] = l2;
     *sweeps_out = sweeps;
     *jconv_out = jconv;
+}
+
+// The folded snapshot of Eq. 4-5 at local sample index i0 of the lane's staged run, as the two real
+// L-vectors X = [Re p, Im q], Y = [Im p, -Re q] (p_i = s[i] + s[L-1-i], q_i = s[i] - s[L-1-i]).
+template <int L>
+__device__ __forceinline__ void folded_snapshot(const float2* __restrict__ seg_l, int i0, float (&X)[L],
+                                                float (&Y)[L]) {
+    constexpr int h = L / 2;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+        const float2 a = seg_l[seg_slot(i0 + i)], b = seg_l[seg_slot(i0 + L - 1 - i)];
+        X[i] = a.x + b.x;
+        Y[i] = a.y + b.y;
+        X[h + i] = a.y - b.y;
+        Y[h + i] = b.x - a.x;
+    }
+}
+
+// S += sg (X X^T + Y Y^T) on the packed upper triangle (sg = +1 or -1).
+template <int L>
+__device__ __forceinline__ void rank2_update(float (&S)[L * (L + 1) / 2], const float (&X)[L], const float (&Y)[L],
+                                             float sg) {
+#pragma unroll
+    for (int r = 0; r < L; ++r) {
+        const float xr = sg * X[r], yr = sg * Y[r];
+#pragma unroll
+        for (int c = r; c < L; ++c) S[tri(r, c, L)] = fmaf(xr, X[c], fmaf(yr, Y[c], S[tri(r, c, L)]));
+    }
 }
 
 // CTAS is the number of 128-thread CTAs the kernel is compiled to keep resident per SM
@@ -425,9 +465,11 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
     static_assert(L % 2 == 0 && L >= 2 && L <= kMaxL, "even L only");
     constexpr int h = L / 2;
     constexpr int NS = L * (L + 1) / 2;
-    __shared__ float2 sh_seg[kBatWarps][32 + kMaxN];
-    __shared__ float2 sh_pre[kBatWarps][kLagBlock * kPreLen];
+    __shared__ float2 sh_seg[kBatWarps][kSegLen];
+    // each thread's running (unnormalised) S, one column per thread, and the factor 1 / trace that
+    // normalises it (0 for pixels without a result)
     __shared__ float sh_S[NS * kBatThreads];
+    __shared__ float sh_sc[kBatThreads];
     // this warp's iteration statistics, added up per item and flushed to args.counters once when
     // the warp leaves the persistent loop (one atomic per statistic per warp, not per item: the
     // per-item atomics on one L2 line cost 4 % of the launch)
@@ -436,7 +478,8 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
     if (lane < kStatSlots) sh_stat[wid][lane] = 0ull;
     __syncwarp();
     float2* seg = sh_seg[wid];
-    float2* pre = sh_pre[wid];
+    const float2* seg_l = seg + (kRowP + 1) * lane;  // the lane's own samples: seg_l[seg_slot(i)]
+    float* const Ssh = sh_S + threadIdx.x;
 
     for (;;) {
         unsigned long long item = 0;
@@ -448,200 +491,153 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         const int64_t local = (int64_t)item - F.item_start;
         // a frame's items number below 2^31: 32-bit division (a 64-bit one is a long routine)
         const int wline = (int)((uint32_t)local / (uint32_t)F.nchunks);
-        const int chunk = (int)((uint32_t)local % (uint32_t)F.nchunks);
+        const int run = (int)((uint32_t)local % (uint32_t)F.nchunks);
         const int N = F.N, K = N - L + 1, wlen = F.wlen;
-        // every index below follows from these (the staging reads 31 + N <= 32 + kMaxN samples, the
-        // prefix sums reach lane + L - 1 + K = 31 + N < kPreLen, the store stays in window line wline);
+        // every index below follows from these (the staging reads kRowRun + N - 1 <= kSegLen samples,
+        // a lane's windows reach its sample kRowP - 1 + N - 1, the store stays in window line wline);
         // checked builds test them and skip a bad item whole (the test is uniform over the warp)
         if (!rm_check(f >= 0 && f < nframes && local >= 0 && local < (int64_t)F.wlines * F.nchunks && F.L == L &&
                           N >= L && N <= kMaxN,
                       args.counters))
             continue;
-        const int pos = chunk * kChunk + lane;
-        const int a0 = chunk * kChunk - N / 2;
+        const int a0 = run * kRowRun - N / 2;
         const float2* gl = gam + F.gam_off + (uint64_t)wline * wlen;
 
         // ---- stage the run's samples (coalesced) --------------------------------------------
-        __syncwarp();
-        for (int j = lane; j < 31 + N; j += 32) {
-            const int p = a0 + j;
-            seg[j] = (p >= 0 && p < wlen) ? gl[p] : make_float2(0.f, 0.f);
+        __syncwarp();  // every lane is done with the previous item's samples
+        for (int e = lane; e < kRowRun + N - 1; e += 32) {
+            const int p = a0 + e;
+            seg[seg_slot(e)] = (p >= 0 && p < wlen) ? gl[p] : make_float2(0.f, 0.f);
         }
         __syncwarp();
-        const bool inside = pos < wlen;
-        const bool valid = inside && (pos - N / 2 >= 0) && (pos - N / 2 + N - 1 <= wlen - 1);
 
-        // ---- S = Re(Q^H R_f Q) accumulated from the lag-product box sums ------------------------
-        // Every box sum K R_f[m][m+d] (and its Hermitian mirror) is added straight into the
-        // entries of S it feeds, so R_f is never held whole. Constant factors (1/K, 1/2) are
-        // dropped: S is normalised by its trace below, which leaves its eigenvectors unchanged.
-        // The lags are taken kLagBlock at a time: a rolled loop forms each lag's products and their
-        // warp scan into its own slot of pre[], then an unrolled pass reads the box sums of the
-        // block's lags into S (compile-time targets). Rolling the scan (two lags per pass, so that two
-        // scans' shuffle chains overlap) keeps the code small enough for the instruction cache, which
-        // the fully unrolled form overran.
-        float S[NS];
+#pragma unroll 1
+        for (int t = 0; t < kRowP; ++t) {
+            const int pos = run * kRowRun + lane * kRowP + t;
+            const bool inside = pos < wlen;
+            const bool valid = inside && (pos - N / 2 >= 0) && (pos - N / 2 + N - 1 <= wlen - 1);
+
+            // ---- S of this pixel: at the lane's first pixel (its anchor) the sum of the window's K
+            // rank-2 terms; at each next pixel the previous pixel's S plus the entering and minus the
+            // leaving snapshot's term. One rolled loop over one copy of the update code. (Constant
+            // factors 1/K and 1/2 are dropped: S is normalised by its trace below, which leaves its
+            // eigenvectors unchanged.)
+            float S[NS];
 #pragma unroll
-        for (int i = 0; i < NS; ++i) S[i] = 0.f;
-#pragma unroll
-        for (int d0 = 0; d0 < L; d0 += kLagBlock) {
-            constexpr int kLB = kLagBlock;
-            const int nd = L - d0 < kLB ? L - d0 : kLB;
-            __syncwarp();  // the previous block's box sums have been read
-#pragma unroll 2
-            for (int dd = 0; dd < nd; ++dd) {
-                const int d = d0 + dd;
-                const int G = 31 + N - d;  // lag products g_d[0 .. G-1] are needed
-                const int j0 = 3 * lane;
-                cx<float> s0 = mkc(0.f, 0.f), s1, s2;
-                if (j0 < G) {
-                    const float2 a = seg[j0], b = seg[j0 + d];
-                    s0 = mulc(mkc(a.x, a.y), mkc(b.x, b.y));
-                }
-                s1 = s0;
-                if (j0 + 1 < G) {
-                    const float2 a = seg[j0 + 1], b = seg[j0 + 1 + d];
-                    s1 = s1 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
-                }
-                s2 = s1;
-                if (j0 + 2 < G) {
-                    const float2 a = seg[j0 + 2], b = seg[j0 + 2 + d];
-                    s2 = s2 + mulc(mkc(a.x, a.y), mkc(b.x, b.y));
-                }
-                cx<float> incl = s2;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const cx<float> t = shfl_up_c(incl, o);
-                    if (lane >= o) incl = incl + t;
-                }
-                cx<float> excl = shfl_up_c(incl, 1);
-                if (lane == 0) excl = mkc(0.f, 0.f);
-                const cx<float> p1 = excl + s0, p2 = excl + s1, p3 = excl + s2;
-                float2* pd = pre + dd * kPreLen;
-                pd[j0 + 1] = make_float2(p1.r, p1.i);
-                pd[j0 + 2] = make_float2(p2.r, p2.i);
-                pd[j0 + 3] = make_float2(p3.r, p3.i);
-                if (lane == 0) pd[0] = make_float2(0.f, 0.f);
+            for (int i = 0; i < NS; ++i) S[i] = t == 0 ? 0.f : Ssh[i * kBatThreads];
+            const int nupd = t == 0 ? K : 2;
+#pragma unroll 1
+            for (int s = 0; s < nupd; ++s) {
+                const int i0 = t == 0 ? s : (s == 0 ? t - 1 + K : t - 1);
+                float X[L], Y[L];
+                folded_snapshot<L>(seg_l, i0, X, Y);
+                rank2_update<L>(S, X, Y, (t > 0 && s == 1) ? -1.f : 1.f);
             }
-            __syncwarp();
+            if (WJ) __syncwarp();  // the warp-per-matrix sweeps of the previous pixel read every lane's S
 #pragma unroll
-            for (int dd = 0; dd < kLB; ++dd) {
-                const int d = d0 + dd;
-                if (d < L) {
-                    const float2* pd = pre + dd * kPreLen;
+            for (int i = 0; i < NS; ++i) Ssh[i * kBatThreads] = S[i];
+            float tr = 0.f;
 #pragma unroll
-                    for (int m = 0; m + d < L; ++m) {
-                        const float2 hi = pd[lane + m + K], lo = pd[lane + m];
-                        const cx<float> v = mkc(hi.x - lo.x, hi.y - lo.y);  // K R_f[m][m+d]
-                        accumulate_s<L>(S, m, m + d, v);
-                        if (d > 0) accumulate_s<L>(S, m + d, m, conjg(v));
+            for (int i = 0; i < L; ++i) tr += S[tri(i, i, L)];
+            const bool nonzero = valid && tr > 0.f && isfinite(tr);
+            const float itr = frcp(tr);
+            sh_sc[threadIdx.x] = nonzero ? itr : 0.f;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) S[i] *= itr;
+            if (!nonzero) {  // border or empty windows: any well-separated stand-in
+#pragma unroll
+                for (int i = 0; i < NS; ++i) S[i] = 0.f;
+#pragma unroll
+                for (int i = 0; i < L; ++i) S[tri(i, i, L)] = (float)(L - i);
+            }
+
+            // ---- signal eigenvector of S --------------------------------------------------------------
+            // The running S is parked in shared memory (one column per thread, times sh_sc): the power
+            // iteration starts from one of its columns, the fallback's inverse iteration reads it back.
+            int sweeps = 0, psteps = 0, eig_fb = 0;
+            bool jconv = false;
+            float l1 = 0.f, l2 = 0.f;
+            float x[L];
+            if constexpr (WJ) {
+                int k1 = 0;
+                __syncwarp();  // every lane's S and scale are parked before the warp reads them
+                warp_jacobi_item<L>(sh_S, sh_sc, wid, lane, args.max_sweeps, &l1, &l2, &k1, &sweeps, &jconv);
+                // the warp-level sweep count, as the thread-per-matrix schedule reports it
+                sweeps = __reduce_max_sync(kFull, (unsigned)sweeps);
+                inverse_iteration<L>(Ssh, sh_sc[threadIdx.x], l1, k1, x);
+            } else {
+                // Shifted power iteration; lanes whose iteration did not settle, or whose eigen-gap the
+                // Frobenius bound cannot certify, take the cyclic Jacobi sweeps and inverse iteration
+                // instead (run by the whole warp when any lane needs them).
+                power_eigvec<L>(S, Ssh, nonzero, x, l1, l2, psteps, jconv);
+                const bool need = nonzero && (args.exhaustive || !jconv || !(l1 - l2 > 4e-6f * l1));
+                if (__any_sync(kFull, need)) {
+                    eig_fb = 1;
+                    float xj[L], jl[2];
+                    bool jc;
+                    jacobi_eigvec<L>(Ssh, sh_sc[threadIdx.x], args.max_sweeps, xj, jl, &sweeps, &jc);
+                    if (need) {
+#pragma unroll
+                        for (int i = 0; i < L; ++i) x[i] = xj[i];
+                        l1 = jl[0];
+                        l2 = jl[1];
+                        jconv = jc;
                     }
                 }
             }
-        }
-        float tr = 0.f;
-#pragma unroll
-        for (int i = 0; i < L; ++i) tr += S[tri(i, i, L)];
-        const bool nonzero = valid && tr > 0.f && isfinite(tr);
-        const float itr = frcp(tr);
-#pragma unroll
-        for (int i = 0; i < NS; ++i) S[i] *= itr;
-        if (!nonzero) {  // border or empty windows: any well-separated stand-in
-#pragma unroll
-            for (int i = 0; i < NS; ++i) S[i] = 0.f;
-#pragma unroll
-            for (int i = 0; i < L; ++i) S[tri(i, i, L)] = (float)(L - i);
-        }
+            const bool separated = l1 - l2 > 4e-6f * l1;
 
-        // ---- signal eigenvector of S ------------------------------------------------------------------
-        // The normalised S is parked in shared memory (one column per thread): the power iteration
-        // starts from one of its columns, the fallback's inverse iteration reads it back.
-        float* const Ssh = sh_S + threadIdx.x;
+            // ---- u1 = Q x1 and the polynomial coefficients ---------------------------------------------
+            cx<float> u[L];
+            const float r2 = 0.70710678118654752f;
 #pragma unroll
-        for (int i = 0; i < NS; ++i) Ssh[i * kBatThreads] = S[i];
-        int sweeps = 0, psteps = 0, eig_fb = 0;
-        bool jconv = false;
-        float l1 = 0.f, l2 = 0.f;
-        float x[L];
-        if constexpr (WJ) {
-            int k1 = 0;
-            __syncwarp();  // every lane's S is parked before the warp reads them
-            warp_jacobi_item<L>(sh_S, wid, lane, args.max_sweeps, &l1, &l2, &k1, &sweeps, &jconv);
-            // the warp-level sweep count, as the thread-per-matrix schedule reports it
-            sweeps = __reduce_max_sync(kFull, (unsigned)sweeps);
-            inverse_iteration<L>(Ssh, l1, k1, x);
-        } else {
-            // Shifted power iteration; lanes whose iteration did not settle, or whose eigen-gap the
-            // Frobenius bound cannot certify, take the cyclic Jacobi sweeps and inverse iteration
-            // instead (run by the whole warp when any lane needs them).
-            power_eigvec<L>(S, Ssh, x, l1, l2, psteps, jconv);
-            const bool need = nonzero && (args.exhaustive || !jconv || !(l1 - l2 > 4e-6f * l1));
-            if (__any_sync(kFull, need)) {
-                eig_fb = 1;
-                float xj[L], jl[2];
-                bool jc;
-                jacobi_eigvec<L>(Ssh, args.max_sweeps, xj, jl, &sweeps, &jc);
-                if (need) {
-#pragma unroll
-                    for (int i = 0; i < L; ++i) x[i] = xj[i];
-                    l1 = jl[0];
-                    l2 = jl[1];
-                    jconv = jc;
+            for (int i = 0; i < h; ++i) {
+                u[i] = mkc(r2 * x[i], r2 * x[h + i]);
+                u[h + i] = mkc(r2 * x[h - 1 - i], -r2 * x[L - 1 - i]);
+            }
+            cx<float> c[L];
+            const float res_lim2 = music_coefs<L>(u, c);
+
+            // ---- the selected root (Algorithm 1) -----------------------------------------------------------
+            bool found, cluster, rconv;
+            RootStats rs;
+            // Newton's starting radius from the noise's share of the window's energy, 1 - l1 (S has unit
+            // trace): on row windows the signal root sits at about 1 - 0.18 (1 - l1) (fitted to the FP64
+            // estimator's roots at 5-40 dB, median error 2e-4), close enough for one Newton step
+            const float r0 = 1.f - 0.18f * (1.f - l1);
+            const cx<float> zz = signal_root_polished_cert<L>(c, res_lim2, args.max_iters, args.exhaustive, nonzero,
+                                                              r0, found, cluster, rconv, rs);
+            const double omd = args.polish64 ? wrap_pi(polish_arg64<L>(c, zz, cluster) - F.omega_ref) : 0.0;
+            float om = args.polish64 ? (float)omd : wrap_pi(atan2f(zz.i, zz.r) - (float)F.omega_ref);
+
+            if (lane == 0 && args.counters) {
+                unsigned long long* cs = sh_stat[wid];
+                cs[0] += (unsigned long long)sweeps;
+                cs[1] += (unsigned long long)rs.iters;
+                cs[2] += 1ull;
+                cs[3] += (unsigned long long)rs.updates;
+                cs[4] += (unsigned long long)rs.evals;
+                cs[5] += (unsigned long long)psteps;
+                cs[6] += (unsigned long long)eig_fb;
+                cs[7] += (unsigned long long)rs.newton;
+                cs[8] += (unsigned long long)rs.fallback;
+                cs[9] += (unsigned long long)rs.polish;
+            }
+
+            // ---- store ---------------------------------------------------------------------------------
+            if (inside) {
+                const uint64_t o = out_index(F, wline, pos);
+                uint8_t st = kStOk;
+                if (!valid) {
+                    st = kStBorder;
+                } else if (!nonzero || !separated || !found) {
+                    st = kStDegenerate;
+                } else if (!rconv || !jconv) {
+                    st = kStNotConverged;
                 }
+                out[o] = (st == kStOk || st == kStNotConverged) ? om : __int_as_float(0x7fc00000);
+                if (status) status[o] = st;
             }
-        }
-        const bool separated = l1 - l2 > 4e-6f * l1;
-
-        // ---- u1 = Q x1 and the polynomial coefficients ---------------------------------------------
-        cx<float> u[L];
-        const float r2 = 0.70710678118654752f;
-#pragma unroll
-        for (int i = 0; i < h; ++i) {
-            u[i] = mkc(r2 * x[i], r2 * x[h + i]);
-            u[h + i] = mkc(r2 * x[h - 1 - i], -r2 * x[L - 1 - i]);
-        }
-        cx<float> c[L];
-        const float res_lim2 = music_coefs<L>(u, c);
-
-        // ---- the selected root (Algorithm 1) -----------------------------------------------------------
-        bool found, cluster, rconv;
-        RootStats rs;
-        // Newton's starting radius from the noise's share of the window's energy, 1 - l1 (S has unit
-        // trace): on row windows the signal root sits at about 1 - 0.18 (1 - l1) (fitted to the FP64
-        // estimator's roots at 5-40 dB, median error 2e-4), close enough for one Newton step
-        const float r0 = 1.f - 0.18f * (1.f - l1);
-        const cx<float> zz = signal_root<L>(c, res_lim2, args.max_iters, args.exhaustive, nonzero, r0, found, cluster,
-                                            rconv, rs);
-        const double omd = args.polish64 ? wrap_pi(polish_arg64<L>(c, zz, cluster) - F.omega_ref) : 0.0;
-        float om = args.polish64 ? (float)omd : wrap_pi(atan2f(zz.i, zz.r) - (float)F.omega_ref);
-
-        if (lane == 0 && args.counters) {
-            unsigned long long* c = sh_stat[wid];
-            c[0] += (unsigned long long)sweeps;
-            c[1] += (unsigned long long)rs.iters;
-            c[2] += 1ull;
-            c[3] += (unsigned long long)rs.updates;
-            c[4] += (unsigned long long)rs.evals;
-            c[5] += (unsigned long long)psteps;
-            c[6] += (unsigned long long)eig_fb;
-            c[7] += (unsigned long long)rs.newton;
-            c[8] += (unsigned long long)rs.fallback;
-            c[9] += (unsigned long long)rs.polish;
-        }
-
-        // ---- store ---------------------------------------------------------------------------------
-        if (inside) {
-            const uint64_t o = out_index(F, wline, pos);
-            uint8_t st = kStOk;
-            if (!valid) {
-                st = kStBorder;
-            } else if (!nonzero || !separated || !found) {
-                st = kStDegenerate;
-            } else if (!rconv || !jconv) {
-                st = kStNotConverged;
-            }
-            out[o] = (st == kStOk || st == kStNotConverged) ? om : __int_as_float(0x7fc00000);
-            if (status) status[o] = st;
         }
     }
     __syncwarp();

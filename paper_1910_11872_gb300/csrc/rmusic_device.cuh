@@ -21,7 +21,10 @@ namespace rmusic {
 constexpr int kMaxL = 12;        // largest covariance order L
 constexpr int kMaxN = 64;        // largest window length N
 constexpr int kMaxLine = 8192;   // longest carrier line the band-pass kernel accepts
-constexpr int kChunk = 32;       // pixels of one window line handled by one warp work item
+// Row geometry, FP32-batched path: one warp work item is a run of kRowRun consecutive pixels of a
+// window line, starting at a multiple of kRowRun; lane l owns its pixels l kRowP .. l kRowP + kRowP - 1.
+constexpr int kRowP = 8;
+constexpr int kRowRun = 32 * kRowP;
 
 enum : uint8_t { kStOk = 0, kStBorder = 1, kStDegenerate = 2, kStNotConverged = 3 };
 
@@ -42,7 +45,7 @@ struct FrameDev {
     int32_t nlines, len;  // carrier lines and their length
     int32_t k_lo, nb;     // kept DFT bins k_lo .. k_lo + nb - 1 of a carrier line
     int32_t wlines, wlen; // window lines and their length
-    int32_t nchunks;      // row geometry: work items per window line (ceil(wlen / kChunk));
+    int32_t nchunks;      // row geometry: work items per window line (ceil(wlen / kRowRun));
                           // square geometry: tiles per tile row (ceil(W / 32))
     int32_t geom;         // kGeomRow or kGeomSquare (then L holds the half-width Lp, N = 2 Lp + 1)
     double omega_ref;     // carrier phase step removed from the angle (rad/pixel)

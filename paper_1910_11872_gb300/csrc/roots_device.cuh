@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include "rmusic_device.cuh"
+#include "rouche_table.h"
 
 namespace rmusic {
 
@@ -411,6 +412,109 @@ __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
     return ok ? N : -1;
 }
 
+// The noise-free deflated polynomial G_L and the lower bounds of min |G_L| on |w| = rho of the Rouche
+// certificate below (rouche_table.h), for the row solver's covariance orders.
+template <int L>
+__device__ __forceinline__ constexpr float rouche_g(int k) {
+    if constexpr (L == 4) return rouche_g4(k);
+    else if constexpr (L == 6) return rouche_g6(k);
+    else if constexpr (L == 8) return rouche_g8(k);
+    else if constexpr (L == 10) return rouche_g10(k);
+    else return rouche_g12(k);
+}
+template <int L>
+__device__ __forceinline__ const float* rouche_min() {
+    if constexpr (L == 4) return kRcMin4;
+    else if constexpr (L == 6) return kRcMin6;
+    else if constexpr (L == 8) return kRcMin8;
+    else if constexpr (L == 10) return kRcMin10;
+    else return kRcMin12;
+}
+
+// roots_inside out of line, for the lanes where the Rouche test does not decide: its straight-line
+// code (about 0.7 K instructions at L = 8) then stays out of the hot path's instruction stream. Takes
+// the caller's copy of the coefficients, made inside the branch.
+template <int L>
+__device__ __noinline__ int roots_inside_cold(const cx<float>* c_in, float r) {
+    cx<float> c[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) c[i] = c_in[i];
+    return roots_inside<L>(c, r);
+}
+
+// A cheaper exact certificate that Q has exactly L - 2 roots in |z| < rho = r - 0.02 (r = |zs|, zs
+// the Newton root; the claim roots_inside checks), by Rouche's theorem against the noise-free
+// polynomial. With e = zs / r and w = z / e, the coefficients c_k e^k (c_0, c_{-k} = conj) give the
+// polynomial Qh(w) = e^{-(L-1)} Q(e w), whose roots are Q's rotated onto zs's ray: r, 1/r among them.
+// Dividing Qh by (w - r)(w - 1/r) = w^2 - (r + 1/r) w + 1 from the top gives the quotient Qh2 of
+// degree 2L - 4 and a remainder R1 w + R0. A window of one complex exponential has u1 = a steering
+// vector and Qh = the real polynomial of rouche_table.h with its double root at w = 1, whose
+// deflation is G_L. On |w| = rho:
+// Write the remainder as R(w) = R1 (w - r) + R(r); since quad = (w - r)(w - 1/r), on |w| = rho
+//   |Qh - quad G_L| <= |quad| (sum_k |Qh2_k - G_L,k| rho^k + |R1| / (1/r - rho) + |R(r)| / qmin),
+//   |quad G_L| >= |quad| min |G_L|,   with |quad| >= qmin = (r - rho)(1/r - rho), |w - 1/r| >= 1/r - rho.
+// So if sum_k |Qh2_k - G_L,k| rho^k + |R1| / (1/r - rho) + |R(r)| / qmin < min_{|w| = rho} |G_L|, Qh
+// has as many roots in |w| < rho as (w - r)(w - 1/r) G_L: G_L's L - 2 inner roots (rho is above all of
+// them where the table's bound is positive; r and 1/r lie outside rho). The test uses
+// |x| <= |Re x| + |Im x|, adds 4e-6 sum_i |q_i| / qmin for the FP32 rounding of the rotated
+// coefficients and of the division, and compares with 0.9 times the tabulated bound (itself rounded
+// down). R(r) = Q(zs) up to a unit factor is the root's residual, so zs must be the polished root:
+// from Newton's unpolished root (~1e-4 off on near-circle pairs) the test fails in a few per cent of
+// lanes. On noisy row windows (5-40 dB, L = 8, polished roots) it holds in every lane measured, at
+// under half the bound; where it fails, the Schur-Cohn count decides. For L = 2 there is nothing to
+// exclude. res_lim2 is music_coefs' (3e-6 sum_i |q_i|)^2.
+template <int L>
+__device__ __forceinline__ bool rouche_certify(const cx<float>* c, cx<float> zs, float r, float res_lim2) {
+    if constexpr (L == 2) {
+        return true;
+    } else {
+        constexpr int n = 2 * L - 2;  // degree of Q
+        const float rho = r - 0.02f;
+        const float ft = (rho - kRcRho0) * (1.f / kRcStep);
+        if (!(ft >= 0.f && ft < (float)kRcN)) return false;
+        const float mlow = __ldg(rouche_min<L>() + (int)ft);
+        if (!(mlow > 0.f)) return false;
+        const float ir = frcp(r);
+        const cx<float> e = ir * zs;
+        cx<float> ch[L];  // c_k e^k
+        ch[0] = c[0];
+        {
+            cx<float> ep = e;
+#pragma unroll
+            for (int k = 1; k < L; ++k) {
+                ch[k] = c[k] * ep;
+                if (k + 1 < L) ep = ep * e;
+            }
+        }
+        auto qh = [&](int i) {  // coefficient of w^i in Qh
+            const int k = i - (L - 1);
+            return k == 0 ? ch[0] : (k > 0 ? ch[k] : conjg(ch[-k]));
+        };
+        const float sig = r + ir;
+        // top-down division: b_{n-2} = qh_n, b_{n-3} = qh_{n-1} + sig b_{n-2},
+        // b_k = qh_{k+2} + sig b_{k+1} - b_{k+2}; the sum over k by Horner in rho
+        cx<float> b2 = mkc(0.f, 0.f), b1 = mkc(0.f, 0.f);
+        float sum = 0.f;
+#pragma unroll
+        for (int k = n - 2; k >= 0; --k) {
+            const cx<float> q = qh(k + 2);
+            const cx<float> b = mkc(fmaf(sig, b1.r, q.r) - b2.r, fmaf(sig, b1.i, q.i) - b2.i);
+            sum = fmaf(sum, rho, fabsf(b.r - rouche_g<L>(k)) + fabsf(b.i));
+            b2 = b1;
+            b1 = b;
+        }
+        // b1 = b_0, b2 = b_1: remainder R1 = qh_1 + sig b_0 - b_1, R0 = qh_0 - b_0, R(r) = R1 r + R0
+        const cx<float> q1 = qh(1), q0 = qh(0);
+        const cx<float> R1 = mkc(fmaf(sig, b1.r, q1.r) - b2.r, fmaf(sig, b1.i, q1.i) - b2.i);
+        const cx<float> Rr = mkc(fmaf(R1.r, r, q0.r - b1.r), fmaf(R1.i, r, q0.i - b1.i));
+        const float qmin = (r - rho) * (ir - rho);
+        const float qsum = sqrtf(res_lim2) * (1.f / 3e-6f);
+        const float lhs = sum + (fabsf(R1.r) + fabsf(R1.i)) * frcp(ir - rho) +
+                          (fabsf(Rr.r) + fabsf(Rr.i) + 4e-6f * qsum) * frcp(qmin);
+        return lhs < 0.9f * mlow;
+    }
+}
+
 // Newton steps of the signal root before a lane counts as not converged (it then takes the full
 // root finder): 3-4 on row windows, 4-7 on square blocks at 0-10 dB.
 constexpr int kNewtonSteps = 16;
@@ -517,6 +621,128 @@ __device__ __forceinline__ cx<float> signal_root(const cx<float>* c, float res_l
     }
     rs.polish = kPolishSteps;
     return polish_isolated<L>(c, zs);
+}
+
+// polish_root of the selected root zs (zn its nearest other root, cluster: the two form a split double
+// root), with the second derivative only in warps where some lane holds a cluster.
+template <int L>
+__device__ __forceinline__ cx<float> polish_selected(const cx<float>* c, cx<float> zs, cx<float> zn, bool cluster) {
+    if (__any_sync(kFull, cluster)) {
+        cx<float> cl[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) cl[i] = c[i];
+        cx<float> zp;
+        polish_cold<L>(cl, zs, zn, cluster, &zp);
+        return zp;
+    }
+    return polish_isolated<L>(c, zs);
+}
+
+// The root stage of the row solver: signal_root's steps in another order. Newton's root is polished
+// first and the certificate then checks the polished root -- by rouche_certify, and by the
+// Schur-Cohn count (roots_inside at |zp| - 0.02) in lanes where that test does not decide. Lanes
+// without a certificate take the full root finder, whose selected root is polished in turn. The
+// selected roots are signal_root's: the same Newton root and polish where certified, the same Aberth
+// selection and polish otherwise. Newton's steps and the polish of an isolated root run in one rolled
+// loop over one copy of the Horner code (newton_signal_root's steps, then polish_isolated's), which
+// keeps the hot code small; warps with a split double root polish out of line (polish_cold).
+template <int L>
+__device__ __forceinline__ cx<float> signal_root_polished_cert(const cx<float>* c, float res_lim2, int max_iters,
+                                                               int exhaustive, bool active, float r0, bool& found,
+                                                               bool& cluster, bool& rconv, RootStats& rs) {
+    bool nconv = false, cert = false;
+    cx<float> zs = mkc(0.f, 0.f), zn = zs, zp = zs;
+    rs.newton = 0;
+    rs.polish = 0;
+    cluster = false;
+    if (!exhaustive) {
+        // Newton's method on the signal root (newton_signal_root), then kPolishSteps polish steps
+        const float rs0 = fminf(fmaxf(r0, 0.5f), 0.9995f);  // start strictly inside the circle
+        const cx<float> rho1 = (-1.f) * c[1];
+        const float n1 = norm2(rho1);
+        cx<float> z = n1 > 0.f ? (rs0 * rsqrtf(n1)) * conjg(rho1) : mkc(rs0, 0.f);
+        nconv = !active;
+        bool polishing = false, cold = false;
+        int pol = 0;
+#pragma unroll 1
+        for (;;) {
+            cx<float> p, dp;
+            horner_pd<L>(c, z, p, dp);
+            const cx<float> w = mirror_newton_step(z, p, dp);
+            const bool fin = isfinite(w.r) && isfinite(w.i);
+            if (!polishing) {
+                ++rs.newton;
+                const bool small = norm2(p) <= res_lim2;
+                if (!nconv && !small && fin) {
+                    z = z - w;
+                    const float r2 = norm2(z);
+                    if (r2 > 1.f) z = frcp(r2) * z;
+                }
+                nconv = nconv || small || (fin && norm2(w) <= 1e-5f);
+                if (rs.newton >= kNewtonSteps || __all_sync(kFull, nconv)) {
+                    zs = z;
+                    zn = frcp(norm2(zs)) * zs;
+                    cluster = norm2(zn - zs) < 4e-3f * 4e-3f;
+                    cold = __any_sync(kFull, cluster);
+                    if (cold) break;
+                    polishing = true;
+                }
+            } else {
+                if (fin) z = z - w;
+                if (++pol == kPolishSteps) break;
+            }
+        }
+        if (cold) {
+            cx<float> cl[L];
+#pragma unroll
+            for (int i = 0; i < L; ++i) cl[i] = c[i];
+            polish_cold<L>(cl, zs, zn, cluster, &zp);
+        } else {
+            zp = z;
+        }
+        rs.polish = kPolishSteps;
+        const float rp = sqrtf(norm2(zp));
+        bool counted = false;
+        if (active && nconv && rp > 0.5f) counted = rouche_certify<L>(c, zp, rp, res_lim2);
+        if (active && nconv && rp > 0.5f && !counted) {
+            cx<float> cl[L];
+#pragma unroll
+            for (int i = 0; i < L; ++i) cl[i] = c[i];
+            counted = roots_inside_cold<L>(cl, rp - 0.02f) == L - 2;
+        }
+        cert = !active || counted;
+    }
+    found = true;
+    rconv = nconv;
+    rs.fallback = 0;
+    rs.iters = rs.evals = rs.updates = 0;
+    if (__any_sync(kFull, !cert)) {
+        rs.fallback = 1;
+        cx<float> cl[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) cl[i] = c[i];
+        bool aconv, afound;
+        cx<float> azs, azn;
+        int st[3];
+        aberth_select<L>(cl, res_lim2, max_iters, &azs, &azn, &afound, &aconv, st);
+        rs.iters = st[0];
+        rs.evals = st[1];
+        rs.updates = st[2];
+        if (!cert) {
+            zs = azs;
+            zn = azn;
+            found = afound;
+            rconv = aconv;
+        }
+        const bool cl2 = norm2(zn - zs) < 4e-3f * 4e-3f;
+        const cx<float> zq = polish_selected<L>(c, zs, zn, cl2);
+        rs.polish += kPolishSteps;
+        if (!cert) {
+            zp = zq;
+            cluster = cl2;
+        }
+    }
+    return zp;
 }
 
 // One more refinement step of the selected root in FP64; returns arg z in double.

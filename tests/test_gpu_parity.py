@@ -336,9 +336,9 @@ def test_invalid_descriptors_rejected():
             (rmusic.rmusic_frame_desc(0, 4, 16, 0, 7, 0, 0, 0), rmusic.RMUSIC_EINVAL),
             (rmusic.rmusic_frame_desc(0, 4, 16, 0, 0, 0, 8, 12), rmusic.RMUSIC_EINVAL),
             (rmusic.rmusic_frame_desc(0, 4, 16, 0, 0, 0, 32, 7), rmusic.RMUSIC_EUNSUPPORTED),
-            # 2^26 rows of 32 work items: 2^31 items, past the solvers' 32-bit item index (rejected
-            # while the descriptors are checked, before anything is queued)
-            (rmusic.rmusic_frame_desc(0, 1 << 26, 1024, 0, 0, 0, 0, 0), rmusic.RMUSIC_EUNSUPPORTED),
+            # 2^29 rows of four 256-pixel work items: 2^31 items, past the solvers' 32-bit item index
+            # (rejected while the descriptors are checked, before anything is queued)
+            (rmusic.rmusic_frame_desc(0, 1 << 29, 1024, 0, 0, 0, 0, 0), rmusic.RMUSIC_EUNSUPPORTED),
         ]:
             with pytest.raises(rmusic.RmusicError) as e:
                 rmusic.rmusic_demodulate_frames(dem.ctx, buf.data_ptr(), [d], 1, out.data_ptr(), None, s)
@@ -448,34 +448,48 @@ def test_uneven_batch_full_sizes_one_launch_sampled():
 
 
 def test_autotune_variants_identical_and_cached(tmp_path, monkeypatch):
-    """Every register-cap variant of the solver computes the same maps bit for bit; rmusic_autotune
-    keeps one per covariance order and records it in the cache file named by RMUSIC_TUNE_CACHE."""
+    """rmusic_autotune keeps one register-cap variant per covariance order and records it in the cache
+    file named by RMUSIC_TUNE_CACHE; the tuned call's maps equal, bit for bit, those of a context
+    pinned to the recorded variants (each variant is deterministic), and agree with the untuned
+    default's to FP32 rounding with identical statuses."""
+    import json
+
     torch = _torch()
     cache = tmp_path / "tune.jsonl"
     monkeypatch.setenv("RMUSIC_TUNE_CACHE", str(cache))
     frames = [synth.peaks_frame(10, 0.1, H=64, W=512).image, synth.peaks_frame(np.inf, 0.1, H=32, W=256).image]
     windows = [(32, 8), (24, 6)]
-    ref = run_gpu(frames, windows=windows)
     descs, nbytes, nout = rmusic.frame_descs([f.shape for f in frames], rmusic.RMUSIC_DTYPE_F32, 4, windows)
     x = torch.from_numpy(np.concatenate([f.ravel() for f in frames])).cuda()
-    dem = rmusic.Demodulator()
-    try:
-        out = torch.empty(nout, device="cuda")
-        st = torch.empty(nout, dtype=torch.uint8, device="cuda")
-        s = torch.cuda.current_stream().cuda_stream
-        rmusic.rmusic_autotune(dem.ctx, x.data_ptr(), descs, 2, out.data_ptr(), st.data_ptr(), s)
-        torch.cuda.synchronize()
-        tuned = out.cpu().numpy()
-        rmusic.rmusic_demodulate_frames(dem.ctx, x.data_ptr(), descs, 2, out.data_ptr(), st.data_ptr(), s)
-        torch.cuda.synchronize()
-        again = out.cpu().numpy()
-    finally:
-        dem.close()
-    flat_ref = np.concatenate([g.ravel() for g, _ in ref])
-    assert np.array_equal(tuned, flat_ref, equal_nan=True)
-    assert np.array_equal(again, flat_ref, equal_nan=True)
-    lines = cache.read_text().strip().splitlines()
-    assert {int(l.split('"L": ')[1].split(",")[0]) for l in lines} == {6, 8}
+    s = torch.cuda.current_stream().cuda_stream
+
+    def call(pin=None, tune=False):
+        dem = rmusic.Demodulator()
+        try:
+            for L, v in (pin or {}).items():
+                rmusic.rmusic_set_solver_variant(dem.ctx, L, v)
+            out = torch.empty(nout, device="cuda")
+            st = torch.empty(nout, dtype=torch.uint8, device="cuda")
+            fn = rmusic.rmusic_autotune if tune else rmusic.rmusic_demodulate_frames
+            fn(dem.ctx, x.data_ptr(), descs, 2, out.data_ptr(), st.data_ptr(), s)
+            torch.cuda.synchronize()
+            return out.cpu().numpy(), st.cpu().numpy()
+        finally:
+            dem.close()
+
+    default = {8: 0, 6: 1}  # the untuned variants (batched_variants.h)
+    ref, ref_st = call(pin=default)
+    tuned, tuned_st = call(tune=True)
+    again, again_st = call()  # the tuned choice, taken from this process's tuning
+    lines = [json.loads(l) for l in cache.read_text().strip().splitlines()]
+    chosen = {int(d["L"]): int(d["variant"]) for d in lines}
+    assert set(chosen) == {6, 8}
+    pinned, pinned_st = call(pin=chosen)
+    assert np.array_equal(tuned, pinned, equal_nan=True) and np.array_equal(tuned_st, pinned_st)
+    assert np.array_equal(again, pinned, equal_nan=True) and np.array_equal(again_st, pinned_st)
+    assert np.array_equal(tuned_st, ref_st)
+    ok = ref_st == 0
+    assert np.abs(tuned[ok] - ref[ok]).max() <= 3e-5
 
 
 @pytest.mark.parametrize("L", [4, 6, 8])
