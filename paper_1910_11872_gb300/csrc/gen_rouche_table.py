@@ -57,8 +57,7 @@ def table(L: int):
     return g, lo, radii[radii < 1].max()
 
 
-def main():
-    here = os.path.dirname(os.path.abspath(__file__))
+def header_text() -> str:
     lines = ["// rouche_table.h -- written by gen_rouche_table.py (do not edit): the noise-free deflated",
              "// root-MUSIC polynomials G_L and lower bounds of min |G_L| on the circles |w| = rho, for the row",
              "// solver's Rouche certificate (roots_device.cuh).",
@@ -76,8 +75,13 @@ def main():
         lines.append(f"__device__ const float kRcMin{L}[{NRHO}] = {{{body}}};")
         lines.append("")
     lines += ["}  // namespace rmusic", ""]
+    return "\n".join(lines)
+
+
+def main():
+    here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "rouche_table.h"), "w") as f:
-        f.write("\n".join(lines))
+        f.write(header_text())
 
 
 if __name__ == "__main__":
