@@ -121,7 +121,7 @@ def rouche_flops(L: int) -> float:
 
 def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float, power_steps: float = 0.0,
                     eig_fallback: float = 0.0, newton: float = 0.0, root_fallback: float = 0.0,
-                    polish: float = 2.0, pixels_per_lane: int = 8) -> float:
+                    polish: float = 2.0, pixels_per_lane: int = 16) -> float:
     """Algorithmic FP32 flops per pixel of the batched solver (FMA = 2, other arithmetic = 1),
     counted from the kernel's steps with the measured work per 32-pixel group (power steps,
     Jacobi sweeps and fallbacks, Newton steps, Aberth evaluations, updates and fallbacks):

@@ -198,8 +198,8 @@ int rmusic_create(const rmusic_params* params, int device, size_t hbm_budget_byt
  *   d_status  device uint8 buffer laid out like d_out, or NULL.
  *   cuda_stream  cudaStream_t (as void*) on which all work is queued.
  * Errors: RMUSIC_EINVAL (NULL pointers with n_frames > 0, a bad descriptor, unsupported
- * (N, L) for the path), RMUSIC_EUNSUPPORTED (a frame of 2^31 or more 256-pixel work items, about
- * 5.5e11 pixels: far beyond what fits a GPU), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a
+ * (N, L) for the path), RMUSIC_EUNSUPPORTED (a frame of 2^31 or more 512-pixel work items, about
+ * 1.1e12 pixels: far beyond what fits a GPU), RMUSIC_ENOMEM, RMUSIC_ECUDA. n_frames == 0 is a
  * no-op. */
 int rmusic_demodulate_frames(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* descs,
                              int32_t n_frames, float* d_out, uint8_t* d_status, void* cuda_stream);
@@ -220,8 +220,9 @@ int rmusic_autotune(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
  * or an event recorded after the call). The frames are always staged into the context's workspace
  * by the copy engine -- which needs no SM -- so a caller alternating two contexts on two streams
  * (double buffering) overlaps the frames' transfer of one call with the kernels of the other;
- * pinned output buffers are written in place by the solver, others through the workspace and a
- * copy queued at the end. The host buffers must stay valid and the input unchanged until the
+ * pinned output buffers are written in place by the solver where its stores are coalesced (plain
+ * paths, square geometry without unwrap), others through the workspace and a copy queued at the
+ * end. The host buffers must stay valid and the input unchanged until the
  * stream has completed the call (pageable input is copied before the call returns), and a context
  * serves one call at a time: the next call on it must follow on the same stream or after the
  * previous one completes. Errors: as rmusic_demodulate_frames_host; a CUDA error met while the
@@ -251,8 +252,11 @@ int rmusic_reserve(rmusic_ctx* ctx, uint64_t max_pixels, int32_t max_frames);
  * the call returns (it synchronises its stream). in_bytes is the size of h_frames. Buffers the GPU
  * can address directly (pinned memory from cudaHostAlloc / cudaMallocHost, or registered with
  * cudaHostRegister) are used in place: the band-pass kernel reads the frames and the solver writes
- * the maps over the host link while it runs, instead of a copy before and after the kernels (with
- * phase assembly, square geometry with unwrap = 1, the maps are still staged on the device).
+ * the maps over the host link while it runs, instead of a copy before and after the kernels. The
+ * maps are staged on the device instead (and copied back at the end) for the FP32-batched row
+ * solver, whose lanes each write 16 consecutive pixels (one store instruction touches 32 pixels 64
+ * bytes apart: one host-link transaction per pixel), and with phase assembly (square geometry with
+ * unwrap = 1), which rereads its maps.
  * Pageable buffers are copied to and from the context's device workspace. The results are
  * identical either way. */
 int rmusic_demodulate_frames_host(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes,

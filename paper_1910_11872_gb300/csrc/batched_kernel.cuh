@@ -42,14 +42,15 @@ namespace rmusic {
 
 constexpr int kBatWarps = 4;
 constexpr int kBatThreads = kBatWarps * 32;
-static_assert(kRowP == 8, "the staging pads one sample every 8 (shift by 3)");
+static_assert(kRowP == 16, "the staging pads one sample every 16 (shift by 4)");
 // staged samples of one run: kRowRun + N - 1 <= kRowRun + kMaxN - 1, plus one pad every kRowP
 constexpr int kSegLen = kRowRun + kMaxN + (kRowRun + kMaxN) / kRowP;
 
 // Shared-memory slot of staged sample e of a run (one pad slot after every kRowP samples): lane l's
-// sample i is e = l kRowP + i at 9 l + i + i / 8, so 32 lanes reading their own sample i touch 32
-// consecutive 9-strided slots -- distinct banks.
-__device__ __forceinline__ int seg_slot(int e) { return e + (e >> 3); }
+// sample i is e = l kRowP + i at 17 l + i + i / 16, so 32 lanes reading their own sample i touch 32
+// slots 17 apart -- 16 distinct 8-byte bank pairs, each read by two lanes (the two wavefronts a
+// 64-bit load takes anyway).
+__device__ __forceinline__ int seg_slot(int e) { return e + (e >> 4); }
 
 __host__ __device__ constexpr int tri(int r, int c, int L) {
     return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);

@@ -965,10 +965,14 @@ int host_entry(rmusic_ctx* ctx, const void* h_frames, size_t in_bytes, const rmu
     }
     // Pinned (device-addressable) buffers are used in place: the band-pass reads the frames and the
     // solver writes the maps over the host link while it computes, instead of a copy before and a
-    // copy after the kernels. The unwrapping pass reads and writes its maps many times, so with
-    // phase assembly the maps are staged on the device.
+    // copy after the kernels. Two solvers' maps are staged on the device instead: the unwrapping
+    // pass reads and writes its maps many times (square geometry with phase assembly), and the
+    // FP32-batched row solver's lanes each own 16 consecutive pixels, so one of its store
+    // instructions writes 32 pixels 64 bytes apart -- merged in the device's L2, but one transaction
+    // per pixel over the host link.
     const void* d_in = sync ? direct_host_ptr(h_frames) : nullptr;
-    const bool staged_maps = ctx->p.geometry == RMUSIC_GEOM_SQUARE && ctx->p.unwrap;
+    const bool staged_maps = (ctx->p.geometry == RMUSIC_GEOM_SQUARE && ctx->p.unwrap) ||
+                             (ctx->p.geometry == RMUSIC_GEOM_ROW && ctx->p.precision == RMUSIC_FP32_BATCHED);
     float* d_out = staged_maps ? nullptr : static_cast<float*>(direct_host_ptr(h_out));
     uint8_t* d_st = nullptr;
     if (d_out && h_status) {

@@ -23,7 +23,7 @@ constexpr int kMaxN = 64;        // largest window length N
 constexpr int kMaxLine = 8192;   // longest carrier line the band-pass kernel accepts
 // Row geometry, FP32-batched path: one warp work item is a run of kRowRun consecutive pixels of a
 // window line, starting at a multiple of kRowRun; lane l owns its pixels l kRowP .. l kRowP + kRowP - 1.
-constexpr int kRowP = 8;
+constexpr int kRowP = 16;
 constexpr int kRowRun = 32 * kRowP;
 
 enum : uint8_t { kStOk = 0, kStBorder = 1, kStDegenerate = 2, kStNotConverged = 3 };

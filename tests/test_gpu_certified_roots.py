@@ -7,8 +7,9 @@ count where that test does not decide -- (24, 12) at 5 dB takes both in most war
 Schur-Cohn); the full Jacobi sweeps and the Aberth iteration on every inner root run only where those
 fail. exhaustive = 1 runs the full methods for every pixel. Both must select the same
 root as the oracle (which computes every root in FP64): identical status maps, noise-free maps within
-1e-4 rad/px of the oracle, noisy maps with the oracle's RMS error within 1 %, and the two GPU
-methods within 1e-5 rad/px of each other.
+1e-4 rad/px of the oracle (noisy ones too), noisy maps with the oracle's RMS error within 1 %, and
+the two GPU methods within 1e-5 rad/px of each other (1e-4 where the window has fewer than 2L
+snapshots).
 """
 import numpy as np
 import pytest
@@ -49,7 +50,12 @@ def test_row_certified_and_exhaustive_select_the_oracles_root(snr, N, L):
     o, os_ = o.ravel(), os_.ravel()
     assert np.array_equal(gs, os_) and np.array_equal(ges, os_)
     v = os_ == 0
-    assert np.abs(g[v] - ge[v]).max() <= 1e-5
+    # the two FP32 eigenvectors (power iteration, Jacobi + inverse iteration) agree to ~1e-6; with
+    # fewer snapshots than 2L (K = 13 for (24, 12)) the eigen-gap is small and the angle difference
+    # reaches ~3e-5 at 5 dB
+    tol = 1e-5 if N - L + 1 >= 2 * L else 1e-4
+    assert np.abs(g[v] - ge[v]).max() <= tol
+    assert np.abs(g[v] - o[v]).max() <= 1e-4 and np.abs(ge[v] - o[v]).max() <= 1e-4
     if np.isinf(snr):
         assert np.abs(g[v] - o[v]).max() <= 1e-4 and np.abs(ge[v] - o[v]).max() <= 1e-4
     else:

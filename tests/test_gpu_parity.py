@@ -336,9 +336,9 @@ def test_invalid_descriptors_rejected():
             (rmusic.rmusic_frame_desc(0, 4, 16, 0, 7, 0, 0, 0), rmusic.RMUSIC_EINVAL),
             (rmusic.rmusic_frame_desc(0, 4, 16, 0, 0, 0, 8, 12), rmusic.RMUSIC_EINVAL),
             (rmusic.rmusic_frame_desc(0, 4, 16, 0, 0, 0, 32, 7), rmusic.RMUSIC_EUNSUPPORTED),
-            # 2^29 rows of four 256-pixel work items: 2^31 items, past the solvers' 32-bit item index
+            # 2^30 rows of two 512-pixel work items: 2^31 items, past the solvers' 32-bit item index
             # (rejected while the descriptors are checked, before anything is queued)
-            (rmusic.rmusic_frame_desc(0, 1 << 29, 1024, 0, 0, 0, 0, 0), rmusic.RMUSIC_EUNSUPPORTED),
+            (rmusic.rmusic_frame_desc(0, 1 << 30, 1024, 0, 0, 0, 0, 0), rmusic.RMUSIC_EUNSUPPORTED),
         ]:
             with pytest.raises(rmusic.RmusicError) as e:
                 rmusic.rmusic_demodulate_frames(dem.ctx, buf.data_ptr(), [d], 1, out.data_ptr(), None, s)
