@@ -119,9 +119,9 @@ extern "C" {
  *                    the line's mean (for model_order 2 or 3). Needs the row geometry with
  *                    deriv_axis == carrier_axis (the carrier decides which of +-omega is meant).
  *   exhaustive       batched path: 0 (default) finds the selected root by Newton's method and
- *                    certifies it with a root count -- in the row geometry by Rouche's theorem
- *                    against the noise-free polynomial, with the Schur-Cohn count where that test
- *                    does not decide; in the square geometry by the Schur-Cohn count -- (every root is
+ *                    certifies it with a root count -- in the row geometry with L <= 10 by Rouche's
+ *                    theorem against the noise-free polynomial, with the Schur-Cohn count where that
+ *                    test does not decide; otherwise by the Schur-Cohn count -- (every root is
  *                    computed only where the certificate fails), and the row geometry's eigenvector by power iteration
  *                    (Jacobi sweeps only where it does not settle); 1 computes every inner root by
  *                    Aberth-Ehrlich and, in the row geometry, runs the Jacobi sweeps for every

@@ -1,12 +1,12 @@
 // batched.cu -- the FP32 batched path: one persistent kernel over every pixel of every frame of
-// a call (frames of uneven sizes and windows mixed), one window-line run of kRowRun = 32 kRowP
-// consecutive pixels per warp work item, kRowP consecutive pixels per lane, items taken from a
-// global atomic counter.
+// a call (frames of uneven sizes and windows mixed), one window-line run of 32 P consecutive pixels
+// per warp work item, P consecutive pixels per lane (P = 16, or 8 on lines where that leaves fewer
+// lanes idle: a property of the frame), items taken from a global atomic counter.
 //
-// Per warp item (a run of one window line; lane l owns pixels l kRowP .. l kRowP + kRowP - 1):
-//   stage     the kRowRun + N - 1 analytic-signal samples the run's windows cover, one coalesced
-//             read into shared memory (Sec. 3, Eq. 2: the moving window), padded by one sample
-//             every kRowP so that the lanes' strided reads fall in distinct banks
+// Per warp item (a run of one window line; lane l owns pixels l P .. l P + P - 1):
+//   stage     the 32 P + N - 1 analytic-signal samples the run's windows cover, one coalesced read
+//             into shared memory (Sec. 3, Eq. 2: the moving window), padded by one sample every P
+//             so that the lanes' strided reads fall in distinct banks
 //   S         with forward-backward averaging R = (R_f + J conj(R_f) J)/2 is centro-Hermitian,
 //             so with the unitary Q = [[I, jI], [J, -jJ]] / sqrt(2) (even L) S = Q^H R Q =
 //             Re(Q^H R_f Q) is real symmetric; R u = l u  <=>  S x = l x with u = Q x. Written out,
@@ -42,15 +42,16 @@ namespace rmusic {
 
 constexpr int kBatWarps = 4;
 constexpr int kBatThreads = kBatWarps * 32;
-static_assert(kRowP == 16, "the staging pads one sample every 16 (shift by 4)");
-// staged samples of one run: kRowRun + N - 1 <= kRowRun + kMaxN - 1, plus one pad every kRowP
-constexpr int kSegLen = kRowRun + kMaxN + (kRowRun + kMaxN) / kRowP;
+// staged samples of one run: 32 P + N - 1 <= 32 P + kMaxN - 1, plus one pad every P, for P = 16 and 8
+constexpr int seg_len(int P) { return 32 * P + kMaxN + (32 * P + kMaxN) / P; }
+constexpr int kSegLen = seg_len(kRowP) > seg_len(kRowPMin) ? seg_len(kRowP) : seg_len(kRowPMin);
+static_assert(kRowP == 2 * kRowPMin, "the frames' pixels per lane are 16 or 8");
 
-// Shared-memory slot of staged sample e of a run (one pad slot after every kRowP samples): lane l's
-// sample i is e = l kRowP + i at 17 l + i + i / 16, so 32 lanes reading their own sample i touch 32
-// slots 17 apart -- 16 distinct 8-byte bank pairs, each read by two lanes (the two wavefronts a
-// 64-bit load takes anyway).
-__device__ __forceinline__ int seg_slot(int e) { return e + (e >> 4); }
+// Shared-memory slot of staged sample e of a run with P = 1 << ps pixels per lane (one pad slot after
+// every P samples): lane l's sample i is e = l P + i at (P + 1) l + i + i / P, so 32 lanes reading
+// their own sample i touch 32 slots P + 1 apart -- 16 distinct 8-byte bank pairs (P + 1 is odd),
+// each read by two lanes (the two wavefronts a 64-bit load takes anyway).
+__device__ __forceinline__ int seg_slot(int e, int ps) { return e + (e >> ps); }
 
 __host__ __device__ constexpr int tri(int r, int c, int L) {
     return r <= c ? r * L - (r * (r - 1)) / 2 + (c - r) : c * L - (c * (c - 1)) / 2 + (r - c);
@@ -428,12 +429,12 @@ __device__ __noinline__ void jacobi_eigvec(const float* Ssh, float sc, int max_s
 // The folded snapshot of Eq. 4-5 at local sample index i0 of the lane's staged run, as the two real
 // L-vectors X = [Re p, Im q], Y = [Im p, -Re q] (p_i = s[i] + s[L-1-i], q_i = s[i] - s[L-1-i]).
 template <int L>
-__device__ __forceinline__ void folded_snapshot(const float2* __restrict__ seg_l, int i0, float (&X)[L],
+__device__ __forceinline__ void folded_snapshot(const float2* __restrict__ seg_l, int ps, int i0, float (&X)[L],
                                                 float (&Y)[L]) {
     constexpr int h = L / 2;
 #pragma unroll
     for (int i = 0; i < h; ++i) {
-        const float2 a = seg_l[seg_slot(i0 + i)], b = seg_l[seg_slot(i0 + L - 1 - i)];
+        const float2 a = seg_l[seg_slot(i0 + i, ps)], b = seg_l[seg_slot(i0 + L - 1 - i, ps)];
         X[i] = a.x + b.x;
         Y[i] = a.y + b.y;
         X[h + i] = a.y - b.y;
@@ -479,7 +480,6 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
     if (lane < kStatSlots) sh_stat[wid][lane] = 0ull;
     __syncwarp();
     float2* seg = sh_seg[wid];
-    const float2* seg_l = seg + (kRowP + 1) * lane;  // the lane's own samples: seg_l[seg_slot(i)]
     float* const Ssh = sh_S + threadIdx.x;
 
     for (;;) {
@@ -494,27 +494,30 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
         const int wline = (int)((uint32_t)local / (uint32_t)F.nchunks);
         const int run = (int)((uint32_t)local % (uint32_t)F.nchunks);
         const int N = F.N, K = N - L + 1, wlen = F.wlen;
-        // every index below follows from these (the staging reads kRowRun + N - 1 <= kSegLen samples,
-        // a lane's windows reach its sample kRowP - 1 + N - 1, the store stays in window line wline);
+        const int ps = F.rowp_shift, P = 1 << ps, run_len = 32 << ps;
+        // every index below follows from these (the staging reads 32 P + N - 1 samples into at most
+        // kSegLen slots, a lane's windows reach its sample P - 1 + N - 1, the store stays in window
+        // line wline);
         // checked builds test them and skip a bad item whole (the test is uniform over the warp)
         if (!rm_check(f >= 0 && f < nframes && local >= 0 && local < (int64_t)F.wlines * F.nchunks && F.L == L &&
-                          N >= L && N <= kMaxN,
+                          N >= L && N <= kMaxN && P >= kRowPMin && P <= kRowP,
                       args.counters))
             continue;
-        const int a0 = run * kRowRun - N / 2;
+        const int a0 = run * run_len - N / 2;
+        const float2* seg_l = seg + (P + 1) * lane;  // the lane's own samples: seg_l[seg_slot(i, ps)]
         const float2* gl = gam + F.gam_off + (uint64_t)wline * wlen;
 
         // ---- stage the run's samples (coalesced) --------------------------------------------
         __syncwarp();  // every lane is done with the previous item's samples
-        for (int e = lane; e < kRowRun + N - 1; e += 32) {
+        for (int e = lane; e < run_len + N - 1; e += 32) {
             const int p = a0 + e;
-            seg[seg_slot(e)] = (p >= 0 && p < wlen) ? gl[p] : make_float2(0.f, 0.f);
+            seg[seg_slot(e, ps)] = (p >= 0 && p < wlen) ? gl[p] : make_float2(0.f, 0.f);
         }
         __syncwarp();
 
 #pragma unroll 1
-        for (int t = 0; t < kRowP; ++t) {
-            const int pos = run * kRowRun + lane * kRowP + t;
+        for (int t = 0; t < P; ++t) {
+            const int pos = run * run_len + lane * P + t;
             const bool inside = pos < wlen;
             const bool valid = inside && (pos - N / 2 >= 0) && (pos - N / 2 + N - 1 <= wlen - 1);
 
@@ -531,7 +534,7 @@ batched_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items
             for (int s = 0; s < nupd; ++s) {
                 const int i0 = t == 0 ? s : (s == 0 ? t - 1 + K : t - 1);
                 float X[L], Y[L];
-                folded_snapshot<L>(seg_l, i0, X, Y);
+                folded_snapshot<L>(seg_l, ps, i0, X, Y);
                 rank2_update<L>(S, X, Y, (t > 0 && s == 1) ? -1.f : 1.f);
             }
             if (WJ) __syncwarp();  // the warp-per-matrix sweeps of the previous pixel read every lane's S

@@ -132,7 +132,9 @@ int describe_frame(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev*
         F->nchunks = (d.width + kSqTX - 1) / kSqTX;  // tiles per tile row
         F->omega_ref = 6.283185307179586476925 * f0;
     } else {
-        F->nchunks = (F->wlen + kRowRun - 1) / kRowRun;
+        F->rowp_shift = row_pixels_per_lane_shift(F->wlen);
+        const int run = 32 << F->rowp_shift;
+        F->nchunks = (F->wlen + run - 1) / run;
         F->omega_ref = p.deriv_axis == p.carrier_axis ? 6.283185307179586476925 * f0 : 0.0;
     }
     // the solvers split a frame's work-item index with 32-bit arithmetic (far above any frame whose

@@ -21,10 +21,20 @@ namespace rmusic {
 constexpr int kMaxL = 12;        // largest covariance order L
 constexpr int kMaxN = 64;        // largest window length N
 constexpr int kMaxLine = 8192;   // longest carrier line the band-pass kernel accepts
-// Row geometry, FP32-batched path: one warp work item is a run of kRowRun consecutive pixels of a
-// window line, starting at a multiple of kRowRun; lane l owns its pixels l kRowP .. l kRowP + kRowP - 1.
+// Row geometry, FP32-batched path: one warp work item is a run of 32 P consecutive pixels of a
+// window line, starting at a multiple of 32 P; lane l owns its pixels l P .. l P + P - 1. P is a
+// property of the frame (FrameDev::rowp_shift, P = 1 << rowp_shift), kRowPMin <= P <= kRowP:
+// row_pixels_per_lane_shift picks it from the window-line length.
 constexpr int kRowP = 16;
+constexpr int kRowPMin = 8;
 constexpr int kRowRun = 32 * kRowP;
+
+// log2 of the pixels per lane for window lines of wlen pixels: 16 (anchors amortised over more
+// pixels), unless 8 leaves fewer idle lanes at the line's end by more than a sixteenth of the line
+// (lines of 256 or 768 pixels take 8, of 512 or 1024 take 16).
+__host__ __device__ constexpr int row_pixels_per_lane_shift(int wlen) {
+    return ((wlen + 511) / 512) * 512 - wlen > ((wlen + 255) / 256) * 256 - wlen + wlen / 16 ? 3 : 4;
+}
 
 enum : uint8_t { kStOk = 0, kStBorder = 1, kStDegenerate = 2, kStNotConverged = 3 };
 
@@ -45,7 +55,7 @@ struct FrameDev {
     int32_t nlines, len;  // carrier lines and their length
     int32_t k_lo, nb;     // kept DFT bins k_lo .. k_lo + nb - 1 of a carrier line
     int32_t wlines, wlen; // window lines and their length
-    int32_t nchunks;      // row geometry: work items per window line (ceil(wlen / kRowRun));
+    int32_t nchunks;      // row geometry: work items per window line (ceil(wlen / (32 << rowp_shift)));
                           // square geometry: tiles per tile row (ceil(W / 32))
     int32_t geom;         // kGeomRow or kGeomSquare (then L holds the half-width Lp, N = 2 Lp + 1)
     double omega_ref;     // carrier phase step removed from the angle (rad/pixel)
@@ -55,6 +65,7 @@ struct FrameDev {
     int32_t raw;          // 1: no band-pass; Gamma = the real line minus its mean
     int32_t band_r;       // band-pass schedule: 0 one CTA per carrier line; 8, 16 or 32: lines of
                           // 32 band_r samples in groups of 4 x 32 / band_r per CTA (warp FFTs)
+    int32_t rowp_shift;   // row geometry, FP32-batched path: log2 of the pixels each lane owns
 };
 
 // Index of the frame that owns global index `g` given each frame's start (non-decreasing).
