@@ -187,10 +187,10 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
 
 SOLVER_PROFILE = os.path.join(ROOT, "profiles", "batched_solver_L8_peaks4x1024.md")
 SOLVER_SOURCES = ["batched_kernel.cuh", "roots_device.cuh", "rmusic_device.cuh", "rmusic_launch.h",
-                  "batched_variants.h", "batched_l8.cu"]
+                  "batched_variants.h", "batched_l8.cu", "rouche_table.h"]
 SQUARE_PROFILE = os.path.join(ROOT, "profiles", "square_solver_Lp5_complex4x1024.md")
 SQUARE_SOURCES = ["square_kernel.cuh", "roots_device.cuh", "rmusic_device.cuh", "rmusic_launch.h",
-                  "square_variants.h", "square_l5.cu"]
+                  "square_variants.h", "square_l5.cu", "rouche_table.h"]
 
 
 def profiled_traffic(profile: str = SOLVER_PROFILE, sources=SOLVER_SOURCES):
