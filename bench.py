@@ -58,6 +58,8 @@ def parse():
                     help="rows per frame in the oracle sample (about 10 s on 16 cores); an eighth of "
                          "them, of one frame, for the one-core figure")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forward-steps", type=int, default=5,
+                    help="timed steps of the forward-only estimate on the main workload (0: skip)")
     ap.add_argument("--square-steps", type=int, default=5,
                     help="timed steps of the paper-geometry leg (square block, both derivatives and alpha)")
     ap.add_argument("--no-workloads", action="store_true",
@@ -294,11 +296,11 @@ def max_over_ranks(world, v: float) -> float:
 # ----------------------------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the workload
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(frames, rows_per_frame: int, nthreads: int = 0):
+def oracle_sample(frames, rows_per_frame: int, nthreads: int = 0, fb: int = 1, seed: int = 11872):
     import oracle as O
 
-    p = O.make_params(N_WIN, L_COV, 1, 0, 0, F0)
-    rng = np.random.default_rng(11872)
+    p = O.make_params(N_WIN, L_COV, fb, 0, 0, F0)
+    rng = np.random.default_rng(seed)
     samples = []
     t0 = time.perf_counter()
     cores = 0
@@ -514,6 +516,8 @@ def run_ours(args):
                 "solver_variants": variants,
                 "bandpass_ms": statistics.mean(bandpass_ms)}
 
+    fwd = (run_forward_leg(args, rank, world, dev, stream, flush, frames, x, step_ms_max)
+           if args.forward_steps > 0 else None)
     sq = run_square_leg(args, rank, world, dev, stream, flush) if args.square_steps > 0 else None
 
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
@@ -535,6 +539,8 @@ def run_ours(args):
                       "path": "plain FP32, thread per pixel, one launch per frame",
                       "timing": f"3 warm-ups, median of {args.plain_steps} event-timed steps, L2 flushed"},
             "speedup_vs_plain": value / plain_value}
+    if fwd is not None:
+        line["forward_estimate"] = fwd
     if sq is not None:
         line["paper_geometry"] = sq
     if not args.no_workloads:
@@ -570,6 +576,68 @@ def run_ours(args):
     dem.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_forward_leg(args, rank, world, dev, stream, flush, frames, x, fb_step_ms):
+    """The same workload on the forward estimate R = R_f alone (forward_backward = 0; Sec. 3, Eq. 4-5),
+    timed like the main leg (graph replay, L2 flushed between steps, CUDA events), with the error of
+    its maps against the oracle's forward estimate on a bounded sample; reported beside the main line."""
+    import torch
+
+    from paper_1910_11872_gb300 import rmusic
+
+    npx = x.numel()
+    out = torch.empty(npx, dtype=torch.float32, device=dev)
+    dem = rmusic.Demodulator(device=dev.index, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0,
+                             forward_backward=0, precision="batched", use_graph=1, timing=1, autotune=1)
+    for _ in range(args.warmup):
+        dem.run(x, out=out, with_status=False)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.forward_steps)]
+    solver_ms, psteps, eigfb, newton, rootfb, launches = [], [], [], [], [], 0
+    for k in range(args.forward_steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        dem.run(x, out=out, with_status=False, stream=stream)
+        ev[k][1].record(stream)
+        st = dem.stats()
+        solver_ms.append(st.solver_ms)
+        psteps.append(st.mean_power_steps)
+        eigfb.append(st.eig_fallback_frac)
+        newton.append(st.mean_newton_steps)
+        rootfb.append(st.root_fallback_frac)
+        launches += st.kernel_launches
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = max_over_ranks(world, statistics.mean(a.elapsed_time(b) for a, b in ev))
+    res = {"workload": WORKLOAD.replace("forward-backward", "forward estimate only"),
+           "value": npx * world / (step_ms * 1e3), "unit": "Mpixel/s", "ms_per_step": step_ms,
+           "steps": args.forward_steps, "gpu_launches": launches, "clocks": clk,
+           "kernel": f"batched_fwd_kernel<{L_COV}, {st.solver_ctas_per_sm}>",
+           "solver_ms": statistics.mean(solver_ms), "mean_power_steps": statistics.mean(psteps),
+           "eig_fallback_frac": statistics.mean(eigfb), "mean_newton_steps": statistics.mean(newton),
+           "root_fallback_frac": statistics.mean(rootfb),
+           "time_vs_forward_backward": step_ms / fb_step_ms,
+           "timing": "graph replay, L2 flushed between steps, CUDA events on the launching stream"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sout, sst, _ = dem.run(x, with_status=True)
+        torch.cuda.synchronize()
+        g_all = sout.view(len(frames), H, W).cpu().numpy()
+        s_all = sst.view(len(frames), H, W).cpu().numpy()
+        rows = max(1, args.cpu_rows // 8)
+        samples, n_or, dt, cores = oracle_sample(frames, rows, fb=0, seed=11873)
+        acc = {}
+        for snr, fr, g, s_, (ys, xs, vals, ost) in zip(SNRS, frames, g_all, s_all, samples):
+            acc[f"{int(snr)}dB"] = _oracle_compare(g[ys, xs], s_[ys, xs], vals, ost, fr.truth[ys, xs])
+        res["accuracy_vs_fp64_oracle"] = acc
+        res["cpu_baseline"] = {"value": n_or / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{rows} random full rows of each frame ({n_or} px), {dt:.1f} s wall"}
+    dem.close()
+    return res
 
 
 def run_square_leg(args, rank, world, dev, stream, flush):

@@ -76,14 +76,19 @@ extern "C" {
  *                    (integer N/2); pixels whose window leaves the line are border pixels.
  *   cov_order        L, length of the snapshots s_i = w[i .. i+L-1], i = 0 .. N-L, and order of
  *                    the L x L auto-correlation matrix (2 <= L <= 12, L <= N). The batched path
- *                    takes even L with forward_backward = 1; other cases need a plain path.
+ *                    takes even L with forward_backward = 1 (a real symmetric transform of R) and
+ *                    any L with forward_backward = 0 (the complex Hermitian R); odd L with the
+ *                    forward-backward average needs a plain path.
  *   model_order      number of complex exponentials per window; the method uses 1 (Eq. 2). The
  *                    plain paths also take 2 or 3 (a real fringe without the analytic step holds
  *                    exp(+-j omega), and a local offset one more at zero frequency): the noise
  *                    projector then removes the p largest eigenvalues' eigenvectors, and the
  *                    derivative comes from the one of the p roots nearest the unit circle whose
  *                    angle is nearest the expected one (2 pi f0). Needs cov_order > model_order.
- *   forward_backward 1: R = (R_f + J conj(R_f) J) / 2 (forward-backward average); 0: R = R_f.
+ *   forward_backward 1: R = (R_f + J conj(R_f) J) / 2 (forward-backward average); 0: R = R_f,
+ *                    the forward estimate of Eq. 4-5 alone (its signal root lies further inside
+ *                    the circle on noisy windows; both give the same derivative on noise-free
+ *                    constant-amplitude fringes).
  *   deriv_axis       0: windows run along x (rows); 1: along y (columns).
  *   carrier_axis     axis of the carrier and of the band-pass (0 = x, 1 = y).
  *   carrier_freq     f0 in cycles/pixel; the band keeps 1 <= k < len/2 with |k/len - f0| < B,

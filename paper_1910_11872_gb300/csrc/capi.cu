@@ -85,7 +85,8 @@ int describe_frame(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev*
         N = d.window_len ? d.window_len : p.window_len;
         L = d.cov_order ? d.cov_order : p.cov_order;
         if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
-        if (p.precision == RMUSIC_FP32_BATCHED && (!batched_supports(L) || p.forward_backward != 1))
+        if (p.precision == RMUSIC_FP32_BATCHED &&
+            !(p.forward_backward ? batched_supports(L) : batched_fwd_supports(L)))
             return RMUSIC_EUNSUPPORTED;
     }
     memset(F, 0, sizeof(*F));
@@ -166,23 +167,35 @@ constexpr int kCounterSlots = 64;  // [0, kStatSlot) work counters, [kStatSlot .
 constexpr int kStatSlot = 32;
 
 // A solver key names one compiled solver family: the covariance order L of the row-window
-// solver (2 .. kMaxL), or kSquareKey0 + Lp for the square-block solver.
+// solver (2 .. kMaxL), kSquareKey0 + Lp for the square-block solver, kFwdKey0 + L for the row-window
+// solver of the forward estimate (no forward-backward average).
 constexpr int kSquareKey0 = 16;
-constexpr int kKeys = kSquareKey0 + kMaxSquareLp + 1;
-static_assert(kMaxL < kSquareKey0, "solver keys overlap");
+constexpr int kFwdKey0 = 32;
+constexpr int kKeys = kFwdKey0 + kMaxL + 1;
+static_assert(kMaxL < kSquareKey0 && kSquareKey0 + kMaxSquareLp < kFwdKey0, "solver keys overlap");
 
-bool key_square(int key) { return key >= kSquareKey0; }
+bool key_square(int key) { return key >= kSquareKey0 && key < kFwdKey0; }
+bool key_fwd(int key) { return key >= kFwdKey0; }
 bool solver_supports(int key) {
-    return key_square(key) ? square_supports(key - kSquareKey0) : batched_supports(key);
+    return key_fwd(key) ? batched_fwd_supports(key - kFwdKey0)
+         : key_square(key) ? square_supports(key - kSquareKey0) : batched_supports(key);
 }
 int solver_num_variants(int key) {
-    return key_square(key) ? square_num_variants(key - kSquareKey0) : batched_num_variants(key);
+    return key_fwd(key) ? batched_fwd_num_variants(key - kFwdKey0)
+         : key_square(key) ? square_num_variants(key - kSquareKey0) : batched_num_variants(key);
 }
 int solver_default_variant(int key) {
-    return key_square(key) ? square_default_variant(key - kSquareKey0) : batched_default_variant(key);
+    return key_fwd(key) ? batched_fwd_default_variant(key - kFwdKey0)
+         : key_square(key) ? square_default_variant(key - kSquareKey0) : batched_default_variant(key);
 }
 int solver_ctas(int key, int v) {
-    return key_square(key) ? square_variant_ctas(key - kSquareKey0, v) : batched_variant_ctas(key, v);
+    return key_fwd(key) ? batched_fwd_variant_ctas(key - kFwdKey0, v)
+         : key_square(key) ? square_variant_ctas(key - kSquareKey0, v) : batched_variant_ctas(key, v);
+}
+// The solver key of a frame of the plan (its table entry's geometry and covariance order).
+int frame_key(const rmusic_params& p, const FrameDev& F) {
+    if (F.geom == kGeomSquare) return kSquareKey0 + F.L;
+    return p.forward_backward ? F.L : kFwdKey0 + F.L;
 }
 
 struct GraphEntry {
@@ -340,7 +353,7 @@ int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Pla
             plan->max_kc = std::max(plan->max_kc, F.cross_kc);
         }
         plan->max_len = std::max(plan->max_len, F.len);
-        const int key = F.geom == kGeomSquare ? kSquareKey0 + F.L : F.L;
+        const int key = frame_key(ctx->p, F);
         if (i == 0 || F.L != plan->frames[i - 1].L) {
             plan->group_L.push_back(key);
             plan->group_first.push_back(i);
@@ -472,8 +485,8 @@ void store_tune(int device, int key, int v, float ms) {
     fprintf(f,
             "{\"device\": \"%s\", \"key\": %d, \"%s\": %d, \"variant\": %d, \"ctas_per_sm\": %d, "
             "\"ms\": %.4f}\n",
-            device_key(device).c_str(), key, key_square(key) ? "Lp" : "L",
-            key_square(key) ? key - kSquareKey0 : key, v, solver_ctas(key, v), ms);
+            device_key(device).c_str(), key, key_square(key) ? "Lp" : key_fwd(key) ? "L_fwd" : "L",
+            key_square(key) ? key - kSquareKey0 : key_fwd(key) ? key - kFwdKey0 : key, v, solver_ctas(key, v), ms);
     fclose(f);
 }
 
@@ -501,7 +514,8 @@ bool solver_tuned(rmusic_ctx* ctx, int L) {
 int solver_grid(rmusic_ctx* ctx, int L, int v) {
     if (ctx->grid_by_Lv[L][v] == 0)
         ctx->grid_by_Lv[L][v] =
-            key_square(L) ? square_grid(L - kSquareKey0, v, ctx->device) : batched_grid(L, v, ctx->device);
+            key_fwd(L) ? batched_fwd_grid(L - kFwdKey0, v, ctx->device)
+            : key_square(L) ? square_grid(L - kSquareKey0, v, ctx->device) : batched_grid(L, v, ctx->device);
     return ctx->grid_by_Lv[L][v];
 }
 
@@ -530,6 +544,10 @@ cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, fl
     a.polish64 = p.polish_fp64;
     a.exhaustive = p.exhaustive;
     a.counters = stat_counters;
+    if (key_fwd(key))
+        return launch_batched_fwd(key - kFwdKey0, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
+                                  plan.group_items[g], ctx->d_counters + g, gamma, d_out, d_status, a,
+                                  solver_grid(ctx, key, v), s);
     return launch_batched(key, v, ctx->d_table + plan.group_first[g], plan.group_count[g], plan.group_items[g],
                           ctx->d_counters + g, gamma, d_out, d_status, a, solver_grid(ctx, key, v), s);
 }
@@ -1035,8 +1053,9 @@ int rmusic_demodulate_frames_host_async(rmusic_ctx* ctx, const void* h_frames, s
 
 int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant) {
     if (!ctx || ctx->p.precision != RMUSIC_FP32_BATCHED) return ctx ? RMUSIC_EUNSUPPORTED : RMUSIC_EINVAL;
-    const int key = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? kSquareKey0 + order : order;
-    if (order < 1 || key < 0 || key >= kKeys || !solver_supports(key)) return RMUSIC_EINVAL;
+    const int key = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? kSquareKey0 + order
+                  : ctx->p.forward_backward ? order : kFwdKey0 + order;
+    if (order < 1 || order > kMaxL || key < 0 || key >= kKeys || !solver_supports(key)) return RMUSIC_EINVAL;
     if (variant < -1 || variant >= solver_num_variants(key)) return RMUSIC_EINVAL;
     ctx->variant_by_L[key] = variant;
     for (auto& g : ctx->graphs) drop_graph(ctx, g);  // captured graphs hold the previous variant

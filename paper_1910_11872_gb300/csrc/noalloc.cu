@@ -79,10 +79,11 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
     if (!params || n_frames < 0) return RMUSIC_EINVAL;
     const rmusic_params& p = *params;
     // the checks every entry point makes (the codes rmusic_create returns), then what this entry
-    // point adds: only the FP32-batched row-window path, without the 2-D band-pass or raw input
+    // point adds: only the FP32-batched row-window path with the forward-backward average, without
+    // the 2-D band-pass or raw input
     if (int rc = params_check(p)) return rc;
-    if (p.precision != RMUSIC_FP32_BATCHED || p.geometry != RMUSIC_GEOM_ROW || p.band_cross != 0.0 ||
-        p.raw_input != 0)
+    if (p.precision != RMUSIC_FP32_BATCHED || p.geometry != RMUSIC_GEOM_ROW || p.forward_backward != 1 ||
+        p.band_cross != 0.0 || p.raw_input != 0)
         return RMUSIC_EUNSUPPORTED;
     if (n_frames == 0) return RMUSIC_OK;
     if (!d_frames || !descs || !d_out) return RMUSIC_EINVAL;

@@ -82,6 +82,17 @@ cudaError_t launch_batched(int L, int v, const FrameDev* d_frames, int nframes, 
                            uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream);
 int batched_grid(int L, int v, int device);
 
+// Batched FP32 path without the forward-backward average (the paper's forward estimate R = R_f):
+// the same work items and arguments on the complex Hermitian R, any covariance order 2 .. kMaxL.
+bool batched_fwd_supports(int L);
+int batched_fwd_num_variants(int L);
+int batched_fwd_default_variant(int L);
+int batched_fwd_variant_ctas(int L, int v);
+cudaError_t launch_batched_fwd(int L, int v, const FrameDev* d_frames, int nframes, int64_t total_items,
+                               unsigned long long* d_counter, const float2* d_gamma, float* d_out,
+                               uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream);
+int batched_fwd_grid(int L, int v, int device);
+
 // Square-block FP32 path (the paper's geometry): persistent, one 32 x 4 pixel tile per CTA work
 // item, over all frames that share the half-width Lp. `counter` must be zero when it starts.
 constexpr int kMaxSquareLp = 8;

@@ -416,18 +416,29 @@ __device__ __forceinline__ int roots_inside(const cx<float>* c, float r) {
 // certificate below (rouche_table.h), for the row solver's covariance orders.
 template <int L>
 __device__ __forceinline__ constexpr float rouche_g(int k) {
-    if constexpr (L == 4) return rouche_g4(k);
+    static_assert(L >= 3 && L <= 12, "tabulated for L = 3 .. 12");
+    if constexpr (L == 3) return rouche_g3(k);
+    else if constexpr (L == 4) return rouche_g4(k);
+    else if constexpr (L == 5) return rouche_g5(k);
     else if constexpr (L == 6) return rouche_g6(k);
+    else if constexpr (L == 7) return rouche_g7(k);
     else if constexpr (L == 8) return rouche_g8(k);
+    else if constexpr (L == 9) return rouche_g9(k);
     else if constexpr (L == 10) return rouche_g10(k);
+    else if constexpr (L == 11) return rouche_g11(k);
     else return rouche_g12(k);
 }
 template <int L>
 __device__ __forceinline__ const float* rouche_min() {
-    if constexpr (L == 4) return kRcMin4;
+    if constexpr (L == 3) return kRcMin3;
+    else if constexpr (L == 4) return kRcMin4;
+    else if constexpr (L == 5) return kRcMin5;
     else if constexpr (L == 6) return kRcMin6;
+    else if constexpr (L == 7) return kRcMin7;
     else if constexpr (L == 8) return kRcMin8;
+    else if constexpr (L == 9) return kRcMin9;
     else if constexpr (L == 10) return kRcMin10;
+    else if constexpr (L == 11) return kRcMin11;
     else return kRcMin12;
 }
 
