@@ -6,24 +6,35 @@
 // differ by their wrapped difference. That order is Kruskal's algorithm for the maximum spanning
 // forest of the pixel grid weighted by edge reliability, and the result is the 2 pi jumps
 // integrated along that forest: it depends on the forest only, not on the order in which its
-// edges are found. The GPU builds the same forest with Boruvka's algorithm, whose rounds are
-// data parallel:
+// edges are found. Edge weights are made unique by the edge index (reliability first, then the
+// smaller index), so the forest is unique, and any algorithm that only ever adds forest edges
+// reproduces the sequential result bit for bit. The GPU builds it in two phases:
 //   reliability  per pixel, R = 1 / D from the wrapped second differences (0 where a neighbour
 //                is missing), computed with explicitly rounded float32 operations so that every
 //                comparison below sees exactly the values of the sequential method;
-//   per round    every component finds its most reliable outgoing edge (64-bit atomicMax on
-//                (reliability bits, ~edge index): reliability first, then the smaller index),
-//                hooks onto the component across it (of two components that chose the same edge
-//                the smaller label stays the root) with the integer shift that makes the edge's
-//                endpoints differ by their wrapped difference, the hooks are resolved to roots
-//                by pointer jumping in place (shifts summed along the way; parent and shift share
-//                one 64-bit word, so a jump always reads a consistent pair), and every pixel is
-//                relabelled. Four launches per round; a round with nothing left to join makes
-//                the later rounds return at once.
-//                Each round at least halves the components, so ceil(log2(pixels)) rounds finish.
+//   tiles        one CTA per 32 x 32 tile runs Boruvka's rounds in shared memory: every local
+//                component finds its most reliable edge over ALL its edges, those that leave the
+//                tile included; where that edge stays inside the tile the component hooks across
+//                it (the most reliable edge leaving a set of pixels belongs to the forest: the cut
+//                property), where it leaves the tile the component waits (others may still hook
+//                onto it). Rounds repeat until no component hooks. What is left of the tile's
+//                edges to the global phase: every edge that leaves the tile, and the edges inside
+//                it between different local components;
+//   global       Boruvka's rounds over that edge list and the local components that touch it
+//                (a few per cent of the pixels and edges), two launches per round: the first
+//                relabels every component to the root its hook chain leads to (in-place pointer
+//                jumping; parent and shift share one 64-bit word, so a jump always reads a
+//                consistent pair) and offers every edge between different components to both
+//                (64-bit atomicMax on (reliability bits, ~edge index), issued only when it can
+//                win); the second lets every root hook onto the component across its best edge
+//                (of two roots that chose the same edge the smaller label stays the root) with the
+//                integer shift that makes the edge's endpoints differ by their wrapped difference.
+//                A round after one that joined nothing returns at once. Each round at least halves
+//                the components that still have edges.
 //   anchor       each connected region keeps its first pixel (row-major) at its wrapped value;
 //                every component carries its smallest pixel index through the merges.
-// All integer bookkeeping is exact; the output is phi + 2 pi k in float32.
+// A pixel's k is its shift within its local component plus that component's shift within its
+// global component. All integer bookkeeping is exact; the output is phi + 2 pi k in float32.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,6 +46,9 @@ namespace rmusic {
 namespace {
 
 constexpr int kUwThreads = 256;
+constexpr int kTile = 32;                          // tile side (pixels)
+constexpr int kTilePx = kTile * kTile;             // pixels per tile
+constexpr int kPxPerThread = kTilePx / kUwThreads; // 4: rows w, w + 8, w + 16, w + 24 of warp w
 constexpr float kPiF = 3.14159265358979f;
 constexpr float kTwoPiF = 6.28318530717959f;
 
@@ -50,6 +64,22 @@ __device__ __forceinline__ int jump(float pp, float pq) {
     return d > kPiF ? -1 : (d <= -kPiF ? 1 : 0);
 }
 
+// Edge e = 2 p + dir (dir 0: p -> p + 1, dir 1: p -> p + W) of weight w = rel[p] + rel[q]: the
+// larger key is the more reliable edge, ties going to the smaller index.
+__device__ __forceinline__ unsigned long long edge_key(float w, uint32_t e) {
+    return ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(0xffffffffu - e);
+}
+__device__ __forceinline__ uint32_t key_edge(unsigned long long key) {
+    return 0xffffffffu - (uint32_t)(key & 0xffffffffull);
+}
+
+// (parent, shift) of a component in one word: the shift is added to the component's k values
+__device__ __forceinline__ unsigned long long pack_hook(int32_t par, int32_t sh) {
+    return ((unsigned long long)(uint32_t)par << 32) | (unsigned long long)(uint32_t)sh;
+}
+__device__ __forceinline__ int32_t hook_par(unsigned long long w) { return (int32_t)(uint32_t)(w >> 32); }
+__device__ __forceinline__ int32_t hook_sh(unsigned long long w) { return (int32_t)(uint32_t)(w & 0xffffffffull); }
+
 struct UwArgs {
     const FrameDev* fr;
     int nframes;
@@ -60,25 +90,75 @@ struct UwArgs {
     int64_t out_maps;
 };
 
-__device__ __forceinline__ const FrameDev& frame_of(const UwArgs& a, int64_t g, int* fidx) {
-    const int f = find_frame(a.fr, a.nframes, g, [](const FrameDev& F) { return (int64_t)F.gam_off; });
-    *fidx = f;
-    return a.fr[f];
+// Workspace carved from one buffer. Per pixel g: wph (wrapped phase), rel, fid (frame), comp (root
+// of g's local component), kk (g's shift within it); per local root r: minpix, comp2 (r's root as
+// of the last relabelling), kk2 (r's shift to it), hook, best (two copies: even and odd rounds). The edge list holds at most the
+// grid's two edges per pixel, the node list at most one local root per pixel.
+struct UwWork {
+    float* wph;
+    float* rel;
+    int32_t* fid;
+    int32_t* comp;
+    int32_t* kk;
+    int32_t* minpix;
+    int32_t* comp2;
+    int32_t* kk2;
+    unsigned long long* hook;
+    unsigned long long* best;   // two arrays of npx: best of even rounds, then of odd rounds
+    uint4* edges;       // (e, weight bits, local root of p, local root of q) per listed edge
+    int32_t* nodes;     // local roots with at least one edge in the list
+    int32_t* tile_start;  // nframes + 1 entries: first tile of each frame, then the total
+    unsigned long long* counts;  // listed edges (low word) and nodes (high word)
+    int32_t* flags;     // rounds + 1 live flags
+};
+
+__device__ __forceinline__ int32_t n_edges(const UwWork& w) { return (int32_t)(uint32_t)(*w.counts & 0xffffffffull); }
+__device__ __forceinline__ int32_t n_nodes(const UwWork& w) { return (int32_t)(uint32_t)(*w.counts >> 32); }
+
+// Tiles of a frame: ceil(H / 32) x ceil(W / 32), row-major.
+__device__ __forceinline__ int32_t frame_tiles(const FrameDev& F) {
+    return ((F.H + kTile - 1) / kTile) * ((F.W + kTile - 1) / kTile);
 }
 
-// wph[g] = wrapped phase, fid[g] = frame, comp[g] = g, kk[g] = 0, minpix[g] = g
-__global__ void __launch_bounds__(kUwThreads) uw_init(UwArgs a, float* __restrict__ wph, int32_t* __restrict__ fid,
-                                                     int32_t* __restrict__ comp, int32_t* __restrict__ kk,
-                                                     int32_t* __restrict__ minpix) {
+// tile_start[f] = tiles of frames 0 .. f - 1 (one block; frames in chunks of its width), counters
+// cleared, round 0 live.
+__global__ void __launch_bounds__(kUwThreads) uw_prepare(UwArgs a, UwWork w, int rounds) {
+    __shared__ int32_t wsum[kUwThreads / 32];
+    __shared__ int32_t carry;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) carry = 0;
+    for (int i = t; i < rounds + 1; i += blockDim.x) w.flags[i] = i == 0 ? 1 : 0;
+    if (t == 0) *w.counts = 0ull;
+    __syncthreads();
+    for (int base = 0; base < a.nframes; base += kUwThreads) {
+        const int f = base + t;
+        const int32_t n = f < a.nframes ? frame_tiles(a.fr[f]) : 0;
+        int32_t x = n;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        int32_t before = carry;
+        for (int k = 0; k < wid; ++k) before += wsum[k];
+        if (f < a.nframes) w.tile_start[f] = before + x - n;
+        __syncthreads();
+        if (t == kUwThreads - 1) carry = before + x;
+        __syncthreads();
+    }
+    if (t == 0) w.tile_start[a.nframes] = carry;
+}
+
+// wph[g] = wrapped phase, fid[g] = frame
+__global__ void __launch_bounds__(kUwThreads) uw_init(UwArgs a, float* __restrict__ wph, int32_t* __restrict__ fid) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
-        int f;
-        const FrameDev& F = frame_of(a, g, &f);
+        const int f = find_frame(a.fr, a.nframes, g, [](const FrameDev& F) { return (int64_t)F.gam_off; });
+        const FrameDev& F = a.fr[f];
         const int64_t local = g - (int64_t)F.gam_off;
         wph[g] = a.in[F.out_off + a.in_maps * (int64_t)F.H * F.W + local];
         fid[g] = f;
-        comp[g] = (int32_t)g;
-        kk[g] = 0;
-        minpix[g] = (int32_t)g;
     }
 }
 
@@ -114,141 +194,426 @@ __global__ void __launch_bounds__(kUwThreads) uw_reliability(UwArgs a, const flo
     }
 }
 
-// best[c] = max over the edges leaving component c of (reliability bits << 32 | ~edge index)
-__global__ void __launch_bounds__(kUwThreads) uw_best_edges(UwArgs a, const float* __restrict__ wph,
-                                                           const int32_t* __restrict__ fid,
-                                                           const float* __restrict__ rel,
-                                                           const int32_t* __restrict__ comp,
-                                                           unsigned long long* __restrict__ best,
-                                                           const int32_t* __restrict__ live) {
-    if (!*live) return;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
-        if (isnan(wph[g])) continue;
-        const FrameDev& F = a.fr[fid[g]];
-        const int64_t local = g - (int64_t)F.gam_off;
-        const int i = (int)(local / F.W), j = (int)(local % F.W);
-        const int32_t cp = comp[g];
+// Every thread of the block asks for ne slots of the edge list and nn of the node list; one 64-bit
+// atomicAdd per block on the packed lengths (edges in the low word: at most two per pixel, below
+// 2^32). Returns the thread's first slots. Called by all threads.
+__device__ __forceinline__ void block_reserve(int32_t ne, int32_t nn, unsigned long long* counter, int32_t* s_wsum,
+                                              unsigned long long* s_base, int32_t* e0, int32_t* n0) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int32_t xe = ne, xn = nn;  // inclusive scans within the warp
 #pragma unroll
-        for (int dir = 0; dir < 2; ++dir) {
-            if (dir == 0 ? j + 1 >= F.W : i + 1 >= F.H) continue;
-            const int64_t q = g + (dir == 0 ? 1 : (int64_t)F.W);
-            if (isnan(wph[q])) continue;
-            const int32_t cq = comp[q];
-            if (cp == cq) continue;
-            const float w = __fadd_rn(rel[g], rel[q]);
-            const unsigned long long e = 2ull * (unsigned long long)g + (unsigned long long)dir;
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(w) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)e);
-            atomicMax(best + cp, key);
-            atomicMax(best + cq, key);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t ye = __shfl_up_sync(0xffffffffu, xe, o), yn = __shfl_up_sync(0xffffffffu, xn, o);
+        if (lane >= o) {
+            xe += ye;
+            xn += yn;
         }
+    }
+    if (lane == 31) {
+        s_wsum[wid] = xe;
+        s_wsum[kUwThreads / 32 + wid] = xn;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int32_t te = 0, tn = 0;
+        for (int k = 0; k < kUwThreads / 32; ++k) {
+            const int32_t ve = s_wsum[k], vn = s_wsum[kUwThreads / 32 + k];
+            s_wsum[k] = te;
+            s_wsum[kUwThreads / 32 + k] = tn;
+            te += ve;
+            tn += vn;
+        }
+        const unsigned long long add = ((unsigned long long)(uint32_t)tn << 32) | (unsigned long long)(uint32_t)te;
+        *s_base = add ? atomicAdd(counter, add) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long base = *s_base;
+    *e0 = (int32_t)(uint32_t)(base & 0xffffffffull) + s_wsum[wid] + xe - ne;
+    *n0 = (int32_t)(uint32_t)(base >> 32) + s_wsum[kUwThreads / 32 + wid] + xn - nn;
+    __syncthreads();
+}
+
+// The most reliable edge seen so far into *slot: a plain read first, so that the atomic is issued
+// only by edges that can still win (best values only grow while edges are scanned).
+__device__ __forceinline__ void offer(unsigned long long* slot, unsigned long long key) {
+    if (key > *(volatile unsigned long long*)slot) atomicMax(slot, key);
+}
+
+// One CTA per 32 x 32 tile (persistent over the tiles of all frames). Pixel l = 32 i + j of the
+// tile is handled by thread l % 256. Shared state per pixel: phase, reliability, local component
+// (its root's tile index; two buffers, read and written alternately by the rounds), shift within
+// it, smallest member (tile index: row-major in the tile is row-major in the frame), best edge,
+// hook, and the best of the edges that leave the tile at this pixel.
+__global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
+    __shared__ float s_ph[kTilePx];
+    __shared__ float s_rel[kTilePx];
+    __shared__ int16_t s_compb[2][kTilePx];
+    __shared__ int32_t s_kk[kTilePx];
+    __shared__ int32_t s_min[kTilePx];
+    __shared__ unsigned long long s_best[kTilePx];
+    __shared__ unsigned long long s_hook[kTilePx];
+    __shared__ unsigned long long s_cross[kTilePx];
+    __shared__ uint8_t s_own[kTilePx];  // bit 0: owns the edge to the right tile, bit 1: to the tile below
+    __shared__ int32_t s_wsum[2 * (kUwThreads / 32)];
+    __shared__ unsigned long long s_base;
+    __shared__ int s_any[2];
+    const int t = threadIdx.x;
+    const int32_t ntiles = w.tile_start[a.nframes];
+    for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int lo = 0, hi = a.nframes - 1;  // frame of the tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (w.tile_start[mid] <= tile)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const FrameDev& F = a.fr[lo];
+        const int H = F.H, W = F.W;
+        const int ntx = (W + kTile - 1) / kTile;
+        const int lt = tile - w.tile_start[lo];
+        const int y0 = (lt / ntx) * kTile, x0 = (lt % ntx) * kTile;
+        const int64_t g0 = (int64_t)F.gam_off;
+        const int64_t tg = g0 + (int64_t)y0 * W + x0;  // pixel (0, 0) of the tile
+        bool in[kPxPerThread];
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads, i = l >> 5, j = l & 31;
+            const int y = y0 + i, x = x0 + j;
+            in[k] = y < H && x < W;
+            const int64_t g = tg + (int64_t)i * W + j;
+            // the pixel and its neighbours across the tile's sides (at most one horizontal and one
+            // vertical), all loads issued before any is used
+            const bool hr = in[k] && j == kTile - 1 && x + 1 < W, hl = in[k] && j == 0 && x >= 1;
+            const bool vd = in[k] && i == kTile - 1 && y + 1 < H, vu = in[k] && i == 0 && y >= 1;
+            const int64_t gh = hr ? g + 1 : g - 1, gv = vd ? g + W : g - W;
+            const float nan = __int_as_float(0x7fffffff);
+            float ph = nan, r = 0.f, phh = nan, rh = 0.f, phv = nan, rv = 0.f;
+            if (in[k]) {
+                ph = w.wph[g];
+                r = w.rel[g];
+            }
+            if (hr || hl) {
+                phh = w.wph[gh];
+                rh = w.rel[gh];
+            }
+            if (vd || vu) {
+                phv = w.wph[gv];
+                rv = w.rel[gv];
+            }
+            unsigned long long cross = 0ull;
+            uint8_t own = 0;
+            if (isnan(ph)) {
+                r = 0.f;
+            } else {
+                if (!isnan(phh)) {
+                    cross = max(cross, hr ? edge_key(__fadd_rn(r, rh), (uint32_t)(2 * g))
+                                          : edge_key(__fadd_rn(rh, r), (uint32_t)(2 * gh)));
+                    own |= hr ? 1 : 0;
+                }
+                if (!isnan(phv)) {
+                    cross = max(cross, vd ? edge_key(__fadd_rn(r, rv), (uint32_t)(2 * g + 1))
+                                          : edge_key(__fadd_rn(rv, r), (uint32_t)(2 * gv + 1)));
+                    own |= vd ? 2 : 0;
+                }
+            }
+            s_ph[l] = ph;
+            s_rel[l] = r;
+            s_cross[l] = cross;
+            s_own[l] = own;
+            s_compb[0][l] = (int16_t)l;
+            s_compb[1][l] = (int16_t)l;
+            s_kk[l] = 0;
+            s_min[l] = (int16_t)l;
+            s_best[l] = 0ull;
+            s_hook[l] = pack_hook(l, 0);
+        }
+        if (t == 0) s_any[0] = s_any[1] = 0;
+        __syncthreads();
+
+        // Boruvka's rounds inside the tile; each round that hooks merges at least two components.
+        // Round r reads the labels of round r - 1 (cur) resolved through its hooks and writes them
+        // to nxt, so the relabelling needs no barrier of its own.
+        int16_t* cur = s_compb[0];
+        int16_t* nxt = s_compb[1];
+        for (int round = 0;; ++round) {
+            int* any = &s_any[round & 1];
+            if (t == 0) s_any[(round + 1) & 1] = 0;  // read last in round - 1, before its last barrier
+            // relabel; every component's most reliable edge, those leaving the tile included
+#pragma unroll
+            for (int k = 0; k < kPxPerThread; ++k) {
+                const int l = t + k * kUwThreads;
+                if (isnan(s_ph[l])) continue;
+                const unsigned long long hw = s_hook[cur[l]];
+                const int32_t c = hook_par(hw);
+                nxt[l] = (int16_t)c;
+                s_kk[l] += hook_sh(hw);
+                if (s_cross[l]) offer(&s_best[c], s_cross[l]);
+                const int64_t g = tg + (int64_t)(l >> 5) * W + (l & 31);
+                if ((l & 31) + 1 < kTile && !isnan(s_ph[l + 1])) {
+                    const int32_t cq = hook_par(s_hook[cur[l + 1]]);
+                    if (cq != c) {
+                        const unsigned long long key = edge_key(__fadd_rn(s_rel[l], s_rel[l + 1]), (uint32_t)(2 * g));
+                        offer(&s_best[c], key);
+                        offer(&s_best[cq], key);
+                    }
+                }
+                if ((l >> 5) + 1 < kTile && !isnan(s_ph[l + kTile])) {
+                    const int32_t cq = hook_par(s_hook[cur[l + kTile]]);
+                    if (cq != c) {
+                        const unsigned long long key =
+                            edge_key(__fadd_rn(s_rel[l], s_rel[l + kTile]), (uint32_t)(2 * g + 1));
+                        offer(&s_best[c], key);
+                        offer(&s_best[cq], key);
+                    }
+                }
+            }
+            __syncthreads();
+            // roots whose best edge stays in the tile hook across it
+#pragma unroll
+            for (int k = 0; k < kPxPerThread; ++k) {
+                const int l = t + k * kUwThreads;
+                if (isnan(s_ph[l]) || nxt[l] != l) continue;
+                const unsigned long long key = s_best[l];
+                unsigned long long hk = pack_hook(l, 0);
+                if (key) {
+                    // the edge's first pixel p relative to the tile: d = pi W + pj; an edge inside
+                    // the tile has 0 <= pi, pj and both endpoints in rows and columns 0 .. 31 (a
+                    // pixel left of or above the tile gives d < 0 or pj >= W - 1 >= 32)
+                    const uint32_t e = key_edge(key);
+                    const int64_t d = (int64_t)(e >> 1) - tg;
+                    if (d >= 0) {
+                        const uint32_t pi = (uint32_t)d / (uint32_t)W, pj = (uint32_t)d - pi * (uint32_t)W;
+                        const uint32_t qi = pi + (e & 1u), qj = pj + 1u - (e & 1u);
+                        if (qi < kTile && qj < kTile) {
+                            const int pl = (int)(pi * kTile + pj), ql = (int)(qi * kTile + qj);
+                            const int32_t cp = nxt[pl], cq = nxt[ql];
+                            const int32_t other = cp == l ? cq : cp;
+                            if (!(s_best[other] == key && l < other)) {
+                                const int s = jump(s_ph[pl], s_ph[ql]);
+                                hk = pack_hook(other, cq == l ? s_kk[pl] + s - s_kk[ql] : s_kk[ql] - s - s_kk[pl]);
+                                *any = 1;
+                            }
+                        }
+                    }
+                }
+                s_hook[l] = hk;
+            }
+            __syncthreads();
+            if (!*any || round == kTilePx - 1) break;  // (a productive round merges: < 1024 of them)
+            // hooks resolved to roots in place (each jump moves up a chain of fewer than 1024
+            // components); the smallest member goes to the root; best edges cleared
+#pragma unroll
+            for (int k = 0; k < kPxPerThread; ++k) {
+                const int l = t + k * kUwThreads;
+                if (isnan(s_ph[l]) || nxt[l] != l) continue;
+                s_best[l] = 0ull;
+                volatile unsigned long long* vh = s_hook;
+                unsigned long long hw = vh[l];
+                for (int it = 0; it < kTilePx; ++it) {
+                    const int32_t p = hook_par(hw);
+                    if (p == l) break;
+                    const unsigned long long wp = vh[p];
+                    const int32_t pp = hook_par(wp);
+                    if (pp == p) break;
+                    hw = pack_hook(pp, hook_sh(hw) + hook_sh(wp));
+                    vh[l] = hw;
+                }
+                const int32_t r = hook_par(hw);
+                if (r != l) atomicMin(&s_min[r], s_min[l]);
+            }
+            __syncthreads();
+            int16_t* sw = cur;
+            cur = nxt;
+            nxt = sw;
+        }
+
+        // local components out (nxt holds the last labels): comp (as a pixel index), kk; per local
+        // root its smallest pixel and the identity as its global state
+        const int16_t* fin = nxt;
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            if (!in[k]) continue;
+            const int64_t g = tg + (int64_t)(l >> 5) * W + (l & 31);
+            const int32_t c = fin[l];
+            w.comp[g] = (int32_t)(tg + (int64_t)(c >> 5) * W + (c & 31));
+            w.kk[g] = s_kk[l];
+            if (c == l) {
+                const int32_t m = s_min[l];
+                w.minpix[g] = (int32_t)(tg + (int64_t)(m >> 5) * W + (m & 31));
+                w.comp2[g] = (int32_t)g;
+                w.kk2[g] = 0;
+                w.best[g] = 0ull;  // best of round 0
+                w.hook[g] = pack_hook((int32_t)g, 0);
+            }
+        }
+        __syncthreads();
+        int32_t* s_mark = s_kk;  // free now: marks the local roots that the global edges touch
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) s_mark[t + k * kUwThreads] = 0;
+        __syncthreads();
+
+        // the global phase's edges: every edge this tile owns across its right and lower sides,
+        // and the edges inside the tile between different local components; and the local roots
+        // that they touch (those with an edge out of the tile on any side, or such an edge inside)
+        int32_t ne = 0;
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            if (isnan(s_ph[l])) continue;
+            const int32_t c = fin[l];
+            if (s_cross[l]) s_mark[c] = 1;
+            ne += (s_own[l] & 1) + ((s_own[l] >> 1) & 1);
+            if ((l & 31) + 1 < kTile && !isnan(s_ph[l + 1]) && fin[l + 1] != c) {
+                ++ne;
+                s_mark[c] = 1;
+                s_mark[fin[l + 1]] = 1;
+            }
+            if ((l >> 5) + 1 < kTile && !isnan(s_ph[l + kTile]) && fin[l + kTile] != c) {
+                ++ne;
+                s_mark[c] = 1;
+                s_mark[fin[l + kTile]] = 1;
+            }
+        }
+        __syncthreads();
+        int32_t nn = 0;
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) nn += s_mark[t + k * kUwThreads];
+        int32_t eslot, nslot;
+        block_reserve(ne, nn, w.counts, s_wsum, &s_base, &eslot, &nslot);
+        // edge records (e, weight bits, local root of p, local root of q); an edge out of the tile
+        // carries q | 2^31 instead, its weight and q's local root are filled in by the first round
+        auto gl = [&](int32_t m) { return (uint32_t)(tg + (int64_t)(m >> 5) * W + (m & 31)); };
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            if (s_mark[l]) w.nodes[nslot++] = (int32_t)gl(l);
+            if (isnan(s_ph[l])) continue;
+            const int32_t c = fin[l];
+            const uint32_t g = gl(l);
+            if (s_own[l] & 1) {
+                w.edges[eslot++] = make_uint4(2u * g, 0u, gl(c), (g + 1u) | 0x80000000u);
+            } else if ((l & 31) + 1 < kTile && !isnan(s_ph[l + 1]) && fin[l + 1] != c) {
+                w.edges[eslot++] = make_uint4(2u * g, __float_as_uint(__fadd_rn(s_rel[l], s_rel[l + 1])), gl(c),
+                                              gl(fin[l + 1]));
+            }
+            if (s_own[l] & 2) {
+                w.edges[eslot++] = make_uint4(2u * g + 1u, 0u, gl(c), (g + (uint32_t)W) | 0x80000000u);
+            } else if ((l >> 5) + 1 < kTile && !isnan(s_ph[l + kTile]) && fin[l + kTile] != c) {
+                w.edges[eslot++] = make_uint4(2u * g + 1u, __float_as_uint(__fadd_rn(s_rel[l], s_rel[l + kTile])),
+                                              gl(c), gl(fin[l + kTile]));
+            }
+        }
+        __syncthreads();
     }
 }
 
-// (parent, shift) of a component in one word: the shift is added to the component's k values
-__device__ __forceinline__ unsigned long long pack_hook(int32_t par, int32_t sh) {
-    return ((unsigned long long)(uint32_t)par << 32) | (unsigned long long)(uint32_t)sh;
+// Root of the component of x and x's shift to it, through the hook chain (hooks of earlier rounds
+// point up the chain; a root's hook is itself). Jumps are written back in place: every word written
+// is a valid (ancestor, summed shift) pair, so threads that chase the same chain help each other.
+// Each jump moves strictly up a chain of fewer than n components, which bounds the loop.
+__device__ __forceinline__ unsigned long long find_root(unsigned long long* hook, int32_t x, int32_t n) {
+    volatile unsigned long long* vh = hook;
+    unsigned long long hw = vh[x];
+    if (hook_par(hw) == x) return hw;
+    for (int32_t it = 0; it < n; ++it) {
+        const int32_t p = hook_par(hw);
+        const unsigned long long wp = vh[p];
+        const int32_t pp = hook_par(wp);
+        if (pp == p) break;  // p is a root
+        hw = pack_hook(pp, hook_sh(hw) + hook_sh(wp));
+        vh[x] = hw;
+    }
+    return hw;
 }
-__device__ __forceinline__ int32_t hook_par(unsigned long long w) { return (int32_t)(uint32_t)(w >> 32); }
-__device__ __forceinline__ int32_t hook_sh(unsigned long long w) { return (int32_t)(uint32_t)(w & 0xffffffffull); }
 
-// every root c hooks onto the component across its best edge: hook[c] = (parent, shift)
-__global__ void __launch_bounds__(kUwThreads) uw_hook(UwArgs a, const float* __restrict__ wph,
-                                                     const int32_t* __restrict__ fid, const int32_t* __restrict__ comp,
-                                                     const int32_t* __restrict__ kk,
-                                                     const unsigned long long* __restrict__ best,
-                                                     unsigned long long* __restrict__ hook,
-                                                     const int32_t* __restrict__ live_in, int32_t* __restrict__ live_out) {
+// Round r, first launch: every listed component takes the hooks of round r - 1 (comp2 = its root,
+// kk2 += its shift to it; a root of round r - 1 that hooked hands its smallest pixel to its new
+// root), and every listed edge between different components is offered to both components'
+// best[r & 1]. Runs while round r - 1 hooked anything (flags[r]).
+__global__ void __launch_bounds__(kUwThreads) uw_gscan(UwWork w, unsigned long long* __restrict__ best,
+                                                      const int32_t* __restrict__ live) {
+    if (!*live) return;
+    const int32_t nn = n_nodes(w), ne = n_edges(w);
+    const int32_t stride = gridDim.x * blockDim.x;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+        const int32_t c = w.nodes[i];
+        const int32_t x = w.comp2[c];
+        const unsigned long long hw = find_root(w.hook, x, nn);
+        const int32_t r = hook_par(hw);
+        if (r != x) {
+            w.comp2[c] = r;
+            w.kk2[c] += hook_sh(hw);
+            if (x == c) atomicMin(w.minpix + r, w.minpix[c]);  // nobody hands pixels to a hooked root
+        }
+    }
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += stride) {
+        uint4 rc = w.edges[i];
+        if (rc.w & 0x80000000u) {  // an edge out of a tile as its tile listed it: completed once
+            const int32_t p = (int32_t)(rc.x >> 1), q = (int32_t)(rc.w & 0x7fffffffu);
+            rc.y = __float_as_uint(__fadd_rn(w.rel[p], w.rel[q]));
+            rc.w = (uint32_t)w.comp[q];
+            w.edges[i] = rc;
+        }
+        const int32_t cp = hook_par(find_root(w.hook, w.comp2[rc.z], nn));
+        const int32_t cq = hook_par(find_root(w.hook, w.comp2[rc.w], nn));
+        if (cp == cq) continue;
+        const unsigned long long key = ((unsigned long long)rc.y << 32) | (unsigned long long)(0xffffffffu - rc.x);
+        offer(best + cp, key);
+        offer(best + cq, key);
+    }
+}
+
+// Round r, second launch: every root hooks onto the component across its best edge (hook[r] =
+// (parent, shift); of two roots that chose the same edge the smaller stays), and clears its slot of
+// best[(r + 1) & 1] for the next round (its roots are among this round's).
+__global__ void __launch_bounds__(kUwThreads) uw_ghook(UwArgs a, UwWork w, const unsigned long long* __restrict__ best,
+                                                      unsigned long long* __restrict__ best_next,
+                                                      const int32_t* __restrict__ live_in, int32_t* __restrict__ live_out) {
     if (!*live_in) return;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.npx; c += (int64_t)gridDim.x * blockDim.x) {
-        if (comp[c] != (int32_t)c) continue;  // not a root
-        const unsigned long long key = best[c];
-        hook[c] = pack_hook((int32_t)c, 0);
-        if (key == 0ull) continue;
-        const uint32_t e = 0xffffffffu - (uint32_t)(key & 0xffffffffull);
-        const int64_t p = (int64_t)(e >> 1);
-        const FrameDev& F = a.fr[fid[p]];
-        const int64_t q = p + ((e & 1u) ? (int64_t)F.W : 1);
-        const int32_t cp = comp[p], cq = comp[q];
-        const int32_t other = cp == (int32_t)c ? cq : cp;
-        if (best[other] == key && (int32_t)c < other) continue;  // both chose this edge: c stays the root
-        const int s = jump(wph[p], wph[q]);                       // k_q - k_p must equal s
-        hook[c] = pack_hook(other, cq == (int32_t)c ? kk[p] + s - kk[q] : kk[q] - s - kk[p]);
+    const int32_t n = n_nodes(w);
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t r = w.nodes[i];
+        if (w.comp2[r] != r) continue;  // not a root
+        const unsigned long long key = best[r];
+        best_next[r] = 0ull;
+        if (!key) continue;
+        const uint32_t e = key_edge(key);
+        const int32_t p = (int32_t)(e >> 1);
+        const int32_t q = p + ((e & 1u) ? a.fr[w.fid[p]].W : 1);
+        const int32_t lp = w.comp[p], lq = w.comp[q];
+        const int32_t cp = w.comp2[lp], cq = w.comp2[lq];
+        const int32_t other = cp == r ? cq : cp;
+        if (best[other] == key && r < other) continue;  // both chose this edge: r stays the root
+        const int s = jump(w.wph[p], w.wph[q]);          // k_q - k_p must equal s
+        const int32_t kp = w.kk[p] + w.kk2[lp], kq = w.kk[q] + w.kk2[lq];
+        w.hook[r] = pack_hook(other, cq == r ? kp + s - kq : kq - s - kp);
         *live_out = 1;
     }
 }
 
-// Resolves every hook chain to its root in place and clears the roots' best edges for the next
-// round. Each root component jumps over its parent until the parent is a root; many components do
-// so at once and help each other (every word read is a consistent (parent, shift) pair, so a
-// component may jump over a parent that has itself jumped already). Every jump moves strictly up
-// a chain of fewer than npx components, which bounds the loop.
-__global__ void __launch_bounds__(kUwThreads) uw_compress(int64_t npx, const int32_t* __restrict__ comp,
-                                                         unsigned long long* hook,
-                                                         unsigned long long* __restrict__ best,
-                                                         int32_t* __restrict__ minpix,
-                                                         const int32_t* __restrict__ hooked) {
-    if (!*hooked) return;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < npx; c += (int64_t)gridDim.x * blockDim.x) {
-        if (comp[c] != (int32_t)c) continue;
-        best[c] = 0ull;
-        unsigned long long w = *(volatile unsigned long long*)(hook + c);
-        for (int64_t it = 0; it < npx; ++it) {
-            const int32_t p = hook_par(w);
-            if (p == (int32_t)c) break;  // c did not hook: a root of this round
-            const unsigned long long wp = *(volatile unsigned long long*)(hook + p);
-            const int32_t pp = hook_par(wp);
-            if (pp == p) break;  // the parent is a root
-            w = pack_hook(pp, hook_sh(w) + hook_sh(wp));
-            *(volatile unsigned long long*)(hook + c) = w;
-        }
-        // the root this component joins inherits its smallest pixel (roots of the round only
-        // receive, so minpix[c] is final here)
-        const int32_t r = hook_par(w);
-        if (r != (int32_t)c) atomicMin(minpix + r, minpix[c]);
-    }
-}
-
-__global__ void __launch_bounds__(kUwThreads) uw_relabel(int64_t npx, int32_t* __restrict__ comp,
-                                                        int32_t* __restrict__ kk,
-                                                        const unsigned long long* __restrict__ hook,
-                                                        const int32_t* __restrict__ live) {
-    if (!*live) return;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < npx; g += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long w = hook[comp[g]];
-        kk[g] += hook_sh(w);
-        comp[g] = hook_par(w);
-    }
-}
-
-__global__ void __launch_bounds__(kUwThreads) uw_write(UwArgs a, const float* __restrict__ wph,
-                                                      const int32_t* __restrict__ fid, const int32_t* __restrict__ comp,
-                                                      const int32_t* __restrict__ kk, const int32_t* __restrict__ minpix) {
+// phi + 2 pi (k - k at the region's first pixel)
+__global__ void __launch_bounds__(kUwThreads) uw_write(UwArgs a, UwWork w) {
+    const int32_t nn = n_nodes(w);
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
-        const FrameDev& F = a.fr[fid[g]];
+        const FrameDev& F = a.fr[w.fid[g]];
         const int64_t local = g - (int64_t)F.gam_off;
-        const float p = wph[g];
+        const float p = w.wph[g];
         float v = p;
         if (!isnan(p)) {
-            const int32_t k = kk[g] - kk[minpix[comp[g]]];
+            const int32_t lr = w.comp[g];
+            const int32_t x = w.comp2[lr];
+            const unsigned long long hw = find_root(w.hook, x, nn);  // x itself once the rounds are done
+            const int32_t m = w.minpix[hook_par(hw)];
+            const int32_t lm = w.comp[m];
+            const unsigned long long hm = find_root(w.hook, w.comp2[lm], nn);
+            const int32_t k = w.kk[g] + w.kk2[lr] + hook_sh(hw) - (w.kk[m] + w.kk2[lm] + hook_sh(hm));
             v = __fadd_rn(p, __fmul_rn(kTwoPiF, (float)k));
         }
         a.out[F.out_off + a.out_maps * (int64_t)F.H * F.W + local] = v;
     }
 }
-
-// Workspace carved from one buffer; every array has npx entries.
-struct UwWork {
-    float* wph;
-    float* rel;
-    int32_t* minpix;  // smallest pixel index of each component (at its root)
-    int32_t* fid;
-    int32_t* comp;
-    int32_t* kk;
-    unsigned long long* hook;
-    unsigned long long* best;
-    int32_t* flags;
-};
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -260,14 +625,21 @@ UwWork carve(void* base, int64_t npx, int rounds) {
         p += align256(bytes);
         return r;
     };
-    w.best = reinterpret_cast<unsigned long long*>(take(8 * (size_t)npx));
-    w.wph = reinterpret_cast<float*>(take(4 * (size_t)npx));
-    w.rel = reinterpret_cast<float*>(take(4 * (size_t)npx));
-    w.fid = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
-    w.comp = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
-    w.kk = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
-    w.minpix = reinterpret_cast<int32_t*>(take(4 * (size_t)npx));
-    w.hook = reinterpret_cast<unsigned long long*>(take(8 * (size_t)npx));
+    const size_t n = (size_t)npx;
+    w.best = reinterpret_cast<unsigned long long*>(take(16 * n));
+    w.hook = reinterpret_cast<unsigned long long*>(take(8 * n));
+    w.edges = reinterpret_cast<uint4*>(take(32 * n));
+    w.wph = reinterpret_cast<float*>(take(4 * n));
+    w.rel = reinterpret_cast<float*>(take(4 * n));
+    w.fid = reinterpret_cast<int32_t*>(take(4 * n));
+    w.comp = reinterpret_cast<int32_t*>(take(4 * n));
+    w.kk = reinterpret_cast<int32_t*>(take(4 * n));
+    w.minpix = reinterpret_cast<int32_t*>(take(4 * n));
+    w.comp2 = reinterpret_cast<int32_t*>(take(4 * n));
+    w.kk2 = reinterpret_cast<int32_t*>(take(4 * n));
+    w.nodes = reinterpret_cast<int32_t*>(take(4 * n));
+    w.tile_start = reinterpret_cast<int32_t*>(take(4 * (n + 2)));  // a call has at most npx frames
+    w.counts = reinterpret_cast<unsigned long long*>(take(8));
     w.flags = reinterpret_cast<int32_t*>(take(4 * (size_t)(rounds + 1)));
     return w;
 }
@@ -284,13 +656,15 @@ int unwrap_rounds(int64_t max_frame_px) { return ceil_log2(max_frame_px < 2 ? 2 
 
 size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_px) {
     const int R = unwrap_rounds(max_frame_px);
-    return 2 * align256(8 * (size_t)npx) + 6 * align256(4 * (size_t)npx) + align256(4 * (size_t)(R + 1));
+    const size_t n = (size_t)npx;
+    return align256(16 * n) + align256(8 * n) + align256(32 * n) + 9 * align256(4 * n) + align256(4 * (n + 2)) + align256(8) +
+           align256(4 * (size_t)(R + 1));
 }
 
 cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_px,
                           const float* in, int64_t in_maps, float* out, int64_t out_maps, void* work,
                           int* launches, cudaStream_t s) {
-    if (npx <= 0) return cudaSuccess;
+    if (npx <= 0 || nframes <= 0) return cudaSuccess;
     const int R = unwrap_rounds(max_frame_px);
     UwWork w = carve(work, npx, R);
     UwArgs a{d_frames, nframes, npx, in, in_maps, out, out_maps};
@@ -299,27 +673,27 @@ cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, in
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = (npx + kUwThreads - 1) / kUwThreads;
     const unsigned grid = (unsigned)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
-    cudaError_t e;
-    // flags[r]: round r is live (round 0 always; round r + 1 if round r joined anything)
-    e = cudaMemsetAsync(w.flags, 0, 4 * (size_t)(R + 1), s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(w.flags, 0xff, 4, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(w.best, 0, 8 * (size_t)npx, s);
-    if (e != cudaSuccess) return e;
-    uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, w.minpix);
+    // persistent over the tiles (their count is known on the device only): no more CTAs than the
+    // tiles of a call can need, about npx / 32 + nframes at most
+    const int64_t tiles_max = npx / kTile + nframes;
+    const unsigned tgrid = (unsigned)(tiles_max < (int64_t)sms * 4 ? tiles_max : (int64_t)sms * 4);
+    // the global rounds: at most two listed edges per pixel
+    const int64_t ewant = (2 * npx + kUwThreads - 1) / kUwThreads;
+    const unsigned egrid = (unsigned)(ewant < (int64_t)sms * 8 ? ewant : (int64_t)sms * 8);
+    uw_prepare<<<1, kUwThreads, 0, s>>>(a, w, R);
+    uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid);
     uw_reliability<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel);
-    *launches += 2;
+    uw_tiles<<<tgrid, kUwThreads, 0, s>>>(a, w);
+    *launches += 4;
     for (int r = 0; r < R; ++r) {
         const int32_t* live = w.flags + r;
-        int32_t* hooked = w.flags + r + 1;
-        uw_best_edges<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel, w.comp, w.best, live);
-        uw_hook<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, w.best, w.hook, live, hooked);
-        uw_compress<<<grid, kUwThreads, 0, s>>>(npx, w.comp, w.hook, w.best, w.minpix, hooked);
-        uw_relabel<<<grid, kUwThreads, 0, s>>>(npx, w.comp, w.kk, w.hook, hooked);
-        *launches += 4;
+        unsigned long long* bcur = w.best + (size_t)(r & 1) * (size_t)npx;
+        unsigned long long* bnext = w.best + (size_t)((r + 1) & 1) * (size_t)npx;
+        uw_gscan<<<egrid, kUwThreads, 0, s>>>(w, bcur, live);
+        uw_ghook<<<grid, kUwThreads, 0, s>>>(a, w, bcur, bnext, live, w.flags + r + 1);
+        *launches += 2;
     }
-    uw_write<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.comp, w.kk, w.minpix);
+    uw_write<<<grid, kUwThreads, 0, s>>>(a, w);
     ++*launches;
     return cudaGetLastError();
 }
