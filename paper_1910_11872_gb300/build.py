@@ -18,7 +18,8 @@ CHECKED_BUILD = os.path.join(HERE, "_build_checked")
 CHECKED_LIB = os.path.join(HERE, "_lib_checked", "librmusic.so")
 SOURCES = ["analytic.cu", "plain.cu", "batched.cu", "batched_l2_l4.cu", "batched_l6.cu", "batched_l8.cu",
            "batched_l10.cu", "batched_l12.cu", "batched_fwd.cu", "batched_fwd_l2_l5.cu", "batched_fwd_l6_l7.cu",
-           "batched_fwd_l8.cu", "batched_fwd_l9_l10.cu", "batched_fwd_l11_l12.cu", "square.cu", "square_l1_l2.cu", "square_l3_l4.cu", "square_l5.cu",
+           "batched_fwd_l8.cu", "batched_fwd_l9_l10.cu", "batched_fwd_l11_l12.cu", "batched_p.cu",
+           "batched_p_l3_l6.cu", "batched_p_l7_l9.cu", "batched_p_l10_l12.cu", "square.cu", "square_l1_l2.cu", "square_l3_l4.cu", "square_l5.cu",
            "square_l6.cu", "square_l7.cu", "square_l8.cu", "unwrap.cu", "crossband.cu", "capi.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

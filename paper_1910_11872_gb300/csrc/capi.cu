@@ -61,7 +61,9 @@ int params_check(const rmusic_params& p) {
     if (p.model_order < 1) return RMUSIC_EINVAL;
     if (p.model_order > kMaxModelOrder) return RMUSIC_EUNSUPPORTED;
     if (!params_ok(p)) return RMUSIC_EINVAL;
-    if (p.model_order > 1 && p.precision == RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
+    // the batched model-order solver works on raw real lines along the carrier (row windows)
+    if (p.model_order > 1 && p.precision == RMUSIC_FP32_BATCHED && (p.geometry != RMUSIC_GEOM_ROW || !p.raw_input))
+        return RMUSIC_EUNSUPPORTED;
     if (p.geometry == RMUSIC_GEOM_SQUARE && p.precision != RMUSIC_FP32_BATCHED) return RMUSIC_EUNSUPPORTED;
     return RMUSIC_OK;
 }
@@ -85,7 +87,10 @@ int describe_frame(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev*
         N = d.window_len ? d.window_len : p.window_len;
         L = d.cov_order ? d.cov_order : p.cov_order;
         if (N < 2 || N > kMaxN || L < 2 || L > kMaxL || L > N) return RMUSIC_EINVAL;
-        if (p.precision == RMUSIC_FP32_BATCHED &&
+        if (p.precision == RMUSIC_FP32_BATCHED && p.model_order > 1 &&
+            (d.dtype == RMUSIC_DTYPE_C64 || !batched_p_supports(p.model_order, L)))
+            return RMUSIC_EUNSUPPORTED;  // real frames only: the solver takes R as real symmetric
+        if (p.precision == RMUSIC_FP32_BATCHED && p.model_order == 1 &&
             !(p.forward_backward ? batched_supports(L) : batched_fwd_supports(L)))
             return RMUSIC_EUNSUPPORTED;
     }
@@ -168,34 +173,50 @@ constexpr int kStatSlot = 32;
 
 // A solver key names one compiled solver family: the covariance order L of the row-window
 // solver (2 .. kMaxL), kSquareKey0 + Lp for the square-block solver, kFwdKey0 + L for the row-window
-// solver of the forward estimate (no forward-backward average).
+// solver of the forward estimate (no forward-backward average), kModelKey0 + 16 (p - 2) + L for the
+// row-window solver of model order p = 2 or 3.
 constexpr int kSquareKey0 = 16;
 constexpr int kFwdKey0 = 32;
-constexpr int kKeys = kFwdKey0 + kMaxL + 1;
-static_assert(kMaxL < kSquareKey0 && kSquareKey0 + kMaxSquareLp < kFwdKey0, "solver keys overlap");
+constexpr int kModelKey0 = 48;
+constexpr int kKeys = kModelKey0 + 32;
+static_assert(kMaxL < kSquareKey0 && kSquareKey0 + kMaxSquareLp < kFwdKey0 && kFwdKey0 + kMaxL < kModelKey0 &&
+                  kMaxL < 16,
+              "solver keys overlap");
 
 bool key_square(int key) { return key >= kSquareKey0 && key < kFwdKey0; }
-bool key_fwd(int key) { return key >= kFwdKey0; }
+bool key_fwd(int key) { return key >= kFwdKey0 && key < kModelKey0; }
+bool key_model(int key) { return key >= kModelKey0; }
+int key_model_p(int key) { return 2 + (key - kModelKey0) / 16; }
+int key_model_L(int key) { return (key - kModelKey0) % 16; }
 bool solver_supports(int key) {
-    return key_fwd(key) ? batched_fwd_supports(key - kFwdKey0)
+    return key_model(key) ? batched_p_supports(key_model_p(key), key_model_L(key))
+         : key_fwd(key) ? batched_fwd_supports(key - kFwdKey0)
          : key_square(key) ? square_supports(key - kSquareKey0) : batched_supports(key);
 }
 int solver_num_variants(int key) {
-    return key_fwd(key) ? batched_fwd_num_variants(key - kFwdKey0)
+    return key_model(key) ? 1
+         : key_fwd(key) ? batched_fwd_num_variants(key - kFwdKey0)
          : key_square(key) ? square_num_variants(key - kSquareKey0) : batched_num_variants(key);
 }
 int solver_default_variant(int key) {
-    return key_fwd(key) ? batched_fwd_default_variant(key - kFwdKey0)
+    return key_model(key) ? 0
+         : key_fwd(key) ? batched_fwd_default_variant(key - kFwdKey0)
          : key_square(key) ? square_default_variant(key - kSquareKey0) : batched_default_variant(key);
 }
 int solver_ctas(int key, int v) {
-    return key_fwd(key) ? batched_fwd_variant_ctas(key - kFwdKey0, v)
+    return key_model(key) ? batched_p_ctas(key_model_L(key))
+         : key_fwd(key) ? batched_fwd_variant_ctas(key - kFwdKey0, v)
          : key_square(key) ? square_variant_ctas(key - kSquareKey0, v) : batched_variant_ctas(key, v);
+}
+// The solver key of a row-window frame of covariance order L under the parameters p.
+int row_key(const rmusic_params& p, int L) {
+    if (p.model_order > 1) return kModelKey0 + 16 * (p.model_order - 2) + L;
+    return p.forward_backward ? L : kFwdKey0 + L;
 }
 // The solver key of a frame of the plan (its table entry's geometry and covariance order).
 int frame_key(const rmusic_params& p, const FrameDev& F) {
     if (F.geom == kGeomSquare) return kSquareKey0 + F.L;
-    return p.forward_backward ? F.L : kFwdKey0 + F.L;
+    return row_key(p, F.L);
 }
 
 struct GraphEntry {
@@ -485,8 +506,10 @@ void store_tune(int device, int key, int v, float ms) {
     fprintf(f,
             "{\"device\": \"%s\", \"key\": %d, \"%s\": %d, \"variant\": %d, \"ctas_per_sm\": %d, "
             "\"ms\": %.4f}\n",
-            device_key(device).c_str(), key, key_square(key) ? "Lp" : key_fwd(key) ? "L_fwd" : "L",
-            key_square(key) ? key - kSquareKey0 : key_fwd(key) ? key - kFwdKey0 : key, v, solver_ctas(key, v), ms);
+            device_key(device).c_str(), key,
+            key_square(key) ? "Lp" : key_fwd(key) ? "L_fwd" : key_model(key) ? (key_model_p(key) == 2 ? "L_p2" : "L_p3") : "L",
+            key_square(key) ? key - kSquareKey0 : key_fwd(key) ? key - kFwdKey0 : key_model(key) ? key_model_L(key) : key,
+            v, solver_ctas(key, v), ms);
     fclose(f);
 }
 
@@ -514,7 +537,8 @@ bool solver_tuned(rmusic_ctx* ctx, int L) {
 int solver_grid(rmusic_ctx* ctx, int L, int v) {
     if (ctx->grid_by_Lv[L][v] == 0)
         ctx->grid_by_Lv[L][v] =
-            key_fwd(L) ? batched_fwd_grid(L - kFwdKey0, v, ctx->device)
+            key_model(L) ? batched_p_grid(key_model_p(L), key_model_L(L), ctx->device)
+            : key_fwd(L) ? batched_fwd_grid(L - kFwdKey0, v, ctx->device)
             : key_square(L) ? square_grid(L - kSquareKey0, v, ctx->device) : batched_grid(L, v, ctx->device);
     return ctx->grid_by_Lv[L][v];
 }
@@ -540,10 +564,17 @@ cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, fl
     }
     BatchedArgs a;
     a.max_sweeps = p.max_sweeps ? p.max_sweeps : 6;
-    a.max_iters = p.max_root_iters ? p.max_root_iters : 16;
+    // the model-order solver takes every root by Aberth's method (noise-free windows put p double
+    // roots on the circle, where it converges linearly): more sweeps by default
+    a.max_iters = p.max_root_iters ? p.max_root_iters : key_model(key) ? 32 : 16;
     a.polish64 = p.polish_fp64;
     a.exhaustive = p.exhaustive;
     a.counters = stat_counters;
+    a.fb = p.forward_backward;
+    if (key_model(key))
+        return launch_batched_p(key_model_p(key), key_model_L(key), ctx->d_table + plan.group_first[g],
+                                plan.group_count[g], plan.group_items[g], ctx->d_counters + g, gamma, d_out, d_status,
+                                a, solver_grid(ctx, key, v), s);
     if (key_fwd(key))
         return launch_batched_fwd(key - kFwdKey0, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
                                   plan.group_items[g], ctx->d_counters + g, gamma, d_out, d_status, a,
@@ -1053,8 +1084,7 @@ int rmusic_demodulate_frames_host_async(rmusic_ctx* ctx, const void* h_frames, s
 
 int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant) {
     if (!ctx || ctx->p.precision != RMUSIC_FP32_BATCHED) return ctx ? RMUSIC_EUNSUPPORTED : RMUSIC_EINVAL;
-    const int key = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? kSquareKey0 + order
-                  : ctx->p.forward_backward ? order : kFwdKey0 + order;
+    const int key = ctx->p.geometry == RMUSIC_GEOM_SQUARE ? kSquareKey0 + order : row_key(ctx->p, order);
     if (order < 1 || order > kMaxL || key < 0 || key >= kKeys || !solver_supports(key)) return RMUSIC_EINVAL;
     if (variant < -1 || variant >= solver_num_variants(key)) return RMUSIC_EINVAL;
     ctx->variant_by_L[key] = variant;

@@ -160,6 +160,7 @@ extern "C" int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int
         a.polish64 = p.polish_fp64;
         a.exhaustive = p.exhaustive;
         a.counters = nullptr;
+        a.fb = 1;
         for (int g = 0; g < ngroups && rc == RMUSIC_OK; ++g) {
             const int L = group_L[g];
             const int v = batched_default_variant(L);

@@ -71,6 +71,7 @@ struct BatchedArgs {
                                    // updates, [4] Aberth evaluations of Q and Q', [5] power steps,
                                    // [6] Jacobi fallbacks, [7] Newton steps, [8] Aberth fallbacks,
                                    // [9] polish steps
+    int fb;                        // model-order solver: 1 = the forward-backward average of R
 };
 bool batched_supports(int L);
 int batched_num_variants(int L);
@@ -92,6 +93,16 @@ cudaError_t launch_batched_fwd(int L, int v, const FrameDev* d_frames, int nfram
                                unsigned long long* d_counter, const float2* d_gamma, float* d_out,
                                uint8_t* d_status, BatchedArgs a, int grid, cudaStream_t stream);
 int batched_fwd_grid(int L, int v, int device);
+
+// Batched FP32 path for model order p = 2 or 3 on raw real lines (batched_p_kernel.cuh): the same
+// work items and arguments (a.fb selects the forward-backward average), L = p + 1 .. kMaxL, one
+// register cap per L.
+bool batched_p_supports(int p, int L);
+int batched_p_ctas(int L);
+cudaError_t launch_batched_p(int p, int L, const FrameDev* d_frames, int nframes, int64_t total_items,
+                             unsigned long long* d_counter, const float2* d_gamma, float* d_out, uint8_t* d_status,
+                             BatchedArgs a, int grid, cudaStream_t stream);
+int batched_p_grid(int p, int L, int device);
 
 // Square-block FP32 path (the paper's geometry): persistent, one 32 x 4 pixel tile per CTA work
 // item, over all frames that share the half-width Lp. `counter` must be zero when it starts.

@@ -135,10 +135,11 @@ __device__ __forceinline__ float music_coefs(const cx<float>* u, cx<float>* c) {
 // mz[] their mirrors 1/conj(z); iters counts sweeps, evals the evaluations of Q and Q' that ran
 // (a root frozen in every lane of the warp is skipped), updates the root updates that ran; rconv
 // is false if max_iters sweeps ended before every root of this lane converged.
+// inner_roots with the signal root's starting direction e (unit modulus) given by the caller.
 template <int L>
-__device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, int max_iters,
-                                            cx<float> (&z)[L - 1], cx<float> (&mz)[L - 1], int& iters,
-                                            int& evals, int& updates, bool& rconv) {
+__device__ __forceinline__ void inner_roots_from(const cx<float>* c, float res_lim2, int max_iters, cx<float> e,
+                                                 cx<float> (&z)[L - 1], cx<float> (&mz)[L - 1], int& iters,
+                                                 int& evals, int& updates, bool& rconv) {
     constexpr int NI = L - 1;
     // Q's coefficients satisfy c_-k = conj(c_k), so its roots come in pairs z, 1/conj(z). Only
     // the L - 1 roots inside the unit disk are iterated; each Aberth sum runs over the other
@@ -147,9 +148,6 @@ __device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, 
     // the current root is always position 0 and the arrays rotate by one after each update,
     // which keeps the code small enough for the instruction cache.
     {
-        const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
-        const float n1 = norm2(rho1);
-        const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
         z[0] = 0.99f * e;
         float sh, ch;
         sincospif(1.0f / (float)L, &sh, &ch);                           // exp(j pi / L)
@@ -232,6 +230,16 @@ __device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, 
         if (iters >= max_iters) break;
         if (__all_sync(kFull, rconv)) break;
     }
+}
+
+template <int L>
+__device__ __forceinline__ void inner_roots(const cx<float>* c, float res_lim2, int max_iters,
+                                            cx<float> (&z)[L - 1], cx<float> (&mz)[L - 1], int& iters,
+                                            int& evals, int& updates, bool& rconv) {
+    const cx<float> rho1 = (-1.f) * c[1];  // proportional to rho_1
+    const float n1 = norm2(rho1);
+    const cx<float> e = n1 > 0.f ? rsqrtf(n1) * conjg(rho1) : mkc(1.f, 0.f);
+    inner_roots_from<L>(c, res_lim2, max_iters, e, z, mz, iters, evals, updates, rconv);
 }
 
 // The candidate of Algorithm 1 among the roots of inner_roots: the inner root nearest the unit

@@ -84,7 +84,7 @@ def test_argument_checks_without_cuda(lib):
     bad = rmusic.make_params(model_order=4)
     ctx = ctypes.c_void_p()
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EUNSUPPORTED
-    bad = rmusic.make_params(model_order=2)  # the batched solvers keep model order 1
+    bad = rmusic.make_params(model_order=2)  # the batched model-order solver takes raw real lines only
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EUNSUPPORTED
     bad = rmusic.make_params(model_order=2, precision="plain_fp32", raw_input=1, deriv_axis=1)
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
