@@ -863,6 +863,74 @@ def run_workloads(args, dev, stream, flush, cpu: bool):
     del umaps, ust
     torch.cuda.empty_cache()
 
+    # ---- model order p = 2 and 3 on raw real lines (Sec. 3 with p exponentials) -------------------
+    res_p = {}
+    for p, offset in ((2, 0.0), (3, 0.15)):
+        frames_p = [synth.raw_fringe_frame(snr, offset, stream=k) for k, snr in enumerate(SNRS)]
+        xp = torch.from_numpy(np.stack([f.image for f in frames_p])).to(dev)
+        outp = torch.empty(xp.numel(), dtype=torch.float32, device=dev)
+        kw = dict(device=dev.index, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0, model_order=p, raw_input=1)
+        demp = rmusic.Demodulator(precision="batched", use_graph=1, timing=1, **kw)
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        for _ in range(3):
+            demp.run(xp, out=outp, with_status=False)
+        ms = []
+        for _ in range(10):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            demp.run(xp, out=outp, with_status=False, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        st = demp.stats()
+        clk = clocks.stop()
+        gp, gps, _ = demp.run(xp)
+        torch.cuda.synchronize()
+        demp.close()
+        plainp = rmusic.Demodulator(precision="plain_fp32", **kw)
+        plainp.run(xp[:1])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plainp.run(xp[:1], stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = a.elapsed_time(b)
+        plainp.close()
+        npx_p = xp.numel()
+        r = {"workload": f"{len(SNRS)} x {H}x{W} float32 raw real fringes (peaks phase 0-10 rad, SNR 40/20/10/5 dB"
+                         f"{', local offset 0.15 sin(x/60)' if offset else ''}), carrier {F0}, N={N_WIN}, L={L_COV}, "
+                         f"model order {p}, forward-backward",
+             "value": npx_p / statistics.median(ms) / 1e3, "unit": "Mpixel/s", "ms_per_call": statistics.median(ms),
+             "solver_ms": st.solver_ms, "mean_subspace_steps": st.mean_power_steps,
+             "jacobi_fallback_frac": st.eig_fallback_frac, "mean_aberth_iters": st.mean_root_iters,
+             "plain_fp32": {"value": H * W / plain_ms / 1e3, "unit": "Mpixel/s", "ms_one_frame": plain_ms},
+             "speedup_vs_plain": (npx_p / statistics.median(ms)) / (H * W / plain_ms),
+             "timing": "graph replay, L2 flushed, 3 warm-ups, median of 10 event-timed calls", "clocks": clk}
+        if cpu:
+            rng = np.random.default_rng(11877 + p)
+            gm, sm = gp.view(len(frames_p), H, W).cpu().numpy(), gps.view(len(frames_p), H, W).cpu().numpy()
+            comp, npx, dt, cores = [], 0, 0.0, 0
+            prm = O.make_params(N_WIN, L_COV, 1, 0, 0, F0, model_order=p, raw_input=1)
+            for fr, g_, s_ in zip(frames_p, gm, sm):
+                rows = np.sort(rng.choice(H, 8, replace=False))
+                ys = np.repeat(rows, W).astype(np.int32)
+                xs = np.tile(np.arange(W), rows.size).astype(np.int32)
+                t0 = time.perf_counter()
+                vals, ost, cores = O.demodulate_pixels(fr.image, prm, ys, xs)
+                dt += time.perf_counter() - t0
+                npx += ys.size
+                comp.append((g_[ys, xs], s_[ys, xs], vals, ost, fr.truth[ys, xs]))
+            cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
+            r["vs_fp64_oracle"] = _oracle_compare(*cat)
+            r["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                                 "sample": f"8 random full rows of each frame ({npx} px), {dt:.1f} s wall"}
+        res_p[f"p{p}"] = r
+        del xp, outp, gp, gps
+    out["model_order"] = res_p
+
     # ---- serving: 16 camera streams, Poisson arrivals at 2000 frames/s ---------------------------
     sargs = argparse.Namespace(streams=16, rate=2000.0, seconds=args.serve_seconds, pool=2, ring_depth=4,
                                max_batch_frames=32, max_batch_mpx=32, inflight=3, budget_gb=64.0, device=dev.index)

@@ -169,6 +169,19 @@ def peaks_frame(snr_db: float, f0: float = 0.1, H: int = 1024, W: int = 1024,
     return Frame(img, f0, truth=dx, meta={"workload": f"peaks {H}x{W} f0={f0} snr={snr_db}dB"})
 
 
+def raw_fringe_frame(snr_db: float, offset_amp: float = 0.0, f0: float = 0.1, H: int = 1024, W: int = 1024,
+                     seed_index: int = 6, stream: int = 0) -> Frame:
+    """Real fringe for model order p > 1 on raw lines: 0.5 + offset_amp sin(x / 60) + 0.4 cos(2 pi f0 x
+    + phi), phi = peaks scaled to 0-10 rad (the local offset varies along the line: the third
+    exponential, at zero frequency, of p = 3), noise at snr_db. float32; truth is dphi/dx."""
+    rng = np.random.Generator(np.random.PCG64([SEED_BASE + seed_index, stream]))
+    phi, dx, _ = peaks(H, W)
+    x = np.arange(W, dtype=np.float64)[None, :]
+    img = add_noise(fringe(phi, f0) + offset_amp * np.sin(x / 60.0), sigma_for_snr(0.4, snr_db), rng)
+    return Frame(img.astype(np.float32), f0, truth=dx,
+                 meta={"workload": f"raw fringe {H}x{W} f0={f0} offset={offset_amp} snr={snr_db}dB"})
+
+
 def diffusion_frame(t: int, T: int = 500, H: int = 1024, W: int = 1024, seed_index: int = 2,
                     amp: float = 8.0, dt0: float = 400.0, dt1: float = 40000.0,
                     sigma: float = 0.01) -> Frame:
