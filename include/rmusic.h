@@ -79,12 +79,15 @@ extern "C" {
  *                    takes even L with forward_backward = 1 (a real symmetric transform of R) and
  *                    any L with forward_backward = 0 (the complex Hermitian R); odd L with the
  *                    forward-backward average needs a plain path.
- *   model_order      number of complex exponentials per window; the method uses 1 (Eq. 2). The
- *                    plain paths also take 2 or 3 (a real fringe without the analytic step holds
- *                    exp(+-j omega), and a local offset one more at zero frequency): the noise
+ *   model_order      number of complex exponentials per window; the method uses 1 (Eq. 2). All
+ *                    row-window paths also take 2 or 3 (a real fringe without the analytic step
+ *                    holds exp(+-j omega), and a local offset one more at zero frequency): the noise
  *                    projector then removes the p largest eigenvalues' eigenvectors, and the
  *                    derivative comes from the one of the p roots nearest the unit circle whose
  *                    angle is nearest the expected one (2 pi f0). Needs cov_order > model_order.
+ *                    RMUSIC_FP32_BATCHED takes it with raw_input = 1 on float32 or uint16 frames
+ *                    (RMUSIC_EUNSUPPORTED otherwise); its FP32 roots lose accuracy (a few 1e-4 rad)
+ *                    when cov_order <= model_order + 2, where the roots crowd in pairs.
  *   forward_backward 1: R = (R_f + J conj(R_f) J) / 2 (forward-backward average); 0: R = R_f,
  *                    the forward estimate of Eq. 4-5 alone (its signal root lies further inside
  *                    the circle on noisy windows; both give the same derivative on noise-free
