@@ -675,9 +675,9 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
         if (p.unwrap) {
             // phase assembly: the alpha maps (third map) unwrapped into the fourth map
             NvtxRange r("rmusic.unwrap");
-            int64_t maxpx = 0;
-            for (const FrameDev& F : plan.frames) maxpx = std::max<int64_t>(maxpx, (int64_t)F.H * F.W);
-            RM_CUDA(launch_unwrap(ctx->d_table, n, (int64_t)plan.gamma_elems, maxpx, d_out, 2, d_out, 3,
+            int64_t maxnodes = 0;
+            for (const FrameDev& F : plan.frames) maxnodes = std::max<int64_t>(maxnodes, unwrap_frame_nodes(F.H, F.W));
+            RM_CUDA(launch_unwrap(ctx->d_table, n, (int64_t)plan.gamma_elems, maxnodes, d_out, 2, d_out, 3,
                                   ctx->d_unwrap, launches, s));
         }
     } else {
@@ -739,7 +739,7 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
     if (rc) return rc;
     if (ctx->p.unwrap) {
         int64_t maxpx = 0;
-        for (const FrameDev& F : plan.frames) maxpx = std::max<int64_t>(maxpx, (int64_t)F.H * F.W);
+        for (const FrameDev& F : plan.frames) maxpx = std::max<int64_t>(maxpx, unwrap_frame_nodes(F.H, F.W));
         if (plan.gamma_elems >= (1ull << 31)) return RMUSIC_EINVAL;
         rc = ensure(ctx, &ctx->d_unwrap, &ctx->unwrap_cap, unwrap_workspace_bytes((int64_t)plan.gamma_elems, maxpx));
         if (rc) return rc;
@@ -1112,7 +1112,7 @@ int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_fram
         F.out_off = d.out_offset;
         F.gam_off = npx;  // first pixel of the frame in the call's pixel numbering
         npx += (uint64_t)d.height * (uint64_t)d.width;
-        maxpx = std::max<int64_t>(maxpx, (int64_t)d.height * d.width);
+        maxpx = std::max<int64_t>(maxpx, unwrap_frame_nodes(d.height, d.width));
     }
     if (npx >= (1ull << 31)) return RMUSIC_EINVAL;
     int rc = ensure_tables(ctx, frames.size());

@@ -131,10 +131,12 @@ int square_grid(int Lp, int v, int device);
 
 // Phase assembly (unwrap.cu): unwraps the wrapped map of every frame of the table (frame f's
 // pixels are g = F.gam_off .. F.gam_off + H W - 1; its input map at in + F.out_off + in_maps H W,
-// its output at out + F.out_off + out_maps H W; NaN = no value). work must hold
-// unwrap_workspace_bytes(npx, max_frame_px) bytes; npx < 2^31.
-size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_px);
-cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_px,
+// its output at out + F.out_off + out_maps H W; NaN = no value). max_frame_nodes is the largest
+// unwrap_frame_nodes(H, W) over the frames (it bounds the rounds); any larger value is safe. work
+// must hold unwrap_workspace_bytes(npx, max_frame_nodes) bytes; npx < 2^31.
+int64_t unwrap_frame_nodes(int H, int W);
+size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_nodes);
+cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_nodes,
                           const float* in, int64_t in_maps, float* out, int64_t out_maps, void* work,
                           int* launches, cudaStream_t s);
 

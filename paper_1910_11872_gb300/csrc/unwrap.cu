@@ -29,8 +29,12 @@
 //                win); the second lets every root hook onto the component across its best edge
 //                (of two roots that chose the same edge the smaller label stays the root) with the
 //                integer shift that makes the edge's endpoints differ by their wrapped difference.
-//                A round after one that joined nothing returns at once. Each round at least halves
-//                the components that still have edges.
+//                The edge list is compacted as it is scanned (an edge inside a component stays
+//                inside). A round after one that joined nothing returns at once. Each round at
+//                least halves the components that still have edges, and they are at most the
+//                tiles' border pixels: ceil(log2) of that many rounds, plus one to relabel.
+//   anchor ka    after the rounds, per local root: its shift to its final root minus the shift of
+//                that root's anchor pixel; a pixel's output needs only its own k and its root's ka.
 //   anchor       each connected region keeps its first pixel (row-major) at its wrapped value;
 //                every component carries its smallest pixel index through the merges.
 // A pixel's k is its shift within its local component plus that component's shift within its
@@ -92,8 +96,9 @@ struct UwArgs {
 
 // Workspace carved from one buffer. Per pixel g: wph (wrapped phase), rel, fid (frame), comp (root
 // of g's local component), kk (g's shift within it); per local root r: minpix, comp2 (r's root as
-// of the last relabelling), kk2 (r's shift to it), hook, best (two copies: even and odd rounds). The edge list holds at most the
-// grid's two edges per pixel, the node list at most one local root per pixel.
+// of the last relabelling), kk2 (r's shift to it), ka, hook, best (two copies: even and odd
+// rounds). Each edge list holds at most the grid's two edges per pixel, the node list at most one
+// local root per pixel.
 struct UwWork {
     float* wph;
     float* rel;
@@ -103,9 +108,12 @@ struct UwWork {
     int32_t* minpix;
     int32_t* comp2;
     int32_t* kk2;
+    int32_t* ka;        // per local root: its shift to its final root minus the anchor pixel's k
     unsigned long long* hook;
     unsigned long long* best;   // two arrays of npx: best of even rounds, then of odd rounds
     uint4* edges;       // (e, weight bits, local root of p, local root of q) per listed edge
+    uint4* edges2;      // the edges still between different components, round by round (ping-pong)
+    int32_t* ecount;    // rounds + 1: edges entering each round after the first
     int32_t* nodes;     // local roots with at least one edge in the list
     int32_t* tile_start;  // nframes + 1 entries: first tile of each frame, then the total
     unsigned long long* counts;  // listed edges (low word) and nodes (high word)
@@ -127,7 +135,10 @@ __global__ void __launch_bounds__(kUwThreads) uw_prepare(UwArgs a, UwWork w, int
     __shared__ int32_t carry;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     if (t == 0) carry = 0;
-    for (int i = t; i < rounds + 1; i += blockDim.x) w.flags[i] = i == 0 ? 1 : 0;
+    for (int i = t; i < rounds + 1; i += blockDim.x) {
+        w.flags[i] = i == 0 ? 1 : 0;
+        w.ecount[i] = 0;
+    }
     if (t == 0) *w.counts = 0ull;
     __syncthreads();
     for (int base = 0; base < a.nframes; base += kUwThreads) {
@@ -151,39 +162,35 @@ __global__ void __launch_bounds__(kUwThreads) uw_prepare(UwArgs a, UwWork w, int
     if (t == 0) w.tile_start[a.nframes] = carry;
 }
 
-// wph[g] = wrapped phase, fid[g] = frame
-__global__ void __launch_bounds__(kUwThreads) uw_init(UwArgs a, float* __restrict__ wph, int32_t* __restrict__ fid) {
+// wph[g] = wrapped phase, fid[g] = frame, rel[g] = reliability R = 1 / D from the wrapped second
+// differences of the 3 x 3 neighbourhood (0 where a neighbour is missing or NaN; NaN at NaN pixels),
+// read from the input map directly (a frame's map is contiguous, row-major).
+__global__ void __launch_bounds__(kUwThreads) uw_init(UwArgs a, float* __restrict__ wph, int32_t* __restrict__ fid,
+                                                     float* __restrict__ rel) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
         const int f = find_frame(a.fr, a.nframes, g, [](const FrameDev& F) { return (int64_t)F.gam_off; });
         const FrameDev& F = a.fr[f];
         const int64_t local = g - (int64_t)F.gam_off;
-        wph[g] = a.in[F.out_off + a.in_maps * (int64_t)F.H * F.W + local];
+        const float* m = a.in + F.out_off + a.in_maps * (int64_t)F.H * F.W;
+        const float c = m[local];
+        wph[g] = c;
         fid[g] = f;
-    }
-}
-
-__global__ void __launch_bounds__(kUwThreads) uw_reliability(UwArgs a, const float* __restrict__ wph,
-                                                            const int32_t* __restrict__ fid, float* __restrict__ rel) {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
-        const FrameDev& F = a.fr[fid[g]];
-        const int64_t local = g - (int64_t)F.gam_off;
-        const int i = (int)(local / F.W), j = (int)(local % F.W), W = F.W;
-        const float c = wph[g];
         if (isnan(c)) {
             rel[g] = c;
             continue;
         }
+        const int i = (int)(local / F.W), j = (int)(local % F.W), W = F.W;
         bool inner = i >= 1 && i + 1 < F.H && j >= 1 && j + 1 < W;
         if (inner) {
             for (int di = -1; di <= 1; ++di)
                 for (int dj = -1; dj <= 1; ++dj)
-                    if (isnan(wph[g + (int64_t)di * W + dj])) inner = false;
+                    if (isnan(m[local + (int64_t)di * W + dj])) inner = false;
         }
         if (!inner) {
             rel[g] = 0.f;
             continue;
         }
-        auto ph = [&](int di, int dj) { return wph[g + (int64_t)di * W + dj]; };
+        auto ph = [&](int di, int dj) { return m[local + (int64_t)di * W + dj]; };
         const float h = __fsub_rn(gam_f(__fsub_rn(ph(0, -1), c)), gam_f(__fsub_rn(c, ph(0, 1))));
         const float v = __fsub_rn(gam_f(__fsub_rn(ph(-1, 0), c)), gam_f(__fsub_rn(c, ph(1, 0))));
         const float d1 = __fsub_rn(gam_f(__fsub_rn(ph(-1, -1), c)), gam_f(__fsub_rn(c, ph(1, 1))));
@@ -444,6 +451,7 @@ __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
                 w.minpix[g] = (int32_t)(tg + (int64_t)(m >> 5) * W + (m & 31));
                 w.comp2[g] = (int32_t)g;
                 w.kk2[g] = 0;
+                w.ka[g] = -s_kk[m];  // a local root outside the global phase is its own final root
                 w.best[g] = 0ull;  // best of round 0
                 w.hook[g] = pack_hook((int32_t)g, 0);
             }
@@ -530,38 +538,69 @@ __device__ __forceinline__ unsigned long long find_root(unsigned long long* hook
 
 // Round r, first launch: every listed component takes the hooks of round r - 1 (comp2 = its root,
 // kk2 += its shift to it; a root of round r - 1 that hooked hands its smallest pixel to its new
-// root), and every listed edge between different components is offered to both components'
-// best[r & 1]. Runs while round r - 1 hooked anything (flags[r]).
+// root), and every edge still between different components is offered to both components'
+// best[r & 1] and kept for round r + 1 (the list shrinks as components merge: an edge inside a
+// component stays inside). Runs while round r - 1 hooked anything (flags[r]).
 __global__ void __launch_bounds__(kUwThreads) uw_gscan(UwWork w, unsigned long long* __restrict__ best,
-                                                      const int32_t* __restrict__ live) {
+                                                      const int32_t* __restrict__ live, int r) {
     if (!*live) return;
-    const int32_t nn = n_nodes(w), ne = n_edges(w);
+    const int32_t nn = n_nodes(w);
     const int32_t stride = gridDim.x * blockDim.x;
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
         const int32_t c = w.nodes[i];
         const int32_t x = w.comp2[c];
         const unsigned long long hw = find_root(w.hook, x, nn);
-        const int32_t r = hook_par(hw);
-        if (r != x) {
-            w.comp2[c] = r;
+        const int32_t root = hook_par(hw);
+        if (root != x) {
+            w.comp2[c] = root;
             w.kk2[c] += hook_sh(hw);
-            if (x == c) atomicMin(w.minpix + r, w.minpix[c]);  // nobody hands pixels to a hooked root
+            if (x == c) atomicMin(w.minpix + root, w.minpix[c]);  // nobody hands pixels to a hooked root
         }
     }
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += stride) {
-        uint4 rc = w.edges[i];
-        if (rc.w & 0x80000000u) {  // an edge out of a tile as its tile listed it: completed once
-            const int32_t p = (int32_t)(rc.x >> 1), q = (int32_t)(rc.w & 0x7fffffffu);
-            rc.y = __float_as_uint(__fadd_rn(w.rel[p], w.rel[q]));
-            rc.w = (uint32_t)w.comp[q];
-            w.edges[i] = rc;
+    const uint4* ein = (r & 1) ? w.edges2 : w.edges;
+    uint4* eout = (r & 1) ? w.edges : w.edges2;
+    const int32_t ne = r == 0 ? n_edges(w) : w.ecount[r];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ int32_t s_wcnt[kUwThreads / 32];
+    __shared__ int32_t s_base;
+    // block-uniform loop: the kept edges are appended with one atomic per block (one per warp on a
+    // single counter serialised in L2)
+    for (int32_t b0 = blockIdx.x * blockDim.x; b0 < ne; b0 += stride) {
+        const int32_t i = b0 + threadIdx.x;
+        bool keep = false;
+        uint4 rc = make_uint4(0u, 0u, 0u, 0u);
+        if (i < ne) {
+            rc = ein[i];
+            if (rc.w & 0x80000000u) {  // an edge out of a tile as its tile listed it: completed once
+                const int32_t p = (int32_t)(rc.x >> 1), q = (int32_t)(rc.w & 0x7fffffffu);
+                rc.y = __float_as_uint(__fadd_rn(w.rel[p], w.rel[q]));
+                rc.w = (uint32_t)w.comp[q];
+            }
+            const int32_t cp = hook_par(find_root(w.hook, w.comp2[rc.z], nn));
+            const int32_t cq = hook_par(find_root(w.hook, w.comp2[rc.w], nn));
+            keep = cp != cq;
+            if (keep) {
+                const unsigned long long key =
+                    ((unsigned long long)rc.y << 32) | (unsigned long long)(0xffffffffu - rc.x);
+                offer(best + cp, key);
+                offer(best + cq, key);
+            }
         }
-        const int32_t cp = hook_par(find_root(w.hook, w.comp2[rc.z], nn));
-        const int32_t cq = hook_par(find_root(w.hook, w.comp2[rc.w], nn));
-        if (cp == cq) continue;
-        const unsigned long long key = ((unsigned long long)rc.y << 32) | (unsigned long long)(0xffffffffu - rc.x);
-        offer(best + cp, key);
-        offer(best + cq, key);
+        const unsigned kept = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_wcnt[wid] = __popc(kept);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t tot = 0;
+            for (int k = 0; k < kUwThreads / 32; ++k) {
+                const int32_t v = s_wcnt[k];
+                s_wcnt[k] = tot;
+                tot += v;
+            }
+            s_base = tot ? atomicAdd(w.ecount + r + 1, tot) : 0;
+        }
+        __syncthreads();
+        if (keep) eout[s_base + s_wcnt[wid] + __popc(kept & ((1u << lane) - 1u))] = rc;
+        __syncthreads();  // s_wcnt and s_base are reused by the next pass
     }
 }
 
@@ -593,22 +632,30 @@ __global__ void __launch_bounds__(kUwThreads) uw_ghook(UwArgs a, UwWork w, const
     }
 }
 
+// After the rounds, for every listed local root r: ka[r] = its shift to its final root minus the k
+// of that root's anchor (its smallest pixel), so that a pixel's k relative to the anchor is
+// kk[g] + ka[comp[g]]. (Local roots outside the list got their ka in the tile kernel.)
+__global__ void __launch_bounds__(kUwThreads) uw_anchor(UwWork w) {
+    const int32_t nn = n_nodes(w);
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+        const int32_t r = w.nodes[i];
+        const unsigned long long hw = find_root(w.hook, w.comp2[r], nn);  // the comp2 itself once relabelled
+        const int32_t m = w.minpix[hook_par(hw)];
+        const int32_t lm = w.comp[m];
+        const unsigned long long hm = find_root(w.hook, w.comp2[lm], nn);
+        w.ka[r] = w.kk2[r] + hook_sh(hw) - (w.kk[m] + w.kk2[lm] + hook_sh(hm));
+    }
+}
+
 // phi + 2 pi (k - k at the region's first pixel)
 __global__ void __launch_bounds__(kUwThreads) uw_write(UwArgs a, UwWork w) {
-    const int32_t nn = n_nodes(w);
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.npx; g += (int64_t)gridDim.x * blockDim.x) {
         const FrameDev& F = a.fr[w.fid[g]];
         const int64_t local = g - (int64_t)F.gam_off;
         const float p = w.wph[g];
         float v = p;
         if (!isnan(p)) {
-            const int32_t lr = w.comp[g];
-            const int32_t x = w.comp2[lr];
-            const unsigned long long hw = find_root(w.hook, x, nn);  // x itself once the rounds are done
-            const int32_t m = w.minpix[hook_par(hw)];
-            const int32_t lm = w.comp[m];
-            const unsigned long long hm = find_root(w.hook, w.comp2[lm], nn);
-            const int32_t k = w.kk[g] + w.kk2[lr] + hook_sh(hw) - (w.kk[m] + w.kk2[lm] + hook_sh(hm));
+            const int32_t k = w.kk[g] + w.ka[w.comp[g]];
             v = __fadd_rn(p, __fmul_rn(kTwoPiF, (float)k));
         }
         a.out[F.out_off + a.out_maps * (int64_t)F.H * F.W + local] = v;
@@ -629,6 +676,7 @@ UwWork carve(void* base, int64_t npx, int rounds) {
     w.best = reinterpret_cast<unsigned long long*>(take(16 * n));
     w.hook = reinterpret_cast<unsigned long long*>(take(8 * n));
     w.edges = reinterpret_cast<uint4*>(take(32 * n));
+    w.edges2 = reinterpret_cast<uint4*>(take(32 * n));
     w.wph = reinterpret_cast<float*>(take(4 * n));
     w.rel = reinterpret_cast<float*>(take(4 * n));
     w.fid = reinterpret_cast<int32_t*>(take(4 * n));
@@ -637,10 +685,12 @@ UwWork carve(void* base, int64_t npx, int rounds) {
     w.minpix = reinterpret_cast<int32_t*>(take(4 * n));
     w.comp2 = reinterpret_cast<int32_t*>(take(4 * n));
     w.kk2 = reinterpret_cast<int32_t*>(take(4 * n));
+    w.ka = reinterpret_cast<int32_t*>(take(4 * n));
     w.nodes = reinterpret_cast<int32_t*>(take(4 * n));
     w.tile_start = reinterpret_cast<int32_t*>(take(4 * (n + 2)));  // a call has at most npx frames
     w.counts = reinterpret_cast<unsigned long long*>(take(8));
     w.flags = reinterpret_cast<int32_t*>(take(4 * (size_t)(rounds + 1)));
+    w.ecount = reinterpret_cast<int32_t*>(take(4 * (size_t)(rounds + 1)));
     return w;
 }
 
@@ -652,20 +702,28 @@ int ceil_log2(int64_t n) {
 
 }  // namespace
 
-int unwrap_rounds(int64_t max_frame_px) { return ceil_log2(max_frame_px < 2 ? 2 : max_frame_px) + 1; }
+int unwrap_rounds(int64_t max_frame_nodes) { return ceil_log2(max_frame_nodes < 2 ? 2 : max_frame_nodes) + 1; }
 
-size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_px) {
-    const int R = unwrap_rounds(max_frame_px);
-    const size_t n = (size_t)npx;
-    return align256(16 * n) + align256(8 * n) + align256(32 * n) + 9 * align256(4 * n) + align256(4 * (n + 2)) + align256(8) +
-           align256(4 * (size_t)(R + 1));
+int64_t unwrap_frame_nodes(int H, int W) {
+    // the global phase's components of a frame are local roots on a tile's border: at most the
+    // 4 * 32 - 4 border pixels of each 32 x 32 tile, and never more than the frame's pixels
+    const int64_t tiles = (int64_t)((H + kTile - 1) / kTile) * ((W + kTile - 1) / kTile);
+    const int64_t px = (int64_t)H * W, b = tiles * (4 * kTile - 4);
+    return b < px ? b : px;
 }
 
-cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_px,
+size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_nodes) {
+    const int R = unwrap_rounds(max_frame_nodes);
+    const size_t n = (size_t)npx;
+    return align256(16 * n) + align256(8 * n) + 2 * align256(32 * n) + 10 * align256(4 * n) + align256(4 * (n + 2)) +
+           align256(8) + 2 * align256(4 * (size_t)(R + 1));
+}
+
+cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_nodes,
                           const float* in, int64_t in_maps, float* out, int64_t out_maps, void* work,
                           int* launches, cudaStream_t s) {
     if (npx <= 0 || nframes <= 0) return cudaSuccess;
-    const int R = unwrap_rounds(max_frame_px);
+    const int R = unwrap_rounds(max_frame_nodes);
     UwWork w = carve(work, npx, R);
     UwArgs a{d_frames, nframes, npx, in, in_maps, out, out_maps};
     int dev = 0, sms = 0;
@@ -681,20 +739,20 @@ cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, in
     const int64_t ewant = (2 * npx + kUwThreads - 1) / kUwThreads;
     const unsigned egrid = (unsigned)(ewant < (int64_t)sms * 8 ? ewant : (int64_t)sms * 8);
     uw_prepare<<<1, kUwThreads, 0, s>>>(a, w, R);
-    uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid);
-    uw_reliability<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel);
+    uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel);
     uw_tiles<<<tgrid, kUwThreads, 0, s>>>(a, w);
-    *launches += 4;
+    *launches += 3;
     for (int r = 0; r < R; ++r) {
         const int32_t* live = w.flags + r;
         unsigned long long* bcur = w.best + (size_t)(r & 1) * (size_t)npx;
         unsigned long long* bnext = w.best + (size_t)((r + 1) & 1) * (size_t)npx;
-        uw_gscan<<<egrid, kUwThreads, 0, s>>>(w, bcur, live);
+        uw_gscan<<<egrid, kUwThreads, 0, s>>>(w, bcur, live, r);
         uw_ghook<<<grid, kUwThreads, 0, s>>>(a, w, bcur, bnext, live, w.flags + r + 1);
         *launches += 2;
     }
+    uw_anchor<<<grid, kUwThreads, 0, s>>>(w);
     uw_write<<<grid, kUwThreads, 0, s>>>(a, w);
-    ++*launches;
+    *launches += 2;
     return cudaGetLastError();
 }
 
