@@ -246,21 +246,101 @@ __device__ __forceinline__ void offer(unsigned long long* slot, unsigned long lo
     if (key > *(volatile unsigned long long*)slot) atomicMax(slot, key);
 }
 
+// Shared-memory layout of uw_tiles (dynamic shared memory, kTileSmem bytes): per pixel l of the
+// tile the phase, reliability, best edge of the edges leaving the tile at l, ownership bits of the
+// edges to the right and lower tiles, the round-0 component and the shift within it; per component
+// (indexed by its root's pixel) the best edge, the hook and whether it is a root of the current
+// round; the lists the rounds after the first iterate over (edges between different components,
+// ping-pong; roots, ping-pong; pixels with an edge out of the tile).
+struct TileSmem {
+    unsigned long long* best;   // kTilePx
+    unsigned long long* hook;   // kTilePx
+    unsigned long long* cross;  // kTilePx
+    float* ph;                  // kTilePx
+    float* rel;                 // kTilePx
+    int32_t* kk;                // kTilePx
+    int16_t* comp0;             // kTilePx
+    uint16_t* elist[2];         // 2 kTilePx each: (pixel << 1) | dir of an edge inside the tile
+    uint16_t* rlist[2];         // kTilePx each
+    uint16_t* blist;            // 4 kTile
+    uint8_t* own;               // kTilePx
+    uint8_t* cur;               // kTilePx: 1 for a root of the current round
+    int32_t* misc;              // [0..2] edge counts, [3..5] root counts (by round modulo 3), [6] border count
+};
+constexpr size_t kTileSmem = 3 * 8 * kTilePx + 3 * 4 * kTilePx + 2 * kTilePx + 2 * (2 * 2 * kTilePx) +
+                             2 * (2 * kTilePx) + 2 * 4 * kTile + 2 * kTilePx + 32 * 4;
+
+__device__ __forceinline__ TileSmem tile_smem(unsigned char* base) {
+    TileSmem t;
+    unsigned char* p = base;
+    t.best = reinterpret_cast<unsigned long long*>(p);
+    p += 8 * kTilePx;
+    t.hook = reinterpret_cast<unsigned long long*>(p);
+    p += 8 * kTilePx;
+    t.cross = reinterpret_cast<unsigned long long*>(p);
+    p += 8 * kTilePx;
+    t.ph = reinterpret_cast<float*>(p);
+    p += 4 * kTilePx;
+    t.rel = reinterpret_cast<float*>(p);
+    p += 4 * kTilePx;
+    t.kk = reinterpret_cast<int32_t*>(p);
+    p += 4 * kTilePx;
+    t.comp0 = reinterpret_cast<int16_t*>(p);
+    p += 2 * kTilePx;
+    for (int b = 0; b < 2; ++b) {
+        t.elist[b] = reinterpret_cast<uint16_t*>(p);
+        p += 2 * 2 * kTilePx;
+    }
+    for (int b = 0; b < 2; ++b) {
+        t.rlist[b] = reinterpret_cast<uint16_t*>(p);
+        p += 2 * kTilePx;
+    }
+    t.blist = reinterpret_cast<uint16_t*>(p);
+    p += 2 * 4 * kTile;
+    t.own = p;
+    p += kTilePx;
+    t.cur = p;
+    p += kTilePx;
+    t.misc = reinterpret_cast<int32_t*>(p);
+    return t;
+}
+
+// Root of the component whose former root is x (a component of round 0), and x's shift to it:
+// chases the hooks, stopping at a root of the current round (cur), jumping in place (every word
+// written is a valid (ancestor, summed shift) pair). A chain has fewer than kTilePx links.
+__device__ __forceinline__ unsigned long long tile_find(const TileSmem& S, int32_t x) {
+    volatile unsigned long long* vh = S.hook;
+    unsigned long long hw = S.cur[x] ? pack_hook(x, 0) : vh[x];
+    for (int it = 0; it < kTilePx && !S.cur[hook_par(hw)]; ++it) {
+        const int32_t p = hook_par(hw);
+        const unsigned long long wp = vh[p];
+        hw = pack_hook(hook_par(wp), hook_sh(hw) + hook_sh(wp));
+        vh[x] = hw;
+    }
+    return hw;
+}
+
+// Appends the flagged items of the block's threads to a shared list: one shared atomic per warp.
+// Called by all threads; returns the item's slot (or -1 when not flagged).
+__device__ __forceinline__ int32_t block_append(bool flag, int32_t* count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    int32_t base = 0;
+    if (lane == 0 && m) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return flag ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
 // One CTA per 32 x 32 tile (persistent over the tiles of all frames). Pixel l = 32 i + j of the
-// tile is handled by thread l % 256. Shared state per pixel: phase, reliability, local component
-// (its root's tile index; two buffers, read and written alternately by the rounds), shift within
-// it, smallest member (tile index: row-major in the tile is row-major in the frame), best edge,
-// hook, and the best of the edges that leave the tile at this pixel.
+// tile is handled by thread l % 256 where the work is per pixel. Round 0 treats every pixel as a
+// component: its best edge is the largest of its own (at most four, and the best of those leaving
+// the tile), with no atomics. The rounds after it iterate only over the lists: the edges inside the
+// tile between different components (compacted as components merge), the pixels with an edge out
+// of the tile, and the roots; labels are looked up through the hook chains (tile_find) and written
+// back per pixel once, after the last round.
 __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
-    __shared__ float s_ph[kTilePx];
-    __shared__ float s_rel[kTilePx];
-    __shared__ int16_t s_compb[2][kTilePx];
-    __shared__ int32_t s_kk[kTilePx];
-    __shared__ int32_t s_min[kTilePx];
-    __shared__ unsigned long long s_best[kTilePx];
-    __shared__ unsigned long long s_hook[kTilePx];
-    __shared__ unsigned long long s_cross[kTilePx];
-    __shared__ uint8_t s_own[kTilePx];  // bit 0: owns the edge to the right tile, bit 1: to the tile below
+    extern __shared__ __align__(16) unsigned char tile_smem_raw[];
+    const TileSmem S = tile_smem(tile_smem_raw);
     __shared__ int32_t s_wsum[2 * (kUwThreads / 32)];
     __shared__ unsigned long long s_base;
     __shared__ int s_any[2];
@@ -282,6 +362,7 @@ __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
         const int y0 = (lt / ntx) * kTile, x0 = (lt % ntx) * kTile;
         const int64_t g0 = (int64_t)F.gam_off;
         const int64_t tg = g0 + (int64_t)y0 * W + x0;  // pixel (0, 0) of the tile
+        auto gl = [&](int32_t m) { return (uint32_t)(tg + (int64_t)(m >> 5) * W + (m & 31)); };
         bool in[kPxPerThread];
 #pragma unroll
         for (int k = 0; k < kPxPerThread; ++k) {
@@ -324,140 +405,258 @@ __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
                     own |= vd ? 2 : 0;
                 }
             }
-            s_ph[l] = ph;
-            s_rel[l] = r;
-            s_cross[l] = cross;
-            s_own[l] = own;
-            s_compb[0][l] = (int16_t)l;
-            s_compb[1][l] = (int16_t)l;
-            s_kk[l] = 0;
-            s_min[l] = (int16_t)l;
-            s_best[l] = 0ull;
-            s_hook[l] = pack_hook(l, 0);
+            S.ph[l] = ph;
+            S.rel[l] = r;
+            S.cross[l] = cross;
+            S.own[l] = own;
         }
+        if (t < 8) S.misc[t] = 0;  // list counts
         if (t == 0) s_any[0] = s_any[1] = 0;
         __syncthreads();
 
-        // Boruvka's rounds inside the tile; each round that hooks merges at least two components.
-        // Round r reads the labels of round r - 1 (cur) resolved through its hooks and writes them
-        // to nxt, so the relabelling needs no barrier of its own.
-        int16_t* cur = s_compb[0];
-        int16_t* nxt = s_compb[1];
-        for (int round = 0;; ++round) {
-            int* any = &s_any[round & 1];
-            if (t == 0) s_any[(round + 1) & 1] = 0;  // read last in round - 1, before its last barrier
-            // relabel; every component's most reliable edge, those leaving the tile included
+        // ---- round 0: each pixel's most reliable edge among its own -----------------------------
 #pragma unroll
-            for (int k = 0; k < kPxPerThread; ++k) {
-                const int l = t + k * kUwThreads;
-                if (isnan(s_ph[l])) continue;
-                const unsigned long long hw = s_hook[cur[l]];
-                const int32_t c = hook_par(hw);
-                nxt[l] = (int16_t)c;
-                s_kk[l] += hook_sh(hw);
-                if (s_cross[l]) offer(&s_best[c], s_cross[l]);
-                const int64_t g = tg + (int64_t)(l >> 5) * W + (l & 31);
-                if ((l & 31) + 1 < kTile && !isnan(s_ph[l + 1])) {
-                    const int32_t cq = hook_par(s_hook[cur[l + 1]]);
-                    if (cq != c) {
-                        const unsigned long long key = edge_key(__fadd_rn(s_rel[l], s_rel[l + 1]), (uint32_t)(2 * g));
-                        offer(&s_best[c], key);
-                        offer(&s_best[cq], key);
-                    }
-                }
-                if ((l >> 5) + 1 < kTile && !isnan(s_ph[l + kTile])) {
-                    const int32_t cq = hook_par(s_hook[cur[l + kTile]]);
-                    if (cq != c) {
-                        const unsigned long long key =
-                            edge_key(__fadd_rn(s_rel[l], s_rel[l + kTile]), (uint32_t)(2 * g + 1));
-                        offer(&s_best[c], key);
-                        offer(&s_best[cq], key);
-                    }
-                }
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads, i = l >> 5, j = l & 31;
+            unsigned long long b = 0ull;
+            if (!isnan(S.ph[l])) {
+                const int64_t g = tg + (int64_t)i * W + j;
+                b = S.cross[l];
+                if (j + 1 < kTile && !isnan(S.ph[l + 1]))
+                    b = max(b, edge_key(__fadd_rn(S.rel[l], S.rel[l + 1]), (uint32_t)(2 * g)));
+                if (i + 1 < kTile && !isnan(S.ph[l + kTile]))
+                    b = max(b, edge_key(__fadd_rn(S.rel[l], S.rel[l + kTile]), (uint32_t)(2 * g + 1)));
+                if (j > 0 && !isnan(S.ph[l - 1]))
+                    b = max(b, edge_key(__fadd_rn(S.rel[l - 1], S.rel[l]), (uint32_t)(2 * (g - 1))));
+                if (i > 0 && !isnan(S.ph[l - kTile]))
+                    b = max(b, edge_key(__fadd_rn(S.rel[l - kTile], S.rel[l]), (uint32_t)(2 * (g - W) + 1)));
             }
-            __syncthreads();
-            // roots whose best edge stays in the tile hook across it
+            S.best[l] = b;
+        }
+        __syncthreads();
+        // hooks across round 0's best edges that stay in the tile (shifts: every k is 0 here)
 #pragma unroll
-            for (int k = 0; k < kPxPerThread; ++k) {
-                const int l = t + k * kUwThreads;
-                if (isnan(s_ph[l]) || nxt[l] != l) continue;
-                const unsigned long long key = s_best[l];
-                unsigned long long hk = pack_hook(l, 0);
-                if (key) {
-                    // the edge's first pixel p relative to the tile: d = pi W + pj; an edge inside
-                    // the tile has 0 <= pi, pj and both endpoints in rows and columns 0 .. 31 (a
-                    // pixel left of or above the tile gives d < 0 or pj >= W - 1 >= 32)
-                    const uint32_t e = key_edge(key);
-                    const int64_t d = (int64_t)(e >> 1) - tg;
-                    if (d >= 0) {
-                        const uint32_t pi = (uint32_t)d / (uint32_t)W, pj = (uint32_t)d - pi * (uint32_t)W;
-                        const uint32_t qi = pi + (e & 1u), qj = pj + 1u - (e & 1u);
-                        if (qi < kTile && qj < kTile) {
-                            const int pl = (int)(pi * kTile + pj), ql = (int)(qi * kTile + qj);
-                            const int32_t cp = nxt[pl], cq = nxt[ql];
-                            const int32_t other = cp == l ? cq : cp;
-                            if (!(s_best[other] == key && l < other)) {
-                                const int s = jump(s_ph[pl], s_ph[ql]);
-                                hk = pack_hook(other, cq == l ? s_kk[pl] + s - s_kk[ql] : s_kk[ql] - s - s_kk[pl]);
-                                *any = 1;
-                            }
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            unsigned long long hk = pack_hook(l, 0);
+            const unsigned long long key = S.best[l];
+            if (key) {
+                const uint32_t e = key_edge(key);
+                const int64_t d = (int64_t)(e >> 1) - tg;
+                if (d >= 0) {
+                    const uint32_t pi = (uint32_t)d / (uint32_t)W, pj = (uint32_t)d - pi * (uint32_t)W;
+                    const uint32_t qi = pi + (e & 1u), qj = pj + 1u - (e & 1u);
+                    if (qi < kTile && qj < kTile) {
+                        const int pl = (int)(pi * kTile + pj), ql = (int)(qi * kTile + qj);
+                        const int32_t other = pl == l ? ql : pl;
+                        if (!(S.best[other] == key && l < other)) {
+                            const int s = jump(S.ph[pl], S.ph[ql]);
+                            hk = pack_hook(other, ql == l ? s : -s);
                         }
                     }
                 }
-                s_hook[l] = hk;
             }
-            __syncthreads();
-            if (!*any || round == kTilePx - 1) break;  // (a productive round merges: < 1024 of them)
-            // hooks resolved to roots in place (each jump moves up a chain of fewer than 1024
-            // components); the smallest member goes to the root; best edges cleared
+            S.hook[l] = hk;
+        }
+        __syncthreads();
+        // every pixel's round-0 root and shift (the hook chains, jumped in place); the roots are the
+        // current ones of round 1 and start with no best edge
 #pragma unroll
-            for (int k = 0; k < kPxPerThread; ++k) {
-                const int l = t + k * kUwThreads;
-                if (isnan(s_ph[l]) || nxt[l] != l) continue;
-                s_best[l] = 0ull;
-                volatile unsigned long long* vh = s_hook;
-                unsigned long long hw = vh[l];
-                for (int it = 0; it < kTilePx; ++it) {
-                    const int32_t p = hook_par(hw);
-                    if (p == l) break;
-                    const unsigned long long wp = vh[p];
-                    const int32_t pp = hook_par(wp);
-                    if (pp == p) break;
-                    hw = pack_hook(pp, hook_sh(hw) + hook_sh(wp));
-                    vh[l] = hw;
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            volatile unsigned long long* vh = S.hook;
+            unsigned long long hw = vh[l];
+            for (int it = 0; it < kTilePx; ++it) {
+                const int32_t p = hook_par(hw);
+                if (p == l) break;
+                const unsigned long long wp = vh[p];
+                const int32_t pp = hook_par(wp);
+                if (pp == p) break;
+                hw = pack_hook(pp, hook_sh(hw) + hook_sh(wp));
+                vh[l] = hw;
+            }
+            S.comp0[l] = (int16_t)hook_par(hw);
+            S.kk[l] = hook_sh(hw);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            const bool root = !isnan(S.ph[l]) && S.comp0[l] == l;
+            S.cur[l] = root ? 1 : 0;
+            S.best[l] = 0ull;
+        }
+        // the lists: edges inside the tile between different round-0 components, roots, pixels with
+        // an edge out of the tile
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            const bool v = !isnan(S.ph[l]);
+            const int c = S.comp0[l];
+            const bool er = v && (l & 31) + 1 < kTile && !isnan(S.ph[l + 1]) && S.comp0[l + 1] != c;
+            const bool ed = v && (l >> 5) + 1 < kTile && !isnan(S.ph[l + kTile]) && S.comp0[l + kTile] != c;
+            int32_t slot = block_append(er, &S.misc[0]);
+            if (er) S.elist[0][slot] = (uint16_t)(l << 1);
+            slot = block_append(ed, &S.misc[0]);
+            if (ed) S.elist[0][slot] = (uint16_t)((l << 1) | 1);
+            slot = block_append(v && c == l, &S.misc[3]);
+            if (slot >= 0) S.rlist[0][slot] = (uint16_t)l;
+            slot = block_append(v && S.cross[l] != 0ull, &S.misc[6]);
+            if (slot >= 0) S.blist[slot] = (uint16_t)l;
+        }
+        __syncthreads();
+
+        // ---- rounds 1, 2, ...: over the lists; round r reads the lists of round r - 1 (buffers by
+        // parity) and their counts (misc[(r - 1) % 3] edges, misc[3 + (r - 1) % 3] roots), writes its
+        // own; the counts of round r + 1 are cleared at the start of round r (their previous
+        // contents were last read in round r - 1, before its last barrier). Each round that hooks
+        // merges at least two components.
+        for (int round = 1;; ++round) {
+            int* any = &s_any[round & 1];
+            if (t == 0) {
+                s_any[(round + 1) & 1] = 0;
+                S.misc[(round + 1) % 3] = 0;
+                S.misc[3 + (round + 1) % 3] = 0;
+            }
+            const uint16_t* ecur = S.elist[(round - 1) & 1];
+            uint16_t* enext = S.elist[round & 1];
+            const uint16_t* rcur = S.rlist[(round - 1) & 1];
+            uint16_t* rnext = S.rlist[round & 1];
+            const int32_t ne = S.misc[(round - 1) % 3];
+            const int32_t nr = S.misc[3 + (round - 1) % 3];
+            // every edge still between different components offered to both; kept for the next round
+            for (int32_t b0 = 0; b0 < ne; b0 += kUwThreads) {
+                const int32_t i = b0 + t;
+                bool keep = false;
+                uint16_t code = 0;
+                if (i < ne) {
+                    code = ecur[i];
+                    const int pl = code >> 1, ql = pl + ((code & 1) ? kTile : 1);
+                    const int32_t cp = hook_par(tile_find(S, S.comp0[pl]));
+                    const int32_t cq = hook_par(tile_find(S, S.comp0[ql]));
+                    if (cp != cq) {
+                        keep = true;
+                        const unsigned long long key =
+                            edge_key(__fadd_rn(S.rel[pl], S.rel[ql]), 2u * gl(pl) + (uint32_t)(code & 1));
+                        offer(&S.best[cp], key);
+                        offer(&S.best[cq], key);
+                    }
                 }
-                const int32_t r = hook_par(hw);
-                if (r != l) atomicMin(&s_min[r], s_min[l]);
+                const int32_t slot = block_append(keep, &S.misc[round % 3]);
+                if (keep) enext[slot] = code;
+            }
+            const int32_t nb = S.misc[6];
+            for (int32_t i = t; i < nb; i += kUwThreads) {
+                const int b = S.blist[i];
+                offer(&S.best[hook_par(tile_find(S, S.comp0[b]))], S.cross[b]);
             }
             __syncthreads();
-            int16_t* sw = cur;
-            cur = nxt;
-            nxt = sw;
+            // roots whose best edge stays in the tile hook across it (tile_find stops at the roots of
+            // this round, so the hooks written meanwhile do not move the endpoints' roots)
+            for (int32_t i = t; i < nr; i += kUwThreads) {
+                const int32_t r = rcur[i];
+                const unsigned long long key = S.best[r];
+                if (!key) continue;
+                const uint32_t e = key_edge(key);
+                const int64_t d = (int64_t)(e >> 1) - tg;
+                if (d < 0) continue;
+                const uint32_t pi = (uint32_t)d / (uint32_t)W, pj = (uint32_t)d - pi * (uint32_t)W;
+                const uint32_t qi = pi + (e & 1u), qj = pj + 1u - (e & 1u);
+                if (qi >= kTile || qj >= kTile) continue;  // the edge leaves the tile: the root waits
+                const int pl = (int)(pi * kTile + pj), ql = (int)(qi * kTile + qj);
+                const unsigned long long hp = tile_find(S, S.comp0[pl]), hq = tile_find(S, S.comp0[ql]);
+                const int32_t cp = hook_par(hp), cq = hook_par(hq);
+                const int32_t other = cp == r ? cq : cp;
+                if (S.best[other] == key && r < other) continue;  // both chose this edge: r stays the root
+                const int s = jump(S.ph[pl], S.ph[ql]);
+                const int32_t kp = S.kk[pl] + hook_sh(hp), kq = S.kk[ql] + hook_sh(hq);
+                S.hook[r] = pack_hook(other, cq == r ? kp + s - kq : kq - s - kp);
+                *any = 1;
+            }
+            __syncthreads();
+            if (!*any || round >= kTilePx) break;  // (a productive round merges: < 1024 of them)
+            // this round's hooks resolved to roots in place; the roots that stay form the next list
+            for (int32_t b0 = 0; b0 < nr; b0 += kUwThreads) {
+                const int32_t i = b0 + t;
+                bool stay = false;
+                int32_t r = 0;
+                if (i < nr) {
+                    r = rcur[i];
+                    S.best[r] = 0ull;
+                    volatile unsigned long long* vh = S.hook;
+                    unsigned long long hw = vh[r];
+                    for (int it = 0; it < kTilePx; ++it) {
+                        const int32_t p = hook_par(hw);
+                        if (p == r) break;
+                        const unsigned long long wp = vh[p];
+                        const int32_t pp = hook_par(wp);
+                        if (pp == p) break;
+                        hw = pack_hook(pp, hook_sh(hw) + hook_sh(wp));
+                        vh[r] = hw;
+                    }
+                    stay = hook_par(hw) == r;
+                    S.cur[r] = stay ? 1 : 0;
+                }
+                const int32_t slot = block_append(stay, &S.misc[3 + round % 3]);
+                if (stay) rnext[slot] = (uint16_t)r;
+            }
+            __syncthreads();
         }
 
-        // local components out (nxt holds the last labels): comp (as a pixel index), kk; per local
-        // root its smallest pixel and the identity as its global state
-        const int16_t* fin = nxt;
+        // ---- every pixel's final component and shift; the smallest member of each component -----
+        int16_t finv[kPxPerThread];
+        int32_t kkv[kPxPerThread];
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            finv[k] = (int16_t)l;
+            kkv[k] = 0;
+            if (!isnan(S.ph[l])) {
+                const unsigned long long hw = tile_find(S, S.comp0[l]);
+                finv[k] = (int16_t)hook_par(hw);
+                kkv[k] = S.kk[l] + hook_sh(hw);
+            }
+        }
+        __syncthreads();
+        int32_t* s_minm = reinterpret_cast<int32_t*>(S.best);  // free now
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            S.comp0[l] = finv[k];
+            S.kk[l] = kkv[k];
+            s_minm[l] = l;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int l = t + k * kUwThreads;
+            if (!isnan(S.ph[l])) atomicMin(&s_minm[finv[k]], l);
+        }
+        __syncthreads();
+
+        // local components out: comp (as a pixel index), kk; per local root its smallest pixel and
+        // the identity as its global state
+        const int16_t* fin = S.comp0;
 #pragma unroll
         for (int k = 0; k < kPxPerThread; ++k) {
             const int l = t + k * kUwThreads;
             if (!in[k]) continue;
             const int64_t g = tg + (int64_t)(l >> 5) * W + (l & 31);
             const int32_t c = fin[l];
-            w.comp[g] = (int32_t)(tg + (int64_t)(c >> 5) * W + (c & 31));
-            w.kk[g] = s_kk[l];
+            w.comp[g] = (int32_t)gl(c);
+            w.kk[g] = S.kk[l];
             if (c == l) {
-                const int32_t m = s_min[l];
-                w.minpix[g] = (int32_t)(tg + (int64_t)(m >> 5) * W + (m & 31));
+                const int32_t m = s_minm[l];
+                w.minpix[g] = (int32_t)gl(m);
                 w.comp2[g] = (int32_t)g;
                 w.kk2[g] = 0;
-                w.ka[g] = -s_kk[m];  // a local root outside the global phase is its own final root
-                w.best[g] = 0ull;  // best of round 0
+                w.ka[g] = -S.kk[m];  // a local root outside the global phase is its own final root
+                w.best[g] = 0ull;    // best of round 0
                 w.hook[g] = pack_hook((int32_t)g, 0);
             }
         }
         __syncthreads();
-        int32_t* s_mark = s_kk;  // free now: marks the local roots that the global edges touch
+        int32_t* s_mark = S.kk;  // free now: marks the local roots that the global edges touch
 #pragma unroll
         for (int k = 0; k < kPxPerThread; ++k) s_mark[t + k * kUwThreads] = 0;
         __syncthreads();
@@ -469,16 +668,16 @@ __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
 #pragma unroll
         for (int k = 0; k < kPxPerThread; ++k) {
             const int l = t + k * kUwThreads;
-            if (isnan(s_ph[l])) continue;
+            if (isnan(S.ph[l])) continue;
             const int32_t c = fin[l];
-            if (s_cross[l]) s_mark[c] = 1;
-            ne += (s_own[l] & 1) + ((s_own[l] >> 1) & 1);
-            if ((l & 31) + 1 < kTile && !isnan(s_ph[l + 1]) && fin[l + 1] != c) {
+            if (S.cross[l]) s_mark[c] = 1;
+            ne += (S.own[l] & 1) + ((S.own[l] >> 1) & 1);
+            if ((l & 31) + 1 < kTile && !isnan(S.ph[l + 1]) && fin[l + 1] != c) {
                 ++ne;
                 s_mark[c] = 1;
                 s_mark[fin[l + 1]] = 1;
             }
-            if ((l >> 5) + 1 < kTile && !isnan(s_ph[l + kTile]) && fin[l + kTile] != c) {
+            if ((l >> 5) + 1 < kTile && !isnan(S.ph[l + kTile]) && fin[l + kTile] != c) {
                 ++ne;
                 s_mark[c] = 1;
                 s_mark[fin[l + kTile]] = 1;
@@ -492,24 +691,23 @@ __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
         block_reserve(ne, nn, w.counts, s_wsum, &s_base, &eslot, &nslot);
         // edge records (e, weight bits, local root of p, local root of q); an edge out of the tile
         // carries q | 2^31 instead, its weight and q's local root are filled in by the first round
-        auto gl = [&](int32_t m) { return (uint32_t)(tg + (int64_t)(m >> 5) * W + (m & 31)); };
 #pragma unroll
         for (int k = 0; k < kPxPerThread; ++k) {
             const int l = t + k * kUwThreads;
             if (s_mark[l]) w.nodes[nslot++] = (int32_t)gl(l);
-            if (isnan(s_ph[l])) continue;
+            if (isnan(S.ph[l])) continue;
             const int32_t c = fin[l];
             const uint32_t g = gl(l);
-            if (s_own[l] & 1) {
+            if (S.own[l] & 1) {
                 w.edges[eslot++] = make_uint4(2u * g, 0u, gl(c), (g + 1u) | 0x80000000u);
-            } else if ((l & 31) + 1 < kTile && !isnan(s_ph[l + 1]) && fin[l + 1] != c) {
-                w.edges[eslot++] = make_uint4(2u * g, __float_as_uint(__fadd_rn(s_rel[l], s_rel[l + 1])), gl(c),
+            } else if ((l & 31) + 1 < kTile && !isnan(S.ph[l + 1]) && fin[l + 1] != c) {
+                w.edges[eslot++] = make_uint4(2u * g, __float_as_uint(__fadd_rn(S.rel[l], S.rel[l + 1])), gl(c),
                                               gl(fin[l + 1]));
             }
-            if (s_own[l] & 2) {
+            if (S.own[l] & 2) {
                 w.edges[eslot++] = make_uint4(2u * g + 1u, 0u, gl(c), (g + (uint32_t)W) | 0x80000000u);
-            } else if ((l >> 5) + 1 < kTile && !isnan(s_ph[l + kTile]) && fin[l + kTile] != c) {
-                w.edges[eslot++] = make_uint4(2u * g + 1u, __float_as_uint(__fadd_rn(s_rel[l], s_rel[l + kTile])),
+            } else if ((l >> 5) + 1 < kTile && !isnan(S.ph[l + kTile]) && fin[l + kTile] != c) {
+                w.edges[eslot++] = make_uint4(2u * g + 1u, __float_as_uint(__fadd_rn(S.rel[l], S.rel[l + kTile])),
                                               gl(c), gl(fin[l + kTile]));
             }
         }
@@ -740,7 +938,9 @@ cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, in
     const unsigned egrid = (unsigned)(ewant < (int64_t)sms * 8 ? ewant : (int64_t)sms * 8);
     uw_prepare<<<1, kUwThreads, 0, s>>>(a, w, R);
     uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel);
-    uw_tiles<<<tgrid, kUwThreads, 0, s>>>(a, w);
+    cudaError_t e = cudaFuncSetAttribute(uw_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    if (e != cudaSuccess) return e;
+    uw_tiles<<<tgrid, kUwThreads, kTileSmem, s>>>(a, w);
     *launches += 3;
     for (int r = 0; r < R; ++r) {
         const int32_t* live = w.flags + r;
