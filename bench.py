@@ -62,6 +62,9 @@ def parse():
                     help="timed steps of the forward-only estimate on the main workload (0: skip)")
     ap.add_argument("--square-steps", type=int, default=5,
                     help="timed steps of the paper-geometry leg (square block, both derivatives and alpha)")
+    ap.add_argument("--workloads", default=None,
+                    help="comma-separated subset of the other workloads to run: gaussian, diffusion, uneven, "
+                         "model_order, serving (default: all)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the other workloads (Gaussian-bump plain FP64, diffusion stack, uneven batch, serving)")
     ap.add_argument("--diffusion-frames", type=int, default=500)
@@ -764,182 +767,192 @@ def run_workloads(args, dev, stream, flush, cpu: bool):
     from paper_1910_11872_gb300 import config_bench, rmusic, serve_bench
 
     out = {}
-    # ---- Gaussian bump 128 x 128: plain FP64 GPU path vs the FP64 oracle, whole frame --------
-    fr = synth.small_gaussian_frame()
-    x = torch.from_numpy(fr.image).to(dev)
-    dem = rmusic.Demodulator(device=dev.index, precision="plain_fp64")
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    for _ in range(3):
-        g1, s1, _ = dem.run(x)
-    ms = []
-    for _ in range(10):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        dem.run(x, out=g1, status=s1, stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    clk = clocks.stop()
-    dem.close()
-    res = {"workload": "Gaussian bump 1 x 128x128 float32, noise 0.02, N=32, L=8, plain FP64 GPU path",
-           "value": fr.image.size / statistics.median(ms) / 1e3, "unit": "Mpixel/s",
-           "ms_per_call": statistics.median(ms), "timing": "3 warm-ups, median of 10 event-timed calls",
-           "clocks": clk}
-    if cpu:
-        t0 = time.perf_counter()
-        o, ost, cores = O.demodulate(fr.image, O.make_params(N_WIN, L_COV, 1, 0, 0, F0))
-        dt = time.perf_counter() - t0
-        res["vs_fp64_oracle"] = _oracle_compare(g1.cpu().numpy(), s1.cpu().numpy(), o.ravel(), ost.ravel())
-        res["cpu_baseline"] = {"value": fr.image.size / dt / 1e6, "unit": "Mpixel/s", "cores": cores,
-                               "kind": "oracle", "sample": f"the whole frame ({fr.image.size} px), {dt:.2f} s wall"}
-    out["gaussian_bump_plain_fp64"] = res
-    del x, g1, s1
 
-    # ---- diffusion time-lapse: 500 x 1024^2 uint16 in one call, column windows ----------------
-    stack = config_bench.diffusion_stack(args.diffusion_frames)
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    res, dmaps, dst = config_bench.run_diffusion(stack, flush)
-    res["clocks"] = clocks.stop()
-    if cpu:
-        rng = np.random.default_rng(11875)
-        T = stack.shape[0]
-        ts = sorted({0, T // 3, (2 * T) // 3, T - 1})
-        comp, npx, dt, cores = [], 0, 0.0, 0
-        p = O.make_params(N_WIN, L_COV, 1, 1, 0, F0)
-        for t in ts:
-            fr = synth.diffusion_frame(int(t), T=T)
-            r0 = int(rng.integers(380, 580))
-            rows = np.arange(r0, r0 + 64)  # 64 rows through the diffusion front, every column
-            ys = np.repeat(rows, W).astype(np.int32)
-            xs = np.tile(np.arange(W), rows.size).astype(np.int32)
-            t0 = time.perf_counter()
-            vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
-            dt += time.perf_counter() - t0
-            npx += ys.size
-            g = dmaps[t].cpu().numpy()[ys, xs]
-            s_ = dst[t].cpu().numpy()[ys, xs]
-            comp.append((g, s_, vals, st, fr.truth[ys, xs]))
-        cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
-        res["vs_fp64_oracle"] = _oracle_compare(*cat)
-        res["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
-                               "sample": f"64 rows through the front, all columns, of frames {ts} ({npx} px), "
-                                         f"{dt:.1f} s wall"}
-    out["diffusion_stack"] = res
-    del dmaps, dst, stack
-    torch.cuda.empty_cache()
+    def want(name: str) -> bool:
+        return args.workloads is None or name in args.workloads.split(",")
 
-    # ---- uneven batch: 64 frames of uneven sizes and windows in one call ------------------------
-    frames = synth.uneven_batch()
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    res, umaps, ust, shapes = config_bench.run_uneven(frames, flush)
-    res["clocks"] = clocks.stop()
-    if cpu:
-        rng = np.random.default_rng(11876)
-        gm, sm = umaps.cpu().numpy(), ust.cpu().numpy()
-        offs = np.cumsum([0] + [h * w for h, w in shapes])
-        comp, npx, dt, cores = [], 0, 0.0, 0
-        for i in sorted(rng.choice(len(frames), 8, replace=False)):
-            fr = frames[i]
-            Hf, Wf = fr.image.shape
-            rows = np.sort(rng.choice(Hf, 16, replace=False))
-            ys = np.repeat(rows, Wf).astype(np.int32)
-            xs = np.tile(np.arange(Wf), rows.size).astype(np.int32)
-            p = O.make_params(fr.window_len, fr.cov_order, 1, 0, 0, fr.carrier_freq)
-            t0 = time.perf_counter()
-            vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
-            dt += time.perf_counter() - t0
-            npx += ys.size
-            g = gm[offs[i]:offs[i + 1]].reshape(Hf, Wf)[ys, xs]
-            s_ = sm[offs[i]:offs[i + 1]].reshape(Hf, Wf)[ys, xs]
-            comp.append((g, s_, vals, st, fr.truth[ys, xs]))
-        cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
-        res["vs_fp64_oracle"] = _oracle_compare(*cat)
-        res["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
-                               "sample": f"16 random full rows of each of 8 random frames ({npx} px), {dt:.1f} s wall"}
-    out["uneven_batch"] = res
-    del umaps, ust
-    torch.cuda.empty_cache()
-
-    # ---- model order p = 2 and 3 on raw real lines (Sec. 3 with p exponentials) -------------------
-    res_p = {}
-    for p, offset in ((2, 0.0), (3, 0.15)):
-        frames_p = [synth.raw_fringe_frame(snr, offset, stream=k) for k, snr in enumerate(SNRS)]
-        xp = torch.from_numpy(np.stack([f.image for f in frames_p])).to(dev)
-        outp = torch.empty(xp.numel(), dtype=torch.float32, device=dev)
-        kw = dict(device=dev.index, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0, model_order=p, raw_input=1)
-        demp = rmusic.Demodulator(precision="batched", use_graph=1, timing=1, **kw)
+    if want("gaussian"):
+        # ---- Gaussian bump 128 x 128: plain FP64 GPU path vs the FP64 oracle, whole frame --------
+        fr = synth.small_gaussian_frame()
+        x = torch.from_numpy(fr.image).to(dev)
+        dem = rmusic.Demodulator(device=dev.index, precision="plain_fp64")
         clocks = ClockSampler(dev.index)
         clocks.start()
         for _ in range(3):
-            demp.run(xp, out=outp, with_status=False)
+            g1, s1, _ = dem.run(x)
         ms = []
         for _ in range(10):
-            flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            demp.run(xp, out=outp, with_status=False, stream=stream)
+            dem.run(x, out=g1, status=s1, stream=stream)
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
-        st = demp.stats()
         clk = clocks.stop()
-        gp, gps, _ = demp.run(xp)
-        torch.cuda.synchronize()
-        demp.close()
-        plainp = rmusic.Demodulator(precision="plain_fp32", **kw)
-        plainp.run(xp[:1])
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        plainp.run(xp[:1], stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        plain_ms = a.elapsed_time(b)
-        plainp.close()
-        npx_p = xp.numel()
-        r = {"workload": f"{len(SNRS)} x {H}x{W} float32 raw real fringes (peaks phase 0-10 rad, SNR 40/20/10/5 dB"
-                         f"{', local offset 0.15 sin(x/60)' if offset else ''}), carrier {F0}, N={N_WIN}, L={L_COV}, "
-                         f"model order {p}, forward-backward",
-             "value": npx_p / statistics.median(ms) / 1e3, "unit": "Mpixel/s", "ms_per_call": statistics.median(ms),
-             "solver_ms": st.solver_ms, "mean_subspace_steps": st.mean_power_steps,
-             "jacobi_fallback_frac": st.eig_fallback_frac, "mean_aberth_iters": st.mean_root_iters,
-             "plain_fp32": {"value": H * W / plain_ms / 1e3, "unit": "Mpixel/s", "ms_one_frame": plain_ms},
-             "speedup_vs_plain": (npx_p / statistics.median(ms)) / (H * W / plain_ms),
-             "timing": "graph replay, L2 flushed, 3 warm-ups, median of 10 event-timed calls", "clocks": clk}
+        dem.close()
+        res = {"workload": "Gaussian bump 1 x 128x128 float32, noise 0.02, N=32, L=8, plain FP64 GPU path",
+               "value": fr.image.size / statistics.median(ms) / 1e3, "unit": "Mpixel/s",
+               "ms_per_call": statistics.median(ms), "timing": "3 warm-ups, median of 10 event-timed calls",
+               "clocks": clk}
         if cpu:
-            rng = np.random.default_rng(11877 + p)
-            gm, sm = gp.view(len(frames_p), H, W).cpu().numpy(), gps.view(len(frames_p), H, W).cpu().numpy()
+            t0 = time.perf_counter()
+            o, ost, cores = O.demodulate(fr.image, O.make_params(N_WIN, L_COV, 1, 0, 0, F0))
+            dt = time.perf_counter() - t0
+            res["vs_fp64_oracle"] = _oracle_compare(g1.cpu().numpy(), s1.cpu().numpy(), o.ravel(), ost.ravel())
+            res["cpu_baseline"] = {"value": fr.image.size / dt / 1e6, "unit": "Mpixel/s", "cores": cores,
+                                   "kind": "oracle", "sample": f"the whole frame ({fr.image.size} px), {dt:.2f} s wall"}
+        out["gaussian_bump_plain_fp64"] = res
+        del x, g1, s1
+
+    if want("diffusion"):
+        # ---- diffusion time-lapse: 500 x 1024^2 uint16 in one call, column windows ----------------
+        stack = config_bench.diffusion_stack(args.diffusion_frames)
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        res, dmaps, dst = config_bench.run_diffusion(stack, flush)
+        res["clocks"] = clocks.stop()
+        if cpu:
+            rng = np.random.default_rng(11875)
+            T = stack.shape[0]
+            ts = sorted({0, T // 3, (2 * T) // 3, T - 1})
             comp, npx, dt, cores = [], 0, 0.0, 0
-            prm = O.make_params(N_WIN, L_COV, 1, 0, 0, F0, model_order=p, raw_input=1)
-            for fr, g_, s_ in zip(frames_p, gm, sm):
-                rows = np.sort(rng.choice(H, 8, replace=False))
+            p = O.make_params(N_WIN, L_COV, 1, 1, 0, F0)
+            for t in ts:
+                fr = synth.diffusion_frame(int(t), T=T)
+                r0 = int(rng.integers(380, 580))
+                rows = np.arange(r0, r0 + 64)  # 64 rows through the diffusion front, every column
                 ys = np.repeat(rows, W).astype(np.int32)
                 xs = np.tile(np.arange(W), rows.size).astype(np.int32)
                 t0 = time.perf_counter()
-                vals, ost, cores = O.demodulate_pixels(fr.image, prm, ys, xs)
+                vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
                 dt += time.perf_counter() - t0
                 npx += ys.size
-                comp.append((g_[ys, xs], s_[ys, xs], vals, ost, fr.truth[ys, xs]))
+                g = dmaps[t].cpu().numpy()[ys, xs]
+                s_ = dst[t].cpu().numpy()[ys, xs]
+                comp.append((g, s_, vals, st, fr.truth[ys, xs]))
             cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
-            r["vs_fp64_oracle"] = _oracle_compare(*cat)
-            r["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
-                                 "sample": f"8 random full rows of each frame ({npx} px), {dt:.1f} s wall"}
-        res_p[f"p{p}"] = r
-        del xp, outp, gp, gps
-    out["model_order"] = res_p
+            res["vs_fp64_oracle"] = _oracle_compare(*cat)
+            res["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                                   "sample": f"64 rows through the front, all columns, of frames {ts} ({npx} px), "
+                                             f"{dt:.1f} s wall"}
+        out["diffusion_stack"] = res
+        del dmaps, dst, stack
+        torch.cuda.empty_cache()
 
-    # ---- serving: 16 camera streams, Poisson arrivals at 2000 frames/s ---------------------------
-    sargs = argparse.Namespace(streams=16, rate=2000.0, seconds=args.serve_seconds, pool=2, ring_depth=4,
-                               max_batch_frames=32, max_batch_mpx=32, inflight=3, budget_gb=64.0, device=dev.index)
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    res = serve_bench.run(sargs)
-    res["clocks"] = clocks.stop()
-    res["shed_frac"] = res["frames_rejected"] / max(res["frames_offered"], 1)
-    out["serving"] = res
+    if want("uneven"):
+        # ---- uneven batch: 64 frames of uneven sizes and windows in one call ------------------------
+        frames = synth.uneven_batch()
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        res, umaps, ust, shapes = config_bench.run_uneven(frames, flush)
+        res["clocks"] = clocks.stop()
+        if cpu:
+            rng = np.random.default_rng(11876)
+            gm, sm = umaps.cpu().numpy(), ust.cpu().numpy()
+            offs = np.cumsum([0] + [h * w for h, w in shapes])
+            comp, npx, dt, cores = [], 0, 0.0, 0
+            for i in sorted(rng.choice(len(frames), 8, replace=False)):
+                fr = frames[i]
+                Hf, Wf = fr.image.shape
+                rows = np.sort(rng.choice(Hf, 16, replace=False))
+                ys = np.repeat(rows, Wf).astype(np.int32)
+                xs = np.tile(np.arange(Wf), rows.size).astype(np.int32)
+                p = O.make_params(fr.window_len, fr.cov_order, 1, 0, 0, fr.carrier_freq)
+                t0 = time.perf_counter()
+                vals, st, cores = O.demodulate_pixels(fr.image, p, ys, xs)
+                dt += time.perf_counter() - t0
+                npx += ys.size
+                g = gm[offs[i]:offs[i + 1]].reshape(Hf, Wf)[ys, xs]
+                s_ = sm[offs[i]:offs[i + 1]].reshape(Hf, Wf)[ys, xs]
+                comp.append((g, s_, vals, st, fr.truth[ys, xs]))
+            cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
+            res["vs_fp64_oracle"] = _oracle_compare(*cat)
+            res["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                                   "sample": f"16 random full rows of each of 8 random frames ({npx} px), {dt:.1f} s wall"}
+        out["uneven_batch"] = res
+        del umaps, ust
+        torch.cuda.empty_cache()
+
+    if want("model_order"):
+        # ---- model order p = 2 and 3 on raw real lines (Sec. 3 with p exponentials) -------------------
+        res_p = {}
+        for p, offset in ((2, 0.0), (3, 0.15)):
+            frames_p = [synth.raw_fringe_frame(snr, offset, stream=k) for k, snr in enumerate(SNRS)]
+            xp = torch.from_numpy(np.stack([f.image for f in frames_p])).to(dev)
+            outp = torch.empty(xp.numel(), dtype=torch.float32, device=dev)
+            kw = dict(device=dev.index, window_len=N_WIN, cov_order=L_COV, carrier_freq=F0, model_order=p, raw_input=1)
+            demp = rmusic.Demodulator(precision="batched", use_graph=1, timing=1, **kw)
+            clocks = ClockSampler(dev.index)
+            clocks.start()
+            for _ in range(3):
+                demp.run(xp, out=outp, with_status=False)
+            ms = []
+            for _ in range(10):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                demp.run(xp, out=outp, with_status=False, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            st = demp.stats()
+            clk = clocks.stop()
+            gp, gps, _ = demp.run(xp)
+            torch.cuda.synchronize()
+            demp.close()
+            plainp = rmusic.Demodulator(precision="plain_fp32", **kw)
+            plainp.run(xp[:1])
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plainp.run(xp[:1], stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            plain_ms = a.elapsed_time(b)
+            plainp.close()
+            npx_p = xp.numel()
+            r = {"workload": f"{len(SNRS)} x {H}x{W} float32 raw real fringes (peaks phase 0-10 rad, SNR 40/20/10/5 dB"
+                             f"{', local offset 0.15 sin(x/60)' if offset else ''}), carrier {F0}, N={N_WIN}, L={L_COV}, "
+                             f"model order {p}, forward-backward",
+                 "value": npx_p / statistics.median(ms) / 1e3, "unit": "Mpixel/s", "ms_per_call": statistics.median(ms),
+                 "solver_ms": st.solver_ms, "mean_subspace_steps": st.mean_power_steps,
+                 "jacobi_fallback_frac": st.eig_fallback_frac, "mean_aberth_iters": st.mean_root_iters,
+                 "plain_fp32": {"value": H * W / plain_ms / 1e3, "unit": "Mpixel/s", "ms_one_frame": plain_ms},
+                 "speedup_vs_plain": (npx_p / statistics.median(ms)) / (H * W / plain_ms),
+                 "timing": "graph replay, L2 flushed, 3 warm-ups, median of 10 event-timed calls", "clocks": clk}
+            if cpu:
+                rng = np.random.default_rng(11877 + p)
+                gm, sm = gp.view(len(frames_p), H, W).cpu().numpy(), gps.view(len(frames_p), H, W).cpu().numpy()
+                comp, npx, dt, cores = [], 0, 0.0, 0
+                prm = O.make_params(N_WIN, L_COV, 1, 0, 0, F0, model_order=p, raw_input=1)
+                for fr, g_, s_ in zip(frames_p, gm, sm):
+                    rows = np.sort(rng.choice(H, 8, replace=False))
+                    ys = np.repeat(rows, W).astype(np.int32)
+                    xs = np.tile(np.arange(W), rows.size).astype(np.int32)
+                    t0 = time.perf_counter()
+                    vals, ost, cores = O.demodulate_pixels(fr.image, prm, ys, xs)
+                    dt += time.perf_counter() - t0
+                    npx += ys.size
+                    comp.append((g_[ys, xs], s_[ys, xs], vals, ost, fr.truth[ys, xs]))
+                cat = [np.concatenate([c[i] for c in comp]) for i in range(5)]
+                r["vs_fp64_oracle"] = _oracle_compare(*cat)
+                r["cpu_baseline"] = {"value": npx / dt / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                                     "sample": f"8 random full rows of each frame ({npx} px), {dt:.1f} s wall"}
+            res_p[f"p{p}"] = r
+            del xp, outp, gp, gps
+        out["model_order"] = res_p
+
+    if want("serving"):
+        # ---- serving: 16 camera streams, Poisson arrivals at 2000 frames/s ---------------------------
+        sargs = argparse.Namespace(streams=16, rate=2000.0, seconds=args.serve_seconds, pool=2, ring_depth=4,
+                                   max_batch_frames=32, max_batch_mpx=32, inflight=3, budget_gb=64.0, device=dev.index)
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        res = serve_bench.run(sargs)
+        res["clocks"] = clocks.stop()
+        res["shed_frac"] = res["frames_rejected"] / max(res["frames_offered"], 1)
+        out["serving"] = res
+
     return out
 
 

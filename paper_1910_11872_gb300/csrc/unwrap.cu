@@ -260,8 +260,10 @@ struct TileSmem {
     float* rel;                 // kTilePx
     int32_t* kk;                // kTilePx
     int16_t* comp0;             // kTilePx
-    uint16_t* elist[2];         // 2 kTilePx each: (pixel << 1) | dir of an edge inside the tile
-    uint16_t* rlist[2];         // kTilePx each
+    uint16_t* elist0;           // 2 kTilePx each: (pixel << 1) | dir of an edge inside the tile
+    uint16_t* elist1;
+    uint16_t* rlist0;           // kTilePx each
+    uint16_t* rlist1;
     uint16_t* blist;            // 4 kTile
     uint8_t* own;               // kTilePx
     uint8_t* cur;               // kTilePx: 1 for a root of the current round
@@ -287,14 +289,16 @@ __device__ __forceinline__ TileSmem tile_smem(unsigned char* base) {
     p += 4 * kTilePx;
     t.comp0 = reinterpret_cast<int16_t*>(p);
     p += 2 * kTilePx;
-    for (int b = 0; b < 2; ++b) {
-        t.elist[b] = reinterpret_cast<uint16_t*>(p);
-        p += 2 * 2 * kTilePx;
-    }
-    for (int b = 0; b < 2; ++b) {
-        t.rlist[b] = reinterpret_cast<uint16_t*>(p);
-        p += 2 * kTilePx;
-    }
+    // (named buffers, picked by ternaries below: a pointer array indexed at run time would put the
+    // whole struct in local memory)
+    t.elist0 = reinterpret_cast<uint16_t*>(p);
+    p += 2 * 2 * kTilePx;
+    t.elist1 = reinterpret_cast<uint16_t*>(p);
+    p += 2 * 2 * kTilePx;
+    t.rlist0 = reinterpret_cast<uint16_t*>(p);
+    p += 2 * kTilePx;
+    t.rlist1 = reinterpret_cast<uint16_t*>(p);
+    p += 2 * kTilePx;
     t.blist = reinterpret_cast<uint16_t*>(p);
     p += 2 * 4 * kTile;
     t.own = p;
@@ -496,11 +500,11 @@ __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
             const bool er = v && (l & 31) + 1 < kTile && !isnan(S.ph[l + 1]) && S.comp0[l + 1] != c;
             const bool ed = v && (l >> 5) + 1 < kTile && !isnan(S.ph[l + kTile]) && S.comp0[l + kTile] != c;
             int32_t slot = block_append(er, &S.misc[0]);
-            if (er) S.elist[0][slot] = (uint16_t)(l << 1);
+            if (er) S.elist0[slot] = (uint16_t)(l << 1);
             slot = block_append(ed, &S.misc[0]);
-            if (ed) S.elist[0][slot] = (uint16_t)((l << 1) | 1);
+            if (ed) S.elist0[slot] = (uint16_t)((l << 1) | 1);
             slot = block_append(v && c == l, &S.misc[3]);
-            if (slot >= 0) S.rlist[0][slot] = (uint16_t)l;
+            if (slot >= 0) S.rlist0[slot] = (uint16_t)l;
             slot = block_append(v && S.cross[l] != 0ull, &S.misc[6]);
             if (slot >= 0) S.blist[slot] = (uint16_t)l;
         }
@@ -518,10 +522,11 @@ __global__ void __launch_bounds__(kUwThreads) uw_tiles(UwArgs a, UwWork w) {
                 S.misc[(round + 1) % 3] = 0;
                 S.misc[3 + (round + 1) % 3] = 0;
             }
-            const uint16_t* ecur = S.elist[(round - 1) & 1];
-            uint16_t* enext = S.elist[round & 1];
-            const uint16_t* rcur = S.rlist[(round - 1) & 1];
-            uint16_t* rnext = S.rlist[round & 1];
+            const bool odd = round & 1;
+            const uint16_t* ecur = odd ? S.elist0 : S.elist1;
+            uint16_t* enext = odd ? S.elist1 : S.elist0;
+            const uint16_t* rcur = odd ? S.rlist0 : S.rlist1;
+            uint16_t* rnext = odd ? S.rlist1 : S.rlist0;
             const int32_t ne = S.misc[(round - 1) % 3];
             const int32_t nr = S.misc[3 + (round - 1) % 3];
             // every edge still between different components offered to both; kept for the next round
