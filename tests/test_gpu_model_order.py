@@ -210,3 +210,38 @@ def test_batched_model_order_mix_equals_alone_and_rejections():
             dem.run(torch.zeros(4, 64, dtype=torch.complex64, device="cuda"))
     finally:
         dem.close()
+
+
+def test_batched_model_order_columns_uint16_and_fp64_step():
+    """Column windows (carrier and windows along y), 12-bit uint16 frames, and the optional FP64
+    step (on Q itself): statuses equal to the oracle's and max |GPU - oracle| <= 1e-4 rad/px."""
+    rng = np.random.default_rng(21)
+    y, x = np.mgrid[0:320, 0:24]
+    phi = 1.2 * np.sin(y / 37.0 + 0.3 * x / 24) + 0.015 * x
+    real = 0.5 + 0.2 * (y > 100) + 0.4 * np.cos(TWO_PI * 0.1 * y + phi) + synth.sigma_for_snr(0.4, 20.0) * rng.normal(size=y.shape)
+    u16 = np.clip(np.round(real * 3000.0), 0, 4095).astype(np.uint16)
+    for p in (2, 3):
+        for polish in (0, 1):
+            g, st = run_u16_cols(u16, p, polish)
+            o, ost, _ = O.demodulate(u16, O.make_params(32, 8, 1, 1, 1, 0.1, model_order=p, raw_input=1))
+            _check_p_cols(g, st, o, ost, what=f"columns uint16 p={p} fp64={polish}")
+
+
+def run_u16_cols(u16, p, polish):
+    torch = _torch()
+    dem = rmusic.Demodulator(window_len=32, cov_order=8, model_order=p, raw_input=1, carrier_freq=0.1,
+                             carrier_axis=1, deriv_axis=1, polish_fp64=polish, precision="batched")
+    try:
+        t16 = torch.from_numpy(u16.astype(np.int16)).cuda()
+        out, st, _ = dem.run(t16)
+        torch.cuda.synchronize()
+    finally:
+        dem.close()
+    return out.cpu().numpy().reshape(u16.shape), st.cpu().numpy().reshape(u16.shape)
+
+
+def _check_p_cols(g, gs, o, os_, what, tol=1e-4):
+    assert np.array_equal(gs, os_), f"{what}: status maps differ at {int((gs != os_).sum())} pixels"
+    both = (gs == 0) & (os_ == 0)
+    d = np.abs((g.astype(np.float64) - o + np.pi) % TWO_PI - np.pi)
+    assert both.sum() > 0 and d[both].max() <= tol, f"{what}: max {d[both].max():.3e}"
