@@ -25,12 +25,16 @@
 //   poly    c_0 = L - p, c_k = -sum_i sum_m V_i[m] V_i[m+k] (Eq. 12-14 with the projector of p
 //           orthonormal vectors); real coefficients. Roots and polish on the lags shrunk by 2e-6
 //           (as for p = 1); the optional FP64 step on Q itself.
-//   roots   every root inside the unit disk by the symmetric Aberth iteration of roots_device.cuh,
-//           started at the carrier's angle (with real coefficients, starting points placed
-//           symmetrically about the real axis would stay so, and a real one would stay real).
-//   select  of the p inner roots nearest the circle, the one whose angle is nearest the carrier's
-//           2 pi f0 (the positive frequency of the fringe); a split double root is located on Q'
-//           between its halves as for p = 1; two polish steps.
+//   roots   p = 2: Newton's method on the signal root from the carrier's angle, polished, certified
+//           by a Schur-Cohn count (the real coefficients make the signal roots an exact pair z,
+//           conj(z): L - 3 roots inside |z| - 0.02 prove the pair the two nearest the circle), the
+//           pair's member whose angle is nearest the carrier's. Otherwise (p = 3, or a lane without
+//           the certificate, and with it its warp) every root inside the unit disk by the symmetric
+//           Aberth iteration of roots_device.cuh, started at the carrier's angle (with real
+//           coefficients, starting points placed symmetrically about the real axis would stay so,
+//           and a real one would stay real); of the p inner roots nearest the circle the one whose
+//           angle is nearest the carrier's 2 pi f0 (the positive frequency of the fringe); a split
+//           double root located on Q' between its halves as for p = 1; two polish steps.
 #pragma once
 
 #include "batched_kernel.cuh"
@@ -546,16 +550,62 @@ batched_p_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_ite
             }
             const float res_lim2 = (3e-6f * qsum) * (3e-6f * qsum);
 
-            // ---- every inner root, selection among the PM nearest the circle, polish ---------------
-            cx<float> z[L - 1], mz[L - 1];
-            int riters, revals, rupdates;
-            bool rconv;
-            inner_roots_from<L>(c, res_lim2, args.max_iters, e0, z, mz, riters, revals, rupdates, rconv);
-            cx<float> zs, zn;
-            bool found;
-            select_p<L, PM>(z, mz, omega_ref, zs, zn, found);
-            const bool cluster = norm2(zn - zs) < 4e-3f * 4e-3f;
-            const cx<float> zz = polish_root<L>(c, zs, zn, cluster);
+            // ---- the selected root ---------------------------------------------------------------
+            // p = 2, certified: the coefficients are real, so the signal roots are an exact pair z,
+            // conj(z). Newton's method (the root's mirror divided out) from radius 0.99 at the
+            // carrier's angle, two polish steps, and a Schur-Cohn count of exactly L - 3 roots inside
+            // |z| - 0.02 prove that z and conj(z) are the two inner roots nearest the circle; of them
+            // the selection takes the one whose angle is nearest omega_ref. Lanes without the
+            // certificate (and all lanes for p = 3, exhaustive runs) take every inner root by Aberth.
+            cx<float> zz = mkc(1.f, 0.f);
+            bool found = true, rconv = true, cluster = false, cert = false;
+            int riters = 0, revals = 0, rupdates = 0, newton = 0, rfb = 0;
+            if constexpr (PM == 2) {
+                if (!args.exhaustive) {
+                    cx<float> z = 0.99f * e0;
+                    bool nconv = !nonzero;
+#pragma unroll 1
+                    for (int it = 0; it < kNewtonSteps; ++it) {
+                        cx<float> pv, dv;
+                        horner_pd<L>(c, z, pv, dv);
+                        const cx<float> wv = mirror_newton_step(z, pv, dv);
+                        const bool fin = isfinite(wv.r) && isfinite(wv.i);
+                        const bool small = norm2(pv) <= res_lim2;
+                        if (!nconv && !small && fin) {
+                            z = z - wv;
+                            const float r2 = norm2(z);
+                            if (r2 > 1.f) z = frcp(r2) * z;
+                        }
+                        nconv = nconv || small || (fin && norm2(wv) <= 1e-5f);
+                        ++newton;
+                        if (__all_sync(kFull, nconv)) break;
+                    }
+                    z = polish_isolated<L>(c, z);
+                    const float r = sqrtf(norm2(z));
+                    // a pair near the real axis may be a split double root: the full root finder
+                    if (nonzero && nconv && r > 0.5f && fabsf(z.i) > 4e-3f) cert = roots_inside<L>(c, r - 0.02f) == L - 3;
+                    cert = cert || !nonzero;
+                    const cx<float> zc = conjg(z);
+                    zz = fabsf(wrap_pi(atan2f(z.i, z.r) - omega_ref)) <= fabsf(wrap_pi(atan2f(zc.i, zc.r) - omega_ref)) ? z : zc;
+                    rconv = nconv;
+                }
+            }
+            if (__any_sync(kFull, !cert)) {
+                rfb = 1;
+                cx<float> z[L - 1], mz[L - 1];
+                bool aconv, afound;
+                inner_roots_from<L>(c, res_lim2, args.max_iters, e0, z, mz, riters, revals, rupdates, aconv);
+                cx<float> zs, zn;
+                select_p<L, PM>(z, mz, omega_ref, zs, zn, afound);
+                const bool cl = norm2(zn - zs) < 4e-3f * 4e-3f;
+                const cx<float> za = polish_root<L>(c, zs, zn, cl);
+                if (!cert) {
+                    zz = za;
+                    cluster = cl;
+                    found = afound;
+                    rconv = aconv;
+                }
+            }
             const float om = args.polish64 ? (float)wrap_pi(polish_arg64<L>(cu, zz, cluster) - F.omega_ref)
                                            : wrap_pi(atan2f(zz.i, zz.r) - omega_ref);
 
@@ -568,7 +618,8 @@ batched_p_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_ite
                 cs[4] += (unsigned long long)revals;
                 cs[5] += (unsigned long long)steps;
                 cs[6] += (unsigned long long)eig_fb;
-                cs[8] += 1ull;  // every pixel takes the full root finder on this path
+                cs[7] += (unsigned long long)newton;
+                cs[8] += (unsigned long long)rfb;
                 cs[9] += (unsigned long long)kPolishSteps;
             }
 

@@ -245,3 +245,27 @@ def _check_p_cols(g, gs, o, os_, what, tol=1e-4):
     both = (gs == 0) & (os_ == 0)
     d = np.abs((g.astype(np.float64) - o + np.pi) % TWO_PI - np.pi)
     assert both.sum() > 0 and d[both].max() <= tol, f"{what}: max {d[both].max():.3e}"
+
+
+@pytest.mark.parametrize("fb,N,L", [(1, 32, 8), (0, 24, 6), (1, 48, 12)])
+def test_batched_model_order_two_certified_equals_exhaustive(fb, N, L):
+    """p = 2: the certified Newton root (the conjugate pair proven the two inner roots nearest the
+    circle by a Schur-Cohn count) selects what the full root finder selects, to FP32 resolution, and
+    decides nearly every lane."""
+    torch = _torch()
+    img, _ = _fringe_rows(16, 320, 15.0, 0.0, seed=5)
+    res = {}
+    for ex in (0, 1):
+        dem = rmusic.Demodulator(window_len=N, cov_order=L, model_order=2, raw_input=1, carrier_freq=0.1,
+                                 forward_backward=fb, precision="batched", exhaustive=ex)
+        try:
+            out, st, _ = dem.run(torch.from_numpy(img).cuda())
+            torch.cuda.synchronize()
+            res[ex] = (out.cpu().numpy(), st.cpu().numpy(), dem.stats())
+        finally:
+            dem.close()
+    (g0, s0, st0), (g1, s1, st1) = res[0], res[1]
+    assert np.array_equal(s0, s1)
+    v = s0 == 0
+    assert np.abs((g0[v].astype(np.float64) - g1[v] + np.pi) % TWO_PI - np.pi).max() <= 2e-5
+    assert st1.root_fallback_frac == 1.0 and st0.root_fallback_frac <= 0.1 and st0.mean_newton_steps >= 1.0
