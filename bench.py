@@ -165,12 +165,14 @@ def flops_per_pixel(L: int, N: int, sweeps: float, evals: float, updates: float,
 
 
 def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: float, newton: float = 0.0,
-                           root_fallback: float = 0.0, polish: float = 4.0) -> float:
+                           root_fallback: float = 0.0, polish: float = 4.0, warm: float = 0.0) -> float:
     """Algorithmic FP32 flops per pixel of the square-block solver (block side M = 2 Lp + 1), from
     its steps with the measured power-iteration steps, Newton steps, Aberth evaluations, updates and
     fallbacks (the root figures add both polynomials):
       power it.   per step G^H u and G y (M^2 complex multiply-adds each, 8 flops), the norm (3 M),
-                  normalisation and step size (8 M); the start vector (5 M)
+                  normalisation and step size (8 M); the start vector (5 M); per measured warm start
+                  (a row that starts from the row above's v1) G v (M^2 complex multiply-adds) and its
+                  normalisation (5 M)
       polynomials per axis: |u|^2 (3 M), M (M - 1) / 2 lag products (8), scaling and moduli (8 per lag)
       roots       Newton steps (newton_flops) and per axis the Schur-Cohn certificate; Aberth fallback:
                   aberth_flops, starting points (10 per root + 20) and selection (13 per root)
@@ -181,7 +183,7 @@ def square_flops_per_pixel(Lp: int, power_its: float, evals: float, updates: flo
     """
     M = 2 * Lp + 1
     NI, NR = M - 1, 2 * M - 2
-    power = 5 * M + power_its * (16 * M * M + 11 * M)
+    power = 5 * M + power_its * (16 * M * M + 11 * M) + warm * (8 * M * M + 5 * M)
     coefs = 2 * (3 * M + 4 * M * (M - 1) + 8 * (M - 1))
     roots = newton * newton_flops(M) + 2 * schur_cohn_flops(M)
     aberth = aberth_flops(M, evals, updates) + root_fallback * (10 * NI + 20 + 13 * NI)
@@ -663,7 +665,7 @@ def run_square_leg(args, rank, world, dev, stream, flush):
     barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.square_steps)]
-    solver_ms, its, evals, updates, launches, newton, rootfb, polish = [], [], [], [], 0, [], [], []
+    solver_ms, its, evals, updates, launches, newton, rootfb, polish, warm = [], [], [], [], 0, [], [], [], []
     for k in range(args.square_steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -677,12 +679,14 @@ def run_square_leg(args, rank, world, dev, stream, flush):
         newton.append(st.mean_newton_steps)
         rootfb.append(st.root_fallback_frac)
         polish.append(st.mean_polish_steps)
+        warm.append(st.mean_power_steps)  # square geometry: warm starts per 32-pixel group
         launches += st.kernel_launches
     torch.cuda.synchronize()
     step_ms = max_over_ranks(world, statistics.mean(a.elapsed_time(b) for a, b in ev))
     value = npx * world / (step_ms * 1e3)
     fpp = square_flops_per_pixel(SQ_LP, statistics.mean(its), statistics.mean(evals), statistics.mean(updates),
-                                 statistics.mean(newton), statistics.mean(rootfb), statistics.mean(polish))
+                                 statistics.mean(newton), statistics.mean(rootfb), statistics.mean(polish),
+                                 statistics.mean(warm))
     solver_avg = statistics.mean(solver_ms)
     achieved = fpp * npx / (solver_avg * 1e-3) / 1e12
     res = {"workload": SQ_WORKLOAD, "value": value, "unit": "Mpixel/s", "ms_per_step": step_ms,
@@ -693,7 +697,7 @@ def run_square_leg(args, rank, world, dev, stream, flush):
                         "kernel": f"square_kernel<{SQ_LP}, {st.solver_ctas_per_sm}>", "flops_per_pixel": fpp,
                         "launch_ms": solver_avg, "mean_power_iters": statistics.mean(its),
                         "mean_newton_steps": statistics.mean(newton), "root_fallback_frac": statistics.mean(rootfb),
-                        "mean_polish_steps": statistics.mean(polish),
+                        "mean_polish_steps": statistics.mean(polish), "warm_start_frac": statistics.mean(warm),
                         "mean_aberth_evals": statistics.mean(evals), "mean_aberth_updates": statistics.mean(updates)},
            "paper_table2_context": PAPER_TABLE2_1024}
 

@@ -317,9 +317,11 @@ int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int device, co
  * as the method does (edges taken by decreasing reliability, the reliability of a pixel being the
  * inverse of its wrapped second differences, 0 where a neighbour has no value) and then shifted so
  * that its first pixel in row-major order keeps its wrapped value. Reliabilities and 2 pi jumps
- * are decided in float32. The work is a fixed sequence of kernels (3 + 4 (ceil(log2(H W)) + 1)
- * launches for the largest frame), queued on cuda_stream. Total pixels of a call: below 2^31.
- * Errors: RMUSIC_EINVAL, RMUSIC_ENOMEM (workspace of 40 bytes per pixel over the budget),
+ * are decided in float32. The work is a fixed sequence of kernels queued on cuda_stream: three per
+ * pixel or per 32 x 32 tile, two per round of the global phase (ceil(log2(n)) + 1 rounds, n the
+ * border pixels of the largest frame's 32 x 32 tiles), two per pixel at the end. Total pixels of a
+ * call: below 2^31.
+ * Errors: RMUSIC_EINVAL, RMUSIC_ENOMEM (workspace of about 132 bytes per pixel over the budget),
  * RMUSIC_ECUDA. */
 int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
                         float* d_out, void* cuda_stream);
@@ -374,9 +376,10 @@ int rmusic_checked_build(void);
  *   check_violations  batched path, checked builds only (rmusic_checked_build() == 1): index
  *                    tests of the solvers that failed in the last call (each skips its work item
  *                    instead of faulting; 0 is the only acceptable value). Always 0 otherwise.
- *   In the square geometry a 32-pixel group is one warp's 32 pixels of a tile row, mean_sweeps counts
- *   power-iteration steps, and the root figures add both polynomials (root_fallback_frac up to 2,
- *   mean_polish_steps counts both).
+ *   In the square geometry a 32-pixel group is one warp's 32 pixels of a strip row, mean_sweeps counts
+ *   power-iteration steps, mean_power_steps the fraction of groups in which some pixel started from
+ *   the row above's right singular vector (one extra block product), and the root figures add both
+ *   polynomials (root_fallback_frac up to 2, mean_polish_steps counts both).
  *   bandpass_ms, solver_ms  with params.timing = 1: summed device time (CUDA events on the
  *                    call's stream) of the band-pass launches and of the solver launches.
  *   solver_ctas_per_sm  batched path: resident CTAs per SM of the solver variant last launched.

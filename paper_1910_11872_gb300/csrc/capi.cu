@@ -145,7 +145,7 @@ int describe_frame(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev*
     }
     // the solvers split a frame's work-item index with 32-bit arithmetic (far above any frame whose
     // analytic signal fits a GPU)
-    const int64_t rows = square ? ((int64_t)d.height + kSqTY - 1) / kSqTY : (int64_t)F->wlines;
+    const int64_t rows = square ? (int64_t)d.height : (int64_t)F->wlines;
     if (rows * (int64_t)F->nchunks >= (int64_t)1 << 31) return RMUSIC_EUNSUPPORTED;
     return RMUSIC_OK;
 }
@@ -341,6 +341,9 @@ struct Plan {
     int max_kc = 0;
     int max_len = 0;
     uint64_t gamma_elems = 0;
+    // square geometry with complex64 frames only: the frames are the analytic signal already, and
+    // the solver reads them in place (no band-pass launch, no copy into the workspace)
+    bool square_direct = false;
 };
 
 int describe(const rmusic_ctx* ctx, const rmusic_frame_desc& d, FrameDev* F) { return describe_frame(ctx->p, d, F); }
@@ -382,14 +385,27 @@ int build_plan(const rmusic_ctx* ctx, const rmusic_frame_desc* descs, int n, Pla
             plan->group_items.push_back(0);
         }
         F.item_start = plan->group_items.back();
-        if (F.geom == kGeomSquare)
-            plan->group_items.back() += (int64_t)((F.H + kSqTY - 1) / kSqTY) * F.nchunks;
-        else
+        if (F.geom == kGeomSquare) {
+            F.sq_strip_rows = square_strip_rows(F.H);
+            plan->group_items.back() += (int64_t)(F.sq_strip_rows / kSqTY) * F.nchunks;
+        } else {
             plan->group_items.back() += (int64_t)F.wlines * F.nchunks;
+        }
         plan->group_count.back() += 1;
+    }
+    // square geometry: every group's single-row items after all of its strips
+    for (size_t g = 0; g < plan->group_first.size(); ++g) {
+        for (int j = 0; j < plan->group_count[g]; ++j) {
+            FrameDev& F = plan->frames[(size_t)(plan->group_first[g] + j)];
+            if (F.geom != kGeomSquare) continue;
+            F.item_start2 = plan->group_items[g];
+            plan->group_items[g] += (int64_t)(F.H - F.sq_strip_rows) * F.nchunks;
+        }
     }
     plan->total_lines = lines;
     plan->gamma_elems = goff;
+    plan->square_direct = ctx->p.geometry == RMUSIC_GEOM_SQUARE && n > 0 && plan->cross_groups == 0;
+    for (const FrameDev& F : plan->frames) plan->square_direct = plan->square_direct && F.dtype == kDtC64;
     return RMUSIC_OK;
 }
 
@@ -545,8 +561,8 @@ int solver_grid(rmusic_ctx* ctx, int L, int v) {
 
 // Launch variant v of the solver of group g of `plan` (solver key plan.group_L[g]) on s; the
 // group's work counter must be zero. stat_counters receives the iteration statistics or is NULL.
-cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, float* d_out, uint8_t* d_status,
-                          unsigned long long* stat_counters, cudaStream_t s) {
+cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, const void* d_frames, float* d_out,
+                          uint8_t* d_status, unsigned long long* stat_counters, cudaStream_t s) {
     const rmusic_params& p = ctx->p;
     const int key = plan.group_L[g];
     const float2* gamma = static_cast<const float2*>(ctx->d_gamma);
@@ -558,6 +574,7 @@ cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, fl
         a.exhaustive = p.exhaustive;
         a.tol2 = 1e-9f;  // power iteration: stop at a step below 3.2e-5 (u1 to ~1e-5)
         a.counters = stat_counters;
+        a.direct = plan.square_direct ? static_cast<const unsigned char*>(d_frames) : nullptr;
         return launch_square(key - kSquareKey0, v, ctx->d_table + plan.group_first[g], plan.group_count[g],
                              plan.group_items[g], ctx->d_counters + g, gamma, d_out, d_status, a,
                              solver_grid(ctx, key, v), s);
@@ -586,7 +603,8 @@ cudaError_t launch_solver(rmusic_ctx* ctx, const Plan& plan, size_t g, int v, fl
 // Time every solver variant on `plan`, whose table and analytic signal are already on the device
 // (queued on s), and keep the fastest for each covariance order not tuned yet (all of them when
 // `force`). Synchronises s; the maps it writes are the call's results.
-int tune_plan(rmusic_ctx* ctx, const Plan& plan, float* d_out, uint8_t* d_status, cudaStream_t s, bool force) {
+int tune_plan(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_out, uint8_t* d_status, cudaStream_t s,
+              bool force) {
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     RM_CUDA(cudaEventCreate(&t0));
     RM_CUDA(cudaEventCreate(&t1));
@@ -603,7 +621,7 @@ int tune_plan(rmusic_ctx* ctx, const Plan& plan, float* d_out, uint8_t* d_status
             for (int rep = 0; rep < 2 && rc == RMUSIC_OK; ++rep) {
                 cudaError_t e = cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s);
                 if (e == cudaSuccess) e = cudaEventRecord(t0, s);
-                if (e == cudaSuccess) e = launch_solver(ctx, plan, g, v, d_out, d_status, nullptr, s);
+                if (e == cudaSuccess) e = launch_solver(ctx, plan, g, v, d_frames, d_out, d_status, nullptr, s);
                 if (e == cudaSuccess) e = cudaEventRecord(t1, s);
                 if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                 float ms = 0.f;
@@ -647,7 +665,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
     const int n = (int)plan.frames.size();
     cudaEvent_t e0 = stamp(ctx, s);
     const bool fp64 = ctx->p.precision == RMUSIC_PLAIN_FP64;
-    {
+    if (!plan.square_direct) {
         NvtxRange r("rmusic.bandpass");
         RM_CUDA(launch_analytic(ctx->d_table, n, plan.total_lines, plan.max_len, plan.band_sched, d_frames,
                                 ctx->d_gamma, fp64, s));
@@ -666,7 +684,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
             NvtxRange r("rmusic.solver");
             RM_CUDA(cudaMemsetAsync(ctx->d_counters + g, 0, sizeof(unsigned long long), s));
             cudaEvent_t e1 = stamp(ctx, s);
-            RM_CUDA(launch_solver(ctx, plan, g, v, d_out, d_status, ctx->d_counters + kStatSlot, s));
+            RM_CUDA(launch_solver(ctx, plan, g, v, d_frames, d_out, d_status, ctx->d_counters + kStatSlot, s));
             stamp_pair(ctx->solver_ev, e1, stamp(ctx, s));
             ctx->stats.solver_ctas_per_sm = solver_ctas(L, v);
             ctx->stats.solver_variant = v;
@@ -755,13 +773,13 @@ int run_group(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_desc* de
             RM_CUDA(cudaMemcpyAsync(ctx->d_table, ctx->h_table, plan.frames.size() * sizeof(FrameDev),
                                     cudaMemcpyHostToDevice, s));
             RM_CUDA(cudaEventRecord(ctx->table_free, s));
-            RM_CUDA(launch_analytic(ctx->d_table, (int)plan.frames.size(), plan.total_lines, plan.max_len,
-                                    plan.band_sched, d_frames,
-                                    ctx->d_gamma, false, s));
+            if (!plan.square_direct)
+                RM_CUDA(launch_analytic(ctx->d_table, (int)plan.frames.size(), plan.total_lines, plan.max_len,
+                                        plan.band_sched, d_frames, ctx->d_gamma, false, s));
             if (plan.cross_groups > 0)
                 RM_CUDA(launch_crossband(ctx->d_table, (int)plan.frames.size(), plan.cross_groups, plan.max_kc,
                                          ctx->d_gamma, false, s));
-            rc = tune_plan(ctx, plan, d_out, d_status, s, force_tune);
+            rc = tune_plan(ctx, plan, d_frames, d_out, d_status, s, force_tune);
             if (rc) return rc;
             for (auto& g : ctx->graphs) drop_graph(ctx, g);  // captured graphs may hold the previous variants
         }

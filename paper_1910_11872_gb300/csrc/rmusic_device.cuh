@@ -49,6 +49,8 @@ struct FrameDev {
     uint64_t gam_off;     // element offset of the frame's analytic signal in the workspace
     int64_t line_start;   // first carrier line of this frame in the band-pass grid
     int64_t item_start;   // first warp work item of this frame in the batched schedule
+    int64_t item_start2;  // square geometry: first single-row item of this frame (they follow every
+                          // frame's strips)
     int32_t H, W, pitch, dtype;
     int32_t N, L;
     int32_t carrier_axis, deriv_axis;
@@ -66,6 +68,8 @@ struct FrameDev {
     int32_t band_r;       // band-pass schedule: 0 one CTA per carrier line; 8, 16 or 32: lines of
                           // 32 band_r samples in groups of 4 x 32 / band_r per CTA (warp FFTs)
     int32_t rowp_shift;   // row geometry, FP32-batched path: log2 of the pixels each lane owns
+    int32_t sq_strip_rows; // square geometry: rows 0 .. sq_strip_rows - 1 go in strips of kSqTY rows,
+                           // the rest one row per item
 };
 
 // Index of the frame that owns global index `g` given each frame's start (non-decreasing).

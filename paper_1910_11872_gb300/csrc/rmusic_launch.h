@@ -104,11 +104,18 @@ cudaError_t launch_batched_p(int p, int L, const FrameDev* d_frames, int nframes
                              BatchedArgs a, int grid, cudaStream_t stream);
 int batched_p_grid(int p, int L, int device);
 
-// Square-block FP32 path (the paper's geometry): persistent, one 32 x 4 pixel tile per CTA work
-// item, over all frames that share the half-width Lp. `counter` must be zero when it starts.
+// Square-block FP32 path (the paper's geometry): persistent, one warp per work item, over all
+// frames that share the half-width Lp. The items: first every frame's 32 x kSqTY strips (the warp
+// walks the rows in order, each row starting from the one above), then every frame's last rows
+// (about an eighth) one 32-pixel row per item, so that the warps end together. `counter` must be
+// zero when it starts.
 constexpr int kMaxSquareLp = 8;
-constexpr int kSqTX = 32;  // tile width in pixels: one warp's pixels along x
-constexpr int kSqTY = 4;   // tile height: one row per warp of the 128-thread CTA
+constexpr int kSqTX = 32;     // item width in pixels: one per lane
+constexpr int kSqTY = 8;      // strip height: the rows one warp walks in order
+constexpr int kSqWarps = 4;   // warps of the 128-thread CTA, each on its own items
+constexpr int kSqTailDiv = 8; // about H / kSqTailDiv rows of each frame go one row per item
+// Rows of an H-row frame that go in strips (a multiple of kSqTY).
+__host__ __device__ constexpr int square_strip_rows(int H) { return kSqTY * ((H - H / kSqTailDiv) / kSqTY); }
 struct SquareArgs {
     int max_power_iters;
     int max_iters;
@@ -116,9 +123,11 @@ struct SquareArgs {
     int exhaustive;                // 1: all roots for every pixel (no Newton certificate)
     float tol2;                    // power iteration stops when |u_new - u|^2 <= tol2
     unsigned long long* counters;  // [0] power iterations, [1] Aberth iterations, [2] warps, [3] Aberth root
-                                   // updates, [4] Aberth evaluations of Q and Q', [7] Newton steps,
-                                   // [8] Aberth fallbacks, [9] polish steps (root figures: both
-                                   // polynomials)
+                                   // updates, [4] Aberth evaluations of Q and Q', [5] warm starts,
+                                   // [7] Newton steps, [8] Aberth fallbacks, [9] polish steps (root
+                                   // figures: both polynomials)
+    const unsigned char* direct;   // non-null: every frame is complex64 and read in place, frame f's
+                                   // row y at direct + F.in_off + 8 F.pitch y (d_gamma is not read)
 };
 bool square_supports(int Lp);
 int square_num_variants(int Lp);

@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kUwThreads) uw_init(UwArgs a, float* __restric
             rel[g] = c;
             continue;
         }
-        const int i = (int)(local / F.W), j = (int)(local % F.W), W = F.W;
+        // a frame has fewer than 2^31 pixels: 32-bit division (a 64-bit one is a long routine)
+        const int W = F.W;
+        const int i = (int)((uint32_t)local / (uint32_t)W), j = (int)((uint32_t)local - (uint32_t)i * (uint32_t)W);
         bool inner = i >= 1 && i + 1 < F.H && j >= 1 && j + 1 < W;
         if (inner) {
             for (int di = -1; di <= 1; ++di)

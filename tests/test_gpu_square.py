@@ -270,10 +270,50 @@ def test_square_variants_identical():
 def test_square_stats_and_launches():
     frames = [synth.complex_fringe_frame(0.0, H=64, W=64).image]
     res, st = run_square(frames, 5, with_stats=True, timing=1)
-    assert st.kernel_launches == 2  # copy of the complex frame into the workspace + the solver
+    assert st.kernel_launches == 1  # a complex frame is the analytic signal: the solver reads it in place
     assert 1.0 <= st.mean_sweeps <= 100.0
     # the signal root of both polynomials by Newton's method; the Aberth fallback only where the
     # certificate fails in some lane (at most both polynomials of every work item)
     assert 2.0 <= st.mean_newton_steps <= 32.0 and 0.0 <= st.root_fallback_frac <= 2.0
     assert st.mean_polish_steps == 4.0, st.mean_polish_steps  # two steps for each polynomial
     assert st.solver_ms > 0
+
+
+def test_square_complex_frames_in_place_pitched():
+    """Complex64 frames are read in place: frames at byte offsets inside a wider, padded buffer (row
+    pitch above the width) give the same maps bit for bit as the same frames packed."""
+    torch = _torch()
+    frames = [synth.complex_fringe_frame(5.0, H=h, W=w, stream=i).image for i, (h, w) in
+              enumerate([(40, 72), (33, 50)])]
+    packed = run_square(frames, 4)
+    pitch = 80
+    rows = sum(f.shape[0] for f in frames) + 3
+    buf = np.full((rows, pitch), np.complex64(7 + 7j))  # padding that must never be read
+    descs = (rmusic.rmusic_frame_desc * 2)()
+    r0, oo = 1, 0
+    for i, f in enumerate(frames):
+        H, W = f.shape
+        buf[r0:r0 + H, 2:2 + W] = f
+        descs[i] = rmusic.rmusic_frame_desc((r0 * pitch + 2) * 8, H, W, pitch, rmusic.RMUSIC_DTYPE_C64, oo, 0, 0)
+        r0 += H + 1
+        oo += 3 * H * W
+    dem = rmusic.Demodulator(geometry="square", half_width=4, carrier_freq=0.0, precision="batched")
+    try:
+        d_in = torch.from_numpy(buf).cuda()
+        out = torch.empty(oo, dtype=torch.float32, device="cuda")
+        st = torch.empty(oo, dtype=torch.uint8, device="cuda")
+        rmusic.rmusic_demodulate_frames(dem.ctx, d_in.data_ptr(), descs, 2, out.data_ptr(), st.data_ptr(), None)
+        torch.cuda.synchronize()
+        assert dem.stats().kernel_launches == 1
+        o, s8 = out.cpu().numpy(), st.cpu().numpy()
+    finally:
+        dem.close()
+    off = 0
+    for (dx, dy, al, stp), f in zip(packed, frames):
+        n = f.size
+        H, W = f.shape
+        assert np.array_equal(o[off:off + n].reshape(H, W), dx, equal_nan=True)
+        assert np.array_equal(o[off + n:off + 2 * n].reshape(H, W), dy, equal_nan=True)
+        assert np.array_equal(o[off + 2 * n:off + 3 * n].reshape(H, W), al, equal_nan=True)
+        assert np.array_equal(s8[off:off + n].reshape(H, W), stp)
+        off += 3 * n
