@@ -318,13 +318,23 @@ int rmusic_demodulate_frames_noalloc(const rmusic_params* params, int device, co
  * inverse of its wrapped second differences, 0 where a neighbour has no value) and then shifted so
  * that its first pixel in row-major order keeps its wrapped value. Reliabilities and 2 pi jumps
  * are decided in float32. The work is a fixed sequence of kernels queued on cuda_stream: three per
- * pixel or per 32 x 32 tile, two per round of the global phase (ceil(log2(n)) + 1 rounds, n the
- * border pixels of the largest frame's 32 x 32 tiles), two per pixel at the end. Total pixels of a
- * call: below 2^31.
+ * pixel or per 32 x 32 tile; for the global phase's R = ceil(log2(n)) + 1 rounds (n the border
+ * pixels of the largest frame's 32 x 32 tiles) two per round of the first ceil(R / 2), then one
+ * cooperative launch (every CTA resident) for the rest, whose CTAs wait on one another at
+ * grid-wide barriers, each wait bounded (see rmusic_stats.wait_timeouts); two per pixel at the
+ * end. Total pixels of a call: below 2^31.
  * Errors: RMUSIC_EINVAL, RMUSIC_ENOMEM (workspace of about 132 bytes per pixel over the budget),
  * RMUSIC_ECUDA. */
 int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
                         float* d_out, void* cuda_stream);
+
+/* rmusic_unwrap_phase with the global phase's schedule given: its first launched_rounds rounds
+ * (clamped to R) as two launches each, the rest in the cooperative launch; -1 is
+ * rmusic_unwrap_phase's own split, ceil(R / 2); 0 runs every round cooperatively. Every split
+ * computes the same maps bit for bit (for tests and measurement).
+ * Errors: those of rmusic_unwrap_phase; RMUSIC_EINVAL for launched_rounds < -1. */
+int rmusic_unwrap_phase_sched(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
+                              float* d_out, int32_t launched_rounds, void* cuda_stream);
 
 /* Batched path: pin the solver variant this context uses for covariance order `order` (row
  * geometry) or half-width `order` (square geometry), overriding the autotuner's choice; -1 returns
@@ -376,6 +386,9 @@ int rmusic_checked_build(void);
  *   check_violations  batched path, checked builds only (rmusic_checked_build() == 1): index
  *                    tests of the solvers that failed in the last call (each skips its work item
  *                    instead of faulting; 0 is the only acceptable value). Always 0 otherwise.
+ *   wait_timeouts    phase assembly (unwrap = 1, or the last rmusic_unwrap_phase call): grid-wide
+ *                    waits of its cooperative kernel that gave up (0.5 s each; the kernel then
+ *                    stops and that call's unwrapped maps are incomplete). 0 in every correct run.
  *   In the square geometry a 32-pixel group is one warp's 32 pixels of a strip row, mean_sweeps counts
  *   power-iteration steps, mean_power_steps the fraction of groups in which some pixel started from
  *   the row above's right singular vector (one extra block product), and the root figures add both
@@ -404,6 +417,7 @@ typedef struct {
     double root_fallback_frac;
     double mean_polish_steps;
     uint64_t check_violations;
+    uint64_t wait_timeouts;
 } rmusic_stats;
 
 int rmusic_get_stats(const rmusic_ctx* ctx, rmusic_stats* out);

@@ -696,7 +696,7 @@ int enqueue(rmusic_ctx* ctx, const Plan& plan, const void* d_frames, float* d_ou
             int64_t maxnodes = 0;
             for (const FrameDev& F : plan.frames) maxnodes = std::max<int64_t>(maxnodes, unwrap_frame_nodes(F.H, F.W));
             RM_CUDA(launch_unwrap(ctx->d_table, n, (int64_t)plan.gamma_elems, maxnodes, d_out, 2, d_out, 3,
-                                  ctx->d_unwrap, launches, s));
+                                  ctx->d_unwrap, -1, ctx->d_counters + kStatSlot + kWaitSlot, launches, s));
         }
     } else {
         PlainArgs a;
@@ -932,7 +932,7 @@ int demodulate_impl(rmusic_ctx* ctx, const void* d_frames, const rmusic_frame_de
         if (rc) return rc;
         pixels += (uint64_t)F.H * (uint64_t)F.W;
     }
-    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, (kStatSlots + 1) * sizeof(unsigned long long), s));
+    RM_CUDA(cudaMemsetAsync(ctx->d_counters + kStatSlot, 0, (kStatSlots + 2) * sizeof(unsigned long long), s));
     // group frames so that each group's analytic signal fits the budget (with room for the frame
     // table when the one held is too small for this call)
     const uint64_t table_reserve =
@@ -1112,7 +1112,12 @@ int rmusic_set_solver_variant(rmusic_ctx* ctx, int32_t order, int32_t variant) {
 
 int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
                         float* d_out, void* cuda_stream) {
-    if (!ctx || n_frames < 0) return RMUSIC_EINVAL;
+    return rmusic_unwrap_phase_sched(ctx, d_phase, descs, n_frames, d_out, -1, cuda_stream);
+}
+
+int rmusic_unwrap_phase_sched(rmusic_ctx* ctx, const float* d_phase, const rmusic_frame_desc* descs, int32_t n_frames,
+                              float* d_out, int32_t launched_rounds, void* cuda_stream) {
+    if (!ctx || n_frames < 0 || launched_rounds < -1) return RMUSIC_EINVAL;
     if (n_frames == 0) return RMUSIC_OK;
     if (!d_phase || !descs || !d_out) return RMUSIC_EINVAL;
     DeviceGuard guard(ctx->device);
@@ -1141,8 +1146,10 @@ int rmusic_unwrap_phase(rmusic_ctx* ctx, const float* d_phase, const rmusic_fram
     RM_CUDA(cudaMemcpyAsync(ctx->d_table, ctx->h_table, frames.size() * sizeof(FrameDev), cudaMemcpyHostToDevice, s));
     RM_CUDA(cudaEventRecord(ctx->table_free, s));
     int launches = 0;
+    unsigned long long* timeouts = ctx->d_counters + kStatSlot + kWaitSlot;
+    RM_CUDA(cudaMemsetAsync(timeouts, 0, sizeof(unsigned long long), s));
     RM_CUDA(launch_unwrap(ctx->d_table, n_frames, (int64_t)npx, maxpx, d_phase, 0, d_out, 0, ctx->d_unwrap,
-                          &launches, s));
+                          launched_rounds, timeouts, &launches, s));
     ctx->stats.kernel_launches = launches;
     return RMUSIC_OK;
 }
@@ -1201,7 +1208,7 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->workspace_bytes = ctx->held;
     out->pixels = ctx->last_pixels;
     RM_CUDA(cudaEventSynchronize(ctx->call_done));
-    unsigned long long c[kStatSlots + 1] = {};  // the statistics and the failed index checks
+    unsigned long long c[kStatSlots + 2] = {};  // the statistics, the failed index checks, the waits given up
     RM_CUDA(cudaMemcpy(c, ctx->d_counters + kStatSlot, sizeof(c), cudaMemcpyDeviceToHost));
     auto mean = [&](int i) { return c[2] ? (double)c[i] / (double)c[2] : 0.0; };
     out->mean_sweeps = mean(0);
@@ -1214,6 +1221,7 @@ int rmusic_get_stats(const rmusic_ctx* ctx_in, rmusic_stats* out) {
     out->root_fallback_frac = mean(8);
     out->mean_polish_steps = mean(9);
     out->check_violations = c[kCheckSlot];
+    out->wait_timeouts = c[kWaitSlot];
     auto sum = [&](const std::vector<cudaEvent_t>& v) {
         float t = 0.f;
         for (size_t i = 0; i + 1 < v.size(); i += 2) {

@@ -45,6 +45,8 @@ cudaError_t launch_plain_fp32(const FrameDev* d_frame, const FrameDev& h_frame, 
 constexpr int kStatSlots = 10;
 // Slot after the statistics: index checks that failed (checked builds only).
 constexpr int kCheckSlot = kStatSlots;
+// Slot after it: grid-wide waits of the phase assembly that gave up.
+constexpr int kWaitSlot = kStatSlots + 1;
 
 #ifdef __CUDACC__
 // Checked builds (-DRMUSIC_CHECKS) test the solvers' data-dependent indices: rm_check(ok, counters)
@@ -142,11 +144,15 @@ int square_grid(int Lp, int v, int device);
 // pixels are g = F.gam_off .. F.gam_off + H W - 1; its input map at in + F.out_off + in_maps H W,
 // its output at out + F.out_off + out_maps H W; NaN = no value). max_frame_nodes is the largest
 // unwrap_frame_nodes(H, W) over the frames (it bounds the rounds); any larger value is safe. work
-// must hold unwrap_workspace_bytes(npx, max_frame_nodes) bytes; npx < 2^31.
+// must hold unwrap_workspace_bytes(npx, max_frame_nodes) bytes; npx < 2^31. The global phase's
+// first launched_rounds rounds (-1: half the rounds bound, rounded up; clamped to the bound) run as
+// two launches each, the rest in one cooperative launch whose CTAs wait on one another at
+// grid-wide barriers; a wait that gives up (after 0.5 s) stops that kernel and adds one to
+// *timeouts (a device counter, may be null): the output of that call is then incomplete.
 int64_t unwrap_frame_nodes(int H, int W);
 size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_nodes);
 cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_nodes,
                           const float* in, int64_t in_maps, float* out, int64_t out_maps, void* work,
-                          int* launches, cudaStream_t s);
+                          int launched_rounds, unsigned long long* timeouts, int* launches, cudaStream_t s);
 
 }  // namespace rmusic

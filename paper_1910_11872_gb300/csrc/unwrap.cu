@@ -92,6 +92,7 @@ struct UwArgs {
     int64_t in_maps;
     float* out;         // map of frame f at out + F.out_off + out_maps * H * W
     int64_t out_maps;
+    unsigned long long* timeouts;  // grid-wide waits of uw_gtail that gave up (device counter, may be null)
 };
 
 // Workspace carved from one buffer. Per pixel g: wph (wrapped phase), rel, fid (frame), comp (root
@@ -118,6 +119,9 @@ struct UwWork {
     int32_t* tile_start;  // nframes + 1 entries: first tile of each frame, then the total
     unsigned long long* counts;  // listed edges (low word) and nodes (high word)
     int32_t* flags;     // rounds + 1 live flags
+    unsigned int* sync; // uw_gtail's grid barriers: [0] arrivals, [32] the last barrier passed
+    int32_t* stop;      // set when one of uw_gtail's grid barriers gave up
+    int64_t npx;
 };
 
 __device__ __forceinline__ int32_t n_edges(const UwWork& w) { return (int32_t)(uint32_t)(*w.counts & 0xffffffffull); }
@@ -139,7 +143,12 @@ __global__ void __launch_bounds__(kUwThreads) uw_prepare(UwArgs a, UwWork w, int
         w.flags[i] = i == 0 ? 1 : 0;
         w.ecount[i] = 0;
     }
-    if (t == 0) *w.counts = 0ull;
+    if (t == 0) {
+        *w.counts = 0ull;
+        w.sync[0] = 0u;
+        w.sync[32] = 0u;
+        *w.stop = 0;
+    }
     __syncthreads();
     for (int base = 0; base < a.nframes; base += kUwThreads) {
         const int f = base + t;
@@ -741,48 +750,63 @@ __device__ __forceinline__ unsigned long long find_root(unsigned long long* hook
     return hw;
 }
 
-// Round r, first launch: every listed component takes the hooks of round r - 1 (comp2 = its root,
-// kk2 += its shift to it; a root of round r - 1 that hooked hands its smallest pixel to its new
-// root), and every edge still between different components is offered to both components'
-// best[r & 1] and kept for round r + 1 (the list shrinks as components merge: an edge inside a
-// component stays inside). Runs while round r - 1 hooked anything (flags[r]).
-__global__ void __launch_bounds__(kUwThreads) uw_gscan(UwWork w, unsigned long long* __restrict__ best,
-                                                      const int32_t* __restrict__ live, int r) {
-    if (!*live) return;
+// Loads of words that other CTAs may have written earlier in the same launch (the cooperative
+// kernel below): from L2 (ld.global.cg), never a stale L1 line. Between launches a plain load.
+template <bool kL2>
+__device__ __forceinline__ int32_t ldx(const int32_t* p) {
+    if constexpr (kL2) return __ldcg(p);
+    else return *p;
+}
+template <bool kL2>
+__device__ __forceinline__ unsigned long long ldx(const unsigned long long* p) {
+    if constexpr (kL2) return __ldcg(p);
+    else return *p;
+}
+template <bool kL2>
+__device__ __forceinline__ uint4 ldx(const uint4* p) {
+    if constexpr (kL2) return __ldcg(p);
+    else return *p;
+}
+
+// Round r, scan: every listed component takes the hooks of round r - 1 (comp2 = its root, kk2 +=
+// its shift to it; a root of round r - 1 that hooked hands its smallest pixel to its new root),
+// and every edge still between different components is offered to both components' best[r & 1]
+// and kept for round r + 1 (the list shrinks as components merge: an edge inside a component
+// stays inside). Called by every thread of the grid (tid, stride: its index and the grid's
+// threads); the edge loop is block-uniform, so the kept edges are appended with one atomic per
+// block (one per warp on a single counter serialises in L2).
+template <bool kL2>
+__device__ __forceinline__ void scan_round(const UwWork& w, unsigned long long* best, int r, int32_t tid,
+                                           int32_t stride, int32_t* s_wcnt, int32_t* s_base) {
     const int32_t nn = n_nodes(w);
-    const int32_t stride = gridDim.x * blockDim.x;
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride) {
+    for (int32_t i = tid; i < nn; i += stride) {
         const int32_t c = w.nodes[i];
-        const int32_t x = w.comp2[c];
+        const int32_t x = ldx<kL2>(w.comp2 + c);
         const unsigned long long hw = find_root(w.hook, x, nn);
         const int32_t root = hook_par(hw);
         if (root != x) {
             w.comp2[c] = root;
-            w.kk2[c] += hook_sh(hw);
-            if (x == c) atomicMin(w.minpix + root, w.minpix[c]);  // nobody hands pixels to a hooked root
+            w.kk2[c] = ldx<kL2>(w.kk2 + c) + hook_sh(hw);
+            if (x == c) atomicMin(w.minpix + root, ldx<kL2>(w.minpix + c));  // nobody hands pixels to a hooked root
         }
     }
     const uint4* ein = (r & 1) ? w.edges2 : w.edges;
     uint4* eout = (r & 1) ? w.edges : w.edges2;
-    const int32_t ne = r == 0 ? n_edges(w) : w.ecount[r];
+    const int32_t ne = r == 0 ? n_edges(w) : ldx<kL2>(w.ecount + r);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __shared__ int32_t s_wcnt[kUwThreads / 32];
-    __shared__ int32_t s_base;
-    // block-uniform loop: the kept edges are appended with one atomic per block (one per warp on a
-    // single counter serialised in L2)
-    for (int32_t b0 = blockIdx.x * blockDim.x; b0 < ne; b0 += stride) {
+    for (int32_t b0 = tid - (int32_t)threadIdx.x; b0 < ne; b0 += stride) {
         const int32_t i = b0 + threadIdx.x;
         bool keep = false;
         uint4 rc = make_uint4(0u, 0u, 0u, 0u);
         if (i < ne) {
-            rc = ein[i];
+            rc = ldx<kL2>(ein + i);
             if (rc.w & 0x80000000u) {  // an edge out of a tile as its tile listed it: completed once
                 const int32_t p = (int32_t)(rc.x >> 1), q = (int32_t)(rc.w & 0x7fffffffu);
                 rc.y = __float_as_uint(__fadd_rn(w.rel[p], w.rel[q]));
                 rc.w = (uint32_t)w.comp[q];
             }
-            const int32_t cp = hook_par(find_root(w.hook, w.comp2[rc.z], nn));
-            const int32_t cq = hook_par(find_root(w.hook, w.comp2[rc.w], nn));
+            const int32_t cp = hook_par(find_root(w.hook, ldx<kL2>(w.comp2 + rc.z), nn));
+            const int32_t cq = hook_par(find_root(w.hook, ldx<kL2>(w.comp2 + rc.w), nn));
             keep = cp != cq;
             if (keep) {
                 const unsigned long long key =
@@ -801,39 +825,126 @@ __global__ void __launch_bounds__(kUwThreads) uw_gscan(UwWork w, unsigned long l
                 s_wcnt[k] = tot;
                 tot += v;
             }
-            s_base = tot ? atomicAdd(w.ecount + r + 1, tot) : 0;
+            *s_base = tot ? atomicAdd(w.ecount + r + 1, tot) : 0;
         }
         __syncthreads();
-        if (keep) eout[s_base + s_wcnt[wid] + __popc(kept & ((1u << lane) - 1u))] = rc;
+        if (keep) eout[*s_base + s_wcnt[wid] + __popc(kept & ((1u << lane) - 1u))] = rc;
         __syncthreads();  // s_wcnt and s_base are reused by the next pass
     }
 }
 
-// Round r, second launch: every root hooks onto the component across its best edge (hook[r] =
-// (parent, shift); of two roots that chose the same edge the smaller stays), and clears its slot of
-// best[(r + 1) & 1] for the next round (its roots are among this round's).
-__global__ void __launch_bounds__(kUwThreads) uw_ghook(UwArgs a, UwWork w, const unsigned long long* __restrict__ best,
-                                                      unsigned long long* __restrict__ best_next,
-                                                      const int32_t* __restrict__ live_in, int32_t* __restrict__ live_out) {
-    if (!*live_in) return;
+// Round r, hook: every root hooks onto the component across its best edge (hook = (parent,
+// shift); of two roots that chose the same edge the smaller stays) and clears its slot of
+// best[(r + 1) & 1] for the next round (its roots are among this round's); flags[r + 1] = 1 if any
+// root hooked.
+template <bool kL2>
+__device__ __forceinline__ void hook_round(const UwArgs& a, const UwWork& w, const unsigned long long* best,
+                                           unsigned long long* best_next, int r, int32_t tid, int32_t stride) {
     const int32_t n = n_nodes(w);
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int32_t r = w.nodes[i];
-        if (w.comp2[r] != r) continue;  // not a root
-        const unsigned long long key = best[r];
-        best_next[r] = 0ull;
+    for (int32_t i = tid; i < n; i += stride) {
+        const int32_t rt = w.nodes[i];
+        if (ldx<kL2>(w.comp2 + rt) != rt) continue;  // not a root
+        const unsigned long long key = ldx<kL2>(best + rt);
+        best_next[rt] = 0ull;
         if (!key) continue;
         const uint32_t e = key_edge(key);
         const int32_t p = (int32_t)(e >> 1);
         const int32_t q = p + ((e & 1u) ? a.fr[w.fid[p]].W : 1);
         const int32_t lp = w.comp[p], lq = w.comp[q];
-        const int32_t cp = w.comp2[lp], cq = w.comp2[lq];
-        const int32_t other = cp == r ? cq : cp;
-        if (best[other] == key && r < other) continue;  // both chose this edge: r stays the root
-        const int s = jump(w.wph[p], w.wph[q]);          // k_q - k_p must equal s
-        const int32_t kp = w.kk[p] + w.kk2[lp], kq = w.kk[q] + w.kk2[lq];
-        w.hook[r] = pack_hook(other, cq == r ? kp + s - kq : kq - s - kp);
-        *live_out = 1;
+        const int32_t cp = ldx<kL2>(w.comp2 + lp), cq = ldx<kL2>(w.comp2 + lq);
+        const int32_t other = cp == rt ? cq : cp;
+        if (ldx<kL2>(best + other) == key && rt < other) continue;  // both chose this edge: rt stays the root
+        const int s = jump(w.wph[p], w.wph[q]);                        // k_q - k_p must equal s
+        const int32_t kp = w.kk[p] + ldx<kL2>(w.kk2 + lp), kq = w.kk[q] + ldx<kL2>(w.kk2 + lq);
+        w.hook[rt] = pack_hook(other, cq == rt ? kp + s - kq : kq - s - kp);
+        w.flags[r + 1] = 1;
+    }
+}
+
+// Round r as two launches (the rounds with most of the work: every CTA of a full grid on it).
+// Both return at once when round r - 1 joined nothing (flags[r] == 0).
+__global__ void __launch_bounds__(kUwThreads) uw_gscan(UwWork w, int r) {
+    __shared__ int32_t s_wcnt[kUwThreads / 32];
+    __shared__ int32_t s_base;
+    if (!w.flags[r]) return;
+    unsigned long long* best = w.best + (size_t)(r & 1) * (size_t)w.npx;
+    scan_round<false>(w, best, r, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, s_wcnt, &s_base);
+}
+__global__ void __launch_bounds__(kUwThreads) uw_ghook(UwArgs a, UwWork w, int r) {
+    if (!w.flags[r]) return;
+    const unsigned long long* best = w.best + (size_t)(r & 1) * (size_t)w.npx;
+    unsigned long long* best_next = w.best + (size_t)((r + 1) & 1) * (size_t)w.npx;
+    hook_round<false>(a, w, best, best_next, r, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long kWaitNs = 500ull * 1000ull * 1000ull;  // a grid-wide wait gives up after 0.5 s
+constexpr unsigned int kWaitSpins = 1u << 24;                        // ... or after this many polls
+
+// Grid-wide barrier of the cooperative kernel uw_gtail: every CTA adds one to *ctr, the last one
+// to arrive (the barrier's index times the grid) publishes the index in *gen, on its own cache
+// line, and the others wait for it there. The wait is bounded: a CTA that gives up sets *stop
+// (counting the first give-up in *timeouts) and returns false, and so does every CTA that finds
+// *stop set while it waits, so the whole grid leaves the kernel at its next barrier at the latest.
+// Returns true when every CTA has arrived; their writes before it are then visible.
+__device__ bool grid_barrier(unsigned int* ctr, unsigned int* gen, unsigned int target, int32_t* stop,
+                             unsigned long long* timeouts) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int old = atomicAdd(ctr, 1u);
+        if (old + 1u == target) atomicExch(gen, target);
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        for (unsigned int it = 0; ld_acquire(gen) < target; ++it) {
+            if (*(volatile int32_t*)stop) {
+                ok = 0;
+                break;
+            }
+            if (it >= kWaitSpins || global_ns() - t0 > kWaitNs) {
+                if (atomicExch(stop, 1) == 0 && timeouts) atomicAdd(timeouts, 1ull);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Rounds r0 .. rounds - 1 in one cooperative launch (every CTA resident), the two halves of each
+// round separated by grid barriers: the tail of rounds with little work left, where separate
+// launches would cost more than the work. Returns at once when round r0 - 1 joined nothing, and
+// after the first round that joins nothing (every CTA reads the same flag after the same barrier).
+__global__ void __launch_bounds__(kUwThreads) uw_gtail(UwArgs a, UwWork w, int r0, int rounds) {
+    __shared__ int32_t s_wcnt[kUwThreads / 32];
+    __shared__ int32_t s_base;
+    const int32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    unsigned int target = 0;
+    for (int r = r0; r < rounds; ++r) {
+        if (!ldx<true>(w.flags + r)) return;
+        unsigned long long* best = w.best + (size_t)(r & 1) * (size_t)w.npx;
+        unsigned long long* best_next = w.best + (size_t)((r + 1) & 1) * (size_t)w.npx;
+        scan_round<true>(w, best, r, tid, stride, s_wcnt, &s_base);
+        target += gridDim.x;
+        if (!grid_barrier(w.sync, w.sync + 32, target, w.stop, a.timeouts)) return;
+        hook_round<true>(a, w, best, best_next, r, tid, stride);
+        target += gridDim.x;
+        if (!grid_barrier(w.sync, w.sync + 32, target, w.stop, a.timeouts)) return;
     }
 }
 
@@ -894,6 +1005,9 @@ UwWork carve(void* base, int64_t npx, int rounds) {
     w.nodes = reinterpret_cast<int32_t*>(take(4 * n));
     w.tile_start = reinterpret_cast<int32_t*>(take(4 * (n + 2)));  // a call has at most npx frames
     w.counts = reinterpret_cast<unsigned long long*>(take(8));
+    w.sync = reinterpret_cast<unsigned int*>(take(256));
+    w.stop = reinterpret_cast<int32_t*>(w.sync + 1);
+    w.npx = npx;
     w.flags = reinterpret_cast<int32_t*>(take(4 * (size_t)(rounds + 1)));
     w.ecount = reinterpret_cast<int32_t*>(take(4 * (size_t)(rounds + 1)));
     return w;
@@ -921,16 +1035,16 @@ size_t unwrap_workspace_bytes(int64_t npx, int64_t max_frame_nodes) {
     const int R = unwrap_rounds(max_frame_nodes);
     const size_t n = (size_t)npx;
     return align256(16 * n) + align256(8 * n) + 2 * align256(32 * n) + 10 * align256(4 * n) + align256(4 * (n + 2)) +
-           align256(8) + 2 * align256(4 * (size_t)(R + 1));
+           align256(8) + align256(256) + 2 * align256(4 * (size_t)(R + 1));
 }
 
 cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, int64_t max_frame_nodes,
                           const float* in, int64_t in_maps, float* out, int64_t out_maps, void* work,
-                          int* launches, cudaStream_t s) {
+                          int launched_rounds, unsigned long long* timeouts, int* launches, cudaStream_t s) {
     if (npx <= 0 || nframes <= 0) return cudaSuccess;
     const int R = unwrap_rounds(max_frame_nodes);
     UwWork w = carve(work, npx, R);
-    UwArgs a{d_frames, nframes, npx, in, in_maps, out, out_maps};
+    UwArgs a{d_frames, nframes, npx, in, in_maps, out, out_maps, timeouts};
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -943,19 +1057,41 @@ cudaError_t launch_unwrap(const FrameDev* d_frames, int nframes, int64_t npx, in
     // the global rounds: at most two listed edges per pixel
     const int64_t ewant = (2 * npx + kUwThreads - 1) / kUwThreads;
     const unsigned egrid = (unsigned)(ewant < (int64_t)sms * 8 ? ewant : (int64_t)sms * 8);
+    // The first half of the rounds bound as separate launches (each round at least halves the
+    // components that still have edges, but typically does much more, so the work is in the first
+    // rounds); the rest in one cooperative launch that stops after the first round that joins
+    // nothing (usually at once), every CTA resident.
+    const int R1 = launched_rounds < 0 ? (R + 1) / 2 : (launched_rounds < R ? launched_rounds : R);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, uw_gtail, kUwThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    const int64_t twant = ewant < (int64_t)sms * per_sm ? ewant : (int64_t)sms * per_sm;
     uw_prepare<<<1, kUwThreads, 0, s>>>(a, w, R);
     uw_init<<<grid, kUwThreads, 0, s>>>(a, w.wph, w.fid, w.rel);
-    cudaError_t e = cudaFuncSetAttribute(uw_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    e = cudaFuncSetAttribute(uw_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
     if (e != cudaSuccess) return e;
     uw_tiles<<<tgrid, kUwThreads, kTileSmem, s>>>(a, w);
     *launches += 3;
-    for (int r = 0; r < R; ++r) {
-        const int32_t* live = w.flags + r;
-        unsigned long long* bcur = w.best + (size_t)(r & 1) * (size_t)npx;
-        unsigned long long* bnext = w.best + (size_t)((r + 1) & 1) * (size_t)npx;
-        uw_gscan<<<egrid, kUwThreads, 0, s>>>(w, bcur, live, r);
-        uw_ghook<<<grid, kUwThreads, 0, s>>>(a, w, bcur, bnext, live, w.flags + r + 1);
+    for (int r = 0; r < R1; ++r) {
+        uw_gscan<<<egrid, kUwThreads, 0, s>>>(w, r);
+        uw_ghook<<<grid, kUwThreads, 0, s>>>(a, w, r);
         *launches += 2;
+    }
+    if (R1 < R) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)twant);
+        cfg.blockDim = dim3(kUwThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, uw_gtail, a, w, R1, R);
+        if (e != cudaSuccess) return e;
+        *launches += 1;
     }
     uw_anchor<<<grid, kUwThreads, 0, s>>>(w);
     uw_write<<<grid, kUwThreads, 0, s>>>(a, w);

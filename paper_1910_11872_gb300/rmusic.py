@@ -101,6 +101,7 @@ class rmusic_stats(ctypes.Structure):
         ("root_fallback_frac", ctypes.c_double),
         ("mean_polish_steps", ctypes.c_double),
         ("check_violations", ctypes.c_uint64),
+        ("wait_timeouts", ctypes.c_uint64),
     ]
 
 
@@ -175,6 +176,8 @@ def load_library(build_if_needed: bool = True) -> ctypes.CDLL:
         lib.rmusic_set_solver_variant.restype = ctypes.c_int
         lib.rmusic_unwrap_phase.argtypes = [vp, vp, ctypes.POINTER(rmusic_frame_desc), i32, vp, vp]
         lib.rmusic_unwrap_phase.restype = ctypes.c_int
+        lib.rmusic_unwrap_phase_sched.argtypes = [vp, vp, ctypes.POINTER(rmusic_frame_desc), i32, vp, i32, vp]
+        lib.rmusic_unwrap_phase_sched.restype = ctypes.c_int
         lib.rmusic_get_stats.argtypes = [vp, ctypes.POINTER(rmusic_stats)]
         lib.rmusic_get_stats.restype = ctypes.c_int
         _lib = lib
@@ -274,6 +277,16 @@ def rmusic_unwrap_phase(ctx, d_phase: int, descs, n_frames: int, d_out: int, cud
                                             cuda_stream or None)
     if rc != RMUSIC_OK:
         raise RmusicError(rc, "rmusic_unwrap_phase", rmusic_last_cuda_error(ctx))
+    return rc
+
+
+def rmusic_unwrap_phase_sched(ctx, d_phase: int, descs, n_frames: int, d_out: int, launched_rounds: int,
+                              cuda_stream: int | None) -> int:
+    arr = _desc_array(descs)
+    rc = load_library().rmusic_unwrap_phase_sched(ctx, d_phase or None, arr, int(n_frames), d_out or None,
+                                                  int(launched_rounds), cuda_stream or None)
+    if rc != RMUSIC_OK:
+        raise RmusicError(rc, "rmusic_unwrap_phase_sched", rmusic_last_cuda_error(ctx))
     return rc
 
 

@@ -101,5 +101,6 @@ def test_argument_checks_without_cuda(lib):
     bad = rmusic.make_params(unwrap=1)  # phase assembly needs the square geometry's alpha maps
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL
     assert L.rmusic_unwrap_phase(None, None, None, 1, None, None) == rmusic.RMUSIC_EINVAL
+    assert L.rmusic_unwrap_phase_sched(None, None, None, 1, None, -1, None) == rmusic.RMUSIC_EINVAL
     bad = rmusic.make_params(band_cross=0.5)
     assert L.rmusic_create(ctypes.byref(bad), 0, 0, ctypes.byref(ctx)) == rmusic.RMUSIC_EINVAL

@@ -44,21 +44,27 @@ def _anchored_k(k, valid):
     return out
 
 
-def gpu_unwrap(maps, in_place=False):
+def gpu_unwrap(maps, in_place=False, launched_rounds=-1):
     torch = _torch()
     dem = rmusic.Demodulator(geometry="square", half_width=1)
     try:
         flat = torch.from_numpy(np.concatenate([m.ravel() for m in maps]).astype(np.float32)).cuda()
         descs, _, n = rmusic.frame_descs([m.shape for m in maps], rmusic.RMUSIC_DTYPE_F32, 4)
         out = flat if in_place else torch.empty_like(flat)
-        rmusic.rmusic_unwrap_phase(dem.ctx, flat.data_ptr(), descs, len(maps), out.data_ptr(), None)
+        if launched_rounds == -1:
+            rmusic.rmusic_unwrap_phase(dem.ctx, flat.data_ptr(), descs, len(maps), out.data_ptr(), None)
+        else:
+            rmusic.rmusic_unwrap_phase_sched(dem.ctx, flat.data_ptr(), descs, len(maps), out.data_ptr(),
+                                             launched_rounds, None)
         torch.cuda.synchronize()
         o = out.cpu().numpy()
         res, off = [], 0
         for m in maps:
             res.append(o[off:off + m.size].reshape(m.shape))
             off += m.size
-        return res, dem.stats().kernel_launches
+        st = dem.stats()
+        assert st.wait_timeouts == 0  # no grid-wide wait of the cooperative rounds gave up
+        return res, st.kernel_launches
     finally:
         dem.close()
 
@@ -153,3 +159,25 @@ def test_square_path_with_unwrap_map():
     _, _, oal, ost, _ = O.square_demodulate(fr.image, O.make_params(carrier_freq=0.0), Lp)
     _, ko, _ = O.unwrap(oal.astype(np.float32))
     assert np.array_equal(k[valid].astype(np.int64), _anchored_k(ko, ~np.isnan(oal))[valid])
+
+
+@pytest.mark.parametrize("launched", [0, 1, 3, 64])
+def test_unwrap_schedules_agree(launched):
+    """Every split of the global rounds between separate launches and the cooperative kernel gives
+    the default's maps bit for bit (0: every round cooperative; 64: every round launched), on
+    noisy maps with residues of uneven sizes in one call, and the oracle's values."""
+    rng = np.random.default_rng(300)
+    maps = []
+    for H, W in ((96, 130), (41, 77), (128, 64)):
+        y, x = np.mgrid[0:H, 0:W]
+        w = _wrapf(0.05 * (x - 30) ** 2 / 7 + 0.4 * y + rng.normal(0, 1.0, (H, W)))
+        w[rng.random((H, W)) < 0.03] = np.nan
+        maps.append(w)
+    ref, n_ref = gpu_unwrap(maps)
+    got, n_got = gpu_unwrap(maps, launched_rounds=launched)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b, equal_nan=True)
+    for w, u in zip(maps, got):
+        _check_exact(w, u)
+    if launched == 0:
+        assert n_got == 6  # prepare, reliabilities, tiles, the cooperative rounds, anchors, output
