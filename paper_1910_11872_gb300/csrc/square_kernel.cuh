@@ -8,12 +8,14 @@
 //   alpha = angle of the block mean of Gamma_w exp(-j(omega_x x + omega_y y)) (Eq. 15), with
 //   x, y centred on the pixel.
 //
-// Work decomposition: one thread per pixel; each warp of a persistent grid takes one item from a
-// global atomic counter -- a 32 x 8 strip of pixels, or, once every frame's strips are taken, one
-// 32-pixel row of a frame's last eighth (short items at the end, so that the warps finish within
-// about one row of each other) -- stages its (32 + 2 Lp) x (rows + 2 Lp) analytic-signal samples
-// in its own part of shared memory with coalesced loads, and walks its rows top to bottom, each
-// lane reading its block from there. Items sit at absolute positions of their frame, so the warps
+// Work decomposition: one thread per pixel; each CTA of a persistent grid takes four consecutive
+// items from a global atomic counter, one per warp -- an item is a 32 x 8 strip of pixels, or, once
+// every frame's strips are taken, one 32-pixel row of a frame's last eighth (short items at the
+// end, so that the warps finish within about one row of each other). Each warp stages its item's
+// (32 + 2 Lp) x (rows + 2 Lp) analytic-signal samples in its own part of shared memory with
+// coalesced loads and walks its rows top to bottom, each lane reading its block from there; the
+// CTA's warps take each row in step (a barrier per row), so that they run the same code at the
+// same time (the kernel is bound by instruction fetch: 1.5 % faster than warps left to drift). Items sit at absolute positions of their frame, so the warps
 // -- and with them every warp-level iteration count and every start vector -- are the same
 // whether a frame runs alone or batched.
 //
@@ -63,7 +65,6 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
     static_assert(LP >= 1 && 2 * LP + 1 <= 2 * kMaxSquareLp + 1, "half-width out of range");
     constexpr int M = 2 * LP + 1;
     constexpr int SW = kSqTX + 2 * LP;     // staged columns
-    constexpr int SH = kSqTY + 2 * LP;     // staged rows
     constexpr int NST = square_stage_elems(LP);
     extern __shared__ __align__(16) unsigned char sq_smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -79,12 +80,14 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
     float2* const vec0 = scr + threadIdx.x;  // entry m at [m * kSqThreads]
     float2* const vec1 = vec0 + M * kSqThreads;
 
+    __shared__ long long sh_item;
     for (;;) {
-        __syncwarp();  // every lane is done with the previous strip's samples
-        long long item = 0;
-        if (lane == 0) item = (long long)atomicAdd(counter, 1ull);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= total_items) break;
+        __syncthreads();  // every warp is done with its previous item
+        if (threadIdx.x == 0) sh_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        if (sh_item * kSqWarps >= total_items) break;
+        const long long item = sh_item * kSqWarps + wid;
+        const bool active = item < total_items;
         // a strip (the first fr[0].item_start2 items) or one row of a frame's last rows
         const bool strip = item < fr[0].item_start2;
         const int f = strip ? find_frame(fr, nframes, (int64_t)item, [](const FrameDev& F) { return F.item_start; })
@@ -95,19 +98,19 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         const int q = (int)((uint32_t)local / (uint32_t)F.nchunks);
         const int tx = (int)((uint32_t)local % (uint32_t)F.nchunks);
         const int row0 = strip ? q * kSqTY : F.sq_strip_rows + q;
-        const int nrows = strip ? kSqTY : 1;
+        int nrows = !active ? 0 : strip ? kSqTY : 1;
         const int H = F.H, W = F.W;
         // every index below follows from these (the staged rows and each lane's block inside them
         // have compile-time extents); checked builds test them and skip a bad item whole (the item
         // is the warp's, so the skip is uniform)
-        if (!rm_check(f >= 0 && f < nframes && local >= 0 && F.L == LP && F.sq_strip_rows % kSqTY == 0 &&
+        if (active && !rm_check(f >= 0 && f < nframes && local >= 0 && F.L == LP && F.sq_strip_rows % kSqTY == 0 &&
                           (strip ? local < (int64_t)(F.sq_strip_rows / kSqTY) * F.nchunks
                                  : local < (int64_t)(H - F.sq_strip_rows) * F.nchunks),
                       args.counters))
-            continue;
+            nrows = 0;
 
         // ---- stage the item's samples (coalesced rows) -----------------------------------------
-        {
+        if (nrows > 0) {
             const int x0 = tx * kSqTX - LP, y0 = row0 - LP;
             // the analytic signal: the workspace (row-major, W per row), or a complex64 frame in place
             const float2* g = args.direct ? reinterpret_cast<const float2*>(args.direct + F.in_off) : gam + F.gam_off;
@@ -127,7 +130,9 @@ square_kernel(const FrameDev* __restrict__ fr, int nframes, int64_t total_items,
         bool prev_ok = false;
         float2* carry = vec1;
 #pragma unroll 1
-        for (int k = 0; k < nrows; ++k) {
+        for (int k = 0; k < kSqTY; ++k) {
+            __syncthreads();  // the CTA's warps walk their rows in step: one code region at a time
+            if (k >= nrows) continue;
             const int py = row0 + k;
             const bool inside = px < W && py < H;
             const bool valid = inside && px - LP >= 0 && px + LP < W && py - LP >= 0 && py + LP < H;
