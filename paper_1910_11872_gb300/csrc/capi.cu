@@ -135,7 +135,7 @@ int describe_frame(const rmusic_params& p, const rmusic_frame_desc& d, FrameDev*
     F->wlen = F->deriv_axis == 0 ? d.width : d.height;
     F->f0 = f0;
     if (square) {
-        F->nchunks = (d.width + kSqTX - 1) / kSqTX;  // tiles per tile row
+        F->nchunks = (d.width + kSqTX - 1) / kSqTX;  // 32-pixel items across a row
         F->omega_ref = 6.283185307179586476925 * f0;
     } else {
         F->rowp_shift = row_pixels_per_lane_shift(F->wlen);
